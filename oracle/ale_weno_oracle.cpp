@@ -1,0 +1,723 @@
+/*
+ * CPU oracle for the one-dimensional well-balanced finite-volume ALE-WENO hybrid
+ * scheme with hydrostatic reconstruction (Zhang, Xia & Xu, "Structure-preserving
+ * finite volume arbitrary Lagrangian-Eulerian WENO schemes for the shallow water
+ * equations", arXiv 2208.06588).
+ *
+ * TEST INFRASTRUCTURE. This file is the slow, plain reference that the CUDA path is
+ * checked against. Only the test suite, __graft_entry__.smoke() and the CPU-baseline /
+ * reference arm of bench.py may load it. It shares no code, header, table or helper with
+ * the CUDA library, and it never calls into it.
+ *
+ * Style: every small polynomial is obtained by solving the linear system that defines it
+ * (cell-average conditions, point-value conditions) with Gaussian elimination, and the
+ * steps follow the order in which the paper states them. FP64 throughout; built with
+ * -ffp-contract=off so that the compiler does not fuse multiply-adds.
+ *
+ * Where the paper leaves a choice open, the reading taken here is stated next to the code
+ * that implements it (the same readings are listed with their reasons in the design notes).
+ *
+ * The state path is templated on the scalar type T so that the same code, instantiated on
+ * a forward-mode dual number, gives the tangent-linear model. Mesh quantities (widths,
+ * node velocities, dt, alpha) stay double.
+ */
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+/* ------------------------------------------------------------------------------------ */
+/* Parameters (mirrored field by field by oracle/__init__.py).                           */
+/* ------------------------------------------------------------------------------------ */
+struct OrcParams {
+  double g;            // gravitational constant (Sec. 5 uses 9.812)
+  double cfl;          // CFL number in dt = cfl * min_j J_j / alpha
+  double eps_weno;     // epsilon of the smoothness detector and WENO-Z weights (Step 2, Eq. omegaj)
+  double eps_pp;       // positivity floor 1e-11 of the limiter (Eq. modifiedhjn)
+  double h_dry;        // an edge depth <= h_dry carries zero velocity
+  double mesh_T;       // period T of the prescribed motion x = xi + P sin(2 pi t / T)
+  double gauss_sigma;  // Gaussian filter width (cells) of the fluid-driven mesh velocity
+  double t_end;        // final time; the last step is clipped to it
+  double dt_fixed;     // > 0: every step uses this dt instead of the CFL formula
+  int32_t bc;          // 0 periodic, 1 transmissive, 2 reflective
+  int32_t mesh;        // 0 static, 1 prescribed profile motion, 2 fluid-driven Gaussian
+  int32_t gauss_half;  // truncation half-width of the Gaussian filter (nodes)
+  int32_t beta_dx_global;  // 1: Delta x in the smoothness indicators is max_j J_j (Step 1)
+};
+
+enum : uint32_t {
+  ST_EWEIGHT = 1u,     // a linear weight d_r <= 0 (the split of Shi-Hu-Shu is not applied)
+  ST_NEGDEPTH = 2u,    // a cell-average depth below -h_dry entered a stage
+  ST_NONFINITE = 4u,   // a non-finite value appeared
+  ST_EMESH = 8u,       // a cell width became <= 0 (mesh assumption A1 violated)
+};
+
+/* ------------------------------------------------------------------------------------ */
+/* Scalar helpers; overloaded for the dual type further down.                            */
+/* ------------------------------------------------------------------------------------ */
+inline double value(double x) { return x; }
+inline double vabs(double x) { return std::fabs(x); }
+inline double vsqrt(double x) { return std::sqrt(x); }
+// max/min returning the first argument on a tie (the tangent follows the first argument).
+inline double vmax(double a, double b) { return (b > a) ? b : a; }
+inline double vmin(double a, double b) { return (b < a) ? b : a; }
+
+/* Forward-mode dual number for the tangent-linear model. Kinks: |x|' = sign(x) with
+ * sign(0) = 0; max/min pass the tangent of the selected argument, the first on a tie. */
+struct Dual {
+  double v, d;
+  Dual() : v(0), d(0) {}
+  Dual(double a) : v(a), d(0) {}
+  Dual(double a, double b) : v(a), d(b) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) {
+  double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+inline double value(Dual x) { return x.v; }
+inline Dual vabs(Dual x) { return x.v > 0 ? x : (x.v < 0 ? -x : Dual(0.0, 0.0)); }
+inline Dual vsqrt(Dual x) {
+  double s = std::sqrt(x.v);
+  return Dual(s, s > 0 ? x.d / (2.0 * s) : 0.0);
+}
+inline Dual vmax(Dual a, Dual b) { return (b.v > a.v) ? b : a; }
+inline Dual vmin(Dual a, Dual b) { return (b.v < a.v) ? b : a; }
+
+inline double ipow(double x, int k) {
+  double r = 1.0;
+  for (int i = 0; i < k; ++i) r *= x;
+  return r;
+}
+
+/* Gaussian elimination with partial pivoting: solves A X = B in place (A n x n, B n x m,
+ * both row-major). The systems here are at most 5 x 5. */
+void gauss_solve(int n, double* A, double* B, int m) {
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[r * n + col]) > std::fabs(A[piv * n + col])) piv = r;
+    if (piv != col) {
+      for (int c = 0; c < n; ++c) std::swap(A[col * n + c], A[piv * n + c]);
+      for (int c = 0; c < m; ++c) std::swap(B[col * m + c], B[piv * m + c]);
+    }
+    for (int r = col + 1; r < n; ++r) {
+      double f = A[r * n + col] / A[col * n + col];
+      for (int c = col; c < n; ++c) A[r * n + c] -= f * A[col * n + c];
+      for (int c = 0; c < m; ++c) B[r * m + c] -= f * B[col * m + c];
+    }
+  }
+  for (int col = n - 1; col >= 0; --col) {
+    for (int c = 0; c < m; ++c) {
+      double s = B[col * m + c];
+      for (int k = col + 1; k < n; ++k) s -= A[col * n + k] * B[k * m + c];
+      B[col * m + c] = s / A[col * n + col];
+    }
+  }
+}
+
+/* Polynomial of degree n-1, p(t) = sum_k a_k t^k, whose averages over the n consecutive
+ * intervals [y_i, y_{i+1}] equal given data. Returns the linear map from the data to the
+ * coefficients: map[k * n + i] = d a_k / d ubar_i. (The definition of a reconstruction
+ * polynomial from cell averages, Step 1 of Sec. 2.2.) */
+void average_poly_map(int n, const double* y, double* map) {
+  double A[25], X[25];
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k)
+      A[i * n + k] = (ipow(y[i + 1], k + 1) - ipow(y[i], k + 1)) / ((k + 1) * (y[i + 1] - y[i]));
+  for (int i = 0; i < n * n; ++i) X[i] = 0.0;
+  for (int i = 0; i < n; ++i) X[i * n + i] = 1.0;
+  gauss_solve(n, A, X, n);
+  for (int i = 0; i < n * n; ++i) map[i] = X[i];
+}
+
+/* Mesh-only WENO data of one cell j, in the cell's own unit coordinate t = (x - x_{j-1/2}) / J_j
+ * (so the cell is [0, 1]). Inputs: the widths J_{j-2..j+2}. */
+struct WenoCoeffs {
+  double sub[3][9];   // sub[r][k*3+i]: coefficient a_k of p_r per unit of ubar_{j-r+i}
+  double c[2][3][3];  // c[e][r][i]: weight of ubar_{j-r+i} in p_r(t_e), e = 0 (t=0), 1 (t=1)
+  double big[2][5];   // weight of ubar_{j-2+i} in the quartic of the big stencil at t_e
+  double d[2][3];     // linear weights d_r at edge e
+};
+
+void weno_coeffs(const double* w5, WenoCoeffs& W) {
+  // Node coordinates of the big stencil S_j = {T_{j-2}, ..., T_{j+2}} in units of J_j.
+  double y[6];
+  y[2] = 0.0;
+  y[3] = 1.0;
+  y[1] = -w5[1] / w5[2];
+  y[0] = y[1] - w5[0] / w5[2];
+  y[4] = 1.0 + w5[3] / w5[2];
+  y[5] = y[4] + w5[4] / w5[2];
+  // Sub-stencil r covers cells j-r .. j-r+2, i.e. nodes y[2-r] .. y[5-r].
+  for (int r = 0; r < 3; ++r) average_poly_map(3, y + 2 - r, W.sub[r]);
+  double big[25];
+  average_poly_map(5, y, big);
+  for (int e = 0; e < 2; ++e) {
+    const double te = (double)e;
+    for (int r = 0; r < 3; ++r)
+      for (int i = 0; i < 3; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < 3; ++k) s += W.sub[r][k * 3 + i] * ipow(te, k);
+        W.c[e][r][i] = s;
+      }
+    for (int i = 0; i < 5; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < 5; ++k) s += big[k * 5 + i] * ipow(te, k);
+      W.big[e][i] = s;
+    }
+    // Linear weights: sum_r d_r p_r(t_e) equals the quartic at t_e. Only p_2 contains
+    // ubar_{j-2} and only p_0 contains ubar_{j+2}; matching those two coefficients fixes
+    // d_2 and d_0, and consistency (all weights of each polynomial sum to one) gives d_1.
+    W.d[e][2] = W.big[e][0] / W.c[e][2][0];
+    W.d[e][0] = W.big[e][4] / W.c[e][0][2];
+    W.d[e][1] = 1.0 - W.d[e][0] - W.d[e][2];
+  }
+}
+
+/* Smoothness indicator of Step 2 for the sub-stencil polynomial p_r of data v5, with the
+ * factor lam = Delta x / J_j carrying the global cell length into unit coordinates:
+ *   beta_r = sum_{l=1,2} (Delta x)^{2l-1} int_cell (d^l p_r / dx^l)^2 dx
+ *          = lam * int_0^1 (p_r')^2 dt + lam^3 * int_0^1 (p_r'')^2 dt. */
+template <class T>
+T beta_of(const WenoCoeffs& W, int r, const T* v5, double lam) {
+  T a1 = T(0.0), a2 = T(0.0);
+  for (int i = 0; i < 3; ++i) {
+    a1 += T(W.sub[r][1 * 3 + i]) * v5[2 - r + i];
+    a2 += T(W.sub[r][2 * 3 + i]) * v5[2 - r + i];
+  }
+  // p' = a1 + 2 a2 t on [0,1]: int (p')^2 = a1^2 + 2 a1 a2 + (4/3) a2^2 ; p'' = 2 a2.
+  T i1 = a1 * a1 + T(2.0) * a1 * a2 + T(4.0 / 3.0) * a2 * a2;
+  T i2 = T(4.0) * a2 * a2;
+  return T(lam) * i1 + T(lam * lam * lam) * i2;
+}
+
+/* Per-cell result of the reconstruction + limiter (cells -1 .. N). Edge e = 0 is the left
+ * edge x_{j-1/2}^+ of the cell, e = 1 the right edge x_{j+1/2}^-. */
+template <class T>
+struct EdgeVals {
+  T E[2], M[2], B[2];  // surface level, discharge, bottom (bottom re-derived after limiting)
+  T h[2], u[2];        // limited depth and velocity
+  uint8_t flag;        // 0 smooth, 1 transition, 2 non-smooth (Step 2)
+  double gamma;        // detector value
+};
+
+/* Ghost index map for the three ghost cells on each side. */
+int64_t ghost_src(int64_t i, int64_t N, int bc) {
+  if (bc == 0) return ((i % N) + N) % N;
+  if (i < 0) return -1 - i;
+  if (i >= N) return 2 * N - 1 - i;
+  return i;
+}
+
+/* Reconstruction (Steps 1-4 of Sec. 2.2 with the shared weights of Eq. alphamodified),
+ * then the bound-preserving limiter (Eq. modifiedhjn / xd in one dimension) and the
+ * bottom re-derivation of the Remark in Sec. 4.3. Returns the largest |u| + sqrt(g h)
+ * over the edges that touch interfaces 0..N (the wave-speed part of alpha, Eq. alpha2D). */
+template <class T>
+double reconstruct(const OrcParams& P, int64_t N, const T* E, const T* M, const T* B, const double* J,
+                   std::vector<EdgeVals<T>>& ed, uint32_t& status) {
+  const int64_t G = 3;
+  std::vector<T> Ex(N + 2 * G), Mx(N + 2 * G), Bx(N + 2 * G);
+  std::vector<double> Jx(N + 2 * G);
+  for (int64_t i = -G; i < N + G; ++i) {
+    int64_t s = ghost_src(i, N, P.bc);
+    Ex[i + G] = E[s];
+    Bx[i + G] = B[s];
+    Mx[i + G] = (P.bc == 2 && (i < 0 || i >= N)) ? -M[s] : M[s];
+    Jx[i + G] = J[s];
+  }
+  // Global cell length at this stage's mesh (Step 1: Delta x = max_j Delta_j).
+  double dxmax = 0.0;
+  for (int64_t j = 0; j < N; ++j) dxmax = std::max(dxmax, J[j]);
+
+  ed.assign(N + 2, EdgeVals<T>());
+  double A = 0.0;
+  for (int64_t j = -1; j <= N; ++j) {
+    const int64_t c = j + G;
+    double w5[5];
+    for (int k = 0; k < 5; ++k) w5[k] = Jx[c - 2 + k];
+    for (int k = 0; k < 5; ++k)
+      if (!(w5[k] > 0.0)) status |= ST_EMESH;
+    WenoCoeffs W;
+    weno_coeffs(w5, W);
+    for (int e = 0; e < 2; ++e)
+      for (int r = 0; r < 3; ++r)
+        if (!(W.d[e][r] > 0.0)) status |= ST_EWEIGHT;
+
+    T e5[5], m5[5], b5[5], h5[5];
+    for (int k = 0; k < 5; ++k) {
+      e5[k] = Ex[c - 2 + k];
+      m5[k] = Mx[c - 2 + k];
+      b5[k] = Bx[c - 2 + k];
+      h5[k] = e5[k] - b5[k];  // conservative variable h = eta - b (Eq. urec)
+    }
+    const double lam = P.beta_dx_global ? dxmax / w5[2] : 1.0;
+    // Step 2 with shared indicators: beta_r summed over the conservative variables (h, hu).
+    T beta[3];
+    for (int r = 0; r < 3; ++r) beta[r] = beta_of(W, r, h5, lam) + beta_of(W, r, m5, lam);
+    const T tau = vabs(beta[0] - beta[2]);
+    const T betaA = (beta[0] + beta[1] + beta[2]) / T(3.0);
+    const T gam = tau / (betaA + T(P.eps_weno));
+    // Reading of the overlapping ranges: smooth if gamma <= 1/2, non-smooth if gamma >= 1.
+    uint8_t flag = value(gam) <= 0.5 ? 0 : (value(gam) >= 1.0 ? 2 : 1);
+
+    EdgeVals<T>& o = ed[j + 1];
+    o.flag = flag;
+    o.gamma = value(gam);
+    for (int e = 0; e < 2; ++e) {
+      // Step 3: phi^L = d, phi^N = WENO-Z, phi^T = M(gamma) phi^N + (1 - M(gamma)) phi^L.
+      T phi[3];
+      if (flag == 0) {
+        for (int r = 0; r < 3; ++r) phi[r] = T(W.d[e][r]);
+      } else {
+        T al[3], s = T(0.0);
+        for (int r = 0; r < 3; ++r) {
+          T q = tau / (beta[r] + T(P.eps_weno));
+          al[r] = T(W.d[e][r]) * (T(1.0) + q * q);
+          s += al[r];
+        }
+        for (int r = 0; r < 3; ++r) phi[r] = al[r] / s;
+        if (flag == 1) {
+          T Mg = T(2.0) * gam - T(1.0);
+          for (int r = 0; r < 3; ++r) phi[r] = Mg * phi[r] + (T(1.0) - Mg) * T(W.d[e][r]);
+        }
+      }
+      // Step 4 with the same weights for eta, hu and b (Sec. 4.1 items 1-2).
+      T ve = T(0.0), vm = T(0.0), vb = T(0.0);
+      for (int r = 0; r < 3; ++r) {
+        T pe = T(0.0), pm = T(0.0), pb = T(0.0);
+        for (int i = 0; i < 3; ++i) {
+          pe += T(W.c[e][r][i]) * e5[2 - r + i];
+          pm += T(W.c[e][r][i]) * m5[2 - r + i];
+          pb += T(W.c[e][r][i]) * b5[2 - r + i];
+        }
+        ve += phi[r] * pe;
+        vm += phi[r] * pm;
+        vb += phi[r] * pb;
+      }
+      o.E[e] = ve;
+      o.M[e] = vm;
+      o.B[e] = vb;
+    }
+
+    // Bound-preserving limiter in 1D: 4-point Gauss-Lobatto rule (k >= (p+2)/2 with p = 5),
+    // end weights sigma_1 = sigma_4 = 1/12. The interior mean delta follows from
+    // hbar = (1 - 2/12) delta + (h^L + h^R)/12.
+    T hbar = e5[2] - b5[2];
+    if (value(hbar) < -P.h_dry) status |= ST_NEGDEPTH;
+    // Reading: a rounding-level negative mean in a dry cell is treated as zero.
+    if (value(hbar) < 0.0) hbar = T(0.0);
+    T hL = o.E[0] - o.B[0], hR = o.E[1] - o.B[1];
+    T delta = (T(12.0) * hbar - hL - hR) / T(10.0);
+    T mn = vmin(vmin(hL, hR), delta);
+    T epsv = vmin(T(P.eps_pp), hbar);
+    T theta = T(1.0);
+    if (value(mn) < value(epsv)) theta = (hbar - epsv) / (hbar - mn);
+    hL = theta * (hL - hbar) + hbar;
+    hR = theta * (hR - hbar) + hbar;
+    o.h[0] = hL;
+    o.h[1] = hR;
+    // Reading: the discharge edge values are scaled about their mean with the same theta
+    // (the positivity limiter of the cited Xing-Zhang-Shu scheme acts on (h, hu) together),
+    // so that u = hu / h stays bounded where h is pulled towards the floor.
+    const T mbar = m5[2];
+    o.M[0] = theta * (o.M[0] - mbar) + mbar;
+    o.M[1] = theta * (o.M[1] - mbar) + mbar;
+    // Remark of Sec. 4.3: b^new = eta - h^new; eta itself is left untouched.
+    o.B[0] = o.E[0] - hL;
+    o.B[1] = o.E[1] - hR;
+    for (int e = 0; e < 2; ++e) {
+      o.u[e] = (value(o.h[e]) > P.h_dry) ? o.M[e] / o.h[e] : T(0.0);
+      if (!std::isfinite(value(o.E[e])) || !std::isfinite(value(o.M[e])) || !std::isfinite(value(o.h[e])))
+        status |= ST_NONFINITE;
+    }
+    // Wave speed over the edges that touch interfaces 0..N.
+    for (int e = 0; e < 2; ++e) {
+      if ((j == -1 && e == 0) || (j == N && e == 1)) continue;
+      double hpos = std::max(value(o.h[e]), 0.0);
+      double s = std::fabs(value(o.u[e])) + std::sqrt(P.g * hpos);
+      A = std::max(A, s);
+    }
+  }
+  return A;
+}
+
+/* Four-point Gauss-Legendre rule on [0, 1] (exact to degree 7). */
+void gauss_legendre4(double* t, double* wq) {
+  const double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
+  const double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
+  const double wa = (18.0 + std::sqrt(30.0)) / 36.0, wb = (18.0 - std::sqrt(30.0)) / 36.0;
+  t[0] = 0.5 * (1.0 - b); wq[0] = 0.5 * wb;
+  t[1] = 0.5 * (1.0 - a); wq[1] = 0.5 * wa;
+  t[2] = 0.5 * (1.0 + a); wq[2] = 0.5 * wa;
+  t[3] = 0.5 * (1.0 + b); wq[3] = 0.5 * wb;
+}
+
+/* Source interpolant (Sec. 4.1, after Eq. HH2D): the quartic on cell j that matches the
+ * averages on cells j-1, j, j+1 and the two edge values of cell j. Reading: "interpolating
+ * fourth-order polynomials" = these five conditions, so that at rest eta_h is constant and
+ * b_h takes the same edge values as the flux side. Returns the coefficient map
+ * map[k*5 + i] for data (avg_{j-1}, avg_j, avg_{j+1}, v^L, v^R), unit coordinate t. */
+void source_interp_map(double rm, double rp, double* map) {
+  const double y[4] = {-rm, 0.0, 1.0, 1.0 + rp};
+  double A[25], X[25];
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 5; ++k)
+      A[i * 5 + k] = (ipow(y[i + 1], k + 1) - ipow(y[i], k + 1)) / ((k + 1) * (y[i + 1] - y[i]));
+  for (int k = 0; k < 5; ++k) {
+    A[3 * 5 + k] = ipow(0.0, k);
+    A[4 * 5 + k] = ipow(1.0, k);
+  }
+  for (int i = 0; i < 25; ++i) X[i] = 0.0;
+  for (int i = 0; i < 5; ++i) X[i * 5 + i] = 1.0;
+  gauss_solve(5, A, X, 5);
+  for (int i = 0; i < 25; ++i) map[i] = X[i];
+}
+
+/* Right-hand side of the well-balanced semi-discrete scheme (Eq. hydro2D-HH2D and
+ * Eq. bottomrk in 1D) for all cells 0..N-1, given the limited edge values, the node
+ * velocities w[0..N] and the global viscosity alpha. */
+template <class T>
+void rhs(const OrcParams& P, int64_t N, const std::vector<EdgeVals<T>>& ed, const T* E, const T* M, const T* B,
+         const double* J, const double* w, double alpha, T* RE, T* RM, T* RB) {
+  (void)M;
+  const double g = P.g;
+  // Interface k: L = right edge of cell k-1 (ed[k]), R = left edge of cell k (ed[k+1]).
+  std::vector<T> FE(N + 1), FMm(N + 1), FMp(N + 1), FB(N + 1);
+  for (int64_t k = 0; k <= N; ++k) {
+    const EdgeVals<T>& l = ed[k];
+    const EdgeVals<T>& r = ed[k + 1];
+    const T EL = l.E[1], ER = r.E[0], BL = l.B[1], BR = r.B[0];
+    const T hL = l.h[1], hR = r.h[0], uL = l.u[1], uR = r.u[0];
+    const T wk = T(w[k]), al = T(alpha);
+    // Hydrostatic reconstruction (Eq. HH2D): h*,+- = max(0, eta+- - max(b+, b-)).
+    const T bstar = vmax(BL, BR);
+    const T sL = vmax(T(0.0), EL - bstar), sR = vmax(T(0.0), ER - bstar);
+    // Reading: the starred discharge is h* u (hydrostatic reconstruction of the cited
+    // well-balanced scheme); the literal hu+- is singular where h* = 0.
+    const T mL = sL * uL, mR = sR * uR;
+    const T etasL = sL + BL, etasR = sR + BR;  // eta*,+- = h*,+- + b+-
+    // First component: LF flux of H = F(q*) - w q* plus the correction theta (Eq. HH2D).
+    const T H1 = T(0.5) * ((mL - wk * etasL) + (mR - wk * etasR)) - T(0.5) * al * (etasR - etasL);
+    const T theta = T(0.5) * (wk + al) * (etasR - ER) + T(0.5) * (wk - al) * (etasL - EL);
+    FE[k] = H1 + theta;
+    // Second component: LF flux of q*, plus the cell-sided pressure correction.
+    const T H2 = T(0.5) * ((mL * uL + T(0.5 * g) * sL * sL - wk * mL) + (mR * uR + T(0.5 * g) * sR * sR - wk * mR)) -
+                 T(0.5) * al * (mR - mL);
+    FMm[k] = H2 + T(0.5 * g) * (hL * hL - sL * sL);  // seen by cell k-1 (outward normal +1)
+    FMp[k] = H2 + T(0.5 * g) * (hR * hR - sR * sR);  // seen by cell k (outward normal -1)
+    // Bottom flux of Eq. bottomrk: B = 1/2 w.n (b- + b+) + 1/2 alpha (b+ - b-), taken for
+    // cell k-1 (n = +1); cell k sees its negative.
+    FB[k] = T(0.5) * wk * (BL + BR) + T(0.5) * al * (BR - BL);
+  }
+  double tq[4], wq[4];
+  gauss_legendre4(tq, wq);
+  const int64_t G = 3;
+  (void)G;
+  for (int64_t j = 0; j < N; ++j) {
+    // Source term: int_cell -g (eta_h - b_h) b_h' dx, 4-point Gauss-Legendre in the unit
+    // coordinate (dx = J dt and d/dx = (1/J) d/dt cancel).
+    const int64_t jm = ghost_src(j - 1, N, P.bc), jp = ghost_src(j + 1, N, P.bc);
+    const double rm = J[jm] / J[j], rp = J[jp] / J[j];
+    double map[25];
+    source_interp_map(rm, rp, map);
+    const EdgeVals<T>& c = ed[j + 1];
+    const T edat[5] = {E[jm], E[j], E[jp], c.E[0], c.E[1]};
+    const T bdat[5] = {B[jm], B[j], B[jp], c.B[0], c.B[1]};
+    T ea[5], ba[5];
+    for (int k = 0; k < 5; ++k) {
+      ea[k] = T(0.0);
+      ba[k] = T(0.0);
+      for (int i = 0; i < 5; ++i) {
+        ea[k] += T(map[k * 5 + i]) * edat[i];
+        ba[k] += T(map[k * 5 + i]) * bdat[i];
+      }
+    }
+    T S = T(0.0);
+    for (int q = 0; q < 4; ++q) {
+      T eh = T(0.0), bh = T(0.0), dbh = T(0.0);
+      for (int k = 0; k < 5; ++k) {
+        eh += ea[k] * T(ipow(tq[q], k));
+        bh += ba[k] * T(ipow(tq[q], k));
+        if (k > 0) dbh += T((double)k * ipow(tq[q], k - 1)) * ba[k];
+      }
+      S += T(wq[q]) * (eh - bh) * dbh;
+    }
+    S = T(-g) * S;
+    RE[j] = -(FE[j + 1] - FE[j]);
+    RM[j] = -(FMm[j + 1] - FMp[j]) + S;
+    RB[j] = FB[j + 1] - FB[j];
+  }
+}
+
+/* Fluid-driven node velocity: raw node velocity = mean of the adjacent cell velocities
+ * (dry cells carry zero), smoothed by a truncated, renormalised Gaussian; end nodes fixed. */
+template <class T>
+void fluid_gauss_velocity(const OrcParams& P, int64_t N, const T* E, const T* M, const T* B, std::vector<double>& w) {
+  std::vector<double> u(N), raw(N + 1, 0.0);
+  for (int64_t j = 0; j < N; ++j) {
+    double h = value(E[j]) - value(B[j]);
+    u[j] = (h > P.h_dry) ? value(M[j]) / h : 0.0;
+  }
+  for (int64_t k = 1; k < N; ++k) raw[k] = 0.5 * (u[k - 1] + u[k]);
+  w.assign(N + 1, 0.0);
+  const int K = P.gauss_half;
+  std::vector<double> gw(2 * K + 1);
+  for (int m = -K; m <= K; ++m) gw[m + K] = std::exp(-(double)(m * m) / (2.0 * P.gauss_sigma * P.gauss_sigma));
+  for (int64_t k = 1; k < N; ++k) {
+    double s = 0.0, sw = 0.0;
+    for (int m = -K; m <= K; ++m) {
+      int64_t q = k + m;
+      if (q < 1 || q > N - 1) continue;
+      s += gw[m + K] * raw[q];
+      sw += gw[m + K];
+    }
+    w[k] = s / sw;
+  }
+}
+
+/* One step of the modified third-order SSP-RK method (Eq. RK32D) with the width recursion
+ * (Eq. Jacobi2D). State: E = eta bar, M = hu bar, B = b bar, J = cell widths, x = nodes.
+ * prof[0..N] is the node profile of the prescribed motion. When alpha_io / dt_io are given
+ * with replay = 1, the recorded dt and alpha are used (tangent-linear replay). */
+template <class T>
+uint32_t ssprk3_step(const OrcParams& P, int64_t N, T* E, T* M, T* B, double* J, double* x, const double* prof,
+                     double* t, double* dt_out, uint8_t* flags, double* alpha_rec, int replay) {
+  uint32_t st = 0;
+  std::vector<EdgeVals<T>> ed;
+  std::vector<double> w(N + 1, 0.0);
+  double Wbar = 0.0;
+  if (P.mesh == 2) {
+    fluid_gauss_velocity(P, N, E, M, B, w);
+    for (int64_t k = 0; k <= N; ++k) Wbar = std::max(Wbar, std::fabs(w[k]));
+  } else if (P.mesh == 1) {
+    double pm = 0.0;
+    for (int64_t k = 0; k <= N; ++k) pm = std::max(pm, std::fabs(prof[k]));
+    // Secant speeds of x = xi + P sin(2 pi t / T) are bounded by (2 pi / T) max |P|.
+    Wbar = 2.0 * M_PI / P.mesh_T * pm;
+  }
+
+  // Stage 1 on the mesh at t_n.
+  double A1 = reconstruct(P, N, E, M, B, J, ed, st);
+  if (flags)
+    for (int64_t j = 0; j < N; ++j) flags[j] = ed[j + 1].flag;
+  double alpha1 = A1 + Wbar;
+  double dt;
+  if (replay) {
+    dt = *dt_out;
+    alpha1 = alpha_rec[0];
+  } else if (P.dt_fixed > 0.0) {
+    dt = P.dt_fixed;
+  } else {
+    double jmin = J[0];
+    for (int64_t j = 1; j < N; ++j) jmin = std::min(jmin, J[j]);
+    dt = P.cfl * jmin / alpha1;
+    if (P.mesh == 2) {
+      double dwmax = 0.0;
+      for (int64_t j = 0; j < N; ++j) dwmax = std::max(dwmax, std::fabs(w[j + 1] - w[j]));
+      if (dwmax > 0.0) dt = std::min(dt, 0.5 * jmin / dwmax);
+    }
+    if (P.t_end > 0.0) dt = std::min(dt, P.t_end - *t);
+  }
+  if (P.mesh == 1) {
+    // Node speed (Eq. w1D): secant of the prescribed trajectory over [t_n, t_n + dt].
+    const double s0 = std::sin(2.0 * M_PI * (*t) / P.mesh_T);
+    const double s1 = std::sin(2.0 * M_PI * (*t + dt) / P.mesh_T);
+    for (int64_t k = 0; k <= N; ++k) w[k] = prof[k] * (s1 - s0) / dt;
+  }
+  // Widths along the linear rays (Eq. Jacobi2D with div w J = w_{j+1/2} - w_{j-1/2}).
+  std::vector<double> dw(N), J1(N), J2(N), J3(N);
+  for (int64_t j = 0; j < N; ++j) {
+    dw[j] = w[j + 1] - w[j];
+    J1[j] = J[j] + dt * dw[j];
+    J2[j] = 0.75 * J[j] + 0.25 * J1[j] + 0.25 * dt * dw[j];
+    J3[j] = (1.0 / 3.0) * J[j] + (2.0 / 3.0) * J2[j] + (2.0 / 3.0) * dt * dw[j];
+    if (!(J1[j] > 0.0) || !(J2[j] > 0.0) || !(J3[j] > 0.0)) st |= ST_EMESH;
+  }
+  std::vector<T> R_E(N), R_M(N), R_B(N), Y1E(N), Y1M(N), Y1B(N), Y2E(N), Y2M(N), Y2B(N);
+  std::vector<T> qE(N), qM(N), qB(N);
+  rhs(P, N, ed, E, M, B, J, w.data(), alpha1, R_E.data(), R_M.data(), R_B.data());
+  for (int64_t j = 0; j < N; ++j) {
+    Y1E[j] = T(J[j]) * E[j] + T(dt) * R_E[j];
+    Y1M[j] = T(J[j]) * M[j] + T(dt) * R_M[j];
+    Y1B[j] = T(J[j]) * B[j] + T(dt) * R_B[j];
+    qE[j] = Y1E[j] / T(J1[j]);
+    qM[j] = Y1M[j] / T(J1[j]);
+    qB[j] = Y1B[j] / T(J1[j]);
+  }
+  // Stage 2 on the mesh at t_{n,1} = t_{n+1}.
+  double A2 = reconstruct(P, N, qE.data(), qM.data(), qB.data(), J1.data(), ed, st);
+  double alpha2 = replay ? alpha_rec[1] : A2 + Wbar;
+  rhs(P, N, ed, qE.data(), qM.data(), qB.data(), J1.data(), w.data(), alpha2, R_E.data(), R_M.data(), R_B.data());
+  for (int64_t j = 0; j < N; ++j) {
+    Y2E[j] = T(0.75) * (T(J[j]) * E[j]) + T(0.25) * (Y1E[j] + T(dt) * R_E[j]);
+    Y2M[j] = T(0.75) * (T(J[j]) * M[j]) + T(0.25) * (Y1M[j] + T(dt) * R_M[j]);
+    Y2B[j] = T(0.75) * (T(J[j]) * B[j]) + T(0.25) * (Y1B[j] + T(dt) * R_B[j]);
+    qE[j] = Y2E[j] / T(J2[j]);
+    qM[j] = Y2M[j] / T(J2[j]);
+    qB[j] = Y2B[j] / T(J2[j]);
+  }
+  // Stage 3 on the mesh at t_{n,2} = (t_n + t_{n+1}) / 2.
+  double A3 = reconstruct(P, N, qE.data(), qM.data(), qB.data(), J2.data(), ed, st);
+  double alpha3 = replay ? alpha_rec[2] : A3 + Wbar;
+  rhs(P, N, ed, qE.data(), qM.data(), qB.data(), J2.data(), w.data(), alpha3, R_E.data(), R_M.data(), R_B.data());
+  for (int64_t j = 0; j < N; ++j) {
+    T Y3E = T(1.0 / 3.0) * (T(J[j]) * E[j]) + T(2.0 / 3.0) * (Y2E[j] + T(dt) * R_E[j]);
+    T Y3M = T(1.0 / 3.0) * (T(J[j]) * M[j]) + T(2.0 / 3.0) * (Y2M[j] + T(dt) * R_M[j]);
+    T Y3B = T(1.0 / 3.0) * (T(J[j]) * B[j]) + T(2.0 / 3.0) * (Y2B[j] + T(dt) * R_B[j]);
+    E[j] = Y3E / T(J3[j]);
+    M[j] = Y3M / T(J3[j]);
+    B[j] = Y3B / T(J3[j]);
+    J[j] = J3[j];
+  }
+  for (int64_t k = 0; k <= N; ++k) x[k] = x[k] + dt * w[k];
+  *t += dt;
+  *dt_out = dt;
+  if (alpha_rec && !replay) {
+    alpha_rec[0] = alpha1;
+    alpha_rec[1] = alpha2;
+    alpha_rec[2] = alpha3;
+  }
+  return st;
+}
+
+OrcParams to_params(const double* p, const int32_t* ip) {
+  OrcParams P;
+  P.g = p[0]; P.cfl = p[1]; P.eps_weno = p[2]; P.eps_pp = p[3]; P.h_dry = p[4];
+  P.mesh_T = p[5]; P.gauss_sigma = p[6]; P.t_end = p[7]; P.dt_fixed = p[8];
+  P.bc = ip[0]; P.mesh = ip[1]; P.gauss_half = ip[2]; P.beta_dx_global = ip[3];
+  return P;
+}
+
+}  // namespace
+
+/* ------------------------------------------------------------------------------------ */
+/* C entry points used by oracle/__init__.py (ctypes). Parameters are passed as a double  */
+/* array p[9] = {g, cfl, eps_weno, eps_pp, h_dry, mesh_T, gauss_sigma, t_end, dt_fixed}   */
+/* and an int array ip[4] = {bc, mesh, gauss_half, beta_dx_global}.                       */
+/* ------------------------------------------------------------------------------------ */
+extern "C" {
+
+/* Mesh-only WENO data of one cell from the five widths J_{j-2..j+2}: c[2][3][3], d[2][3],
+ * big[2][5] (weights of the quartic at the two edges), sub[3][9] (coefficient maps). */
+void orc_weno_coeffs(const double* w5, double* c, double* d, double* big, double* sub) {
+  WenoCoeffs W;
+  weno_coeffs(w5, W);
+  std::memcpy(c, W.c, sizeof(W.c));
+  std::memcpy(d, W.d, sizeof(W.d));
+  std::memcpy(big, W.big, sizeof(W.big));
+  std::memcpy(sub, W.sub, sizeof(W.sub));
+}
+
+/* Smoothness indicators beta_r (r = 0,1,2) of data v5 on widths w5 with lam = Dx / J_j. */
+void orc_beta(const double* w5, const double* v5, double lam, double* beta) {
+  WenoCoeffs W;
+  weno_coeffs(w5, W);
+  for (int r = 0; r < 3; ++r) beta[r] = beta_of(W, r, v5, lam);
+}
+
+/* Source-interpolant coefficient map (5 x 5) for neighbour width ratios rm, rp. */
+void orc_source_map(double rm, double rp, double* map) { source_interp_map(rm, rp, map); }
+
+/* Reconstruction + limiter of one stage. edges: 10 arrays of N+2 (cells -1..N):
+ * E_L, E_R, M_L, M_R, B_L, B_R, h_L, h_R, u_L, u_R. flags[N+2], gamma[N+2].
+ * Returns the largest edge wave speed |u| + sqrt(g h); status in *st. */
+double orc_reconstruct(const double* p, const int32_t* ip, int64_t N, const double* E, const double* M,
+                       const double* B, const double* J, double* edges, uint8_t* flags, double* gamma,
+                       uint32_t* st) {
+  OrcParams P = to_params(p, ip);
+  std::vector<EdgeVals<double>> ed;
+  uint32_t s = 0;
+  double A = reconstruct(P, N, E, M, B, J, ed, s);
+  const int64_t n2 = N + 2;
+  for (int64_t i = 0; i < n2; ++i) {
+    const EdgeVals<double>& o = ed[i];
+    edges[0 * n2 + i] = o.E[0]; edges[1 * n2 + i] = o.E[1];
+    edges[2 * n2 + i] = o.M[0]; edges[3 * n2 + i] = o.M[1];
+    edges[4 * n2 + i] = o.B[0]; edges[5 * n2 + i] = o.B[1];
+    edges[6 * n2 + i] = o.h[0]; edges[7 * n2 + i] = o.h[1];
+    edges[8 * n2 + i] = o.u[0]; edges[9 * n2 + i] = o.u[1];
+    if (flags) flags[i] = o.flag;
+    if (gamma) gamma[i] = o.gamma;
+  }
+  if (st) *st = s;
+  return A;
+}
+
+/* Semi-discrete right-hand side of one stage for given node velocities w[0..N] and alpha
+ * (alpha <= 0: alpha = max edge wave speed + Wbar with Wbar = max |w|). */
+uint32_t orc_rhs(const double* p, const int32_t* ip, int64_t N, const double* E, const double* M, const double* B,
+                 const double* J, const double* w, double alpha, double* RE, double* RM, double* RB,
+                 double* alpha_used) {
+  OrcParams P = to_params(p, ip);
+  std::vector<EdgeVals<double>> ed;
+  uint32_t s = 0;
+  double A = reconstruct(P, N, E, M, B, J, ed, s);
+  if (!(alpha > 0.0)) {
+    double wb = 0.0;
+    for (int64_t k = 0; k <= N; ++k) wb = std::max(wb, std::fabs(w[k]));
+    alpha = A + wb;
+  }
+  rhs(P, N, ed, E, M, B, J, w, alpha, RE, RM, RB);
+  if (alpha_used) *alpha_used = alpha;
+  return s;
+}
+
+/* nsteps steps (or until t reaches t_end > 0) of the fully discrete scheme, in place.
+ * flags[N]: stage-1 flags of the last step (may be null). dts[nsteps], alphas[3*nsteps]:
+ * recorded dt and stage alphas (may be null). Returns the OR of all status bits. */
+uint32_t orc_run(const double* p, const int32_t* ip, int64_t N, double* E, double* M, double* B, double* J,
+                 double* x, const double* prof, double* t, int64_t nsteps, int64_t* steps_done, uint8_t* flags,
+                 double* dts, double* alphas) {
+  OrcParams P = to_params(p, ip);
+  uint32_t st = 0;
+  int64_t n = 0;
+  for (; n < nsteps; ++n) {
+    if (P.t_end > 0.0 && *t >= P.t_end) break;
+    double dt = 0.0, al[3] = {0, 0, 0};
+    st |= ssprk3_step<double>(P, N, E, M, B, J, x, prof, t, &dt, flags, al, 0);
+    if (dts) dts[n] = dt;
+    if (alphas) { alphas[3 * n] = al[0]; alphas[3 * n + 1] = al[1]; alphas[3 * n + 2] = al[2]; }
+    if (st & (ST_NONFINITE | ST_EMESH)) { ++n; break; }
+  }
+  if (steps_done) *steps_done = n;
+  return st;
+}
+
+/* Tangent-linear model of nsteps steps in replay mode: dt and the stage alphas are the
+ * recorded ones (dts, alphas from orc_run), flags and limiter branches follow the base
+ * trajectory. (dE, dM, dB) is the perturbation on entry and its image on exit. The mesh
+ * is prescribed (static or profile motion), so widths and nodes carry no tangent. */
+uint32_t orc_tangent(const double* p, const int32_t* ip, int64_t N, double* E, double* M, double* B, double* J,
+                     double* x, const double* prof, double* t, int64_t nsteps, const double* dts,
+                     const double* alphas, double* dE, double* dM, double* dB) {
+  OrcParams P = to_params(p, ip);
+  if (P.mesh == 2) return 0xffffffffu;  // fluid-driven motion would need tangent widths
+  std::vector<Dual> e(N), m(N), b(N);
+  for (int64_t j = 0; j < N; ++j) {
+    e[j] = Dual(E[j], dE[j]);
+    m[j] = Dual(M[j], dM[j]);
+    b[j] = Dual(B[j], dB[j]);
+  }
+  uint32_t st = 0;
+  for (int64_t n = 0; n < nsteps; ++n) {
+    double dt = dts[n];
+    double al[3] = {alphas[3 * n], alphas[3 * n + 1], alphas[3 * n + 2]};
+    st |= ssprk3_step<Dual>(P, N, e.data(), m.data(), b.data(), J, x, prof, t, &dt, nullptr, al, 1);
+  }
+  for (int64_t j = 0; j < N; ++j) {
+    E[j] = e[j].v; M[j] = m[j].v; B[j] = b[j].v;
+    dE[j] = e[j].d; dM[j] = m[j].d; dB[j] = b[j].d;
+  }
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+"""Seeded synthetic inputs for the 1D ALE-WENO shallow-water solver.
+
+This module only builds input data: node coordinates, cell averages of analytic initial
+conditions (5-point Gauss-Legendre per cell, split at discontinuities), prescribed mesh
+motion profiles and scheme constants. It contains none of the scheme's arithmetic and is
+the one module that both the CUDA path's callers and the CPU oracle's callers share.
+
+Every problem returns a ``Problem``: cell averages (h, hu, b), the surface level
+E = h + b, nodes x[0..N], widths J = diff(x), the node profile P of the prescribed motion
+x_k(t) = xi_k + P_k sin(2 pi t / T) (zeros when the mesh is static or fluid-driven) and the
+constants (g, CFL, boundary condition, mesh kind, T, t_end).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+G_PAPER = 9.812  # Sec. 5
+MASTER_SEED = 20220812
+
+_GL5_X = np.array([-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831, 0.9061798459386640])
+_GL5_W = np.array([0.2369268850561891, 0.4786286704993665, 0.5688888888888889, 0.4786286704993665,
+                   0.2369268850561891])
+
+
+def cell_averages(f, x, breaks=()):
+    """Cell averages of f over [x_j, x_{j+1}] by 5-point Gauss-Legendre, splitting each cell
+    at the given discontinuity points so that piecewise-smooth data is integrated exactly
+    enough."""
+    x = np.asarray(x, dtype=np.float64)
+    a, b = x[:-1], x[1:]
+    pts = [a] + [np.clip(np.full_like(a, c), a, b) for c in sorted(breaks)] + [b]
+    total = np.zeros_like(a)
+    for lo, hi in zip(pts[:-1], pts[1:]):
+        half, mid = 0.5 * (hi - lo), 0.5 * (hi + lo)
+        for xq, wq in zip(_GL5_X, _GL5_W):
+            total += wq * half * f(mid + half * xq)
+    return total / (b - a)
+
+
+@dataclass
+class Problem:
+    name: str
+    x: np.ndarray
+    h: np.ndarray
+    hu: np.ndarray
+    b: np.ndarray
+    E: np.ndarray
+    profile: np.ndarray
+    bc: str
+    mesh: str
+    mesh_T: float = 1.0
+    t_end: float = 0.0
+    cfl: float = 0.6
+    g: float = G_PAPER
+    eps_weno: float = 1e-6
+    gauss_sigma: float = 8.0
+    gauss_half: int = 24
+    dt_fixed: float = 0.0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def N(self):
+        return self.h.size
+
+    @property
+    def J(self):
+        return np.diff(self.x)
+
+
+def _uniform(a, b, N):
+    return a + (b - a) * np.arange(N + 1, dtype=np.float64) / N
+
+
+def _paper_motion_profile(xi, xmin, xmax):
+    """Node profile of the paper's default 1D motion (Sec. 5, Eq. wangge1):
+    x(t) = xi + sin(2 pi t / t_end) (xi - xmax)(xi - xmin) / (3 (xmax - xmin)^2)."""
+    return (xi - xmax) * (xi - xmin) / (3.0 * (xmax - xmin) ** 2)
+
+
+def _sine_profile(xi, xmin, xmax, A):
+    """x(t) = xi + A sin(2 pi (xi - xmin) / L) sin(2 pi t / T)."""
+    p = A * np.sin(2.0 * np.pi * (xi - xmin) / (xmax - xmin))
+    p[0] = 0.0
+    p[-1] = 0.0
+    return p
+
+
+def _make(name, x, hf, huf, bf, breaks=(), lake_level=None, **kw):
+    b = cell_averages(bf, x, breaks)
+    hu = cell_averages(huf, x, breaks)
+    if lake_level is not None:
+        E = np.full_like(b, float(lake_level))
+        h = E - b
+    else:
+        h = cell_averages(hf, x, breaks)
+        E = h + b
+    return Problem(name=name, x=x, h=h, hu=hu, b=b, E=E, **kw)
+
+
+# --------------------------------------------------------------------------------------
+# Problems of the paper's Sec. 5.1 (used as oracle pins)
+# --------------------------------------------------------------------------------------
+def accuracy_test(N, t_end=0.1, moving=True, cfl=0.1):
+    """Sec. 5.1 accuracy test (Eq. inismoo): periodic [0,1], b = sin^2(pi x),
+    h = 5 + exp(cos 2 pi x), hu = sin(cos 2 pi x), CFL 0.1, paper mesh motion with T = t_end."""
+    x = _uniform(0.0, 1.0, N)
+    prof = _paper_motion_profile(x, 0.0, 1.0) if moving else np.zeros(N + 1)
+    return _make("accuracy", x, lambda s: 5.0 + np.exp(np.cos(2 * np.pi * s)), lambda s: np.sin(np.cos(2 * np.pi * s)),
+                 lambda s: np.sin(np.pi * s) ** 2, profile=prof, bc="periodic",
+                 mesh="profile" if moving else "static", mesh_T=t_end, t_end=t_end, cfl=cfl)
+
+
+def lake_at_rest(N=200, bottom="smooth", t_end=0.5, moving=True):
+    """Sec. 5.1 well-balance test: [0,10], eta = 10, hu = 0, b smooth 5 exp(-0.4 (x-5)^2)
+    (Eq. smo1D) or the step 4 on [4,8] (Eq. dis1D); paper mesh motion with T = t_end."""
+    x = _uniform(0.0, 10.0, N)
+    if bottom == "smooth":
+        bf, br = (lambda s: 5.0 * np.exp(-0.4 * (s - 5.0) ** 2)), ()
+    else:
+        bf, br = (lambda s: np.where((s >= 4.0) & (s <= 8.0), 4.0, 0.0)), (4.0, 8.0)
+    prof = _paper_motion_profile(x, 0.0, 10.0) if moving else np.zeros(N + 1)
+    return _make(f"lake_{bottom}", x, None, lambda s: 0.0 * s, bf, breaks=br, lake_level=10.0, profile=prof,
+                 bc="transmissive", mesh="profile" if moving else "static", mesh_T=t_end, t_end=t_end)
+
+
+def moses_first(N=200, t_end=2.0, moving=True):
+    """Sec. 5.1 Moses's first problem (Eq. flat2): [-200,400], flat bottom, h = 5, u = 0 for
+    x <= 0 and h = 10, u = 40 otherwise; transmissive; CFL 0.08."""
+    x = _uniform(-200.0, 400.0, N)
+    prof = _paper_motion_profile(x, -200.0, 400.0) if moving else np.zeros(N + 1)
+    return _make("moses1", x, lambda s: np.where(s <= 0.0, 5.0, 10.0), lambda s: np.where(s <= 0.0, 0.0, 400.0),
+                 lambda s: 0.0 * s, breaks=(0.0,), profile=prof, bc="transmissive",
+                 mesh="profile" if moving else "static", mesh_T=t_end, t_end=t_end, cfl=0.08)
+
+
+def moses_second(N=200, t_end=1.0, moving=True):
+    """Sec. 5.1 Moses's second problem (Eq. flat3): [-300,300], h = 10 outside (-70,70), dry
+    inside, u = 0; transmissive; CFL 0.08."""
+    x = _uniform(-300.0, 300.0, N)
+    prof = _paper_motion_profile(x, -300.0, 300.0) if moving else np.zeros(N + 1)
+    return _make("moses2", x, lambda s: np.where((s > -70.0) & (s < 70.0), 0.0, 10.0), lambda s: 0.0 * s,
+                 lambda s: 0.0 * s, breaks=(-70.0, 70.0), profile=prof, bc="transmissive",
+                 mesh="profile" if moving else "static", mesh_T=t_end, t_end=t_end, cfl=0.08)
+
+
+# --------------------------------------------------------------------------------------
+# Benchmark workloads
+# --------------------------------------------------------------------------------------
+def smooth_periodic(N=200, lake=False, t_end=0.1):
+    """Single small instance: periodic [0,1], N = 200, b = sin^2(pi x), h = 5 + exp(cos 2 pi x),
+    hu = sin(cos 2 pi x); motion x = xi + 0.05 sin(2 pi xi) sin(2 pi t); CFL 0.6, t_end = 0.1.
+    lake=True: the lake at rest eta = 6, hu = 0 on the same mesh motion."""
+    x = _uniform(0.0, 1.0, N)
+    prof = _sine_profile(x, 0.0, 1.0, 0.05)
+    if lake:
+        return _make("smooth_periodic_lake", x, None, lambda s: 0.0 * s, lambda s: np.sin(np.pi * s) ** 2,
+                     lake_level=6.0, profile=prof, bc="periodic", mesh="profile", mesh_T=1.0, t_end=t_end)
+    return _make("smooth_periodic", x, lambda s: 5.0 + np.exp(np.cos(2 * np.pi * s)),
+                 lambda s: np.sin(np.cos(2 * np.pi * s)), lambda s: np.sin(np.pi * s) ** 2, profile=prof,
+                 bc="periodic", mesh="profile", mesh_T=1.0, t_end=t_end)
+
+
+def dam_break_dry(N=1 << 20):
+    """Large single instance: N cells on [0,10], transmissive; h = 2 for x < 5, 0.5 on [5,8),
+    dry (h = 0) on [8,10]; hu = 0; b = 0.8 exp(-5 (x-5)^2); mesh velocity = Gaussian-smoothed
+    fluid velocity (sigma 8 cells, +-24 nodes); CFL 0.08 (the paper's wet/dry value)."""
+    x = _uniform(0.0, 10.0, N)
+    return _make("dam_break_dry", x, lambda s: np.where(s < 5.0, 2.0, np.where(s < 8.0, 0.5, 0.0)),
+                 lambda s: 0.0 * s, lambda s: 0.8 * np.exp(-5.0 * (s - 5.0) ** 2), breaks=(5.0, 8.0),
+                 profile=np.zeros(N + 1), bc="transmissive", mesh="fluid_gauss", cfl=0.08,
+                 gauss_sigma=8.0, gauss_half=24)
