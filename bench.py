@@ -1,0 +1,283 @@
+#!/usr/bin/env python3
+"""Benchmark: FP64 cell-updates/s of the ALE-WENO hot path on GB300.
+
+Workload: the large single instance of the 1D shallow-water dam break with a dry region
+(N = 2^20 cells on [0, 10], h = 2 / 0.5 / 0 on [0,5) / [5,8) / [8,10], hu = 0,
+b = 0.8 exp(-5 (x-5)^2), transmissive, mesh velocity = Gaussian-smoothed fluid velocity
+(sigma 8 cells), CFL 0.08). A step is one full SSP-RK3 step (mesh velocity, three
+reconstruction + limiter + wave-speed reduction stages, three flux + source + update stages).
+A cell-update is one cell advanced by one step.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank advances an independent replica (weak scaling, no
+collective on the data path); the timing is the max over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS = 1 << 20
+WORKLOAD = "dam_break_dry: N=2^20 cells on [0,10], FP64, transmissive, dry region, Gaussian fluid-driven mesh, CFL 0.08"
+METRIC = "cell-updates/s FP64 (fwd, plain single instance)"
+UNIT = "cell-updates/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def problem():
+    from paper_2208_06588_gb300 import workloads as W
+    return W.dam_break_dry(N=N_CELLS)
+
+
+def config_of(pr):
+    from paper_2208_06588_gb300 import binding as B
+    return B.make_config(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, gauss_sigma=pr.gauss_sigma,
+                         gauss_half=pr.gauss_half, bc=pr.bc, mesh=pr.mesh)
+
+
+def op_counts(pr):
+    """FP64 operations per cell of the reconstruction and update kernels, counted by running the
+    kernels' own per-cell code (swale_cell.cuh) on a host counting type over a sample of cells."""
+    from paper_2208_06588_gb300 import opcount
+    return opcount.count_stage(pr.E, pr.hu, pr.b, pr.J, bc=pr.bc, sample=1 << 16)
+
+
+def cpu_oracle_rate(n_cells, steps):
+    """The CPU oracle as it stands, single thread, on a sample of the same workload."""
+    import oracle
+    from paper_2208_06588_gb300 import workloads as W
+    pr = W.dam_break_dry(N=n_cells)
+    st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+    P = oracle.Params(g=pr.g, cfl=pr.cfl, bc=pr.bc, mesh=pr.mesh, gauss_sigma=pr.gauss_sigma,
+                      gauss_half=pr.gauss_half)
+    oracle.lib()
+    t0 = time.perf_counter()
+    r = oracle.run(P, st, pr.profile, nsteps=steps)
+    dt = time.perf_counter() - t0
+    return n_cells * r["steps"] / dt, dt
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle (plain C++ FP64, one thread), each step one SSP-RK3 step of
+    a 2^15-cell sample of the same workload."""
+    rank, _, ws = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2208_06588_gb300 import workloads as W
+    n = 1 << 15
+    pr = W.dam_break_dry(N=n)
+    st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+    P = oracle.Params(g=pr.g, cfl=pr.cfl, bc=pr.bc, mesh=pr.mesh, gauss_sigma=pr.gauss_sigma,
+                      gauss_half=pr.gauss_half)
+    oracle.run(P, st, pr.profile, nsteps=max(args.warmup, 0))
+    t0 = time.perf_counter()
+    r = oracle.run(P, st, pr.profile, nsteps=args.steps)
+    el = time.perf_counter() - t0
+    v = n * r["steps"] / el
+    sample = f"{args.steps} SSP-RK3 steps of the dam-break workload at N=2^15 cells (same shape, 1/32 of the cells)"
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(r["steps"], 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD.replace("N=2^20", "N=2^15 sample")},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, local, ws = dist_env()
+    import torch
+    import torch.distributed as dist
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2208_06588_gb300 import binding as B
+    B.lib()
+    pr = problem()
+    N = pr.N
+    stream = torch.cuda.Stream(device=dev)
+    ctx = B.swale_create(config_of(pr), stream.cuda_stream)
+    B.swale_set_problem(ctx, N, pr.x, pr.E, pr.hu, pr.b, None, 1)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    # Warm-up (also instantiates the step graph).
+    B.swale_enqueue(ctx, args.warmup)
+    stream.synchronize()
+    # ---- device-timed region: K steps, kernels timed by events on the launch stream ----
+    B.swale_set_timing(ctx, True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    B.swale_enqueue(ctx, args.steps)
+    ev1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    fam = B.swale_get_timing(ctx)
+    B.swale_set_timing(ctx, False)
+    bits, steps_done, last_dt = B.swale_get_status(ctx)
+    B.swale_destroy(ctx)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * N * args.steps / (ms * 1e-3)
+    launches = sum(n for _, n in fam.values())
+
+    # ---- end-to-end through the public C ABI with host buffers ----
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+           for k, v in (("x", pr.x), ("E", pr.E), ("hu", pr.hu), ("b", pr.b))}
+    outs = {k: torch.empty(n, dtype=torch.float64).pin_memory()
+            for k, n in (("eta", N), ("hu", N), ("b", N), ("x", N + 1), ("t", 1))}
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx2 = B.swale_create(config_of(pr), stream.cuda_stream)
+    B.swale_set_problem(ctx2, N, pin["x"], pin["E"], pin["hu"], pin["b"], None, 1)
+    B.swale_advance(ctx2, args.steps)
+    B.swale_get_state(ctx2, None, outs["hu"], outs["b"], outs["eta"], outs["x"], outs["t"])
+    e2e_s = time.perf_counter() - t0
+    B.swale_destroy(ctx2)
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(v.numel() * 8 for v in pin.values())
+    d2h = sum(v.numel() * 8 for v in outs.values())
+    e2e = {"value": ws * N * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+           "d2h_bytes_per_step": d2h / args.steps,
+           "call": "swale_create + swale_set_problem(host) + swale_advance(K) + swale_get_state(host) + destroy"}
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (FP64 ALU bound) ----
+    oc = op_counts(pr)
+    ms_rec, n_rec = fam["reconstruction"]
+    ms_upd, n_upd = fam["update"]
+    dom = "reconstruction" if ms_rec >= ms_upd else "update"
+    flops_cell = oc["recon_flops"] if dom == "reconstruction" else oc["update_flops"]
+    ms_dom, n_dom = fam[dom]
+    achieved = flops_cell * N / (ms_dom / n_dom * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": f"k_{'recon' if dom == 'reconstruction' else 'update'} (per stage)",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": None, "flops_per_cell": flops_cell, "cells_per_launch": N,
+            "avg_launch_ms": ms_dom / n_dom,
+            "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA chain: 1.195 TFLOP/s)",
+            "kernel_ms_share": {k: round(v[0] / max(sum(x[0] for x in fam.values()), 1e-30), 4)
+                                for k, v in fam.items()}}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, secs = cpu_oracle_rate(N_CELLS, 3)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"3 SSP-RK3 steps of the full 2^20-cell workload ({secs:.1f} s, one thread)"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "cells": N, "parallelism": f"replicas x{ws}" if ws > 1 else "single",
+                      "l2": "working set ~230 MB per stage > 126 MB L2 (no flush needed)"},
+           "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+           "status_bits": bits, "steps_done_device": steps_done, "last_dt": last_dt,
+           "fp64_ops_per_cell_stage": oc}
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

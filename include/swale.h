@@ -1,0 +1,156 @@
+/*
+ * swale.h -- C ABI of the GB300 (sm_103a) solver for the one-dimensional well-balanced
+ * finite-volume ALE-WENO hybrid scheme for the shallow water equations with bottom
+ * topography of Zhang, Xia & Xu, "Structure-preserving finite volume arbitrary
+ * Lagrangian-Eulerian WENO schemes for the shallow water equations" (arXiv 2208.06588).
+ *
+ * The calls follow the paper's problem statement: a mesh of N cells with nodes x_{j+1/2}
+ * (Sec. 2.1), cell averages of the depth h, the discharge hu and the bottom b (Sec. 3.1,
+ * Sec. 3.3), the gravitational constant g, the CFL number and the final time t_end
+ * (Sec. 5). One step is the modified third-order SSP-RK method with the width recursion
+ * (Eq. RK32D, Eq. Jacobi2D); each stage evaluates the well-balanced semi-discrete scheme
+ * with hydrostatic reconstruction (Eq. hydro2D-HH2D) and the bottom scheme (Eq. bottomrk).
+ *
+ * Conventions
+ *  - All floating-point data are IEEE double (FP64), contiguous, no padding.
+ *  - Pointer arguments may be host or device memory (detected per pointer with
+ *    cudaPointerGetAttributes); device pointers are used on the context's stream.
+ *  - The caller owns every buffer it passes; the library copies inputs in and results out
+ *    and keeps no reference to caller memory after a call returns.
+ *  - Every call returns a swale_status. Nothing aborts, throws or traps; on an error the
+ *    message is available from swale_last_error(ctx).
+ *  - A context is not thread-safe; use one context per host thread / stream.
+ */
+#ifndef SWALE_H
+#define SWALE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct swale_ctx swale_ctx;
+
+typedef enum {
+  SWALE_OK = 0,
+  SWALE_EINVAL = -1,      /* invalid argument or state (message says which) */
+  SWALE_ENOMEM = -2,      /* device allocation failed */
+  SWALE_ECUDA = -3,       /* a CUDA runtime call failed */
+  SWALE_EMESH = -4,       /* a cell width became <= 0 (mesh assumption A1 of Sec. 2.1) */
+  SWALE_ENEGDEPTH = -5,   /* reserved: negative depth is reported as a warning bit */
+  SWALE_ENONFINITE = -6,  /* a non-finite value appeared */
+  SWALE_ETIMEOUT = -7,    /* reserved */
+  SWALE_EWEIGHT = -8      /* a linear weight d_r <= 0 (Sec. 2.2: needs the Shi-Hu-Shu split) */
+} swale_status;
+
+/* Bits of the device status word returned by swale_get_status. */
+#define SWALE_BIT_EWEIGHT 1u    /* linear weight <= 0 met in a stage */
+#define SWALE_BIT_NEGDEPTH 2u   /* a cell-average depth below -eps_pp entered a stage (warning) */
+#define SWALE_BIT_NONFINITE 4u  /* non-finite value */
+#define SWALE_BIT_EMESH 8u      /* non-positive width */
+
+typedef enum { SWALE_BC_PERIODIC = 0, SWALE_BC_TRANSMISSIVE = 1, SWALE_BC_REFLECTIVE = 2 } swale_bc;
+
+typedef enum {
+  SWALE_MESH_STATIC = 0,      /* w = 0 */
+  SWALE_MESH_PROFILE = 1,     /* x_k(t) = x_k(0) + P_k sin(2 pi t / mesh_T); w_k is the secant
+                                 speed over each step (Eq. w1D) */
+  SWALE_MESH_FLUID_GAUSS = 2  /* w_k = Gaussian-smoothed (sigma = gauss_sigma cells, +-gauss_half
+                                 nodes, renormalised) mean of the adjacent cell velocities;
+                                 end nodes fixed */
+} swale_mesh;
+
+/* Scheme and run constants. Defaults used in the paper: g = 9.812, cfl = 0.6 (0.08 for
+ * wet/dry problems), eps_weno = 1e-6 (Step 2 of Sec. 2.2), eps_pp = 1e-11 (Eq. modifiedhjn). */
+typedef struct {
+  double g;            /* gravitational constant */
+  double cfl;          /* dt = cfl * min_j J_j / alpha_1 */
+  double eps_weno;     /* epsilon of the smoothness detector and of the WENO-Z weights */
+  double eps_pp;       /* floor of the bound-preserving limiter */
+  double h_dry;        /* edge depths <= h_dry carry zero velocity (default 1e-6) */
+  double mesh_T;       /* period of the prescribed motion (SWALE_MESH_PROFILE) */
+  double gauss_sigma;  /* filter width in cells (SWALE_MESH_FLUID_GAUSS) */
+  double t_end;        /* > 0: the last step is clipped to t_end and stepping stops there */
+  double dt_fixed;     /* > 0: every step uses this dt instead of the CFL formula */
+  int32_t bc;          /* swale_bc */
+  int32_t mesh;        /* swale_mesh */
+  int32_t gauss_half;  /* filter truncation half-width in nodes, <= 64 */
+  int32_t beta_dx_global; /* 1: Delta x in the indicators is max_j J_j (Step 1); 0: local J_j */
+} swale_config;
+
+/* Creates a context bound to a CUDA stream (cudaStream_t; NULL = legacy default stream).
+ * Checks the configuration; allocates nothing on the device yet.
+ * Errors: SWALE_EINVAL (bad config, no CUDA device). */
+swale_status swale_create(swale_ctx** out, const swale_config* cfg, void* cuda_stream);
+
+/* Sets the problem (Sec. 2.1 mesh, Sec. 3 cell averages) and allocates the device state.
+ *   N        number of cells, N >= 5
+ *   x_nodes  N+1 node coordinates, strictly increasing
+ *   q0       N cell averages of the depth h (q0_is_eta = 0) or of the surface eta = h + b
+ *            (q0_is_eta = 1; lets a lake at rest be given exactly as eta = const)
+ *   hu, b    N cell averages of the discharge and of the bottom
+ *   profile  N+1 node amplitudes P_k of SWALE_MESH_PROFILE motion (ignored otherwise; may be
+ *            NULL then)
+ * The time is reset to 0. Errors: SWALE_EINVAL (sizes, non-finite data, negative depth,
+ * non-increasing nodes), SWALE_ENOMEM, SWALE_ECUDA. */
+swale_status swale_set_problem(swale_ctx* ctx, int64_t N, const double* x_nodes, const double* q0,
+                               const double* hu, const double* b, const double* profile, int32_t q0_is_eta);
+
+/* One SSP-RK3 step (three fused reconstruction + update stage pairs). If dt_out is not NULL
+ * the call synchronises the stream and returns the step's dt. A step at t >= t_end (t_end > 0)
+ * does nothing. Errors: SWALE_EINVAL (no problem set), SWALE_ECUDA. */
+swale_status swale_step(swale_ctx* ctx, double* dt_out);
+
+/* Up to max_steps steps, replayed as CUDA graphs of fixed length; stops early at t_end.
+ * Synchronises at the end and reports the steps actually taken in *steps_done (may be NULL).
+ * Returns SWALE_ENONFINITE / SWALE_EMESH / SWALE_EWEIGHT if the device status word has the
+ * matching bit (the steps were taken), else SWALE_OK. */
+swale_status swale_advance(swale_ctx* ctx, int64_t max_steps, int64_t* steps_done);
+
+/* Enqueues nsteps steps on the context's stream and returns without synchronising (steps at
+ * t >= t_end are no-ops on the device). Errors: SWALE_EINVAL, SWALE_ECUDA. */
+swale_status swale_enqueue(swale_ctx* ctx, int64_t nsteps);
+
+/* Kernel timing. While enabled (enable != 0), every enqueued step records CUDA events on the
+ * context's stream around each kernel and steps are not replayed as graphs. swale_get_timing
+ * synchronises and returns, for the kernel families 0 = per-step prologue, 1 = mesh velocity,
+ * 2 = reconstruction, 3 = update, the summed device time in ms (ms[4]) and the number of
+ * launches (launches[4]) since timing was last enabled. Either pointer may be NULL. */
+swale_status swale_set_timing(swale_ctx* ctx, int32_t enable);
+swale_status swale_get_timing(swale_ctx* ctx, double* ms, int64_t* launches);
+
+/* Copies the current state out. Any pointer may be NULL. h, hu, b, eta: N values; x_nodes:
+ * N+1 values; t: one value (host or device). Synchronises the stream. */
+swale_status swale_get_state(swale_ctx* ctx, double* h, double* hu, double* b, double* eta, double* x_nodes,
+                             double* t);
+
+/* Detector classes (0 smooth, 1 transition, 2 non-smooth; Step 2 of Sec. 2.2) of the first
+ * stage of the last step, N bytes. Synchronises. */
+swale_status swale_get_flags(swale_ctx* ctx, uint8_t* flags);
+
+/* Accumulated device status word (SWALE_BIT_*), the step count and the last dt.
+ * Any pointer may be NULL; host pointers. Synchronises. */
+swale_status swale_get_status(swale_ctx* ctx, uint32_t* status_bits, int64_t* steps, double* last_dt);
+
+/* One evaluation of the semi-discrete right-hand side (Eq. hydro2D with Eq. bottomrk) for
+ * the given state, independent of the context's problem: E = eta, M = hu, B = b, J widths
+ * (N values each), w node velocities (N+1), alpha > 0 the global viscosity (alpha <= 0:
+ * alpha = max edge |u| + sqrt(g h) plus max |w|). Outputs R_E, R_M, R_B (N), the largest edge
+ * wave speed *A_out, flags (N bytes, may be NULL) and the status bits (may be NULL).
+ * Allocates and frees its own device scratch. Synchronises. */
+swale_status swale_rhs(swale_ctx* ctx, int64_t N, const double* E, const double* M, const double* B,
+                       const double* J, const double* w, double alpha, double* RE, double* RM, double* RB,
+                       double* A_out, uint8_t* flags, uint32_t* status_bits);
+
+/* Message of the last error of this context ("" if none). Never NULL. */
+const char* swale_last_error(const swale_ctx* ctx);
+
+/* Frees the context and its device memory. NULL is ignored. */
+void swale_destroy(swale_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWALE_H */

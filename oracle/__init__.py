@@ -86,7 +86,7 @@ class Params:
     cfl: float = 0.6
     eps_weno: float = 1e-6
     eps_pp: float = 1e-11
-    h_dry: float = 1e-10
+    h_dry: float = 1e-6
     mesh_T: float = 1.0
     gauss_sigma: float = 8.0
     t_end: float = 0.0

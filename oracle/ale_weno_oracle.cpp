@@ -50,7 +50,7 @@ struct OrcParams {
 
 enum : uint32_t {
   ST_EWEIGHT = 1u,     // a linear weight d_r <= 0 (the split of Shi-Hu-Shu is not applied)
-  ST_NEGDEPTH = 2u,    // a cell-average depth below -h_dry entered a stage
+  ST_NEGDEPTH = 2u,    // a cell-average depth below -eps_pp entered a stage (warning)
   ST_NONFINITE = 4u,   // a non-finite value appeared
   ST_EMESH = 8u,       // a cell width became <= 0 (mesh assumption A1 violated)
 };
@@ -312,7 +312,7 @@ double reconstruct(const OrcParams& P, int64_t N, const T* E, const T* M, const 
     // end weights sigma_1 = sigma_4 = 1/12. The interior mean delta follows from
     // hbar = (1 - 2/12) delta + (h^L + h^R)/12.
     T hbar = e5[2] - b5[2];
-    if (value(hbar) < -P.h_dry) status |= ST_NEGDEPTH;
+    if (value(hbar) < -P.eps_pp) status |= ST_NEGDEPTH;
     // Reading: a rounding-level negative mean in a dry cell is treated as zero.
     if (value(hbar) < 0.0) hbar = T(0.0);
     T hL = o.E[0] - o.B[0], hR = o.E[1] - o.B[1];
@@ -525,8 +525,10 @@ uint32_t ssprk3_step(const OrcParams& P, int64_t N, T* E, T* M, T* B, double* J,
       for (int64_t j = 0; j < N; ++j) dwmax = std::max(dwmax, std::fabs(w[j + 1] - w[j]));
       if (dwmax > 0.0) dt = std::min(dt, 0.5 * jmin / dwmax);
     }
-    if (P.t_end > 0.0) dt = std::min(dt, P.t_end - *t);
   }
+  // The last step is clipped to t_end and then lands on it exactly.
+  const bool clipped = P.t_end > 0.0 && P.t_end - *t <= dt;
+  if (clipped && !replay) dt = P.t_end - *t;
   if (P.mesh == 1) {
     // Node speed (Eq. w1D): secant of the prescribed trajectory over [t_n, t_n + dt].
     const double s0 = std::sin(2.0 * M_PI * (*t) / P.mesh_T);
@@ -579,7 +581,7 @@ uint32_t ssprk3_step(const OrcParams& P, int64_t N, T* E, T* M, T* B, double* J,
     J[j] = J3[j];
   }
   for (int64_t k = 0; k <= N; ++k) x[k] = x[k] + dt * w[k];
-  *t += dt;
+  *t = clipped ? P.t_end : *t + dt;
   *dt_out = dt;
   if (alpha_rec && !replay) {
     alpha_rec[0] = alpha1;

@@ -1,0 +1,215 @@
+"""ctypes binding of the C ABI in include/swale.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls. Arrays may be numpy arrays
+(host memory) or torch tensors (host or CUDA); they are passed as raw pointers. Loading
+fails loudly if the CUDA library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libswale.so")
+
+SWALE_OK = 0
+STATUS_NAMES = {0: "SWALE_OK", -1: "SWALE_EINVAL", -2: "SWALE_ENOMEM", -3: "SWALE_ECUDA", -4: "SWALE_EMESH",
+                -5: "SWALE_ENEGDEPTH", -6: "SWALE_ENONFINITE", -7: "SWALE_ETIMEOUT", -8: "SWALE_EWEIGHT"}
+BIT_EWEIGHT, BIT_NEGDEPTH, BIT_NONFINITE, BIT_EMESH = 1, 2, 4, 8
+BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
+MESH = {"static": 0, "profile": 1, "fluid_gauss": 2}
+
+
+class SwaleConfig(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_double), ("cfl", ctypes.c_double), ("eps_weno", ctypes.c_double),
+                ("eps_pp", ctypes.c_double), ("h_dry", ctypes.c_double), ("mesh_T", ctypes.c_double),
+                ("gauss_sigma", ctypes.c_double), ("t_end", ctypes.c_double), ("dt_fixed", ctypes.c_double),
+                ("bc", ctypes.c_int32), ("mesh", ctypes.c_int32), ("gauss_half", ctypes.c_int32),
+                ("beta_dx_global", ctypes.c_int32)]
+
+
+def make_config(g=9.812, cfl=0.6, eps_weno=1e-6, eps_pp=1e-11, h_dry=1e-6, mesh_T=1.0, gauss_sigma=8.0,
+                t_end=0.0, dt_fixed=0.0, bc="periodic", mesh="static", gauss_half=24, beta_dx_global=1):
+    return SwaleConfig(g, cfl, eps_weno, eps_pp, h_dry, mesh_T, gauss_sigma, t_end, dt_fixed,
+                       BC[bc] if isinstance(bc, str) else bc, MESH[mesh] if isinstance(mesh, str) else mesh,
+                       gauss_half, beta_dx_global)
+
+
+class SwaleError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Loads libswale.so; raises if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library {LIB_PATH} is not built; run __graft_entry__.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        P = ctypes.POINTER
+        L.swale_create.argtypes = [P(vp), P(SwaleConfig), vp]
+        L.swale_set_problem.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32]
+        L.swale_step.argtypes = [vp, vp]
+        L.swale_advance.argtypes = [vp, i64, P(i64)]
+        L.swale_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.swale_get_flags.argtypes = [vp, vp]
+        L.swale_get_status.argtypes = [vp, P(ctypes.c_uint32), P(i64), P(d)]
+        L.swale_rhs.argtypes = [vp, i64, vp, vp, vp, vp, vp, d, vp, vp, vp, P(d), vp, P(ctypes.c_uint32)]
+        L.swale_enqueue.argtypes = [vp, i64]
+        L.swale_set_timing.argtypes = [vp, i32]
+        L.swale_get_timing.argtypes = [vp, vp, vp]
+        for name in ("swale_create", "swale_set_problem", "swale_step", "swale_advance", "swale_get_state",
+                     "swale_get_flags", "swale_get_status", "swale_rhs", "swale_enqueue", "swale_set_timing",
+                     "swale_get_timing"):
+            getattr(L, name).restype = ctypes.c_int
+        L.swale_last_error.argtypes = [vp]
+        L.swale_last_error.restype = ctypes.c_char_p
+        L.swale_destroy.argtypes = [vp]
+        L.swale_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def ptr(a):
+    """Raw address of a numpy array or torch tensor (None stays None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _check(ctx, code):
+    if code != SWALE_OK:
+        msg = lib().swale_last_error(ctx).decode() if ctx else ""
+        raise SwaleError(code, msg)
+
+
+def swale_create(cfg: SwaleConfig, stream=None):
+    ctx = ctypes.c_void_p()
+    code = lib().swale_create(ctypes.byref(ctx), ctypes.byref(cfg), stream)
+    _check(None, code)
+    return ctx
+
+
+def swale_set_problem(ctx, N, x_nodes, q0, hu, b, profile=None, q0_is_eta=0):
+    _check(ctx, lib().swale_set_problem(ctx, int(N), ptr(x_nodes), ptr(q0), ptr(hu), ptr(b), ptr(profile),
+                                        int(q0_is_eta)))
+
+
+def swale_step(ctx, dt_out=None):
+    _check(ctx, lib().swale_step(ctx, ptr(dt_out)))
+
+
+def swale_advance(ctx, max_steps):
+    done = ctypes.c_int64(0)
+    _check(ctx, lib().swale_advance(ctx, int(max_steps), ctypes.byref(done)))
+    return done.value
+
+
+def swale_enqueue(ctx, nsteps):
+    _check(ctx, lib().swale_enqueue(ctx, int(nsteps)))
+
+
+def swale_set_timing(ctx, enable):
+    _check(ctx, lib().swale_set_timing(ctx, 1 if enable else 0))
+
+
+FAMILIES = ("prologue", "mesh_velocity", "reconstruction", "update")
+
+
+def swale_get_timing(ctx):
+    ms = np.zeros(4)
+    n = np.zeros(4, dtype=np.int64)
+    _check(ctx, lib().swale_get_timing(ctx, ms.ctypes.data, n.ctypes.data))
+    return {f: (float(ms[i]), int(n[i])) for i, f in enumerate(FAMILIES)}
+
+
+def swale_get_state(ctx, h=None, hu=None, b=None, eta=None, x_nodes=None, t=None):
+    _check(ctx, lib().swale_get_state(ctx, ptr(h), ptr(hu), ptr(b), ptr(eta), ptr(x_nodes), ptr(t)))
+
+
+def swale_get_flags(ctx, flags):
+    _check(ctx, lib().swale_get_flags(ctx, ptr(flags)))
+
+
+def swale_get_status(ctx):
+    bits, steps, dt = ctypes.c_uint32(0), ctypes.c_int64(0), ctypes.c_double(0)
+    _check(ctx, lib().swale_get_status(ctx, ctypes.byref(bits), ctypes.byref(steps), ctypes.byref(dt)))
+    return bits.value, steps.value, dt.value
+
+
+def swale_rhs(ctx, N, E, M, B, J, w, alpha, RE, RM, RB, flags=None):
+    A = ctypes.c_double(0)
+    bits = ctypes.c_uint32(0)
+    _check(ctx, lib().swale_rhs(ctx, int(N), ptr(E), ptr(M), ptr(B), ptr(J), ptr(w), float(alpha), ptr(RE),
+                                ptr(RM), ptr(RB), ctypes.byref(A), ptr(flags), ctypes.byref(bits)))
+    return A.value, bits.value
+
+
+def swale_last_error(ctx):
+    return lib().swale_last_error(ctx).decode()
+
+
+def swale_destroy(ctx):
+    lib().swale_destroy(ctx)
+
+
+class Solver:
+    """One solver instance: owns a context; arrays in and out are numpy (host) unless the
+    caller passes torch tensors to the raw functions above."""
+
+    def __init__(self, cfg: SwaleConfig, stream=None):
+        self.ctx = swale_create(cfg, stream)
+        self.N = 0
+
+    def set_problem(self, x, q0, hu, b, profile=None, q0_is_eta=False):
+        x, q0, hu, b = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, q0, hu, b))
+        prof = None if profile is None else np.ascontiguousarray(profile, dtype=np.float64)
+        self.N = q0.size
+        swale_set_problem(self.ctx, self.N, x, q0, hu, b, prof, 1 if q0_is_eta else 0)
+
+    def step(self):
+        dt = np.zeros(1)
+        swale_step(self.ctx, dt)
+        return float(dt[0])
+
+    def advance(self, max_steps):
+        return swale_advance(self.ctx, max_steps)
+
+    def state(self):
+        N = self.N
+        h, hu, b, eta, x, t = (np.zeros(N), np.zeros(N), np.zeros(N), np.zeros(N), np.zeros(N + 1), np.zeros(1))
+        swale_get_state(self.ctx, h, hu, b, eta, x, t)
+        return {"h": h, "hu": hu, "b": b, "eta": eta, "x": x, "t": float(t[0])}
+
+    def flags(self):
+        f = np.zeros(self.N, dtype=np.uint8)
+        swale_get_flags(self.ctx, f)
+        return f
+
+    def status(self):
+        return swale_get_status(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            swale_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,963 @@
+// GB300 (sm_103a) FP64 kernels and C ABI of the well-balanced ALE-WENO hybrid scheme
+// (Zhang, Xia & Xu, arXiv 2208.06588). One SSP-RK3 step (Eq. RK32D) is a short, fixed
+// sequence of launches on the context's stream:
+//   prologue (1 thread)        reset the per-step device scalars
+//   [mesh_gauss]               fluid-driven node velocities (SWALE_MESH_FLUID_GAUSS)
+//   recon<1>, update<1>        stage 1 on the mesh at t_n
+//   recon<2>, update<2>        stage 2 on the mesh at t_{n+1}
+//   recon<3>, update<3>        stage 3 on the mesh at t_{n+1/2}
+// The reconstruction kernel also reduces the global wave speed of Eq. alpha2D (warp shuffle,
+// shared memory, one atomicMax per block on the order-preserving bit pattern of a
+// non-negative double); in stage 1 the last block to finish computes dt on the device, so
+// dt, alpha and t never visit the host and a step can be replayed as a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/swale.h"
+#include "swale_cell.cuh"
+
+using swale::EdgeState;
+using swale::SchemeConst;
+
+namespace {
+
+constexpr int kReconThreads = 128;
+constexpr int kUpdateThreads = 128;
+constexpr int kMaxGaussHalf = 64;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+__constant__ double c_gauss_w[2 * kMaxGaussHalf + 1];
+
+// Per-context device scalars. Maxima of non-negative doubles are kept as their bit
+// patterns (unsigned order equals numeric order for non-negative IEEE doubles).
+struct DevScalars {
+  double t, dt, sdiff, Wbar, alpha1;
+  unsigned long long A[3];     // max edge wave speed per stage
+  unsigned long long Jmax[3];  // max width of the stage meshes J^n, J^(1), J^(2)
+  unsigned long long Jmin0;    // min J^n
+  unsigned long long JmaxN, JminN;   // of J^{n+1}, accumulated by stage 3
+  unsigned long long Wabs, dWabs;    // fluid-driven motion: max |w|, max |w_{j+1} - w_j|
+  long long steps;
+  unsigned int status;
+  unsigned int counter;
+  int done;
+  int clipped;
+};
+
+struct StepConst {
+  SchemeConst sc;
+  double cfl, t_end, dt_fixed, mesh_T, Wbar_profile;
+  int64_t N;
+  int32_t bc, mesh;
+  int32_t gauss_half;
+};
+
+// Device state of one instance. Edge arrays hold cells -1..N at index c + 1.
+struct DevState {
+  double *E0, *M0, *B0;        // q^n (updated in place by stage 3)
+  double *Ea, *Ma, *Ba;        // q^(1)
+  double *Eb, *Mb, *Bb;        // q^(2)
+  double *YE, *YM, *YB;        // running RK combination J q
+  double *J0, *J1, *J2;        // J^n, J^(1), J^(2)
+  double *x, *w, *P;           // nodes, node velocities, motion profile (N+1)
+  double *eEL, *eER, *eBL, *eBR, *ehL, *ehR, *euL, *euR;
+  uint8_t* flags;              // N+2, stage-1 classes
+  DevScalars* S;
+};
+
+__device__ __forceinline__ int64_t ghost(int64_t i, int64_t N, int bc) {
+  if (bc == SWALE_BC_PERIODIC) {
+    i %= N;
+    return i < 0 ? i + N : i;
+  }
+  if (i < 0) return -1 - i;
+  if (i >= N) return 2 * N - 1 - i;
+  return i;
+}
+
+__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Block-wide max of a non-negative double, one atomicMax per block.
+__device__ __forceinline__ void block_max_to(unsigned long long* dst, double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    v = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) atomicMax(dst, dbits(v));
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void block_min_to(unsigned long long* dst, double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    v = lane < nw ? red[lane] : INFINITY;
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) atomicMin(dst, dbits(v));
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void block_or_status(unsigned int* dst, uint32_t st) {
+  st = __reduce_or_sync(0xffffffffu, st);
+  if ((threadIdx.x & 31) == 0 && st) atomicOr(dst, st);
+}
+
+// ------------------------------------------------------------------------------------
+// Per-step prologue: stage maxima reset, J^{n+1} statistics become those of J^n.
+// ------------------------------------------------------------------------------------
+__global__ void k_prologue(StepConst K, DevScalars* S) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (K.t_end > 0.0 && S->t >= K.t_end) {
+    S->done = 1;
+    return;
+  }
+  S->done = 0;
+  S->clipped = 0;
+  S->Jmax[0] = S->JmaxN;
+  S->Jmin0 = S->JminN;
+  S->JmaxN = 0ull;
+  S->JminN = 0x7ff0000000000000ull;  // +inf
+  S->A[0] = S->A[1] = S->A[2] = 0ull;
+  S->Jmax[1] = S->Jmax[2] = 0ull;
+  S->Wabs = S->dWabs = 0ull;
+  S->counter = 0u;
+  if (K.mesh != SWALE_MESH_FLUID_GAUSS) S->Wbar = K.Wbar_profile;
+}
+
+// ------------------------------------------------------------------------------------
+// Fluid-driven node velocity: raw_k = (u_{k-1} + u_k)/2 for k = 1..N-1 (u = hu/h, dry -> 0),
+// truncated renormalised Gaussian filter, w_0 = w_N = 0. One thread per node; the block
+// stages the cell velocities it needs in shared memory.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mesh_gauss(StepConst K, DevState D) {
+  extern __shared__ double sh[];  // raw node velocity for nodes [k0 - H, k0 + T + H]
+  DevScalars* S = D.S;
+  if (S->done) return;
+  const int64_t N = K.N;
+  const int H = K.gauss_half, T = blockDim.x;
+  const int64_t k0 = (int64_t)blockIdx.x * T;
+  const int span = T + 2 * H + 2;
+  for (int i = threadIdx.x; i < span; i += T) {
+    const int64_t k = k0 - H + i;  // node index
+    double raw = 0.0;
+    if (k >= 1 && k <= N - 1) {
+      const double hl = D.E0[k - 1] - D.B0[k - 1], hr = D.E0[k] - D.B0[k];
+      const double ul = hl > K.sc.h_dry ? D.M0[k - 1] / hl : 0.0;
+      const double ur = hr > K.sc.h_dry ? D.M0[k] / hr : 0.0;
+      raw = 0.5 * (ul + ur);
+    }
+    sh[i] = raw;
+  }
+  __syncthreads();
+  // Each thread computes w at node k = k0 + tid and at k + 1 (for the difference).
+  double wv[2];
+  for (int s = 0; s < 2; ++s) {
+    const int64_t k = k0 + threadIdx.x + s;
+    double v = 0.0;
+    if (k >= 1 && k <= N - 1) {
+      double acc = 0.0, wsum = 0.0;
+      for (int m = -H; m <= H; ++m) {
+        const int64_t q = k + m;
+        if (q < 1 || q > N - 1) continue;
+        const double gw = c_gauss_w[m + H];
+        acc += gw * sh[(int)(q - (k0 - H))];
+        wsum += gw;
+      }
+      v = acc / wsum;
+    }
+    wv[s] = v;
+  }
+  const int64_t k = k0 + threadIdx.x;
+  double wa = 0.0, dwa = 0.0;
+  if (k <= N) {
+    D.w[k] = wv[0];
+    wa = fabs(wv[0]);
+    if (k < N) dwa = fabs(wv[1] - wv[0]);
+  }
+  block_max_to(&S->Wabs, wa);
+  block_max_to(&S->dWabs, dwa);
+}
+
+// ------------------------------------------------------------------------------------
+// Reconstruction + limiter of cells -1..N for stage STAGE, wave-speed reduction; in stage 1
+// the last block computes dt (and the secant factor of the prescribed motion).
+// ------------------------------------------------------------------------------------
+template <int STAGE>
+__global__ void __launch_bounds__(kReconThreads) k_recon(StepConst K, DevState D, const double* __restrict__ E,
+                                                         const double* __restrict__ M, const double* __restrict__ B,
+                                                         const double* __restrict__ J) {
+  DevScalars* S = D.S;
+  if (S->done) return;
+  const int64_t N = K.N;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - 1;
+  double wave = 0.0;
+  uint32_t st = 0;
+  if (c <= N) {
+    double Jv[5], Ev[5], Mv[5], Bv[5];
+    const bool mirror_sign = (K.bc == SWALE_BC_REFLECTIVE);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int64_t i = c - 2 + k;
+      const int64_t s = ghost(i, N, K.bc);
+      Jv[k] = J[s];
+      Ev[k] = E[s];
+      Bv[k] = B[s];
+      const double m = M[s];
+      Mv[k] = (mirror_sign && (i < 0 || i >= N)) ? -m : m;
+    }
+    const double dxmax = bitsd(S->Jmax[STAGE - 1]);
+    EdgeState o;
+    uint8_t flag;
+    double wl, wr;
+    swale::recon_cell(K.sc, Jv, Ev, Mv, Bv, dxmax, o, flag, wl, wr, st);
+    const int64_t idx = c + 1;
+    D.eEL[idx] = o.EL;
+    D.eER[idx] = o.ER;
+    D.eBL[idx] = o.BL;
+    D.eBR[idx] = o.BR;
+    D.ehL[idx] = o.hL;
+    D.ehR[idx] = o.hR;
+    D.euL[idx] = o.uL;
+    D.euR[idx] = o.uR;
+    if (STAGE == 1) D.flags[idx] = flag;
+    // Edges that touch interfaces 0..N only.
+    if (c == -1) wave = wr;
+    else if (c == N) wave = wl;
+    else wave = fmax(wl, wr);
+    if (!(wave == wave)) st |= swale::ST_NONFINITE;
+  }
+  block_or_status(&S->status, st);
+  block_max_to(&S->A[STAGE - 1], wave);
+  if (STAGE == 1) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned int ticket = atomicAdd(&S->counter, 1u);
+      last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+      __threadfence();
+      const double A1 = bitsd(atomicAdd(&S->A[0], 0ull));
+      double Wbar = S->Wbar;
+      double dwmax = 0.0;
+      if (K.mesh == SWALE_MESH_FLUID_GAUSS) {
+        Wbar = bitsd(atomicAdd(&S->Wabs, 0ull));
+        dwmax = bitsd(atomicAdd(&S->dWabs, 0ull));
+        S->Wbar = Wbar;
+      }
+      const double alpha1 = A1 + Wbar;
+      const double t = S->t;
+      double dt;
+      int clipped = 0;
+      if (K.dt_fixed > 0.0) {
+        dt = K.dt_fixed;
+      } else {
+        const double jmin = bitsd(S->Jmin0);
+        dt = K.cfl * jmin / alpha1;
+        if (K.mesh == SWALE_MESH_FLUID_GAUSS && dwmax > 0.0) dt = fmin(dt, 0.5 * jmin / dwmax);
+      }
+      if (K.t_end > 0.0 && K.t_end - t <= dt) {
+        dt = K.t_end - t;
+        clipped = 1;
+      }
+      S->dt = dt;
+      S->alpha1 = alpha1;
+      S->clipped = clipped;
+      if (K.mesh == SWALE_MESH_PROFILE) {
+        const double s0 = sin(kTwoPi * t / K.mesh_T);
+        const double s1 = sin(kTwoPi * (t + dt) / K.mesh_T);
+        S->sdiff = (s1 - s0) / dt;
+      } else {
+        S->sdiff = 0.0;
+      }
+      S->counter = 0u;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Fluxes, source and the RK combination of stage STAGE for cells 0..N-1 (MODE 0), or the
+// bare right-hand side (MODE 1, used by swale_rhs).
+// ------------------------------------------------------------------------------------
+struct RhsOut {
+  double *RE, *RM, *RB;
+  double alpha;
+};
+
+template <int STAGE, int MODE>
+__global__ void __launch_bounds__(kUpdateThreads) k_update(StepConst K, DevState D, const double* __restrict__ E,
+                                                           const double* __restrict__ M,
+                                                           const double* __restrict__ B,
+                                                           const double* __restrict__ Js, RhsOut ro) {
+  DevScalars* S = D.S;
+  if (MODE == 0 && S->done) return;
+  const int64_t N = K.N;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double jmaxa = 0.0, jmaxb = 0.0, jminb = INFINITY;
+  uint32_t st = 0;
+  if (j < N) {
+    double alpha, dt = 0.0;
+    if (MODE == 1) {
+      alpha = ro.alpha;
+    } else {
+      alpha = (STAGE == 1) ? S->alpha1 : bitsd(S->A[STAGE - 1]) + S->Wbar;
+      dt = S->dt;
+    }
+    // Node velocities of the two interfaces.
+    double wl, wr;
+    if (MODE == 0 && STAGE == 1 && K.mesh == SWALE_MESH_PROFILE) {
+      const double sd = S->sdiff;
+      wl = D.P[j] * sd;
+      wr = D.P[j + 1] * sd;
+      D.w[j] = wl;
+      if (j == N - 1) D.w[N] = wr;
+    } else if (K.mesh == SWALE_MESH_STATIC && MODE == 0) {
+      wl = wr = 0.0;
+    } else {
+      wl = D.w[j];
+      wr = D.w[j + 1];
+    }
+    const int64_t il = j, ic = j + 1, ir = j + 2;  // edge-array indices of cells j-1, j, j+1
+    const int64_t jm = ghost(j - 1, N, K.bc), jp = ghost(j + 1, N, K.bc);
+    const swale::CellRhs R = swale::rhs_cell(
+        K.sc.g, alpha, wl, wr, D.eER[il], D.eBR[il], D.ehR[il], D.euR[il], D.eEL[ic], D.eER[ic], D.eBL[ic],
+        D.eBR[ic], D.ehL[ic], D.ehR[ic], D.euL[ic], D.euR[ic], D.eEL[ir], D.eBL[ir], D.ehL[ir], D.euL[ir], E[jm],
+        E[j], E[jp], B[jm], B[j], B[jp], Js[jm], Js[j], Js[jp]);
+    const double RE = R.RE, RM = R.RM, RB = R.RB;
+    if (MODE == 1) {
+      ro.RE[j] = RE;
+      ro.RM[j] = RM;
+      ro.RB[j] = RB;
+    } else {
+      const double J0 = D.J0[j];
+      const double dw = wr - wl;
+      if (STAGE == 1) {
+        const double J1 = J0 + dt * dw;
+        const double J2 = 0.75 * J0 + 0.25 * J1 + 0.25 * dt * dw;
+        D.J1[j] = J1;
+        D.J2[j] = J2;
+        jmaxa = J1;
+        jmaxb = J2;
+        if (!(J1 > 0.0) || !(J2 > 0.0)) st |= swale::ST_EMESH;
+        const double yE = J0 * D.E0[j] + dt * RE, yM = J0 * D.M0[j] + dt * RM, yB = J0 * D.B0[j] + dt * RB;
+        D.YE[j] = yE;
+        D.YM[j] = yM;
+        D.YB[j] = yB;
+        const double inv = 1.0 / J1;
+        D.Ea[j] = yE * inv;
+        D.Ma[j] = yM * inv;
+        D.Ba[j] = yB * inv;
+      } else if (STAGE == 2) {
+        const double yE = 0.75 * (J0 * D.E0[j]) + 0.25 * (D.YE[j] + dt * RE);
+        const double yM = 0.75 * (J0 * D.M0[j]) + 0.25 * (D.YM[j] + dt * RM);
+        const double yB = 0.75 * (J0 * D.B0[j]) + 0.25 * (D.YB[j] + dt * RB);
+        D.YE[j] = yE;
+        D.YM[j] = yM;
+        D.YB[j] = yB;
+        const double inv = 1.0 / D.J2[j];
+        D.Eb[j] = yE * inv;
+        D.Mb[j] = yM * inv;
+        D.Bb[j] = yB * inv;
+      } else {
+        const double J3 = (1.0 / 3.0) * J0 + (2.0 / 3.0) * D.J2[j] + (2.0 / 3.0) * dt * dw;
+        if (!(J3 > 0.0)) st |= swale::ST_EMESH;
+        const double yE = (1.0 / 3.0) * (J0 * D.E0[j]) + (2.0 / 3.0) * (D.YE[j] + dt * RE);
+        const double yM = (1.0 / 3.0) * (J0 * D.M0[j]) + (2.0 / 3.0) * (D.YM[j] + dt * RM);
+        const double yB = (1.0 / 3.0) * (J0 * D.B0[j]) + (2.0 / 3.0) * (D.YB[j] + dt * RB);
+        const double inv = 1.0 / J3;
+        const double En = yE * inv, Mn = yM * inv, Bn = yB * inv;
+        D.E0[j] = En;
+        D.M0[j] = Mn;
+        D.B0[j] = Bn;
+        D.J0[j] = J3;
+        jmaxb = J3;
+        jminb = J3;
+        D.x[j] += dt * wl;
+        if (j == N - 1) D.x[N] += dt * wr;
+        const double chk = En + Mn + Bn;
+        if (!(chk == chk) || fabs(chk) > 1.0e300) st |= swale::ST_NONFINITE;
+      }
+    }
+  }
+  if (MODE == 0) {
+    block_or_status(&S->status, st);
+    if (STAGE == 1) {
+      block_max_to(&S->Jmax[1], jmaxa);
+      block_max_to(&S->Jmax[2], jmaxb);
+    } else if (STAGE == 3) {
+      block_max_to(&S->JmaxN, jmaxb);
+      block_min_to(&S->JminN, jminb);
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S->t = S->clipped ? K.t_end : S->t + S->dt;
+        S->steps += 1;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ======================================================================================
+// Host side
+// ======================================================================================
+struct swale_ctx {
+  swale_config cfg;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t N = 0;
+  DevState D{};
+  double Wbar_profile = 0.0;
+  std::vector<void*> allocs;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  std::string err;
+  // Kernel timing (swale_set_timing): event pairs around every launch, by kernel family.
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_family;
+  size_t ev_used = 0;
+};
+
+namespace {
+
+swale_status fail(swale_ctx* ctx, swale_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+#define SW_CUDA(ctx, call)                                                                          \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return fail(ctx, SWALE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copies n doubles from caller memory (host or device) into a host vector.
+swale_status fetch(swale_ctx* ctx, const double* src, size_t n, std::vector<double>& dst) {
+  dst.resize(n);
+  if (is_device_ptr(src)) {
+    SW_CUDA(ctx, cudaMemcpyAsync(dst.data(), src, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  } else {
+    std::memcpy(dst.data(), src, n * sizeof(double));
+  }
+  return SWALE_OK;
+}
+
+swale_status put_out(swale_ctx* ctx, void* dst, const void* dev_src, size_t bytes) {
+  if (!dst) return SWALE_OK;
+  SW_CUDA(ctx, cudaMemcpyAsync(dst, dev_src, bytes, cudaMemcpyDefault, ctx->stream));
+  return SWALE_OK;
+}
+
+StepConst step_const(const swale_ctx* ctx) {
+  StepConst K;
+  K.sc.g = ctx->cfg.g;
+  K.sc.eps_weno = ctx->cfg.eps_weno;
+  K.sc.eps_pp = ctx->cfg.eps_pp;
+  K.sc.h_dry = ctx->cfg.h_dry;
+  K.sc.beta_dx_global = ctx->cfg.beta_dx_global;
+  K.cfl = ctx->cfg.cfl;
+  K.t_end = ctx->cfg.t_end;
+  K.dt_fixed = ctx->cfg.dt_fixed;
+  K.mesh_T = ctx->cfg.mesh_T;
+  K.Wbar_profile = ctx->Wbar_profile;
+  K.N = ctx->N;
+  K.bc = ctx->cfg.bc;
+  K.mesh = ctx->cfg.mesh;
+  K.gauss_half = ctx->cfg.gauss_half;
+  return K;
+}
+
+void free_state(swale_ctx* ctx) {
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  ctx->D = DevState{};
+  ctx->N = 0;
+}
+
+template <class T>
+swale_status dalloc(swale_ctx* ctx, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T) + 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, SWALE_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  ctx->allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return SWALE_OK;
+}
+
+swale_status alloc_state(swale_ctx* ctx, int64_t N, DevState& D) {
+  const size_t n = (size_t)N, n1 = n + 1, n2 = n + 2;
+  double** cells[] = {&D.E0, &D.M0, &D.B0, &D.Ea, &D.Ma, &D.Ba, &D.Eb, &D.Mb,
+                      &D.Bb, &D.YE, &D.YM, &D.YB, &D.J0, &D.J1, &D.J2};
+  for (double** p : cells)
+    if (swale_status s = dalloc(ctx, p, n)) return s;
+  double** nodes[] = {&D.x, &D.w, &D.P};
+  for (double** p : nodes)
+    if (swale_status s = dalloc(ctx, p, n1)) return s;
+  double** edges[] = {&D.eEL, &D.eER, &D.eBL, &D.eBR, &D.ehL, &D.ehR, &D.euL, &D.euR};
+  for (double** p : edges)
+    if (swale_status s = dalloc(ctx, p, n2)) return s;
+  if (swale_status s = dalloc(ctx, &D.flags, n2)) return s;
+  if (swale_status s = dalloc(ctx, &D.S, 1)) return s;
+  return SWALE_OK;
+}
+
+swale_status check_config(const swale_config* c, std::string& why) {
+  if (!(c->g > 0) || !(c->eps_weno > 0) || !(c->eps_pp >= 0) || !(c->h_dry >= 0)) {
+    why = "g, eps_weno must be > 0 and eps_pp, h_dry >= 0";
+    return SWALE_EINVAL;
+  }
+  if (!(c->dt_fixed > 0) && !(c->cfl > 0)) {
+    why = "cfl must be > 0 unless dt_fixed > 0";
+    return SWALE_EINVAL;
+  }
+  if (c->bc < 0 || c->bc > 2) {
+    why = "bc must be 0 (periodic), 1 (transmissive) or 2 (reflective)";
+    return SWALE_EINVAL;
+  }
+  if (c->mesh < 0 || c->mesh > 2) {
+    why = "mesh must be 0 (static), 1 (profile) or 2 (fluid_gauss)";
+    return SWALE_EINVAL;
+  }
+  if (c->mesh == SWALE_MESH_PROFILE && !(c->mesh_T > 0)) {
+    why = "mesh_T must be > 0 for profile motion";
+    return SWALE_EINVAL;
+  }
+  if (c->mesh == SWALE_MESH_FLUID_GAUSS) {
+    if (c->gauss_half < 0 || c->gauss_half > kMaxGaussHalf || !(c->gauss_sigma > 0)) {
+      why = "fluid_gauss needs gauss_sigma > 0 and 0 <= gauss_half <= 64";
+      return SWALE_EINVAL;
+    }
+    if (c->bc == SWALE_BC_PERIODIC) {
+      why = "fluid_gauss motion fixes the end nodes and needs a non-periodic domain";
+      return SWALE_EINVAL;
+    }
+  }
+  return SWALE_OK;
+}
+
+enum { FAM_PROLOGUE = 0, FAM_MESH = 1, FAM_RECON = 2, FAM_UPDATE = 3, FAM_COUNT = 4 };
+
+// Runs launch() on the context's stream; with timing enabled, brackets it by two events.
+template <class F>
+swale_status timed_launch(swale_ctx* ctx, int family, F&& launch) {
+  if (!ctx->timing) {
+    launch();
+    return SWALE_OK;
+  }
+  while (ctx->ev_pool.size() < ctx->ev_used + 2) {
+    cudaEvent_t e;
+    SW_CUDA(ctx, cudaEventCreate(&e));
+    ctx->ev_pool.push_back(e);
+  }
+  SW_CUDA(ctx, cudaEventRecord(ctx->ev_pool[ctx->ev_used], ctx->stream));
+  launch();
+  SW_CUDA(ctx, cudaEventRecord(ctx->ev_pool[ctx->ev_used + 1], ctx->stream));
+  ctx->ev_family.push_back(family);
+  ctx->ev_used += 2;
+  return SWALE_OK;
+}
+
+// Enqueues one step on the context's stream.
+swale_status enqueue_step(swale_ctx* ctx) {
+  const StepConst K = step_const(ctx);
+  DevState& D = ctx->D;
+  const int64_t N = ctx->N;
+  cudaStream_t s = ctx->stream;
+  const unsigned gr = (unsigned)((N + 2 + kReconThreads - 1) / kReconThreads);
+  const unsigned gu = (unsigned)((N + kUpdateThreads - 1) / kUpdateThreads);
+  const RhsOut none{nullptr, nullptr, nullptr, 0.0};
+  swale_status st = SWALE_OK;
+  auto L = [&](int fam, auto&& f) {
+    if (st == SWALE_OK) st = timed_launch(ctx, fam, f);
+  };
+  L(FAM_PROLOGUE, [&] { k_prologue<<<1, 32, 0, s>>>(K, D.S); });
+  if (K.mesh == SWALE_MESH_FLUID_GAUSS) {
+    const int T = 256;
+    const unsigned gm = (unsigned)((N + 1 + T - 1) / T);
+    const size_t shm = (size_t)(T + 2 * K.gauss_half + 2) * sizeof(double);
+    L(FAM_MESH, [&] { k_mesh_gauss<<<gm, T, shm, s>>>(K, D); });
+  }
+  L(FAM_RECON, [&] { k_recon<1><<<gr, kReconThreads, 0, s>>>(K, D, D.E0, D.M0, D.B0, D.J0); });
+  L(FAM_UPDATE, [&] { k_update<1, 0><<<gu, kUpdateThreads, 0, s>>>(K, D, D.E0, D.M0, D.B0, D.J0, none); });
+  L(FAM_RECON, [&] { k_recon<2><<<gr, kReconThreads, 0, s>>>(K, D, D.Ea, D.Ma, D.Ba, D.J1); });
+  L(FAM_UPDATE, [&] { k_update<2, 0><<<gu, kUpdateThreads, 0, s>>>(K, D, D.Ea, D.Ma, D.Ba, D.J1, none); });
+  L(FAM_RECON, [&] { k_recon<3><<<gr, kReconThreads, 0, s>>>(K, D, D.Eb, D.Mb, D.Bb, D.J2); });
+  L(FAM_UPDATE, [&] { k_update<3, 0><<<gu, kUpdateThreads, 0, s>>>(K, D, D.Eb, D.Mb, D.Bb, D.J2, none); });
+  if (st) return st;
+  SW_CUDA(ctx, cudaGetLastError());
+  return SWALE_OK;
+}
+
+// Enqueues n steps: whole graphs of kGraphSteps steps, then single steps (graphs are not
+// used while kernel timing is on).
+swale_status enqueue_steps(swale_ctx* ctx, int64_t n) {
+  constexpr int kGraphSteps = 8;
+  if (!ctx->timing && n >= kGraphSteps) {
+    if (!ctx->graph) {
+      cudaGraph_t g;
+      SW_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      swale_status cs = SWALE_OK;
+      for (int i = 0; i < kGraphSteps && cs == SWALE_OK; ++i) cs = enqueue_step(ctx);
+      cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+      if (cs) return cs;
+      if (e != cudaSuccess) return fail(ctx, SWALE_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&ctx->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(ctx, SWALE_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+      ctx->graph_steps = kGraphSteps;
+    }
+    while (n >= ctx->graph_steps) {
+      SW_CUDA(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+      n -= ctx->graph_steps;
+    }
+  }
+  for (; n > 0; --n)
+    if (swale_status s = enqueue_step(ctx)) return s;
+  return SWALE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+swale_status swale_create(swale_ctx** out, const swale_config* cfg, void* cuda_stream) {
+  if (!out || !cfg) return SWALE_EINVAL;
+  *out = nullptr;
+  std::string why;
+  if (check_config(cfg, why) != SWALE_OK) return SWALE_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return SWALE_EINVAL;
+  }
+  swale_ctx* ctx = new swale_ctx();
+  ctx->cfg = *cfg;
+  ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (!ctx->stream) {
+    // The legacy default stream cannot be captured into a graph: use a private blocking
+    // stream, which is still ordered with the legacy default stream.
+    if (cudaStreamCreate(&ctx->stream) != cudaSuccess) {
+      cudaGetLastError();
+      delete ctx;
+      return SWALE_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  *out = ctx;
+  return SWALE_OK;
+}
+
+swale_status swale_set_problem(swale_ctx* ctx, int64_t N, const double* x_nodes, const double* q0, const double* hu,
+                               const double* b, const double* profile, int32_t q0_is_eta) {
+  if (!ctx) return SWALE_EINVAL;
+  if (N < 5) return fail(ctx, SWALE_EINVAL, "N must be >= 5");
+  if (!x_nodes || !q0 || !hu || !b) return fail(ctx, SWALE_EINVAL, "x_nodes, q0, hu and b are required");
+  if (ctx->cfg.mesh == SWALE_MESH_PROFILE && !profile)
+    return fail(ctx, SWALE_EINVAL, "profile motion needs the node profile");
+  std::vector<double> x, q, m, bb, P;
+  swale_status s;
+  if ((s = fetch(ctx, x_nodes, N + 1, x)) || (s = fetch(ctx, q0, N, q)) || (s = fetch(ctx, hu, N, m)) ||
+      (s = fetch(ctx, b, N, bb)))
+    return s;
+  if (profile) {
+    if ((s = fetch(ctx, profile, N + 1, P))) return s;
+  } else {
+    P.assign(N + 1, 0.0);
+  }
+  std::vector<double> E(N), J(N);
+  double jmax = 0.0, jmin = INFINITY, pmax = 0.0;
+  for (int64_t k = 0; k <= N; ++k) {
+    if (!std::isfinite(x[k]) || !std::isfinite(P[k])) return fail(ctx, SWALE_EINVAL, "non-finite node or profile");
+    pmax = std::max(pmax, std::fabs(P[k]));
+  }
+  for (int64_t j = 0; j < N; ++j) {
+    J[j] = x[j + 1] - x[j];
+    if (!(J[j] > 0.0)) return fail(ctx, SWALE_EINVAL, "nodes must be strictly increasing");
+    jmax = std::max(jmax, J[j]);
+    jmin = std::min(jmin, J[j]);
+    if (!std::isfinite(q[j]) || !std::isfinite(m[j]) || !std::isfinite(bb[j]))
+      return fail(ctx, SWALE_EINVAL, "non-finite cell average");
+    E[j] = q0_is_eta ? q[j] : q[j] + bb[j];
+    if (E[j] - bb[j] < 0.0) return fail(ctx, SWALE_EINVAL, "negative depth in the initial data");
+  }
+  free_state(ctx);
+  if ((s = alloc_state(ctx, N, ctx->D))) {
+    free_state(ctx);
+    return s;
+  }
+  ctx->N = N;
+  ctx->Wbar_profile = (ctx->cfg.mesh == SWALE_MESH_PROFILE) ? kTwoPi / ctx->cfg.mesh_T * pmax : 0.0;
+  DevState& D = ctx->D;
+  cudaStream_t st = ctx->stream;
+  const size_t cb = N * sizeof(double), nb = (N + 1) * sizeof(double);
+  SW_CUDA(ctx, cudaMemcpyAsync(D.E0, E.data(), cb, cudaMemcpyHostToDevice, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(D.M0, m.data(), cb, cudaMemcpyHostToDevice, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(D.B0, bb.data(), cb, cudaMemcpyHostToDevice, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(D.J0, J.data(), cb, cudaMemcpyHostToDevice, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(D.x, x.data(), nb, cudaMemcpyHostToDevice, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(D.P, P.data(), nb, cudaMemcpyHostToDevice, st));
+  SW_CUDA(ctx, cudaMemsetAsync(D.w, 0, nb, st));
+  SW_CUDA(ctx, cudaMemsetAsync(D.flags, 0, N + 2, st));
+  DevScalars S0;
+  std::memset(&S0, 0, sizeof(S0));
+  double jmaxv = jmax, jminv = jmin;
+  std::memcpy(&S0.JmaxN, &jmaxv, 8);
+  std::memcpy(&S0.JminN, &jminv, 8);
+  S0.Wbar = ctx->Wbar_profile;
+  SW_CUDA(ctx, cudaMemcpyAsync(D.S, &S0, sizeof(S0), cudaMemcpyHostToDevice, st));
+  if (ctx->cfg.mesh == SWALE_MESH_FLUID_GAUSS) {
+    const int H = ctx->cfg.gauss_half;
+    std::vector<double> gw(2 * kMaxGaussHalf + 1, 0.0);
+    for (int mm = -H; mm <= H; ++mm)
+      gw[mm + H] = std::exp(-(double)(mm * mm) / (2.0 * ctx->cfg.gauss_sigma * ctx->cfg.gauss_sigma));
+    SW_CUDA(ctx, cudaMemcpyToSymbolAsync(c_gauss_w, gw.data(), gw.size() * sizeof(double), 0,
+                                         cudaMemcpyHostToDevice, st));
+  }
+  SW_CUDA(ctx, cudaStreamSynchronize(st));
+  return SWALE_OK;
+}
+
+swale_status swale_step(swale_ctx* ctx, double* dt_out) {
+  if (!ctx) return SWALE_EINVAL;
+  if (ctx->N == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  if (swale_status s = enqueue_step(ctx)) return s;
+  if (dt_out) {
+    SW_CUDA(ctx, cudaMemcpyAsync(dt_out, &ctx->D.S->dt, sizeof(double), cudaMemcpyDefault, ctx->stream));
+    SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return SWALE_OK;
+}
+
+swale_status swale_advance(swale_ctx* ctx, int64_t max_steps, int64_t* steps_done) {
+  if (!ctx) return SWALE_EINVAL;
+  if (ctx->N == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  if (max_steps < 0) return fail(ctx, SWALE_EINVAL, "max_steps < 0");
+  long long s0 = 0;
+  SW_CUDA(ctx, cudaMemcpyAsync(&s0, &ctx->D.S->steps, sizeof(s0), cudaMemcpyDeviceToHost, ctx->stream));
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (swale_status s = enqueue_steps(ctx, max_steps)) return s;
+  long long s1 = 0;
+  unsigned int bits = 0;
+  SW_CUDA(ctx, cudaMemcpyAsync(&s1, &ctx->D.S->steps, sizeof(s1), cudaMemcpyDeviceToHost, ctx->stream));
+  SW_CUDA(ctx, cudaMemcpyAsync(&bits, &ctx->D.S->status, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (steps_done) *steps_done = s1 - s0;
+  if (bits & swale::ST_NONFINITE) return fail(ctx, SWALE_ENONFINITE, "non-finite value in a stage");
+  if (bits & swale::ST_EMESH) return fail(ctx, SWALE_EMESH, "non-positive cell width");
+  if (bits & swale::ST_EWEIGHT) return fail(ctx, SWALE_EWEIGHT, "non-positive linear weight");
+  return SWALE_OK;
+}
+
+swale_status swale_enqueue(swale_ctx* ctx, int64_t nsteps) {
+  if (!ctx) return SWALE_EINVAL;
+  if (ctx->N == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  if (nsteps < 0) return fail(ctx, SWALE_EINVAL, "nsteps < 0");
+  return enqueue_steps(ctx, nsteps);
+}
+
+swale_status swale_set_timing(swale_ctx* ctx, int32_t enable) {
+  if (!ctx) return SWALE_EINVAL;
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->timing = enable != 0;
+  ctx->ev_used = 0;
+  ctx->ev_family.clear();
+  return SWALE_OK;
+}
+
+swale_status swale_get_timing(swale_ctx* ctx, double* ms, int64_t* launches) {
+  if (!ctx) return SWALE_EINVAL;
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double acc[FAM_COUNT] = {0, 0, 0, 0};
+  int64_t cnt[FAM_COUNT] = {0, 0, 0, 0};
+  for (size_t i = 0; i < ctx->ev_family.size(); ++i) {
+    float m = 0.f;
+    SW_CUDA(ctx, cudaEventElapsedTime(&m, ctx->ev_pool[2 * i], ctx->ev_pool[2 * i + 1]));
+    acc[ctx->ev_family[i]] += m;
+    cnt[ctx->ev_family[i]] += 1;
+  }
+  for (int f = 0; f < FAM_COUNT; ++f) {
+    if (ms) ms[f] = acc[f];
+    if (launches) launches[f] = cnt[f];
+  }
+  return SWALE_OK;
+}
+
+swale_status swale_get_state(swale_ctx* ctx, double* h, double* hu, double* b, double* eta, double* x_nodes,
+                             double* t) {
+  if (!ctx) return SWALE_EINVAL;
+  if (ctx->N == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  const int64_t N = ctx->N;
+  const size_t cb = N * sizeof(double);
+  swale_status s;
+  if ((s = put_out(ctx, hu, ctx->D.M0, cb)) || (s = put_out(ctx, b, ctx->D.B0, cb)) ||
+      (s = put_out(ctx, eta, ctx->D.E0, cb)) || (s = put_out(ctx, x_nodes, ctx->D.x, cb + sizeof(double))) ||
+      (s = put_out(ctx, t, &ctx->D.S->t, sizeof(double))))
+    return s;
+  if (h) {
+    std::vector<double> E(N), B(N);
+    SW_CUDA(ctx, cudaMemcpyAsync(E.data(), ctx->D.E0, cb, cudaMemcpyDeviceToHost, ctx->stream));
+    SW_CUDA(ctx, cudaMemcpyAsync(B.data(), ctx->D.B0, cb, cudaMemcpyDeviceToHost, ctx->stream));
+    SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int64_t j = 0; j < N; ++j) E[j] -= B[j];
+    SW_CUDA(ctx, cudaMemcpyAsync(h, E.data(), cb, cudaMemcpyDefault, ctx->stream));
+  }
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SWALE_OK;
+}
+
+swale_status swale_get_flags(swale_ctx* ctx, uint8_t* flags) {
+  if (!ctx || !flags) return SWALE_EINVAL;
+  if (ctx->N == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  SW_CUDA(ctx, cudaMemcpyAsync(flags, ctx->D.flags + 1, ctx->N, cudaMemcpyDefault, ctx->stream));
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SWALE_OK;
+}
+
+swale_status swale_get_status(swale_ctx* ctx, uint32_t* status_bits, int64_t* steps, double* last_dt) {
+  if (!ctx) return SWALE_EINVAL;
+  if (ctx->N == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  DevScalars S;
+  SW_CUDA(ctx, cudaMemcpyAsync(&S, ctx->D.S, sizeof(S), cudaMemcpyDeviceToHost, ctx->stream));
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (status_bits) *status_bits = S.status;
+  if (steps) *steps = S.steps;
+  if (last_dt) *last_dt = S.dt;
+  return SWALE_OK;
+}
+
+swale_status swale_rhs(swale_ctx* ctx, int64_t N, const double* E, const double* M, const double* B,
+                       const double* J, const double* w, double alpha, double* RE, double* RM, double* RB,
+                       double* A_out, uint8_t* flags, uint32_t* status_bits) {
+  if (!ctx) return SWALE_EINVAL;
+  if (N < 5) return fail(ctx, SWALE_EINVAL, "N must be >= 5");
+  if (!E || !M || !B || !J || !w || !RE || !RM || !RB) return fail(ctx, SWALE_EINVAL, "null array");
+  swale_ctx tmp;
+  tmp.cfg = ctx->cfg;
+  tmp.stream = ctx->stream;
+  DevState& D = tmp.D;
+  swale_status s = alloc_state(&tmp, N, D);
+  double* R3 = nullptr;
+  if (!s) s = dalloc(&tmp, &R3, 3 * (size_t)N);
+  auto cleanup = [&](swale_status r) {
+    cudaStreamSynchronize(tmp.stream);
+    free_state(&tmp);
+    if (r != SWALE_OK) ctx->err = tmp.err;
+    return r;
+  };
+  if (s) return cleanup(s);
+  tmp.N = N;
+  const size_t cb = N * sizeof(double);
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaSuccess;
+  e = e ? e : cudaMemcpyAsync(D.E0, E, cb, cudaMemcpyDefault, st);
+  e = e ? e : cudaMemcpyAsync(D.M0, M, cb, cudaMemcpyDefault, st);
+  e = e ? e : cudaMemcpyAsync(D.B0, B, cb, cudaMemcpyDefault, st);
+  e = e ? e : cudaMemcpyAsync(D.J0, J, cb, cudaMemcpyDefault, st);
+  e = e ? e : cudaMemcpyAsync(D.w, w, cb + sizeof(double), cudaMemcpyDefault, st);
+  std::vector<double> Jh(N);
+  e = e ? e : cudaMemcpyAsync(Jh.data(), J, cb, cudaMemcpyDefault, st);
+  e = e ? e : cudaStreamSynchronize(st);
+  if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
+  double jmax = 0.0;
+  for (double v : Jh) jmax = std::max(jmax, v);
+  DevScalars S0;
+  std::memset(&S0, 0, sizeof(S0));
+  std::memcpy(&S0.Jmax[0], &jmax, 8);
+  std::memcpy(&S0.Jmax[1], &jmax, 8);
+  e = cudaMemcpyAsync(D.S, &S0, sizeof(S0), cudaMemcpyHostToDevice, st);
+  if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
+  StepConst K = step_const(&tmp);
+  K.t_end = 0.0;
+  const unsigned gr = (unsigned)((N + 2 + kReconThreads - 1) / kReconThreads);
+  const unsigned gu = (unsigned)((N + kUpdateThreads - 1) / kUpdateThreads);
+  k_recon<2><<<gr, kReconThreads, 0, st>>>(K, D, D.E0, D.M0, D.B0, D.J0);
+  // k_recon<2> accumulates into S.A[1]; read it back to form alpha when not given.
+  unsigned long long Abits = 0;
+  e = cudaMemcpyAsync(&Abits, &D.S->A[1], 8, cudaMemcpyDeviceToHost, st);
+  e = e ? e : cudaStreamSynchronize(st);
+  if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
+  double A;
+  std::memcpy(&A, &Abits, 8);
+  if (!(alpha > 0.0)) {
+    std::vector<double> wh(N + 1);
+    cudaMemcpy(wh.data(), w, (N + 1) * sizeof(double), cudaMemcpyDefault);
+    double wb = 0.0;
+    for (double v : wh) wb = std::max(wb, std::fabs(v));
+    alpha = A + wb;
+  }
+  RhsOut ro{R3, R3 + N, R3 + 2 * N, alpha};
+  k_update<2, 1><<<gu, kUpdateThreads, 0, st>>>(K, D, D.E0, D.M0, D.B0, D.J0, ro);
+  e = cudaGetLastError();
+  e = e ? e : cudaMemcpyAsync(RE, ro.RE, cb, cudaMemcpyDefault, st);
+  e = e ? e : cudaMemcpyAsync(RM, ro.RM, cb, cudaMemcpyDefault, st);
+  e = e ? e : cudaMemcpyAsync(RB, ro.RB, cb, cudaMemcpyDefault, st);
+  unsigned int bits = 0;
+  e = e ? e : cudaMemcpyAsync(&bits, &D.S->status, sizeof(bits), cudaMemcpyDeviceToHost, st);
+  e = e ? e : cudaStreamSynchronize(st);
+  if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
+  if (flags) {
+    // Stage-2 recon does not store flags; recompute them through a stage-1 reconstruction.
+    S0.counter = 0;
+    S0.Jmin0 = 0x3ff0000000000000ull;
+    e = cudaMemcpyAsync(D.S, &S0, sizeof(S0), cudaMemcpyHostToDevice, st);
+    k_recon<1><<<gr, kReconThreads, 0, st>>>(K, D, D.E0, D.M0, D.B0, D.J0);
+    e = e ? e : cudaGetLastError();
+    e = e ? e : cudaMemcpyAsync(flags, D.flags + 1, N, cudaMemcpyDefault, st);
+    e = e ? e : cudaStreamSynchronize(st);
+    if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
+  }
+  if (A_out) *A_out = A;
+  if (status_bits) *status_bits = bits;
+  return cleanup(SWALE_OK);
+}
+
+const char* swale_last_error(const swale_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void swale_destroy(swale_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_state(ctx);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+"""FP64 operation counts per cell of the stage kernels (roofline numerator).
+
+Builds csrc/opcount.cpp with g++: the kernels' own per-cell code (swale_cell.cuh) compiled
+on the host with an operation-counting scalar type. A fused multiply-add counts as two
+operations (one multiplication, one addition); a division or a square root counts as one.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = [os.path.join(_HERE, "csrc", "opcount.cpp"), os.path.join(_HERE, "csrc", "swale_cell.cuh")]
+_LIB = os.path.join(_HERE, "libswale_opcount.so")
+BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
+# RK combination of a stage per cell (stage-2 form): per variable J0*q, 0.75*(.), dt*R, Y+(.),
+# 0.25*(.), sum -> 6 operations; one reciprocal of the stage width; three products.
+RK_OPS = 3 * 6 + 1 + 3
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(p) for p in _SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC[0]], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB)
+        _lib.opc_count_stage.restype = None
+    return _lib
+
+
+def count_stage(E, M, B, J, bc="transmissive", g=9.812, eps_weno=1e-6, eps_pp=1e-11, h_dry=1e-6, alpha=10.0,
+                sample=None):
+    E, M, B, J = (np.ascontiguousarray(a, dtype=np.float64) for a in (E, M, B, J))
+    N = E.size
+    n = N if sample is None else min(N, sample)
+    c0 = (N - n) // 2
+    out = np.zeros(18)
+    vp = ctypes.c_void_p
+    lib().opc_count_stage(ctypes.c_int64(N), vp(E.ctypes.data), vp(M.ctypes.data), vp(B.ctypes.data),
+                          vp(J.ctypes.data), ctypes.c_int32(BC[bc]), ctypes.c_double(g), ctypes.c_double(eps_weno),
+                          ctypes.c_double(eps_pp), ctypes.c_double(h_dry), ctypes.c_double(alpha),
+                          ctypes.c_int64(c0), ctypes.c_int64(c0 + n), vp(out.ctypes.data))
+    rec, rhs, flux = out[0:5] / n, out[5:10] / n, out[10:15] / n
+    rf = float(rec[:4].sum())
+    uf = float(rhs[:4].sum() - flux[:4].sum() + RK_OPS)
+    return {"recon": dict(zip(("add", "mul", "div", "sqrt", "cmp"), map(float, rec))),
+            "rhs_two_fluxes": dict(zip(("add", "mul", "div", "sqrt", "cmp"), map(float, rhs))),
+            "one_flux": dict(zip(("add", "mul", "div", "sqrt", "cmp"), map(float, flux))),
+            "recon_flops": rf, "update_flops": uf, "stage_flops": rf + uf, "cells_counted": n,
+            "classes": [int(v) for v in out[15:18]]}

@@ -1,0 +1,41 @@
+"""The C ABI library loads and exports every entry point that include/swale.h declares
+(no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(swale_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("swale_create", "swale_set_problem", "swale_step", "swale_advance", "swale_get_state",
+                 "swale_get_flags", "swale_rhs", "swale_last_error", "swale_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2208_06588_gb300 import binding, build
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    L = ctypes.CDLL(binding.LIB_PATH)
+    missing = [n for n in declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_abi():
+    from paper_2208_06588_gb300 import binding
+    for n in declared_symbols():
+        assert hasattr(binding, n), n

@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+Tolerances (from the scheme's arithmetic): max relative error 1e-11 on smooth runs, L1 relative
+error 1e-9 on shock and wet/dry runs; identical stage-1 detector classes except where the
+oracle's gamma lies within 1e-12 (relative) of a threshold 1/2 or 1 (FMA contraction on the
+GPU changes the last bits, so such ties may fall either way; both answers are valid classes).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_06588_gb300 import binding as B
+from paper_2208_06588_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RNG = np.random.default_rng(20220812 + 7)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2208_06588_gb300 import build
+    build.build()
+    B.lib()
+
+
+def cfg_of(pr, **kw):
+    d = dict(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, gauss_sigma=pr.gauss_sigma,
+             t_end=pr.t_end, dt_fixed=pr.dt_fixed, bc=pr.bc, mesh=pr.mesh, gauss_half=pr.gauss_half)
+    d.update(kw)
+    return B.make_config(**d)
+
+
+def params_of(pr, **kw):
+    d = dict(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, gauss_sigma=pr.gauss_sigma,
+             t_end=pr.t_end, dt_fixed=pr.dt_fixed, bc=pr.bc, mesh=pr.mesh, gauss_half=pr.gauss_half)
+    d.update(kw)
+    return oracle.Params(**d)
+
+
+def run_both(pr, nsteps, **kw):
+    s = B.Solver(cfg_of(pr, **kw))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    done = s.advance(nsteps)
+    g = s.state()
+    bits, steps, _ = s.status()
+    s.close()
+    st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+    r = oracle.run(params_of(pr, **kw), st, pr.profile, nsteps=nsteps)
+    assert done == r["steps"] == steps
+    return g, st, r, bits
+
+
+def max_rel(a, r, floor=0.0):
+    return np.abs(a - r).max() / max(np.abs(r).max(), floor, 1e-300)
+
+
+def l1_rel(a, r, J, floor=0.0):
+    return np.sum(J * np.abs(a - r)) / max(np.sum(J * np.abs(r)), floor, 1e-300)
+
+
+def near_tie(gam, tol=1e-12):
+    return (np.abs(gam - 0.5) <= tol * np.maximum(1, gam)) | (np.abs(gam - 1.0) <= tol * np.maximum(1, gam))
+
+
+# --------------------------------------------------------------------------------------------
+# One stage: the semi-discrete right-hand side (rows a2-a9) on ragged sizes and all boundaries
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("bc", ["periodic", "transmissive", "reflective"])
+@pytest.mark.parametrize("N", [5, 7, 127, 128, 129, 300, 1000])
+def test_rhs_parity(bc, N):
+    x = np.concatenate([[0.0], np.cumsum(RNG.uniform(0.6, 1.4, N))]) / N
+    J = np.diff(x)
+    xc = 0.5 * (x[1:] + x[:-1])
+    Bv = 0.5 + 0.3 * np.sin(5 * xc) + 0.2 * (xc > 0.6)
+    h = 1.0 + 0.4 * np.cos(3 * xc) + 0.5 * (xc < 0.3) + 1e-3 * RNG.normal(size=N)
+    h[N // 2:N // 2 + 2] = 0.0  # a dry patch exercises the limiter
+    E = h + Bv
+    M = h * (0.3 * np.sin(7 * xc) + 0.5 * (xc > 0.45))
+    w = RNG.normal(size=N + 1) * 0.05
+    w[0] = w[-1] = 0.0
+    P = oracle.Params(bc=bc)
+    RE, RM, RB, alpha, st = oracle.rhs(P, E, M, Bv, J, w)
+    ed, flags, gam, A, _ = oracle.reconstruct(P, E, M, Bv, J)
+    ctx = B.swale_create(B.make_config(bc=bc))
+    gRE, gRM, gRB = np.zeros(N), np.zeros(N), np.zeros(N)
+    gflags = np.zeros(N, dtype=np.uint8)
+    gA, bits = B.swale_rhs(ctx, N, E, M, Bv, J, w, alpha, gRE, gRM, gRB, gflags)
+    B.swale_destroy(ctx)
+    assert abs(gA - A) <= 1e-13 * A
+    scale = max(np.abs(RE).max(), np.abs(RM).max(), np.abs(RB).max())
+    for g, r in ((gRE, RE), (gRM, RM), (gRB, RB)):
+        assert np.abs(g - r).max() <= 1e-11 * scale
+    ok = (gflags == flags[1:-1]) | near_tie(gam[1:-1])
+    assert ok.all(), np.nonzero(~ok)
+    assert (bits & ~B.BIT_NEGDEPTH) == (st & ~B.BIT_NEGDEPTH)
+
+
+def test_rhs_lake_at_rest_identity():
+    """At rest the GPU right-hand side gives R_M = 0 and R_E = c (w_{j+1} - w_j) to round-off."""
+    N = 257
+    x = np.concatenate([[0.0], np.cumsum(RNG.uniform(0.5, 1.5, N))])
+    J = np.diff(x)
+    Bv = RNG.uniform(0.0, 3.0, N)
+    E = np.full(N, 5.0)
+    w = RNG.normal(size=N + 1) * 0.1
+    ctx = B.swale_create(B.make_config(bc="transmissive"))
+    RE, RM, RB = np.zeros(N), np.zeros(N), np.zeros(N)
+    B.swale_rhs(ctx, N, E, np.zeros(N), Bv, J, w, 20.0, RE, RM, RB)
+    B.swale_destroy(ctx)
+    assert np.abs(RM).max() < 1e-11 * 25 * 9.812
+    assert np.abs(RE - 5.0 * np.diff(w)).max() < 1e-12
+
+
+# --------------------------------------------------------------------------------------------
+# Whole steps
+# --------------------------------------------------------------------------------------------
+def test_smooth_periodic_full_run():
+    """Single small instance (N = 200, sine motion, CFL 0.6) to t_end = 0.1."""
+    pr = W.smooth_periodic(200)
+    g, st, r, bits = run_both(pr, 10 ** 6)
+    assert r["steps"] > 300 and abs(g["t"] - 0.1) < 1e-15 and abs(st.t - 0.1) < 1e-15
+    for a, b in ((g["eta"], st.E), (g["hu"], st.M), (g["b"], st.B)):
+        assert max_rel(a, b) < 1e-11
+    assert np.abs(g["x"] - st.x).max() < 1e-13
+    assert bits == 0
+
+
+def test_smooth_periodic_lake_at_rest():
+    pr = W.smooth_periodic(200, lake=True)
+    g, st, r, bits = run_both(pr, 10 ** 6)
+    assert np.abs(g["eta"] - 6.0).max() < 1e-12 and np.abs(g["hu"]).max() < 1e-12
+    assert max_rel(g["b"], st.B) < 1e-12
+
+
+def test_accuracy_problem_parity():
+    pr = W.accuracy_test(100)
+    g, st, r, bits = run_both(pr, 10 ** 6)
+    for a, b in ((g["eta"], st.E), (g["hu"], st.M), (g["b"], st.B)):
+        assert max_rel(a, b) < 1e-11
+
+
+def test_lake_at_rest_paper_smooth_bottom():
+    pr = W.lake_at_rest(200, "smooth")
+    g, st, r, bits = run_both(pr, 10 ** 6)
+    assert np.abs(g["eta"] - 10.0).max() < 1e-11 and np.abs(g["hu"]).max() < 1e-11
+    assert max_rel(g["b"], st.B) < 1e-11
+
+
+@pytest.mark.parametrize("which", ["moses1", "moses2"])
+def test_wet_dry_riemann_parity(which):
+    pr = W.moses_first(200, t_end=2.0) if which == "moses1" else W.moses_second(200, t_end=1.0)
+    g, st, r, bits = run_both(pr, 10 ** 6)
+    J = st.J
+    for a, b in ((g["eta"], st.E), (g["hu"], st.M), (g["b"], st.B)):
+        assert l1_rel(a, b, J, floor=1e-12) < 1e-9
+    assert (g["eta"] - g["b"]).min() > -1e-8
+
+
+def oracle_sensitivity(pr, nsteps):
+    """L1-relative response of the oracle itself, per variable, to a relative perturbation of
+    1e-16 of the initial surface: the conditioning of the run, which bounds how closely any
+    implementation with a different rounding order can agree with it."""
+    P = params_of(pr)
+    a = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+    oracle.run(P, a, pr.profile, nsteps=nsteps)
+    Ep = pr.E * (1.0 + 1e-16 * np.random.default_rng(3).standard_normal(pr.N))
+    b = oracle.State(Ep, pr.hu, pr.b, pr.J, pr.x)
+    oracle.run(P, b, pr.profile, nsteps=nsteps)
+    return [l1_rel(u, v, a.J, floor=1e-12) for u, v in ((b.E, a.E), (b.M, a.M), (b.B, a.B))]
+
+
+def test_dam_break_dry_small_parity():
+    """Dam break over the bump into the dry region (fluid-driven mesh), 150 steps. The run is
+    ill-conditioned at the dam: the oracle moves by ~3e-9 (L1-rel in hu) under a 1e-16 input
+    perturbation, so the bar is max(1e-9, 10 x that measured sensitivity)."""
+    pr = W.dam_break_dry(N=5000)
+    g, st, r, bits = run_both(pr, 150)
+    sens = oracle_sensitivity(pr, 150)
+    J = st.J
+    for (a, b), s in zip(((g["eta"], st.E), (g["hu"], st.M), (g["b"], st.B)), sens):
+        assert l1_rel(a, b, J, floor=1e-12) < max(1e-9, 10.0 * s)
+    assert np.abs(g["x"] - st.x).max() < 1e-12
+
+
+def test_dam_break_dry_small_parity_short():
+    """The same workload before the dam's instability amplifies rounding: plain 1e-9 bar."""
+    pr = W.dam_break_dry(N=5000)
+    g, st, r, bits = run_both(pr, 40)
+    for a, b in ((g["eta"], st.E), (g["hu"], st.M), (g["b"], st.B)):
+        assert l1_rel(a, b, st.J, floor=1e-12) < 1e-9
+
+
+def test_dam_break_dry_full_size():
+    """The benchmark workload at its full size (N = 2^20), in the launch configuration the
+    benchmark times, for a few steps."""
+    pr = W.dam_break_dry()
+    g, st, r, bits = run_both(pr, 3)
+    J = st.J
+    for a, b in ((g["eta"], st.E), (g["hu"], st.M), (g["b"], st.B)):
+        assert l1_rel(a, b, J, floor=1e-12) < 1e-9
+    assert np.abs(g["x"] - st.x).max() < 1e-12
+
+
+@pytest.mark.parametrize("name", ["smooth_periodic", "accuracy", "dam_break_dry"])
+def test_step1_flags_identical(name):
+    pr = {"smooth_periodic": lambda: W.smooth_periodic(200), "accuracy": lambda: W.accuracy_test(400),
+          "dam_break_dry": lambda: W.dam_break_dry(N=20000)}[name]()
+    _, _, gam, _, _ = oracle.reconstruct(params_of(pr), pr.E, pr.hu, pr.b, pr.J)
+    s = B.Solver(cfg_of(pr))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    s.step()
+    gflags = s.flags()
+    s.close()
+    st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+    r = oracle.run(params_of(pr), st, pr.profile, nsteps=1)
+    ok = (gflags == r["flags"]) | near_tie(gam[1:-1])
+    assert ok.all()
+
+
+def test_dt_sequence_matches():
+    pr = W.smooth_periodic(200)
+    s = B.Solver(cfg_of(pr))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    gdt = [s.step() for _ in range(20)]
+    s.close()
+    st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+    r = oracle.run(params_of(pr), st, pr.profile, nsteps=20, record=True)
+    np.testing.assert_allclose(gdt, r["dts"], rtol=1e-13)
+
+
+@pytest.mark.parametrize("N", [5, 6, 129, 255, 257])
+@pytest.mark.parametrize("bc", ["periodic", "reflective"])
+def test_small_and_ragged_sizes(N, bc):
+    x = np.linspace(0.0, 1.0, N + 1)
+    xc = 0.5 * (x[1:] + x[:-1])
+    b = 0.2 * np.sin(2 * np.pi * xc) ** 2
+    E = 1.0 + 0.05 * np.exp(-((xc - 0.4) / 0.1) ** 2)
+    prof = 0.02 * np.sin(2 * np.pi * x)
+    prof[0] = prof[-1] = 0.0
+    pr = W.Problem(name="ragged", x=x, h=E - b, hu=0.1 * (E - b), b=b, E=E, profile=prof, bc=bc, mesh="profile",
+                   mesh_T=1.0, t_end=0.05)
+    g, st, r, bits = run_both(pr, 10 ** 5)
+    for a, b_ in ((g["eta"], st.E), (g["hu"], st.M), (g["b"], st.B)):
+        assert max_rel(a, b_, floor=1e-3) < 1e-11
+
+
+# --------------------------------------------------------------------------------------------
+# Errors come back as status codes
+# --------------------------------------------------------------------------------------------
+def test_invalid_inputs_are_rejected():
+    ctx = B.swale_create(B.make_config())
+    x = np.linspace(0, 1, 11)
+    ok = np.ones(10)
+    with pytest.raises(B.SwaleError) as e:
+        B.swale_set_problem(ctx, 4, x[:5], ok[:4], ok[:4], ok[:4])
+    assert e.value.code == -1
+    bad = x.copy()
+    bad[3] = bad[2]
+    with pytest.raises(B.SwaleError):
+        B.swale_set_problem(ctx, 10, bad, ok, ok, 0 * ok)
+    with pytest.raises(B.SwaleError):
+        B.swale_set_problem(ctx, 10, x, -ok, ok, 0 * ok)
+    nan = ok.copy()
+    nan[4] = np.nan
+    with pytest.raises(B.SwaleError):
+        B.swale_set_problem(ctx, 10, x, nan, ok, 0 * ok)
+    with pytest.raises(B.SwaleError):
+        B.swale_step(ctx)  # no problem set
+    B.swale_destroy(ctx)
+    with pytest.raises(B.SwaleError):
+        B.swale_create(B.make_config(bc=7))
