@@ -143,6 +143,29 @@ swale_status swale_rhs(swale_ctx* ctx, int64_t N, const double* E, const double*
                        const double* J, const double* w, double alpha, double* RE, double* RM, double* RB,
                        double* A_out, uint8_t* flags, uint32_t* status_bits);
 
+/* Allocation-free variant of swale_rhs, for callers that cannot call cudaMalloc (code running
+ * inside another framework's memory pool, or work recorded into a CUDA graph whose device
+ * memory must not grow). The paper has no counterpart: this is a library-side addition.
+ *   cfg, cuda_stream   configuration and stream (NULL = legacy default stream); no context
+ *   N                  number of cells, 5 <= N <= 65536 (SWALE_NOALLOC_MAX_CELLS)
+ *   E, M, B, J, w      device pointers: surface, discharge, bottom, widths (N), node velocities (N+1)
+ *   alpha              the global viscosity, > 0 (it is not derived here)
+ *   RE, RM, RB         device pointers, N values each: the right-hand side
+ *   A_out              host pointer or NULL: largest edge wave speed; when given, the call
+ *                      synchronises the stream, otherwise it returns after enqueueing
+ *   flags              N bytes (host or device) or NULL: detector classes
+ * Scratch lives in one fixed array of about 4.3 MB per device, held from library load until
+ * the process exits; the call allocates nothing and clears what it reuses. Every call shares
+ * that array, so calls that overlap on the GPU (other streams, other host threads) race; run
+ * them one after the other. The first call on a device looks up the array's device address;
+ * make that first call before any stream capture.
+ * Errors: SWALE_EINVAL (N out of range, alpha <= 0, null or host pointer where a device pointer
+ * is required, bad config), SWALE_ECUDA. */
+#define SWALE_NOALLOC_MAX_CELLS 65536
+swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64_t N, const double* E,
+                               const double* M, const double* B, const double* J, const double* w, double alpha,
+                               double* RE, double* RM, double* RB, double* A_out, uint8_t* flags);
+
 /* Message of the last error of this context ("" if none). Never NULL. */
 const char* swale_last_error(const swale_ctx* ctx);
 

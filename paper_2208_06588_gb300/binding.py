@@ -64,11 +64,12 @@ def lib():
         L.swale_get_status.argtypes = [vp, P(ctypes.c_uint32), P(i64), P(d)]
         L.swale_rhs.argtypes = [vp, i64, vp, vp, vp, vp, vp, d, vp, vp, vp, P(d), vp, P(ctypes.c_uint32)]
         L.swale_enqueue.argtypes = [vp, i64]
+        L.swale_rhs_noalloc.argtypes = [P(SwaleConfig), vp, i64, vp, vp, vp, vp, vp, d, vp, vp, vp, P(d), vp]
         L.swale_set_timing.argtypes = [vp, i32]
         L.swale_get_timing.argtypes = [vp, vp, vp]
         for name in ("swale_create", "swale_set_problem", "swale_step", "swale_advance", "swale_get_state",
                      "swale_get_flags", "swale_get_status", "swale_rhs", "swale_enqueue", "swale_set_timing",
-                     "swale_get_timing"):
+                     "swale_get_timing", "swale_rhs_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         L.swale_last_error.argtypes = [vp]
         L.swale_last_error.restype = ctypes.c_char_p
@@ -157,6 +158,20 @@ def swale_rhs(ctx, N, E, M, B, J, w, alpha, RE, RM, RB, flags=None):
     _check(ctx, lib().swale_rhs(ctx, int(N), ptr(E), ptr(M), ptr(B), ptr(J), ptr(w), float(alpha), ptr(RE),
                                 ptr(RM), ptr(RB), ctypes.byref(A), ptr(flags), ctypes.byref(bits)))
     return A.value, bits.value
+
+
+NOALLOC_MAX_CELLS = 65536
+
+
+def swale_rhs_noalloc(cfg: SwaleConfig, stream, N, E, M, B, J, w, alpha, RE, RM, RB, flags=None, want_A=True):
+    """Allocation-free right-hand side: device arrays in and out, scratch in a fixed device array."""
+    A = ctypes.c_double(0)
+    code = lib().swale_rhs_noalloc(ctypes.byref(cfg), stream, int(N), ptr(E), ptr(M), ptr(B), ptr(J), ptr(w),
+                                   float(alpha), ptr(RE), ptr(RM), ptr(RB), ctypes.byref(A) if want_A else None,
+                                   ptr(flags))
+    if code != SWALE_OK:
+        raise SwaleError(code, "swale_rhs_noalloc")
+    return A.value
 
 
 def swale_last_error(ctx):

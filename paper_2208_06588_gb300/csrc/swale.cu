@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -947,6 +948,135 @@ swale_status swale_rhs(swale_ctx* ctx, int64_t N, const double* E, const double*
   if (A_out) *A_out = A;
   if (status_bits) *status_bits = bits;
   return cleanup(SWALE_OK);
+}
+
+}  // extern "C"
+
+// ======================================================================================
+// Allocation-free right-hand side (swale_rhs_noalloc)
+// ======================================================================================
+// Some callers cannot call cudaMalloc: code that runs inside another framework's memory
+// pool, or between the captures of a CUDA graph that must not grow device memory. For them
+// swale_rhs_noalloc evaluates the same right-hand side as swale_rhs with its scratch (the
+// edge values, detector classes and reduction scalars) in the fixed array below, which
+// every GPU that loads this library holds until the process exits.
+namespace {
+
+constexpr int64_t kNoAllocMaxCells = 65536;
+constexpr int kNoAllocMaxDevices = 64;
+
+struct NoAllocScratch {
+  double edges[8][kNoAllocMaxCells + 2];
+  uint8_t flags[kNoAllocMaxCells + 2];
+  DevScalars S;
+};
+
+// Fixed scratch of the allocation-free entry point (about 4.3 MB per device).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+// Device address of g_noalloc_scratch per device, obtained once with that device current.
+void* g_noalloc_addr[kNoAllocMaxDevices];
+std::once_flag g_noalloc_once[kNoAllocMaxDevices];
+cudaError_t g_noalloc_err[kNoAllocMaxDevices];
+
+// Max of the widths into S->Jmax[0] (the global cell length of the indicators).
+__global__ void k_noalloc_maxJ(const double* __restrict__ J, int64_t N, DevScalars* S) {
+  double m = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, J[i]);
+  block_max_to(&S->Jmax[0], m);
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64_t N, const double* E,
+                               const double* M, const double* B, const double* J, const double* w, double alpha,
+                               double* RE, double* RM, double* RB, double* A_out, uint8_t* flags) {
+  if (!cfg || !E || !M || !B || !J || !w || !RE || !RM || !RB) return SWALE_EINVAL;
+  if (N < 5 || N > kNoAllocMaxCells || !(alpha > 0.0)) return SWALE_EINVAL;
+  if (!(cfg->g > 0) || !(cfg->eps_weno > 0) || !(cfg->eps_pp >= 0) || !(cfg->h_dry >= 0) || cfg->bc < 0 ||
+      cfg->bc > 2)
+    return SWALE_EINVAL;
+  const void* dev_ptrs[] = {E, M, B, J, w, RE, RM, RB};
+  for (const void* p : dev_ptrs)
+    if (!on_device(p)) return SWALE_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    cudaGetLastError();
+    return SWALE_ECUDA;
+  }
+  // First call on this device: look up the device address of the scratch array.
+  std::call_once(g_noalloc_once[dev], [dev] {
+    g_noalloc_err[dev] = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch);
+  });
+  if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_addr[dev]) return SWALE_ECUDA;
+  NoAllocScratch* scr = reinterpret_cast<NoAllocScratch*>(g_noalloc_addr[dev]);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+
+  DevState D{};
+  D.eEL = scr->edges[0];
+  D.eER = scr->edges[1];
+  D.eBL = scr->edges[2];
+  D.eBR = scr->edges[3];
+  D.ehL = scr->edges[4];
+  D.ehR = scr->edges[5];
+  D.euL = scr->edges[6];
+  D.euR = scr->edges[7];
+  D.flags = scr->flags;
+  D.S = &scr->S;
+  D.w = const_cast<double*>(w);
+  StepConst K;
+  K.sc.g = cfg->g;
+  K.sc.eps_weno = cfg->eps_weno;
+  K.sc.eps_pp = cfg->eps_pp;
+  K.sc.h_dry = cfg->h_dry;
+  K.sc.beta_dx_global = cfg->beta_dx_global;
+  K.cfl = 1.0;
+  K.t_end = 0.0;
+  K.dt_fixed = 0.0;
+  K.mesh_T = 1.0;
+  K.Wbar_profile = 0.0;
+  K.N = N;
+  K.bc = cfg->bc;
+  K.mesh = SWALE_MESH_STATIC;
+  K.gauss_half = 0;
+  // The scalars keep the previous call's contents: start them from zero (J^n minimum at 1 so
+  // the stage-1 time-step arithmetic stays finite; its result is not used here).
+  DevScalars S0;
+  std::memset(&S0, 0, sizeof(S0));
+  S0.Jmin0 = 0x3ff0000000000000ull;
+  cudaError_t e = cudaMemcpyAsync(&scr->S, &S0, sizeof(S0), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return SWALE_ECUDA;
+  const unsigned gr = (unsigned)((N + 2 + kReconThreads - 1) / kReconThreads);
+  const unsigned gu = (unsigned)((N + kUpdateThreads - 1) / kUpdateThreads);
+  k_noalloc_maxJ<<<64, 256, 0, st>>>(J, N, &scr->S);
+  k_recon<1><<<gr, kReconThreads, 0, st>>>(K, D, E, M, B, J);
+  RhsOut ro{RE, RM, RB, alpha};
+  k_update<2, 1><<<gu, kUpdateThreads, 0, st>>>(K, D, E, M, B, J, ro);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, scr->flags + 1, (size_t)N, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && A_out) {
+    unsigned long long bits = 0;
+    e = cudaMemcpyAsync(&bits, &scr->S.A[0], sizeof(bits), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) std::memcpy(A_out, &bits, sizeof(double));
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SWALE_ECUDA;
+  }
+  return SWALE_OK;
 }
 
 const char* swale_last_error(const swale_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
