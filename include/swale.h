@@ -154,7 +154,7 @@ swale_status swale_rhs(swale_ctx* ctx, int64_t N, const double* E, const double*
  *   A_out              host pointer or NULL: largest edge wave speed; when given, the call
  *                      synchronises the stream, otherwise it returns after enqueueing
  *   flags              N bytes (host or device) or NULL: detector classes
- * Scratch lives in one fixed array of about 4.3 MB per device, held from library load until
+ * Scratch lives in one fixed array of about 5.3 MB per device, held from library load until
  * the process exits; the call allocates nothing and clears what it reuses. Every call shares
  * that array, so calls that overlap on the GPU (other streams, other host threads) race; run
  * them one after the other. The first call on a device looks up the array's device address;

@@ -51,10 +51,11 @@ void take(opc::Counts& into, double* out) {
 
 extern "C" {
 
-// Counts over cells [c0, c1) of one stage state. out[0..4]: reconstruction (add, mul, div,
-// sqrt, cmp) summed over the cells; out[5..9]: right-hand side (two interface fluxes, the
-// source, the flux differences) summed; out[10..14]: one interface flux (the redundant half
-// of the right-hand side); out[15..17]: number of smooth / transition / non-smooth cells.
+// Counts over cells [c0, c1) of one stage state. out[0..4]: reconstruction per cell summed
+// (add, mul, div, sqrt, cmp): the pair and triple terms a cell owns plus recon_cell;
+// out[5..9]: update per cell summed: one interface flux, the cell's reciprocal width, the
+// source geometry and source, the flux differences (the RK combination is added in Python);
+// out[10..14]: one interface flux alone; out[15..17]: smooth / transition / non-smooth cells.
 void opc_count_stage(int64_t N, const double* E, const double* M, const double* B, const double* J, int32_t bc,
                      double g, double eps_weno, double eps_pp, double h_dry, double alpha, int64_t c0, int64_t c1,
                      double* out) {
@@ -62,41 +63,71 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
   swale::SchemeConst P{g, eps_weno, eps_pp, h_dry, 1};
   double dxmax = 0.0;
   for (int64_t j = 0; j < N; ++j) dxmax = J[j] > dxmax ? J[j] : dxmax;
-  opc::Counts rec, rhs, flux;
+  opc::Counts rec, upd, flux;
   long long cls[3] = {0, 0, 0};
+  auto add_to = [](opc::Counts& a) {
+    a.add += opc::C.add; a.mul += opc::C.mul; a.div += opc::C.div; a.sqrt += opc::C.sqrt; a.cmp += opc::C.cmp;
+  };
   for (int64_t c = c0; c < c1; ++c) {
-    CD Jv[5], Ev[5], Mv[5], Bv[5];
-    for (int k = 0; k < 5; ++k) {
-      const int64_t i = c - 2 + k, s = wrap(i, N, bc);
+    CD Jv[7], V[3][7];  // cells c-3 .. c+3
+    for (int k = 0; k < 7; ++k) {
+      const int64_t i = c - 3 + k, s = wrap(i, N, bc);
       Jv[k] = J[s];
-      Ev[k] = E[s];
-      Bv[k] = B[s];
-      Mv[k] = (bc == 2 && (i < 0 || i >= N)) ? -M[s] : M[s];
+      V[0][k] = E[s];
+      V[1][k] = (bc == 2 && (i < 0 || i >= N)) ? -M[s] : M[s];
+      V[2][k] = B[s];
     }
+    // Divided differences of the stencil (uncounted: each pair / triple is counted once below).
+    swale::StencilDD DD;
+    CD ip[6], d2[3][6], it[5];
+    for (int m = 0; m < 6; ++m) {
+      ip[m] = CD(1.0 / (Jv[m].v + Jv[m + 1].v));
+      for (int v = 0; v < 3; ++v) d2[v][m] = CD((V[v][m + 1].v - V[v][m].v) * ip[m].v);
+    }
+    for (int m = 0; m < 5; ++m) it[m] = CD(1.0 / (Jv[m].v + Jv[m + 1].v + Jv[m + 2].v));
+    for (int v = 0; v < 3; ++v) {
+      for (int a = 0; a < 4; ++a) DD.D2[v][a] = d2[v][a + 1];
+      for (int a = 0; a < 3; ++a) DD.D3[v][a] = CD((d2[v][a + 2].v - d2[v][a + 1].v) * it[a + 1].v);
+    }
+    // The work one cell owns: its pair (c, c+1) and its triple, counted with the kernel's code.
+    opc::C = opc::Counts();
+    const CD ipc = swale::pair_recip(Jv[3], Jv[4]);
+    for (int v = 0; v < 3; ++v) (void)swale::pair_dd(V[v][3], V[v][4], ipc);
+    const CD itc = swale::triple_recip(Jv[2], Jv[3], Jv[4]);
+    for (int v = 0; v < 3; ++v) (void)swale::triple_dd(d2[v][2], d2[v][3], itc);
+    CD h5[5], v0[3][3];
+    for (int k = 0; k < 5; ++k) h5[k] = Jv[k + 1];
+    for (int v = 0; v < 3; ++v)
+      for (int a = 0; a < 3; ++a) v0[v][a] = V[v][a + 1];
     swale::EdgeState o;
     uint8_t flag;
     CD wl, wr;
     uint32_t st = 0;
-    opc::C = opc::Counts();
-    swale::recon_cell(P, Jv, Ev, Mv, Bv, CD(dxmax), o, flag, wl, wr, st);
-    rec.add += opc::C.add; rec.mul += opc::C.mul; rec.div += opc::C.div; rec.sqrt += opc::C.sqrt;
-    rec.cmp += opc::C.cmp;
+    swale::recon_cell(P, h5, v0, DD, CD(dxmax), o, flag, wl, wr, st);
+    add_to(rec);
     cls[flag] += 1;
-    // Right-hand side of the cell with its own edges standing in for the neighbours' (the
-    // operation count does not depend on the values except through max/min branches).
+    // Update: one flux (the cell's right interface, with its own edges standing in for the
+    // neighbour's), its reciprocal width, the source and the flux differences.
     opc::C = opc::Counts();
-    swale::rhs_cell(CD(g), CD(alpha), CD(0.01), CD(0.02), o.ER, o.BR, o.hR, o.uR, o.EL, o.ER, o.BL, o.BR, o.hL,
-                    o.hR, o.uL, o.uR, o.EL, o.BL, o.hL, o.uL, Ev[1], Ev[2], Ev[3], Bv[1], Bv[2], Bv[3], Jv[1],
-                    Jv[2], Jv[3]);
-    rhs.add += opc::C.add; rhs.mul += opc::C.mul; rhs.div += opc::C.div; rhs.sqrt += opc::C.sqrt;
-    rhs.cmp += opc::C.cmp;
+    const swale::Flux F = swale::interface_flux(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL, o.uR,
+                                                o.uL);
+    const CD iJc = CD(1.0) / Jv[3];
+    const swale::SourceGeom sg =
+        swale::source_geom(Jv[2], Jv[3], CD(1.0 / Jv[2].v), iJc, CD(1.0 / Jv[4].v), ip[2], ip[3], it[2]);
+    const CD hd[5] = {V[0][2] - V[2][2], V[0][3] - V[2][3], V[0][4] - V[2][4], o.hL, o.hR};
+    const CD bd[5] = {V[2][2], V[2][3], V[2][4], o.BL, o.BR};
+    const CD Sj = swale::source_cell(CD(g), hd, bd, sg);
+    (void)swale::cell_rhs(F, F, Sj);
+    add_to(upd);
+    // The three depth averages above are formed once per cell in the kernel: remove the two
+    // extra subtractions counted for the neighbours.
+    upd.add -= 2;
     opc::C = opc::Counts();
-    swale::interface_flux(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL, o.uR, o.uL);
-    flux.add += opc::C.add; flux.mul += opc::C.mul; flux.div += opc::C.div; flux.sqrt += opc::C.sqrt;
-    flux.cmp += opc::C.cmp;
+    (void)swale::interface_flux(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL, o.uR, o.uL);
+    add_to(flux);
   }
   take(rec, out);
-  take(rhs, out + 5);
+  take(upd, out + 5);
   take(flux, out + 10);
   out[15] = (double)cls[0];
   out[16] = (double)cls[1];

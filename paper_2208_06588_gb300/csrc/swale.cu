@@ -54,6 +54,7 @@ struct DevScalars {
 struct StepConst {
   SchemeConst sc;
   double cfl, t_end, dt_fixed, mesh_T, Wbar_profile;
+  double gauss_wsum;  // sum of the full Gaussian window, summed from -H to H
   int64_t N;
   int32_t bc, mesh;
   int32_t gauss_half;
@@ -68,6 +69,7 @@ struct DevState {
   double *J0, *J1, *J2;        // J^n, J^(1), J^(2)
   double *x, *w, *P;           // nodes, node velocities, motion profile (N+1)
   double *eEL, *eER, *eBL, *eBR, *ehL, *ehR, *euL, *euR;
+  double *ipair, *itri;        // N+2: 1/(J_c + J_{c+1}) and 1/(J_{c-1} + J_c + J_{c+1}) of the stage mesh
   uint8_t* flags;              // N+2, stage-1 classes
   DevScalars* S;
 };
@@ -145,53 +147,63 @@ __global__ void k_prologue(StepConst K, DevScalars* S) {
 
 // ------------------------------------------------------------------------------------
 // Fluid-driven node velocity: raw_k = (u_{k-1} + u_k)/2 for k = 1..N-1 (u = hu/h, dry -> 0),
-// truncated renormalised Gaussian filter, w_0 = w_N = 0. One thread per node; the block
-// stages the cell velocities it needs in shared memory.
+// truncated renormalised Gaussian filter, w_0 = w_N = 0. One thread per node; the block stages
+// the cell velocities, the raw node velocities and its filtered nodes in shared memory.
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_mesh_gauss(StepConst K, DevState D) {
-  extern __shared__ double sh[];  // raw node velocity for nodes [k0 - H, k0 + T + H]
+  extern __shared__ double sh[];
   DevScalars* S = D.S;
   if (S->done) return;
   const int64_t N = K.N;
-  const int H = K.gauss_half, T = blockDim.x;
-  const int64_t k0 = (int64_t)blockIdx.x * T;
-  const int span = T + 2 * H + 2;
-  for (int i = threadIdx.x; i < span; i += T) {
-    const int64_t k = k0 - H + i;  // node index
-    double raw = 0.0;
-    if (k >= 1 && k <= N - 1) {
-      const double hl = D.E0[k - 1] - D.B0[k - 1], hr = D.E0[k] - D.B0[k];
-      const double ul = hl > K.sc.h_dry ? D.M0[k - 1] / hl : 0.0;
-      const double ur = hr > K.sc.h_dry ? D.M0[k] / hr : 0.0;
-      raw = 0.5 * (ul + ur);
+  const int H = K.gauss_half, T = blockDim.x, tid = threadIdx.x;
+  const int64_t k0 = (int64_t)blockIdx.x * T;  // first node of the tile
+  const int nu = T + 2 * H + 2, nr = T + 2 * H + 1;
+  double* su = sh;         // cell velocities, cells [k0 - H - 1, k0 + T + H]
+  double* sraw = sh + nu;  // raw node velocities, nodes [k0 - H, k0 + T + H]
+  double* sw = sraw + nr;  // filtered velocities, nodes [k0, k0 + T]
+  for (int i = tid; i < nu; i += T) {
+    const int64_t c = k0 - H - 1 + i;
+    double u = 0.0;
+    if (c >= 0 && c < N) {
+      const double h = D.E0[c] - D.B0[c];
+      u = h > K.sc.h_dry ? D.M0[c] / h : 0.0;
     }
-    sh[i] = raw;
+    su[i] = u;
   }
   __syncthreads();
-  // Each thread computes w at node k = k0 + tid and at k + 1 (for the difference).
-  double wv[2];
-  for (int s = 0; s < 2; ++s) {
-    const int64_t k = k0 + threadIdx.x + s;
+  for (int i = tid; i < nr; i += T) {
+    const int64_t k = k0 - H + i;
+    sraw[i] = (k >= 1 && k <= N - 1) ? 0.5 * (su[i] + su[i + 1]) : 0.0;
+  }
+  __syncthreads();
+  for (int i = tid; i <= T; i += T) {
+    const int64_t k = k0 + i;
     double v = 0.0;
     if (k >= 1 && k <= N - 1) {
-      double acc = 0.0, wsum = 0.0;
-      for (int m = -H; m <= H; ++m) {
-        const int64_t q = k + m;
-        if (q < 1 || q > N - 1) continue;
-        const double gw = c_gauss_w[m + H];
-        acc += gw * sh[(int)(q - (k0 - H))];
-        wsum += gw;
+      double acc = 0.0;
+      if (k - H >= 1 && k + H <= N - 1) {
+        for (int m = -H; m <= H; ++m) acc += c_gauss_w[m + H] * sraw[i + m + H];
+        v = acc / K.gauss_wsum;
+      } else {
+        double wsum = 0.0;
+        for (int m = -H; m <= H; ++m) {
+          const int64_t q = k + m;
+          if (q < 1 || q > N - 1) continue;
+          acc += c_gauss_w[m + H] * sraw[i + m + H];
+          wsum += c_gauss_w[m + H];
+        }
+        v = acc / wsum;
       }
-      v = acc / wsum;
     }
-    wv[s] = v;
+    sw[i] = v;
   }
-  const int64_t k = k0 + threadIdx.x;
+  __syncthreads();
+  const int64_t k = k0 + tid;
   double wa = 0.0, dwa = 0.0;
   if (k <= N) {
-    D.w[k] = wv[0];
-    wa = fabs(wv[0]);
-    if (k < N) dwa = fabs(wv[1] - wv[0]);
+    D.w[k] = sw[tid];
+    wa = fabs(sw[tid]);
+    if (k < N) dwa = fabs(sw[tid + 1] - sw[tid]);
   }
   block_max_to(&S->Wabs, wa);
   block_max_to(&S->dWabs, dwa);
@@ -200,35 +212,78 @@ __global__ void __launch_bounds__(256) k_mesh_gauss(StepConst K, DevState D) {
 // ------------------------------------------------------------------------------------
 // Reconstruction + limiter of cells -1..N for stage STAGE, wave-speed reduction; in stage 1
 // the last block computes dt (and the secant factor of the prescribed motion).
+// A block owns kReconThreads consecutive cells: it stages their 5-cell stencils (tile plus a
+// 2-cell halo each side) in shared memory, computes each pair's and each triple's reciprocal
+// width and divided differences once, then reconstructs one cell per thread. It also stores
+// the pair / triple reciprocals for the update kernel of the same stage.
 // ------------------------------------------------------------------------------------
 template <int STAGE>
 __global__ void __launch_bounds__(kReconThreads) k_recon(StepConst K, DevState D, const double* __restrict__ E,
                                                          const double* __restrict__ M, const double* __restrict__ B,
                                                          const double* __restrict__ J) {
+  constexpr int T = kReconThreads;
+  __shared__ double sJ[T + 4], sV[3][T + 4];  // cells c0-2 .. c0+T+1
+  __shared__ double sIP[T + 3], sD2[3][T + 3];  // pairs starting at those cells
+  __shared__ double sIT[T + 2], sD3[3][T + 2];  // triples centred at cells c0-1 .. c0+T
   DevScalars* S = D.S;
   if (S->done) return;
   const int64_t N = K.N;
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - 1;
+  const int tid = threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.x * T - 1;  // first cell of the tile (cells -1..N)
+  const bool refl = (K.bc == SWALE_BC_REFLECTIVE);
+  for (int i = tid; i < T + 4; i += T) {
+    const int64_t c = c0 - 2 + i;
+    double jv = 1.0, ev = 0.0, mv = 0.0, bv = 0.0;  // filler beyond the last ghost cell
+    if (c >= -3 && c <= N + 2) {
+      const int64_t s = ghost(c, N, K.bc);
+      jv = J[s];
+      ev = E[s];
+      bv = B[s];
+      mv = M[s];
+      if (refl && (c < 0 || c >= N)) mv = -mv;
+    }
+    sJ[i] = jv;
+    sV[0][i] = ev;
+    sV[1][i] = mv;
+    sV[2][i] = bv;
+  }
+  __syncthreads();
+  for (int i = tid; i < T + 3; i += T) {
+    const double ip = swale::pair_recip(sJ[i], sJ[i + 1]);
+    sIP[i] = ip;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) sD2[v][i] = swale::pair_dd(sV[v][i], sV[v][i + 1], ip);
+  }
+  __syncthreads();
+  for (int i = tid; i < T + 2; i += T) {
+    const double it = swale::triple_recip(sJ[i], sJ[i + 1], sJ[i + 2]);
+    sIT[i] = it;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) sD3[v][i] = swale::triple_dd(sD2[v][i], sD2[v][i + 1], it);
+  }
+  __syncthreads();
+  const int64_t c = c0 + tid;
   double wave = 0.0;
   uint32_t st = 0;
   if (c <= N) {
-    double Jv[5], Ev[5], Mv[5], Bv[5];
-    const bool mirror_sign = (K.bc == SWALE_BC_REFLECTIVE);
+    double h[5], v0[3][3];
+    swale::StencilDD DD;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      const int64_t i = c - 2 + k;
-      const int64_t s = ghost(i, N, K.bc);
-      Jv[k] = J[s];
-      Ev[k] = E[s];
-      Bv[k] = B[s];
-      const double m = M[s];
-      Mv[k] = (mirror_sign && (i < 0 || i >= N)) ? -m : m;
+    for (int k = 0; k < 5; ++k) h[k] = sJ[tid + k];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) v0[v][a] = sV[v][tid + a];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) DD.D2[v][a] = sD2[v][tid + a];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) DD.D3[v][a] = sD3[v][tid + a];
     }
     const double dxmax = bitsd(S->Jmax[STAGE - 1]);
     EdgeState o;
     uint8_t flag;
     double wl, wr;
-    swale::recon_cell(K.sc, Jv, Ev, Mv, Bv, dxmax, o, flag, wl, wr, st);
+    swale::recon_cell(K.sc, h, v0, DD, dxmax, o, flag, wl, wr, st);
     const int64_t idx = c + 1;
     D.eEL[idx] = o.EL;
     D.eER[idx] = o.ER;
@@ -238,6 +293,8 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(StepConst K, DevState D
     D.ehR[idx] = o.hR;
     D.euL[idx] = o.uL;
     D.euR[idx] = o.uR;
+    D.ipair[idx] = sIP[tid + 2];  // pair (c, c+1)
+    D.itri[idx] = sIT[tid + 1];   // triple centred at c
     if (STAGE == 1) D.flags[idx] = flag;
     // Edges that touch interfaces 0..N only.
     if (c == -1) wave = wr;
@@ -297,7 +354,10 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(StepConst K, DevState D
 
 // ------------------------------------------------------------------------------------
 // Fluxes, source and the RK combination of stage STAGE for cells 0..N-1 (MODE 0), or the
-// bare right-hand side (MODE 1, used by swale_rhs).
+// bare right-hand side (MODE 1, used by swale_rhs). A block owns kUpdateThreads consecutive
+// cells: each of its interfaces' fluxes is computed once into shared memory, the widths,
+// their reciprocals and the depth / bottom averages of the tile plus one halo cell each
+// side are staged there too.
 // ------------------------------------------------------------------------------------
 struct RhsOut {
   double *RE, *RM, *RB;
@@ -309,46 +369,77 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(StepConst K, DevState
                                                            const double* __restrict__ M,
                                                            const double* __restrict__ B,
                                                            const double* __restrict__ Js, RhsOut ro) {
+  constexpr int T = kUpdateThreads;
+  __shared__ double sF[4][T + 1], sW[T + 1];               // interfaces / nodes j0 .. j0+T
+  __shared__ double sJ[T + 2], siJ[T + 2], sH[T + 2], sB[T + 2];  // cells j0-1 .. j0+T
   DevScalars* S = D.S;
   if (MODE == 0 && S->done) return;
   const int64_t N = K.N;
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int tid = threadIdx.x;
+  const int64_t j0 = (int64_t)blockIdx.x * T;
+  double alpha, dt = 0.0;
+  if (MODE == 1) {
+    alpha = ro.alpha;
+  } else {
+    alpha = (STAGE == 1) ? S->alpha1 : bitsd(S->A[STAGE - 1]) + S->Wbar;
+    dt = S->dt;
+  }
+  const double sdiff = (MODE == 0 && STAGE == 1 && K.mesh == SWALE_MESH_PROFILE) ? S->sdiff : 0.0;
+  for (int i = tid; i <= T; i += T) {
+    const int64_t k = j0 + i;  // node / interface index
+    if (k <= N) {
+      double wk;
+      if (MODE == 0 && STAGE == 1 && K.mesh == SWALE_MESH_PROFILE) {
+        wk = D.P[k] * sdiff;
+        if (i < T || k == N) D.w[k] = wk;
+      } else if (MODE == 0 && K.mesh == SWALE_MESH_STATIC) {
+        wk = 0.0;
+      } else {
+        wk = D.w[k];
+      }
+      sW[i] = wk;
+      // Interface k: left state = right edge of cell k-1 (edge index k), right state = left
+      // edge of cell k (edge index k+1).
+      const swale::Flux F = swale::interface_flux(K.sc.g, alpha, wk, D.eER[k], D.eEL[k + 1], D.eBR[k], D.eBL[k + 1],
+                                                  D.ehR[k], D.ehL[k + 1], D.euR[k], D.euL[k + 1]);
+      sF[0][i] = F.FE;
+      sF[1][i] = F.FMm;
+      sF[2][i] = F.FMp;
+      sF[3][i] = F.FB;
+    }
+  }
+  for (int i = tid; i < T + 2; i += T) {
+    const int64_t c = j0 - 1 + i;
+    if (c >= -1 && c <= N) {
+      const int64_t s = ghost(c, N, K.bc);
+      const double jv = Js[s];
+      sJ[i] = jv;
+      siJ[i] = 1.0 / jv;
+      sH[i] = E[s] - B[s];
+      sB[i] = B[s];
+    }
+  }
+  __syncthreads();
+  const int64_t j = j0 + tid;
   double jmaxa = 0.0, jmaxb = 0.0, jminb = INFINITY;
   uint32_t st = 0;
   if (j < N) {
-    double alpha, dt = 0.0;
-    if (MODE == 1) {
-      alpha = ro.alpha;
-    } else {
-      alpha = (STAGE == 1) ? S->alpha1 : bitsd(S->A[STAGE - 1]) + S->Wbar;
-      dt = S->dt;
-    }
-    // Node velocities of the two interfaces.
-    double wl, wr;
-    if (MODE == 0 && STAGE == 1 && K.mesh == SWALE_MESH_PROFILE) {
-      const double sd = S->sdiff;
-      wl = D.P[j] * sd;
-      wr = D.P[j + 1] * sd;
-      D.w[j] = wl;
-      if (j == N - 1) D.w[N] = wr;
-    } else if (K.mesh == SWALE_MESH_STATIC && MODE == 0) {
-      wl = wr = 0.0;
-    } else {
-      wl = D.w[j];
-      wr = D.w[j + 1];
-    }
-    const int64_t il = j, ic = j + 1, ir = j + 2;  // edge-array indices of cells j-1, j, j+1
-    const int64_t jm = ghost(j - 1, N, K.bc), jp = ghost(j + 1, N, K.bc);
-    const swale::CellRhs R = swale::rhs_cell(
-        K.sc.g, alpha, wl, wr, D.eER[il], D.eBR[il], D.ehR[il], D.euR[il], D.eEL[ic], D.eER[ic], D.eBL[ic],
-        D.eBR[ic], D.ehL[ic], D.ehR[ic], D.euL[ic], D.euR[ic], D.eEL[ir], D.eBL[ir], D.ehL[ir], D.euL[ir], E[jm],
-        E[j], E[jp], B[jm], B[j], B[jp], Js[jm], Js[j], Js[jp]);
+    const swale::Flux Fl = {sF[0][tid], sF[1][tid], sF[2][tid], sF[3][tid]};
+    const swale::Flux Fr = {sF[0][tid + 1], sF[1][tid + 1], sF[2][tid + 1], sF[3][tid + 1]};
+    const int64_t ic = j + 1;  // edge-array index of cell j
+    const swale::SourceGeom sg = swale::source_geom(sJ[tid], sJ[tid + 1], siJ[tid], siJ[tid + 1], siJ[tid + 2],
+                                                    D.ipair[j], D.ipair[j + 1], D.itri[j + 1]);
+    const double hd[5] = {sH[tid], sH[tid + 1], sH[tid + 2], D.ehL[ic], D.ehR[ic]};
+    const double bd[5] = {sB[tid], sB[tid + 1], sB[tid + 2], D.eBL[ic], D.eBR[ic]};
+    const double Sj = swale::source_cell(K.sc.g, hd, bd, sg);
+    const swale::CellRhs R = swale::cell_rhs(Fl, Fr, Sj);
     const double RE = R.RE, RM = R.RM, RB = R.RB;
     if (MODE == 1) {
       ro.RE[j] = RE;
       ro.RM[j] = RM;
       ro.RB[j] = RB;
     } else {
+      const double wl = sW[tid], wr = sW[tid + 1];
       const double J0 = D.J0[j];
       const double dw = wr - wl;
       if (STAGE == 1) {
@@ -427,6 +518,7 @@ struct swale_ctx {
   int64_t N = 0;
   DevState D{};
   double Wbar_profile = 0.0;
+  double gauss_wsum = 1.0;
   std::vector<void*> allocs;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
@@ -492,6 +584,7 @@ StepConst step_const(const swale_ctx* ctx) {
   K.dt_fixed = ctx->cfg.dt_fixed;
   K.mesh_T = ctx->cfg.mesh_T;
   K.Wbar_profile = ctx->Wbar_profile;
+  K.gauss_wsum = ctx->gauss_wsum;
   K.N = ctx->N;
   K.bc = ctx->cfg.bc;
   K.mesh = ctx->cfg.mesh;
@@ -532,7 +625,7 @@ swale_status alloc_state(swale_ctx* ctx, int64_t N, DevState& D) {
   double** nodes[] = {&D.x, &D.w, &D.P};
   for (double** p : nodes)
     if (swale_status s = dalloc(ctx, p, n1)) return s;
-  double** edges[] = {&D.eEL, &D.eER, &D.eBL, &D.eBR, &D.ehL, &D.ehR, &D.euL, &D.euR};
+  double** edges[] = {&D.eEL, &D.eER, &D.eBL, &D.eBR, &D.ehL, &D.ehR, &D.euL, &D.euR, &D.ipair, &D.itri};
   for (double** p : edges)
     if (swale_status s = dalloc(ctx, p, n2)) return s;
   if (swale_status s = dalloc(ctx, &D.flags, n2)) return s;
@@ -613,7 +706,7 @@ swale_status enqueue_step(swale_ctx* ctx) {
   if (K.mesh == SWALE_MESH_FLUID_GAUSS) {
     const int T = 256;
     const unsigned gm = (unsigned)((N + 1 + T - 1) / T);
-    const size_t shm = (size_t)(T + 2 * K.gauss_half + 2) * sizeof(double);
+    const size_t shm = (size_t)(3 * T + 4 * K.gauss_half + 4) * sizeof(double);
     L(FAM_MESH, [&] { k_mesh_gauss<<<gm, T, shm, s>>>(K, D); });
   }
   L(FAM_RECON, [&] { k_recon<1><<<gr, kReconThreads, 0, s>>>(K, D, D.E0, D.M0, D.B0, D.J0); });
@@ -749,6 +842,9 @@ swale_status swale_set_problem(swale_ctx* ctx, int64_t N, const double* x_nodes,
     std::vector<double> gw(2 * kMaxGaussHalf + 1, 0.0);
     for (int mm = -H; mm <= H; ++mm)
       gw[mm + H] = std::exp(-(double)(mm * mm) / (2.0 * ctx->cfg.gauss_sigma * ctx->cfg.gauss_sigma));
+    double ws = 0.0;
+    for (int mm = -H; mm <= H; ++mm) ws += gw[mm + H];
+    ctx->gauss_wsum = ws;
     SW_CUDA(ctx, cudaMemcpyToSymbolAsync(c_gauss_w, gw.data(), gw.size() * sizeof(double), 0,
                                          cudaMemcpyHostToDevice, st));
   }
@@ -966,12 +1062,12 @@ constexpr int64_t kNoAllocMaxCells = 65536;
 constexpr int kNoAllocMaxDevices = 64;
 
 struct NoAllocScratch {
-  double edges[8][kNoAllocMaxCells + 2];
+  double edges[10][kNoAllocMaxCells + 2];
   uint8_t flags[kNoAllocMaxCells + 2];
   DevScalars S;
 };
 
-// Fixed scratch of the allocation-free entry point (about 4.3 MB per device).
+// Fixed scratch of the allocation-free entry point (about 5.3 MB per device).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
 // Device address of g_noalloc_scratch per device, obtained once with that device current.
@@ -1033,6 +1129,8 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   D.ehR = scr->edges[5];
   D.euL = scr->edges[6];
   D.euR = scr->edges[7];
+  D.ipair = scr->edges[8];
+  D.itri = scr->edges[9];
   D.flags = scr->flags;
   D.S = &scr->S;
   D.w = const_cast<double*>(w);

@@ -1,21 +1,24 @@
 // Per-cell and per-interface arithmetic of one stage of the well-balanced ALE-WENO hybrid
-// scheme (Zhang, Xia & Xu, arXiv 2208.06588), written once for the device kernels.
+// scheme (Zhang, Xia & Xu, arXiv 2208.06588), shared by the device kernels and by the host
+// operation counter.
 //
-// Formulation (same mathematics as the paper's definitions, arranged for few FP64 ops):
-//  * Step 1 of Sec. 2.2: each sub-stencil quadratic p_r is the derivative of the cubic
-//    interpolating the primitive function, kept in Newton form. Its coefficients are the
-//    divided differences D2 (pairs of cells) and D3 (triples of cells) of the cell averages,
-//    and the geometry enters only through node offsets. The linear weights d_r at the two
-//    edges come from matching the coefficients of the outermost averages of the big-stencil
-//    quartic and of p_2 / p_0, also in Newton form.
-//  * Step 2: beta_r = Dx int (p_r')^2 + Dx^3 int (p_r'')^2 evaluated in closed form about
-//    the cell midpoint.
-//  * Sec. 4.1 source term: the quartic interpolants (three cell averages + two edge values)
-//    are built as the derivative of a confluent Newton (Hermite) form of their primitive;
-//    the Newton basis derivatives at the four Gauss-Legendre points are affine in the ratio
-//    of the left neighbour's width, with constant coefficients.
-// All lengths are physical; nothing here allocates or branches on data except the
-// detector classes, the limiter and the dry-edge test that the scheme itself defines.
+// Formulation (the paper's definitions, arranged for few FP64 operations; GB300 runs FP64 at
+// 1/42 of its FP32 rate and a division costs about nine FMA slots):
+//  * Step 1 of Sec. 2.2: each sub-stencil quadratic p_r is the derivative of the cubic that
+//    interpolates the primitive function, in Newton form. Its coefficients are the divided
+//    differences D2 (pairs of cells) and D3 (triples of cells) of the cell averages; these and
+//    their reciprocal widths are computed once per pair / triple and shared by the cells that
+//    use them. The linear weights d_r at the two edges have closed forms in the node offsets
+//    y0..y5 of the big stencil (obtained by matching the coefficients of the outermost
+//    averages of the big-stencil quartic and of p_2 / p_0), e.g. at x_{j+1/2}:
+//      d_2 = (y4-y3)(y5-y3) / ((y4-y0)(y5-y0)),  d_0 = (y3-y1)(y3-y0) / ((y5-y1)(y5-y0)).
+//  * Step 2: beta_r = Dx int (p_r')^2 + Dx^3 int (p_r'')^2 in closed form about the cell
+//    midpoint; the classes come from comparing tau with (beta^A + eps) and (beta^A + eps)/2.
+//  * Step 3: reciprocals of products stand in for several divisions (one division each).
+//  * Sec. 4.1 source: the quartic interpolants (three averages + two edge values) are the
+//    derivative of a confluent Newton (Hermite) form of their primitive; the Newton basis
+//    derivatives at the four Gauss-Legendre points are affine in J_{j-1}/J_j with constant
+//    coefficients.
 #pragma once
 
 #include <stdint.h>
@@ -64,182 +67,154 @@ SWALE_HD real rsqrt_(real a) { return swale_sqrt(a); }
 SWALE_HD real rsqrt_(real a) { return sqrt(a); }
 #endif
 
-// Value and derivative at x of prod_i (x - y_i), accumulated factor by factor.
-struct ProdD {
-  real p, dp;
-};
-SWALE_HD ProdD prod_push(ProdD a, real x, real y) {
-  real f = x - y;
-  ProdD r;
-  r.dp = a.dp * f + a.p;
-  r.p = a.p * f;
-  return r;
-}
+// ------------------------------------------------------------------------------------
+// Shared per-pair and per-triple terms (Step 1): reciprocal widths and divided differences.
+// ------------------------------------------------------------------------------------
+// Pair of cells (m, m+1): 1 / (J_m + J_{m+1}).
+SWALE_HD real pair_recip(real Jm, real Jp) { return 1.0 / (Jm + Jp); }
+// D2 of one variable on the pair.
+SWALE_HD real pair_dd(real vm, real vp, real ip) { return (vp - vm) * ip; }
+// Triple centred at c: 1 / (J_{c-1} + J_c + J_{c+1}).
+SWALE_HD real triple_recip(real Jm, real Jc, real Jp) { return 1.0 / (Jm + Jc + Jp); }
+// D3 of one variable on the triple from the D2 of its two pairs.
+SWALE_HD real triple_dd(real d2l, real d2r, real it) { return (d2r - d2l) * it; }
 
-// Mesh-only data of one cell from the five widths J_{j-2..j+2}.
-struct CellGeom {
-  real ip[4];    // 1 / (J_m + J_{m+1}), pairs (j-2,j-1) .. (j+1,j+2)
-  real it[3];    // 1 / (J_m + J_{m+1} + J_{m+2}), triples starting at j-2, j-1, j
-  real G1[2][3]; // G1[e][a] = (x_e - y_a) + (x_e - y_{a+1})
-  real G2[2][3]; // G2[e][a] = sum of the pairwise products of (x_e - y_{a..a+2})
-  real F[3];     // F[a] = 1.5 J_j - (y_a + y_{a+1} + y_{a+2})
-  real d[2][3];  // linear weights d_r at edge e (r = 0,1,2)
-  real c4, c3;   // beta factors: 4 Dx J_j and 3 Dx J_j^3 + 36 Dx^3 J_j
+// Divided differences of the big stencil of cell j for the three variables (eta, hu, b):
+// D2[v][a], a = 0..3 the pairs (j-2,j-1)..(j+1,j+2); D3[v][a], a = 0..2 the triples
+// starting at j-2, j-1, j.
+struct StencilDD {
+  real D2[3][4];
+  real D3[3][3];
 };
 
-SWALE_HD void cell_geom(const real J[5], real dx, CellGeom& G, uint32_t& st) {
-  // Node offsets relative to x_{j-1/2}: y0 .. y5 bound cells j-2 .. j+2.
-  const real y[6] = {-(J[0] + J[1]), -J[1], 0.0, J[2], J[2] + J[3], J[2] + J[3] + J[4]};
-  for (int m = 0; m < 4; ++m) G.ip[m] = 1.0 / (J[m] + J[m + 1]);
-  for (int m = 0; m < 3; ++m) G.it[m] = 1.0 / (J[m] + J[m + 1] + J[m + 2]);
-  const real xe[2] = {0.0, J[2]};
-  for (int e = 0; e < 2; ++e) {
-    const real x = xe[e];
-    for (int a = 0; a < 3; ++a) {
-      const real p = x - y[a], q = x - y[a + 1], r = x - y[a + 2];
-      G.G1[e][a] = p + q;
-      G.G2[e][a] = q * r + p * r + p * q;
-    }
-    // Coefficient of ubar_{j-2} in p_2(x) (Newton form from the left end of the stencil)
-    // and in the big-stencil quartic; their ratio is d_2.
-    ProdD L = {1.0, 0.0};
-    L = prod_push(L, x, y[0]);
-    L = prod_push(L, x, y[1]);
-    const real pi2d = L.dp;
-    L = prod_push(L, x, y[2]);
-    const real pi3d = L.dp;
-    L = prod_push(L, x, y[3]);
-    const real pi4d = L.dp;
-    L = prod_push(L, x, y[4]);
-    const real pi5d = L.dp;
-    const real a1 = y[2] - y[0], a2 = a1 * (y[3] - y[0]), a3 = a2 * (y[4] - y[0]), a4 = a3 * (y[5] - y[0]);
-    const real c20 = 1.0 - pi2d / a1 + pi3d / a2;
-    const real C0 = c20 - pi4d / a3 + pi5d / a4;
-    // Coefficient of ubar_{j+2} in p_0(x) and in the quartic (Newton form from the right end).
-    ProdD R = {1.0, 0.0};
-    R = prod_push(R, x, y[5]);
-    R = prod_push(R, x, y[4]);
-    const real s2d = R.dp;
-    R = prod_push(R, x, y[3]);
-    const real s3d = R.dp;
-    R = prod_push(R, x, y[2]);
-    const real s4d = R.dp;
-    R = prod_push(R, x, y[1]);
-    const real s5d = R.dp;
-    const real b1 = y[5] - y[3], b2 = b1 * (y[5] - y[2]), b3 = b2 * (y[5] - y[1]), b4 = b3 * (y[5] - y[0]);
-    const real c02 = 1.0 + s2d / b1 + s3d / b2;
-    const real C4 = c02 + s4d / b3 + s5d / b4;
-    G.d[e][2] = C0 / c20;
-    G.d[e][0] = C4 / c02;
-    G.d[e][1] = 1.0 - G.d[e][0] - G.d[e][2];
-    if (!(G.d[e][0] > 0.0) || !(G.d[e][1] > 0.0) || !(G.d[e][2] > 0.0)) st |= ST_EWEIGHT;
-  }
-  for (int a = 0; a < 3; ++a) G.F[a] = 1.5 * J[2] - (y[a] + y[a + 1] + y[a + 2]);
-  const real h0 = J[2];
-  G.c4 = 4.0 * dx * h0;
-  G.c3 = 3.0 * dx * h0 * h0 * h0 + 36.0 * dx * dx * dx * h0;
+// Reconstruction of cell j (Steps 1-4 of Sec. 2.2 with the shared indicators of
+// Eq. alphamodified), bound-preserving limiter (Eq. modifiedhjn in 1D with the 4-point
+// Gauss-Lobatto rule) and the bottom re-derivation of the Remark in Sec. 4.3.
+//   h[5]      widths J_{j-2..j+2};   v0[v][a] averages of (eta, hu, b) on cells j-2+a, a = 0..2
+//   DD        shared divided differences;   dxmax  the global cell length (Step 1)
+// Outputs the limited edge state, the class, and |u| + sqrt(g h) at both edges.
+SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
+                         real dxmax, EdgeState& o, uint8_t& flag, real& waveL, real& waveR, uint32_t& st) {
   for (int k = 0; k < 5; ++k)
-    if (!(J[k] > 0.0)) st |= ST_EMESH;
-}
-
-// Divided differences of one variable on the big stencil.
-struct DivDiff {
-  real D2[4], D3[3];
-};
-SWALE_HD void divdiff(const CellGeom& G, const real v[5], DivDiff& D) {
-  for (int m = 0; m < 4; ++m) D.D2[m] = (v[m + 1] - v[m]) * G.ip[m];
-  for (int m = 0; m < 3; ++m) D.D3[m] = (D.D2[m + 1] - D.D2[m]) * G.it[m];
-}
-
-// Sub-stencil value p_r at edge e; sub-stencil r starts at cell a = 2 - r.
-SWALE_HD real sub_value(const CellGeom& G, const DivDiff& D, const real v[5], int e, int a) {
-  return v[a] + D.D2[a] * G.G1[e][a] + D.D3[a] * G.G2[e][a];
-}
-
-// Reconstruction of one cell (Steps 1-4 of Sec. 2.2 with the shared indicators of
-// Eq. alphamodified), bound-preserving limiter (Eq. modifiedhjn in 1D, Gauss-Lobatto
-// k = 4) and the bottom re-derivation of the Remark in Sec. 4.3.
-// Returns the largest |u| + sqrt(g h) over the two edges in *wave_L / *wave_R.
-SWALE_HD void recon_cell(const SchemeConst& P, const real J[5], const real E[5], const real M[5],
-                         const real B[5], real dxmax, EdgeState& o, uint8_t& flag, real& waveL,
-                         real& waveR, uint32_t& st) {
-  const real dx = P.beta_dx_global ? dxmax : J[2];
-  CellGeom G;
-  cell_geom(J, dx, G, st);
-  DivDiff DE, DM, DB;
-  divdiff(G, E, DE);
-  divdiff(G, M, DM);
-  divdiff(G, B, DB);
-  // Indicators from the conservative variables h = eta - b and hu, summed (shared weights).
+    if (!(h[k] > 0.0)) st |= ST_EMESH;
+  const real h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3], h4 = h[4];
+  const real dx = P.beta_dx_global ? dxmax : h2;
+  // Node offsets relative to x_{j-1/2}: y0 = -(h0+h1), y1 = -h1, y2 = 0, y3 = h2,
+  // y4 = h2+h3, y5 = h2+h3+h4. Newton-form factors of p_r at the left (x = 0) and right
+  // (x = h2) edges: G1 = (x-y_a) + (x-y_{a+1}), G2 = sum of pairwise products of
+  // (x-y_a), (x-y_{a+1}), (x-y_{a+2}); sub-stencil r starts at cell a = 2 - r.
+  const real s01 = h0 + h1, s12 = h1 + h2, s23 = h2 + h3;
+  const real s012 = s01 + h2;
+  real G1[2][3], G2[2][3];
+  G1[0][0] = s01 + h1;
+  G2[0][0] = s01 * h1;
+  G1[0][1] = h1;
+  G2[0][1] = -(h1 * h2);
+  G1[0][2] = -h2;
+  G2[0][2] = h2 * s23;
+  G1[1][0] = s012 + s12;
+  G2[1][0] = s12 * h2 + s012 * (h2 + s12);
+  G1[1][1] = s12 + h2;
+  G2[1][1] = s12 * h2;
+  G1[1][2] = h2;
+  G2[1][2] = -(h2 * h3);
+  // Linear weights (closed forms), one division for the four outer weights.
+  const real Sa = s012 + h3;         // y4 - y0
+  const real Sb = Sa + h4;           // y5 - y0
+  const real Sc = s12 + h3 + h4;     // y5 - y1
+  const real inv = 1.0 / (Sa * Sb * Sc);
+  const real iab = Sc * inv, icb = Sa * inv;  // 1/(Sa Sb), 1/(Sc Sb)
+  real d[2][3];
+  d[1][2] = h3 * (h3 + h4) * iab;
+  d[1][0] = s12 * s012 * icb;
+  d[0][2] = s23 * (s23 + h4) * iab;
+  d[0][0] = h1 * s01 * icb;
+  d[0][1] = 1.0 - d[0][0] - d[0][2];
+  d[1][1] = 1.0 - d[1][0] - d[1][2];
+  if (!(d[0][1] > 0.0) || !(d[1][1] > 0.0)) st |= ST_EWEIGHT;
+  // Indicators of h = eta - b and hu, summed (shared weights). F[a] = 1.5 h2 - (y_a+y_{a+1}+y_{a+2}).
+  const real F[3] = {1.5 * h2 + s01 + h1, 0.5 * h2 + h1, -(0.5 * h2 + h3)};
+  const real c4 = 4.0 * dx * h2;
+  const real c3 = (3.0 * h2 * h2 + 36.0 * dx * dx) * dx * h2;
   real beta[3];
   for (int r = 0; r < 3; ++r) {
     const int a = 2 - r;
-    const real d2h = DE.D2[a] - DB.D2[a], d3h = DE.D3[a] - DB.D3[a];
-    const real qh = d2h + d3h * G.F[a], qm = DM.D2[a] + DM.D3[a] * G.F[a];
-    beta[r] = G.c4 * (qh * qh + qm * qm) + G.c3 * (d3h * d3h + DM.D3[a] * DM.D3[a]);
+    const real d2h = DD.D2[0][a] - DD.D2[2][a], d3h = DD.D3[0][a] - DD.D3[2][a];
+    const real qh = d2h + d3h * F[a], qm = DD.D2[1][a] + DD.D3[1][a] * F[a];
+    beta[r] = c4 * (qh * qh + qm * qm) + c3 * (d3h * d3h + DD.D3[1][a] * DD.D3[1][a]);
   }
   const real tau = dabs(beta[0] - beta[2]);
-  const real betaA = (beta[0] + beta[1] + beta[2]) * (1.0 / 3.0);
-  const real gam = tau / (betaA + P.eps_weno);
-  flag = gam <= 0.5 ? 0 : (gam >= 1.0 ? 2 : 1);
-  real X[3] = {1.0, 1.0, 1.0};
-  if (flag != 0) {
+  const real den = (beta[0] + beta[1] + beta[2]) * (1.0 / 3.0) + P.eps_weno;  // beta^A + eps
+  // gamma = tau / den: smooth if gamma <= 1/2, non-smooth if gamma >= 1.
+  flag = (tau <= 0.5 * den) ? 0 : ((tau >= den) ? 2 : 1);
+  real phi[2][3];
+  if (flag == 0) {
+    for (int e = 0; e < 2; ++e)
+      for (int r = 0; r < 3; ++r) phi[e][r] = d[e][r];
+  } else {
+    // WENO-Z: alpha_r = d_r (1 + (tau / (beta_r + eps))^2), normalised per edge.
+    const real e0 = beta[0] + P.eps_weno, e1 = beta[1] + P.eps_weno, e2 = beta[2] + P.eps_weno;
+    const real e01 = e0 * e1;
+    const real ie = tau / (e01 * e2);
+    const real q[3] = {e1 * e2 * ie, e0 * e2 * ie, e01 * ie};
+    real X[3];
+    for (int r = 0; r < 3; ++r) X[r] = 1.0 + q[r] * q[r];
+    real al[2][3];
+    for (int e = 0; e < 2; ++e)
+      for (int r = 0; r < 3; ++r) al[e][r] = d[e][r] * X[r];
+    const real sL = al[0][0] + al[0][1] + al[0][2], sR = al[1][0] + al[1][1] + al[1][2];
+    const real is = 1.0 / (sL * sR);
+    const real isL = sR * is, isR = sL * is;
     for (int r = 0; r < 3; ++r) {
-      const real q = tau / (beta[r] + P.eps_weno);
-      X[r] = 1.0 + q * q;
+      phi[0][r] = al[0][r] * isL;
+      phi[1][r] = al[1][r] * isR;
+    }
+    if (flag == 1) {
+      const real Mg = 2.0 * (tau / den) - 1.0;
+      for (int e = 0; e < 2; ++e)
+        for (int r = 0; r < 3; ++r) phi[e][r] = Mg * phi[e][r] + (1.0 - Mg) * d[e][r];
     }
   }
-  real ev[2], mv[2], bv[2];
-  for (int e = 0; e < 2; ++e) {
-    real phi[3];
-    if (flag == 0) {
-      for (int r = 0; r < 3; ++r) phi[r] = G.d[e][r];
-    } else {
-      real al[3];
-      for (int r = 0; r < 3; ++r) al[r] = G.d[e][r] * X[r];
-      const real inv = 1.0 / (al[0] + al[1] + al[2]);
-      for (int r = 0; r < 3; ++r) phi[r] = al[r] * inv;
-      if (flag == 1) {
-        const real Mg = 2.0 * gam - 1.0;
-        for (int r = 0; r < 3; ++r) phi[r] = Mg * phi[r] + (1.0 - Mg) * G.d[e][r];
+  // Edge values of eta, hu, b with the shared weights (Step 4).
+  real ev[3][2];
+  for (int v = 0; v < 3; ++v)
+    for (int e = 0; e < 2; ++e) {
+      real s = 0.0;
+      for (int r = 0; r < 3; ++r) {
+        const int a = 2 - r;
+        s += phi[e][r] * (v0[v][a] + DD.D2[v][a] * G1[e][a] + DD.D3[v][a] * G2[e][a]);
       }
+      ev[v][e] = s;
     }
-    real se = 0.0, sm = 0.0, sb = 0.0;
-    for (int r = 0; r < 3; ++r) {
-      const int a = 2 - r;
-      se += phi[r] * sub_value(G, DE, E, e, a);
-      sm += phi[r] * sub_value(G, DM, M, e, a);
-      sb += phi[r] * sub_value(G, DB, B, e, a);
-    }
-    ev[e] = se;
-    mv[e] = sm;
-    bv[e] = sb;
-  }
   // Limiter on h = eta - b with the Gauss-Lobatto mean delta; hu scaled by the same theta.
-  real hbar = E[2] - B[2];
+  real hbar = v0[0][2] - v0[2][2];
   if (hbar < -P.eps_pp) st |= ST_NEGDEPTH;
   hbar = dmax(hbar, 0.0);
-  real hL = ev[0] - bv[0], hR = ev[1] - bv[1];
+  real hL = ev[0][0] - ev[2][0], hR = ev[0][1] - ev[2][1];
   const real delta = (12.0 * hbar - hL - hR) * 0.1;
   const real mn = dmin(dmin(hL, hR), delta);
   const real epsv = dmin(P.eps_pp, hbar);
-  real mL = mv[0], mR = mv[1];
+  real mL = ev[1][0], mR = ev[1][1];
   if (mn < epsv) {
     const real theta = (hbar - epsv) / (hbar - mn);
-    const real mbar = M[2];
+    const real mbar = v0[1][2];
     hL = theta * (hL - hbar) + hbar;
     hR = theta * (hR - hbar) + hbar;
     mL = theta * (mL - mbar) + mbar;
     mR = theta * (mR - mbar) + mbar;
   }
-  o.EL = ev[0];
-  o.ER = ev[1];
+  o.EL = ev[0][0];
+  o.ER = ev[0][1];
   o.hL = hL;
   o.hR = hR;
-  o.BL = ev[0] - hL;
-  o.BR = ev[1] - hR;
-  o.uL = hL > P.h_dry ? mL / hL : 0.0;
-  o.uR = hR > P.h_dry ? mR / hR : 0.0;
+  o.BL = ev[0][0] - hL;
+  o.BR = ev[0][1] - hR;
+  // Velocities with one division: u_L = m_L h_R' / (h_L' h_R'), dry edges (h <= h_dry) -> 0.
+  const bool wetL = hL > P.h_dry, wetR = hR > P.h_dry;
+  const real hLs = wetL ? hL : real(1.0), hRs = wetR ? hR : real(1.0);
+  const real ihh = 1.0 / (hLs * hRs);
+  o.uL = wetL ? mL * hRs * ihh : real(0.0);
+  o.uR = wetR ? mR * hLs * ihh : real(0.0);
   waveL = dabs(o.uL) + rsqrt_(P.g * dmax(hL, 0.0));
   waveR = dabs(o.uR) + rsqrt_(P.g * dmax(hR, 0.0));
   // NaN propagates into the comparisons as false: catch it explicitly.
@@ -247,10 +222,11 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real J[5], const real E[5],
   if (!(chk == chk) || dabs(chk) > 1.0e300) st |= ST_NONFINITE;
 }
 
-// Interface fluxes of the hydrostatic-reconstruction ALE-LF scheme (Eq. hydro2D-HH2D and
-// the bottom flux of Eq. bottomrk): FE (eta), FMm (momentum seen by the left cell),
-// FMp (seen by the right cell), FB (bottom). L is the right edge of the left cell, R the
-// left edge of the right cell; w is the node velocity, alpha the global viscosity.
+// ------------------------------------------------------------------------------------
+// Interface flux (Eq. hydro2D-HH2D and the bottom flux of Eq. bottomrk): FE (eta), FMm
+// (momentum seen by the left cell), FMp (seen by the right cell), FB (bottom). L is the right
+// edge of the left cell, R the left edge of the right cell; w the node velocity.
+// ------------------------------------------------------------------------------------
 struct Flux {
   real FE, FMm, FMp, FB;
 };
@@ -264,7 +240,7 @@ SWALE_HD Flux interface_flux(real g, real alpha, real w, real EL, real ER, real 
   f.FE = 0.5 * (mL + mR) - 0.5 * w * (EL + ER) - 0.5 * alpha * (ER - EL);
   const real hg = 0.5 * g;
   const real H2 = 0.5 * ((mL * uL + hg * sL * sL - w * mL) + (mR * uR + hg * sR * sR - w * mR)) -
-                    0.5 * alpha * (mR - mL);
+                  0.5 * alpha * (mR - mL);
   f.FMm = H2 + hg * (hL * hL - sL * sL);
   f.FMp = H2 + hg * (hR * hR - sR * sR);
   f.FB = 0.5 * w * (BL + BR) + 0.5 * alpha * (BR - BL);
@@ -279,13 +255,27 @@ SWALE_HD Flux interface_flux(real g, real alpha, real w, real EL, real ER, real 
 #define SWALE_GL4_W0 0.173927422568726929
 #define SWALE_GL4_W1 0.326072577431273071
 
-// Source term int_cell -g (eta_h - b_h) b_h' dx of Sec. 4.1, with eta_h - b_h interpolating
-// the depth data (averages h_{j-1}, h_j, h_{j+1}, limited edge depths h^L, h^R) and b_h the
-// bottom data (averages and limited edge bottoms). In the unit coordinate t of the cell,
-// rm = J_{j-1}/J_j and rp = J_{j+1}/J_j; irm = 1/rm, irp = 1/rp, i1m = 1/(1+rm),
-// i1p = 1/(1+rp), i1mp = 1/(1+rm+rp).
-SWALE_HD real source_cell(real g, const real hd[5], const real bd[5], real rm, real irm, real irp,
-                            real i1m, real i1p, real i1mp) {
+// Width ratios of the source interpolant of cell j in its unit coordinate, from the shared
+// reciprocals: rm = J_{j-1}/J_j, irm = J_j/J_{j-1}, irp = J_j/J_{j+1}, i1m = J_j/(J_{j-1}+J_j),
+// i1p = J_j/(J_j+J_{j+1}), i1mp = J_j/(J_{j-1}+J_j+J_{j+1}).
+struct SourceGeom {
+  real rm, irm, irp, i1m, i1p, i1mp;
+};
+SWALE_HD SourceGeom source_geom(real Jm, real Jc, real iJm, real iJc, real iJp, real ipl, real ipr, real itc) {
+  SourceGeom s;
+  s.rm = Jm * iJc;
+  s.irm = Jc * iJm;
+  s.irp = Jc * iJp;
+  s.i1m = Jc * ipl;
+  s.i1p = Jc * ipr;
+  s.i1mp = Jc * itc;
+  return s;
+}
+
+// Source term int_cell -g (eta_h - b_h) b_h' dx of Sec. 4.1, with eta_h - b_h interpolating the
+// depth data (averages h_{j-1}, h_j, h_{j+1}, limited edge depths h^L, h^R) and b_h the bottom
+// data (averages and limited edge bottoms), in the unit coordinate t of the cell.
+SWALE_HD real source_cell(real g, const real hd[5], const real bd[5], const SourceGeom& sg) {
   // Confluent divided differences of the primitive on nodes (-rm, 0, 0, 1, 1, 1+rp):
   // data order (avg_{j-1}, avg_j, avg_{j+1}, v_L, v_R).
   real ch[6], cb[6];
@@ -293,16 +283,16 @@ SWALE_HD real source_cell(real g, const real hd[5], const real bd[5], real rm, r
   real* cf[2] = {ch, cb};
   for (int v = 0; v < 2; ++v) {
     const real* u = dat[v];
-    const real o2a = (u[3] - u[0]) * irm;  // [z1, z2, z2]
-    const real o2b = u[1] - u[3];          // [z2, z2, z3]
-    const real o2c = u[4] - u[1];          // [z2, z3, z3]
-    const real o2d = (u[2] - u[4]) * irp;  // [z3, z3, z4]
-    const real o3a = (o2b - o2a) * i1m;    // [z1, z2, z2, z3]
-    const real o3b = o2c - o2b;            // [z2, z2, z3, z3]
-    const real o3c = (o2d - o2c) * i1p;    // [z2, z3, z3, z4]
-    const real o4a = (o3b - o3a) * i1m;    // [z1, z2, z2, z3, z3]
-    const real o4b = (o3c - o3b) * i1p;    // [z2, z2, z3, z3, z4]
-    const real o5 = (o4b - o4a) * i1mp;    // [z1 .. z4]
+    const real o2a = (u[3] - u[0]) * sg.irm;  // [z1, z2, z2]
+    const real o2b = u[1] - u[3];             // [z2, z2, z3]
+    const real o2c = u[4] - u[1];             // [z2, z3, z3]
+    const real o2d = (u[2] - u[4]) * sg.irp;  // [z3, z3, z4]
+    const real o3a = (o2b - o2a) * sg.i1m;    // [z1, z2, z2, z3]
+    const real o3b = o2c - o2b;               // [z2, z2, z3, z3]
+    const real o3c = (o2d - o2c) * sg.i1p;    // [z2, z3, z3, z4]
+    const real o4a = (o3b - o3a) * sg.i1m;    // [z1, z2, z2, z3, z3]
+    const real o4b = (o3c - o3b) * sg.i1p;    // [z2, z2, z3, z3, z4]
+    const real o5 = (o4b - o4a) * sg.i1mp;    // [z1 .. z4]
     real* c = cf[v];
     c[1] = u[0];
     c[2] = o2a;
@@ -310,20 +300,20 @@ SWALE_HD real source_cell(real g, const real hd[5], const real bd[5], real rm, r
     c[4] = o4a;
     c[5] = o5;
   }
-  // Basis n_k = (t + rm) m_k(t), m_2 = t, m_3 = t^2, m_4 = t^3 - t^2, m_5 = t^4 - 2 t^3 + t^2.
+  // Basis n_k = (t + rm) m_k(t), m_2 = t, m_3 = t^2, m_4 = t^3 - t^2, m_5 = t^4 - 2 t^3 + t^2:
   // n_k' = (m_k + t m_k') + rm m_k', n_k'' = (2 m_k' + t m_k'') + rm m_k''.
-  const real tq[4] = {SWALE_GL4_T0, SWALE_GL4_T1, SWALE_GL4_T2, SWALE_GL4_T3};
-  const real wq[4] = {SWALE_GL4_W0, SWALE_GL4_W1, SWALE_GL4_W1, SWALE_GL4_W0};
+  const double tq[4] = {SWALE_GL4_T0, SWALE_GL4_T1, SWALE_GL4_T2, SWALE_GL4_T3};
+  const double wq[4] = {SWALE_GL4_W0, SWALE_GL4_W1, SWALE_GL4_W1, SWALE_GL4_W0};
   real S = 0.0;
   for (int q = 0; q < 4; ++q) {
-    const real t = tq[q], t2 = t * t, t3 = t2 * t, t4 = t3 * t;
-    const real m[6] = {0, 0, t, t2, t3 - t2, t4 - 2.0 * t3 + t2};
-    const real md[6] = {0, 0, 1.0, 2.0 * t, 3.0 * t2 - 2.0 * t, 4.0 * t3 - 6.0 * t2 + 2.0 * t};
-    const real mdd[6] = {0, 0, 0.0, 2.0, 6.0 * t - 2.0, 12.0 * t2 - 12.0 * t + 2.0};
+    const double t = tq[q], t2 = t * t, t3 = t2 * t, t4 = t3 * t;
+    const double m[6] = {0, 0, t, t2, t3 - t2, t4 - 2.0 * t3 + t2};
+    const double md[6] = {0, 0, 1.0, 2.0 * t, 3.0 * t2 - 2.0 * t, 4.0 * t3 - 6.0 * t2 + 2.0 * t};
+    const double mdd[6] = {0, 0, 0.0, 2.0, 6.0 * t - 2.0, 12.0 * t2 - 12.0 * t + 2.0};
     real hv = ch[1], bdv = 0.0;
     for (int k = 2; k <= 5; ++k) {
-      const real n1 = (m[k] + t * md[k]) + rm * md[k];
-      const real n2 = (2.0 * md[k] + t * mdd[k]) + rm * mdd[k];
+      const real n1 = (m[k] + t * md[k]) + sg.rm * md[k];
+      const real n2 = (2.0 * md[k] + t * mdd[k]) + sg.rm * mdd[k];
       hv += ch[k] * n1;
       bdv += cb[k] * n2;
     }
@@ -332,30 +322,14 @@ SWALE_HD real source_cell(real g, const real hd[5], const real bd[5], real rm, r
   return -g * S;
 }
 
-// Right-hand side of cell j for one stage (Eq. hydro2D with Eq. bottomrk in 1D): fluxes at
-// its two interfaces, the source term on its stage width, and the flux differences.
-// Edge inputs: the right edge of cell j-1 (l*), both edges of cell j (c*), the left edge of
-// cell j+1 (r*). Averages and widths of cells j-1, j, j+1: (Em, Ec, Ep), (Bm, Bc, Bp),
-// (Jm, Jc, Jp). wl, wr: velocities of nodes j-1/2 and j+1/2.
+// Flux differences and source of cell j: R = (R_E, R_M, R_B) of Eq. hydro2D / bottomrk.
 struct CellRhs {
   real RE, RM, RB;
 };
-SWALE_HD CellRhs rhs_cell(real g, real alpha, real wl, real wr, real lE, real lB, real lh, real lu, real cEL,
-                          real cER, real cBL, real cBR, real chL, real chR, real cuL, real cuR, real rE, real rB,
-                          real rh, real ru, real Em, real Ec, real Ep, real Bm, real Bc, real Bp, real Jm,
-                          real Jc, real Jp) {
-  const Flux Fl = interface_flux(g, alpha, wl, lE, cEL, lB, cBL, lh, chL, lu, cuL);
-  const Flux Fr = interface_flux(g, alpha, wr, cER, rE, cBR, rB, chR, rh, cuR, ru);
-  const real ic0 = 1.0 / Jc;
-  const real rm = Jm * ic0;
-  const real irm = Jc / Jm, irp = Jc / Jp;
-  const real i1m = Jc / (Jm + Jc), i1p = Jc / (Jc + Jp), i1mp = Jc / (Jm + Jc + Jp);
-  const real hd[5] = {Em - Bm, Ec - Bc, Ep - Bp, chL, chR};
-  const real bd[5] = {Bm, Bc, Bp, cBL, cBR};
-  const real Sj = source_cell(g, hd, bd, rm, irm, irp, i1m, i1p, i1mp);
+SWALE_HD CellRhs cell_rhs(const Flux& Fl, const Flux& Fr, real S) {
   CellRhs o;
   o.RE = -(Fr.FE - Fl.FE);
-  o.RM = -(Fr.FMm - Fl.FMp) + Sj;
+  o.RM = -(Fr.FMm - Fl.FMp) + S;
   o.RB = Fr.FB - Fl.FB;
   return o;
 }

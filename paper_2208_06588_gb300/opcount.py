@@ -52,11 +52,12 @@ def count_stage(E, M, B, J, bc="transmissive", g=9.812, eps_weno=1e-6, eps_pp=1e
                           vp(J.ctypes.data), ctypes.c_int32(BC[bc]), ctypes.c_double(g), ctypes.c_double(eps_weno),
                           ctypes.c_double(eps_pp), ctypes.c_double(h_dry), ctypes.c_double(alpha),
                           ctypes.c_int64(c0), ctypes.c_int64(c0 + n), vp(out.ctypes.data))
-    rec, rhs, flux = out[0:5] / n, out[5:10] / n, out[10:15] / n
+    rec, upd, flux = out[0:5] / n, out[5:10] / n, out[10:15] / n
     rf = float(rec[:4].sum())
-    uf = float(rhs[:4].sum() - flux[:4].sum() + RK_OPS)
-    return {"recon": dict(zip(("add", "mul", "div", "sqrt", "cmp"), map(float, rec))),
-            "rhs_two_fluxes": dict(zip(("add", "mul", "div", "sqrt", "cmp"), map(float, rhs))),
-            "one_flux": dict(zip(("add", "mul", "div", "sqrt", "cmp"), map(float, flux))),
+    uf = float(upd[:4].sum() + RK_OPS)
+    keys = ("add", "mul", "div", "sqrt", "cmp")
+    return {"recon": dict(zip(keys, map(float, rec))),
+            "update_without_rk": dict(zip(keys, map(float, upd))),
+            "one_flux": dict(zip(keys, map(float, flux))),
             "recon_flops": rf, "update_flops": uf, "stage_flops": rf + uf, "cells_counted": n,
             "classes": [int(v) for v in out[15:18]]}
