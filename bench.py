@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -131,6 +133,78 @@ def cpu_oracle_rate(n_cells, steps):
     r = oracle.run(P, st, pr.profile, nsteps=steps)
     dt = time.perf_counter() - t0
     return n_cells * r["steps"] / dt, dt
+
+
+def bench_batched(args, stream, dev):
+    """Batched forward: 4096 instances, 256..16384 cells each, one launch per kernel per stage for
+    all instances (autotuned tile sizes), against the plain per-instance launch loop on the same
+    512-instance subset."""
+    import torch
+    from paper_2208_06588_gb300 import binding as B
+    from paper_2208_06588_gb300 import workloads as W
+    bt = W.many_basins(B=4096)
+    cfg = B.make_config(g=bt.g, eps_weno=bt.eps_weno, mesh_T=bt.mesh_T, bc=bt.bc, mesh=bt.mesh, cfl=0.6)
+    s = B.Solver(cfg, stream.cuda_stream)
+    s.set_batch(bt)
+    cache = os.path.join(os.path.expanduser("~"), ".cache", "swale_autotune.jsonl")
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    tiles = B.swale_autotune(s.ctx, 3, cache)
+    B.swale_enqueue(s.ctx, 3)
+    stream.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    B.swale_enqueue(s.ctx, args.batched_steps)
+    ev1.record(stream)
+    stream.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    bits = s.status()[0]
+    s.close()
+    ntot = int(bt.off[-1])
+    out = {"workload": "many_basins: 4096 instances, N_i ~ U{256..16384} (sum %d cells), reflective, sine mesh "
+                       "motion A ~ U[0,0.05], CFL 0.6 / 0.08 (dry)" % ntot,
+           "value": ntot * args.batched_steps / (ms * 1e-3), "unit": UNIT, "steps": args.batched_steps,
+           "ms_per_step": ms / args.batched_steps, "tiles": list(tiles), "status_bits": bits}
+    # Same work, batched vs one context per instance (launches per instance and step).
+    sub = 512
+    sb = W.Batch(name="subset", off=bt.off[:sub + 1].copy(), x=bt.x[:int(bt.off[sub]) + sub],
+                 h=bt.h[:int(bt.off[sub])], hu=bt.hu[:int(bt.off[sub])], b=bt.b[:int(bt.off[sub])],
+                 E=bt.E[:int(bt.off[sub])], profile=bt.profile[:int(bt.off[sub]) + sub], cfl=bt.cfl[:sub])
+    nsub = int(sb.off[-1])
+    ksub = 5
+    s = B.Solver(cfg, stream.cuda_stream)
+    s.set_batch(sb)
+    B.swale_set_tiles(s.ctx, *tiles)
+    B.swale_enqueue(s.ctx, 2)
+    stream.synchronize()
+    ev0.record(stream)
+    B.swale_enqueue(s.ctx, ksub)
+    ev1.record(stream)
+    stream.synchronize()
+    ms_b = ev0.elapsed_time(ev1)
+    s.close()
+    solvers = []
+    for i in range(sub):
+        pr = sb.instance(i)
+        c = B.make_config(g=pr.g, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, bc=pr.bc, mesh=pr.mesh, cfl=pr.cfl)
+        si = B.Solver(c, stream.cuda_stream)
+        si.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+        B.swale_enqueue(si.ctx, 2)
+        solvers.append(si)
+    stream.synchronize()
+    ev0.record(stream)
+    for _ in range(ksub):
+        for si in solvers:
+            B.swale_step(si.ctx)
+    ev1.record(stream)
+    stream.synchronize()
+    ms_l = ev0.elapsed_time(ev1)
+    for si in solvers:
+        si.close()
+    out["vs_per_instance_loop"] = {"instances": sub, "cells": nsub, "steps": ksub,
+                                   "batched": nsub * ksub / (ms_b * 1e-3),
+                                   "per_instance_loop": nsub * ksub / (ms_l * 1e-3),
+                                   "speedup": ms_l / ms_b}
+    return out
 
 
 def run_reference(args):
@@ -266,13 +340,17 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"3 SSP-RK3 steps of the full 2^20-cell workload ({secs:.1f} s, one thread)"}
 
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(args, stream, dev)
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "cells": N, "parallelism": f"replicas x{ws}" if ws > 1 else "single",
                       "l2": "working set ~230 MB per stage > 126 MB L2 (no flush needed)"},
            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
-           "status_bits": bits, "steps_done_device": steps_done, "last_dt": last_dt,
+           "status_bits": bits, "steps_done_device": steps_done, "last_dt": last_dt, "batched": batched,
            "fp64_ops_per_cell_stage": oc}
     print(json.dumps(out), flush=True)
     if ws > 1:

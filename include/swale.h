@@ -97,6 +97,17 @@ swale_status swale_create(swale_ctx** out, const swale_config* cfg, void* cuda_s
 swale_status swale_set_problem(swale_ctx* ctx, int64_t N, const double* x_nodes, const double* q0,
                                const double* hu, const double* b, const double* profile, int32_t q0_is_eta);
 
+/* Sets a batch of B independent instances (offsets[B+1] cells, offsets[0] = 0, each instance
+ * N_i = offsets[i+1] - offsets[i] >= 5 cells, total < 2^31). Arrays are concatenated over the
+ * instances: cells of instance i at [offsets[i], offsets[i+1]), its N_i + 1 nodes (and profile
+ * values) at [offsets[i] + i, offsets[i+1] + i + 1). cfl: B per-instance CFL numbers (NULL: the
+ * configuration's). Every instance advances with its own dt (its own alpha, Eq. alpha2D) in the
+ * same launches; the configuration (g, eps, boundary condition, mesh kind, T) is shared.
+ * Errors as swale_set_problem. */
+swale_status swale_batch_set_problem(swale_ctx* ctx, int64_t B, const int64_t* offsets, const double* x_nodes,
+                                     const double* q0, const double* hu, const double* b, const double* profile,
+                                     const double* cfl, int32_t q0_is_eta);
+
 /* One SSP-RK3 step (three fused reconstruction + update stage pairs). If dt_out is not NULL
  * the call synchronises the stream and returns the step's dt. A step at t >= t_end (t_end > 0)
  * does nothing. Errors: SWALE_EINVAL (no problem set), SWALE_ECUDA. */
@@ -120,17 +131,39 @@ swale_status swale_enqueue(swale_ctx* ctx, int64_t nsteps);
 swale_status swale_set_timing(swale_ctx* ctx, int32_t enable);
 swale_status swale_get_timing(swale_ctx* ctx, double* ms, int64_t* launches);
 
-/* Copies the current state out. Any pointer may be NULL. h, hu, b, eta: N values; x_nodes:
- * N+1 values; t: one value (host or device). Synchronises the stream. */
+/* Copies the current state of a single instance out (a batch: swale_batch_get_state). Any
+ * pointer may be NULL. h, hu, b, eta: N values; x_nodes: N+1 values; t: one value (host or
+ * device). Synchronises the stream. */
 swale_status swale_get_state(swale_ctx* ctx, double* h, double* hu, double* b, double* eta, double* x_nodes,
                              double* t);
 
+/* State of a batch in the concatenated layout of swale_batch_set_problem; t and dt: B values
+ * (the time and the last step of each instance). Any pointer may be NULL. Synchronises. */
+swale_status swale_batch_get_state(swale_ctx* ctx, double* hu, double* b, double* eta, double* x_nodes, double* t,
+                                   double* dt);
+
+/* Launch shape: the tile (cells per block: 64, 128 or 256) of the reconstruction and update
+ * kernels and their grid (0 = one block per tile; G > 0 = a persistent grid of G blocks
+ * walking the (instance, tile) work list). tiles[4] = {recon_tile, update_tile, recon_grid,
+ * update_grid}. Results do not depend on the launch shape (bitwise). */
+swale_status swale_set_tiles(swale_ctx* ctx, int32_t recon_tile, int32_t update_tile, int32_t recon_grid,
+                             int32_t update_grid);
+swale_status swale_get_tiles(swale_ctx* ctx, int32_t* tiles);
+
+/* Autotuner: times `steps` steps (after one untimed step) for each tile size pair in
+ * {64, 128, 256}^2, each with one block per tile and with a persistent grid, from a snapshot of
+ * the current state that is restored afterwards, and keeps the fastest. With a cache_path, a
+ * matching entry (key: SM count, B, log2 of the total cells, mesh kind) is used without timing,
+ * and a new result is appended as one JSON object per line. tiles_out[4] (may be NULL) receives
+ * the chosen shape. Allocates a temporary snapshot (5 doubles per cell). */
+swale_status swale_autotune(swale_ctx* ctx, int32_t steps, const char* cache_path, int32_t* tiles_out);
+
 /* Detector classes (0 smooth, 1 transition, 2 non-smooth; Step 2 of Sec. 2.2) of the first
- * stage of the last step, N bytes. Synchronises. */
+ * stage of the last step, N bytes (a batch: all instances' cells in order). Synchronises. */
 swale_status swale_get_flags(swale_ctx* ctx, uint8_t* flags);
 
-/* Accumulated device status word (SWALE_BIT_*), the step count and the last dt.
- * Any pointer may be NULL; host pointers. Synchronises. */
+/* Accumulated device status word (SWALE_BIT_*; OR over the instances of a batch), the step
+ * count and the last dt (of instance 0). Any pointer may be NULL; host pointers. Synchronises. */
 swale_status swale_get_status(swale_ctx* ctx, uint32_t* status_bits, int64_t* steps, double* last_dt);
 
 /* One evaluation of the semi-discrete right-hand side (Eq. hydro2D with Eq. bottomrk) for

@@ -64,12 +64,18 @@ def lib():
         L.swale_get_status.argtypes = [vp, P(ctypes.c_uint32), P(i64), P(d)]
         L.swale_rhs.argtypes = [vp, i64, vp, vp, vp, vp, vp, d, vp, vp, vp, P(d), vp, P(ctypes.c_uint32)]
         L.swale_enqueue.argtypes = [vp, i64]
+        L.swale_batch_set_problem.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, i32]
+        L.swale_batch_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.swale_set_tiles.argtypes = [vp, i32, i32, i32, i32]
+        L.swale_get_tiles.argtypes = [vp, vp]
+        L.swale_autotune.argtypes = [vp, i32, ctypes.c_char_p, vp]
         L.swale_rhs_noalloc.argtypes = [P(SwaleConfig), vp, i64, vp, vp, vp, vp, vp, d, vp, vp, vp, P(d), vp]
         L.swale_set_timing.argtypes = [vp, i32]
         L.swale_get_timing.argtypes = [vp, vp, vp]
         for name in ("swale_create", "swale_set_problem", "swale_step", "swale_advance", "swale_get_state",
                      "swale_get_flags", "swale_get_status", "swale_rhs", "swale_enqueue", "swale_set_timing",
-                     "swale_get_timing", "swale_rhs_noalloc"):
+                     "swale_get_timing", "swale_rhs_noalloc", "swale_batch_set_problem", "swale_batch_get_state",
+                     "swale_set_tiles", "swale_get_tiles", "swale_autotune"):
             getattr(L, name).restype = ctypes.c_int
         L.swale_last_error.argtypes = [vp]
         L.swale_last_error.restype = ctypes.c_char_p
@@ -118,6 +124,32 @@ def swale_advance(ctx, max_steps):
     done = ctypes.c_int64(0)
     _check(ctx, lib().swale_advance(ctx, int(max_steps), ctypes.byref(done)))
     return done.value
+
+
+def swale_batch_set_problem(ctx, B, offsets, x_nodes, q0, hu, b, profile=None, cfl=None, q0_is_eta=0):
+    _check(ctx, lib().swale_batch_set_problem(ctx, int(B), ptr(offsets), ptr(x_nodes), ptr(q0), ptr(hu), ptr(b),
+                                              ptr(profile), ptr(cfl), int(q0_is_eta)))
+
+
+def swale_batch_get_state(ctx, hu=None, b=None, eta=None, x_nodes=None, t=None, dt=None):
+    _check(ctx, lib().swale_batch_get_state(ctx, ptr(hu), ptr(b), ptr(eta), ptr(x_nodes), ptr(t), ptr(dt)))
+
+
+def swale_set_tiles(ctx, recon_tile=128, update_tile=128, recon_grid=0, update_grid=0):
+    _check(ctx, lib().swale_set_tiles(ctx, int(recon_tile), int(update_tile), int(recon_grid), int(update_grid)))
+
+
+def swale_get_tiles(ctx):
+    t = np.zeros(4, dtype=np.int32)
+    _check(ctx, lib().swale_get_tiles(ctx, t.ctypes.data))
+    return tuple(int(v) for v in t)
+
+
+def swale_autotune(ctx, steps=3, cache_path=None):
+    t = np.zeros(4, dtype=np.int32)
+    cp = cache_path.encode() if cache_path else None
+    _check(ctx, lib().swale_autotune(ctx, int(steps), cp, t.ctypes.data))
+    return tuple(int(v) for v in t)
 
 
 def swale_enqueue(ctx, nsteps):
@@ -217,6 +249,21 @@ class Solver:
 
     def status(self):
         return swale_get_status(self.ctx)
+
+    def set_batch(self, batch, q0_is_eta=True):
+        """A workloads.Batch (concatenated instances)."""
+        self.N = int(batch.off[-1])
+        self.B = batch.B
+        arr = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        swale_batch_set_problem(self.ctx, batch.B, np.ascontiguousarray(batch.off, dtype=np.int64), arr(batch.x),
+                                arr(batch.E if q0_is_eta else batch.h), arr(batch.hu), arr(batch.b),
+                                arr(batch.profile), arr(batch.cfl), 1 if q0_is_eta else 0)
+
+    def batch_state(self):
+        N, B = self.N, self.B
+        hu, b, eta, x, t, dt = (np.zeros(N), np.zeros(N), np.zeros(N), np.zeros(N + B), np.zeros(B), np.zeros(B))
+        swale_batch_get_state(self.ctx, hu, b, eta, x, t, dt)
+        return {"hu": hu, "b": b, "eta": eta, "x": x, "t": t, "dt": dt}
 
     def close(self):
         if self.ctx:

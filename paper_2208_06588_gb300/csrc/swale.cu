@@ -1,525 +1,36 @@
-// GB300 (sm_103a) FP64 kernels and C ABI of the well-balanced ALE-WENO hybrid scheme
-// (Zhang, Xia & Xu, arXiv 2208.06588). One SSP-RK3 step (Eq. RK32D) is a short, fixed
-// sequence of launches on the context's stream:
-//   prologue (1 thread)        reset the per-step device scalars
-//   [mesh_gauss]               fluid-driven node velocities (SWALE_MESH_FLUID_GAUSS)
-//   recon<1>, update<1>        stage 1 on the mesh at t_n
-//   recon<2>, update<2>        stage 2 on the mesh at t_{n+1}
-//   recon<3>, update<3>        stage 3 on the mesh at t_{n+1/2}
-// The reconstruction kernel also reduces the global wave speed of Eq. alpha2D (warp shuffle,
-// shared memory, one atomicMax per block on the order-preserving bit pattern of a
-// non-negative double); in stage 1 the last block to finish computes dt on the device, so
-// dt, alpha and t never visit the host and a step can be replayed as a CUDA graph.
+// Host side and C ABI (include/swale.h) of the GB300 (sm_103a) FP64 solver for the
+// well-balanced ALE-WENO hybrid scheme (Zhang, Xia & Xu, arXiv 2208.06588). The kernels are in
+// swale_kernels.cuh, the per-cell arithmetic in swale_cell.cuh.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
 #include "../../include/swale.h"
-#include "swale_cell.cuh"
+#include "swale_kernels.cuh"
 
-using swale::EdgeState;
-using swale::SchemeConst;
+using namespace swale_dev;
 
-namespace {
-
-constexpr int kReconThreads = 128;
-constexpr int kUpdateThreads = 128;
-constexpr int kMaxGaussHalf = 64;
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-
-__constant__ double c_gauss_w[2 * kMaxGaussHalf + 1];
-
-// Per-context device scalars. Maxima of non-negative doubles are kept as their bit
-// patterns (unsigned order equals numeric order for non-negative IEEE doubles).
-struct DevScalars {
-  double t, dt, sdiff, Wbar, alpha1;
-  unsigned long long A[3];     // max edge wave speed per stage
-  unsigned long long Jmax[3];  // max width of the stage meshes J^n, J^(1), J^(2)
-  unsigned long long Jmin0;    // min J^n
-  unsigned long long JmaxN, JminN;   // of J^{n+1}, accumulated by stage 3
-  unsigned long long Wabs, dWabs;    // fluid-driven motion: max |w|, max |w_{j+1} - w_j|
-  long long steps;
-  unsigned int status;
-  unsigned int counter;
-  int done;
-  int clipped;
-};
-
-struct StepConst {
-  SchemeConst sc;
-  double cfl, t_end, dt_fixed, mesh_T, Wbar_profile;
-  double gauss_wsum;  // sum of the full Gaussian window, summed from -H to H
-  int64_t N;
-  int32_t bc, mesh;
-  int32_t gauss_half;
-};
-
-// Device state of one instance. Edge arrays hold cells -1..N at index c + 1.
-struct DevState {
-  double *E0, *M0, *B0;        // q^n (updated in place by stage 3)
-  double *Ea, *Ma, *Ba;        // q^(1)
-  double *Eb, *Mb, *Bb;        // q^(2)
-  double *YE, *YM, *YB;        // running RK combination J q
-  double *J0, *J1, *J2;        // J^n, J^(1), J^(2)
-  double *x, *w, *P;           // nodes, node velocities, motion profile (N+1)
-  double *eEL, *eER, *eBL, *eBR, *ehL, *ehR, *euL, *euR;
-  double *ipair, *itri;        // N+2: 1/(J_c + J_{c+1}) and 1/(J_{c-1} + J_c + J_{c+1}) of the stage mesh
-  uint8_t* flags;              // N+2, stage-1 classes
-  DevScalars* S;
-};
-
-__device__ __forceinline__ int64_t ghost(int64_t i, int64_t N, int bc) {
-  if (bc == SWALE_BC_PERIODIC) {
-    i %= N;
-    return i < 0 ? i + N : i;
-  }
-  if (i < 0) return -1 - i;
-  if (i >= N) return 2 * N - 1 - i;
-  return i;
-}
-
-__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
-__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
-
-// Block-wide max of a non-negative double, one atomicMax per block.
-__device__ __forceinline__ void block_max_to(unsigned long long* dst, double v) {
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    v = lane < nw ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) atomicMax(dst, dbits(v));
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ void block_min_to(unsigned long long* dst, double v) {
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    v = lane < nw ? red[lane] : INFINITY;
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) atomicMin(dst, dbits(v));
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ void block_or_status(unsigned int* dst, uint32_t st) {
-  st = __reduce_or_sync(0xffffffffu, st);
-  if ((threadIdx.x & 31) == 0 && st) atomicOr(dst, st);
-}
-
-// ------------------------------------------------------------------------------------
-// Per-step prologue: stage maxima reset, J^{n+1} statistics become those of J^n.
-// ------------------------------------------------------------------------------------
-__global__ void k_prologue(StepConst K, DevScalars* S) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (K.t_end > 0.0 && S->t >= K.t_end) {
-    S->done = 1;
-    return;
-  }
-  S->done = 0;
-  S->clipped = 0;
-  S->Jmax[0] = S->JmaxN;
-  S->Jmin0 = S->JminN;
-  S->JmaxN = 0ull;
-  S->JminN = 0x7ff0000000000000ull;  // +inf
-  S->A[0] = S->A[1] = S->A[2] = 0ull;
-  S->Jmax[1] = S->Jmax[2] = 0ull;
-  S->Wabs = S->dWabs = 0ull;
-  S->counter = 0u;
-  if (K.mesh != SWALE_MESH_FLUID_GAUSS) S->Wbar = K.Wbar_profile;
-}
-
-// ------------------------------------------------------------------------------------
-// Fluid-driven node velocity: raw_k = (u_{k-1} + u_k)/2 for k = 1..N-1 (u = hu/h, dry -> 0),
-// truncated renormalised Gaussian filter, w_0 = w_N = 0. One thread per node; the block stages
-// the cell velocities, the raw node velocities and its filtered nodes in shared memory.
-// ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_mesh_gauss(StepConst K, DevState D) {
-  extern __shared__ double sh[];
-  DevScalars* S = D.S;
-  if (S->done) return;
-  const int64_t N = K.N;
-  const int H = K.gauss_half, T = blockDim.x, tid = threadIdx.x;
-  const int64_t k0 = (int64_t)blockIdx.x * T;  // first node of the tile
-  const int nu = T + 2 * H + 2, nr = T + 2 * H + 1;
-  double* su = sh;         // cell velocities, cells [k0 - H - 1, k0 + T + H]
-  double* sraw = sh + nu;  // raw node velocities, nodes [k0 - H, k0 + T + H]
-  double* sw = sraw + nr;  // filtered velocities, nodes [k0, k0 + T]
-  for (int i = tid; i < nu; i += T) {
-    const int64_t c = k0 - H - 1 + i;
-    double u = 0.0;
-    if (c >= 0 && c < N) {
-      const double h = D.E0[c] - D.B0[c];
-      u = h > K.sc.h_dry ? D.M0[c] / h : 0.0;
-    }
-    su[i] = u;
-  }
-  __syncthreads();
-  for (int i = tid; i < nr; i += T) {
-    const int64_t k = k0 - H + i;
-    sraw[i] = (k >= 1 && k <= N - 1) ? 0.5 * (su[i] + su[i + 1]) : 0.0;
-  }
-  __syncthreads();
-  for (int i = tid; i <= T; i += T) {
-    const int64_t k = k0 + i;
-    double v = 0.0;
-    if (k >= 1 && k <= N - 1) {
-      double acc = 0.0;
-      if (k - H >= 1 && k + H <= N - 1) {
-        for (int m = -H; m <= H; ++m) acc += c_gauss_w[m + H] * sraw[i + m + H];
-        v = acc / K.gauss_wsum;
-      } else {
-        double wsum = 0.0;
-        for (int m = -H; m <= H; ++m) {
-          const int64_t q = k + m;
-          if (q < 1 || q > N - 1) continue;
-          acc += c_gauss_w[m + H] * sraw[i + m + H];
-          wsum += c_gauss_w[m + H];
-        }
-        v = acc / wsum;
-      }
-    }
-    sw[i] = v;
-  }
-  __syncthreads();
-  const int64_t k = k0 + tid;
-  double wa = 0.0, dwa = 0.0;
-  if (k <= N) {
-    D.w[k] = sw[tid];
-    wa = fabs(sw[tid]);
-    if (k < N) dwa = fabs(sw[tid + 1] - sw[tid]);
-  }
-  block_max_to(&S->Wabs, wa);
-  block_max_to(&S->dWabs, dwa);
-}
-
-// ------------------------------------------------------------------------------------
-// Reconstruction + limiter of cells -1..N for stage STAGE, wave-speed reduction; in stage 1
-// the last block computes dt (and the secant factor of the prescribed motion).
-// A block owns kReconThreads consecutive cells: it stages their 5-cell stencils (tile plus a
-// 2-cell halo each side) in shared memory, computes each pair's and each triple's reciprocal
-// width and divided differences once, then reconstructs one cell per thread. It also stores
-// the pair / triple reciprocals for the update kernel of the same stage.
-// ------------------------------------------------------------------------------------
-template <int STAGE>
-__global__ void __launch_bounds__(kReconThreads) k_recon(StepConst K, DevState D, const double* __restrict__ E,
-                                                         const double* __restrict__ M, const double* __restrict__ B,
-                                                         const double* __restrict__ J) {
-  constexpr int T = kReconThreads;
-  __shared__ double sJ[T + 4], sV[3][T + 4];  // cells c0-2 .. c0+T+1
-  __shared__ double sIP[T + 3], sD2[3][T + 3];  // pairs starting at those cells
-  __shared__ double sIT[T + 2], sD3[3][T + 2];  // triples centred at cells c0-1 .. c0+T
-  DevScalars* S = D.S;
-  if (S->done) return;
-  const int64_t N = K.N;
-  const int tid = threadIdx.x;
-  const int64_t c0 = (int64_t)blockIdx.x * T - 1;  // first cell of the tile (cells -1..N)
-  const bool refl = (K.bc == SWALE_BC_REFLECTIVE);
-  for (int i = tid; i < T + 4; i += T) {
-    const int64_t c = c0 - 2 + i;
-    double jv = 1.0, ev = 0.0, mv = 0.0, bv = 0.0;  // filler beyond the last ghost cell
-    if (c >= -3 && c <= N + 2) {
-      const int64_t s = ghost(c, N, K.bc);
-      jv = J[s];
-      ev = E[s];
-      bv = B[s];
-      mv = M[s];
-      if (refl && (c < 0 || c >= N)) mv = -mv;
-    }
-    sJ[i] = jv;
-    sV[0][i] = ev;
-    sV[1][i] = mv;
-    sV[2][i] = bv;
-  }
-  __syncthreads();
-  for (int i = tid; i < T + 3; i += T) {
-    const double ip = swale::pair_recip(sJ[i], sJ[i + 1]);
-    sIP[i] = ip;
-#pragma unroll
-    for (int v = 0; v < 3; ++v) sD2[v][i] = swale::pair_dd(sV[v][i], sV[v][i + 1], ip);
-  }
-  __syncthreads();
-  for (int i = tid; i < T + 2; i += T) {
-    const double it = swale::triple_recip(sJ[i], sJ[i + 1], sJ[i + 2]);
-    sIT[i] = it;
-#pragma unroll
-    for (int v = 0; v < 3; ++v) sD3[v][i] = swale::triple_dd(sD2[v][i], sD2[v][i + 1], it);
-  }
-  __syncthreads();
-  const int64_t c = c0 + tid;
-  double wave = 0.0;
-  uint32_t st = 0;
-  if (c <= N) {
-    double h[5], v0[3][3];
-    swale::StencilDD DD;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) h[k] = sJ[tid + k];
-#pragma unroll
-    for (int v = 0; v < 3; ++v) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) v0[v][a] = sV[v][tid + a];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) DD.D2[v][a] = sD2[v][tid + a];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) DD.D3[v][a] = sD3[v][tid + a];
-    }
-    const double dxmax = bitsd(S->Jmax[STAGE - 1]);
-    EdgeState o;
-    uint8_t flag;
-    double wl, wr;
-    swale::recon_cell(K.sc, h, v0, DD, dxmax, o, flag, wl, wr, st);
-    const int64_t idx = c + 1;
-    D.eEL[idx] = o.EL;
-    D.eER[idx] = o.ER;
-    D.eBL[idx] = o.BL;
-    D.eBR[idx] = o.BR;
-    D.ehL[idx] = o.hL;
-    D.ehR[idx] = o.hR;
-    D.euL[idx] = o.uL;
-    D.euR[idx] = o.uR;
-    D.ipair[idx] = sIP[tid + 2];  // pair (c, c+1)
-    D.itri[idx] = sIT[tid + 1];   // triple centred at c
-    if (STAGE == 1) D.flags[idx] = flag;
-    // Edges that touch interfaces 0..N only.
-    if (c == -1) wave = wr;
-    else if (c == N) wave = wl;
-    else wave = fmax(wl, wr);
-    if (!(wave == wave)) st |= swale::ST_NONFINITE;
-  }
-  block_or_status(&S->status, st);
-  block_max_to(&S->A[STAGE - 1], wave);
-  if (STAGE == 1) {
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned int ticket = atomicAdd(&S->counter, 1u);
-      last = (ticket == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-      __threadfence();
-      const double A1 = bitsd(atomicAdd(&S->A[0], 0ull));
-      double Wbar = S->Wbar;
-      double dwmax = 0.0;
-      if (K.mesh == SWALE_MESH_FLUID_GAUSS) {
-        Wbar = bitsd(atomicAdd(&S->Wabs, 0ull));
-        dwmax = bitsd(atomicAdd(&S->dWabs, 0ull));
-        S->Wbar = Wbar;
-      }
-      const double alpha1 = A1 + Wbar;
-      const double t = S->t;
-      double dt;
-      int clipped = 0;
-      if (K.dt_fixed > 0.0) {
-        dt = K.dt_fixed;
-      } else {
-        const double jmin = bitsd(S->Jmin0);
-        dt = K.cfl * jmin / alpha1;
-        if (K.mesh == SWALE_MESH_FLUID_GAUSS && dwmax > 0.0) dt = fmin(dt, 0.5 * jmin / dwmax);
-      }
-      if (K.t_end > 0.0 && K.t_end - t <= dt) {
-        dt = K.t_end - t;
-        clipped = 1;
-      }
-      S->dt = dt;
-      S->alpha1 = alpha1;
-      S->clipped = clipped;
-      if (K.mesh == SWALE_MESH_PROFILE) {
-        const double s0 = sin(kTwoPi * t / K.mesh_T);
-        const double s1 = sin(kTwoPi * (t + dt) / K.mesh_T);
-        S->sdiff = (s1 - s0) / dt;
-      } else {
-        S->sdiff = 0.0;
-      }
-      S->counter = 0u;
-    }
-  }
-}
-
-// ------------------------------------------------------------------------------------
-// Fluxes, source and the RK combination of stage STAGE for cells 0..N-1 (MODE 0), or the
-// bare right-hand side (MODE 1, used by swale_rhs). A block owns kUpdateThreads consecutive
-// cells: each of its interfaces' fluxes is computed once into shared memory, the widths,
-// their reciprocals and the depth / bottom averages of the tile plus one halo cell each
-// side are staged there too.
-// ------------------------------------------------------------------------------------
-struct RhsOut {
-  double *RE, *RM, *RB;
-  double alpha;
-};
-
-template <int STAGE, int MODE>
-__global__ void __launch_bounds__(kUpdateThreads) k_update(StepConst K, DevState D, const double* __restrict__ E,
-                                                           const double* __restrict__ M,
-                                                           const double* __restrict__ B,
-                                                           const double* __restrict__ Js, RhsOut ro) {
-  constexpr int T = kUpdateThreads;
-  __shared__ double sF[4][T + 1], sW[T + 1];               // interfaces / nodes j0 .. j0+T
-  __shared__ double sJ[T + 2], siJ[T + 2], sH[T + 2], sB[T + 2];  // cells j0-1 .. j0+T
-  DevScalars* S = D.S;
-  if (MODE == 0 && S->done) return;
-  const int64_t N = K.N;
-  const int tid = threadIdx.x;
-  const int64_t j0 = (int64_t)blockIdx.x * T;
-  double alpha, dt = 0.0;
-  if (MODE == 1) {
-    alpha = ro.alpha;
-  } else {
-    alpha = (STAGE == 1) ? S->alpha1 : bitsd(S->A[STAGE - 1]) + S->Wbar;
-    dt = S->dt;
-  }
-  const double sdiff = (MODE == 0 && STAGE == 1 && K.mesh == SWALE_MESH_PROFILE) ? S->sdiff : 0.0;
-  for (int i = tid; i <= T; i += T) {
-    const int64_t k = j0 + i;  // node / interface index
-    if (k <= N) {
-      double wk;
-      if (MODE == 0 && STAGE == 1 && K.mesh == SWALE_MESH_PROFILE) {
-        wk = D.P[k] * sdiff;
-        if (i < T || k == N) D.w[k] = wk;
-      } else if (MODE == 0 && K.mesh == SWALE_MESH_STATIC) {
-        wk = 0.0;
-      } else {
-        wk = D.w[k];
-      }
-      sW[i] = wk;
-      // Interface k: left state = right edge of cell k-1 (edge index k), right state = left
-      // edge of cell k (edge index k+1).
-      const swale::Flux F = swale::interface_flux(K.sc.g, alpha, wk, D.eER[k], D.eEL[k + 1], D.eBR[k], D.eBL[k + 1],
-                                                  D.ehR[k], D.ehL[k + 1], D.euR[k], D.euL[k + 1]);
-      sF[0][i] = F.FE;
-      sF[1][i] = F.FMm;
-      sF[2][i] = F.FMp;
-      sF[3][i] = F.FB;
-    }
-  }
-  for (int i = tid; i < T + 2; i += T) {
-    const int64_t c = j0 - 1 + i;
-    if (c >= -1 && c <= N) {
-      const int64_t s = ghost(c, N, K.bc);
-      const double jv = Js[s];
-      sJ[i] = jv;
-      siJ[i] = 1.0 / jv;
-      sH[i] = E[s] - B[s];
-      sB[i] = B[s];
-    }
-  }
-  __syncthreads();
-  const int64_t j = j0 + tid;
-  double jmaxa = 0.0, jmaxb = 0.0, jminb = INFINITY;
-  uint32_t st = 0;
-  if (j < N) {
-    const swale::Flux Fl = {sF[0][tid], sF[1][tid], sF[2][tid], sF[3][tid]};
-    const swale::Flux Fr = {sF[0][tid + 1], sF[1][tid + 1], sF[2][tid + 1], sF[3][tid + 1]};
-    const int64_t ic = j + 1;  // edge-array index of cell j
-    const swale::SourceGeom sg = swale::source_geom(sJ[tid], sJ[tid + 1], siJ[tid], siJ[tid + 1], siJ[tid + 2],
-                                                    D.ipair[j], D.ipair[j + 1], D.itri[j + 1]);
-    const double hd[5] = {sH[tid], sH[tid + 1], sH[tid + 2], D.ehL[ic], D.ehR[ic]};
-    const double bd[5] = {sB[tid], sB[tid + 1], sB[tid + 2], D.eBL[ic], D.eBR[ic]};
-    const double Sj = swale::source_cell(K.sc.g, hd, bd, sg);
-    const swale::CellRhs R = swale::cell_rhs(Fl, Fr, Sj);
-    const double RE = R.RE, RM = R.RM, RB = R.RB;
-    if (MODE == 1) {
-      ro.RE[j] = RE;
-      ro.RM[j] = RM;
-      ro.RB[j] = RB;
-    } else {
-      const double wl = sW[tid], wr = sW[tid + 1];
-      const double J0 = D.J0[j];
-      const double dw = wr - wl;
-      if (STAGE == 1) {
-        const double J1 = J0 + dt * dw;
-        const double J2 = 0.75 * J0 + 0.25 * J1 + 0.25 * dt * dw;
-        D.J1[j] = J1;
-        D.J2[j] = J2;
-        jmaxa = J1;
-        jmaxb = J2;
-        if (!(J1 > 0.0) || !(J2 > 0.0)) st |= swale::ST_EMESH;
-        const double yE = J0 * D.E0[j] + dt * RE, yM = J0 * D.M0[j] + dt * RM, yB = J0 * D.B0[j] + dt * RB;
-        D.YE[j] = yE;
-        D.YM[j] = yM;
-        D.YB[j] = yB;
-        const double inv = 1.0 / J1;
-        D.Ea[j] = yE * inv;
-        D.Ma[j] = yM * inv;
-        D.Ba[j] = yB * inv;
-      } else if (STAGE == 2) {
-        const double yE = 0.75 * (J0 * D.E0[j]) + 0.25 * (D.YE[j] + dt * RE);
-        const double yM = 0.75 * (J0 * D.M0[j]) + 0.25 * (D.YM[j] + dt * RM);
-        const double yB = 0.75 * (J0 * D.B0[j]) + 0.25 * (D.YB[j] + dt * RB);
-        D.YE[j] = yE;
-        D.YM[j] = yM;
-        D.YB[j] = yB;
-        const double inv = 1.0 / D.J2[j];
-        D.Eb[j] = yE * inv;
-        D.Mb[j] = yM * inv;
-        D.Bb[j] = yB * inv;
-      } else {
-        const double J3 = (1.0 / 3.0) * J0 + (2.0 / 3.0) * D.J2[j] + (2.0 / 3.0) * dt * dw;
-        if (!(J3 > 0.0)) st |= swale::ST_EMESH;
-        const double yE = (1.0 / 3.0) * (J0 * D.E0[j]) + (2.0 / 3.0) * (D.YE[j] + dt * RE);
-        const double yM = (1.0 / 3.0) * (J0 * D.M0[j]) + (2.0 / 3.0) * (D.YM[j] + dt * RM);
-        const double yB = (1.0 / 3.0) * (J0 * D.B0[j]) + (2.0 / 3.0) * (D.YB[j] + dt * RB);
-        const double inv = 1.0 / J3;
-        const double En = yE * inv, Mn = yM * inv, Bn = yB * inv;
-        D.E0[j] = En;
-        D.M0[j] = Mn;
-        D.B0[j] = Bn;
-        D.J0[j] = J3;
-        jmaxb = J3;
-        jminb = J3;
-        D.x[j] += dt * wl;
-        if (j == N - 1) D.x[N] += dt * wr;
-        const double chk = En + Mn + Bn;
-        if (!(chk == chk) || fabs(chk) > 1.0e300) st |= swale::ST_NONFINITE;
-      }
-    }
-  }
-  if (MODE == 0) {
-    block_or_status(&S->status, st);
-    if (STAGE == 1) {
-      block_max_to(&S->Jmax[1], jmaxa);
-      block_max_to(&S->Jmax[2], jmaxb);
-    } else if (STAGE == 3) {
-      block_max_to(&S->JmaxN, jmaxb);
-      block_min_to(&S->JminN, jminb);
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
-        S->t = S->clipped ? K.t_end : S->t + S->dt;
-        S->steps += 1;
-      }
-    }
-  }
-}
-
-}  // namespace
-
-// ======================================================================================
-// Host side
-// ======================================================================================
 struct swale_ctx {
   swale_config cfg;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  int64_t N = 0;
+  int64_t B = 0, Ntot = 0;        // instances, total cells
+  std::vector<int64_t> off;       // B + 1 cell offsets
   DevState D{};
-  double Wbar_profile = 0.0;
+  int Tr = 128, Tu = 128;         // tile sizes of the reconstruction / update kernels
+  int grid_r = 0, grid_u = 0;     // 0: one block per tile, else a persistent grid of that size
   double gauss_wsum = 1.0;
-  std::vector<void*> allocs;
+  std::vector<void*> allocs;      // state
+  std::vector<void*> tile_allocs; // work lists (rebuilt when the tile sizes change)
+  uint8_t* flag_buf = nullptr;    // dense classes of a batch
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
   std::string err;
@@ -554,14 +65,15 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Copies n doubles from caller memory (host or device) into a host vector.
-swale_status fetch(swale_ctx* ctx, const double* src, size_t n, std::vector<double>& dst) {
+// Copies n values from caller memory (host or device) into a host vector.
+template <class T>
+swale_status fetch(swale_ctx* ctx, const T* src, size_t n, std::vector<T>& dst) {
   dst.resize(n);
   if (is_device_ptr(src)) {
-    SW_CUDA(ctx, cudaMemcpyAsync(dst.data(), src, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    SW_CUDA(ctx, cudaMemcpyAsync(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
     SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   } else {
-    std::memcpy(dst.data(), src, n * sizeof(double));
+    std::memcpy(dst.data(), src, n * sizeof(T));
   }
   return SWALE_OK;
 }
@@ -579,57 +91,70 @@ StepConst step_const(const swale_ctx* ctx) {
   K.sc.eps_pp = ctx->cfg.eps_pp;
   K.sc.h_dry = ctx->cfg.h_dry;
   K.sc.beta_dx_global = ctx->cfg.beta_dx_global;
-  K.cfl = ctx->cfg.cfl;
   K.t_end = ctx->cfg.t_end;
   K.dt_fixed = ctx->cfg.dt_fixed;
   K.mesh_T = ctx->cfg.mesh_T;
-  K.Wbar_profile = ctx->Wbar_profile;
   K.gauss_wsum = ctx->gauss_wsum;
-  K.N = ctx->N;
   K.bc = ctx->cfg.bc;
   K.mesh = ctx->cfg.mesh;
   K.gauss_half = ctx->cfg.gauss_half;
+  K.B = (int32_t)ctx->B;
   return K;
 }
 
-void free_state(swale_ctx* ctx) {
+void drop_graph(swale_ctx* ctx) {
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
   }
+}
+
+void free_tiles(swale_ctx* ctx) {
+  for (void* p : ctx->tile_allocs) cudaFree(p);
+  ctx->tile_allocs.clear();
+  ctx->D.rtiles = ctx->D.utiles = ctx->D.mtiles = nullptr;
+}
+
+void free_state(swale_ctx* ctx) {
+  drop_graph(ctx);
+  free_tiles(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   ctx->D = DevState{};
-  ctx->N = 0;
+  ctx->B = ctx->Ntot = 0;
+  ctx->off.clear();
+  ctx->flag_buf = nullptr;
 }
 
 template <class T>
-swale_status dalloc(swale_ctx* ctx, T** p, size_t n) {
+swale_status dalloc(swale_ctx* ctx, std::vector<void*>& list, T** p, size_t n) {
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, n * sizeof(T) + 256);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, SWALE_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   }
-  ctx->allocs.push_back(q);
+  list.push_back(q);
   *p = reinterpret_cast<T*>(q);
   return SWALE_OK;
 }
 
-swale_status alloc_state(swale_ctx* ctx, int64_t N, DevState& D) {
-  const size_t n = (size_t)N, n1 = n + 1, n2 = n + 2;
+// Device arrays of B instances with Ntot cells in total.
+swale_status alloc_state(swale_ctx* ctx, int64_t B, int64_t Ntot, DevState& D) {
+  const size_t nc = (size_t)Ntot, nn = nc + B, ne = nc + 2 * B;
   double** cells[] = {&D.E0, &D.M0, &D.B0, &D.Ea, &D.Ma, &D.Ba, &D.Eb, &D.Mb,
                       &D.Bb, &D.YE, &D.YM, &D.YB, &D.J0, &D.J1, &D.J2};
   for (double** p : cells)
-    if (swale_status s = dalloc(ctx, p, n)) return s;
+    if (swale_status s = dalloc(ctx, ctx->allocs, p, nc)) return s;
   double** nodes[] = {&D.x, &D.w, &D.P};
   for (double** p : nodes)
-    if (swale_status s = dalloc(ctx, p, n1)) return s;
+    if (swale_status s = dalloc(ctx, ctx->allocs, p, nn)) return s;
   double** edges[] = {&D.eEL, &D.eER, &D.eBL, &D.eBR, &D.ehL, &D.ehR, &D.euL, &D.euR, &D.ipair, &D.itri};
   for (double** p : edges)
-    if (swale_status s = dalloc(ctx, p, n2)) return s;
-  if (swale_status s = dalloc(ctx, &D.flags, n2)) return s;
-  if (swale_status s = dalloc(ctx, &D.S, 1)) return s;
+    if (swale_status s = dalloc(ctx, ctx->allocs, p, ne)) return s;
+  if (swale_status s = dalloc(ctx, ctx->allocs, &D.flags, ne)) return s;
+  if (swale_status s = dalloc(ctx, ctx->allocs, &D.IC, (size_t)B)) return s;
+  if (swale_status s = dalloc(ctx, ctx->allocs, &D.S, (size_t)B)) return s;
   return SWALE_OK;
 }
 
@@ -667,6 +192,59 @@ swale_status check_config(const swale_config* c, std::string& why) {
   return SWALE_OK;
 }
 
+bool valid_tile(int T) { return T == 64 || T == 128 || T == 256; }
+
+// Builds the work lists for the current tile sizes (implicit for one instance) and the
+// per-instance tile counts; uploads the instance constants.
+swale_status build_tiles(swale_ctx* ctx, std::vector<InstConst>& ic) {
+  drop_graph(ctx);
+  free_tiles(ctx);
+  const int64_t B = ctx->B;
+  const int Tr = ctx->Tr, Tu = ctx->Tu, Tm = kMeshThreads;
+  std::vector<Tile> rt, ut, mt;
+  for (int64_t i = 0; i < B; ++i) {
+    const int64_t N = ic[i].N;
+    const int64_t nr = (N + 2 + Tr - 1) / Tr, nu = (N + Tu - 1) / Tu, nm = (N + 1 + Tm - 1) / Tm;
+    ic[i].ntiles_r = (int32_t)nr;
+    if (B > 1) {
+      for (int64_t t = 0; t < nr; ++t) rt.push_back(Tile{(int32_t)i, (int32_t)(t * Tr - 1)});
+      for (int64_t t = 0; t < nu; ++t) ut.push_back(Tile{(int32_t)i, (int32_t)(t * Tu)});
+      for (int64_t t = 0; t < nm; ++t) mt.push_back(Tile{(int32_t)i, (int32_t)(t * Tm)});
+    } else {
+      ctx->D.nr = (int32_t)nr;
+      ctx->D.nu = (int32_t)nu;
+      ctx->D.nm = (int32_t)nm;
+    }
+  }
+  if (B > 1) {
+    Tile *dr, *du, *dm;
+    if (swale_status s = dalloc(ctx, ctx->tile_allocs, &dr, rt.size())) return s;
+    if (swale_status s = dalloc(ctx, ctx->tile_allocs, &du, ut.size())) return s;
+    if (swale_status s = dalloc(ctx, ctx->tile_allocs, &dm, mt.size())) return s;
+    SW_CUDA(ctx, cudaMemcpyAsync(dr, rt.data(), rt.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream));
+    SW_CUDA(ctx, cudaMemcpyAsync(du, ut.data(), ut.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream));
+    SW_CUDA(ctx, cudaMemcpyAsync(dm, mt.data(), mt.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream));
+    ctx->D.rtiles = dr;
+    ctx->D.utiles = du;
+    ctx->D.mtiles = dm;
+    ctx->D.nr = (int32_t)rt.size();
+    ctx->D.nu = (int32_t)ut.size();
+    ctx->D.nm = (int32_t)mt.size();
+  }
+  SW_CUDA(ctx, cudaMemcpyAsync(ctx->D.IC, ic.data(), B * sizeof(InstConst), cudaMemcpyHostToDevice, ctx->stream));
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SWALE_OK;
+}
+
+// Re-reads the instance constants from the device, rebuilds the work lists.
+swale_status rebuild_tiles(swale_ctx* ctx) {
+  std::vector<InstConst> ic(ctx->B);
+  SW_CUDA(ctx, cudaMemcpyAsync(ic.data(), ctx->D.IC, ctx->B * sizeof(InstConst), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return build_tiles(ctx, ic);
+}
+
 enum { FAM_PROLOGUE = 0, FAM_MESH = 1, FAM_RECON = 2, FAM_UPDATE = 3, FAM_COUNT = 4 };
 
 // Runs launch() on the context's stream; with timing enabled, brackets it by two events.
@@ -689,39 +267,57 @@ swale_status timed_launch(swale_ctx* ctx, int family, F&& launch) {
   return SWALE_OK;
 }
 
+template <int STAGE>
+void launch_recon(const StepConst& K, const DevState& D, int T, unsigned grid, cudaStream_t s, const double* E,
+                  const double* M, const double* B, const double* J) {
+  if (T == 64) k_recon<STAGE, 64><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
+  else if (T == 256) k_recon<STAGE, 256><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
+  else k_recon<STAGE, 128><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
+}
+
+template <int STAGE, int MODE>
+void launch_update(const StepConst& K, const DevState& D, int T, unsigned grid, cudaStream_t s, const double* E,
+                   const double* M, const double* B, const double* J, RhsOut ro) {
+  if (T == 64) k_update<STAGE, MODE, 64><<<grid, 64, 0, s>>>(K, D, E, M, B, J, ro);
+  else if (T == 256) k_update<STAGE, MODE, 256><<<grid, 256, 0, s>>>(K, D, E, M, B, J, ro);
+  else k_update<STAGE, MODE, 128><<<grid, 128, 0, s>>>(K, D, E, M, B, J, ro);
+}
+
+unsigned grid_of(int32_t ntiles, int persistent) {
+  if (persistent > 0 && persistent < ntiles) return (unsigned)persistent;
+  return (unsigned)std::max(ntiles, 1);
+}
+
 // Enqueues one step on the context's stream.
 swale_status enqueue_step(swale_ctx* ctx) {
   const StepConst K = step_const(ctx);
-  DevState& D = ctx->D;
-  const int64_t N = ctx->N;
+  const DevState& D = ctx->D;
   cudaStream_t s = ctx->stream;
-  const unsigned gr = (unsigned)((N + 2 + kReconThreads - 1) / kReconThreads);
-  const unsigned gu = (unsigned)((N + kUpdateThreads - 1) / kUpdateThreads);
+  const unsigned gr = grid_of(D.nr, ctx->grid_r), gu = grid_of(D.nu, ctx->grid_u);
+  const int Tr = ctx->Tr, Tu = ctx->Tu;
   const RhsOut none{nullptr, nullptr, nullptr, 0.0};
   swale_status st = SWALE_OK;
   auto L = [&](int fam, auto&& f) {
     if (st == SWALE_OK) st = timed_launch(ctx, fam, f);
   };
-  L(FAM_PROLOGUE, [&] { k_prologue<<<1, 32, 0, s>>>(K, D.S); });
+  L(FAM_PROLOGUE, [&] { k_prologue<<<(unsigned)((ctx->B + 127) / 128), 128, 0, s>>>(K, D); });
   if (K.mesh == SWALE_MESH_FLUID_GAUSS) {
-    const int T = 256;
-    const unsigned gm = (unsigned)((N + 1 + T - 1) / T);
-    const size_t shm = (size_t)(3 * T + 4 * K.gauss_half + 4) * sizeof(double);
-    L(FAM_MESH, [&] { k_mesh_gauss<<<gm, T, shm, s>>>(K, D); });
+    const size_t shm = (size_t)(3 * kMeshThreads + 4 * K.gauss_half + 4) * sizeof(double);
+    L(FAM_MESH, [&] { k_mesh_gauss<<<(unsigned)std::max(D.nm, 1), kMeshThreads, shm, s>>>(K, D); });
   }
-  L(FAM_RECON, [&] { k_recon<1><<<gr, kReconThreads, 0, s>>>(K, D, D.E0, D.M0, D.B0, D.J0); });
-  L(FAM_UPDATE, [&] { k_update<1, 0><<<gu, kUpdateThreads, 0, s>>>(K, D, D.E0, D.M0, D.B0, D.J0, none); });
-  L(FAM_RECON, [&] { k_recon<2><<<gr, kReconThreads, 0, s>>>(K, D, D.Ea, D.Ma, D.Ba, D.J1); });
-  L(FAM_UPDATE, [&] { k_update<2, 0><<<gu, kUpdateThreads, 0, s>>>(K, D, D.Ea, D.Ma, D.Ba, D.J1, none); });
-  L(FAM_RECON, [&] { k_recon<3><<<gr, kReconThreads, 0, s>>>(K, D, D.Eb, D.Mb, D.Bb, D.J2); });
-  L(FAM_UPDATE, [&] { k_update<3, 0><<<gu, kUpdateThreads, 0, s>>>(K, D, D.Eb, D.Mb, D.Bb, D.J2, none); });
+  L(FAM_RECON, [&] { launch_recon<1>(K, D, Tr, gr, s, D.E0, D.M0, D.B0, D.J0); });
+  L(FAM_UPDATE, [&] { launch_update<1, 0>(K, D, Tu, gu, s, D.E0, D.M0, D.B0, D.J0, none); });
+  L(FAM_RECON, [&] { launch_recon<2>(K, D, Tr, gr, s, D.Ea, D.Ma, D.Ba, D.J1); });
+  L(FAM_UPDATE, [&] { launch_update<2, 0>(K, D, Tu, gu, s, D.Ea, D.Ma, D.Ba, D.J1, none); });
+  L(FAM_RECON, [&] { launch_recon<3>(K, D, Tr, gr, s, D.Eb, D.Mb, D.Bb, D.J2); });
+  L(FAM_UPDATE, [&] { launch_update<3, 0>(K, D, Tu, gu, s, D.Eb, D.Mb, D.Bb, D.J2, none); });
   if (st) return st;
   SW_CUDA(ctx, cudaGetLastError());
   return SWALE_OK;
 }
 
-// Enqueues n steps: whole graphs of kGraphSteps steps, then single steps (graphs are not
-// used while kernel timing is on).
+// Enqueues n steps: whole graphs of kGraphSteps steps, then single steps (graphs are not used
+// while kernel timing is on).
 swale_status enqueue_steps(swale_ctx* ctx, int64_t n) {
   constexpr int kGraphSteps = 8;
   if (!ctx->timing && n >= kGraphSteps) {
@@ -745,6 +341,98 @@ swale_status enqueue_steps(swale_ctx* ctx, int64_t n) {
   }
   for (; n > 0; --n)
     if (swale_status s = enqueue_step(ctx)) return s;
+  return SWALE_OK;
+}
+
+// Common set-up of B instances from host vectors.
+swale_status set_instances(swale_ctx* ctx, const std::vector<int64_t>& off, const std::vector<double>& x,
+                           const std::vector<double>& q, const std::vector<double>& m, const std::vector<double>& bb,
+                           const std::vector<double>& P, const std::vector<double>& cfl, bool q0_is_eta) {
+  const int64_t B = (int64_t)off.size() - 1;
+  const int64_t Ntot = off[B];
+  std::vector<double> E(Ntot), J(Ntot);
+  std::vector<InstConst> ic(B);
+  std::vector<DevScalars> S0(B);
+  for (int64_t i = 0; i < B; ++i) {
+    const int64_t c0 = off[i], N = off[i + 1] - off[i], n0 = c0 + i;
+    if (N < 5) return fail(ctx, SWALE_EINVAL, "every instance needs N >= 5 cells");
+    double jmax = 0.0, jmin = INFINITY, pmax = 0.0;
+    for (int64_t k = 0; k <= N; ++k) {
+      if (!std::isfinite(x[n0 + k]) || !std::isfinite(P[n0 + k]))
+        return fail(ctx, SWALE_EINVAL, "non-finite node or profile");
+      pmax = std::max(pmax, std::fabs(P[n0 + k]));
+    }
+    for (int64_t j = 0; j < N; ++j) {
+      const int64_t g = c0 + j;
+      J[g] = x[n0 + j + 1] - x[n0 + j];
+      if (!(J[g] > 0.0)) return fail(ctx, SWALE_EINVAL, "nodes must be strictly increasing");
+      jmax = std::max(jmax, J[g]);
+      jmin = std::min(jmin, J[g]);
+      if (!std::isfinite(q[g]) || !std::isfinite(m[g]) || !std::isfinite(bb[g]))
+        return fail(ctx, SWALE_EINVAL, "non-finite cell average");
+      E[g] = q0_is_eta ? q[g] : q[g] + bb[g];
+      if (E[g] - bb[g] < 0.0) return fail(ctx, SWALE_EINVAL, "negative depth in the initial data");
+    }
+    if (!(cfl[i] > 0.0) && !(ctx->cfg.dt_fixed > 0.0)) return fail(ctx, SWALE_EINVAL, "cfl must be > 0");
+    ic[i].N = N;
+    ic[i].coff = c0;
+    ic[i].cfl = cfl[i];
+    ic[i].Wbar_profile = (ctx->cfg.mesh == SWALE_MESH_PROFILE) ? kTwoPi / ctx->cfg.mesh_T * pmax : 0.0;
+    ic[i].ntiles_r = 0;
+    ic[i].pad_ = 0;
+    std::memset(&S0[i], 0, sizeof(DevScalars));
+    std::memcpy(&S0[i].JmaxN, &jmax, 8);
+    std::memcpy(&S0[i].JminN, &jmin, 8);
+    S0[i].Wbar = ic[i].Wbar_profile;
+  }
+  free_state(ctx);
+  swale_status s = alloc_state(ctx, B, Ntot, ctx->D);
+  if (s) {
+    free_state(ctx);
+    return s;
+  }
+  ctx->B = B;
+  ctx->Ntot = Ntot;
+  ctx->off = off;
+  DevState& D = ctx->D;
+  cudaStream_t st = ctx->stream;
+  const size_t cb = Ntot * sizeof(double), nb = (Ntot + B) * sizeof(double);
+  SW_CUDA(ctx, cudaMemcpyAsync(D.E0, E.data(), cb, cudaMemcpyHostToDevice, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(D.M0, m.data(), cb, cudaMemcpyHostToDevice, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(D.B0, bb.data(), cb, cudaMemcpyHostToDevice, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(D.J0, J.data(), cb, cudaMemcpyHostToDevice, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(D.x, x.data(), nb, cudaMemcpyHostToDevice, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(D.P, P.data(), nb, cudaMemcpyHostToDevice, st));
+  SW_CUDA(ctx, cudaMemsetAsync(D.w, 0, nb, st));
+  SW_CUDA(ctx, cudaMemsetAsync(D.flags, 0, Ntot + 2 * B, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(D.S, S0.data(), B * sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+  if (ctx->cfg.mesh == SWALE_MESH_FLUID_GAUSS) {
+    const int H = ctx->cfg.gauss_half;
+    std::vector<double> gw(2 * kMaxGaussHalf + 1, 0.0);
+    for (int mm = -H; mm <= H; ++mm)
+      gw[mm + H] = std::exp(-(double)(mm * mm) / (2.0 * ctx->cfg.gauss_sigma * ctx->cfg.gauss_sigma));
+    double ws = 0.0;
+    for (int mm = -H; mm <= H; ++mm) ws += gw[mm + H];
+    ctx->gauss_wsum = ws;
+    SW_CUDA(ctx, cudaMemcpyToSymbolAsync(c_gauss_w, gw.data(), gw.size() * sizeof(double), 0,
+                                         cudaMemcpyHostToDevice, st));
+  }
+  return build_tiles(ctx, ic);
+}
+
+swale_status status_from_bits(swale_ctx* ctx, unsigned int bits) {
+  if (bits & swale::ST_NONFINITE) return fail(ctx, SWALE_ENONFINITE, "non-finite value in a stage");
+  if (bits & swale::ST_EMESH) return fail(ctx, SWALE_EMESH, "non-positive cell width");
+  if (bits & swale::ST_EWEIGHT) return fail(ctx, SWALE_EWEIGHT, "non-positive linear weight");
+  return SWALE_OK;
+}
+
+// Per-instance scalars to the host.
+swale_status read_scalars(swale_ctx* ctx, std::vector<DevScalars>& S) {
+  S.resize(ctx->B);
+  SW_CUDA(ctx, cudaMemcpyAsync(S.data(), ctx->D.S, ctx->B * sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return SWALE_OK;
 }
 
@@ -783,6 +471,7 @@ swale_status swale_set_problem(swale_ctx* ctx, int64_t N, const double* x_nodes,
                                const double* b, const double* profile, int32_t q0_is_eta) {
   if (!ctx) return SWALE_EINVAL;
   if (N < 5) return fail(ctx, SWALE_EINVAL, "N must be >= 5");
+  if (N > 0x7fffffffLL) return fail(ctx, SWALE_EINVAL, "N must be < 2^31");
   if (!x_nodes || !q0 || !hu || !b) return fail(ctx, SWALE_EINVAL, "x_nodes, q0, hu and b are required");
   if (ctx->cfg.mesh == SWALE_MESH_PROFILE && !profile)
     return fail(ctx, SWALE_EINVAL, "profile motion needs the node profile");
@@ -796,65 +485,46 @@ swale_status swale_set_problem(swale_ctx* ctx, int64_t N, const double* x_nodes,
   } else {
     P.assign(N + 1, 0.0);
   }
-  std::vector<double> E(N), J(N);
-  double jmax = 0.0, jmin = INFINITY, pmax = 0.0;
-  for (int64_t k = 0; k <= N; ++k) {
-    if (!std::isfinite(x[k]) || !std::isfinite(P[k])) return fail(ctx, SWALE_EINVAL, "non-finite node or profile");
-    pmax = std::max(pmax, std::fabs(P[k]));
-  }
-  for (int64_t j = 0; j < N; ++j) {
-    J[j] = x[j + 1] - x[j];
-    if (!(J[j] > 0.0)) return fail(ctx, SWALE_EINVAL, "nodes must be strictly increasing");
-    jmax = std::max(jmax, J[j]);
-    jmin = std::min(jmin, J[j]);
-    if (!std::isfinite(q[j]) || !std::isfinite(m[j]) || !std::isfinite(bb[j]))
-      return fail(ctx, SWALE_EINVAL, "non-finite cell average");
-    E[j] = q0_is_eta ? q[j] : q[j] + bb[j];
-    if (E[j] - bb[j] < 0.0) return fail(ctx, SWALE_EINVAL, "negative depth in the initial data");
-  }
-  free_state(ctx);
-  if ((s = alloc_state(ctx, N, ctx->D))) {
-    free_state(ctx);
+  return set_instances(ctx, {0, N}, x, q, m, bb, P, {ctx->cfg.cfl}, q0_is_eta != 0);
+}
+
+swale_status swale_batch_set_problem(swale_ctx* ctx, int64_t B, const int64_t* offsets, const double* x_nodes,
+                                     const double* q0, const double* hu, const double* b, const double* profile,
+                                     const double* cfl, int32_t q0_is_eta) {
+  if (!ctx) return SWALE_EINVAL;
+  if (B < 1 || B > 0x7fffffff) return fail(ctx, SWALE_EINVAL, "B must be >= 1");
+  if (!offsets || !x_nodes || !q0 || !hu || !b)
+    return fail(ctx, SWALE_EINVAL, "offsets, x_nodes, q0, hu and b are required");
+  if (ctx->cfg.mesh == SWALE_MESH_PROFILE && !profile)
+    return fail(ctx, SWALE_EINVAL, "profile motion needs the node profile");
+  std::vector<int64_t> off;
+  swale_status s;
+  if ((s = fetch(ctx, offsets, (size_t)B + 1, off))) return s;
+  if (off[0] != 0) return fail(ctx, SWALE_EINVAL, "offsets[0] must be 0");
+  for (int64_t i = 0; i < B; ++i)
+    if (off[i + 1] - off[i] < 5) return fail(ctx, SWALE_EINVAL, "every instance needs N >= 5 cells");
+  if (off[B] > 0x7fffffffLL) return fail(ctx, SWALE_EINVAL, "total cells must be < 2^31");
+  const int64_t Ntot = off[B];
+  std::vector<double> x, q, m, bb, P, c;
+  if ((s = fetch(ctx, x_nodes, Ntot + B, x)) || (s = fetch(ctx, q0, Ntot, q)) || (s = fetch(ctx, hu, Ntot, m)) ||
+      (s = fetch(ctx, b, Ntot, bb)))
     return s;
+  if (profile) {
+    if ((s = fetch(ctx, profile, Ntot + B, P))) return s;
+  } else {
+    P.assign(Ntot + B, 0.0);
   }
-  ctx->N = N;
-  ctx->Wbar_profile = (ctx->cfg.mesh == SWALE_MESH_PROFILE) ? kTwoPi / ctx->cfg.mesh_T * pmax : 0.0;
-  DevState& D = ctx->D;
-  cudaStream_t st = ctx->stream;
-  const size_t cb = N * sizeof(double), nb = (N + 1) * sizeof(double);
-  SW_CUDA(ctx, cudaMemcpyAsync(D.E0, E.data(), cb, cudaMemcpyHostToDevice, st));
-  SW_CUDA(ctx, cudaMemcpyAsync(D.M0, m.data(), cb, cudaMemcpyHostToDevice, st));
-  SW_CUDA(ctx, cudaMemcpyAsync(D.B0, bb.data(), cb, cudaMemcpyHostToDevice, st));
-  SW_CUDA(ctx, cudaMemcpyAsync(D.J0, J.data(), cb, cudaMemcpyHostToDevice, st));
-  SW_CUDA(ctx, cudaMemcpyAsync(D.x, x.data(), nb, cudaMemcpyHostToDevice, st));
-  SW_CUDA(ctx, cudaMemcpyAsync(D.P, P.data(), nb, cudaMemcpyHostToDevice, st));
-  SW_CUDA(ctx, cudaMemsetAsync(D.w, 0, nb, st));
-  SW_CUDA(ctx, cudaMemsetAsync(D.flags, 0, N + 2, st));
-  DevScalars S0;
-  std::memset(&S0, 0, sizeof(S0));
-  double jmaxv = jmax, jminv = jmin;
-  std::memcpy(&S0.JmaxN, &jmaxv, 8);
-  std::memcpy(&S0.JminN, &jminv, 8);
-  S0.Wbar = ctx->Wbar_profile;
-  SW_CUDA(ctx, cudaMemcpyAsync(D.S, &S0, sizeof(S0), cudaMemcpyHostToDevice, st));
-  if (ctx->cfg.mesh == SWALE_MESH_FLUID_GAUSS) {
-    const int H = ctx->cfg.gauss_half;
-    std::vector<double> gw(2 * kMaxGaussHalf + 1, 0.0);
-    for (int mm = -H; mm <= H; ++mm)
-      gw[mm + H] = std::exp(-(double)(mm * mm) / (2.0 * ctx->cfg.gauss_sigma * ctx->cfg.gauss_sigma));
-    double ws = 0.0;
-    for (int mm = -H; mm <= H; ++mm) ws += gw[mm + H];
-    ctx->gauss_wsum = ws;
-    SW_CUDA(ctx, cudaMemcpyToSymbolAsync(c_gauss_w, gw.data(), gw.size() * sizeof(double), 0,
-                                         cudaMemcpyHostToDevice, st));
+  if (cfl) {
+    if ((s = fetch(ctx, cfl, (size_t)B, c))) return s;
+  } else {
+    c.assign(B, ctx->cfg.cfl);
   }
-  SW_CUDA(ctx, cudaStreamSynchronize(st));
-  return SWALE_OK;
+  return set_instances(ctx, off, x, q, m, bb, P, c, q0_is_eta != 0);
 }
 
 swale_status swale_step(swale_ctx* ctx, double* dt_out) {
   if (!ctx) return SWALE_EINVAL;
-  if (ctx->N == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
   if (swale_status s = enqueue_step(ctx)) return s;
   if (dt_out) {
     SW_CUDA(ctx, cudaMemcpyAsync(dt_out, &ctx->D.S->dt, sizeof(double), cudaMemcpyDefault, ctx->stream));
@@ -865,27 +535,23 @@ swale_status swale_step(swale_ctx* ctx, double* dt_out) {
 
 swale_status swale_advance(swale_ctx* ctx, int64_t max_steps, int64_t* steps_done) {
   if (!ctx) return SWALE_EINVAL;
-  if (ctx->N == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
   if (max_steps < 0) return fail(ctx, SWALE_EINVAL, "max_steps < 0");
   long long s0 = 0;
   SW_CUDA(ctx, cudaMemcpyAsync(&s0, &ctx->D.S->steps, sizeof(s0), cudaMemcpyDeviceToHost, ctx->stream));
   SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (swale_status s = enqueue_steps(ctx, max_steps)) return s;
-  long long s1 = 0;
+  std::vector<DevScalars> S;
+  if (swale_status s = read_scalars(ctx, S)) return s;
   unsigned int bits = 0;
-  SW_CUDA(ctx, cudaMemcpyAsync(&s1, &ctx->D.S->steps, sizeof(s1), cudaMemcpyDeviceToHost, ctx->stream));
-  SW_CUDA(ctx, cudaMemcpyAsync(&bits, &ctx->D.S->status, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
-  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (steps_done) *steps_done = s1 - s0;
-  if (bits & swale::ST_NONFINITE) return fail(ctx, SWALE_ENONFINITE, "non-finite value in a stage");
-  if (bits & swale::ST_EMESH) return fail(ctx, SWALE_EMESH, "non-positive cell width");
-  if (bits & swale::ST_EWEIGHT) return fail(ctx, SWALE_EWEIGHT, "non-positive linear weight");
-  return SWALE_OK;
+  for (const DevScalars& v : S) bits |= v.status;
+  if (steps_done) *steps_done = S[0].steps - s0;
+  return status_from_bits(ctx, bits);
 }
 
 swale_status swale_enqueue(swale_ctx* ctx, int64_t nsteps) {
   if (!ctx) return SWALE_EINVAL;
-  if (ctx->N == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
   if (nsteps < 0) return fail(ctx, SWALE_EINVAL, "nsteps < 0");
   return enqueue_steps(ctx, nsteps);
 }
@@ -920,8 +586,9 @@ swale_status swale_get_timing(swale_ctx* ctx, double* ms, int64_t* launches) {
 swale_status swale_get_state(swale_ctx* ctx, double* h, double* hu, double* b, double* eta, double* x_nodes,
                              double* t) {
   if (!ctx) return SWALE_EINVAL;
-  if (ctx->N == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
-  const int64_t N = ctx->N;
+  if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  if (ctx->B != 1) return fail(ctx, SWALE_EINVAL, "a batch: use swale_batch_get_state");
+  const int64_t N = ctx->Ntot;
   const size_t cb = N * sizeof(double);
   swale_status s;
   if ((s = put_out(ctx, hu, ctx->D.M0, cb)) || (s = put_out(ctx, b, ctx->D.B0, cb)) ||
@@ -940,24 +607,198 @@ swale_status swale_get_state(swale_ctx* ctx, double* h, double* hu, double* b, d
   return SWALE_OK;
 }
 
+swale_status swale_batch_get_state(swale_ctx* ctx, double* hu, double* b, double* eta, double* x_nodes, double* t,
+                                   double* dt) {
+  if (!ctx) return SWALE_EINVAL;
+  if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  const size_t cb = ctx->Ntot * sizeof(double), nb = (ctx->Ntot + ctx->B) * sizeof(double);
+  swale_status s;
+  if ((s = put_out(ctx, hu, ctx->D.M0, cb)) || (s = put_out(ctx, b, ctx->D.B0, cb)) ||
+      (s = put_out(ctx, eta, ctx->D.E0, cb)) || (s = put_out(ctx, x_nodes, ctx->D.x, nb)))
+    return s;
+  if (t || dt) {
+    std::vector<DevScalars> S;
+    if ((s = read_scalars(ctx, S))) return s;
+    std::vector<double> tv(ctx->B), dv(ctx->B);
+    for (int64_t i = 0; i < ctx->B; ++i) {
+      tv[i] = S[i].t;
+      dv[i] = S[i].dt;
+    }
+    if (t) SW_CUDA(ctx, cudaMemcpyAsync(t, tv.data(), ctx->B * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    if (dt) SW_CUDA(ctx, cudaMemcpyAsync(dt, dv.data(), ctx->B * sizeof(double), cudaMemcpyDefault, ctx->stream));
+  }
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SWALE_OK;
+}
+
 swale_status swale_get_flags(swale_ctx* ctx, uint8_t* flags) {
   if (!ctx || !flags) return SWALE_EINVAL;
-  if (ctx->N == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
-  SW_CUDA(ctx, cudaMemcpyAsync(flags, ctx->D.flags + 1, ctx->N, cudaMemcpyDefault, ctx->stream));
+  if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  if (ctx->B == 1) {
+    SW_CUDA(ctx, cudaMemcpyAsync(flags, ctx->D.flags + 1, ctx->Ntot, cudaMemcpyDefault, ctx->stream));
+  } else {
+    if (!ctx->flag_buf)
+      if (swale_status s = dalloc(ctx, ctx->allocs, &ctx->flag_buf, (size_t)ctx->Ntot)) return s;
+    k_gather_flags<<<(unsigned)std::min<int64_t>(ctx->B, 65535), 256, 0, ctx->stream>>>(ctx->D, (int32_t)ctx->B,
+                                                                                        ctx->flag_buf);
+    SW_CUDA(ctx, cudaGetLastError());
+    SW_CUDA(ctx, cudaMemcpyAsync(flags, ctx->flag_buf, ctx->Ntot, cudaMemcpyDefault, ctx->stream));
+  }
   SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return SWALE_OK;
 }
 
 swale_status swale_get_status(swale_ctx* ctx, uint32_t* status_bits, int64_t* steps, double* last_dt) {
   if (!ctx) return SWALE_EINVAL;
-  if (ctx->N == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
-  DevScalars S;
-  SW_CUDA(ctx, cudaMemcpyAsync(&S, ctx->D.S, sizeof(S), cudaMemcpyDeviceToHost, ctx->stream));
-  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (status_bits) *status_bits = S.status;
-  if (steps) *steps = S.steps;
-  if (last_dt) *last_dt = S.dt;
+  if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  std::vector<DevScalars> S;
+  if (swale_status s = read_scalars(ctx, S)) return s;
+  unsigned int bits = 0;
+  for (const DevScalars& v : S) bits |= v.status;
+  if (status_bits) *status_bits = bits;
+  if (steps) *steps = S[0].steps;
+  if (last_dt) *last_dt = S[0].dt;
   return SWALE_OK;
+}
+
+swale_status swale_set_tiles(swale_ctx* ctx, int32_t recon_tile, int32_t update_tile, int32_t recon_grid,
+                             int32_t update_grid) {
+  if (!ctx) return SWALE_EINVAL;
+  if (!valid_tile(recon_tile) || !valid_tile(update_tile) || recon_grid < 0 || update_grid < 0)
+    return fail(ctx, SWALE_EINVAL, "tiles must be 64, 128 or 256 and grids >= 0");
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const bool retile = (recon_tile != ctx->Tr || update_tile != ctx->Tu);
+  ctx->Tr = recon_tile;
+  ctx->Tu = update_tile;
+  ctx->grid_r = recon_grid;
+  ctx->grid_u = update_grid;
+  drop_graph(ctx);
+  if (retile && ctx->B > 0) return rebuild_tiles(ctx);
+  return SWALE_OK;
+}
+
+swale_status swale_get_tiles(swale_ctx* ctx, int32_t* tiles) {
+  if (!ctx || !tiles) return SWALE_EINVAL;
+  tiles[0] = ctx->Tr;
+  tiles[1] = ctx->Tu;
+  tiles[2] = ctx->grid_r;
+  tiles[3] = ctx->grid_u;
+  return SWALE_OK;
+}
+
+swale_status swale_autotune(swale_ctx* ctx, int32_t steps, const char* cache_path, int32_t* tiles_out) {
+  if (!ctx) return SWALE_EINVAL;
+  if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  if (steps < 1) return fail(ctx, SWALE_EINVAL, "steps must be >= 1");
+  int dev = 0, sms = 0;
+  SW_CUDA(ctx, cudaGetDevice(&dev));
+  SW_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // Cache key: device size, batch shape (instances, log2 of the cells), mesh kind.
+  std::ostringstream key;
+  key << "sm" << sms << "_B" << ctx->B << "_N2^" << (int)std::lround(std::log2((double)ctx->Ntot)) << "_mesh"
+      << ctx->cfg.mesh;
+  if (cache_path && *cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      if (line.find("\"" + key.str() + "\"") == std::string::npos) continue;
+      int v[4];
+      const char* names[4] = {"\"recon_tile\":", "\"update_tile\":", "\"recon_grid\":", "\"update_grid\":"};
+      bool ok = true;
+      for (int k = 0; k < 4 && ok; ++k) {
+        size_t p = line.find(names[k]);
+        if (p == std::string::npos) ok = false;
+        else v[k] = std::atoi(line.c_str() + p + std::strlen(names[k]));
+      }
+      if (ok && valid_tile(v[0]) && valid_tile(v[1])) {
+        if (swale_status s = swale_set_tiles(ctx, v[0], v[1], v[2], v[3])) return s;
+        if (tiles_out) swale_get_tiles(ctx, tiles_out);
+        return SWALE_OK;
+      }
+    }
+  }
+  // Snapshot of the evolving state; every candidate runs from it and it is restored after.
+  DevState& D = ctx->D;
+  const size_t cb = ctx->Ntot * sizeof(double), nb = (ctx->Ntot + ctx->B) * sizeof(double);
+  const size_t sb = ctx->B * sizeof(DevScalars);
+  std::vector<void*> snap_allocs;
+  double *sE = nullptr, *sM = nullptr, *sB = nullptr, *sJ = nullptr, *sx = nullptr;
+  DevScalars* sS = nullptr;
+  swale_status s = SWALE_OK;
+  if (!s) s = dalloc(ctx, snap_allocs, &sE, ctx->Ntot);
+  if (!s) s = dalloc(ctx, snap_allocs, &sM, ctx->Ntot);
+  if (!s) s = dalloc(ctx, snap_allocs, &sB, ctx->Ntot);
+  if (!s) s = dalloc(ctx, snap_allocs, &sJ, ctx->Ntot);
+  if (!s) s = dalloc(ctx, snap_allocs, &sx, ctx->Ntot + ctx->B);
+  if (!s) s = dalloc(ctx, snap_allocs, &sS, (size_t)ctx->B);
+  auto release = [&](swale_status r) {
+    cudaStreamSynchronize(ctx->stream);
+    for (void* p : snap_allocs) cudaFree(p);
+    return r;
+  };
+  if (s) return release(s);
+  auto copy_state = [&](bool save) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    double* dst[5] = {sE, sM, sB, sJ, sx};
+    double* src[5] = {D.E0, D.M0, D.B0, D.J0, D.x};
+    const size_t sz[5] = {cb, cb, cb, cb, nb};
+    for (int i = 0; i < 5 && !e; ++i)
+      e = save ? cudaMemcpyAsync(dst[i], src[i], sz[i], k, ctx->stream)
+               : cudaMemcpyAsync(src[i], dst[i], sz[i], k, ctx->stream);
+    if (!e) e = save ? cudaMemcpyAsync(sS, D.S, sb, k, ctx->stream) : cudaMemcpyAsync(D.S, sS, sb, k, ctx->stream);
+    return e;
+  };
+  if (cudaError_t e = copy_state(true)) return release(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
+  const bool timing = ctx->timing;
+  ctx->timing = false;
+  const int occ_r = 4, occ_u = 8;  // resident 128-thread blocks per SM of the persistent candidates
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = INFINITY;
+  int bt[4] = {ctx->Tr, ctx->Tu, ctx->grid_r, ctx->grid_u};
+  const int tiles[3] = {64, 128, 256};
+  for (int tr : tiles)
+    for (int tu : tiles)
+      for (int pers = 0; pers < 2 && !s; ++pers) {
+        const int gr = pers ? sms * occ_r * 128 / tr : 0, gu = pers ? sms * occ_u * 128 / tu : 0;
+        s = swale_set_tiles(ctx, tr, tu, gr, gu);
+        if (s) break;
+        float ms = 0.f;
+        cudaError_t e = copy_state(false);
+        // One untimed step, then the timed ones.
+        if (!e && !(s = enqueue_steps(ctx, 1))) {
+          cudaEventRecord(e0, ctx->stream);
+          s = enqueue_steps(ctx, steps);
+          cudaEventRecord(e1, ctx->stream);
+          e = cudaEventSynchronize(e1);
+          if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (e) s = fail(ctx, SWALE_ECUDA, cudaGetErrorString(e));
+        if (!s && ms < best) {
+          best = ms;
+          bt[0] = tr;
+          bt[1] = tu;
+          bt[2] = gr;
+          bt[3] = gu;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->timing = timing;
+  if (!s) s = swale_set_tiles(ctx, bt[0], bt[1], bt[2], bt[3]);
+  if (!s) {
+    if (cudaError_t e = copy_state(false)) s = fail(ctx, SWALE_ECUDA, cudaGetErrorString(e));
+  }
+  if (!s && cache_path && *cache_path) {
+    std::ofstream outf(cache_path, std::ios::app);
+    outf << "{\"key\": \"" << key.str() << "\", \"recon_tile\": " << bt[0] << ", \"update_tile\": " << bt[1]
+         << ", \"recon_grid\": " << bt[2] << ", \"update_grid\": " << bt[3] << ", \"ms_per_step\": "
+         << best / steps << "}\n";
+  }
+  if (!s && tiles_out) swale_get_tiles(ctx, tiles_out);
+  return release(s);
 }
 
 swale_status swale_rhs(swale_ctx* ctx, int64_t N, const double* E, const double* M, const double* B,
@@ -970,17 +811,19 @@ swale_status swale_rhs(swale_ctx* ctx, int64_t N, const double* E, const double*
   tmp.cfg = ctx->cfg;
   tmp.stream = ctx->stream;
   DevState& D = tmp.D;
-  swale_status s = alloc_state(&tmp, N, D);
+  swale_status s = alloc_state(&tmp, 1, N, D);
   double* R3 = nullptr;
-  if (!s) s = dalloc(&tmp, &R3, 3 * (size_t)N);
+  if (!s) s = dalloc(&tmp, tmp.allocs, &R3, 3 * (size_t)N);
   auto cleanup = [&](swale_status r) {
     cudaStreamSynchronize(tmp.stream);
     free_state(&tmp);
-    if (r != SWALE_OK) ctx->err = tmp.err;
+    tmp.stream = nullptr;
+    if (r != SWALE_OK && !tmp.err.empty()) ctx->err = tmp.err;
     return r;
   };
   if (s) return cleanup(s);
-  tmp.N = N;
+  tmp.B = 1;
+  tmp.Ntot = N;
   const size_t cb = N * sizeof(double);
   cudaStream_t st = ctx->stream;
   cudaError_t e = cudaSuccess;
@@ -989,61 +832,62 @@ swale_status swale_rhs(swale_ctx* ctx, int64_t N, const double* E, const double*
   e = e ? e : cudaMemcpyAsync(D.B0, B, cb, cudaMemcpyDefault, st);
   e = e ? e : cudaMemcpyAsync(D.J0, J, cb, cudaMemcpyDefault, st);
   e = e ? e : cudaMemcpyAsync(D.w, w, cb + sizeof(double), cudaMemcpyDefault, st);
-  std::vector<double> Jh(N);
-  e = e ? e : cudaMemcpyAsync(Jh.data(), J, cb, cudaMemcpyDefault, st);
-  e = e ? e : cudaStreamSynchronize(st);
   if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
-  double jmax = 0.0;
-  for (double v : Jh) jmax = std::max(jmax, v);
+  std::vector<InstConst> ic(1);
+  std::memset(ic.data(), 0, sizeof(InstConst));
+  ic[0].N = N;
+  ic[0].cfl = 1.0;
   DevScalars S0;
   std::memset(&S0, 0, sizeof(S0));
-  std::memcpy(&S0.Jmax[0], &jmax, 8);
-  std::memcpy(&S0.Jmax[1], &jmax, 8);
+  S0.Jmin0 = 0x3ff0000000000000ull;  // 1.0: keeps the unused stage-1 dt arithmetic finite
   e = cudaMemcpyAsync(D.S, &S0, sizeof(S0), cudaMemcpyHostToDevice, st);
   if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
+  if ((s = build_tiles(&tmp, ic))) return cleanup(s);
   StepConst K = step_const(&tmp);
   K.t_end = 0.0;
-  const unsigned gr = (unsigned)((N + 2 + kReconThreads - 1) / kReconThreads);
-  const unsigned gu = (unsigned)((N + kUpdateThreads - 1) / kUpdateThreads);
-  k_recon<2><<<gr, kReconThreads, 0, st>>>(K, D, D.E0, D.M0, D.B0, D.J0);
-  // k_recon<2> accumulates into S.A[1]; read it back to form alpha when not given.
+  K.mesh = SWALE_MESH_STATIC;
+  k_widths_max<<<64, 256, 0, st>>>(D.J0, N, D.S);
+  launch_recon<1>(K, D, tmp.Tr, grid_of(D.nr, 0), st, D.E0, D.M0, D.B0, D.J0);
   unsigned long long Abits = 0;
-  e = cudaMemcpyAsync(&Abits, &D.S->A[1], 8, cudaMemcpyDeviceToHost, st);
+  e = cudaGetLastError();
+  e = e ? e : cudaMemcpyAsync(&Abits, &D.S->A[0], 8, cudaMemcpyDeviceToHost, st);
   e = e ? e : cudaStreamSynchronize(st);
   if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
   double A;
   std::memcpy(&A, &Abits, 8);
   if (!(alpha > 0.0)) {
     std::vector<double> wh(N + 1);
-    cudaMemcpy(wh.data(), w, (N + 1) * sizeof(double), cudaMemcpyDefault);
+    e = cudaMemcpy(wh.data(), w, (N + 1) * sizeof(double), cudaMemcpyDefault);
+    if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
     double wb = 0.0;
     for (double v : wh) wb = std::max(wb, std::fabs(v));
     alpha = A + wb;
   }
   RhsOut ro{R3, R3 + N, R3 + 2 * N, alpha};
-  k_update<2, 1><<<gu, kUpdateThreads, 0, st>>>(K, D, D.E0, D.M0, D.B0, D.J0, ro);
+  launch_update<2, 1>(K, D, tmp.Tu, grid_of(D.nu, 0), st, D.E0, D.M0, D.B0, D.J0, ro);
   e = cudaGetLastError();
   e = e ? e : cudaMemcpyAsync(RE, ro.RE, cb, cudaMemcpyDefault, st);
   e = e ? e : cudaMemcpyAsync(RM, ro.RM, cb, cudaMemcpyDefault, st);
   e = e ? e : cudaMemcpyAsync(RB, ro.RB, cb, cudaMemcpyDefault, st);
+  if (flags) e = e ? e : cudaMemcpyAsync(flags, D.flags + 1, N, cudaMemcpyDefault, st);
   unsigned int bits = 0;
   e = e ? e : cudaMemcpyAsync(&bits, &D.S->status, sizeof(bits), cudaMemcpyDeviceToHost, st);
   e = e ? e : cudaStreamSynchronize(st);
   if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
-  if (flags) {
-    // Stage-2 recon does not store flags; recompute them through a stage-1 reconstruction.
-    S0.counter = 0;
-    S0.Jmin0 = 0x3ff0000000000000ull;
-    e = cudaMemcpyAsync(D.S, &S0, sizeof(S0), cudaMemcpyHostToDevice, st);
-    k_recon<1><<<gr, kReconThreads, 0, st>>>(K, D, D.E0, D.M0, D.B0, D.J0);
-    e = e ? e : cudaGetLastError();
-    e = e ? e : cudaMemcpyAsync(flags, D.flags + 1, N, cudaMemcpyDefault, st);
-    e = e ? e : cudaStreamSynchronize(st);
-    if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
-  }
   if (A_out) *A_out = A;
   if (status_bits) *status_bits = bits;
   return cleanup(SWALE_OK);
+}
+
+const char* swale_last_error(const swale_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void swale_destroy(swale_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_state(ctx);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
 }
 
 }  // extern "C"
@@ -1054,16 +898,18 @@ swale_status swale_rhs(swale_ctx* ctx, int64_t N, const double* E, const double*
 // Some callers cannot call cudaMalloc: code that runs inside another framework's memory
 // pool, or between the captures of a CUDA graph that must not grow device memory. For them
 // swale_rhs_noalloc evaluates the same right-hand side as swale_rhs with its scratch (the
-// edge values, detector classes and reduction scalars) in the fixed array below, which
-// every GPU that loads this library holds until the process exits.
+// edge values, shared reciprocals, detector classes and reduction scalars) in the fixed array
+// below, which every GPU that loads this library holds until the process exits.
 namespace {
 
 constexpr int64_t kNoAllocMaxCells = 65536;
 constexpr int kNoAllocMaxDevices = 64;
+constexpr int kNoAllocTile = 128;
 
 struct NoAllocScratch {
   double edges[10][kNoAllocMaxCells + 2];
   uint8_t flags[kNoAllocMaxCells + 2];
+  InstConst ic;
   DevScalars S;
 };
 
@@ -1074,14 +920,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocS
 void* g_noalloc_addr[kNoAllocMaxDevices];
 std::once_flag g_noalloc_once[kNoAllocMaxDevices];
 cudaError_t g_noalloc_err[kNoAllocMaxDevices];
-
-// Max of the widths into S->Jmax[0] (the global cell length of the indicators).
-__global__ void k_noalloc_maxJ(const double* __restrict__ J, int64_t N, DevScalars* S) {
-  double m = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    m = fmax(m, J[i]);
-  block_max_to(&S->Jmax[0], m);
-}
 
 bool on_device(const void* p) {
   cudaPointerAttributes a;
@@ -1132,36 +970,42 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   D.ipair = scr->edges[8];
   D.itri = scr->edges[9];
   D.flags = scr->flags;
+  D.IC = &scr->ic;
   D.S = &scr->S;
   D.w = const_cast<double*>(w);
+  D.nr = (int32_t)((N + 2 + kNoAllocTile - 1) / kNoAllocTile);
+  D.nu = (int32_t)((N + kNoAllocTile - 1) / kNoAllocTile);
   StepConst K;
   K.sc.g = cfg->g;
   K.sc.eps_weno = cfg->eps_weno;
   K.sc.eps_pp = cfg->eps_pp;
   K.sc.h_dry = cfg->h_dry;
   K.sc.beta_dx_global = cfg->beta_dx_global;
-  K.cfl = 1.0;
   K.t_end = 0.0;
   K.dt_fixed = 0.0;
   K.mesh_T = 1.0;
-  K.Wbar_profile = 0.0;
-  K.N = N;
+  K.gauss_wsum = 1.0;
   K.bc = cfg->bc;
   K.mesh = SWALE_MESH_STATIC;
   K.gauss_half = 0;
+  K.B = 1;
   // The scalars keep the previous call's contents: start them from zero (J^n minimum at 1 so
   // the stage-1 time-step arithmetic stays finite; its result is not used here).
+  InstConst ic0;
+  std::memset(&ic0, 0, sizeof(ic0));
+  ic0.N = N;
+  ic0.cfl = 1.0;
+  ic0.ntiles_r = D.nr;
   DevScalars S0;
   std::memset(&S0, 0, sizeof(S0));
   S0.Jmin0 = 0x3ff0000000000000ull;
-  cudaError_t e = cudaMemcpyAsync(&scr->S, &S0, sizeof(S0), cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyAsync(&scr->ic, &ic0, sizeof(InstConst), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&scr->S, &S0, sizeof(DevScalars), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return SWALE_ECUDA;
-  const unsigned gr = (unsigned)((N + 2 + kReconThreads - 1) / kReconThreads);
-  const unsigned gu = (unsigned)((N + kUpdateThreads - 1) / kUpdateThreads);
-  k_noalloc_maxJ<<<64, 256, 0, st>>>(J, N, &scr->S);
-  k_recon<1><<<gr, kReconThreads, 0, st>>>(K, D, E, M, B, J);
+  k_widths_max<<<64, 256, 0, st>>>(J, N, &scr->S);
+  k_recon<1, kNoAllocTile><<<(unsigned)D.nr, kNoAllocTile, 0, st>>>(K, D, E, M, B, J);
   RhsOut ro{RE, RM, RB, alpha};
-  k_update<2, 1><<<gu, kUpdateThreads, 0, st>>>(K, D, E, M, B, J, ro);
+  k_update<2, 1, kNoAllocTile><<<(unsigned)D.nu, kNoAllocTile, 0, st>>>(K, D, E, M, B, J, ro);
   e = cudaGetLastError();
   if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, scr->flags + 1, (size_t)N, cudaMemcpyDefault, st);
   if (e == cudaSuccess && A_out) {
@@ -1175,17 +1019,6 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
     return SWALE_ECUDA;
   }
   return SWALE_OK;
-}
-
-const char* swale_last_error(const swale_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
-
-void swale_destroy(swale_ctx* ctx) {
-  if (!ctx) return;
-  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  free_state(ctx);
-  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
-  delete ctx;
 }
 
 }  // extern "C"

@@ -1,0 +1,574 @@
+// Device side of the GB300 (sm_103a) FP64 solver for the well-balanced ALE-WENO hybrid scheme
+// (Zhang, Xia & Xu, arXiv 2208.06588): data layout and the stage kernels.
+//
+// One SSP-RK3 step (Eq. RK32D) is a fixed sequence of launches on one stream:
+//   k_prologue                 per-instance scalar resets
+//   [k_mesh_gauss]             fluid-driven node velocities
+//   k_recon<1>, k_update<1>    stage 1 on the mesh at t_n
+//   k_recon<2>, k_update<2>    stage 2 on the mesh at t_{n+1}
+//   k_recon<3>, k_update<3>    stage 3 on the mesh at t_{n+1/2}
+// Every launch serves all instances of a batch: blocks walk a work list of (instance, tile)
+// entries in grid-stride order (one pass when the grid has one block per tile, a persistent
+// loop when it is smaller). A single instance uses the implicit list t -> (0, t * T + first).
+// The reconstruction also reduces the per-instance global wave speed of Eq. alpha2D (warp
+// shuffle, shared memory, one atomicMax per tile on the order-preserving bit pattern of a
+// non-negative double); in stage 1 the last tile of each instance computes that instance's
+// dt, so dt, alpha and t never visit the host and steps replay as CUDA graphs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/swale.h"
+#include "swale_cell.cuh"
+
+namespace swale_dev {
+
+using swale::EdgeState;
+using swale::SchemeConst;
+
+constexpr int kMaxGaussHalf = 64;
+constexpr int kMeshThreads = 256;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// Per-instance device scalars. Maxima of non-negative doubles are kept as their bit patterns
+// (unsigned order equals numeric order for non-negative IEEE doubles).
+struct DevScalars {
+  double t, dt, sdiff, Wbar, alpha1;
+  unsigned long long A[3];           // max edge wave speed per stage
+  unsigned long long Jmax[3];        // max width of the stage meshes J^n, J^(1), J^(2)
+  unsigned long long Jmin0;          // min J^n
+  unsigned long long JmaxN, JminN;   // of J^{n+1}, accumulated by stage 3
+  unsigned long long Wabs, dWabs;    // fluid-driven motion: max |w|, max |w_{j+1} - w_j|
+  long long steps;
+  unsigned int status;
+  unsigned int counter;              // reconstruction tiles finished in stage 1
+  int done;
+  int clipped;
+};
+
+// Per-instance constants.
+struct InstConst {
+  int64_t N;           // cells
+  int64_t coff;        // first cell in the concatenated cell arrays (nodes: coff + i,
+                       // edge arrays: coff + 2 i)
+  double cfl;
+  double Wbar_profile; // (2 pi / T) max |P| of the prescribed motion
+  int32_t ntiles_r;    // reconstruction tiles of the instance
+  int32_t pad_;
+};
+
+struct Tile {
+  int32_t inst, c0;  // instance and first cell (reconstruction tiles start at cell -1)
+};
+
+// Constants of the whole launch.
+struct StepConst {
+  SchemeConst sc;
+  double t_end, dt_fixed, mesh_T;
+  double gauss_wsum;  // sum of the full Gaussian window, summed from -H to H
+  int32_t bc, mesh, gauss_half, B;
+};
+
+// Device arrays of a batch (concatenated over instances).
+struct DevState {
+  double *E0, *M0, *B0;        // q^n (updated in place by stage 3)
+  double *Ea, *Ma, *Ba;        // q^(1)
+  double *Eb, *Mb, *Bb;        // q^(2)
+  double *YE, *YM, *YB;        // running RK combination J q
+  double *J0, *J1, *J2;        // J^n, J^(1), J^(2)
+  double *x, *w, *P;           // nodes, node velocities, motion profile (N_i + 1 per instance)
+  // Edge arrays hold cells -1..N_i of each instance (N_i + 2 per instance).
+  double *eEL, *eER, *eBL, *eBR, *ehL, *ehR, *euL, *euR;
+  double *ipair, *itri;        // 1/(J_c + J_{c+1}) and 1/(J_{c-1} + J_c + J_{c+1}) of the stage mesh
+  uint8_t* flags;              // stage-1 classes, edge layout
+  InstConst* IC;
+  DevScalars* S;
+  const Tile *rtiles, *utiles, *mtiles;  // work lists (null: one instance, implicit tiles)
+  int32_t nr, nu, nm;                    // tiles in each list
+};
+
+__constant__ double c_gauss_w[2 * kMaxGaussHalf + 1];
+
+__device__ __forceinline__ int64_t ghost(int64_t i, int64_t N, int bc) {
+  if (bc == SWALE_BC_PERIODIC) {
+    i %= N;
+    return i < 0 ? i + N : i;
+  }
+  if (i < 0) return -1 - i;
+  if (i >= N) return 2 * N - 1 - i;
+  return i;
+}
+
+__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Block-wide max of a non-negative double, one atomicMax per block.
+__device__ __forceinline__ void block_max_to(unsigned long long* dst, double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    v = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) atomicMax(dst, dbits(v));
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void block_min_to(unsigned long long* dst, double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    v = lane < nw ? red[lane] : INFINITY;
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) atomicMin(dst, dbits(v));
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void block_or_status(unsigned int* dst, uint32_t st) {
+  st = __reduce_or_sync(0xffffffffu, st);
+  if ((threadIdx.x & 31) == 0 && st) atomicOr(dst, st);
+}
+
+// ------------------------------------------------------------------------------------
+// Per-step prologue, one thread per instance: stage maxima reset, J^{n+1} statistics become
+// those of J^n; an instance whose time reached t_end (t_end > 0) is marked done.
+// ------------------------------------------------------------------------------------
+__global__ void k_prologue(StepConst K, DevState D) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= K.B) return;
+  DevScalars* S = D.S + i;
+  if (K.t_end > 0.0 && S->t >= K.t_end) {
+    S->done = 1;
+    return;
+  }
+  S->done = 0;
+  S->clipped = 0;
+  S->Jmax[0] = S->JmaxN;
+  S->Jmin0 = S->JminN;
+  S->JmaxN = 0ull;
+  S->JminN = 0x7ff0000000000000ull;  // +inf
+  S->A[0] = S->A[1] = S->A[2] = 0ull;
+  S->Jmax[1] = S->Jmax[2] = 0ull;
+  S->Wabs = S->dWabs = 0ull;
+  S->counter = 0u;
+  if (K.mesh != SWALE_MESH_FLUID_GAUSS) S->Wbar = D.IC[i].Wbar_profile;
+}
+
+// ------------------------------------------------------------------------------------
+// Fluid-driven node velocity: raw_k = (u_{k-1} + u_k)/2 for k = 1..N-1 (u = hu/h, dry -> 0),
+// truncated renormalised Gaussian filter, w_0 = w_N = 0. A tile is kMeshThreads nodes; the
+// block stages the cell velocities, the raw node velocities and its filtered nodes in shared
+// memory (dynamic, 3 T + 4 H + 4 doubles).
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevState D) {
+  extern __shared__ double sh[];
+  const int H = K.gauss_half, T = kMeshThreads, tid = threadIdx.x;
+  const int nu = T + 2 * H + 2, nr = T + 2 * H + 1;
+  double* su = sh;         // cell velocities, cells [k0 - H - 1, k0 + T + H]
+  double* sraw = sh + nu;  // raw node velocities, nodes [k0 - H, k0 + T + H]
+  double* sw = sraw + nr;  // filtered velocities, nodes [k0, k0 + T]
+  for (int t = blockIdx.x; t < D.nm; t += gridDim.x) {
+    const Tile tl = D.mtiles ? D.mtiles[t] : Tile{0, t * T};
+    DevScalars* S = D.S + tl.inst;
+    if (S->done) continue;
+    const InstConst ic = D.IC[tl.inst];
+    const int64_t N = ic.N, k0 = tl.c0;
+    const double* E0 = D.E0 + ic.coff;
+    const double* M0 = D.M0 + ic.coff;
+    const double* B0 = D.B0 + ic.coff;
+    double* w = D.w + ic.coff + tl.inst;
+    __syncthreads();
+    for (int i = tid; i < nu; i += T) {
+      const int64_t c = k0 - H - 1 + i;
+      double u = 0.0;
+      if (c >= 0 && c < N) {
+        const double h = E0[c] - B0[c];
+        u = h > K.sc.h_dry ? M0[c] / h : 0.0;
+      }
+      su[i] = u;
+    }
+    __syncthreads();
+    for (int i = tid; i < nr; i += T) {
+      const int64_t k = k0 - H + i;
+      sraw[i] = (k >= 1 && k <= N - 1) ? 0.5 * (su[i] + su[i + 1]) : 0.0;
+    }
+    __syncthreads();
+    for (int i = tid; i <= T; i += T) {
+      const int64_t k = k0 + i;
+      double v = 0.0;
+      if (k >= 1 && k <= N - 1) {
+        double acc = 0.0;
+        if (k - H >= 1 && k + H <= N - 1) {
+          for (int m = -H; m <= H; ++m) acc += c_gauss_w[m + H] * sraw[i + m + H];
+          v = acc / K.gauss_wsum;
+        } else {
+          double wsum = 0.0;
+          for (int m = -H; m <= H; ++m) {
+            const int64_t q = k + m;
+            if (q < 1 || q > N - 1) continue;
+            acc += c_gauss_w[m + H] * sraw[i + m + H];
+            wsum += c_gauss_w[m + H];
+          }
+          v = acc / wsum;
+        }
+      }
+      sw[i] = v;
+    }
+    __syncthreads();
+    const int64_t k = k0 + tid;
+    double wa = 0.0, dwa = 0.0;
+    if (k <= N) {
+      w[k] = sw[tid];
+      wa = fabs(sw[tid]);
+      if (k < N) dwa = fabs(sw[tid + 1] - sw[tid]);
+    }
+    block_max_to(&S->Wabs, wa);
+    block_max_to(&S->dWabs, dwa);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Reconstruction + limiter of cells -1..N_i (rows a2-a7) for stage STAGE. A tile is T
+// consecutive cells; the block stages their 5-cell stencils (tile plus a 2-cell halo each
+// side) in shared memory, computes each pair's and each triple's reciprocal width and divided
+// differences once, then reconstructs one cell per thread. It stores the pair / triple
+// reciprocals for the update kernel of the same stage, reduces the wave speed, and in stage 1
+// the instance's last tile computes its dt (and the secant factor of the prescribed motion).
+// ------------------------------------------------------------------------------------
+template <int STAGE, int T>
+__global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
+                                             const double* __restrict__ Mg, const double* __restrict__ Bg,
+                                             const double* __restrict__ Jg) {
+  __shared__ double sJ[T + 4], sV[3][T + 4];    // cells c0-2 .. c0+T+1
+  __shared__ double sIP[T + 3], sD2[3][T + 3];  // pairs starting at those cells
+  __shared__ double sIT[T + 2], sD3[3][T + 2];  // triples centred at cells c0-1 .. c0+T
+  __shared__ bool last;
+  const int tid = threadIdx.x;
+  const bool refl = (K.bc == SWALE_BC_REFLECTIVE);
+  for (int t = blockIdx.x; t < D.nr; t += gridDim.x) {
+    const Tile tl = D.rtiles ? D.rtiles[t] : Tile{0, t * T - 1};
+    DevScalars* S = D.S + tl.inst;
+    if (S->done) continue;
+    const InstConst ic = D.IC[tl.inst];
+    const int64_t N = ic.N, c0 = tl.c0;
+    const double* E = Eg + ic.coff;
+    const double* M = Mg + ic.coff;
+    const double* B = Bg + ic.coff;
+    const double* J = Jg + ic.coff;
+    const int64_t eb = ic.coff + 2 * (int64_t)tl.inst;  // edge-array base of the instance
+    __syncthreads();
+    for (int i = tid; i < T + 4; i += T) {
+      const int64_t c = c0 - 2 + i;
+      double jv = 1.0, ev = 0.0, mv = 0.0, bv = 0.0;  // filler beyond the last ghost cell
+      if (c >= -3 && c <= N + 2) {
+        const int64_t s = ghost(c, N, K.bc);
+        jv = J[s];
+        ev = E[s];
+        bv = B[s];
+        mv = M[s];
+        if (refl && (c < 0 || c >= N)) mv = -mv;
+      }
+      sJ[i] = jv;
+      sV[0][i] = ev;
+      sV[1][i] = mv;
+      sV[2][i] = bv;
+    }
+    __syncthreads();
+    for (int i = tid; i < T + 3; i += T) {
+      const double ip = swale::pair_recip(sJ[i], sJ[i + 1]);
+      sIP[i] = ip;
+#pragma unroll
+      for (int v = 0; v < 3; ++v) sD2[v][i] = swale::pair_dd(sV[v][i], sV[v][i + 1], ip);
+    }
+    __syncthreads();
+    for (int i = tid; i < T + 2; i += T) {
+      const double it = swale::triple_recip(sJ[i], sJ[i + 1], sJ[i + 2]);
+      sIT[i] = it;
+#pragma unroll
+      for (int v = 0; v < 3; ++v) sD3[v][i] = swale::triple_dd(sD2[v][i], sD2[v][i + 1], it);
+    }
+    __syncthreads();
+    const int64_t c = c0 + tid;
+    double wave = 0.0;
+    uint32_t st = 0;
+    if (c <= N) {
+      double h[5], v0[3][3];
+      swale::StencilDD DD;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) h[k] = sJ[tid + k];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v0[v][a] = sV[v][tid + a];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) DD.D2[v][a] = sD2[v][tid + a];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) DD.D3[v][a] = sD3[v][tid + a];
+      }
+      const double dxmax = bitsd(S->Jmax[STAGE - 1]);
+      EdgeState o;
+      uint8_t flag;
+      double wl, wr;
+      swale::recon_cell(K.sc, h, v0, DD, dxmax, o, flag, wl, wr, st);
+      const int64_t idx = eb + c + 1;
+      D.eEL[idx] = o.EL;
+      D.eER[idx] = o.ER;
+      D.eBL[idx] = o.BL;
+      D.eBR[idx] = o.BR;
+      D.ehL[idx] = o.hL;
+      D.ehR[idx] = o.hR;
+      D.euL[idx] = o.uL;
+      D.euR[idx] = o.uR;
+      D.ipair[idx] = sIP[tid + 2];  // pair (c, c+1)
+      D.itri[idx] = sIT[tid + 1];   // triple centred at c
+      if (STAGE == 1) D.flags[idx] = flag;
+      // Edges that touch interfaces 0..N only.
+      if (c == -1) wave = wr;
+      else if (c == N) wave = wl;
+      else wave = fmax(wl, wr);
+      if (!(wave == wave)) st |= swale::ST_NONFINITE;
+    }
+    block_or_status(&S->status, st);
+    block_max_to(&S->A[STAGE - 1], wave);
+    if (STAGE == 1) {
+      if (tid == 0) {
+        __threadfence();
+        const unsigned int ticket = atomicAdd(&S->counter, 1u);
+        last = (ticket == (unsigned)ic.ntiles_r - 1u);
+      }
+      __syncthreads();
+      if (last && tid == 0) {
+        __threadfence();
+        const double A1 = bitsd(atomicAdd(&S->A[0], 0ull));
+        double Wbar = S->Wbar;
+        double dwmax = 0.0;
+        if (K.mesh == SWALE_MESH_FLUID_GAUSS) {
+          Wbar = bitsd(atomicAdd(&S->Wabs, 0ull));
+          dwmax = bitsd(atomicAdd(&S->dWabs, 0ull));
+          S->Wbar = Wbar;
+        }
+        const double alpha1 = A1 + Wbar;
+        const double tn = S->t;
+        double dt;
+        int clipped = 0;
+        if (K.dt_fixed > 0.0) {
+          dt = K.dt_fixed;
+        } else {
+          const double jmin = bitsd(S->Jmin0);
+          dt = ic.cfl * jmin / alpha1;
+          if (K.mesh == SWALE_MESH_FLUID_GAUSS && dwmax > 0.0) dt = fmin(dt, 0.5 * jmin / dwmax);
+        }
+        if (K.t_end > 0.0 && K.t_end - tn <= dt) {
+          dt = K.t_end - tn;
+          clipped = 1;
+        }
+        S->dt = dt;
+        S->alpha1 = alpha1;
+        S->clipped = clipped;
+        if (K.mesh == SWALE_MESH_PROFILE) {
+          const double s0 = sin(kTwoPi * tn / K.mesh_T);
+          const double s1 = sin(kTwoPi * (tn + dt) / K.mesh_T);
+          S->sdiff = (s1 - s0) / dt;
+        } else {
+          S->sdiff = 0.0;
+        }
+        S->counter = 0u;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Fluxes, source and the RK combination of stage STAGE for cells 0..N_i-1 (rows a1, a8, a9;
+// MODE 0), or the bare right-hand side of one instance (MODE 1, used by swale_rhs). A tile is
+// T consecutive cells: each of its interfaces' fluxes is computed once into shared memory;
+// the widths, their reciprocals and the depth / bottom averages of the tile plus one halo
+// cell each side are staged there too.
+// ------------------------------------------------------------------------------------
+struct RhsOut {
+  double *RE, *RM, *RB;
+  double alpha;
+};
+
+template <int STAGE, int MODE, int T>
+__global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const double* __restrict__ Eg,
+                                              const double* __restrict__ Mg, const double* __restrict__ Bg,
+                                              const double* __restrict__ Jsg, RhsOut ro) {
+  __shared__ double sF[4][T + 1], sW[T + 1];                      // interfaces / nodes j0 .. j0+T
+  __shared__ double sJ[T + 2], siJ[T + 2], sH[T + 2], sB[T + 2];  // cells j0-1 .. j0+T
+  const int tid = threadIdx.x;
+  (void)Mg;
+  for (int t = blockIdx.x; t < D.nu; t += gridDim.x) {
+    const Tile tl = D.utiles ? D.utiles[t] : Tile{0, t * T};
+    const int inst = tl.inst;
+    DevScalars* S = D.S + inst;
+    if (MODE == 0 && S->done) continue;
+    const InstConst ic = D.IC[inst];
+    const int64_t N = ic.N, j0 = tl.c0;
+    const int64_t cb = ic.coff, nb = ic.coff + inst, eb = ic.coff + 2 * (int64_t)inst;
+    const double* E = Eg + cb;
+    const double* B = Bg + cb;
+    const double* Js = Jsg + cb;
+    double alpha, dt = 0.0;
+    if (MODE == 1) {
+      alpha = ro.alpha;
+    } else {
+      alpha = (STAGE == 1) ? S->alpha1 : bitsd(S->A[STAGE - 1]) + S->Wbar;
+      dt = S->dt;
+    }
+    const bool fresh_w = (MODE == 0 && STAGE == 1 && K.mesh == SWALE_MESH_PROFILE);
+    const double sdiff = fresh_w ? S->sdiff : 0.0;
+    __syncthreads();
+    for (int i = tid; i <= T; i += T) {
+      const int64_t k = j0 + i;  // node / interface index
+      if (k <= N) {
+        double wk;
+        if (fresh_w) {
+          wk = D.P[nb + k] * sdiff;
+          if (i < T || k == N) D.w[nb + k] = wk;
+        } else if (MODE == 0 && K.mesh == SWALE_MESH_STATIC) {
+          wk = 0.0;
+        } else {
+          wk = D.w[nb + k];
+        }
+        sW[i] = wk;
+        // Interface k: left state = right edge of cell k-1 (edge index k), right state = left
+        // edge of cell k (edge index k+1).
+        const int64_t el = eb + k, er = eb + k + 1;
+        const swale::Flux F = swale::interface_flux(K.sc.g, alpha, wk, D.eER[el], D.eEL[er], D.eBR[el], D.eBL[er],
+                                                    D.ehR[el], D.ehL[er], D.euR[el], D.euL[er]);
+        sF[0][i] = F.FE;
+        sF[1][i] = F.FMm;
+        sF[2][i] = F.FMp;
+        sF[3][i] = F.FB;
+      }
+    }
+    for (int i = tid; i < T + 2; i += T) {
+      const int64_t c = j0 - 1 + i;
+      if (c >= -1 && c <= N) {
+        const int64_t s = ghost(c, N, K.bc);
+        const double jv = Js[s];
+        sJ[i] = jv;
+        siJ[i] = 1.0 / jv;
+        sH[i] = E[s] - B[s];
+        sB[i] = B[s];
+      }
+    }
+    __syncthreads();
+    const int64_t j = j0 + tid;
+    double jmaxa = 0.0, jmaxb = 0.0, jminb = INFINITY;
+    uint32_t st = 0;
+    if (j < N) {
+      const swale::Flux Fl = {sF[0][tid], sF[1][tid], sF[2][tid], sF[3][tid]};
+      const swale::Flux Fr = {sF[0][tid + 1], sF[1][tid + 1], sF[2][tid + 1], sF[3][tid + 1]};
+      const int64_t ic_e = eb + j + 1;  // edge-array index of cell j
+      const swale::SourceGeom sg = swale::source_geom(sJ[tid], sJ[tid + 1], siJ[tid], siJ[tid + 1], siJ[tid + 2],
+                                                      D.ipair[eb + j], D.ipair[eb + j + 1], D.itri[eb + j + 1]);
+      const double hd[5] = {sH[tid], sH[tid + 1], sH[tid + 2], D.ehL[ic_e], D.ehR[ic_e]};
+      const double bd[5] = {sB[tid], sB[tid + 1], sB[tid + 2], D.eBL[ic_e], D.eBR[ic_e]};
+      const double Sj = swale::source_cell(K.sc.g, hd, bd, sg);
+      const swale::CellRhs R = swale::cell_rhs(Fl, Fr, Sj);
+      const double RE = R.RE, RM = R.RM, RB = R.RB;
+      if (MODE == 1) {
+        ro.RE[j] = RE;
+        ro.RM[j] = RM;
+        ro.RB[j] = RB;
+      } else {
+        const int64_t g = cb + j;  // global cell index
+        const double wl = sW[tid], wr = sW[tid + 1];
+        const double J0 = D.J0[g];
+        const double dw = wr - wl;
+        if (STAGE == 1) {
+          const double J1 = J0 + dt * dw;
+          const double J2 = 0.75 * J0 + 0.25 * J1 + 0.25 * dt * dw;
+          D.J1[g] = J1;
+          D.J2[g] = J2;
+          jmaxa = J1;
+          jmaxb = J2;
+          if (!(J1 > 0.0) || !(J2 > 0.0)) st |= swale::ST_EMESH;
+          const double yE = J0 * D.E0[g] + dt * RE, yM = J0 * D.M0[g] + dt * RM, yB = J0 * D.B0[g] + dt * RB;
+          D.YE[g] = yE;
+          D.YM[g] = yM;
+          D.YB[g] = yB;
+          const double inv = 1.0 / J1;
+          D.Ea[g] = yE * inv;
+          D.Ma[g] = yM * inv;
+          D.Ba[g] = yB * inv;
+        } else if (STAGE == 2) {
+          const double yE = 0.75 * (J0 * D.E0[g]) + 0.25 * (D.YE[g] + dt * RE);
+          const double yM = 0.75 * (J0 * D.M0[g]) + 0.25 * (D.YM[g] + dt * RM);
+          const double yB = 0.75 * (J0 * D.B0[g]) + 0.25 * (D.YB[g] + dt * RB);
+          D.YE[g] = yE;
+          D.YM[g] = yM;
+          D.YB[g] = yB;
+          const double inv = 1.0 / D.J2[g];
+          D.Eb[g] = yE * inv;
+          D.Mb[g] = yM * inv;
+          D.Bb[g] = yB * inv;
+        } else {
+          const double J3 = (1.0 / 3.0) * J0 + (2.0 / 3.0) * D.J2[g] + (2.0 / 3.0) * dt * dw;
+          if (!(J3 > 0.0)) st |= swale::ST_EMESH;
+          const double yE = (1.0 / 3.0) * (J0 * D.E0[g]) + (2.0 / 3.0) * (D.YE[g] + dt * RE);
+          const double yM = (1.0 / 3.0) * (J0 * D.M0[g]) + (2.0 / 3.0) * (D.YM[g] + dt * RM);
+          const double yB = (1.0 / 3.0) * (J0 * D.B0[g]) + (2.0 / 3.0) * (D.YB[g] + dt * RB);
+          const double inv = 1.0 / J3;
+          const double En = yE * inv, Mn = yM * inv, Bn = yB * inv;
+          D.E0[g] = En;
+          D.M0[g] = Mn;
+          D.B0[g] = Bn;
+          D.J0[g] = J3;
+          jmaxb = J3;
+          jminb = J3;
+          D.x[nb + j] += dt * wl;
+          if (j == N - 1) D.x[nb + N] += dt * wr;
+          const double chk = En + Mn + Bn;
+          if (!(chk == chk) || fabs(chk) > 1.0e300) st |= swale::ST_NONFINITE;
+        }
+      }
+    }
+    if (MODE == 0) {
+      block_or_status(&S->status, st);
+      if (STAGE == 1) {
+        block_max_to(&S->Jmax[1], jmaxa);
+        block_max_to(&S->Jmax[2], jmaxb);
+      } else if (STAGE == 3) {
+        block_max_to(&S->JmaxN, jmaxb);
+        block_min_to(&S->JminN, jminb);
+        if (j0 == 0 && tid == 0) {
+          S->t = S->clipped ? K.t_end : S->t + S->dt;
+          S->steps += 1;
+        }
+      }
+    }
+  }
+}
+
+// Detector classes of every instance into a dense array (N_i bytes per instance, in order).
+__global__ void k_gather_flags(DevState D, int32_t B, uint8_t* out) {
+  for (int i = blockIdx.x; i < B; i += gridDim.x) {
+    const InstConst ic = D.IC[i];
+    const int64_t eb = ic.coff + 2 * (int64_t)i;
+    for (int64_t c = threadIdx.x; c < ic.N; c += blockDim.x) out[ic.coff + c] = D.flags[eb + c + 1];
+  }
+}
+
+// Max of the widths of one instance into S->Jmax[0] and S->Jmax[1] (used by swale_rhs and
+// swale_rhs_noalloc, which evaluate a stage outside a step).
+__global__ void k_widths_max(const double* __restrict__ J, int64_t N, DevScalars* S) {
+  double m = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, J[i]);
+  block_max_to(&S->Jmax[0], m);
+}
+
+}  // namespace swale_dev

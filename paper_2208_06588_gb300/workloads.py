@@ -171,3 +171,78 @@ def dam_break_dry(N=1 << 20):
                  lambda s: 0.0 * s, lambda s: 0.8 * np.exp(-5.0 * (s - 5.0) ** 2), breaks=(5.0, 8.0),
                  profile=np.zeros(N + 1), bc="transmissive", mesh="fluid_gauss", cfl=0.08,
                  gauss_sigma=8.0, gauss_half=24)
+
+
+# --------------------------------------------------------------------------------------
+# Batched workload: thousands of independent instances of uneven size
+# --------------------------------------------------------------------------------------
+@dataclass
+class Batch:
+    """Concatenated instances: cell offsets off[B+1], nodes of instance i at
+    x[off[i] + i : off[i+1] + i + 1], per-instance CFL."""
+    name: str
+    off: np.ndarray
+    x: np.ndarray
+    h: np.ndarray
+    hu: np.ndarray
+    b: np.ndarray
+    E: np.ndarray
+    profile: np.ndarray
+    cfl: np.ndarray
+    bc: str = "reflective"
+    mesh: str = "profile"
+    mesh_T: float = 1.0
+    g: float = G_PAPER
+    eps_weno: float = 1e-6
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def B(self):
+        return self.off.size - 1
+
+    def instance(self, i) -> Problem:
+        a, c = int(self.off[i]), int(self.off[i + 1])
+        xs = self.x[a + i:c + i + 1]
+        return Problem(name=f"{self.name}[{i}]", x=xs, h=self.h[a:c], hu=self.hu[a:c], b=self.b[a:c], E=self.E[a:c],
+                       profile=self.profile[a + i:c + i + 1], bc=self.bc, mesh=self.mesh, mesh_T=self.mesh_T,
+                       cfl=float(self.cfl[i]), g=self.g, eps_weno=self.eps_weno)
+
+
+def many_basins(B=4096, n_min=256, n_max=16384, seed=MASTER_SEED + 3, n_cells=None):
+    """B instances on [0,1], reflective, cell counts ~ U{n_min..n_max} (or all n_cells);
+    bottom = sum of 1-6 Gaussians (heights U[0,0.9], centres U[0,1], widths U[0.02,0.2]);
+    still water level 1 plus a Gaussian bump of amplitude U[1e-3,1e-1] (centre U[0.2,0.8],
+    width 0.05); h = max(0, eta - b); hu = 0; sine motion x = xi + A sin(2 pi xi) sin(2 pi t)
+    with A ~ U[0, 0.05]; CFL 0.6, or 0.08 for instances with a dry cell."""
+    root = np.random.SeedSequence(seed)
+    kids = root.spawn(B)
+    sizes = np.empty(B, dtype=np.int64)
+    parts = []
+    for i, ss in enumerate(kids):
+        rng = np.random.Generator(np.random.PCG64(ss))
+        n = int(n_cells) if n_cells is not None else int(rng.integers(n_min, n_max + 1))
+        ng = int(rng.integers(1, 7))
+        amp, cen, wid = rng.uniform(0, 0.9, ng), rng.uniform(0, 1, ng), rng.uniform(0.02, 0.2, ng)
+        eps, c0 = rng.uniform(1e-3, 1e-1), rng.uniform(0.2, 0.8)
+        A = rng.uniform(0.0, 0.05)
+
+        def bf(s, amp=amp, cen=cen, wid=wid):
+            return sum(a * np.exp(-(s - c) ** 2 / (2 * w * w)) for a, c, w in zip(amp, cen, wid))
+
+        def etaf(s, eps=eps, c0=c0):
+            return 1.0 + eps * np.exp(-(s - c0) ** 2 / (2 * 0.05 ** 2))
+
+        x = _uniform(0.0, 1.0, n)
+        b = cell_averages(bf, x)
+        h = cell_averages(lambda s: np.maximum(0.0, etaf(s) - bf(s)), x)
+        prof = _sine_profile(x, 0.0, 1.0, A)
+        sizes[i] = n
+        parts.append((x, h, b, prof, 0.08 if np.any(h <= 0.0) else 0.6))
+    off = np.zeros(B + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    x = np.concatenate([p[0] for p in parts])
+    h = np.concatenate([p[1] for p in parts])
+    b = np.concatenate([p[2] for p in parts])
+    prof = np.concatenate([p[3] for p in parts])
+    cfl = np.array([p[4] for p in parts])
+    return Batch(name="many_basins", off=off, x=x, h=h, hu=np.zeros_like(h), b=b, E=h + b, profile=prof, cfl=cfl)

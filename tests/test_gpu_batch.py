@@ -1,0 +1,131 @@
+"""Batched solver: many independent instances of uneven size advanced by the same launches.
+
+* A batch equals its instances run one at a time, bitwise (the per-cell arithmetic does not
+  depend on which block computes a cell, and every reduction is a max).
+* The launch shape (tile size, persistent grid) does not change results (bitwise).
+* Sampled instances agree with the CPU oracle (max-rel 1e-11 on wet instances, L1-rel 1e-9 on
+  instances with dry cells).
+* The autotuner restores the state it times from and reuses its cache.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_06588_gb300 import binding as B
+from paper_2208_06588_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2208_06588_gb300 import build
+    build.build()
+    B.lib()
+
+
+def cfg_of(bt):
+    return B.make_config(g=bt.g, eps_weno=bt.eps_weno, mesh_T=bt.mesh_T, bc=bt.bc, mesh=bt.mesh, cfl=0.6)
+
+
+def run_batch(bt, nsteps, tiles=None):
+    s = B.Solver(cfg_of(bt))
+    s.set_batch(bt)
+    if tiles:
+        B.swale_set_tiles(s.ctx, *tiles)
+    s.advance(nsteps)
+    out = s.batch_state()
+    out["bits"] = s.status()[0]
+    s.close()
+    return out
+
+
+def split(bt, arr, nodes=False, i=0):
+    a, c = int(bt.off[i]), int(bt.off[i + 1])
+    return arr[a + i:c + i + 1] if nodes else arr[a:c]
+
+
+def test_batch_equals_single_instances_bitwise():
+    bt = W.many_basins(B=12, n_min=200, n_max=3000, seed=101)
+    got = run_batch(bt, 12)
+    for i in range(bt.B):
+        pr = bt.instance(i)
+        s = B.Solver(B.make_config(g=pr.g, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, bc=pr.bc, mesh=pr.mesh,
+                                   cfl=pr.cfl))
+        s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+        s.advance(12)
+        g = s.state()
+        s.close()
+        assert np.array_equal(split(bt, got["eta"], i=i), g["eta"])
+        assert np.array_equal(split(bt, got["hu"], i=i), g["hu"])
+        assert np.array_equal(split(bt, got["b"], i=i), g["b"])
+        assert np.array_equal(split(bt, got["x"], nodes=True, i=i), g["x"])
+        assert got["t"][i] == g["t"]
+
+
+@pytest.mark.parametrize("tiles", [(64, 64, 0, 0), (256, 256, 0, 0), (128, 64, 300, 600), (64, 256, 152, 152)])
+def test_launch_shape_does_not_change_results(tiles):
+    bt = W.many_basins(B=20, n_min=100, n_max=2000, seed=102)
+    ref = run_batch(bt, 10)
+    got = run_batch(bt, 10, tiles)
+    for k in ("eta", "hu", "b", "x", "t", "dt"):
+        assert np.array_equal(ref[k], got[k]), k
+
+
+def test_batch_parity_against_oracle_sampled():
+    bt = W.many_basins(B=48, n_min=256, n_max=2048, seed=103)
+    nsteps = 15
+    got = run_batch(bt, nsteps)
+    rng = np.random.default_rng(7)
+    for i in sorted(rng.choice(bt.B, 10, replace=False)):
+        pr = bt.instance(i)
+        st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+        P = oracle.Params(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, bc=pr.bc, mesh=pr.mesh)
+        oracle.run(P, st, pr.profile, nsteps=nsteps)
+        dry = pr.cfl < 0.5
+        for name, ref in (("eta", st.E), ("hu", st.M), ("b", st.B)):
+            g = split(bt, got[name], i=i)
+            if dry:
+                err = np.sum(st.J * np.abs(g - ref)) / max(np.sum(st.J * np.abs(ref)), 1e-12)
+                assert err < 1e-9, (i, name, err)
+            else:
+                err = np.abs(g - ref).max() / max(np.abs(ref).max(), 1e-3)
+                assert err < 1e-11, (i, name, err)
+        assert abs(got["t"][i] - st.t) <= 1e-13 * st.t
+
+
+def test_full_size_batch_runs_and_samples_match(tmp_path):
+    """4096 instances, 256..16384 cells each (3.4e7 cells): two steps, then sampled instances
+    against the oracle."""
+    bt = W.many_basins(B=4096)
+    got = run_batch(bt, 2)
+    assert not (got["bits"] & (B.BIT_NONFINITE | B.BIT_EMESH))
+    for i in (0, 1234, 4095):
+        pr = bt.instance(i)
+        st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+        P = oracle.Params(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, bc=pr.bc, mesh=pr.mesh)
+        oracle.run(P, st, pr.profile, nsteps=2)
+        for name, ref in (("eta", st.E), ("hu", st.M), ("b", st.B)):
+            g = split(bt, got[name], i=i)
+            err = np.sum(st.J * np.abs(g - ref)) / max(np.sum(st.J * np.abs(ref)), 1e-12)
+            assert err < 1e-9, (i, name, err)
+
+
+def test_autotune_restores_state_and_uses_cache(tmp_path):
+    bt = W.many_basins(B=16, n_min=200, n_max=3000, seed=104)
+    cache = str(tmp_path / "tune.jsonl")
+    s = B.Solver(cfg_of(bt))
+    s.set_batch(bt)
+    s.advance(3)
+    before = s.batch_state()
+    tiles = B.swale_autotune(s.ctx, 2, cache)
+    after = s.batch_state()
+    for k in ("eta", "hu", "b", "x", "t"):
+        assert np.array_equal(before[k], after[k]), k
+    assert tiles[0] in (64, 128, 256) and tiles[1] in (64, 128, 256)
+    assert os.path.exists(cache) and open(cache).read().count("\n") == 1
+    assert B.swale_autotune(s.ctx, 2, cache) == tiles  # from the cache, no new line
+    assert open(cache).read().count("\n") == 1
+    s.close()
