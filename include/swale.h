@@ -199,6 +199,31 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
                                const double* M, const double* B, const double* J, const double* w, double alpha,
                                double* RE, double* RM, double* RB, double* A_out, uint8_t* flags);
 
+/* Stage viscosities alpha (Eq. alpha2D) of the next nsteps steps, 3 per step and instance, in
+ * a log the context owns: mode 1 records them, mode 2 replays `log` (nsteps * B * 3 values,
+ * host or device) instead of computing them, mode 0 turns the log off. Rows count from the
+ * context's step counter at the call. Replay is the convention under which the discrete
+ * adjoint differentiates (alpha held fixed), e.g. for finite-difference checks. */
+swale_status swale_alpha_log(swale_ctx* ctx, int32_t mode, int64_t nsteps, const double* log);
+swale_status swale_get_alpha_log(swale_ctx* ctx, double* log);
+
+/* Discrete adjoint of a gauge misfit over the next nsteps steps from the current state, for
+ * every instance i of the context:
+ *   J_i = sum_{n=1..nsteps} dt_n sum_{g<G} (h_g(q^n) - h_obs[n-1][i][g])^2,
+ * where h_g is the depth average of the cell that contains gauges_x[i*G + g] on the mesh at t_n.
+ * Outputs (host or device, any may be NULL): J[B], and the gradients of J with respect to the
+ * initial cell averages of eta, hu and b (Ntot values each; b varied with eta fixed).
+ * The gradient is that of the discrete scheme under the replay convention: dt and the stage
+ * viscosities alpha are those of the forward run, detector classes, limiter branches, dry-edge
+ * tests and max/min selections are frozen (a tie follows the first argument). Checkpoints of
+ * the state every ckpt_every steps; each segment is recomputed once with per-step snapshots and
+ * each step once more inside its reverse sweep. Memory: about 5 (nsteps/ckpt_every +
+ * ckpt_every) + 35 doubles per cell. The mesh must be prescribed (static or profile motion)
+ * and t_end = 0. On return the context holds the state after the nsteps steps.
+ * Errors: SWALE_EINVAL, SWALE_ENOMEM, SWALE_ECUDA, and the status errors of swale_advance. */
+swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, int32_t G, const double* gauges_x,
+                           const double* h_obs, double* J, double* dJ_deta0, double* dJ_dhu0, double* dJ_db0);
+
 /* Message of the last error of this context ("" if none). Never NULL. */
 const char* swale_last_error(const swale_ctx* ctx);
 

@@ -69,13 +69,17 @@ def lib():
         L.swale_set_tiles.argtypes = [vp, i32, i32, i32, i32]
         L.swale_get_tiles.argtypes = [vp, vp]
         L.swale_autotune.argtypes = [vp, i32, ctypes.c_char_p, vp]
+        L.swale_alpha_log.argtypes = [vp, i32, i64, vp]
+        L.swale_get_alpha_log.argtypes = [vp, vp]
+        L.swale_adjoint.argtypes = [vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
         L.swale_rhs_noalloc.argtypes = [P(SwaleConfig), vp, i64, vp, vp, vp, vp, vp, d, vp, vp, vp, P(d), vp]
         L.swale_set_timing.argtypes = [vp, i32]
         L.swale_get_timing.argtypes = [vp, vp, vp]
         for name in ("swale_create", "swale_set_problem", "swale_step", "swale_advance", "swale_get_state",
                      "swale_get_flags", "swale_get_status", "swale_rhs", "swale_enqueue", "swale_set_timing",
                      "swale_get_timing", "swale_rhs_noalloc", "swale_batch_set_problem", "swale_batch_get_state",
-                     "swale_set_tiles", "swale_get_tiles", "swale_autotune"):
+                     "swale_set_tiles", "swale_get_tiles", "swale_autotune", "swale_alpha_log",
+                     "swale_get_alpha_log", "swale_adjoint"):
             getattr(L, name).restype = ctypes.c_int
         L.swale_last_error.argtypes = [vp]
         L.swale_last_error.restype = ctypes.c_char_p
@@ -150,6 +154,19 @@ def swale_autotune(ctx, steps=3, cache_path=None):
     cp = cache_path.encode() if cache_path else None
     _check(ctx, lib().swale_autotune(ctx, int(steps), cp, t.ctypes.data))
     return tuple(int(v) for v in t)
+
+
+def swale_alpha_log(ctx, mode, nsteps=0, log=None):
+    _check(ctx, lib().swale_alpha_log(ctx, int(mode), int(nsteps), ptr(log)))
+
+
+def swale_get_alpha_log(ctx, log):
+    _check(ctx, lib().swale_get_alpha_log(ctx, ptr(log)))
+
+
+def swale_adjoint(ctx, nsteps, ckpt_every, G, gauges_x, h_obs, J=None, dJ_deta0=None, dJ_dhu0=None, dJ_db0=None):
+    _check(ctx, lib().swale_adjoint(ctx, int(nsteps), int(ckpt_every), int(G), ptr(gauges_x), ptr(h_obs), ptr(J),
+                                    ptr(dJ_deta0), ptr(dJ_dhu0), ptr(dJ_db0)))
 
 
 def swale_enqueue(ctx, nsteps):

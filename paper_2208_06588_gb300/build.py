@@ -10,8 +10,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libswale.so")
 SOURCES = [os.path.join(CSRC, "swale.cu")]
-HEADERS = [os.path.join(CSRC, "swale_cell.cuh"), os.path.join(CSRC, "swale_kernels.cuh"),
-           os.path.join(ROOT, "include", "swale.h")]
+HEADERS = [os.path.join(CSRC, f) for f in ("swale_cell.cuh", "swale_kernels.cuh", "swale_adjoint.cuh",
+                                             "swale_adjoint_kernels.cuh")] + [os.path.join(ROOT, "include", "swale.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

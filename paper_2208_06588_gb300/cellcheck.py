@@ -1,0 +1,85 @@
+"""Host builds of the per-cell arithmetic for checking the hand-written adjoint.
+
+csrc/celltest_tangent.cpp compiles swale_cell.cuh on a forward-mode dual scalar (tangents);
+csrc/celltest_adjoint.cpp compiles the reverse sweeps of swale_adjoint.cuh. Both are linked
+into libswale_cellcheck.so; tests compare <ob, T u> with <T^T ob, u> per function.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_C = os.path.join(_HERE, "csrc")
+_SRC = [os.path.join(_C, f) for f in ("celltest_tangent.cpp", "celltest_adjoint.cpp")]
+_DEPS = _SRC + [os.path.join(_C, f) for f in ("swale_cell.cuh", "swale_adjoint.cuh")]
+_LIB = os.path.join(_HERE, "libswale_cellcheck.so")
+_lib = None
+
+
+def build(force=False):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(p) for p in _DEPS):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-o", tmp, *_SRC], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB)
+        _lib.ct_recon_tangent.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def recon_tangent(h, v0, D2, D3, tv0, tD2, tD3, prm):
+    val, tan = np.zeros(8), np.zeros(8)
+    args = [f64(x) for x in (h, v0, D2, D3, tv0, tD2, tD3, prm)]
+    flag = lib().ct_recon_tangent(*map(_p, args), _p(val), _p(tan))
+    return val, tan, flag
+
+
+def recon_adjoint(h, v0, D2, D3, prm, ob):
+    v0b, D2b, D3b = np.zeros(9), np.zeros(12), np.zeros(9)
+    args = [f64(x) for x in (h, v0, D2, D3, prm, ob)]
+    lib().ct_recon_adjoint(*map(_p, args), _p(v0b), _p(D2b), _p(D3b))
+    return v0b, D2b, D3b
+
+
+def flux_tangent(e, te, prm):
+    F, tF = np.zeros(4), np.zeros(4)
+    lib().ct_flux_tangent(*map(_p, (f64(e), f64(te), f64(prm))), _p(F), _p(tF))
+    return F, tF
+
+
+def flux_adjoint(e, prm, Fb):
+    eb = np.zeros(8)
+    lib().ct_flux_adjoint(*map(_p, (f64(e), f64(prm), f64(Fb))), _p(eb))
+    return eb
+
+
+def source_tangent(hd, bd, thd, tbd, geom, g):
+    S, tS = ctypes.c_double(0), ctypes.c_double(0)
+    lib().ct_source_tangent(*map(_p, (f64(hd), f64(bd), f64(thd), f64(tbd), f64(geom))), ctypes.c_double(g),
+                            ctypes.byref(S), ctypes.byref(tS))
+    return S.value, tS.value
+
+
+def source_adjoint(hd, bd, geom, g, Sb):
+    hdb, bdb = np.zeros(5), np.zeros(5)
+    lib().ct_source_adjoint(*map(_p, (f64(hd), f64(bd), f64(geom))), ctypes.c_double(g), ctypes.c_double(Sb),
+                            _p(hdb), _p(bdb))
+    return hdb, bdb

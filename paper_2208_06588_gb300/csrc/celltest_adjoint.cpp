@@ -1,0 +1,46 @@
+// Host build of the hand-written reverse sweeps (swale_adjoint.cuh) for the dot-product checks
+// against the dual-number tangents of celltest_tangent.cpp. Test tooling.
+#include <cmath>
+#include <cstdint>
+
+#include "swale_adjoint.cuh"
+
+extern "C" {
+
+// ob[8] adjoints of (EL, ER, BL, BR, hL, hR, uL, uR) -> v0b[9], D2b[12], D3b[9].
+void ct_recon_adjoint(const double* h, const double* v0, const double* D2, const double* D3, const double* prm,
+                      const double* ob, double* v0b, double* D2b, double* D3b) {
+  swale::SchemeConst P{prm[0], prm[1], prm[2], prm[3], 1};
+  double vv[3][3];
+  swale::StencilDD DD, DDb;
+  for (int v = 0; v < 3; ++v) {
+    for (int a = 0; a < 3; ++a) vv[v][a] = v0[v * 3 + a];
+    for (int a = 0; a < 4; ++a) DD.D2[v][a] = D2[v * 4 + a];
+    for (int a = 0; a < 3; ++a) DD.D3[v][a] = D3[v * 3 + a];
+  }
+  swale::EdgeAdj a{ob[0], ob[1], ob[2], ob[3], ob[4], ob[5], ob[6], ob[7]};
+  double vb[3][3];
+  swale::recon_cell_rev(P, h, vv, DD, prm[4], a, vb, DDb);
+  for (int v = 0; v < 3; ++v) {
+    for (int k = 0; k < 3; ++k) v0b[v * 3 + k] = vb[v][k];
+    for (int k = 0; k < 4; ++k) D2b[v * 4 + k] = DDb.D2[v][k];
+    for (int k = 0; k < 3; ++k) D3b[v * 3 + k] = DDb.D3[v][k];
+  }
+}
+
+void ct_flux_adjoint(const double* e, const double* prm, const double* Fb, double* eb) {
+  swale::Flux f{Fb[0], Fb[1], Fb[2], Fb[3]};
+  const swale::EdgeAdj a = swale::interface_flux_rev(prm[0], prm[1], prm[2], e[0], e[1], e[2], e[3], e[4], e[5], e[6],
+                                                     e[7], f);
+  const double o[8] = {a.EL, a.ER, a.BL, a.BR, a.hL, a.hR, a.uL, a.uR};
+  for (int k = 0; k < 8; ++k) eb[k] = o[k];
+}
+
+void ct_source_adjoint(const double* hd, const double* bd, const double* geom, double g, double Sb, double* hdb,
+                       double* bdb) {
+  swale::SourceGeom sg{geom[0], geom[1], geom[2], geom[3], geom[4], geom[5]};
+  for (int k = 0; k < 5; ++k) hdb[k] = bdb[k] = 0.0;
+  swale::source_cell_rev(g, hd, bd, sg, Sb, hdb, bdb);
+}
+
+}  // extern "C"

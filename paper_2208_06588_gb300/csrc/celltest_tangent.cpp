@@ -1,0 +1,93 @@
+// Host build of the per-cell arithmetic on a forward-mode dual scalar: tangents of
+// recon_cell, interface_flux and source_cell for the dot-product checks of their hand-written
+// reverse sweeps (swale_adjoint.cuh). Test tooling.
+#include <cmath>
+#include <cstdint>
+
+namespace dt {
+struct D {
+  double v, d;
+  D(double a = 0.0) : v(a), d(0.0) {}
+  D(double a, double b) : v(a), d(b) {}
+};
+inline D operator+(D a, D b) { return D(a.v + b.v, a.d + b.d); }
+inline D operator-(D a, D b) { return D(a.v - b.v, a.d - b.d); }
+inline D operator-(D a) { return D(-a.v, -a.d); }
+inline D operator*(D a, D b) { return D(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline D operator/(D a, D b) {
+  const double q = a.v / b.v;
+  return D(q, (a.d - q * b.d) / b.v);
+}
+inline D& operator+=(D& a, D b) { a = a + b; return a; }
+inline bool operator<(D a, D b) { return a.v < b.v; }
+inline bool operator>(D a, D b) { return a.v > b.v; }
+inline bool operator<=(D a, D b) { return a.v <= b.v; }
+inline bool operator>=(D a, D b) { return a.v >= b.v; }
+inline bool operator==(D a, D b) { return a.v == b.v; }
+inline D swale_sqrt(D a) {
+  const double s = std::sqrt(a.v);
+  return D(s, s > 0 ? a.d / (2.0 * s) : 0.0);
+}
+}  // namespace dt
+
+#define SWALE_REAL dt::D
+#include "swale_cell.cuh"
+
+using dt::D;
+
+extern "C" {
+
+// in: h[5], v0[9], D2[12], D3[9]; tangents tv0[9], tD2[12], tD3[9]; prm = {g, eps, eps_pp, h_dry, dxmax}.
+// out: edge state values [8] and tangents [8] (EL, ER, BL, BR, hL, hR, uL, uR), flag.
+int ct_recon_tangent(const double* h, const double* v0, const double* D2, const double* D3, const double* tv0,
+                     const double* tD2, const double* tD3, const double* prm, double* val, double* tan) {
+  swale::SchemeConst P{prm[0], prm[1], prm[2], prm[3], 1};
+  D hh[5], vv[3][3];
+  swale::StencilDD DD;
+  for (int k = 0; k < 5; ++k) hh[k] = D(h[k]);
+  for (int v = 0; v < 3; ++v) {
+    for (int a = 0; a < 3; ++a) vv[v][a] = D(v0[v * 3 + a], tv0[v * 3 + a]);
+    for (int a = 0; a < 4; ++a) DD.D2[v][a] = D(D2[v * 4 + a], tD2[v * 4 + a]);
+    for (int a = 0; a < 3; ++a) DD.D3[v][a] = D(D3[v * 3 + a], tD3[v * 3 + a]);
+  }
+  swale::EdgeState o;
+  uint8_t flag;
+  D wl, wr;
+  uint32_t st = 0;
+  swale::recon_cell(P, hh, vv, DD, D(prm[4]), o, flag, wl, wr, st);
+  const D outs[8] = {o.EL, o.ER, o.BL, o.BR, o.hL, o.hR, o.uL, o.uR};
+  for (int k = 0; k < 8; ++k) {
+    val[k] = outs[k].v;
+    tan[k] = outs[k].d;
+  }
+  return flag;
+}
+
+// in: e[8] = (EL, ER, BL, BR, hL, hR, uL, uR), te[8]; prm = {g, alpha, w}. out: F[4], tF[4].
+void ct_flux_tangent(const double* e, const double* te, const double* prm, double* F, double* tF) {
+  D x[8];
+  for (int k = 0; k < 8; ++k) x[k] = D(e[k], te[k]);
+  const swale::Flux f = swale::interface_flux(D(prm[0]), D(prm[1]), D(prm[2]), x[0], x[1], x[2], x[3], x[4], x[5],
+                                              x[6], x[7]);
+  const D o[4] = {f.FE, f.FMm, f.FMp, f.FB};
+  for (int k = 0; k < 4; ++k) {
+    F[k] = o[k].v;
+    tF[k] = o[k].d;
+  }
+}
+
+// in: hd[5], bd[5], thd[5], tbd[5]; geom[6] = (rm, irm, irp, i1m, i1p, i1mp); g. out: S, tS.
+void ct_source_tangent(const double* hd, const double* bd, const double* thd, const double* tbd, const double* geom,
+                       double g, double* S, double* tS) {
+  D a[5], b[5];
+  for (int k = 0; k < 5; ++k) {
+    a[k] = D(hd[k], thd[k]);
+    b[k] = D(bd[k], tbd[k]);
+  }
+  swale::SourceGeom sg{D(geom[0]), D(geom[1]), D(geom[2]), D(geom[3]), D(geom[4]), D(geom[5])};
+  const D s = swale::source_cell(D(g), a, b, sg);
+  *S = s.v;
+  *tS = s.d;
+}
+
+}  // extern "C"

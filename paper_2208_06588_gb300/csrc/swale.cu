@@ -15,6 +15,7 @@
 
 #include "../../include/swale.h"
 #include "swale_kernels.cuh"
+#include "swale_adjoint_kernels.cuh"
 
 using namespace swale_dev;
 
@@ -39,6 +40,10 @@ struct swale_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_family;
   size_t ev_used = 0;
+  // Stage-viscosity log (swale_alpha_log): device array of 3 values per step and instance.
+  double* alpha_log = nullptr;
+  int64_t alpha_cap = 0, alpha_base = 0;
+  int32_t alpha_mode = 0;
 };
 
 namespace {
@@ -99,6 +104,10 @@ StepConst step_const(const swale_ctx* ctx) {
   K.mesh = ctx->cfg.mesh;
   K.gauss_half = ctx->cfg.gauss_half;
   K.B = (int32_t)ctx->B;
+  K.alpha_log = ctx->alpha_log;
+  K.alpha_cap = ctx->alpha_cap;
+  K.alpha_base = ctx->alpha_base;
+  K.alpha_mode = ctx->alpha_mode;
   return K;
 }
 
@@ -115,9 +124,17 @@ void free_tiles(swale_ctx* ctx) {
   ctx->D.rtiles = ctx->D.utiles = ctx->D.mtiles = nullptr;
 }
 
+void free_alpha_log(swale_ctx* ctx) {
+  if (ctx->alpha_log) cudaFree(ctx->alpha_log);
+  ctx->alpha_log = nullptr;
+  ctx->alpha_cap = 0;
+  ctx->alpha_mode = 0;
+}
+
 void free_state(swale_ctx* ctx) {
   drop_graph(ctx);
   free_tiles(ctx);
+  free_alpha_log(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   ctx->D = DevState{};
@@ -893,6 +910,267 @@ void swale_destroy(swale_ctx* ctx) {
 }  // extern "C"
 
 // ======================================================================================
+// Stage-viscosity log and the discrete adjoint
+// ======================================================================================
+namespace {
+
+long long device_steps(swale_ctx* ctx) {
+  long long s = 0;
+  cudaMemcpyAsync(&s, &ctx->D.S->steps, sizeof(s), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  return s;
+}
+
+template <int STAGE>
+void launch_adj_stage(swale_ctx* ctx, const StepConst& K, const AdjState& A, const double* E, const double* M,
+                      const double* B, const double* J) {
+  const DevState& D = ctx->D;
+  cudaStream_t s = ctx->stream;
+  const unsigned gu = grid_of(D.nu, ctx->grid_u), gr = grid_of(D.nr, ctx->grid_r);
+  const int Tu = ctx->Tu, Tr = ctx->Tr;
+  if (Tu == 64) {
+    k_adj_flux<STAGE, 64><<<gu, 64, 0, s>>>(K, D, A);
+    k_adj_source<STAGE, 64><<<gu, 64, 0, s>>>(K, D, A, E, B, J);
+  } else if (Tu == 256) {
+    k_adj_flux<STAGE, 256><<<gu, 256, 0, s>>>(K, D, A);
+    k_adj_source<STAGE, 256><<<gu, 256, 0, s>>>(K, D, A, E, B, J);
+  } else {
+    k_adj_flux<STAGE, 128><<<gu, 128, 0, s>>>(K, D, A);
+    k_adj_source<STAGE, 128><<<gu, 128, 0, s>>>(K, D, A, E, B, J);
+  }
+  if (Tr == 64) k_adj_recon<STAGE, 64><<<gr, 64, 0, s>>>(K, D, A, E, M, B, J);
+  else if (Tr == 256) k_adj_recon<STAGE, 256><<<gr, 256, 0, s>>>(K, D, A, E, M, B, J);
+  else k_adj_recon<STAGE, 128><<<gr, 128, 0, s>>>(K, D, A, E, M, B, J);
+}
+
+template <int PH>
+void launch_adj_rk(swale_ctx* ctx, const AdjState& A) {
+  const DevState& D = ctx->D;
+  const unsigned gu = grid_of(D.nu, ctx->grid_u);
+  if (ctx->Tu == 64) k_adj_rk<PH, 64><<<gu, 64, 0, ctx->stream>>>(D, A);
+  else if (ctx->Tu == 256) k_adj_rk<PH, 256><<<gu, 256, 0, ctx->stream>>>(D, A);
+  else k_adj_rk<PH, 128><<<gu, 128, 0, ctx->stream>>>(D, A);
+}
+
+template <int STAGE>
+void launch_recon_replay(swale_ctx* ctx, const StepConst& K, const double* E, const double* M, const double* B,
+                         const double* J) {
+  const DevState& D = ctx->D;
+  const unsigned gr = grid_of(D.nr, ctx->grid_r);
+  if (ctx->Tr == 64) k_recon<STAGE, 64, 1><<<gr, 64, 0, ctx->stream>>>(K, D, E, M, B, J);
+  else if (ctx->Tr == 256) k_recon<STAGE, 256, 1><<<gr, 256, 0, ctx->stream>>>(K, D, E, M, B, J);
+  else k_recon<STAGE, 128, 1><<<gr, 128, 0, ctx->stream>>>(K, D, E, M, B, J);
+}
+
+// Copies of the evolving state (q^n, J^n, nodes, per-instance scalars).
+struct StateCopy {
+  double *E, *M, *B, *J, *x;
+  DevScalars* S;
+};
+
+}  // namespace
+
+extern "C" {
+
+swale_status swale_alpha_log(swale_ctx* ctx, int32_t mode, int64_t nsteps, const double* log) {
+  if (!ctx) return SWALE_EINVAL;
+  if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  if (mode < 0 || mode > 2 || (mode != 0 && nsteps < 1)) return fail(ctx, SWALE_EINVAL, "bad mode or nsteps");
+  if (mode == 2 && !log) return fail(ctx, SWALE_EINVAL, "replay needs a log");
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  drop_graph(ctx);
+  free_alpha_log(ctx);
+  if (mode == 0) return SWALE_OK;
+  const size_t n = (size_t)nsteps * ctx->B * 3;
+  void* q = nullptr;
+  if (cudaMalloc(&q, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, SWALE_ENOMEM, "alpha log");
+  }
+  ctx->alpha_log = (double*)q;
+  ctx->alpha_cap = nsteps;
+  ctx->alpha_base = device_steps(ctx);
+  ctx->alpha_mode = mode;
+  if (mode == 2) SW_CUDA(ctx, cudaMemcpyAsync(ctx->alpha_log, log, n * sizeof(double), cudaMemcpyDefault, ctx->stream));
+  else SW_CUDA(ctx, cudaMemsetAsync(ctx->alpha_log, 0, n * sizeof(double), ctx->stream));
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SWALE_OK;
+}
+
+swale_status swale_get_alpha_log(swale_ctx* ctx, double* log) {
+  if (!ctx || !log) return SWALE_EINVAL;
+  if (!ctx->alpha_log) return fail(ctx, SWALE_EINVAL, "no alpha log");
+  SW_CUDA(ctx, cudaMemcpyAsync(log, ctx->alpha_log, (size_t)ctx->alpha_cap * ctx->B * 3 * sizeof(double),
+                               cudaMemcpyDefault, ctx->stream));
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SWALE_OK;
+}
+
+swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, int32_t G, const double* gauges_x,
+                           const double* h_obs, double* J, double* dJ_deta0, double* dJ_dhu0, double* dJ_db0) {
+  if (!ctx) return SWALE_EINVAL;
+  if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  if (nsteps < 1 || ckpt_every < 1 || G < 1 || !gauges_x || !h_obs)
+    return fail(ctx, SWALE_EINVAL, "nsteps, ckpt_every, G >= 1 and gauges, observations required");
+  if (ctx->cfg.mesh == SWALE_MESH_FLUID_GAUSS)
+    return fail(ctx, SWALE_EINVAL, "the adjoint needs a prescribed mesh (static or profile motion)");
+  if (ctx->cfg.t_end > 0.0) return fail(ctx, SWALE_EINVAL, "the adjoint runs a fixed number of steps: t_end = 0");
+  const int64_t B = ctx->B, Nt = ctx->Ntot, NN = Nt + B, NE = Nt + 2 * B;
+  const int64_t C = std::min(ckpt_every, nsteps), nseg = (nsteps + C - 1) / C;
+  cudaStream_t st = ctx->stream;
+  std::vector<void*> mem;
+  swale_status s = SWALE_OK;
+  auto alloc_copy = [&](StateCopy& c) {
+    if (!s) s = dalloc(ctx, mem, &c.E, (size_t)Nt);
+    if (!s) s = dalloc(ctx, mem, &c.M, (size_t)Nt);
+    if (!s) s = dalloc(ctx, mem, &c.B, (size_t)Nt);
+    if (!s) s = dalloc(ctx, mem, &c.J, (size_t)Nt);
+    if (!s) s = dalloc(ctx, mem, &c.x, (size_t)NN);
+    if (!s) s = dalloc(ctx, mem, &c.S, (size_t)B);
+  };
+  auto release = [&](swale_status r) {
+    cudaStreamSynchronize(st);
+    for (void* p : mem) cudaFree(p);
+    return r;
+  };
+  AdjState A{};
+  double** cellbufs[] = {&A.lE, &A.lM, &A.lB, &A.yE, &A.yM, &A.yB, &A.pE, &A.pM, &A.pB,
+                         &A.aE, &A.aM, &A.aB, &A.rE, &A.rM, &A.rB};
+  for (double** p : cellbufs)
+    if (!s) s = dalloc(ctx, mem, p, (size_t)Nt);
+  for (int k = 0; k < 8 && !s; ++k) s = dalloc(ctx, mem, &A.ab[k], (size_t)NE);
+  std::vector<StateCopy> ckpt(nseg), seg(C);
+  StateCopy fin, snap;
+  for (auto& c : ckpt) alloc_copy(c);
+  for (auto& c : seg) alloc_copy(c);
+  alloc_copy(fin);
+  alloc_copy(snap);
+  double *gx = nullptr, *obs = nullptr, *Jacc = nullptr, *alog = nullptr;
+  if (!s) s = dalloc(ctx, mem, &gx, (size_t)B * G);
+  if (!s) s = dalloc(ctx, mem, &obs, (size_t)nsteps * B * G);
+  if (!s) s = dalloc(ctx, mem, &Jacc, (size_t)B);
+  if (!s) s = dalloc(ctx, mem, &alog, (size_t)nsteps * B * 3);
+  if (s) return release(s);
+  A.sE = snap.E;
+  A.sM = snap.M;
+  A.sB = snap.B;
+  A.sJ = snap.J;
+  cudaError_t e = cudaSuccess;
+  e = e ? e : cudaMemcpyAsync(gx, gauges_x, (size_t)B * G * sizeof(double), cudaMemcpyDefault, st);
+  e = e ? e : cudaMemcpyAsync(obs, h_obs, (size_t)nsteps * B * G * sizeof(double), cudaMemcpyDefault, st);
+  e = e ? e : cudaMemsetAsync(Jacc, 0, B * sizeof(double), st);
+  e = e ? e : cudaMemsetAsync(A.aE, 0, Nt * sizeof(double), st);
+  e = e ? e : cudaMemsetAsync(A.aM, 0, Nt * sizeof(double), st);
+  e = e ? e : cudaMemsetAsync(A.aB, 0, Nt * sizeof(double), st);
+  e = e ? e : cudaMemsetAsync(A.lE, 0, Nt * sizeof(double), st);
+  e = e ? e : cudaMemsetAsync(A.lM, 0, Nt * sizeof(double), st);
+  e = e ? e : cudaMemsetAsync(A.lB, 0, Nt * sizeof(double), st);
+  if (e) return release(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
+  DevState& D = ctx->D;
+  auto save = [&](StateCopy& c) {
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    cudaError_t r = cudaMemcpyAsync(c.E, D.E0, Nt * sizeof(double), k, st);
+    r = r ? r : cudaMemcpyAsync(c.M, D.M0, Nt * sizeof(double), k, st);
+    r = r ? r : cudaMemcpyAsync(c.B, D.B0, Nt * sizeof(double), k, st);
+    r = r ? r : cudaMemcpyAsync(c.J, D.J0, Nt * sizeof(double), k, st);
+    r = r ? r : cudaMemcpyAsync(c.x, D.x, NN * sizeof(double), k, st);
+    r = r ? r : cudaMemcpyAsync(c.S, D.S, B * sizeof(DevScalars), k, st);
+    return r;
+  };
+  auto load = [&](const StateCopy& c) {
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    cudaError_t r = cudaMemcpyAsync(D.E0, c.E, Nt * sizeof(double), k, st);
+    r = r ? r : cudaMemcpyAsync(D.M0, c.M, Nt * sizeof(double), k, st);
+    r = r ? r : cudaMemcpyAsync(D.B0, c.B, Nt * sizeof(double), k, st);
+    r = r ? r : cudaMemcpyAsync(D.J0, c.J, Nt * sizeof(double), k, st);
+    r = r ? r : cudaMemcpyAsync(D.x, c.x, NN * sizeof(double), k, st);
+    r = r ? r : cudaMemcpyAsync(D.S, c.S, B * sizeof(DevScalars), k, st);
+    return r;
+  };
+  // The forward records the stage viscosities; every recomputation replays them.
+  double* old_log = ctx->alpha_log;
+  const int64_t old_cap = ctx->alpha_cap, old_base = ctx->alpha_base;
+  const int32_t old_mode = ctx->alpha_mode;
+  const bool old_timing = ctx->timing;
+  ctx->timing = false;
+  drop_graph(ctx);
+  ctx->alpha_log = alog;
+  ctx->alpha_cap = nsteps;
+  ctx->alpha_base = device_steps(ctx);
+  ctx->alpha_mode = 1;
+  auto restore_ctx = [&]() {
+    drop_graph(ctx);
+    ctx->alpha_log = old_log;
+    ctx->alpha_cap = old_cap;
+    ctx->alpha_base = old_base;
+    ctx->alpha_mode = old_mode;
+    ctx->timing = old_timing;
+  };
+  const unsigned gg = (unsigned)((B * G + 127) / 128);
+  // ---- forward with checkpoints and the misfit ----
+  for (int64_t n = 0; n < nsteps && !s; ++n) {
+    if (n % C == 0 && (e = save(ckpt[n / C]))) break;
+    s = enqueue_step(ctx);
+    if (!s) k_misfit<0><<<gg, 128, 0, st>>>(D, A, (int32_t)B, G, gx, obs + n * B * G, Jacc);
+  }
+  if (!s && !e) e = save(fin);
+  if (!s && !e) e = cudaGetLastError();
+  ctx->alpha_mode = 2;
+  StepConst K = step_const(ctx);
+  // ---- reverse, segment by segment ----
+  for (int64_t sg = nseg - 1; sg >= 0 && !s && !e; --sg) {
+    const int64_t n0 = sg * C, n1 = std::min(nsteps, n0 + C);
+    e = load(ckpt[sg]);
+    for (int64_t m = n0; m < n1 && !s && !e; ++m) {
+      e = save(seg[m - n0]);
+      if (!e && m + 1 < n1) s = enqueue_step(ctx);
+    }
+    for (int64_t m = n1 - 1; m >= n0 && !s && !e; --m) {
+      const StateCopy& c = seg[m - n0];
+      e = load(c);
+      // q^n, J^n of this step for stage 1 and the RK combination.
+      e = e ? e : cudaMemcpyAsync(snap.E, c.E, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      e = e ? e : cudaMemcpyAsync(snap.M, c.M, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      e = e ? e : cudaMemcpyAsync(snap.B, c.B, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      e = e ? e : cudaMemcpyAsync(snap.J, c.J, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      if (e) break;
+      // Recompute the step: q^(1), q^(2), the stage meshes, node velocities and the stage-3
+      // edge values stay in the state arrays.
+      if ((s = enqueue_step(ctx))) break;
+      k_misfit<1><<<gg, 128, 0, st>>>(D, A, (int32_t)B, G, gx, obs + m * B * G, Jacc);
+      launch_adj_rk<3>(ctx, A);
+      launch_adj_stage<3>(ctx, K, A, D.Eb, D.Mb, D.Bb, D.J2);
+      launch_adj_rk<2>(ctx, A);
+      launch_recon_replay<2>(ctx, K, D.Ea, D.Ma, D.Ba, D.J1);
+      launch_adj_stage<2>(ctx, K, A, D.Ea, D.Ma, D.Ba, D.J1);
+      launch_adj_rk<1>(ctx, A);
+      launch_recon_replay<1>(ctx, K, snap.E, snap.M, snap.B, snap.J);
+      launch_adj_stage<1>(ctx, K, A, snap.E, snap.M, snap.B, snap.J);
+      launch_adj_rk<0>(ctx, A);
+      e = cudaGetLastError();
+    }
+  }
+  if (!s && !e) e = load(fin);
+  restore_ctx();
+  if (s) return release(s);
+  if (e) return release(fail(ctx, SWALE_ECUDA, std::string("adjoint: ") + cudaGetErrorString(e)));
+  e = cudaSuccess;
+  if (J) e = cudaMemcpyAsync(J, Jacc, B * sizeof(double), cudaMemcpyDefault, st);
+  if (!e && dJ_deta0) e = cudaMemcpyAsync(dJ_deta0, A.lE, Nt * sizeof(double), cudaMemcpyDefault, st);
+  if (!e && dJ_dhu0) e = cudaMemcpyAsync(dJ_dhu0, A.lM, Nt * sizeof(double), cudaMemcpyDefault, st);
+  if (!e && dJ_db0) e = cudaMemcpyAsync(dJ_db0, A.lB, Nt * sizeof(double), cudaMemcpyDefault, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (e) return release(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
+  std::vector<DevScalars> Sh;
+  if ((s = read_scalars(ctx, Sh))) return release(s);
+  unsigned int bits = 0;
+  for (const DevScalars& v : Sh) bits |= v.status;
+  return release(status_from_bits(ctx, bits));
+}
+
+}  // extern "C"
+
+// ======================================================================================
 // Allocation-free right-hand side (swale_rhs_noalloc)
 // ======================================================================================
 // Some callers cannot call cudaMalloc: code that runs inside another framework's memory
@@ -989,6 +1267,10 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   K.mesh = SWALE_MESH_STATIC;
   K.gauss_half = 0;
   K.B = 1;
+  K.alpha_log = nullptr;
+  K.alpha_cap = 0;
+  K.alpha_base = 0;
+  K.alpha_mode = 0;
   // The scalars keep the previous call's contents: start them from zero (J^n minimum at 1 so
   // the stage-1 time-step arithmetic stays finite; its result is not used here).
   InstConst ic0;

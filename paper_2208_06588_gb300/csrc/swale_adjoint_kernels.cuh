@@ -1,0 +1,318 @@
+// Device kernels of the discrete adjoint of one SSP-RK3 step (Eq. RK32D) of the well-balanced
+// ALE-WENO hybrid scheme: reverse of the RK combination, and for each stage the reverse of the
+// interface fluxes, of the source term and of the reconstruction + limiter. They walk the same
+// (instance, tile) work lists as the forward kernels; the adjoints of the stage input are
+// accumulated with FP64 atomicAdd (each cell receives the contributions of the stencils, fluxes
+// and sources that read it; ghost cells map back to their physical image, with the discharge's
+// sign flipped at reflective boundaries).
+#pragma once
+
+#include "swale_adjoint.cuh"
+#include "swale_kernels.cuh"
+
+namespace swale_dev {
+
+// Adjoint work arrays (concatenated like the state; edge adjoints in the edge layout).
+struct AdjState {
+  double *lE, *lM, *lB;   // lambda: adjoint of q^{n+1} on entry, of q^n on exit
+  double *yE, *yM, *yB;   // adjoint of the running RK combination Y
+  double *pE, *pM, *pB;   // accumulated adjoint of q^n through the RK combination
+  double *aE, *aM, *aB;   // adjoint of the current stage input (atomically accumulated)
+  double *rE, *rM, *rB;   // adjoint of the current stage's right-hand side
+  double *ab[8];          // adjoints of the edge state (EL, ER, BL, BR, hL, hR, uL, uR)
+  double *sE, *sM, *sB, *sJ;  // q^n and J^n of the step being reversed
+};
+
+__device__ __forceinline__ Tile utile_of(const DevState& D, int t, int T) {
+  return D.utiles ? D.utiles[t] : Tile{0, t * T};
+}
+
+// Reverse of the RK combination, one phase per call. With Y3 = J3 q^{n+1}:
+//   PH 3: Y = lambda / J3;  p = J0 Y / 3;  y = 2 Y / 3;  r = 2 dt Y / 3
+//   PH 2: y += a / J2;      p += 3 J0 y / 4;  r = dt y / 4;  y = y / 4
+//   PH 1: y += a / J1;      p += J0 y;        r = dt y
+//   PH 0: lambda = p + a
+// a (the stage adjoint of the previous phase) is read and cleared.
+template <int PH, int T>
+__global__ void __launch_bounds__(T) k_adj_rk(DevState D, AdjState A) {
+  for (int t = blockIdx.x; t < D.nu; t += gridDim.x) {
+    const Tile tl = utile_of(D, t, T);
+    const InstConst ic = D.IC[tl.inst];
+    const int64_t j = tl.c0 + threadIdx.x;
+    if (j >= ic.N) continue;
+    const int64_t g = ic.coff + j;
+    const double dt = D.S[tl.inst].dt;
+    double* lv[3] = {A.lE, A.lM, A.lB};
+    double* yv[3] = {A.yE, A.yM, A.yB};
+    double* pv[3] = {A.pE, A.pM, A.pB};
+    double* av[3] = {A.aE, A.aM, A.aB};
+    double* rv[3] = {A.rE, A.rM, A.rB};
+    const double J0 = A.sJ[g];
+    if (PH == 3) {
+      const double iJ3 = 1.0 / D.J0[g];  // J^{n+1} after the recomputed step
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const double Y = lv[v][g] * iJ3;
+        pv[v][g] = (1.0 / 3.0) * J0 * Y;
+        yv[v][g] = (2.0 / 3.0) * Y;
+        rv[v][g] = (2.0 / 3.0) * dt * Y;
+      }
+    } else if (PH == 2) {
+      const double iJ2 = 1.0 / D.J2[g];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const double y = yv[v][g] + av[v][g] * iJ2;
+        av[v][g] = 0.0;
+        pv[v][g] += 0.75 * J0 * y;
+        rv[v][g] = 0.25 * dt * y;
+        yv[v][g] = 0.25 * y;
+      }
+    } else if (PH == 1) {
+      const double iJ1 = 1.0 / D.J1[g];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const double y = yv[v][g] + av[v][g] * iJ1;
+        av[v][g] = 0.0;
+        pv[v][g] += J0 * y;
+        rv[v][g] = dt * y;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        lv[v][g] = pv[v][g] + av[v][g];
+        av[v][g] = 0.0;
+      }
+    }
+  }
+}
+
+// Reverse of the interface fluxes of stage STAGE: interface k of cells k-1 and k gets the
+// flux adjoints from the right-hand-side adjoints of its two cells and writes the adjoints of
+// the right edge of cell k-1 and of the left edge of cell k (each edge slot has one writer).
+template <int STAGE, int T>
+__global__ void __launch_bounds__(T) k_adj_flux(StepConst K, DevState D, AdjState A) {
+  for (int t = blockIdx.x; t < D.nu; t += gridDim.x) {
+    const Tile tl = utile_of(D, t, T);
+    const InstConst ic = D.IC[tl.inst];
+    const DevScalars* S = D.S + tl.inst;
+    const int64_t N = ic.N, cb = ic.coff, nb = ic.coff + tl.inst, eb = ic.coff + 2 * (int64_t)tl.inst;
+    double alpha = (STAGE == 1) ? S->alpha1 : bitsd(S->A[STAGE - 1]) + S->Wbar;
+    if (STAGE > 1 && K.alpha_mode == 2) alpha = stage_alpha(K, tl.inst, STAGE, alpha, S->step_idx);
+    for (int i = threadIdx.x; i <= T; i += T) {
+      const int64_t k = tl.c0 + i;
+      if (k > N || (i == T && k != N)) continue;
+      swale::Flux Fb;
+      const double rEr = (k < N) ? A.rE[cb + k] : 0.0, rEl = (k > 0) ? A.rE[cb + k - 1] : 0.0;
+      const double rMr = (k < N) ? A.rM[cb + k] : 0.0, rMl = (k > 0) ? A.rM[cb + k - 1] : 0.0;
+      const double rBr = (k < N) ? A.rB[cb + k] : 0.0, rBl = (k > 0) ? A.rB[cb + k - 1] : 0.0;
+      Fb.FE = rEr - rEl;
+      Fb.FMm = -rMl;
+      Fb.FMp = rMr;
+      Fb.FB = rBl - rBr;
+      const double wk = (K.mesh == SWALE_MESH_STATIC) ? 0.0 : D.w[nb + k];
+      const int64_t el = eb + k, er = eb + k + 1;
+      if (k == 0) {  // the ghost cell -1 has no left interface
+        A.ab[0][el] = 0.0;
+        A.ab[2][el] = 0.0;
+        A.ab[4][el] = 0.0;
+        A.ab[6][el] = 0.0;
+      }
+      if (k == N) {  // the ghost cell N has no right interface
+        A.ab[1][er] = 0.0;
+        A.ab[3][er] = 0.0;
+        A.ab[5][er] = 0.0;
+        A.ab[7][er] = 0.0;
+      }
+      const swale::EdgeAdj a = swale::interface_flux_rev(K.sc.g, alpha, wk, D.eER[el], D.eEL[er], D.eBR[el],
+                                                         D.eBL[er], D.ehR[el], D.ehL[er], D.euR[el], D.euL[er], Fb);
+      // interface_flux_rev names its inputs as (left state, right state) = (EL, ER, ...).
+      A.ab[1][el] = a.EL;  // right edge of cell k-1
+      A.ab[3][el] = a.BL;
+      A.ab[5][el] = a.hL;
+      A.ab[7][el] = a.uL;
+      A.ab[0][er] = a.ER;  // left edge of cell k
+      A.ab[2][er] = a.BR;
+      A.ab[4][er] = a.hR;
+      A.ab[6][er] = a.uR;
+    }
+  }
+}
+
+// Reverse of the source term of stage STAGE for cell j: adds to the adjoints of its own
+// limited edge depths and bottoms, and (atomically) to the stage-input adjoints of the depth
+// and bottom averages of cells j-1, j, j+1.
+template <int STAGE, int T>
+__global__ void __launch_bounds__(T) k_adj_source(StepConst K, DevState D, AdjState A, const double* __restrict__ Eg,
+                                                  const double* __restrict__ Bg, const double* __restrict__ Jsg) {
+  for (int t = blockIdx.x; t < D.nu; t += gridDim.x) {
+    const Tile tl = utile_of(D, t, T);
+    const InstConst ic = D.IC[tl.inst];
+    const int64_t N = ic.N, cb = ic.coff, eb = ic.coff + 2 * (int64_t)tl.inst;
+    const int64_t j = tl.c0 + threadIdx.x;
+    if (j >= N) continue;
+    const int64_t jm = ghost(j - 1, N, K.bc), jp = ghost(j + 1, N, K.bc);
+    const double* E = Eg + cb;
+    const double* B = Bg + cb;
+    const double* Js = Jsg + cb;
+    const double Jm = Js[jm], Jc = Js[j], Jp = Js[jp];
+    const swale::SourceGeom sg = swale::source_geom(Jm, Jc, 1.0 / Jm, 1.0 / Jc, 1.0 / Jp, D.ipair[eb + j],
+                                                    D.ipair[eb + j + 1], D.itri[eb + j + 1]);
+    const int64_t ie = eb + j + 1;
+    const double hd[5] = {E[jm] - B[jm], E[j] - B[j], E[jp] - B[jp], D.ehL[ie], D.ehR[ie]};
+    const double bd[5] = {B[jm], B[j], B[jp], D.eBL[ie], D.eBR[ie]};
+    double hdb[5] = {0, 0, 0, 0, 0}, bdb[5] = {0, 0, 0, 0, 0};
+    swale::source_cell_rev(K.sc.g, hd, bd, sg, A.rM[cb + j], hdb, bdb);
+    A.ab[4][ie] += hdb[3];
+    A.ab[5][ie] += hdb[4];
+    A.ab[2][ie] += bdb[3];
+    A.ab[3][ie] += bdb[4];
+    const int64_t cells[3] = {jm, j, jp};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      atomicAdd(&A.aE[cb + cells[k]], hdb[k]);
+      atomicAdd(&A.aB[cb + cells[k]], bdb[k] - hdb[k]);
+    }
+  }
+}
+
+// Reverse of the reconstruction + limiter of stage STAGE for cells -1..N (tiles of T cells
+// staged like the forward kernel): each cell's reverse sweep gives the adjoints of its stencil
+// averages and divided differences, which map to the 5 stencil cells and are added atomically.
+template <int STAGE, int T>
+__global__ void __launch_bounds__(T) k_adj_recon(StepConst K, DevState D, AdjState A, const double* __restrict__ Eg,
+                                                 const double* __restrict__ Mg, const double* __restrict__ Bg,
+                                                 const double* __restrict__ Jg) {
+  __shared__ double sJ[T + 4], sV[3][T + 4];
+  __shared__ double sIP[T + 3], sD2[3][T + 3];
+  __shared__ double sIT[T + 2], sD3[3][T + 2];
+  const int tid = threadIdx.x;
+  const bool refl = (K.bc == SWALE_BC_REFLECTIVE);
+  for (int t = blockIdx.x; t < D.nr; t += gridDim.x) {
+    const Tile tl = D.rtiles ? D.rtiles[t] : Tile{0, t * T - 1};
+    const DevScalars* S = D.S + tl.inst;
+    const InstConst ic = D.IC[tl.inst];
+    const int64_t N = ic.N, c0 = tl.c0, cb = ic.coff;
+    const double* E = Eg + cb;
+    const double* M = Mg + cb;
+    const double* B = Bg + cb;
+    const double* J = Jg + cb;
+    const int64_t eb = ic.coff + 2 * (int64_t)tl.inst;
+    __syncthreads();
+    for (int i = tid; i < T + 4; i += T) {
+      const int64_t c = c0 - 2 + i;
+      double jv = 1.0, ev = 0.0, mv = 0.0, bv = 0.0;
+      if (c >= -3 && c <= N + 2) {
+        const int64_t s = ghost(c, N, K.bc);
+        jv = J[s];
+        ev = E[s];
+        bv = B[s];
+        mv = M[s];
+        if (refl && (c < 0 || c >= N)) mv = -mv;
+      }
+      sJ[i] = jv;
+      sV[0][i] = ev;
+      sV[1][i] = mv;
+      sV[2][i] = bv;
+    }
+    __syncthreads();
+    for (int i = tid; i < T + 3; i += T) {
+      const double ip = swale::pair_recip(sJ[i], sJ[i + 1]);
+      sIP[i] = ip;
+#pragma unroll
+      for (int v = 0; v < 3; ++v) sD2[v][i] = swale::pair_dd(sV[v][i], sV[v][i + 1], ip);
+    }
+    __syncthreads();
+    for (int i = tid; i < T + 2; i += T) {
+      const double it = swale::triple_recip(sJ[i], sJ[i + 1], sJ[i + 2]);
+      sIT[i] = it;
+#pragma unroll
+      for (int v = 0; v < 3; ++v) sD3[v][i] = swale::triple_dd(sD2[v][i], sD2[v][i + 1], it);
+    }
+    __syncthreads();
+    const int64_t c = c0 + tid;
+    if (c > N) continue;
+    double h[5], v0[3][3];
+    swale::StencilDD DD, DDb;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) h[k] = sJ[tid + k];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) v0[v][a] = sV[v][tid + a];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) DD.D2[v][a] = sD2[v][tid + a];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) DD.D3[v][a] = sD3[v][tid + a];
+    }
+    const int64_t idx = eb + c + 1;
+    const swale::EdgeAdj ob = {A.ab[0][idx], A.ab[1][idx], A.ab[2][idx], A.ab[3][idx],
+                               A.ab[4][idx], A.ab[5][idx], A.ab[6][idx], A.ab[7][idx]};
+    double v0b[3][3];
+    swale::recon_cell_rev(K.sc, h, v0, DD, bitsd(S->Jmax[STAGE - 1]), ob, v0b, DDb);
+    // Stencil cell adjoints: cv[v][k] for cells c-2+k.
+    double cv[3][5];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) cv[v][k] = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) cv[v][a] += v0b[v][a];
+      double d2b[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) d2b[a] = DDb.D2[v][a];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {  // D3[a] = (D2[a+1] - D2[a]) it[a]
+        const double x = DDb.D3[v][a] * sIT[tid + a];
+        d2b[a + 1] += x;
+        d2b[a] -= x;
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {  // D2[a] = (v[a+1] - v[a]) ip[a]
+        const double x = d2b[a] * sIP[tid + a];
+        cv[v][a + 1] += x;
+        cv[v][a] -= x;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int64_t vc = c - 2 + k;
+      const int64_t s = ghost(vc, N, K.bc);
+      const double sgn = (refl && (vc < 0 || vc >= N)) ? -1.0 : 1.0;
+      atomicAdd(&A.aE[cb + s], cv[0][k]);
+      atomicAdd(&A.aM[cb + s], sgn * cv[1][k]);
+      atomicAdd(&A.aB[cb + s], cv[2][k]);
+    }
+  }
+}
+
+// Gauge misfit of the state after a step: gauge g of instance i sits at x = gx[i * G + g]; its
+// depth is the average of the cell that contains x on the current mesh. MODE 0 adds
+// dt (h - obs)^2 to Jout[i]; MODE 1 adds its gradient 2 dt (h - obs) to lambda (eta: +, b: -).
+// obs points at the row of the observed depths for this step (B x G values).
+template <int MODE>
+__global__ void k_misfit(DevState D, AdjState A, int32_t B, int32_t G, const double* __restrict__ gx,
+                         const double* __restrict__ obs, double* Jout) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)B * G) return;
+  const int i = (int)(id / G);
+  const InstConst ic = D.IC[i];
+  const double* x = D.x + ic.coff + i;
+  const double xg = gx[id];
+  int64_t lo = 0, hi = ic.N;  // find c with x[c] <= xg < x[c+1]
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (x[mid] <= xg) lo = mid;
+    else hi = mid;
+  }
+  const int64_t g = ic.coff + lo;
+  const double r = (D.E0[g] - D.B0[g]) - obs[id];
+  const double dt = D.S[i].dt;
+  if (MODE == 0) {
+    atomicAdd(&Jout[i], dt * r * r);
+  } else {
+    atomicAdd(&A.lE[g], 2.0 * dt * r);
+    atomicAdd(&A.lB[g], -2.0 * dt * r);
+  }
+}
+
+}  // namespace swale_dev

@@ -41,6 +41,7 @@ struct DevScalars {
   unsigned long long JmaxN, JminN;   // of J^{n+1}, accumulated by stage 3
   unsigned long long Wabs, dWabs;    // fluid-driven motion: max |w|, max |w_{j+1} - w_j|
   long long steps;
+  long long step_idx;                // index of the step in progress (set by the prologue)
   unsigned int status;
   unsigned int counter;              // reconstruction tiles finished in stage 1
   int done;
@@ -68,7 +69,25 @@ struct StepConst {
   double t_end, dt_fixed, mesh_T;
   double gauss_wsum;  // sum of the full Gaussian window, summed from -H to H
   int32_t bc, mesh, gauss_half, B;
+  // Stage viscosities: log of 3 values per step and instance (index (step * B + i) * 3 + s - 1);
+  // alpha_mode 1 records the computed values, 2 replays the logged ones (the adjoint's and the
+  // finite-difference checks' convention: alpha held fixed).
+  double* alpha_log;
+  int64_t alpha_cap;   // steps the log holds
+  int64_t alpha_base;  // step counter value of log row 0
+  int32_t alpha_mode;
 };
+
+// Stage viscosity of instance i in stage s of step `step` (DevScalars::step_idx): the computed
+// value, or the logged one in replay mode; recorded in record mode.
+__device__ __forceinline__ double stage_alpha(const StepConst& K, int i, int s, double computed, long long step) {
+  step -= K.alpha_base;
+  if (K.alpha_mode == 0 || K.alpha_log == nullptr || step < 0 || step >= K.alpha_cap) return computed;
+  double* slot = K.alpha_log + ((int64_t)step * K.B + i) * 3 + (s - 1);
+  if (K.alpha_mode == 2) return *slot;
+  *slot = computed;
+  return computed;
+}
 
 // Device arrays of a batch (concatenated over instances).
 struct DevState {
@@ -153,6 +172,7 @@ __global__ void k_prologue(StepConst K, DevState D) {
   }
   S->done = 0;
   S->clipped = 0;
+  S->step_idx = S->steps;
   S->Jmax[0] = S->JmaxN;
   S->Jmin0 = S->JminN;
   S->JmaxN = 0ull;
@@ -245,10 +265,12 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevSta
 // reciprocals for the update kernel of the same stage, reduces the wave speed, and in stage 1
 // the instance's last tile computes its dt (and the secant factor of the prescribed motion).
 // ------------------------------------------------------------------------------------
-template <int STAGE, int T>
+template <int STAGE, int T, int MODE = 0>
 __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
                                              const double* __restrict__ Mg, const double* __restrict__ Bg,
                                              const double* __restrict__ Jg) {
+  // MODE 0: a stage of a step. MODE 1 (replay, used by the adjoint): edge values and shared
+  // reciprocals only, no reductions, classes or time step.
   __shared__ double sJ[T + 4], sV[3][T + 4];    // cells c0-2 .. c0+T+1
   __shared__ double sIP[T + 3], sD2[3][T + 3];  // pairs starting at those cells
   __shared__ double sIT[T + 2], sD3[3][T + 2];  // triples centred at cells c0-1 .. c0+T
@@ -258,7 +280,7 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
   for (int t = blockIdx.x; t < D.nr; t += gridDim.x) {
     const Tile tl = D.rtiles ? D.rtiles[t] : Tile{0, t * T - 1};
     DevScalars* S = D.S + tl.inst;
-    if (S->done) continue;
+    if (MODE == 0 && S->done) continue;
     const InstConst ic = D.IC[tl.inst];
     const int64_t N = ic.N, c0 = tl.c0;
     const double* E = Eg + ic.coff;
@@ -331,13 +353,14 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
       D.euR[idx] = o.uR;
       D.ipair[idx] = sIP[tid + 2];  // pair (c, c+1)
       D.itri[idx] = sIT[tid + 1];   // triple centred at c
-      if (STAGE == 1) D.flags[idx] = flag;
+      if (STAGE == 1 && MODE == 0) D.flags[idx] = flag;
       // Edges that touch interfaces 0..N only.
       if (c == -1) wave = wr;
       else if (c == N) wave = wl;
       else wave = fmax(wl, wr);
       if (!(wave == wave)) st |= swale::ST_NONFINITE;
     }
+    if (MODE == 1) continue;
     block_or_status(&S->status, st);
     block_max_to(&S->A[STAGE - 1], wave);
     if (STAGE == 1) {
@@ -357,7 +380,7 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
           dwmax = bitsd(atomicAdd(&S->dWabs, 0ull));
           S->Wbar = Wbar;
         }
-        const double alpha1 = A1 + Wbar;
+        const double alpha1 = stage_alpha(K, tl.inst, 1, A1 + Wbar, S->step_idx);
         const double tn = S->t;
         double dt;
         int clipped = 0;
@@ -424,6 +447,12 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
       alpha = ro.alpha;
     } else {
       alpha = (STAGE == 1) ? S->alpha1 : bitsd(S->A[STAGE - 1]) + S->Wbar;
+      if (STAGE > 1) {
+        // Record / replay of stages 2 and 3 (stage 1 is handled where alpha1 is formed): every
+        // tile computes the same value; the first tile of the instance records it.
+        if (K.alpha_mode == 2) alpha = stage_alpha(K, inst, STAGE, alpha, S->step_idx);
+        else if (K.alpha_mode == 1 && j0 == 0 && threadIdx.x == 0) stage_alpha(K, inst, STAGE, alpha, S->step_idx);
+      }
       dt = S->dt;
     }
     const bool fresh_w = (MODE == 0 && STAGE == 1 && K.mesh == SWALE_MESH_PROFILE);

@@ -246,3 +246,60 @@ def many_basins(B=4096, n_min=256, n_max=16384, seed=MASTER_SEED + 3, n_cells=No
     prof = np.concatenate([p[3] for p in parts])
     cfl = np.array([p[4] for p in parts])
     return Batch(name="many_basins", off=off, x=x, h=h, hu=np.zeros_like(h), b=b, E=h + b, profile=prof, cfl=cfl)
+
+
+# --------------------------------------------------------------------------------------
+# Adjoint workloads: gauge misfit of a smooth basin
+# --------------------------------------------------------------------------------------
+@dataclass
+class GaugeProblem:
+    problem: Problem
+    gauges: np.ndarray   # G gauge positions
+    h_obs: np.ndarray    # nsteps x G observed depths
+    nsteps: int
+
+
+def gaussian_basin(N=65536, seed=MASTER_SEED + 4, n_gauss=4, n_basis=32, A=0.02, cfl=0.6):
+    """[0,1], reflective; b = sum of n_gauss Gaussians (heights U[0,0.5], centres U[0.1,0.9],
+    widths U[0.05,0.2]), scaled down to a maximum of 0.5 where the bumps stack higher; eta0 = 1 + sum_{k<n_basis} c_k exp(-(x - (k+1/2)/n_basis)^2 / (2 (1/(2 n_basis))^2))
+    with c_k ~ U[-0.01, 0.01]; hu = 0; sine motion x = xi + A sin(2 pi xi) sin(2 pi t), T = 1;
+    fixed dt = 0.9 CFL min J / alpha0 with alpha0 = max sqrt(g h) + 2 pi A (the CFL value at t = 0)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    amp, cen, wid = rng.uniform(0, 0.5, n_gauss), rng.uniform(0.1, 0.9, n_gauss), rng.uniform(0.05, 0.2, n_gauss)
+    coef = rng.uniform(-0.01, 0.01, n_basis)
+    sig = 1.0 / (2 * n_basis)
+
+    xs = np.linspace(0.0, 1.0, 4097)
+    peak = float(sum(a * np.exp(-(xs - c) ** 2 / (2 * w * w)) for a, c, w in zip(amp, cen, wid)).max())
+    amp = amp * min(1.0, 0.5 / peak)
+
+    def bf(s):
+        return sum(a * np.exp(-(s - c) ** 2 / (2 * w * w)) for a, c, w in zip(amp, cen, wid))
+
+    def etaf(s):
+        return 1.0 + sum(ck * np.exp(-(s - (k + 0.5) / n_basis) ** 2 / (2 * sig * sig)) for k, ck in enumerate(coef))
+
+    x = _uniform(0.0, 1.0, N)
+    b = cell_averages(bf, x)
+    E = cell_averages(etaf, x)
+    h = E - b
+    prof = _sine_profile(x, 0.0, 1.0, A)
+    alpha0 = float(np.sqrt(G_PAPER * h.max())) + 2 * np.pi * A
+    dt = 0.9 * cfl * float(np.diff(x).min()) / alpha0
+    pr = Problem(name="gaussian_basin", x=x, h=h, hu=np.zeros(N), b=b, E=E, profile=prof, bc="reflective",
+                 mesh="profile", mesh_T=1.0, cfl=cfl, dt_fixed=dt)
+    pr.meta.update(coef=coef, amp=amp, cen=cen, wid=wid)
+    return pr
+
+
+def gauge_problem(N=65536, nsteps=4000, G=16, seed=MASTER_SEED + 4):
+    """The basin of gaussian_basin with G gauges at (g + 1/2)/G and observations h_obs from the
+    same generator with seed + 1 (different surface coefficients), sampled as the cell averages
+    of the observation run's initial depth at the gauges, held for every step (a synthetic
+    stand-in for recorded gauge series)."""
+    pr = gaussian_basin(N=N, seed=seed)
+    ob = gaussian_basin(N=N, seed=seed + 1)
+    gx = (np.arange(G) + 0.5) / G
+    idx = np.minimum((gx * N).astype(np.int64), N - 1)
+    h0 = ob.h[idx]
+    return GaugeProblem(problem=pr, gauges=gx, h_obs=np.tile(h0, (nsteps, 1)), nsteps=nsteps)

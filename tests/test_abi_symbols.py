@@ -39,3 +39,13 @@ def test_binding_names_match_abi():
     from paper_2208_06588_gb300 import binding
     for n in declared_symbols():
         assert hasattr(binding, n), n
+
+
+def test_autograd_wrapper_has_no_cpu_path():
+    import torch
+
+    from paper_2208_06588_gb300 import binding as B
+    from paper_2208_06588_gb300.autograd import gauge_misfit
+    z = torch.zeros(8, dtype=torch.float64, requires_grad=True)
+    with pytest.raises(ValueError, match="CUDA"):
+        gauge_misfit(z, z, z, torch.linspace(0, 1, 9), None, [0.5], [[0.0]], B.make_config(), 1)

@@ -1,0 +1,100 @@
+"""Dot-product checks of the hand-written reverse sweeps of the per-cell arithmetic (no GPU):
+for random directions u and adjoint seeds ob, <ob, T u> from a forward-mode dual-number build
+of the same per-cell code must equal <T^T ob, u> from the reverse sweep, in every branch the
+scheme has (smooth / transition / non-smooth classes, limiter on / off, wet / dry edges)."""
+import numpy as np
+import pytest
+
+from paper_2208_06588_gb300 import cellcheck as C
+
+RNG = np.random.default_rng(424242)
+PRM = np.array([9.812, 1e-6, 1e-11, 1e-6, 0.0])
+
+
+def stencil(E, M, B, h):
+    """v0 (averages of cells j-2..j) and the divided differences of the big stencil."""
+    v = np.stack([E, M, B])
+    ip = 1.0 / (h[:-1] + h[1:])
+    D2 = (v[:, 1:] - v[:, :-1]) * ip
+    it = 1.0 / (h[:-2] + h[1:-1] + h[2:])
+    D3 = (D2[:, 1:] - D2[:, :-1]) * it
+    return v[:, :3].ravel(), D2.ravel(), D3.ravel()
+
+
+def cases():
+    out = []
+    for k in range(60):
+        h = RNG.uniform(0.5, 1.5, 5) * 0.01
+        x = np.cumsum(h) - h[0]
+        kind = k % 6
+        if kind == 0:    # smooth, deep
+            B = 0.3 * np.sin(x * 30); E = 2.0 + 0.01 * np.cos(x * 40) + B * 0; M = 0.4 + 0.1 * x
+        elif kind == 1:  # jump in the surface
+            B = 0.2 * x; E = np.where(np.arange(5) < 2 + (k % 3), 2.0, 1.0) + B; M = 0.3 * np.ones(5)
+        elif kind == 2:  # mild kink (transition)
+            B = 0.1 * np.ones(5); E = 1.5 + 0.02 * np.abs(np.arange(5) - 2.0 + 0.3 * RNG.normal()); M = 0.1 * x
+        elif kind == 3:  # wet / dry front (limiter active)
+            B = np.zeros(5); E = np.array([1.0, 0.6, 1e-4, 0.0, 0.0])[::(1 if k % 2 else -1)]; M = 0.2 * E
+        elif kind == 4:  # near-dry cell with steep neighbours
+            B = np.array([0.0, 0.1, 0.5, 0.9, 1.2]); E = B + np.array([1.0, 0.5, 2e-3, 0.0, 0.0]); M = 0.05 * (E - B)
+        else:            # random rough data
+            B = RNG.uniform(0, 0.5, 5); E = B + RNG.uniform(0.0, 1.0, 5); M = RNG.normal(size=5) * 0.3
+        E = E + 1e-3 * RNG.normal(size=5) * (kind not in (3, 4))
+        out.append((h, E, M, B))
+    return out
+
+
+@pytest.mark.parametrize("case", range(60))
+def test_recon_reverse_matches_tangent(case):
+    h, E, M, B = cases()[case]
+    v0, D2, D3 = stencil(E, M, B, h)
+    prm = PRM.copy()
+    prm[4] = 0.015
+    tv0, tD2, tD3 = RNG.normal(size=9), RNG.normal(size=12), RNG.normal(size=9)
+    ob = RNG.normal(size=8)
+    val, tan, flag = C.recon_tangent(h, v0, D2, D3, tv0, tD2, tD3, prm)
+    v0b, D2b, D3b = C.recon_adjoint(h, v0, D2, D3, prm, ob)
+    lhs = ob @ tan
+    rhs = v0b @ tv0 + D2b @ tD2 + D3b @ tD3
+    scale = np.abs(ob * tan).sum() + np.abs(v0b * tv0).sum() + np.abs(D2b * tD2).sum() + np.abs(D3b * tD3).sum()
+    assert abs(lhs - rhs) <= 1e-12 * scale + 1e-300, (flag, lhs, rhs)
+
+
+def test_recon_cases_cover_every_class():
+    flags = set()
+    for h, E, M, B in cases():
+        v0, D2, D3 = stencil(E, M, B, h)
+        prm = PRM.copy()
+        prm[4] = 0.015
+        flags.add(C.recon_tangent(h, v0, D2, D3, np.zeros(9), np.zeros(12), np.zeros(9), prm)[2])
+    assert flags == {0, 1, 2}
+
+
+@pytest.mark.parametrize("trial", range(40))
+def test_flux_reverse_matches_tangent(trial):
+    rng = np.random.default_rng(trial)
+    BL, BR = rng.uniform(0, 1, 2)
+    if trial % 4 == 0:
+        BR = BL  # tie in b* = max(BL, BR)
+    EL, ER = max(BL, BR) + rng.uniform(-0.2, 1.0, 2)
+    hL, hR = EL - BL, ER - BR
+    e = np.array([EL, ER, BL, BR, hL, hR, rng.normal(), rng.normal()])
+    prm = np.array([9.812, rng.uniform(5, 20), rng.normal()])
+    te, Fb = rng.normal(size=8), rng.normal(size=4)
+    F, tF = C.flux_tangent(e, te, prm)
+    eb = C.flux_adjoint(e, prm, Fb)
+    scale = np.abs(Fb * tF).sum() + np.abs(eb * te).sum()
+    assert abs(Fb @ tF - eb @ te) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("trial", range(20))
+def test_source_reverse_matches_tangent(trial):
+    rng = np.random.default_rng(100 + trial)
+    Jm, Jc, Jp = rng.uniform(0.3, 3.0, 3)
+    geom = np.array([Jm / Jc, Jc / Jm, Jc / Jp, Jc / (Jm + Jc), Jc / (Jc + Jp), Jc / (Jm + Jc + Jp)])
+    hd, bd = rng.uniform(0.1, 2, 5), rng.uniform(0, 1, 5)
+    thd, tbd, Sb = rng.normal(size=5), rng.normal(size=5), rng.normal()
+    S, tS = C.source_tangent(hd, bd, thd, tbd, geom, 9.812)
+    hdb, bdb = C.source_adjoint(hd, bd, geom, 9.812, Sb)
+    lhs, rhs = Sb * tS, hdb @ thd + bdb @ tbd
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + np.abs(hdb * thd).sum() + np.abs(bdb * tbd).sum())
