@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=4000)
+    ap.add_argument("--batched-adjoint-steps", type=int, default=256)
     return ap.parse_args()
 
 
@@ -207,6 +210,135 @@ def bench_batched(args, stream, dev):
     return out
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _timed(stream, fn):
+    ev0, ev1 = _events()
+    stream.synchronize()
+    ev0.record(stream)
+    fn()
+    ev1.record(stream)
+    stream.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def bench_adjoint(args, stream):
+    """Gradient of the gauge misfit (16 gauges) of the 65536-cell Gaussian basin over
+    args.adjoint_steps steps, checkpoints every 64 steps: one swale_adjoint call with host
+    observations and host gradients, against the forward alone over the same steps."""
+    import torch
+    from paper_2208_06588_gb300 import binding as B
+    from paper_2208_06588_gb300 import workloads as W
+    K, C = args.adjoint_steps, 64
+    gp = W.gauge_problem(N=65536, nsteps=K, G=16)
+    pr = gp.problem
+    N, G = pr.N, gp.gauges.size
+    cfg = B.make_config(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, bc=pr.bc, mesh=pr.mesh,
+                        dt_fixed=pr.dt_fixed)
+    free0 = torch.cuda.mem_get_info()[0]
+    s = B.Solver(cfg, stream.cuda_stream)
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    stream.synchronize()
+    state_bytes = free0 - torch.cuda.mem_get_info()[0]
+    B.swale_enqueue(s.ctx, 16)
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    ms_fwd = _timed(stream, lambda: B.swale_enqueue(s.ctx, K))
+    J, gE, gM, gB = np.zeros(1), np.zeros(N), np.zeros(N), np.zeros(N)
+    obs = np.ascontiguousarray(gp.h_obs)
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    B.swale_adjoint(s.ctx, 32, 8, G, gp.gauges, obs, J, gE, gM, gB)  # warm-up
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    ms = _timed(stream, lambda: B.swale_adjoint(s.ctx, K, C, G, gp.gauges, obs, J, gE, gM, gB))
+    bits = s.status()[0]
+    s.close()
+    adj_bytes = B.swale_adjoint_bytes(1, N, K, C, G)
+    return {"workload": f"gaussian_basin N={N} [0,1] reflective, 4 Gaussian bumps, eta0 from 32 Gaussian basis "
+                        f"functions, sine mesh motion A=0.02, fixed dt; {K} SSP-RK3 steps; 16 gauges",
+            "metric": "cell-updates/s FP64 (forward + adjoint)", "unit": UNIT,
+            "value": N * K / (ms * 1e-3), "gradients_per_s": 1e3 / ms, "ms_per_gradient": ms,
+            "ckpt_every": C, "forward_only_ms": ms_fwd, "adjoint_over_forward": ms / ms_fwd,
+            "forward_only_value": N * K / (ms_fwd * 1e-3),
+            "peak_device_bytes": int(state_bytes + adj_bytes), "adjoint_scratch_bytes": int(adj_bytes),
+            "J": float(J[0]), "grad_norms": [float(np.linalg.norm(v)) for v in (gE, gM, gB)], "status_bits": bits,
+            "call": "swale_adjoint (host gauges, observations and gradients)"}
+
+
+def bench_batched_adjoint(args, stream):
+    """Batched gradients: 512 Gaussian basins (N_i ~ U{1024..32768}, per-instance seeds and CFL
+    dt), args.batched_adjoint_steps steps, checkpoints every 64 steps, all instances in the same
+    launches; against one swale_adjoint call per instance on a 32-instance subset."""
+    import torch
+    from paper_2208_06588_gb300 import binding as B
+    from paper_2208_06588_gb300 import workloads as W
+    K, C, G = args.batched_adjoint_steps, 64, 16
+    gb = W.many_gauge_basins(B=512, nsteps=K, G=G)
+    bt = gb.batch
+    Nt = int(bt.off[-1])
+    cfg = B.make_config(g=bt.g, eps_weno=bt.eps_weno, mesh_T=bt.mesh_T, bc=bt.bc, mesh=bt.mesh, cfl=0.6)
+    free0 = torch.cuda.mem_get_info()[0]
+    s = B.Solver(cfg, stream.cuda_stream)
+    s.set_batch(bt)
+    stream.synchronize()
+    state_bytes = free0 - torch.cuda.mem_get_info()[0]
+    B.swale_set_tiles(s.ctx, 128, 128, 0, 0)
+    B.swale_enqueue(s.ctx, 4)
+    s.set_batch(bt)
+    ms_fwd = _timed(stream, lambda: B.swale_enqueue(s.ctx, K))
+    s.set_batch(bt)
+    J, gE, gM, gB = np.zeros(bt.B), np.zeros(Nt), np.zeros(Nt), np.zeros(Nt)
+    obs = np.ascontiguousarray(gb.h_obs)
+    B.swale_adjoint(s.ctx, 8, 4, G, gb.gauges, obs, J, gE, gM, gB)  # warm-up
+    s.set_batch(bt)
+    ms = _timed(stream, lambda: B.swale_adjoint(s.ctx, K, C, G, gb.gauges, obs, J, gE, gM, gB))
+    bits = s.status()[0]
+    s.close()
+    adj_bytes = B.swale_adjoint_bytes(bt.B, Nt, K, C, G)
+    full_bytes = B.swale_adjoint_bytes(bt.B, Nt, 2000, C, G)
+    out = {"workload": f"many_gauge_basins: 512 instances, N_i ~ U{{1024..32768}} (sum {Nt} cells), per-instance "
+                       f"seeds, CFL 0.6 dt per instance, 16 gauges each; {K} steps timed (of 2000 in the full "
+                       f"case; the cost per step does not depend on the step count)",
+           "metric": "cell-updates/s FP64 (forward + adjoint)", "unit": UNIT,
+           "value": Nt * K / (ms * 1e-3), "gradients_per_s": bt.B * 1e3 / ms, "steps": K, "ckpt_every": C,
+           "forward_only_value": Nt * K / (ms_fwd * 1e-3), "adjoint_over_forward": ms / ms_fwd,
+           "peak_device_bytes": int(state_bytes + adj_bytes), "peak_device_bytes_2000_steps": int(state_bytes + full_bytes),
+           "status_bits": bits}
+    # One swale_adjoint per instance on a subset, same steps, against the batch of the subset.
+    sub, Ks = 32, min(K, 64)
+    sb = W.Batch(name="subset", off=bt.off[:sub + 1].copy(), x=bt.x[:int(bt.off[sub]) + sub],
+                 h=bt.h[:int(bt.off[sub])], hu=bt.hu[:int(bt.off[sub])], b=bt.b[:int(bt.off[sub])],
+                 E=bt.E[:int(bt.off[sub])], profile=bt.profile[:int(bt.off[sub]) + sub], cfl=bt.cfl[:sub])
+    ns = int(sb.off[-1])
+    gx = np.ascontiguousarray(gb.gauges[:sub * G])
+    ob = np.ascontiguousarray(gb.h_obs[:Ks, :sub, :])
+    s = B.Solver(cfg, stream.cuda_stream)
+    s.set_batch(sb)
+    Jb, g1, g2, g3 = np.zeros(sub), np.zeros(ns), np.zeros(ns), np.zeros(ns)
+    ms_b = _timed(stream, lambda: B.swale_adjoint(s.ctx, Ks, C, G, gx, ob, Jb, g1, g2, g3))
+    s.close()
+    solvers = []
+    for i in range(sub):
+        pr = sb.instance(i)
+        si = B.Solver(cfg, stream.cuda_stream)
+        si.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+        solvers.append((si, pr.N, np.ascontiguousarray(gx[i * G:(i + 1) * G]),
+                        np.ascontiguousarray(ob[:, i, :])))
+
+    def loop():
+        for si, n, gxi, obi in solvers:
+            Ji, a, b_, c = np.zeros(1), np.zeros(n), np.zeros(n), np.zeros(n)
+            B.swale_adjoint(si.ctx, Ks, C, G, gxi, obi, Ji, a, b_, c)
+
+    ms_l = _timed(stream, loop)
+    for si, *_ in solvers:
+        si.close()
+    out["vs_per_instance_loop"] = {"instances": sub, "cells": ns, "steps": Ks, "batched": ns * Ks / (ms_b * 1e-3),
+                                   "per_instance_loop": ns * Ks / (ms_l * 1e-3), "speedup": ms_l / ms_b}
+    return out
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle (plain C++ FP64, one thread), each step one SSP-RK3 step of
     a 2^15-cell sample of the same workload."""
@@ -344,6 +476,11 @@ def main():
     if not args.no_batched:
         batched = bench_batched(args, stream, dev)
 
+    adjoint = batched_adjoint = None
+    if not args.no_adjoint:
+        adjoint = bench_adjoint(args, stream)
+        batched_adjoint = bench_batched_adjoint(args, stream)
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -351,6 +488,7 @@ def main():
                       "l2": "working set ~230 MB per stage > 126 MB L2 (no flush needed)"},
            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
            "status_bits": bits, "steps_done_device": steps_done, "last_dt": last_dt, "batched": batched,
+           "adjoint": adjoint, "batched_adjoint": batched_adjoint,
            "fp64_ops_per_cell_stage": oc}
     print(json.dumps(out), flush=True)
     if ws > 1:

@@ -217,12 +217,21 @@ swale_status swale_get_alpha_log(swale_ctx* ctx, double* log);
  * viscosities alpha are those of the forward run, detector classes, limiter branches, dry-edge
  * tests and max/min selections are frozen (a tie follows the first argument). Checkpoints of
  * the state every ckpt_every steps; each segment is recomputed once with per-step snapshots and
- * each step once more inside its reverse sweep. Memory: about 5 (nsteps/ckpt_every +
- * ckpt_every) + 35 doubles per cell. The mesh must be prescribed (static or profile motion)
- * and t_end = 0. On return the context holds the state after the nsteps steps.
+ * each step once more inside its reverse sweep. Device memory beyond the context's own: about
+ * 5 (ceil(nsteps/C) + C + 2) + 23 doubles per cell with C = min(ckpt_every, nsteps), exactly
+ * the value of swale_adjoint_bytes; all of it is freed before the call returns. The mesh must
+ * be prescribed (static or profile motion) and t_end = 0. On return the context holds the
+ * state after the nsteps steps.
  * Errors: SWALE_EINVAL, SWALE_ENOMEM, SWALE_ECUDA, and the status errors of swale_advance. */
 swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, int32_t G, const double* gauges_x,
                            const double* h_obs, double* J, double* dJ_deta0, double* dJ_dhu0, double* dJ_db0);
+
+/* Device bytes swale_adjoint allocates for B instances with Ntot cells in total (host-only
+ * arithmetic; needs no device). Lets a caller pick ckpt_every for the memory it has: the
+ * checkpoints grow as nsteps / ckpt_every, the per-segment snapshots as ckpt_every.
+ * Errors: SWALE_EINVAL (a size < 1 or a NULL bytes pointer). */
+swale_status swale_adjoint_bytes(int64_t B, int64_t Ntot, int64_t nsteps, int64_t ckpt_every, int32_t G,
+                                 uint64_t* bytes);
 
 /* Message of the last error of this context ("" if none). Never NULL. */
 const char* swale_last_error(const swale_ctx* ctx);

@@ -72,6 +72,7 @@ def lib():
         L.swale_alpha_log.argtypes = [vp, i32, i64, vp]
         L.swale_get_alpha_log.argtypes = [vp, vp]
         L.swale_adjoint.argtypes = [vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
+        L.swale_adjoint_bytes.argtypes = [i64, i64, i64, i64, i32, P(ctypes.c_uint64)]
         L.swale_rhs_noalloc.argtypes = [P(SwaleConfig), vp, i64, vp, vp, vp, vp, vp, d, vp, vp, vp, P(d), vp]
         L.swale_set_timing.argtypes = [vp, i32]
         L.swale_get_timing.argtypes = [vp, vp, vp]
@@ -79,7 +80,7 @@ def lib():
                      "swale_get_flags", "swale_get_status", "swale_rhs", "swale_enqueue", "swale_set_timing",
                      "swale_get_timing", "swale_rhs_noalloc", "swale_batch_set_problem", "swale_batch_get_state",
                      "swale_set_tiles", "swale_get_tiles", "swale_autotune", "swale_alpha_log",
-                     "swale_get_alpha_log", "swale_adjoint"):
+                     "swale_get_alpha_log", "swale_adjoint", "swale_adjoint_bytes"):
             getattr(L, name).restype = ctypes.c_int
         L.swale_last_error.argtypes = [vp]
         L.swale_last_error.restype = ctypes.c_char_p
@@ -167,6 +168,14 @@ def swale_get_alpha_log(ctx, log):
 def swale_adjoint(ctx, nsteps, ckpt_every, G, gauges_x, h_obs, J=None, dJ_deta0=None, dJ_dhu0=None, dJ_db0=None):
     _check(ctx, lib().swale_adjoint(ctx, int(nsteps), int(ckpt_every), int(G), ptr(gauges_x), ptr(h_obs), ptr(J),
                                     ptr(dJ_deta0), ptr(dJ_dhu0), ptr(dJ_db0)))
+
+
+def swale_adjoint_bytes(B, Ntot, nsteps, ckpt_every, G):
+    n = ctypes.c_uint64(0)
+    code = lib().swale_adjoint_bytes(int(B), int(Ntot), int(nsteps), int(ckpt_every), int(G), ctypes.byref(n))
+    if code != SWALE_OK:
+        raise SwaleError(code, "swale_adjoint_bytes")
+    return n.value
 
 
 def swale_enqueue(ctx, nsteps):

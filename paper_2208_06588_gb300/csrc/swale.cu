@@ -968,6 +968,17 @@ struct StateCopy {
   DevScalars* S;
 };
 
+// Bytes of the device arrays swale_adjoint allocates (each dalloc adds 256 bytes of slack); the
+// list follows the allocations in swale_adjoint one for one.
+uint64_t adjoint_bytes(int64_t B, int64_t Nt, int64_t nsteps, int64_t ckpt_every, int32_t G) {
+  const int64_t NN = Nt + B, NE = Nt + 2 * B;
+  const int64_t C = std::min(ckpt_every, nsteps), nseg = (nsteps + C - 1) / C;
+  auto a = [](uint64_t n, uint64_t size) { return n * size + 256; };
+  const uint64_t copy = 4 * a(Nt, 8) + a(NN, 8) + a(B, sizeof(DevScalars));
+  return 15 * a(Nt, 8) + 8 * a(NE, 8) + (uint64_t)(nseg + C + 2) * copy + a((uint64_t)B * G, 8) +
+         a((uint64_t)nsteps * B * G, 8) + a(B, 8) + a((uint64_t)nsteps * B * 3, 8);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1003,6 +1014,13 @@ swale_status swale_get_alpha_log(swale_ctx* ctx, double* log) {
   SW_CUDA(ctx, cudaMemcpyAsync(log, ctx->alpha_log, (size_t)ctx->alpha_cap * ctx->B * 3 * sizeof(double),
                                cudaMemcpyDefault, ctx->stream));
   SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SWALE_OK;
+}
+
+swale_status swale_adjoint_bytes(int64_t B, int64_t Ntot, int64_t nsteps, int64_t ckpt_every, int32_t G,
+                                 uint64_t* bytes) {
+  if (!bytes || B < 1 || Ntot < 1 || nsteps < 1 || ckpt_every < 1 || G < 1) return SWALE_EINVAL;
+  *bytes = adjoint_bytes(B, Ntot, nsteps, ckpt_every, G);
   return SWALE_OK;
 }
 

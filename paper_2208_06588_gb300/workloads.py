@@ -29,7 +29,11 @@ def cell_averages(f, x, breaks=()):
     at the given discontinuity points so that piecewise-smooth data is integrated exactly
     enough."""
     x = np.asarray(x, dtype=np.float64)
-    a, b = x[:-1], x[1:]
+    return cell_averages_between(f, x[:-1], x[1:], breaks)
+
+
+def cell_averages_between(f, a, b, breaks=()):
+    """Averages of f over the intervals [a_i, b_i] (5-point Gauss-Legendre, split at breaks)."""
     pts = [a] + [np.clip(np.full_like(a, c), a, b) for c in sorted(breaks)] + [b]
     total = np.zeros_like(a)
     for lo, hi in zip(pts[:-1], pts[1:]):
@@ -259,16 +263,12 @@ class GaugeProblem:
     nsteps: int
 
 
-def gaussian_basin(N=65536, seed=MASTER_SEED + 4, n_gauss=4, n_basis=32, A=0.02, cfl=0.6):
-    """[0,1], reflective; b = sum of n_gauss Gaussians (heights U[0,0.5], centres U[0.1,0.9],
-    widths U[0.05,0.2]), scaled down to a maximum of 0.5 where the bumps stack higher; eta0 = 1 + sum_{k<n_basis} c_k exp(-(x - (k+1/2)/n_basis)^2 / (2 (1/(2 n_basis))^2))
-    with c_k ~ U[-0.01, 0.01]; hu = 0; sine motion x = xi + A sin(2 pi xi) sin(2 pi t), T = 1;
-    fixed dt = 0.9 CFL min J / alpha0 with alpha0 = max sqrt(g h) + 2 pi A (the CFL value at t = 0)."""
+def _gaussian_basin_fns(seed, n_gauss=4, n_basis=32):
+    """Bottom and initial surface functions of gaussian_basin for one seed."""
     rng = np.random.Generator(np.random.PCG64(seed))
     amp, cen, wid = rng.uniform(0, 0.5, n_gauss), rng.uniform(0.1, 0.9, n_gauss), rng.uniform(0.05, 0.2, n_gauss)
     coef = rng.uniform(-0.01, 0.01, n_basis)
     sig = 1.0 / (2 * n_basis)
-
     xs = np.linspace(0.0, 1.0, 4097)
     peak = float(sum(a * np.exp(-(xs - c) ** 2 / (2 * w * w)) for a, c, w in zip(amp, cen, wid)).max())
     amp = amp * min(1.0, 0.5 / peak)
@@ -277,8 +277,26 @@ def gaussian_basin(N=65536, seed=MASTER_SEED + 4, n_gauss=4, n_basis=32, A=0.02,
         return sum(a * np.exp(-(s - c) ** 2 / (2 * w * w)) for a, c, w in zip(amp, cen, wid))
 
     def etaf(s):
-        return 1.0 + sum(ck * np.exp(-(s - (k + 0.5) / n_basis) ** 2 / (2 * sig * sig)) for k, ck in enumerate(coef))
+        # Basis functions more than 12 widths away contribute below exp(-72) and are skipped;
+        # s is sorted (quadrature points of increasing cells), so each window is a slice.
+        s = np.asarray(s, dtype=np.float64)
+        acc = np.zeros_like(s)
+        for k, ck in enumerate(coef):
+            c = (k + 0.5) / n_basis
+            lo, hi = np.searchsorted(s, [c - 12 * sig, c + 12 * sig])
+            acc[lo:hi] += ck * np.exp(-(s[lo:hi] - c) ** 2 / (2 * sig * sig))
+        return 1.0 + acc
 
+    return bf, etaf, dict(coef=coef, amp=amp, cen=cen, wid=wid)
+
+
+def gaussian_basin(N=65536, seed=MASTER_SEED + 4, n_gauss=4, n_basis=32, A=0.02, cfl=0.6):
+    """[0,1], reflective; b = sum of n_gauss Gaussians (heights U[0,0.5], centres U[0.1,0.9],
+    widths U[0.05,0.2]), scaled down to a maximum of 0.5 where the bumps stack higher;
+    eta0 = 1 + sum_{k<n_basis} c_k exp(-(x - (k+1/2)/n_basis)^2 / (2 (1/(2 n_basis))^2)) with
+    c_k ~ U[-0.01, 0.01]; hu = 0; sine motion x = xi + A sin(2 pi xi) sin(2 pi t), T = 1;
+    fixed dt = 0.9 CFL min J / alpha0 with alpha0 = max sqrt(g h) + 2 pi A (the CFL value at t = 0)."""
+    bf, etaf, meta = _gaussian_basin_fns(seed, n_gauss, n_basis)
     x = _uniform(0.0, 1.0, N)
     b = cell_averages(bf, x)
     E = cell_averages(etaf, x)
@@ -288,8 +306,16 @@ def gaussian_basin(N=65536, seed=MASTER_SEED + 4, n_gauss=4, n_basis=32, A=0.02,
     dt = 0.9 * cfl * float(np.diff(x).min()) / alpha0
     pr = Problem(name="gaussian_basin", x=x, h=h, hu=np.zeros(N), b=b, E=E, profile=prof, bc="reflective",
                  mesh="profile", mesh_T=1.0, cfl=cfl, dt_fixed=dt)
-    pr.meta.update(coef=coef, amp=amp, cen=cen, wid=wid)
+    pr.meta.update(meta)
     return pr
+
+
+def _gauge_depths(N, seed, gx):
+    """Initial cell-average depth of gaussian_basin(N, seed) in the cells that hold gx."""
+    bf, etaf, _ = _gaussian_basin_fns(seed)
+    x = _uniform(0.0, 1.0, N)
+    idx = np.minimum((gx * N).astype(np.int64), N - 1)
+    return cell_averages_between(etaf, x[idx], x[idx + 1]) - cell_averages_between(bf, x[idx], x[idx + 1])
 
 
 def gauge_problem(N=65536, nsteps=4000, G=16, seed=MASTER_SEED + 4):
@@ -298,8 +324,38 @@ def gauge_problem(N=65536, nsteps=4000, G=16, seed=MASTER_SEED + 4):
     of the observation run's initial depth at the gauges, held for every step (a synthetic
     stand-in for recorded gauge series)."""
     pr = gaussian_basin(N=N, seed=seed)
-    ob = gaussian_basin(N=N, seed=seed + 1)
     gx = (np.arange(G) + 0.5) / G
-    idx = np.minimum((gx * N).astype(np.int64), N - 1)
-    h0 = ob.h[idx]
+    h0 = _gauge_depths(N, seed + 1, gx)
     return GaugeProblem(problem=pr, gauges=gx, h_obs=np.tile(h0, (nsteps, 1)), nsteps=nsteps)
+
+
+@dataclass
+class GaugeBatch:
+    batch: Batch
+    gauges: np.ndarray   # B*G gauge positions (instance-major)
+    h_obs: np.ndarray    # nsteps x B x G observed depths
+    nsteps: int
+
+
+def many_gauge_basins(B=512, n_min=1024, n_max=32768, nsteps=2000, G=16, seed=MASTER_SEED + 5):
+    """B instances of gaussian_basin, cell counts ~ U{n_min..n_max}, each with its own seed (and
+    its own observation seed) drawn from one SeedSequence; gauges and h_obs as gauge_problem.
+    Every instance advances with its own CFL dt (CFL 0.6; the fixed dt of gaussian_basin is
+    dropped, since a batch shares one configuration)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = rng.integers(n_min, n_max + 1, size=B)
+    seeds = rng.integers(0, 2 ** 31, size=B)
+    gx = (np.arange(G) + 0.5) / G
+    parts, obs = [], []
+    for n, sd in zip(sizes, seeds):
+        n, sd = int(n), int(sd)
+        parts.append(gaussian_basin(N=n, seed=sd))
+        obs.append(_gauge_depths(n, sd + 1, gx))
+    off = np.zeros(B + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    cat = lambda f: np.concatenate([f(p) for p in parts])
+    bt = Batch(name="many_gauge_basins", off=off, x=cat(lambda p: p.x), h=cat(lambda p: p.h), hu=cat(lambda p: p.hu),
+               b=cat(lambda p: p.b), E=cat(lambda p: p.E), profile=cat(lambda p: p.profile),
+               cfl=np.full(B, 0.6))
+    h_obs = np.broadcast_to(np.stack(obs)[None], (nsteps, B, G)).copy()
+    return GaugeBatch(batch=bt, gauges=np.tile(gx, B), h_obs=h_obs, nsteps=nsteps)

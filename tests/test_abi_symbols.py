@@ -49,3 +49,16 @@ def test_autograd_wrapper_has_no_cpu_path():
     z = torch.zeros(8, dtype=torch.float64, requires_grad=True)
     with pytest.raises(ValueError, match="CUDA"):
         gauge_misfit(z, z, z, torch.linspace(0, 1, 9), None, [0.5], [[0.0]], B.make_config(), 1)
+
+
+def test_adjoint_bytes_formula():
+    """swale_adjoint_bytes is host arithmetic: 5 (ceil(K/C) + C + 2) + 23 doubles per cell, plus
+    per-instance scalars, gauges, observations and the viscosity log."""
+    from paper_2208_06588_gb300 import binding as B
+    Nt, Bn, K, C, G = 1_000_000, 4, 4000, 64, 16
+    n = B.swale_adjoint_bytes(Bn, Nt, K, C, G)
+    per_cell = 8 * (5 * (-(-K // C) + C + 2) + 23)
+    assert per_cell * Nt <= n <= per_cell * Nt + 8 * (K * Bn * (G + 3)) + 2_000_000
+    assert B.swale_adjoint_bytes(Bn, Nt, K, K, G) > B.swale_adjoint_bytes(Bn, Nt, K, 64, G)
+    with pytest.raises(B.SwaleError):
+        B.swale_adjoint_bytes(0, Nt, K, C, G)
