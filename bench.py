@@ -139,14 +139,17 @@ def cpu_oracle_rate(n_cells, steps):
     return n_cells * r["steps"] / dt, dt
 
 
-def bench_batched(args, stream, dev):
+def bench_batched(args, stream, dev, rank=0, ws=1):
     """Batched forward: 4096 instances, 256..16384 cells each, one launch per kernel per stage for
     all instances (autotuned tile sizes), against the plain per-instance launch loop on the same
-    512-instance subset."""
+    512-instance subset. With several ranks each takes a contiguous, cell-balanced share of the
+    instances (no data exchange); the time is the max over ranks."""
     import torch
     from paper_2208_06588_gb300 import binding as B
+    from paper_2208_06588_gb300 import shard
     from paper_2208_06588_gb300 import workloads as W
-    bt = W.many_basins(B=4096)
+    bt_all = W.many_basins(B=4096)
+    bt = shard.subset(bt_all, *shard.partition(bt_all.off, ws, rank)) if ws > 1 else bt_all
     cfg = B.make_config(g=bt.g, eps_weno=bt.eps_weno, mesh_T=bt.mesh_T, bc=bt.bc, mesh=bt.mesh, cfl=0.6)
     s = B.Solver(cfg, stream.cuda_stream)
     s.set_batch(bt)
@@ -156,18 +159,20 @@ def bench_batched(args, stream, dev):
     B.swale_enqueue(s.ctx, 3)
     stream.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    shard.barrier()
     ev0.record(stream)
     B.swale_enqueue(s.ctx, args.batched_steps)
     ev1.record(stream)
     stream.synchronize()
-    ms = ev0.elapsed_time(ev1)
+    ms = shard.max_over_ranks(ev0.elapsed_time(ev1), dev)
     bits = s.status()[0]
     s.close()
-    ntot = int(bt.off[-1])
+    ntot = int(bt_all.off[-1])
     out = {"workload": "many_basins: 4096 instances, N_i ~ U{256..16384} (sum %d cells), reflective, sine mesh "
                        "motion A ~ U[0,0.05], CFL 0.6 / 0.08 (dry)" % ntot,
            "value": ntot * args.batched_steps / (ms * 1e-3), "unit": UNIT, "steps": args.batched_steps,
-           "ms_per_step": ms / args.batched_steps, "tiles": list(tiles), "status_bits": bits}
+           "ms_per_step": ms / args.batched_steps, "tiles": list(tiles), "status_bits": bits,
+           "parallelism": f"instances sharded over {ws} ranks" if ws > 1 else "single", "scaling": "weak"}
     # Same work, batched vs one context per instance (launches per instance and step).
     sub = 512
     sb = W.Batch(name="subset", off=bt.off[:sub + 1].copy(), x=bt.x[:int(bt.off[sub]) + sub],
@@ -226,13 +231,14 @@ def _timed(stream, fn):
     return ev0.elapsed_time(ev1)
 
 
-def bench_adjoint(args, stream):
+def bench_adjoint(args, stream, dev=None, ws=1):
     """Gradient of the gauge misfit (16 gauges) of the 65536-cell Gaussian basin over
     args.adjoint_steps steps, checkpoints every 64 steps: one swale_adjoint call with host
     observations and host gradients, against the forward alone over the same steps."""
     import torch
     from paper_2208_06588_gb300 import binding as B
     from paper_2208_06588_gb300 import workloads as W
+    from paper_2208_06588_gb300 import shard
     K, C = args.adjoint_steps, 64
     gp = W.gauge_problem(N=65536, nsteps=K, G=16)
     pr = gp.problem
@@ -252,14 +258,17 @@ def bench_adjoint(args, stream):
     s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
     B.swale_adjoint(s.ctx, min(K, 32), 8, G, gp.gauges, obs, J, gE, gM, gB)  # warm-up
     s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
-    ms = _timed(stream, lambda: B.swale_adjoint(s.ctx, K, C, G, gp.gauges, obs, J, gE, gM, gB))
+    shard.barrier()
+    ms = shard.max_over_ranks(_timed(stream, lambda: B.swale_adjoint(s.ctx, K, C, G, gp.gauges, obs, J, gE, gM, gB)),
+                              dev)
     bits = s.status()[0]
     s.close()
     adj_bytes = B.swale_adjoint_bytes(1, N, K, C, G)
     return {"workload": f"gaussian_basin N={N} [0,1] reflective, 4 Gaussian bumps, eta0 from 32 Gaussian basis "
                         f"functions, sine mesh motion A=0.02, fixed dt; {K} SSP-RK3 steps; 16 gauges",
             "metric": "cell-updates/s FP64 (forward + adjoint)", "unit": UNIT,
-            "value": N * K / (ms * 1e-3), "gradients_per_s": 1e3 / ms, "ms_per_gradient": ms,
+            "value": ws * N * K / (ms * 1e-3), "gradients_per_s": ws * 1e3 / ms, "ms_per_gradient": ms,
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single",
             "ckpt_every": C, "forward_only_ms": ms_fwd, "adjoint_over_forward": ms / ms_fwd,
             "forward_only_value": N * K / (ms_fwd * 1e-3),
             "peak_device_bytes": int(state_bytes + adj_bytes), "adjoint_scratch_bytes": int(adj_bytes),
@@ -267,15 +276,21 @@ def bench_adjoint(args, stream):
             "call": "swale_adjoint (host gauges, observations and gradients)"}
 
 
-def bench_batched_adjoint(args, stream):
+def bench_batched_adjoint(args, stream, dev=None, rank=0, ws=1):
     """Batched gradients: 512 Gaussian basins (N_i ~ U{1024..32768}, per-instance seeds and CFL
     dt), args.batched_adjoint_steps steps, checkpoints every 64 steps, all instances in the same
     launches; against one swale_adjoint call per instance on a 32-instance subset."""
     import torch
     from paper_2208_06588_gb300 import binding as B
     from paper_2208_06588_gb300 import workloads as W
+    from paper_2208_06588_gb300 import shard
     K, C, G = args.batched_adjoint_steps, 64, 16
     gb = W.many_gauge_basins(B=512, nsteps=K, G=G)
+    Nt_all, B_all = int(gb.batch.off[-1]), gb.batch.B
+    if ws > 1:  # a contiguous, cell-balanced share of the instances per rank
+        i0, i1 = shard.partition(gb.batch.off, ws, rank)
+        gb = W.GaugeBatch(batch=shard.subset(gb.batch, i0, i1), gauges=gb.gauges[i0 * G:i1 * G],
+                          h_obs=np.ascontiguousarray(gb.h_obs[:, i0:i1, :]), nsteps=K)
     bt = gb.batch
     Nt = int(bt.off[-1])
     cfg = B.make_config(g=bt.g, eps_weno=bt.eps_weno, mesh_T=bt.mesh_T, bc=bt.bc, mesh=bt.mesh, cfl=0.6)
@@ -293,7 +308,9 @@ def bench_batched_adjoint(args, stream):
     obs = np.ascontiguousarray(gb.h_obs)
     B.swale_adjoint(s.ctx, 8, 4, G, gb.gauges, obs, J, gE, gM, gB)  # warm-up
     s.set_batch(bt)
-    ms = _timed(stream, lambda: B.swale_adjoint(s.ctx, K, C, G, gb.gauges, obs, J, gE, gM, gB))
+    shard.barrier()
+    ms = shard.max_over_ranks(_timed(stream, lambda: B.swale_adjoint(s.ctx, K, C, G, gb.gauges, obs, J, gE, gM, gB)),
+                              dev)
     bits = s.status()[0]
     s.close()
     adj_bytes = B.swale_adjoint_bytes(bt.B, Nt, K, C, G)
@@ -302,7 +319,8 @@ def bench_batched_adjoint(args, stream):
                        f"seeds, CFL 0.6 dt per instance, 16 gauges each; {K} steps timed (of 2000 in the full "
                        f"case; the cost per step does not depend on the step count)",
            "metric": "cell-updates/s FP64 (forward + adjoint)", "unit": UNIT,
-           "value": Nt * K / (ms * 1e-3), "gradients_per_s": bt.B * 1e3 / ms, "steps": K, "ckpt_every": C,
+           "value": Nt_all * K / (ms * 1e-3), "gradients_per_s": B_all * 1e3 / ms, "steps": K, "ckpt_every": C,
+           "parallelism": f"instances sharded over {ws} ranks" if ws > 1 else "single",
            "forward_only_value": Nt * K / (ms_fwd * 1e-3), "adjoint_over_forward": ms / ms_fwd,
            "peak_device_bytes": int(state_bytes + adj_bytes), "peak_device_bytes_2000_steps": int(state_bytes + full_bytes),
            "status_bits": bits}
@@ -448,6 +466,16 @@ def main():
            "d2h_bytes_per_step": d2h / args.steps,
            "call": "swale_create + swale_set_problem(host) + swale_advance(K) + swale_get_state(host) + destroy"}
 
+    # ---- batched and adjoint sections (every rank: sharded batches, replicated single instance) ----
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(args, stream, dev, rank, ws)
+    adjoint = batched_adjoint = None
+    if not args.no_adjoint:
+        adjoint = bench_adjoint(args, stream, dev, ws)
+        if not args.no_batched_adjoint:
+            batched_adjoint = bench_batched_adjoint(args, stream, dev, rank, ws)
+
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
@@ -474,16 +502,6 @@ def main():
         rate, secs = cpu_oracle_rate(N_CELLS, 3)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"3 SSP-RK3 steps of the full 2^20-cell workload ({secs:.1f} s, one thread)"}
-
-    batched = None
-    if not args.no_batched:
-        batched = bench_batched(args, stream, dev)
-
-    adjoint = batched_adjoint = None
-    if not args.no_adjoint:
-        adjoint = bench_adjoint(args, stream)
-        if not args.no_batched_adjoint:
-            batched_adjoint = bench_batched_adjoint(args, stream)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
