@@ -101,9 +101,8 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
       for (int a = 0; a < 3; ++a) v0[v][a] = V[v][a + 1];
     swale::EdgeState o;
     uint8_t flag;
-    CD wl, wr;
     uint32_t st = 0;
-    swale::recon_cell(P, h5, v0, DD, CD(dxmax), o, flag, wl, wr, st);
+    swale::recon_cell(P, h5, v0, DD, CD(dxmax), o, flag, st);
     add_to(rec);
     cls[flag] += 1;
     // Update: one flux (the cell's right interface, with its own edges standing in for the

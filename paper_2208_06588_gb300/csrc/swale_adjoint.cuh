@@ -23,10 +23,10 @@ struct EdgeAdj {
 // Adjoint of interface_flux: adjoints of the eight edge inputs from those of the four fluxes.
 SWALE_HD EdgeAdj interface_flux_rev(real g, real alpha, real w, real EL, real ER, real BL, real BR, real hL,
                                     real hR, real uL, real uR, const Flux& Fb) {
-  const bool selR = BR > BL;
+  const bool selR = dlt(BL, BR);
   const real bstar = selR ? BR : BL;
   const real aL = EL - bstar, aR = ER - bstar;
-  const bool pL = aL > 0.0, pR = aR > 0.0;
+  const bool pL = gt0(aL), pR = gt0(aR);
   const real sL = pL ? aL : real(0.0), sR = pR ? aR : real(0.0);
   const real mL = sL * uL, mR = sR * uR;
   const real hg = 0.5 * g;
@@ -169,7 +169,7 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real v
   G1[1][2] = h2;
   G2[1][2] = -(h2 * h3);
   const real Sa = s012 + h3, Sb = Sa + h4, Sc = s12 + h3 + h4;
-  const real inv = 1.0 / (Sa * Sb * Sc);
+  const real inv = recip(Sa * Sb * Sc);
   const real iab = Sc * inv, icb = Sa * inv;
   real d[2][3];
   d[1][2] = h3 * (h3 + h4) * iab;
@@ -191,7 +191,7 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real v
   const real tdiff = beta[0] - beta[2];
   const real tau = dabs(tdiff);
   const real den = (beta[0] + beta[1] + beta[2]) * (1.0 / 3.0) + P.eps_weno;
-  const uint8_t flag = (tau <= 0.5 * den) ? 0 : ((tau >= den) ? 2 : 1);
+  const uint8_t flag = le_nn(tau, 0.5 * den) ? 0 : (le_nn(den, tau) ? 2 : 1);
   real phi[2][3], phiN[2][3], al[2][3], q[3], e[3], isE[2], Mg = 0.0;
   if (flag == 0) {
     for (int ee = 0; ee < 2; ++ee)
@@ -201,7 +201,7 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real v
     e[1] = beta[1] + P.eps_weno;
     e[2] = beta[2] + P.eps_weno;
     const real e01 = e[0] * e[1];
-    const real ie = tau / (e01 * e[2]);
+    const real ie = tau * recip(e01 * e[2]);
     q[0] = e[1] * e[2] * ie;
     q[1] = e[0] * e[2] * ie;
     q[2] = e01 * ie;
@@ -210,7 +210,7 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real v
     for (int ee = 0; ee < 2; ++ee)
       for (int r = 0; r < 3; ++r) al[ee][r] = d[ee][r] * X[r];
     const real sL = al[0][0] + al[0][1] + al[0][2], sR = al[1][0] + al[1][1] + al[1][2];
-    const real is = 1.0 / (sL * sR);
+    const real is = recip(sL * sR);
     isE[0] = sR * is;
     isE[1] = sL * is;
     for (int r = 0; r < 3; ++r) {
@@ -218,7 +218,7 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real v
       phiN[1][r] = al[1][r] * isE[1];
     }
     if (flag == 1) {
-      Mg = 2.0 * (tau / den) - 1.0;
+      Mg = 2.0 * (tau * recip(den)) - 1.0;
       for (int ee = 0; ee < 2; ++ee)
         for (int r = 0; r < 3; ++r) phi[ee][r] = Mg * phiN[ee][r] + (1.0 - Mg) * d[ee][r];
     } else {
@@ -238,28 +238,28 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real v
       ev[v][ee] = s;
     }
   const real hb0 = v0[0][2] - v0[2][2];
-  const real hbar = dmax(hb0, 0.0);
+  const real hbar = pos0(hb0);
   const real hL0 = ev[0][0] - ev[2][0], hR0 = ev[0][1] - ev[2][1];
   const real delta = (12.0 * hbar - hL0 - hR0) * 0.1;
-  const bool selR1 = hR0 < hL0;
+  const bool selR1 = dlt(hR0, hL0);
   const real m1 = selR1 ? hR0 : hL0;
-  const bool selD = delta < m1;
+  const bool selD = dlt(delta, m1);
   const real mn = selD ? delta : m1;
-  const bool epsSel = hbar < P.eps_pp;  // epsv = min(eps_pp, hbar) selects hbar
+  const bool epsSel = dlt(hbar, P.eps_pp);  // epsv = min(eps_pp, hbar) selects hbar
   const real epsv = epsSel ? hbar : real(P.eps_pp);
   const real mL0 = ev[1][0], mR0 = ev[1][1], mbar = v0[1][2];
-  const bool active = mn < epsv;
+  const bool active = dlt(mn, epsv);
   real theta = 1.0, iD = 0.0;
   real hL = hL0, hR = hR0, mL = mL0, mR = mR0;
   if (active) {
-    iD = 1.0 / (hbar - mn);
+    iD = recip(hbar - mn);
     theta = (hbar - epsv) * iD;
     hL = theta * (hL0 - hbar) + hbar;
     hR = theta * (hR0 - hbar) + hbar;
     mL = theta * (mL0 - mbar) + mbar;
     mR = theta * (mR0 - mbar) + mbar;
   }
-  const bool wetL = hL > P.h_dry, wetR = hR > P.h_dry;
+  const bool wetL = dlt(P.h_dry, hL), wetR = dlt(P.h_dry, hR);
   // ---------------- reverse sweep ----------------
   for (int v = 0; v < 3; ++v)
     for (int a = 0; a < 3; ++a) v0b[v][a] = 0.0;
@@ -276,12 +276,12 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real v
   hRb = hRb - ob.BR;
   // u = m / h on wet edges
   if (wetL) {
-    const real iL = 1.0 / hL;
+    const real iL = recip(hL);
     mLb = mLb + ob.uL * iL;
     hLb = hLb - ob.uL * mL * iL * iL;
   }
   if (wetR) {
-    const real iR = 1.0 / hR;
+    const real iR = recip(hR);
     mRb = mRb + ob.uR * iR;
     hRb = hRb - ob.uR * mR * iR * iR;
   }
@@ -365,7 +365,7 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real v
   real betab[3] = {0, 0, 0};
   for (int r = 0; r < 3; ++r) {
     const real qb = 2.0 * q[r] * Xb[r];  // X = 1 + q^2
-    const real ier = 1.0 / e[r];
+    const real ier = recip(e[r]);
     taub = taub + qb * ier;              // q = tau / e_r
     betab[r] = betab[r] - qb * q[r] * ier;
   }

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(T) k_adj_rk(DevState D, AdjState A) {
     double* rv[3] = {A.rE, A.rM, A.rB};
     const double J0 = A.sJ[g];
     if (PH == 3) {
-      const double iJ3 = 1.0 / D.J0[g];  // J^{n+1} after the recomputed step
+      const double iJ3 = swale::recip(D.J0[g]);  // J^{n+1} after the recomputed step
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
         const double Y = lv[v][g] * iJ3;
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(T) k_adj_rk(DevState D, AdjState A) {
         rv[v][g] = (2.0 / 3.0) * dt * Y;
       }
     } else if (PH == 2) {
-      const double iJ2 = 1.0 / D.J2[g];
+      const double iJ2 = swale::recip(D.J2[g]);
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
         const double y = yv[v][g] + av[v][g] * iJ2;
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(T) k_adj_rk(DevState D, AdjState A) {
         yv[v][g] = 0.25 * y;
       }
     } else if (PH == 1) {
-      const double iJ1 = 1.0 / D.J1[g];
+      const double iJ1 = swale::recip(D.J1[g]);
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
         const double y = yv[v][g] + av[v][g] * iJ1;
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(T) k_adj_source(StepConst K, DevState D, AdjSt
     const double* B = Bg + cb;
     const double* Js = Jsg + cb;
     const double Jm = Js[jm], Jc = Js[j], Jp = Js[jp];
-    const swale::SourceGeom sg = swale::source_geom(Jm, Jc, 1.0 / Jm, 1.0 / Jc, 1.0 / Jp, D.ipair[eb + j],
+    const swale::SourceGeom sg = swale::source_geom(Jm, Jc, swale::recip(Jm), swale::recip(Jc), swale::recip(Jp), D.ipair[eb + j],
                                                     D.ipair[eb + j + 1], D.itri[eb + j + 1]);
     const int64_t ie = eb + j + 1;
     const double hd[5] = {E[jm] - B[jm], E[j] - B[j], E[jp] - B[jp], D.ehL[ie], D.ehR[ie]};

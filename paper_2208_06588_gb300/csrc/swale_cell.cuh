@@ -58,24 +58,75 @@ struct EdgeState {
   real EL, ER, BL, BR, hL, hR, uL, uR;
 };
 
+// ------------------------------------------------------------------------------------
+// Scalar helpers. A GB300 SM retires about two FP64 lanes per clock against 64 INT32 and
+// 128 FP32 lanes, and comparisons, min / max and divisions of doubles all occupy the FP64
+// pipe. On the device (double, no counting type) these helpers therefore compare IEEE bit
+// patterns on the integer pipe (an order-preserving key: the bits, with the magnitude bits
+// flipped for negative values) and form reciprocals from the hardware's 20-bit reciprocal
+// approximation refined by one cubic Newton step (y <- y (1 + e + e^2), e = 1 - x y), which
+// leaves a relative error below 2^-52 (3 FMAs instead of a full division). Zero, infinite and
+// subnormal arguments give NaN there; no caller passes them on valid data. Elsewhere they are
+// the plain operators. Ties of min / max return the first argument.
+// ------------------------------------------------------------------------------------
+#if defined(__CUDA_ARCH__) && !defined(SWALE_REAL)
+#define SWALE_INT_COMPARE 1
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+SWALE_HD double dmax(double a, double b) { return okey(b) > okey(a) ? b : a; }
+SWALE_HD double dmin(double a, double b) { return okey(b) < okey(a) ? b : a; }
+SWALE_HD bool dlt(double a, double b) { return okey(a) < okey(b); }
+// max(a, 0) (a negative zero gives +0).
+SWALE_HD double pos0(double a) { return __double_as_longlong(a) < 0 ? 0.0 : a; }
+// a > 0.
+SWALE_HD bool gt0(double a) { return __double_as_longlong(a) > 0; }
+// a <= b for a, b >= +0.
+SWALE_HD bool le_nn(double a, double b) {
+  return (unsigned long long)__double_as_longlong(a) <= (unsigned long long)__double_as_longlong(b);
+}
+// NaN, infinite or of magnitude above 1e300.
+SWALE_HD bool bad(double a) {
+  return ((unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull) > 0x7e37e43c8800759cull;
+}
+SWALE_HD double dabs(double a) { return fabs(a); }
+SWALE_HD double recip(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y, 1.0);
+  return fma(fma(e, e, e), y, y);
+}
+SWALE_HD double dsqrt(double a) { return sqrt(a); }
+#else
 SWALE_HD real dmax(real a, real b) { return (b > a) ? b : a; }
 SWALE_HD real dmin(real a, real b) { return (b < a) ? b : a; }
+SWALE_HD bool dlt(real a, real b) { return a < b; }
+SWALE_HD real pos0(real a) { return (real(0.0) > a) ? real(0.0) : a; }
+SWALE_HD bool gt0(real a) { return a > 0.0; }
+SWALE_HD bool le_nn(real a, real b) { return a <= b; }
 SWALE_HD real dabs(real a) { return a < 0.0 ? -a : a; }
+SWALE_HD bool bad(real a) { return !(a == a) || dabs(a) > 1.0e300; }
+SWALE_HD real recip(real x) { return 1.0 / x; }
 #ifdef SWALE_REAL
-SWALE_HD real rsqrt_(real a) { return swale_sqrt(a); }
+SWALE_HD real dsqrt(real a) { return swale_sqrt(a); }
 #else
-SWALE_HD real rsqrt_(real a) { return sqrt(a); }
+SWALE_HD real dsqrt(real a) { return sqrt(a); }
 #endif
+#endif
+
+// Wave speed |u| + sqrt(g max(h, 0)) of one limited edge state (Eq. alpha2D).
+SWALE_HD real wave_speed(real g, real h, real u) { return dabs(u) + dsqrt(g * pos0(h)); }
 
 // ------------------------------------------------------------------------------------
 // Shared per-pair and per-triple terms (Step 1): reciprocal widths and divided differences.
 // ------------------------------------------------------------------------------------
 // Pair of cells (m, m+1): 1 / (J_m + J_{m+1}).
-SWALE_HD real pair_recip(real Jm, real Jp) { return 1.0 / (Jm + Jp); }
+SWALE_HD real pair_recip(real Jm, real Jp) { return recip(Jm + Jp); }
 // D2 of one variable on the pair.
 SWALE_HD real pair_dd(real vm, real vp, real ip) { return (vp - vm) * ip; }
 // Triple centred at c: 1 / (J_{c-1} + J_c + J_{c+1}).
-SWALE_HD real triple_recip(real Jm, real Jc, real Jp) { return 1.0 / (Jm + Jc + Jp); }
+SWALE_HD real triple_recip(real Jm, real Jc, real Jp) { return recip(Jm + Jc + Jp); }
 // D3 of one variable on the triple from the D2 of its two pairs.
 SWALE_HD real triple_dd(real d2l, real d2r, real it) { return (d2r - d2l) * it; }
 
@@ -92,12 +143,12 @@ struct StencilDD {
 // Gauss-Lobatto rule) and the bottom re-derivation of the Remark in Sec. 4.3.
 //   h[5]      widths J_{j-2..j+2};   v0[v][a] averages of (eta, hu, b) on cells j-2+a, a = 0..2
 //   DD        shared divided differences;   dxmax  the global cell length (Step 1)
-// Outputs the limited edge state, the class, and |u| + sqrt(g h) at both edges.
+// Outputs the limited edge state and the class (wave speeds: wave_speed on the edge state).
+// Only the cell's own width is checked (every cell checks its own).
 SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
-                         real dxmax, EdgeState& o, uint8_t& flag, real& waveL, real& waveR, uint32_t& st) {
-  for (int k = 0; k < 5; ++k)
-    if (!(h[k] > 0.0)) st |= ST_EMESH;
+                         real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
   const real h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3], h4 = h[4];
+  if (!gt0(h2)) st |= ST_EMESH;
   const real dx = P.beta_dx_global ? dxmax : h2;
   // Node offsets relative to x_{j-1/2}: y0 = -(h0+h1), y1 = -h1, y2 = 0, y3 = h2,
   // y4 = h2+h3, y5 = h2+h3+h4. Newton-form factors of p_r at the left (x = 0) and right
@@ -122,7 +173,7 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3]
   const real Sa = s012 + h3;         // y4 - y0
   const real Sb = Sa + h4;           // y5 - y0
   const real Sc = s12 + h3 + h4;     // y5 - y1
-  const real inv = 1.0 / (Sa * Sb * Sc);
+  const real inv = recip(Sa * Sb * Sc);
   const real iab = Sc * inv, icb = Sa * inv;  // 1/(Sa Sb), 1/(Sc Sb)
   real d[2][3];
   d[1][2] = h3 * (h3 + h4) * iab;
@@ -131,7 +182,7 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3]
   d[0][0] = h1 * s01 * icb;
   d[0][1] = 1.0 - d[0][0] - d[0][2];
   d[1][1] = 1.0 - d[1][0] - d[1][2];
-  if (!(d[0][1] > 0.0) || !(d[1][1] > 0.0)) st |= ST_EWEIGHT;
+  if (!gt0(d[0][1]) || !gt0(d[1][1])) st |= ST_EWEIGHT;
   // Indicators of h = eta - b and hu, summed (shared weights). F[a] = 1.5 h2 - (y_a+y_{a+1}+y_{a+2}).
   const real F[3] = {1.5 * h2 + s01 + h1, 0.5 * h2 + h1, -(0.5 * h2 + h3)};
   const real c4 = 4.0 * dx * h2;
@@ -146,7 +197,7 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3]
   const real tau = dabs(beta[0] - beta[2]);
   const real den = (beta[0] + beta[1] + beta[2]) * (1.0 / 3.0) + P.eps_weno;  // beta^A + eps
   // gamma = tau / den: smooth if gamma <= 1/2, non-smooth if gamma >= 1.
-  flag = (tau <= 0.5 * den) ? 0 : ((tau >= den) ? 2 : 1);
+  flag = le_nn(tau, 0.5 * den) ? 0 : (le_nn(den, tau) ? 2 : 1);
   real phi[2][3];
   if (flag == 0) {
     for (int e = 0; e < 2; ++e)
@@ -155,7 +206,7 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3]
     // WENO-Z: alpha_r = d_r (1 + (tau / (beta_r + eps))^2), normalised per edge.
     const real e0 = beta[0] + P.eps_weno, e1 = beta[1] + P.eps_weno, e2 = beta[2] + P.eps_weno;
     const real e01 = e0 * e1;
-    const real ie = tau / (e01 * e2);
+    const real ie = tau * recip(e01 * e2);
     const real q[3] = {e1 * e2 * ie, e0 * e2 * ie, e01 * ie};
     real X[3];
     for (int r = 0; r < 3; ++r) X[r] = 1.0 + q[r] * q[r];
@@ -163,14 +214,14 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3]
     for (int e = 0; e < 2; ++e)
       for (int r = 0; r < 3; ++r) al[e][r] = d[e][r] * X[r];
     const real sL = al[0][0] + al[0][1] + al[0][2], sR = al[1][0] + al[1][1] + al[1][2];
-    const real is = 1.0 / (sL * sR);
+    const real is = recip(sL * sR);
     const real isL = sR * is, isR = sL * is;
     for (int r = 0; r < 3; ++r) {
       phi[0][r] = al[0][r] * isL;
       phi[1][r] = al[1][r] * isR;
     }
     if (flag == 1) {
-      const real Mg = 2.0 * (tau / den) - 1.0;
+      const real Mg = 2.0 * (tau * recip(den)) - 1.0;
       for (int e = 0; e < 2; ++e)
         for (int r = 0; r < 3; ++r) phi[e][r] = Mg * phi[e][r] + (1.0 - Mg) * d[e][r];
     }
@@ -188,15 +239,15 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3]
     }
   // Limiter on h = eta - b with the Gauss-Lobatto mean delta; hu scaled by the same theta.
   real hbar = v0[0][2] - v0[2][2];
-  if (hbar < -P.eps_pp) st |= ST_NEGDEPTH;
-  hbar = dmax(hbar, 0.0);
+  if (dlt(hbar, -P.eps_pp)) st |= ST_NEGDEPTH;
+  hbar = pos0(hbar);
   real hL = ev[0][0] - ev[2][0], hR = ev[0][1] - ev[2][1];
   const real delta = (12.0 * hbar - hL - hR) * 0.1;
   const real mn = dmin(dmin(hL, hR), delta);
   const real epsv = dmin(P.eps_pp, hbar);
   real mL = ev[1][0], mR = ev[1][1];
-  if (mn < epsv) {
-    const real theta = (hbar - epsv) / (hbar - mn);
+  if (dlt(mn, epsv)) {
+    const real theta = (hbar - epsv) * recip(hbar - mn);
     const real mbar = v0[1][2];
     hL = theta * (hL - hbar) + hbar;
     hR = theta * (hR - hbar) + hbar;
@@ -210,16 +261,13 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3]
   o.BL = ev[0][0] - hL;
   o.BR = ev[0][1] - hR;
   // Velocities with one division: u_L = m_L h_R' / (h_L' h_R'), dry edges (h <= h_dry) -> 0.
-  const bool wetL = hL > P.h_dry, wetR = hR > P.h_dry;
+  const bool wetL = dlt(P.h_dry, hL), wetR = dlt(P.h_dry, hR);
   const real hLs = wetL ? hL : real(1.0), hRs = wetR ? hR : real(1.0);
-  const real ihh = 1.0 / (hLs * hRs);
+  const real ihh = recip(hLs * hRs);
   o.uL = wetL ? mL * hRs * ihh : real(0.0);
   o.uR = wetR ? mR * hLs * ihh : real(0.0);
-  waveL = dabs(o.uL) + rsqrt_(P.g * dmax(hL, 0.0));
-  waveR = dabs(o.uR) + rsqrt_(P.g * dmax(hR, 0.0));
   // NaN propagates into the comparisons as false: catch it explicitly.
-  const real chk = o.EL + o.ER + o.hL + o.hR + mL + mR;
-  if (!(chk == chk) || dabs(chk) > 1.0e300) st |= ST_NONFINITE;
+  if (bad(o.EL) || bad(o.ER) || bad(hL) || bad(hR) || bad(mL) || bad(mR)) st |= ST_NONFINITE;
 }
 
 // ------------------------------------------------------------------------------------
@@ -233,7 +281,7 @@ struct Flux {
 SWALE_HD Flux interface_flux(real g, real alpha, real w, real EL, real ER, real BL, real BR, real hL,
                              real hR, real uL, real uR) {
   const real bstar = dmax(BL, BR);
-  const real sL = dmax(0.0, EL - bstar), sR = dmax(0.0, ER - bstar);
+  const real sL = pos0(EL - bstar), sR = pos0(ER - bstar);
   const real mL = sL * uL, mR = sR * uR;
   Flux f;
   // Hat-H^(1)(q*) + theta simplifies exactly to this expression.

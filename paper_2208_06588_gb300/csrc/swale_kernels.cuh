@@ -122,35 +122,80 @@ __device__ __forceinline__ int64_t ghost(int64_t i, int64_t N, int bc) {
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
 
-// Block-wide max of a non-negative double, one atomicMax per block.
+// Block-wide max / min of non-negative doubles, one atomicMax / atomicMin per block. The bit
+// patterns of doubles >= +0 order like unsigned integers, so the reductions run on the integer
+// pipe (the FP64 pipe is the bottleneck of the stage kernels). A NaN wins the max.
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
+
 __device__ __forceinline__ void block_max_to(unsigned long long* dst, double v) {
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ unsigned long long red[32];
+  unsigned long long b = dbits(v);
+  for (int o = 16; o > 0; o >>= 1) b = umax64(b, __shfl_xor_sync(0xffffffffu, b, o));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = v;
+  if (lane == 0) red[wid] = b;
   __syncthreads();
   if (wid == 0) {
     const int nw = blockDim.x >> 5;
-    v = lane < nw ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) atomicMax(dst, dbits(v));
+    b = lane < nw ? red[lane] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) b = umax64(b, __shfl_xor_sync(0xffffffffu, b, o));
+    if (lane == 0) atomicMax(dst, b);
   }
   __syncthreads();
 }
 
 __device__ __forceinline__ void block_min_to(unsigned long long* dst, double v) {
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ unsigned long long red[32];
+  unsigned long long b = dbits(v);
+  for (int o = 16; o > 0; o >>= 1) b = umin64(b, __shfl_xor_sync(0xffffffffu, b, o));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = v;
+  if (lane == 0) red[wid] = b;
   __syncthreads();
   if (wid == 0) {
     const int nw = blockDim.x >> 5;
-    v = lane < nw ? red[lane] : INFINITY;
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) atomicMin(dst, dbits(v));
+    b = lane < nw ? red[lane] : dbits(INFINITY);
+    for (int o = 16; o > 0; o >>= 1) b = umin64(b, __shfl_xor_sync(0xffffffffu, b, o));
+    if (lane == 0) atomicMin(dst, b);
   }
   __syncthreads();
+}
+
+// Exact maximum of the edge wave speeds (Eq. alpha2D) of a block's cells with few FP64
+// operations: an FP32 estimate of every edge's |u| + sqrt(g h) (relative error below 2^-21)
+// gives the block's FP32 maximum; only edges within 2^-16 of it can hold the exact maximum, and
+// only those are evaluated in FP64 (in a warp, one edge per lane first, then the rare second
+// one). When the FP32 maximum is below 1e-10 every edge is evaluated. Returns this thread's
+// contribution to the exact block maximum (0 for non-candidates).
+template <int T>
+__device__ __forceinline__ double block_wave(double g, bool useL, bool useR, double hL, double uL, double hR,
+                                             double uR) {
+  __shared__ unsigned int wmax[T / 32];
+  const float gf = (float)g;
+  const float fl = useL ? fabsf((float)uL) + __fsqrt_rn(gf * fmaxf((float)hL, 0.0f)) : 0.0f;
+  const float fr = useR ? fabsf((float)uR) + __fsqrt_rn(gf * fmaxf((float)hR, 0.0f)) : 0.0f;
+  const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fl, fr)));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  unsigned bm = 0;
+#pragma unroll
+  for (int w = 0; w < T / 32; ++w) bm = bm > wmax[w] ? bm : wmax[w];
+  const float bmf = __uint_as_float(bm);
+  const float thr = (bmf < 1e-10f) ? 0.0f : bmf * (1.0f - 1.0f / 65536.0f);
+  const bool cl = useL && fl >= thr, cr = useR && fr >= thr;
+  double wave = 0.0;
+  const bool c1 = cl || cr;
+  if (__any_sync(0xffffffffu, c1)) {
+    const bool right = cr && (!cl || fr > fl);
+    const double w1 = swale::wave_speed(g, right ? hR : hL, right ? uR : uL);
+    wave = c1 ? w1 : 0.0;
+  }
+  const bool c2 = cl && cr;
+  if (__any_sync(0xffffffffu, c2)) {
+    const bool right = !(fr > fl);  // the edge the first pass did not take
+    const double w2 = swale::wave_speed(g, right ? hR : hL, right ? uR : uL);
+    if (c2 && w2 > wave) wave = w2;
+  }
+  return wave;
 }
 
 __device__ __forceinline__ void block_or_status(unsigned int* dst, uint32_t st) {
@@ -321,7 +366,8 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
     }
     __syncthreads();
     const int64_t c = c0 + tid;
-    double wave = 0.0;
+    double wave = 0.0, ehL = 0.0, euL = 0.0, ehR = 0.0, euR = 0.0;
+    bool useL = false, useR = false;
     uint32_t st = 0;
     if (c <= N) {
       double h[5], v0[3][3];
@@ -340,8 +386,7 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
       const double dxmax = bitsd(S->Jmax[STAGE - 1]);
       EdgeState o;
       uint8_t flag;
-      double wl, wr;
-      swale::recon_cell(K.sc, h, v0, DD, dxmax, o, flag, wl, wr, st);
+      swale::recon_cell(K.sc, h, v0, DD, dxmax, o, flag, st);
       const int64_t idx = eb + c + 1;
       D.eEL[idx] = o.EL;
       D.eER[idx] = o.ER;
@@ -355,12 +400,15 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
       D.itri[idx] = sIT[tid + 1];   // triple centred at c
       if (STAGE == 1 && MODE == 0) D.flags[idx] = flag;
       // Edges that touch interfaces 0..N only.
-      if (c == -1) wave = wr;
-      else if (c == N) wave = wl;
-      else wave = fmax(wl, wr);
-      if (!(wave == wave)) st |= swale::ST_NONFINITE;
+      useL = (c != -1);
+      useR = (c != N);
+      ehL = o.hL;
+      euL = o.uL;
+      ehR = o.hR;
+      euR = o.uR;
     }
     if (MODE == 1) continue;
+    wave = block_wave<T>(K.sc.g, useL, useR, ehL, euL, ehR, euR);
     block_or_status(&S->status, st);
     block_max_to(&S->A[STAGE - 1], wave);
     if (STAGE == 1) {
@@ -488,7 +536,7 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
         const int64_t s = ghost(c, N, K.bc);
         const double jv = Js[s];
         sJ[i] = jv;
-        siJ[i] = 1.0 / jv;
+        siJ[i] = swale::recip(jv);
         sH[i] = E[s] - B[s];
         sB[i] = B[s];
       }
@@ -524,12 +572,12 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
           D.J2[g] = J2;
           jmaxa = J1;
           jmaxb = J2;
-          if (!(J1 > 0.0) || !(J2 > 0.0)) st |= swale::ST_EMESH;
+          if (!swale::gt0(J1) || !swale::gt0(J2)) st |= swale::ST_EMESH;
           const double yE = J0 * D.E0[g] + dt * RE, yM = J0 * D.M0[g] + dt * RM, yB = J0 * D.B0[g] + dt * RB;
           D.YE[g] = yE;
           D.YM[g] = yM;
           D.YB[g] = yB;
-          const double inv = 1.0 / J1;
+          const double inv = swale::recip(J1);
           D.Ea[g] = yE * inv;
           D.Ma[g] = yM * inv;
           D.Ba[g] = yB * inv;
@@ -540,17 +588,17 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
           D.YE[g] = yE;
           D.YM[g] = yM;
           D.YB[g] = yB;
-          const double inv = 1.0 / D.J2[g];
+          const double inv = swale::recip(D.J2[g]);
           D.Eb[g] = yE * inv;
           D.Mb[g] = yM * inv;
           D.Bb[g] = yB * inv;
         } else {
           const double J3 = (1.0 / 3.0) * J0 + (2.0 / 3.0) * D.J2[g] + (2.0 / 3.0) * dt * dw;
-          if (!(J3 > 0.0)) st |= swale::ST_EMESH;
+          if (!swale::gt0(J3)) st |= swale::ST_EMESH;
           const double yE = (1.0 / 3.0) * (J0 * D.E0[g]) + (2.0 / 3.0) * (D.YE[g] + dt * RE);
           const double yM = (1.0 / 3.0) * (J0 * D.M0[g]) + (2.0 / 3.0) * (D.YM[g] + dt * RM);
           const double yB = (1.0 / 3.0) * (J0 * D.B0[g]) + (2.0 / 3.0) * (D.YB[g] + dt * RB);
-          const double inv = 1.0 / J3;
+          const double inv = swale::recip(J3);
           const double En = yE * inv, Mn = yM * inv, Bn = yB * inv;
           D.E0[g] = En;
           D.M0[g] = Mn;
@@ -560,8 +608,7 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
           jminb = J3;
           D.x[nb + j] += dt * wl;
           if (j == N - 1) D.x[nb + N] += dt * wr;
-          const double chk = En + Mn + Bn;
-          if (!(chk == chk) || fabs(chk) > 1.0e300) st |= swale::ST_NONFINITE;
+          if (swale::bad(En) || swale::bad(Mn) || swale::bad(Bn)) st |= swale::ST_NONFINITE;
         }
       }
     }
