@@ -139,6 +139,37 @@ def cpu_oracle_rate(n_cells, steps):
     return n_cells * r["steps"] / dt, dt
 
 
+def _oracle_instance(job):
+    """One batched instance advanced by the CPU oracle (runs in a spawned worker process)."""
+    import oracle
+    x, E, hu, b, prof, cfl, steps = job
+    st = oracle.State(E, hu, b, np.diff(x), x)
+    P = oracle.Params(cfl=cfl, bc="reflective", mesh="profile", mesh_T=1.0)
+    return oracle.run(P, st, prof, nsteps=steps)["steps"] * E.size
+
+
+def cpu_oracle_batched_rate(n_inst=1024, steps=5):
+    """The CPU oracle as it stands on the batched workload's first n_inst instances, one
+    instance per task over a spawned process pool with one worker per available core."""
+    import multiprocessing as mp
+    from paper_2208_06588_gb300 import workloads as W
+    bt = W.many_basins(B=4096)
+    jobs = []
+    for i in range(n_inst):
+        pr = bt.instance(i)
+        jobs.append((pr.x, pr.E, pr.hu, pr.b, pr.profile, pr.cfl, steps))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_instance, jobs[:cores])  # start-up and library load outside the timing
+        t0 = time.perf_counter()
+        done = sum(pool.map(_oracle_instance, jobs, chunksize=1))
+        el = time.perf_counter() - t0
+    cells = int(bt.off[n_inst])
+    return {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} SSP-RK3 steps of the first {n_inst} instances of the batched workload ({cells} cells, "
+                      f"{el:.1f} s), one instance per task on {cores} worker processes"}
+
+
 def bench_batched(args, stream, dev, rank=0, ws=1):
     """Batched forward: 4096 instances, 256..16384 cells each, one launch per kernel per stage for
     all instances (autotuned tile sizes), against the plain per-instance launch loop on the same
@@ -502,6 +533,8 @@ def main():
         rate, secs = cpu_oracle_rate(N_CELLS, 3)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"3 SSP-RK3 steps of the full 2^20-cell workload ({secs:.1f} s, one thread)"}
+        if batched is not None:
+            batched["cpu_baseline"] = cpu_oracle_batched_rate()
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
