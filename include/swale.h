@@ -199,6 +199,18 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
                                const double* M, const double* B, const double* J, const double* w, double alpha,
                                double* RE, double* RM, double* RB, double* A_out, uint8_t* flags);
 
+/* Bottom by L2 projection (Eq. baverage, Sec. 3.3) instead of its evolution by Eq. bottomrk:
+ * b(x) is the piecewise polynomial with npieces pieces on breaks[npieces + 1] (increasing,
+ * covering every instance's domain), piece p being sum_{k<=degree} coef[p (degree+1) + k]
+ * (x - breaks[p])^k (degree <= 8; host or device arrays, copied). The bottom average of every
+ * cell is then the exact average of b over the cell on each stage mesh (t_n, t_{n+1},
+ * t_{n+1/2}) and after every step; the bottom averages passed to swale_set_problem should be
+ * that projection at t = 0. All instances of a batch share b. npieces = 0 returns to Eq.
+ * bottomrk; a new problem also does. Needs a problem set; not available with swale_adjoint.
+ * Errors: SWALE_EINVAL (sizes, order, coverage, non-finite values), SWALE_ENOMEM, SWALE_ECUDA. */
+swale_status swale_set_bottom_function(swale_ctx* ctx, int32_t npieces, int32_t degree, const double* breaks,
+                                       const double* coef);
+
 /* Stage viscosities alpha (Eq. alpha2D) of the next nsteps steps, 3 per step and instance, in
  * a log the context owns: mode 1 records them, mode 2 replays `log` (nsteps * B * 3 values,
  * host or device) instead of computing them, mode 0 turns the log off. Rows count from the

@@ -67,6 +67,10 @@ def lib():
         L.orc_tangent.argtypes = [P(d), P(i32), i64, P(d), P(d), P(d), P(d), P(d), P(d), P(d), i64, P(d), P(d),
                                   P(d), P(d), P(d)]
         L.orc_tangent.restype = u32
+        L.orc_set_bottom.argtypes = [i32, i32, P(d), P(d)]
+        L.orc_set_bottom.restype = None
+        L.orc_bottom_average.argtypes = [P(d), P(i32), d, d]
+        L.orc_bottom_average.restype = d
         _lib = L
     return _lib
 
@@ -95,12 +99,27 @@ class Params:
     mesh: str = "static"
     gauss_half: int = 24
     beta_dx_global: int = 1
+    # L2-projection bottom (Eq. baverage): (breaks[npieces+1], coef[npieces, deg+1]) of a
+    # piecewise polynomial b(x) = sum_k coef[p, k] (x - breaks[p])^k, or None to evolve b by
+    # Eq. bottomrk.
+    bottom: tuple | None = None
 
     def arrays(self):
         p = np.array([self.g, self.cfl, self.eps_weno, self.eps_pp, self.h_dry, self.mesh_T, self.gauss_sigma,
                       self.t_end, self.dt_fixed], dtype=np.float64)
-        ip = np.array([BC[self.bc], MESH[self.mesh], self.gauss_half, self.beta_dx_global], dtype=np.int32)
+        mode = 0
+        if self.bottom is not None:
+            br, cf = _f64(self.bottom[0]), np.atleast_2d(_f64(self.bottom[1]))
+            lib().orc_set_bottom(cf.shape[0], cf.shape[1] - 1, _p(br), _p(np.ascontiguousarray(cf)))
+            mode = 1
+        ip = np.array([BC[self.bc], MESH[self.mesh], self.gauss_half, self.beta_dx_global, mode], dtype=np.int32)
         return p, ip
+
+
+def bottom_average(params: Params, a, c):
+    """Average of the projection-mode bottom over [a, c]."""
+    p, ip = params.arrays()
+    return lib().orc_bottom_average(_p(p), _p(ip, ctypes.c_int32), float(a), float(c))
 
 
 def weno_coeffs(w5):

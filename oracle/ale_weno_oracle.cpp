@@ -46,7 +46,17 @@ struct OrcParams {
   int32_t mesh;        // 0 static, 1 prescribed profile motion, 2 fluid-driven Gaussian
   int32_t gauss_half;  // truncation half-width of the Gaussian filter (nodes)
   int32_t beta_dx_global;  // 1: Delta x in the smoothness indicators is max_j J_j (Step 1)
+  // Bottom: 0 = cell averages evolved by the ALE scheme of Eq. bottomrk (the paper's default);
+  // 1 = L2 projection (Eq. baverage) of a piecewise polynomial b(x) onto every stage mesh.
+  int32_t bottom_mode;
+  int32_t bpieces, bdeg;                  // number of pieces, polynomial degree
+  const double* bbreaks;                  // bpieces + 1 increasing breakpoints
+  const double* bcoef;                    // piece p: sum_k bcoef[p (bdeg+1) + k] (x - bbreaks[p])^k
 };
+
+// Piecewise polynomial bottom of the L2-projection mode (set by orc_set_bottom).
+std::vector<double> g_bbreaks, g_bcoef;
+int32_t g_bdeg = 0;
 
 enum : uint32_t {
   ST_EWEIGHT = 1u,     // a linear weight d_r <= 0 (the split of Shi-Hu-Shu is not applied)
@@ -488,6 +498,20 @@ void fluid_gauss_velocity(const OrcParams& P, int64_t N, const T* E, const T* M,
  * (Eq. Jacobi2D). State: E = eta bar, M = hu bar, B = b bar, J = cell widths, x = nodes.
  * prof[0..N] is the node profile of the prescribed motion. When alpha_io / dt_io are given
  * with replay = 1, the recorded dt and alpha are used (tangent-linear replay). */
+/* L2 projection of the bottom on one cell (Eq. baverage): the average of the piecewise
+ * polynomial b over [a, c], integrated exactly piece by piece with the antiderivatives of
+ * the monomials (x - x_p)^k. */
+double bottom_average(const OrcParams& P, double a, double c) {
+  double s = 0.0;
+  for (int p = 0; p < P.bpieces; ++p) {
+    const double x0 = P.bbreaks[p], lo = std::max(a, x0), hi = std::min(c, P.bbreaks[p + 1]);
+    if (!(hi > lo)) continue;
+    for (int k = 0; k <= P.bdeg; ++k)
+      s += P.bcoef[p * (P.bdeg + 1) + k] * (ipow(hi - x0, k + 1) - ipow(lo - x0, k + 1)) / (k + 1);
+  }
+  return s / (c - a);
+}
+
 template <class T>
 uint32_t ssprk3_step(const OrcParams& P, int64_t N, T* E, T* M, T* B, double* J, double* x, const double* prof,
                      double* t, double* dt_out, uint8_t* flags, double* alpha_rec, int replay) {
@@ -555,6 +579,9 @@ uint32_t ssprk3_step(const OrcParams& P, int64_t N, T* E, T* M, T* B, double* J,
     qM[j] = Y1M[j] / T(J1[j]);
     qB[j] = Y1B[j] / T(J1[j]);
   }
+  // L2-projection mode: the bottom of stage 2 is the projection onto the mesh at t_{n+1}.
+  if (P.bottom_mode == 1)
+    for (int64_t j = 0; j < N; ++j) qB[j] = T(bottom_average(P, x[j] + dt * w[j], x[j + 1] + dt * w[j + 1]));
   // Stage 2 on the mesh at t_{n,1} = t_{n+1}.
   double A2 = reconstruct(P, N, qE.data(), qM.data(), qB.data(), J1.data(), ed, st);
   double alpha2 = replay ? alpha_rec[1] : A2 + Wbar;
@@ -567,6 +594,10 @@ uint32_t ssprk3_step(const OrcParams& P, int64_t N, T* E, T* M, T* B, double* J,
     qM[j] = Y2M[j] / T(J2[j]);
     qB[j] = Y2B[j] / T(J2[j]);
   }
+  // ... and of stage 3 the projection onto the mesh at t_{n+1/2}.
+  if (P.bottom_mode == 1)
+    for (int64_t j = 0; j < N; ++j)
+      qB[j] = T(bottom_average(P, x[j] + 0.5 * dt * w[j], x[j + 1] + 0.5 * dt * w[j + 1]));
   // Stage 3 on the mesh at t_{n,2} = (t_n + t_{n+1}) / 2.
   double A3 = reconstruct(P, N, qE.data(), qM.data(), qB.data(), J2.data(), ed, st);
   double alpha3 = replay ? alpha_rec[2] : A3 + Wbar;
@@ -581,6 +612,9 @@ uint32_t ssprk3_step(const OrcParams& P, int64_t N, T* E, T* M, T* B, double* J,
     J[j] = J3[j];
   }
   for (int64_t k = 0; k <= N; ++k) x[k] = x[k] + dt * w[k];
+  // ... and after the step the projection onto the mesh at t_{n+1}.
+  if (P.bottom_mode == 1)
+    for (int64_t j = 0; j < N; ++j) B[j] = T(bottom_average(P, x[j], x[j + 1]));
   *t = clipped ? P.t_end : *t + dt;
   *dt_out = dt;
   if (alpha_rec && !replay) {
@@ -596,6 +630,12 @@ OrcParams to_params(const double* p, const int32_t* ip) {
   P.g = p[0]; P.cfl = p[1]; P.eps_weno = p[2]; P.eps_pp = p[3]; P.h_dry = p[4];
   P.mesh_T = p[5]; P.gauss_sigma = p[6]; P.t_end = p[7]; P.dt_fixed = p[8];
   P.bc = ip[0]; P.mesh = ip[1]; P.gauss_half = ip[2]; P.beta_dx_global = ip[3];
+  P.bottom_mode = ip[4];
+  P.bpieces = (int32_t)g_bbreaks.size() - 1;
+  P.bdeg = g_bdeg;
+  P.bbreaks = g_bbreaks.data();
+  P.bcoef = g_bcoef.data();
+  if (P.bottom_mode == 1 && P.bpieces < 1) P.bottom_mode = 0;
   return P;
 }
 
@@ -607,6 +647,20 @@ OrcParams to_params(const double* p, const int32_t* ip) {
 /* and an int array ip[4] = {bc, mesh, gauss_half, beta_dx_global}.                       */
 /* ------------------------------------------------------------------------------------ */
 extern "C" {
+
+/* Piecewise polynomial bottom b(x) of the L2-projection mode (ip[4] = 1): npieces pieces on
+ * breaks[npieces + 1], piece p = sum_k coef[p (deg + 1) + k] (x - breaks[p])^k. */
+void orc_set_bottom(int32_t npieces, int32_t deg, const double* breaks, const double* coef) {
+  g_bbreaks.assign(breaks, breaks + npieces + 1);
+  g_bcoef.assign(coef, coef + (size_t)npieces * (deg + 1));
+  g_bdeg = deg;
+}
+
+/* Average of the bottom over [a, c] (the projection of one cell). */
+double orc_bottom_average(const double* p, const int32_t* ip, double a, double c) {
+  OrcParams P = to_params(p, ip);
+  return bottom_average(P, a, c);
+}
 
 /* Mesh-only WENO data of one cell from the five widths J_{j-2..j+2}: c[2][3][3], d[2][3],
  * big[2][5] (weights of the quartic at the two edges), sub[3][9] (coefficient maps). */

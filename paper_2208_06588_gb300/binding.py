@@ -73,6 +73,7 @@ def lib():
         L.swale_get_alpha_log.argtypes = [vp, vp]
         L.swale_adjoint.argtypes = [vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
         L.swale_adjoint_bytes.argtypes = [i64, i64, i64, i64, i32, P(ctypes.c_uint64)]
+        L.swale_set_bottom_function.argtypes = [vp, i32, i32, vp, vp]
         L.swale_rhs_noalloc.argtypes = [P(SwaleConfig), vp, i64, vp, vp, vp, vp, vp, d, vp, vp, vp, P(d), vp]
         L.swale_set_timing.argtypes = [vp, i32]
         L.swale_get_timing.argtypes = [vp, vp, vp]
@@ -80,7 +81,7 @@ def lib():
                      "swale_get_flags", "swale_get_status", "swale_rhs", "swale_enqueue", "swale_set_timing",
                      "swale_get_timing", "swale_rhs_noalloc", "swale_batch_set_problem", "swale_batch_get_state",
                      "swale_set_tiles", "swale_get_tiles", "swale_autotune", "swale_alpha_log",
-                     "swale_get_alpha_log", "swale_adjoint", "swale_adjoint_bytes"):
+                     "swale_get_alpha_log", "swale_adjoint", "swale_adjoint_bytes", "swale_set_bottom_function"):
             getattr(L, name).restype = ctypes.c_int
         L.swale_last_error.argtypes = [vp]
         L.swale_last_error.restype = ctypes.c_char_p
@@ -155,6 +156,16 @@ def swale_autotune(ctx, steps=3, cache_path=None):
     cp = cache_path.encode() if cache_path else None
     _check(ctx, lib().swale_autotune(ctx, int(steps), cp, t.ctypes.data))
     return tuple(int(v) for v in t)
+
+
+def swale_set_bottom_function(ctx, breaks=None, coef=None):
+    """L2-projection bottom: breaks[npieces+1], coef[npieces, degree+1] (None: evolve b)."""
+    if breaks is None:
+        _check(ctx, lib().swale_set_bottom_function(ctx, 0, 0, None, None))
+        return
+    br = np.ascontiguousarray(breaks, dtype=np.float64)
+    cf = np.ascontiguousarray(np.atleast_2d(coef), dtype=np.float64)
+    _check(ctx, lib().swale_set_bottom_function(ctx, cf.shape[0], cf.shape[1] - 1, ptr(br), ptr(cf)))
 
 
 def swale_alpha_log(ctx, mode, nsteps=0, log=None):

@@ -44,6 +44,9 @@ struct swale_ctx {
   double* alpha_log = nullptr;
   int64_t alpha_cap = 0, alpha_base = 0;
   int32_t alpha_mode = 0;
+  // L2-projection bottom (swale_set_bottom_function); part of the state allocations.
+  int32_t bot_pieces = 0, bot_deg = 0;
+  double *bot_breaks = nullptr, *bot_icoef = nullptr;
 };
 
 namespace {
@@ -108,6 +111,10 @@ StepConst step_const(const swale_ctx* ctx) {
   K.alpha_cap = ctx->alpha_cap;
   K.alpha_base = ctx->alpha_base;
   K.alpha_mode = ctx->alpha_mode;
+  K.bot_pieces = ctx->bot_pieces;
+  K.bot_deg = ctx->bot_deg;
+  K.bot_breaks = ctx->bot_breaks;
+  K.bot_icoef = ctx->bot_icoef;
   return K;
 }
 
@@ -141,6 +148,8 @@ void free_state(swale_ctx* ctx) {
   ctx->B = ctx->Ntot = 0;
   ctx->off.clear();
   ctx->flag_buf = nullptr;
+  ctx->bot_pieces = ctx->bot_deg = 0;
+  ctx->bot_breaks = ctx->bot_icoef = nullptr;
 }
 
 template <class T>
@@ -678,6 +687,48 @@ swale_status swale_get_status(swale_ctx* ctx, uint32_t* status_bits, int64_t* st
   return SWALE_OK;
 }
 
+swale_status swale_set_bottom_function(swale_ctx* ctx, int32_t npieces, int32_t degree, const double* breaks,
+                                       const double* coef) {
+  if (!ctx) return SWALE_EINVAL;
+  if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "set the problem first");
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  drop_graph(ctx);
+  if (npieces == 0) {
+    ctx->bot_pieces = 0;
+    return SWALE_OK;
+  }
+  if (npieces < 0 || npieces > (1 << 20) || degree < 0 || degree > 8 || !breaks || !coef)
+    return fail(ctx, SWALE_EINVAL, "need 1 <= npieces <= 2^20, 0 <= degree <= 8, breaks and coef");
+  std::vector<double> br, cf, x;
+  swale_status st;
+  if ((st = fetch(ctx, breaks, (size_t)npieces + 1, br)) || (st = fetch(ctx, coef, (size_t)npieces * (degree + 1), cf)))
+    return st;
+  for (int32_t p = 0; p < npieces; ++p)
+    if (!(br[p + 1] > br[p]) || !std::isfinite(br[p]) || !std::isfinite(br[p + 1]))
+      return fail(ctx, SWALE_EINVAL, "breakpoints must be finite and increasing");
+  for (double c : cf)
+    if (!std::isfinite(c)) return fail(ctx, SWALE_EINVAL, "non-finite coefficient");
+  if ((st = fetch(ctx, (const double*)ctx->D.x, (size_t)(ctx->Ntot + ctx->B), x))) return st;
+  for (int64_t i = 0; i < ctx->B; ++i)
+    if (x[ctx->off[i] + i] < br[0] || x[ctx->off[i + 1] + i] > br[npieces])
+      return fail(ctx, SWALE_EINVAL, "the breakpoints must cover every instance's domain");
+  // Antiderivative coefficients: int_0^t sum_k c_k s^k ds = t sum_k (c_k / (k + 1)) t^k.
+  for (int32_t p = 0; p < npieces; ++p)
+    for (int32_t k = 0; k <= degree; ++k) cf[(size_t)p * (degree + 1) + k] /= (double)(k + 1);
+  double *dbr = nullptr, *dcf = nullptr;
+  if ((st = dalloc(ctx, ctx->allocs, &dbr, br.size())) || (st = dalloc(ctx, ctx->allocs, &dcf, cf.size())))
+    return st;
+  if (!ctx->D.xn && (st = dalloc(ctx, ctx->allocs, &ctx->D.xn, (size_t)(ctx->Ntot + ctx->B)))) return st;
+  SW_CUDA(ctx, cudaMemcpyAsync(dbr, br.data(), br.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  SW_CUDA(ctx, cudaMemcpyAsync(dcf, cf.data(), cf.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->bot_breaks = dbr;
+  ctx->bot_icoef = dcf;
+  ctx->bot_pieces = npieces;
+  ctx->bot_deg = degree;
+  return SWALE_OK;
+}
+
 swale_status swale_set_tiles(swale_ctx* ctx, int32_t recon_tile, int32_t update_tile, int32_t recon_grid,
                              int32_t update_grid) {
   if (!ctx) return SWALE_EINVAL;
@@ -1033,6 +1084,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   if (ctx->cfg.mesh == SWALE_MESH_FLUID_GAUSS)
     return fail(ctx, SWALE_EINVAL, "the adjoint needs a prescribed mesh (static or profile motion)");
   if (ctx->cfg.t_end > 0.0) return fail(ctx, SWALE_EINVAL, "the adjoint runs a fixed number of steps: t_end = 0");
+  if (ctx->bot_pieces > 0) return fail(ctx, SWALE_EINVAL, "the adjoint evolves the bottom (no L2-projection bottom)");
   const int64_t B = ctx->B, Nt = ctx->Ntot, NN = Nt + B, NE = Nt + 2 * B;
   const int64_t C = std::min(ckpt_every, nsteps), nseg = (nsteps + C - 1) / C;
   cudaStream_t st = ctx->stream;
@@ -1289,6 +1341,8 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   K.alpha_cap = 0;
   K.alpha_base = 0;
   K.alpha_mode = 0;
+  K.bot_pieces = K.bot_deg = 0;
+  K.bot_breaks = K.bot_icoef = nullptr;
   // The scalars keep the previous call's contents: start them from zero (J^n minimum at 1 so
   // the stage-1 time-step arithmetic stays finite; its result is not used here).
   InstConst ic0;

@@ -76,6 +76,10 @@ struct StepConst {
   int64_t alpha_cap;   // steps the log holds
   int64_t alpha_base;  // step counter value of log row 0
   int32_t alpha_mode;
+  // L2-projection bottom (Eq. baverage); bot_pieces == 0: b evolves by Eq. bottomrk.
+  int32_t bot_pieces, bot_deg;
+  const double* bot_breaks;  // bot_pieces + 1 breakpoints
+  const double* bot_icoef;   // piece p: coefficients a_k of the antiderivative t sum_k a_k t^k, t = x - break_p
 };
 
 // Stage viscosity of instance i in stage s of step `step` (DevScalars::step_idx): the computed
@@ -100,6 +104,7 @@ struct DevState {
   // Edge arrays hold cells -1..N_i of each instance (N_i + 2 per instance).
   double *eEL, *eER, *eBL, *eBR, *ehL, *ehR, *euL, *euR;
   double *ipair, *itri;        // 1/(J_c + J_{c+1}) and 1/(J_{c-1} + J_c + J_{c+1}) of the stage mesh
+  double* xn;                  // nodes at t_{n+1}, written by stage 2 (L2-projection bottom only)
   uint8_t* flags;              // stage-1 classes, edge layout
   InstConst* IC;
   DevScalars* S;
@@ -117,6 +122,33 @@ __device__ __forceinline__ int64_t ghost(int64_t i, int64_t N, int bc) {
   if (i < 0) return -1 - i;
   if (i >= N) return 2 * N - 1 - i;
   return i;
+}
+
+// L2 projection of the bottom onto one cell [a, c] (Eq. baverage): the exact average of the
+// piecewise polynomial, from its antiderivative on every piece the cell overlaps (the first one
+// found by bisection of the breakpoints).
+__device__ __noinline__ double bottom_average(const StepConst& K, double a, double c) {
+  const double* br = K.bot_breaks;
+  int lo = 0, hi = K.bot_pieces;  // the piece p with br[p] <= a < br[p + 1] (clamped)
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (br[mid] <= a) lo = mid;
+    else hi = mid;
+  }
+  double s = 0.0;
+  for (int p = lo; p < K.bot_pieces && br[p] < c; ++p) {
+    const double x0 = br[p];
+    const double tl = fmax(a, x0) - x0, th = fmin(c, br[p + 1]) - x0;
+    if (!(th > tl)) continue;
+    const double* ak = K.bot_icoef + p * (K.bot_deg + 1);
+    double Fl = 0.0, Fh = 0.0;
+    for (int k = K.bot_deg; k >= 0; --k) {
+      Fl = Fl * tl + ak[k];
+      Fh = Fh * th + ak[k];
+    }
+    s += Fh * th - Fl * tl;
+  }
+  return s / (c - a);
 }
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
@@ -581,6 +613,8 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
           D.Ea[g] = yE * inv;
           D.Ma[g] = yM * inv;
           D.Ba[g] = yB * inv;
+          if (K.bot_pieces > 0)  // bottom of stage 2: projection onto the mesh at t_{n+1}
+            D.Ba[g] = bottom_average(K, D.x[nb + j] + dt * wl, D.x[nb + j + 1] + dt * wr);
         } else if (STAGE == 2) {
           const double yE = 0.75 * (J0 * D.E0[g]) + 0.25 * (D.YE[g] + dt * RE);
           const double yM = 0.75 * (J0 * D.M0[g]) + 0.25 * (D.YM[g] + dt * RM);
@@ -592,6 +626,12 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
           D.Eb[g] = yE * inv;
           D.Mb[g] = yM * inv;
           D.Bb[g] = yB * inv;
+          if (K.bot_pieces > 0) {  // bottom of stage 3: projection onto the mesh at t_{n+1/2}
+            const double xl = D.x[nb + j], xr = D.x[nb + j + 1];
+            D.Bb[g] = bottom_average(K, xl + 0.5 * dt * wl, xr + 0.5 * dt * wr);
+            D.xn[nb + j] = xl + dt * wl;  // nodes at t_{n+1} for the projection after the step
+            if (j == N - 1) D.xn[nb + N] = xr + dt * wr;
+          }
         } else {
           const double J3 = (1.0 / 3.0) * J0 + (2.0 / 3.0) * D.J2[g] + (2.0 / 3.0) * dt * dw;
           if (!swale::gt0(J3)) st |= swale::ST_EMESH;
@@ -606,8 +646,15 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
           D.J0[g] = J3;
           jmaxb = J3;
           jminb = J3;
-          D.x[nb + j] += dt * wl;
-          if (j == N - 1) D.x[nb + N] += dt * wr;
+          if (K.bot_pieces > 0) {  // bottom after the step: projection onto the mesh at t_{n+1}
+            const double xl = D.xn[nb + j], xr = D.xn[nb + j + 1];
+            D.B0[g] = bottom_average(K, xl, xr);
+            D.x[nb + j] = xl;
+            if (j == N - 1) D.x[nb + N] = xr;
+          } else {
+            D.x[nb + j] += dt * wl;
+            if (j == N - 1) D.x[nb + N] += dt * wr;
+          }
           if (swale::bad(En) || swale::bad(Mn) || swale::bad(Bn)) st |= swale::ST_NONFINITE;
         }
       }

@@ -166,6 +166,37 @@ def smooth_periodic(N=200, lake=False, t_end=0.1):
                  bc="periodic", mesh="profile", mesh_T=1.0, t_end=t_end)
 
 
+def _aligned_motion_profile(xi, xmin, xmax, fixed):
+    """Node profile of the paper's bump-aligned motion (Eq. wangge3): x(t) = xi +
+    sin(2 pi t / t_end) (xi - xmax)(xi - xmin) prod_f (xi - f) / (3 (xmax - xmin)^4); nodes
+    starting at the points ``fixed`` never move."""
+    p = (xi - xmax) * (xi - xmin) / (3.0 * (xmax - xmin) ** 4)
+    for f in fixed:
+        p = p * (xi - f)
+    return p
+
+
+def bump_dam_break(N=1 << 20, t_end=60.0):
+    """Dam break over a rectangular bump (Sec. 5.1, Eq. bdam / inidam): [0,1500], b = 8 on
+    [562.5, 937.5] else 0, eta = 20 for x <= 750 and 15 beyond, hu = 0, transmissive; the
+    bump-aligned motion (Eq. wangge3) with T = t_end; the bottom is the L2 projection
+    (Eq. baverage) of b onto every stage mesh. N must be a multiple of 8 so that the bump edges
+    are nodes (the paper's 100 cells do not put them on nodes; see the design notes). CFL 0.6."""
+    if N % 8:
+        raise ValueError("N must be a multiple of 8 (bump edges on nodes)")
+    x = _uniform(0.0, 1500.0, N)
+    breaks = np.array([0.0, 562.5, 937.5, 1500.0])
+    coef = np.array([[0.0], [8.0], [0.0]])
+    xc = 0.5 * (x[1:] + x[:-1])  # every cell lies on one side of 562.5, 750 and 937.5
+    b = np.where((xc > 562.5) & (xc < 937.5), 8.0, 0.0)
+    E = np.where(xc < 750.0, 20.0, 15.0)
+    pr = Problem(name="bump_dam_break", x=x, h=E - b, hu=np.zeros(N), b=b, E=E,
+                 profile=_aligned_motion_profile(x, 0.0, 1500.0, (562.5, 937.5)), bc="transmissive",
+                 mesh="profile", mesh_T=t_end, cfl=0.6)
+    pr.meta["bottom"] = (breaks, coef)
+    return pr
+
+
 def dam_break_dry(N=1 << 20):
     """Large single instance: N cells on [0,10], transmissive; h = 2 for x < 5, 0.5 on [5,8),
     dry (h = 0) on [8,10]; hu = 0; b = 0.8 exp(-5 (x-5)^2); mesh velocity = Gaussian-smoothed

@@ -1,0 +1,124 @@
+"""L2-projection bottom (Eq. baverage) on the GPU: parity with the oracle on the dam break over
+a rectangular bump with the bump-aligned mesh (Eq. bdam / wangge3), lake at rest, batches,
+and the error paths."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_06588_gb300 import binding as B
+from paper_2208_06588_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2208_06588_gb300 import build
+    build.build()
+    B.lib()
+
+
+def cfg_of(pr):
+    return B.make_config(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, t_end=pr.t_end, bc=pr.bc,
+                         mesh=pr.mesh)
+
+
+def l1_rel(a, r, J):
+    return float(np.sum(J * np.abs(a - r)) / max(np.sum(J * np.abs(r)), 1e-300))
+
+
+def run_gpu(pr, nsteps):
+    s = B.Solver(cfg_of(pr))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    B.swale_set_bottom_function(s.ctx, *pr.meta["bottom"])
+    done = s.advance(nsteps)
+    out = s.state()
+    out["bits"] = s.status()[0]
+    s.close()
+    assert done == nsteps
+    return out
+
+
+@pytest.mark.parametrize("N,nsteps", [(1024, 120), (1001, 60)])
+def test_bump_dam_break_parity(N, nsteps):
+    pr = W.bump_dam_break(N=N) if N % 8 == 0 else None
+    if pr is None:  # a ragged size: bump edges off the nodes (projection mixes 0 and 8)
+        pr = W.bump_dam_break(N=8)
+        x = np.linspace(0.0, 1500.0, N + 1)
+        P = oracle.Params(bottom=pr.meta["bottom"])
+        b = np.array([oracle.bottom_average(P, x[j], x[j + 1]) for j in range(N)])
+        xc = 0.5 * (x[1:] + x[:-1])
+        E = np.where(xc < 750.0, 20.0, 15.0)
+        pr = W.Problem(name="bump_ragged", x=x, h=E - b, hu=np.zeros(N), b=b, E=E, profile=(x - 1500.0) * x * (
+            x - 562.5) * (x - 937.5) / (3.0 * 1500.0 ** 4), bc="transmissive", mesh="profile", mesh_T=60.0,
+                       cfl=0.6, meta={"bottom": pr.meta["bottom"]})
+    g = run_gpu(pr, nsteps)
+    st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+    P = oracle.Params(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, bc=pr.bc, mesh=pr.mesh,
+                      bottom=pr.meta["bottom"])
+    r = oracle.run(P, st, pr.profile, nsteps=nsteps)
+    assert r["steps"] == nsteps and r["status"] == 0 and g["bits"] == 0
+    assert abs(g["t"] - st.t) <= 1e-12 * st.t
+    assert l1_rel(g["eta"], st.E, st.J) <= 1e-9
+    assert l1_rel(g["hu"], st.M, st.J) <= 1e-9
+    np.testing.assert_allclose(g["b"], st.B, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(g["x"], st.x, rtol=0, atol=1e-12)
+    if N % 8 == 0:  # aligned: the bump stays exact
+        assert set(np.unique(np.round(g["b"], 12))) <= {0.0, 8.0}
+
+
+def test_lake_at_rest_with_projected_polynomial_bottom():
+    N = 333
+    x = np.linspace(0.0, 10.0, N + 1)
+    coef = np.array([[0.0, 0.0, 4.0 * 100 / 625, -4.0 * 20 / 625, 4.0 / 625]])
+    bott = (np.array([0.0, 10.0]), coef)
+    P = oracle.Params(bottom=bott)
+    b = np.array([oracle.bottom_average(P, x[j], x[j + 1]) for j in range(N)])
+    pr = W.Problem(name="lake_poly", x=x, h=10.0 - b, hu=np.zeros(N), b=b, E=np.full(N, 10.0),
+                   profile=(x - 10.0) * x / 300.0, bc="transmissive", mesh="profile", mesh_T=0.5, cfl=0.6,
+                   meta={"bottom": bott})
+    g = run_gpu(pr, 60)
+    assert np.abs(g["eta"] - 10.0).max() < 1e-12
+    assert np.abs(g["hu"]).max() < 1e-11
+    bn = np.array([oracle.bottom_average(P, g["x"][j], g["x"][j + 1]) for j in range(N)])
+    np.testing.assert_allclose(g["b"], bn, rtol=1e-14, atol=1e-14)
+
+
+def test_batch_with_projected_bottom_equals_single_instances():
+    prs = [W.bump_dam_break(N=n) for n in (512, 776)]
+    off = np.array([0, prs[0].N, prs[0].N + prs[1].N], dtype=np.int64)
+    cat = lambda f: np.concatenate([f(p) for p in prs])
+    bt = W.Batch(name="bumps", off=off, x=cat(lambda p: p.x), h=cat(lambda p: p.h), hu=cat(lambda p: p.hu),
+                 b=cat(lambda p: p.b), E=cat(lambda p: p.E), profile=cat(lambda p: p.profile),
+                 cfl=np.array([0.6, 0.6]), bc="transmissive", mesh="profile", mesh_T=60.0)
+    s = B.Solver(B.make_config(cfl=0.6, mesh_T=60.0, bc="transmissive", mesh="profile"))
+    s.set_batch(bt)
+    B.swale_set_bottom_function(s.ctx, *prs[0].meta["bottom"])
+    s.advance(40)
+    out = s.batch_state()
+    s.close()
+    for i, p in enumerate(prs):
+        g = run_gpu(p, 40)
+        a, c = int(off[i]), int(off[i + 1])
+        np.testing.assert_array_equal(out["eta"][a:c], g["eta"])
+        np.testing.assert_array_equal(out["b"][a:c], g["b"])
+        np.testing.assert_array_equal(out["x"][a + i:c + i + 1], g["x"])
+
+
+def test_bottom_function_errors():
+    pr = W.bump_dam_break(N=64)
+    s = B.Solver(cfg_of(pr))
+    with pytest.raises(B.SwaleError):  # no problem yet
+        B.swale_set_bottom_function(s.ctx, *pr.meta["bottom"])
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    with pytest.raises(B.SwaleError):  # does not cover [0, 1500]
+        B.swale_set_bottom_function(s.ctx, np.array([10.0, 1500.0]), np.array([[0.0]]))
+    with pytest.raises(B.SwaleError):  # decreasing breakpoints
+        B.swale_set_bottom_function(s.ctx, np.array([0.0, 900.0, 800.0, 1500.0]), np.zeros((3, 1)))
+    B.swale_set_bottom_function(s.ctx, *pr.meta["bottom"])
+    with pytest.raises(B.SwaleError):  # the adjoint evolves b
+        B.swale_adjoint(s.ctx, 2, 1, 1, np.array([100.0]), np.zeros(2), np.zeros(1), np.zeros(64), np.zeros(64),
+                        np.zeros(64))
+    B.swale_set_bottom_function(s.ctx)  # back to Eq. bottomrk
+    s.advance(2)
+    s.close()
