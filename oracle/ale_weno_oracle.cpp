@@ -498,16 +498,31 @@ void fluid_gauss_velocity(const OrcParams& P, int64_t N, const T* E, const T* M,
  * (Eq. Jacobi2D). State: E = eta bar, M = hu bar, B = b bar, J = cell widths, x = nodes.
  * prof[0..N] is the node profile of the prescribed motion. When alpha_io / dt_io are given
  * with replay = 1, the recorded dt and alpha are used (tangent-linear replay). */
-/* L2 projection of the bottom on one cell (Eq. baverage): the average of the piecewise
- * polynomial b over [a, c], integrated exactly piece by piece with the antiderivatives of
- * the monomials (x - x_p)^k. */
+/* L2 projection of the bottom on one cell (Eq. baverage; "a sufficiently accurate quadrature
+ * rule"): on every piece the cell overlaps, the 5-point Gauss-Legendre rule (exact for the
+ * degree <= 8 pieces) gives the piece's mean over the overlap, normalised by the sum of the
+ * weights so that a constant piece averages to its value exactly; the cell average is the
+ * length-weighted sum of these means. Quadrature, not differences of antiderivatives: those
+ * cancel badly on short cells far from the breakpoint. */
 double bottom_average(const OrcParams& P, double a, double c) {
+  const double r1 = std::sqrt(5.0 - 2.0 * std::sqrt(10.0 / 7.0)) / 3.0;
+  const double r2 = std::sqrt(5.0 + 2.0 * std::sqrt(10.0 / 7.0)) / 3.0;
+  const double xi[5] = {-r2, -r1, 0.0, r1, r2};
+  const double w1 = (322.0 + 13.0 * std::sqrt(70.0)) / 900.0, w2 = (322.0 - 13.0 * std::sqrt(70.0)) / 900.0;
+  const double wq[5] = {w2, w1, 128.0 / 225.0, w1, w2};
   double s = 0.0;
   for (int p = 0; p < P.bpieces; ++p) {
     const double x0 = P.bbreaks[p], lo = std::max(a, x0), hi = std::min(c, P.bbreaks[p + 1]);
     if (!(hi > lo)) continue;
-    for (int k = 0; k <= P.bdeg; ++k)
-      s += P.bcoef[p * (P.bdeg + 1) + k] * (ipow(hi - x0, k + 1) - ipow(lo - x0, k + 1)) / (k + 1);
+    double num = 0.0, den = 0.0;
+    for (int q = 0; q < 5; ++q) {
+      const double xq = 0.5 * (lo + hi) + 0.5 * (hi - lo) * xi[q];
+      double v = 0.0;
+      for (int k = 0; k <= P.bdeg; ++k) v += P.bcoef[p * (P.bdeg + 1) + k] * ipow(xq - x0, k);
+      num += wq[q] * v;
+      den += wq[q];
+    }
+    s += (hi - lo) * (num / den);
   }
   return s / (c - a);
 }

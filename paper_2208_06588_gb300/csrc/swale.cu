@@ -46,7 +46,7 @@ struct swale_ctx {
   int32_t alpha_mode = 0;
   // L2-projection bottom (swale_set_bottom_function); part of the state allocations.
   int32_t bot_pieces = 0, bot_deg = 0;
-  double *bot_breaks = nullptr, *bot_icoef = nullptr;
+  double *bot_breaks = nullptr, *bot_coef = nullptr;
 };
 
 namespace {
@@ -114,7 +114,7 @@ StepConst step_const(const swale_ctx* ctx) {
   K.bot_pieces = ctx->bot_pieces;
   K.bot_deg = ctx->bot_deg;
   K.bot_breaks = ctx->bot_breaks;
-  K.bot_icoef = ctx->bot_icoef;
+  K.bot_coef = ctx->bot_coef;
   return K;
 }
 
@@ -149,7 +149,7 @@ void free_state(swale_ctx* ctx) {
   ctx->off.clear();
   ctx->flag_buf = nullptr;
   ctx->bot_pieces = ctx->bot_deg = 0;
-  ctx->bot_breaks = ctx->bot_icoef = nullptr;
+  ctx->bot_breaks = ctx->bot_coef = nullptr;
 }
 
 template <class T>
@@ -712,9 +712,6 @@ swale_status swale_set_bottom_function(swale_ctx* ctx, int32_t npieces, int32_t 
   for (int64_t i = 0; i < ctx->B; ++i)
     if (x[ctx->off[i] + i] < br[0] || x[ctx->off[i + 1] + i] > br[npieces])
       return fail(ctx, SWALE_EINVAL, "the breakpoints must cover every instance's domain");
-  // Antiderivative coefficients: int_0^t sum_k c_k s^k ds = t sum_k (c_k / (k + 1)) t^k.
-  for (int32_t p = 0; p < npieces; ++p)
-    for (int32_t k = 0; k <= degree; ++k) cf[(size_t)p * (degree + 1) + k] /= (double)(k + 1);
   double *dbr = nullptr, *dcf = nullptr;
   if ((st = dalloc(ctx, ctx->allocs, &dbr, br.size())) || (st = dalloc(ctx, ctx->allocs, &dcf, cf.size())))
     return st;
@@ -723,7 +720,7 @@ swale_status swale_set_bottom_function(swale_ctx* ctx, int32_t npieces, int32_t 
   SW_CUDA(ctx, cudaMemcpyAsync(dcf, cf.data(), cf.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->bot_breaks = dbr;
-  ctx->bot_icoef = dcf;
+  ctx->bot_coef = dcf;
   ctx->bot_pieces = npieces;
   ctx->bot_deg = degree;
   return SWALE_OK;
@@ -1342,7 +1339,7 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   K.alpha_base = 0;
   K.alpha_mode = 0;
   K.bot_pieces = K.bot_deg = 0;
-  K.bot_breaks = K.bot_icoef = nullptr;
+  K.bot_breaks = K.bot_coef = nullptr;
   // The scalars keep the previous call's contents: start them from zero (J^n minimum at 1 so
   // the stage-1 time-step arithmetic stays finite; its result is not used here).
   InstConst ic0;

@@ -79,7 +79,7 @@ struct StepConst {
   // L2-projection bottom (Eq. baverage); bot_pieces == 0: b evolves by Eq. bottomrk.
   int32_t bot_pieces, bot_deg;
   const double* bot_breaks;  // bot_pieces + 1 breakpoints
-  const double* bot_icoef;   // piece p: coefficients a_k of the antiderivative t sum_k a_k t^k, t = x - break_p
+  const double* bot_coef;    // piece p: sum_k bot_coef[p (bot_deg + 1) + k] (x - break_p)^k
 };
 
 // Stage viscosity of instance i in stage s of step `step` (DevScalars::step_idx): the computed
@@ -124,10 +124,16 @@ __device__ __forceinline__ int64_t ghost(int64_t i, int64_t N, int bc) {
   return i;
 }
 
-// L2 projection of the bottom onto one cell [a, c] (Eq. baverage): the exact average of the
-// piecewise polynomial, from its antiderivative on every piece the cell overlaps (the first one
-// found by bisection of the breakpoints).
+// L2 projection of the bottom onto one cell [a, c] (Eq. baverage): on each piece the cell
+// overlaps (the first found by bisection of the breakpoints), the mean of the polynomial by the
+// 5-point Gauss-Legendre rule, exact for degree <= 8 and divided by the sum of the weights so
+// that constants come out exact; the cell average weights these means by the overlap lengths.
+// (Differences of antiderivatives would cancel on short cells far from the breakpoint.)
 __device__ __noinline__ double bottom_average(const StepConst& K, double a, double c) {
+  const double xi[5] = {-0.9061798459386639928, -0.5384693101056830910, 0.0, 0.5384693101056830910,
+                        0.9061798459386639928};
+  const double wq[5] = {0.2369268850561890875, 0.4786286704993664680, 0.5688888888888888889, 0.4786286704993664680,
+                        0.2369268850561890875};
   const double* br = K.bot_breaks;
   int lo = 0, hi = K.bot_pieces;  // the piece p with br[p] <= a < br[p + 1] (clamped)
   while (hi - lo > 1) {
@@ -137,16 +143,20 @@ __device__ __noinline__ double bottom_average(const StepConst& K, double a, doub
   }
   double s = 0.0;
   for (int p = lo; p < K.bot_pieces && br[p] < c; ++p) {
-    const double x0 = br[p];
-    const double tl = fmax(a, x0) - x0, th = fmin(c, br[p + 1]) - x0;
-    if (!(th > tl)) continue;
-    const double* ak = K.bot_icoef + p * (K.bot_deg + 1);
-    double Fl = 0.0, Fh = 0.0;
-    for (int k = K.bot_deg; k >= 0; --k) {
-      Fl = Fl * tl + ak[k];
-      Fh = Fh * th + ak[k];
+    const double x0 = br[p], l = fmax(a, x0), h = fmin(c, br[p + 1]);
+    if (!(h > l)) continue;
+    const double* ck = K.bot_coef + p * (K.bot_deg + 1);
+    const double m = 0.5 * (l + h), hw = 0.5 * (h - l);
+    double num = 0.0, den = 0.0;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const double t = m + hw * xi[q] - x0;
+      double v = 0.0;
+      for (int k = K.bot_deg; k >= 0; --k) v = v * t + ck[k];
+      num += wq[q] * v;
+      den += wq[q];
     }
-    s += Fh * th - Fl * tl;
+    s += (h - l) * (num / den);
   }
   return s / (c - a);
 }

@@ -81,7 +81,7 @@ def test_lake_at_rest_with_projected_polynomial_bottom():
     assert np.abs(g["eta"] - 10.0).max() < 1e-12
     assert np.abs(g["hu"]).max() < 1e-11
     bn = np.array([oracle.bottom_average(P, g["x"][j], g["x"][j + 1]) for j in range(N)])
-    np.testing.assert_allclose(g["b"], bn, rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(g["b"], bn, rtol=1e-13, atol=1e-15)
 
 
 def test_batch_with_projected_bottom_equals_single_instances():
