@@ -29,6 +29,7 @@ ST_EWEIGHT, ST_NEGDEPTH, ST_NONFINITE, ST_EMESH = 1, 2, 4, 8
 
 BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
 MESH = {"static": 0, "profile": 1, "fluid_gauss": 2}
+SCHEME = {"hydrostatic": 0, "nonwb": 1}
 
 
 def build(force: bool = False) -> str:
@@ -103,6 +104,9 @@ class Params:
     # piecewise polynomial b(x) = sum_k coef[p, k] (x - breaks[p])^k, or None to evolve b by
     # Eq. bottomrk.
     bottom: tuple | None = None
+    # "hydrostatic": the well-balanced scheme of Sec. 4.1; "nonwb": the ALE-WENO scheme of
+    # Eq. se2D / s2D with local characteristic reconstruction and the plain LF flux.
+    scheme: str = "hydrostatic"
 
     def arrays(self):
         p = np.array([self.g, self.cfl, self.eps_weno, self.eps_pp, self.h_dry, self.mesh_T, self.gauss_sigma,
@@ -112,7 +116,8 @@ class Params:
             br, cf = _f64(self.bottom[0]), np.atleast_2d(_f64(self.bottom[1]))
             lib().orc_set_bottom(cf.shape[0], cf.shape[1] - 1, _p(br), _p(np.ascontiguousarray(cf)))
             mode = 1
-        ip = np.array([BC[self.bc], MESH[self.mesh], self.gauss_half, self.beta_dx_global, mode], dtype=np.int32)
+        ip = np.array([BC[self.bc], MESH[self.mesh], self.gauss_half, self.beta_dx_global, mode,
+                       SCHEME[self.scheme]], dtype=np.int32)
         return p, ip
 
 

@@ -49,6 +49,10 @@ struct OrcParams {
   // Bottom: 0 = cell averages evolved by the ALE scheme of Eq. bottomrk (the paper's default);
   // 1 = L2 projection (Eq. baverage) of a piecewise polynomial b(x) onto every stage mesh.
   int32_t bottom_mode;
+  // 0: well-balanced scheme with hydrostatic reconstruction (Sec. 4.1); 1: the non-well-balanced
+  // ALE-WENO scheme (Eq. se2D / s2D): local characteristic reconstruction of (eta, hu) and the
+  // plain Lax-Friedrichs flux.
+  int32_t scheme;
   int32_t bpieces, bdeg;                  // number of pieces, polynomial degree
   const double* bbreaks;                  // bpieces + 1 increasing breakpoints
   const double* bcoef;                    // piece p: sum_k bcoef[p (bdeg+1) + k] (x - bbreaks[p])^k
@@ -209,6 +213,62 @@ T beta_of(const WenoCoeffs& W, int r, const T* v5, double lam) {
   return T(lam) * i1 + T(lam * lam * lam) * i2;
 }
 
+/* Steps 2-3 for one scalar field v5 on its own (no shared indicators): class and the hybrid
+ * weights phi[e][r] at both edges. Returns gamma. */
+template <class T>
+double hybrid_weights(const OrcParams& P, const WenoCoeffs& W, double lam, const T* v5, T phi[2][3], uint8_t& flag) {
+  T beta[3];
+  for (int r = 0; r < 3; ++r) beta[r] = beta_of(W, r, v5, lam);
+  const T tau = vabs(beta[0] - beta[2]);
+  const T gam = tau / ((beta[0] + beta[1] + beta[2]) / T(3.0) + T(P.eps_weno));
+  flag = value(gam) <= 0.5 ? 0 : (value(gam) >= 1.0 ? 2 : 1);
+  for (int e = 0; e < 2; ++e) {
+    if (flag == 0) {
+      for (int r = 0; r < 3; ++r) phi[e][r] = T(W.d[e][r]);
+      continue;
+    }
+    T al[3], sum = T(0.0);
+    for (int r = 0; r < 3; ++r) {
+      T q = tau / (beta[r] + T(P.eps_weno));
+      al[r] = T(W.d[e][r]) * (T(1.0) + q * q);
+      sum += al[r];
+    }
+    for (int r = 0; r < 3; ++r) phi[e][r] = al[r] / sum;
+    if (flag == 1) {
+      T Mg = T(2.0) * gam - T(1.0);
+      for (int r = 0; r < 3; ++r) phi[e][r] = Mg * phi[e][r] + (T(1.0) - Mg) * T(W.d[e][r]);
+    }
+  }
+  return value(gam);
+}
+
+/* Step 4 for one field: sum_r phi_r p_r at edge e. */
+template <class T>
+T edge_value(const WenoCoeffs& W, const T phi[2][3], const T* v5, int e) {
+  T v = T(0.0);
+  for (int r = 0; r < 3; ++r) {
+    T p = T(0.0);
+    for (int i = 0; i < 3; ++i) p += T(W.c[e][r][i]) * v5[2 - r + i];
+    v += phi[e][r] * p;
+  }
+  return v;
+}
+
+template <class T>
+struct EdgeVals;
+
+/* Edge values of the non-well-balanced scheme (Sec. 2.2, last paragraph: local characteristic
+ * decomposition for systems). Reading: the eigenvectors of the flux Jacobian d f / d (eta, hu)
+ * = [[0, 1], [c^2 - u^2, 2u]] are taken at cell j's average state (u = hu/h, c = sqrt(g h)),
+ * R = [[1, 1], [u - c, u + c]]; the five stencil averages are projected with R^-1, each
+ * characteristic field is reconstructed with its own indicators, class and weights, and the
+ * edge values are mapped back with R. Where the cell is dry (h <= h_dry) the fields are eta and
+ * hu themselves. The bottom is reconstructed on its own. The reported class is the largest of
+ * the three fields'. */
+template <class T>
+void nonwb_edges(const OrcParams& P, const WenoCoeffs& W, double lam, const T* e5, const T* m5, const T* b5,
+                 EdgeVals<T>& o);
+
 /* Per-cell result of the reconstruction + limiter (cells -1 .. N). Edge e = 0 is the left
  * edge x_{j-1/2}^+ of the cell, e = 1 the right edge x_{j+1/2}^-. */
 template <class T>
@@ -218,6 +278,46 @@ struct EdgeVals {
   uint8_t flag;        // 0 smooth, 1 transition, 2 non-smooth (Step 2)
   double gamma;        // detector value
 };
+
+template <class T>
+void nonwb_edges(const OrcParams& P, const WenoCoeffs& W, double lam, const T* e5, const T* m5, const T* b5,
+                 EdgeVals<T>& o) {
+  const double hb = value(e5[2]) - value(b5[2]);
+  double u = 0.0, c = 0.0;
+  const bool wet = hb > P.h_dry;
+  if (wet) {
+    u = value(m5[2]) / hb;
+    c = std::sqrt(P.g * hb);
+  }
+  T w1[5], w2[5];
+  for (int k = 0; k < 5; ++k) {
+    if (wet) {  // R^-1 = 1/(2c) [[u + c, -1], [-(u - c), 1]]
+      w1[k] = (T(u + c) * e5[k] - m5[k]) / T(2.0 * c);
+      w2[k] = (m5[k] - T(u - c) * e5[k]) / T(2.0 * c);
+    } else {
+      w1[k] = e5[k];
+      w2[k] = m5[k];
+    }
+  }
+  T p1[2][3], p2[2][3], pb[2][3];
+  uint8_t f1, f2, fb;
+  const double g1 = hybrid_weights(P, W, lam, w1, p1, f1);
+  const double g2 = hybrid_weights(P, W, lam, w2, p2, f2);
+  const double gb = hybrid_weights(P, W, lam, b5, pb, fb);
+  o.flag = std::max(f1, std::max(f2, fb));
+  o.gamma = std::max(g1, std::max(g2, gb));
+  for (int e = 0; e < 2; ++e) {
+    const T a = edge_value(W, p1, w1, e), b = edge_value(W, p2, w2, e);
+    if (wet) {
+      o.E[e] = a + b;
+      o.M[e] = T(u - c) * a + T(u + c) * b;
+    } else {
+      o.E[e] = a;
+      o.M[e] = b;
+    }
+    o.B[e] = edge_value(W, pb, b5, e);
+  }
+}
 
 /* Ghost index map for the three ghost cells on each side. */
 int64_t ghost_src(int64_t i, int64_t N, int bc) {
@@ -282,6 +382,9 @@ double reconstruct(const OrcParams& P, int64_t N, const T* E, const T* M, const 
     EdgeVals<T>& o = ed[j + 1];
     o.flag = flag;
     o.gamma = value(gam);
+    if (P.scheme == 1) {
+      nonwb_edges(P, W, lam, e5, m5, b5, o);
+    } else
     for (int e = 0; e < 2; ++e) {
       // Step 3: phi^L = d, phi^N = WENO-Z, phi^T = M(gamma) phi^N + (1 - M(gamma)) phi^L.
       T phi[3];
@@ -408,6 +511,19 @@ void rhs(const OrcParams& P, int64_t N, const std::vector<EdgeVals<T>>& ed, cons
     const T EL = l.E[1], ER = r.E[0], BL = l.B[1], BR = r.B[0];
     const T hL = l.h[1], hR = r.h[0], uL = l.u[1], uR = r.u[0];
     const T wk = T(w[k]), al = T(alpha);
+    if (P.scheme == 1) {
+      // Non-well-balanced scheme (Eq. alpha2D on q = (eta, hu)): plain Lax-Friedrichs flux of
+      // H = F(q) - w q with the limited edge states; discharge h u (zero on dry edges).
+      const T mL = hL * uL, mR = hR * uR;
+      const T al2 = T(alpha);
+      FE[k] = T(0.5) * ((mL - wk * EL) + (mR - wk * ER)) - T(0.5) * al2 * (ER - EL);
+      const T H2 = T(0.5) * ((mL * uL + T(0.5 * g) * hL * hL - wk * mL) + (mR * uR + T(0.5 * g) * hR * hR - wk * mR)) -
+                   T(0.5) * al2 * (mR - mL);
+      FMm[k] = H2;
+      FMp[k] = H2;
+      FB[k] = T(0.5) * wk * (BL + BR) + T(0.5) * al2 * (BR - BL);
+      continue;
+    }
     // Hydrostatic reconstruction (Eq. HH2D): h*,+- = max(0, eta+- - max(b+, b-)).
     const T bstar = vmax(BL, BR);
     const T sL = vmax(T(0.0), EL - bstar), sR = vmax(T(0.0), ER - bstar);
@@ -646,6 +762,7 @@ OrcParams to_params(const double* p, const int32_t* ip) {
   P.mesh_T = p[5]; P.gauss_sigma = p[6]; P.t_end = p[7]; P.dt_fixed = p[8];
   P.bc = ip[0]; P.mesh = ip[1]; P.gauss_half = ip[2]; P.beta_dx_global = ip[3];
   P.bottom_mode = ip[4];
+  P.scheme = ip[5];
   P.bpieces = (int32_t)g_bbreaks.size() - 1;
   P.bdeg = g_bdeg;
   P.bbreaks = g_bbreaks.data();
