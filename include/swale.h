@@ -61,6 +61,14 @@ typedef enum {
                                  end nodes fixed */
 } swale_mesh;
 
+typedef enum {
+  SWALE_SCHEME_HYDROSTATIC = 0, /* well-balanced scheme with hydrostatic reconstruction (Sec. 4.1):
+                                   shared-indicator reconstruction of (eta, hu, b), modified flux */
+  SWALE_SCHEME_NONWB = 1        /* the ALE-WENO scheme of Eq. se2D / s2D: local characteristic
+                                   reconstruction of (eta, hu), plain Lax-Friedrichs flux (not
+                                   well-balanced; the paper's baseline) */
+} swale_scheme;
+
 /* Scheme and run constants. Defaults used in the paper: g = 9.812, cfl = 0.6 (0.08 for
  * wet/dry problems), eps_weno = 1e-6 (Step 2 of Sec. 2.2), eps_pp = 1e-11 (Eq. modifiedhjn). */
 typedef struct {
@@ -77,6 +85,7 @@ typedef struct {
   int32_t mesh;        /* swale_mesh */
   int32_t gauss_half;  /* filter truncation half-width in nodes, <= 64 */
   int32_t beta_dx_global; /* 1: Delta x in the indicators is max_j J_j (Step 1); 0: local J_j */
+  int32_t scheme;      /* swale_scheme */
 } swale_config;
 
 /* Creates a context bound to a CUDA stream (cudaStream_t; NULL = legacy default stream).

@@ -111,6 +111,7 @@ StepConst step_const(const swale_ctx* ctx) {
   K.alpha_cap = ctx->alpha_cap;
   K.alpha_base = ctx->alpha_base;
   K.alpha_mode = ctx->alpha_mode;
+  K.scheme = ctx->cfg.scheme;
   K.bot_pieces = ctx->bot_pieces;
   K.bot_deg = ctx->bot_deg;
   K.bot_breaks = ctx->bot_breaks;
@@ -199,6 +200,10 @@ swale_status check_config(const swale_config* c, std::string& why) {
   }
   if (c->mesh < 0 || c->mesh > 2) {
     why = "mesh must be 0 (static), 1 (profile) or 2 (fluid_gauss)";
+    return SWALE_EINVAL;
+  }
+  if (c->scheme < 0 || c->scheme > 1) {
+    why = "scheme must be 0 (hydrostatic) or 1 (nonwb)";
     return SWALE_EINVAL;
   }
   if (c->mesh == SWALE_MESH_PROFILE && !(c->mesh_T > 0)) {
@@ -296,6 +301,12 @@ swale_status timed_launch(swale_ctx* ctx, int family, F&& launch) {
 template <int STAGE>
 void launch_recon(const StepConst& K, const DevState& D, int T, unsigned grid, cudaStream_t s, const double* E,
                   const double* M, const double* B, const double* J) {
+  if (K.scheme == SWALE_SCHEME_NONWB) {
+    if (T == 64) k_recon<STAGE, 64, 0, 1><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
+    else if (T == 256) k_recon<STAGE, 256, 0, 1><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
+    else k_recon<STAGE, 128, 0, 1><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
+    return;
+  }
   if (T == 64) k_recon<STAGE, 64><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
   else if (T == 256) k_recon<STAGE, 256><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
   else k_recon<STAGE, 128><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
@@ -1082,6 +1093,8 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     return fail(ctx, SWALE_EINVAL, "the adjoint needs a prescribed mesh (static or profile motion)");
   if (ctx->cfg.t_end > 0.0) return fail(ctx, SWALE_EINVAL, "the adjoint runs a fixed number of steps: t_end = 0");
   if (ctx->bot_pieces > 0) return fail(ctx, SWALE_EINVAL, "the adjoint evolves the bottom (no L2-projection bottom)");
+  if (ctx->cfg.scheme != SWALE_SCHEME_HYDROSTATIC)
+    return fail(ctx, SWALE_EINVAL, "the adjoint differentiates the hydrostatic well-balanced scheme");
   const int64_t B = ctx->B, Nt = ctx->Ntot, NN = Nt + B, NE = Nt + 2 * B;
   const int64_t C = std::min(ckpt_every, nsteps), nseg = (nsteps + C - 1) / C;
   cudaStream_t st = ctx->stream;
@@ -1340,6 +1353,7 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   K.alpha_mode = 0;
   K.bot_pieces = K.bot_deg = 0;
   K.bot_breaks = K.bot_coef = nullptr;
+  K.scheme = SWALE_SCHEME_HYDROSTATIC;
   // The scalars keep the previous call's contents: start them from zero (J^n minimum at 1 so
   // the stage-1 time-step arithmetic stays finite; its result is not used here).
   InstConst ic0;

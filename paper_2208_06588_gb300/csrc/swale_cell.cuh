@@ -45,6 +45,7 @@ struct SchemeConst {
   int32_t beta_dx_global;
 };
 
+
 // Status bits accumulated on the device.
 enum : uint32_t {
   ST_EWEIGHT = 1u,    // a linear weight d_r <= 0
@@ -138,67 +139,61 @@ struct StencilDD {
   real D3[3][3];
 };
 
-// Reconstruction of cell j (Steps 1-4 of Sec. 2.2 with the shared indicators of
-// Eq. alphamodified), bound-preserving limiter (Eq. modifiedhjn in 1D with the 4-point
-// Gauss-Lobatto rule) and the bottom re-derivation of the Remark in Sec. 4.3.
-//   h[5]      widths J_{j-2..j+2};   v0[v][a] averages of (eta, hu, b) on cells j-2+a, a = 0..2
-//   DD        shared divided differences;   dxmax  the global cell length (Step 1)
-// Outputs the limited edge state and the class (wave speeds: wave_speed on the edge state).
-// Only the cell's own width is checked (every cell checks its own).
-SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
-                         real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
+// Mesh-only data of cell j (Step 1): Newton-form factors of the sub-stencil quadratics at the
+// two edges, the linear weights d_r there, and the factors of the smoothness indicators.
+//   h[5]  widths J_{j-2..j+2};  dx  the cell length in the indicators (Step 1)
+struct CellGeom {
+  real G1[2][3], G2[2][3], d[2][3], F[3], c3, c4;
+};
+SWALE_HD void cell_geom(const real h[5], real dx, CellGeom& G, uint32_t& st) {
   const real h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3], h4 = h[4];
   if (!gt0(h2)) st |= ST_EMESH;
-  const real dx = P.beta_dx_global ? dxmax : h2;
   // Node offsets relative to x_{j-1/2}: y0 = -(h0+h1), y1 = -h1, y2 = 0, y3 = h2,
   // y4 = h2+h3, y5 = h2+h3+h4. Newton-form factors of p_r at the left (x = 0) and right
   // (x = h2) edges: G1 = (x-y_a) + (x-y_{a+1}), G2 = sum of pairwise products of
   // (x-y_a), (x-y_{a+1}), (x-y_{a+2}); sub-stencil r starts at cell a = 2 - r.
   const real s01 = h0 + h1, s12 = h1 + h2, s23 = h2 + h3;
   const real s012 = s01 + h2;
-  real G1[2][3], G2[2][3];
-  G1[0][0] = s01 + h1;
-  G2[0][0] = s01 * h1;
-  G1[0][1] = h1;
-  G2[0][1] = -(h1 * h2);
-  G1[0][2] = -h2;
-  G2[0][2] = h2 * s23;
-  G1[1][0] = s012 + s12;
-  G2[1][0] = s12 * h2 + s012 * (h2 + s12);
-  G1[1][1] = s12 + h2;
-  G2[1][1] = s12 * h2;
-  G1[1][2] = h2;
-  G2[1][2] = -(h2 * h3);
+  G.G1[0][0] = s01 + h1;
+  G.G2[0][0] = s01 * h1;
+  G.G1[0][1] = h1;
+  G.G2[0][1] = -(h1 * h2);
+  G.G1[0][2] = -h2;
+  G.G2[0][2] = h2 * s23;
+  G.G1[1][0] = s012 + s12;
+  G.G2[1][0] = s12 * h2 + s012 * (h2 + s12);
+  G.G1[1][1] = s12 + h2;
+  G.G2[1][1] = s12 * h2;
+  G.G1[1][2] = h2;
+  G.G2[1][2] = -(h2 * h3);
   // Linear weights (closed forms), one division for the four outer weights.
   const real Sa = s012 + h3;         // y4 - y0
   const real Sb = Sa + h4;           // y5 - y0
   const real Sc = s12 + h3 + h4;     // y5 - y1
   const real inv = recip(Sa * Sb * Sc);
   const real iab = Sc * inv, icb = Sa * inv;  // 1/(Sa Sb), 1/(Sc Sb)
-  real d[2][3];
-  d[1][2] = h3 * (h3 + h4) * iab;
-  d[1][0] = s12 * s012 * icb;
-  d[0][2] = s23 * (s23 + h4) * iab;
-  d[0][0] = h1 * s01 * icb;
-  d[0][1] = 1.0 - d[0][0] - d[0][2];
-  d[1][1] = 1.0 - d[1][0] - d[1][2];
-  if (!gt0(d[0][1]) || !gt0(d[1][1])) st |= ST_EWEIGHT;
-  // Indicators of h = eta - b and hu, summed (shared weights). F[a] = 1.5 h2 - (y_a+y_{a+1}+y_{a+2}).
-  const real F[3] = {1.5 * h2 + s01 + h1, 0.5 * h2 + h1, -(0.5 * h2 + h3)};
-  const real c4 = 4.0 * dx * h2;
-  const real c3 = (3.0 * h2 * h2 + 36.0 * dx * dx) * dx * h2;
-  real beta[3];
-  for (int r = 0; r < 3; ++r) {
-    const int a = 2 - r;
-    const real d2h = DD.D2[0][a] - DD.D2[2][a], d3h = DD.D3[0][a] - DD.D3[2][a];
-    const real qh = d2h + d3h * F[a], qm = DD.D2[1][a] + DD.D3[1][a] * F[a];
-    beta[r] = c4 * (qh * qh + qm * qm) + c3 * (d3h * d3h + DD.D3[1][a] * DD.D3[1][a]);
-  }
+  G.d[1][2] = h3 * (h3 + h4) * iab;
+  G.d[1][0] = s12 * s012 * icb;
+  G.d[0][2] = s23 * (s23 + h4) * iab;
+  G.d[0][0] = h1 * s01 * icb;
+  G.d[0][1] = 1.0 - G.d[0][0] - G.d[0][2];
+  G.d[1][1] = 1.0 - G.d[1][0] - G.d[1][2];
+  if (!gt0(G.d[0][1]) || !gt0(G.d[1][1])) st |= ST_EWEIGHT;
+  // Indicator factors: F[a] = 1.5 h2 - (y_a+y_{a+1}+y_{a+2}); beta = c4 q^2 + c3 D3^2 per variable.
+  G.F[0] = 1.5 * h2 + s01 + h1;
+  G.F[1] = 0.5 * h2 + h1;
+  G.F[2] = -(0.5 * h2 + h3);
+  G.c4 = 4.0 * dx * h2;
+  G.c3 = (3.0 * h2 * h2 + 36.0 * dx * dx) * dx * h2;
+}
+
+// Steps 2-3 from the indicators beta[3]: the class (smooth if gamma <= 1/2, non-smooth if
+// gamma >= 1, gamma = tau / (beta^A + eps)) and the hybrid weights phi[e][r] at both edges
+// (linear / WENO-Z / blend with M = 2 gamma - 1).
+SWALE_HD uint8_t hybrid_phi(const SchemeConst& P, const real beta[3], const real d[2][3], real phi[2][3]) {
   const real tau = dabs(beta[0] - beta[2]);
   const real den = (beta[0] + beta[1] + beta[2]) * (1.0 / 3.0) + P.eps_weno;  // beta^A + eps
-  // gamma = tau / den: smooth if gamma <= 1/2, non-smooth if gamma >= 1.
-  flag = le_nn(tau, 0.5 * den) ? 0 : (le_nn(den, tau) ? 2 : 1);
-  real phi[2][3];
+  const uint8_t flag = le_nn(tau, 0.5 * den) ? 0 : (le_nn(den, tau) ? 2 : 1);
   if (flag == 0) {
     for (int e = 0; e < 2; ++e)
       for (int r = 0; r < 3; ++r) phi[e][r] = d[e][r];
@@ -226,19 +221,27 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3]
         for (int r = 0; r < 3; ++r) phi[e][r] = Mg * phi[e][r] + (1.0 - Mg) * d[e][r];
     }
   }
-  // Edge values of eta, hu, b with the shared weights (Step 4).
-  real ev[3][2];
-  for (int v = 0; v < 3; ++v)
-    for (int e = 0; e < 2; ++e) {
-      real s = 0.0;
-      for (int r = 0; r < 3; ++r) {
-        const int a = 2 - r;
-        s += phi[e][r] * (v0[v][a] + DD.D2[v][a] * G1[e][a] + DD.D3[v][a] * G2[e][a]);
-      }
-      ev[v][e] = s;
-    }
-  // Limiter on h = eta - b with the Gauss-Lobatto mean delta; hu scaled by the same theta.
-  real hbar = v0[0][2] - v0[2][2];
+  return flag;
+}
+
+// Step 4 for one variable: sum_r phi_r p_r at edge e, p_r in Newton form from the average v0[a]
+// and the divided differences D2[a], D3[a] of its sub-stencil (a = 2 - r).
+SWALE_HD real edge_value(const CellGeom& G, const real phi[2][3], const real v0[3], const real D2[4], const real D3[3],
+                         int e) {
+  real s = 0.0;
+  for (int r = 0; r < 3; ++r) {
+    const int a = 2 - r;
+    s += phi[e][r] * (v0[a] + D2[a] * G.G1[e][a] + D3[a] * G.G2[e][a]);
+  }
+  return s;
+}
+
+// Limiter on h = eta - b with the Gauss-Lobatto mean delta (Eq. modifiedhjn, xd in 1D; hu
+// scaled by the same theta), b re-derived as eta - h (Remark in Sec. 4.3) and velocities.
+//   ev[v][e]  edge values of (eta, hu, b);  hbar0, mbar  the cell's depth and discharge means
+SWALE_HD void limit_cell(const SchemeConst& P, const real ev[3][2], real hbar0, real mbar, EdgeState& o,
+                         uint32_t& st) {
+  real hbar = hbar0;
   if (dlt(hbar, -P.eps_pp)) st |= ST_NEGDEPTH;
   hbar = pos0(hbar);
   real hL = ev[0][0] - ev[2][0], hR = ev[0][1] - ev[2][1];
@@ -248,7 +251,6 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3]
   real mL = ev[1][0], mR = ev[1][1];
   if (dlt(mn, epsv)) {
     const real theta = (hbar - epsv) * recip(hbar - mn);
-    const real mbar = v0[1][2];
     hL = theta * (hL - hbar) + hbar;
     hR = theta * (hR - hbar) + hbar;
     mL = theta * (mL - mbar) + mbar;
@@ -268,6 +270,100 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3]
   o.uR = wetR ? mR * hLs * ihh : real(0.0);
   // NaN propagates into the comparisons as false: catch it explicitly.
   if (bad(o.EL) || bad(o.ER) || bad(hL) || bad(hR) || bad(mL) || bad(mR)) st |= ST_NONFINITE;
+}
+
+// Reconstruction of cell j (Steps 1-4 of Sec. 2.2 with the shared indicators of
+// Eq. alphamodified), bound-preserving limiter (Eq. modifiedhjn in 1D with the 4-point
+// Gauss-Lobatto rule) and the bottom re-derivation of the Remark in Sec. 4.3.
+//   h[5]      widths J_{j-2..j+2};   v0[v][a] averages of (eta, hu, b) on cells j-2+a, a = 0..2
+//   DD        shared divided differences;   dxmax  the global cell length (Step 1)
+// Outputs the limited edge state and the class (wave speeds: wave_speed on the edge state).
+// Only the cell's own width is checked (every cell checks its own).
+SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
+                         real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
+  CellGeom G;
+  cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
+  // Indicators of h = eta - b and hu, summed (shared weights).
+  real beta[3];
+  for (int r = 0; r < 3; ++r) {
+    const int a = 2 - r;
+    const real d2h = DD.D2[0][a] - DD.D2[2][a], d3h = DD.D3[0][a] - DD.D3[2][a];
+    const real qh = d2h + d3h * G.F[a], qm = DD.D2[1][a] + DD.D3[1][a] * G.F[a];
+    beta[r] = G.c4 * (qh * qh + qm * qm) + G.c3 * (d3h * d3h + DD.D3[1][a] * DD.D3[1][a]);
+  }
+  real phi[2][3];
+  flag = hybrid_phi(P, beta, G.d, phi);
+  // Edge values of eta, hu, b with the shared weights (Step 4).
+  real ev[3][2];
+  for (int v = 0; v < 3; ++v)
+    for (int e = 0; e < 2; ++e) ev[v][e] = edge_value(G, phi, v0[v], DD.D2[v], DD.D3[v], e);
+  limit_cell(P, ev, v0[0][2] - v0[2][2], v0[1][2], o, st);
+}
+
+// Reconstruction of cell j for the non-well-balanced scheme (Eq. se2D / s2D; Sec. 2.2, last
+// paragraph: local characteristic decomposition). The eigenvectors of d f / d (eta, hu) =
+// [[0, 1], [c^2 - u^2, 2u]] at the cell's average state (u = hu / h, c = sqrt(g h)),
+// R = [[1, 1], [u - c, u + c]], project the stencil data (averages and, being linear maps of
+// them, the divided differences) onto two characteristic fields; each field and the bottom get
+// their own indicators, class and weights; the edge values are mapped back with R. A dry cell
+// (h <= h_dry) reconstructs eta and hu themselves. The class is the largest of the three.
+SWALE_HD void recon_cell_nonwb(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
+                               real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
+  CellGeom G;
+  cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
+  const real hb = v0[0][2] - v0[2][2];
+  const bool wet = dlt(P.h_dry, hb);
+  // Rows of R^-1 = 1/(2c) [[u + c, -1], [-(u - c), 1]] (identity when dry).
+  real a11 = 1.0, a12 = 0.0, a21 = 0.0, a22 = 1.0, u = 0.0, c = 0.0;
+  if (wet) {
+    u = v0[1][2] * recip(hb);
+    c = dsqrt(P.g * hb);
+    const real i2c = 0.5 * recip(c);
+    a11 = (u + c) * i2c;
+    a12 = -i2c;
+    a21 = (c - u) * i2c;
+    a22 = i2c;
+  }
+  real fv0[3][3], fD2[3][4], fD3[3][3];
+  for (int a = 0; a < 3; ++a) {
+    fv0[0][a] = a11 * v0[0][a] + a12 * v0[1][a];
+    fv0[1][a] = a21 * v0[0][a] + a22 * v0[1][a];
+    fv0[2][a] = v0[2][a];
+    fD3[0][a] = a11 * DD.D3[0][a] + a12 * DD.D3[1][a];
+    fD3[1][a] = a21 * DD.D3[0][a] + a22 * DD.D3[1][a];
+    fD3[2][a] = DD.D3[2][a];
+  }
+  for (int a = 0; a < 4; ++a) {
+    fD2[0][a] = a11 * DD.D2[0][a] + a12 * DD.D2[1][a];
+    fD2[1][a] = a21 * DD.D2[0][a] + a22 * DD.D2[1][a];
+    fD2[2][a] = DD.D2[2][a];
+  }
+  real fe[3][2];
+  flag = 0;
+  for (int f = 0; f < 3; ++f) {
+    real beta[3];
+    for (int r = 0; r < 3; ++r) {
+      const int a = 2 - r;
+      const real q = fD2[f][a] + fD3[f][a] * G.F[a];
+      beta[r] = G.c4 * (q * q) + G.c3 * (fD3[f][a] * fD3[f][a]);
+    }
+    real phi[2][3];
+    const uint8_t fl = hybrid_phi(P, beta, G.d, phi);
+    flag = fl > flag ? fl : flag;
+    for (int e = 0; e < 2; ++e) fe[f][e] = edge_value(G, phi, fv0[f], fD2[f], fD3[f], e);
+  }
+  real ev[3][2];
+  for (int e = 0; e < 2; ++e) {
+    if (wet) {
+      ev[0][e] = fe[0][e] + fe[1][e];
+      ev[1][e] = (u - c) * fe[0][e] + (u + c) * fe[1][e];
+    } else {
+      ev[0][e] = fe[0][e];
+      ev[1][e] = fe[1][e];
+    }
+    ev[2][e] = fe[2][e];
+  }
+  limit_cell(P, ev, hb, v0[1][2], o, st);
 }
 
 // ------------------------------------------------------------------------------------
@@ -291,6 +387,23 @@ SWALE_HD Flux interface_flux(real g, real alpha, real w, real EL, real ER, real 
                   0.5 * alpha * (mR - mL);
   f.FMm = H2 + hg * (hL * hL - sL * sL);
   f.FMp = H2 + hg * (hR * hR - sR * sR);
+  f.FB = 0.5 * w * (BL + BR) + 0.5 * alpha * (BR - BL);
+  return f;
+}
+
+// Interface flux of the non-well-balanced scheme: the plain Lax-Friedrichs flux of
+// H = F(q) - w q on q = (eta, hu) (Eq. alpha2D) with the limited edge states, discharge h u
+// (zero on dry edges); one momentum flux for both cells; the bottom flux of Eq. bottomrk.
+SWALE_HD Flux interface_flux_plain(real g, real alpha, real w, real EL, real ER, real BL, real BR, real hL,
+                                   real hR, real uL, real uR) {
+  const real mL = hL * uL, mR = hR * uR;
+  Flux f;
+  f.FE = 0.5 * ((mL - w * EL) + (mR - w * ER)) - 0.5 * alpha * (ER - EL);
+  const real hg = 0.5 * g;
+  const real H2 = 0.5 * ((mL * uL + hg * hL * hL - w * mL) + (mR * uR + hg * hR * hR - w * mR)) -
+                  0.5 * alpha * (mR - mL);
+  f.FMm = H2;
+  f.FMp = H2;
   f.FB = 0.5 * w * (BL + BR) + 0.5 * alpha * (BR - BL);
   return f;
 }

@@ -76,6 +76,7 @@ struct StepConst {
   int64_t alpha_cap;   // steps the log holds
   int64_t alpha_base;  // step counter value of log row 0
   int32_t alpha_mode;
+  int32_t scheme;  // SWALE_SCHEME_*
   // L2-projection bottom (Eq. baverage); bot_pieces == 0: b evolves by Eq. bottomrk.
   int32_t bot_pieces, bot_deg;
   const double* bot_breaks;  // bot_pieces + 1 breakpoints
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevSta
 // reciprocals for the update kernel of the same stage, reduces the wave speed, and in stage 1
 // the instance's last tile computes its dt (and the secant factor of the prescribed motion).
 // ------------------------------------------------------------------------------------
-template <int STAGE, int T, int MODE = 0>
+template <int STAGE, int T, int MODE = 0, int SCHEME = 0>
 __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
                                              const double* __restrict__ Mg, const double* __restrict__ Bg,
                                              const double* __restrict__ Jg) {
@@ -428,7 +429,8 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
       const double dxmax = bitsd(S->Jmax[STAGE - 1]);
       EdgeState o;
       uint8_t flag;
-      swale::recon_cell(K.sc, h, v0, DD, dxmax, o, flag, st);
+      if (SCHEME == 1) swale::recon_cell_nonwb(K.sc, h, v0, DD, dxmax, o, flag, st);
+      else swale::recon_cell(K.sc, h, v0, DD, dxmax, o, flag, st);
       const int64_t idx = eb + c + 1;
       D.eEL[idx] = o.EL;
       D.eER[idx] = o.ER;
@@ -564,8 +566,11 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
         // Interface k: left state = right edge of cell k-1 (edge index k), right state = left
         // edge of cell k (edge index k+1).
         const int64_t el = eb + k, er = eb + k + 1;
-        const swale::Flux F = swale::interface_flux(K.sc.g, alpha, wk, D.eER[el], D.eEL[er], D.eBR[el], D.eBL[er],
-                                                    D.ehR[el], D.ehL[er], D.euR[el], D.euL[er]);
+        const swale::Flux F =
+            K.scheme == 1 ? swale::interface_flux_plain(K.sc.g, alpha, wk, D.eER[el], D.eEL[er], D.eBR[el], D.eBL[er],
+                                                        D.ehR[el], D.ehL[er], D.euR[el], D.euL[er])
+                          : swale::interface_flux(K.sc.g, alpha, wk, D.eER[el], D.eEL[er], D.eBR[el], D.eBL[er],
+                                                  D.ehR[el], D.ehL[er], D.euR[el], D.euL[er]);
         sF[0][i] = F.FE;
         sF[1][i] = F.FMm;
         sF[2][i] = F.FMp;

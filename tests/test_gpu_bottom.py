@@ -81,7 +81,8 @@ def test_lake_at_rest_with_projected_polynomial_bottom():
     assert np.abs(g["eta"] - 10.0).max() < 1e-12
     assert np.abs(g["hu"]).max() < 1e-11
     bn = np.array([oracle.bottom_average(P, g["x"][j], g["x"][j + 1]) for j in range(N)])
-    np.testing.assert_allclose(g["b"], bn, rtol=1e-13, atol=1e-15)
+    # near x = 10 the monomial terms (~100) cancel to ~1e-4: absolute rounding ~1e-14
+    np.testing.assert_allclose(g["b"], bn, rtol=1e-13, atol=1e-13)
 
 
 def test_batch_with_projected_bottom_equals_single_instances():
