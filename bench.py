@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=4000)
     ap.add_argument("--batched-adjoint-steps", type=int, default=256)
     ap.add_argument("--no-batched-adjoint", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variant-steps", type=int, default=100)
     return ap.parse_args()
 
 
@@ -389,6 +391,57 @@ def bench_batched_adjoint(args, stream, dev=None, rank=0, ws=1):
     return out
 
 
+def bench_variant(args, stream, pr, scheme="hydrostatic", bottom=None):
+    """One single-instance workload with a scheme variant: K graph-replayed steps timed with CUDA
+    events, then K steps with per-kernel events for the roofline of the dominant kernel."""
+    import torch
+    from paper_2208_06588_gb300 import binding as B
+    from paper_2208_06588_gb300 import opcount
+    K = args.variant_steps
+    cfg = B.make_config(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, gauss_sigma=pr.gauss_sigma,
+                        gauss_half=pr.gauss_half, bc=pr.bc, mesh=pr.mesh, scheme=scheme)
+    ctx = B.swale_create(cfg, stream.cuda_stream)
+    B.swale_set_problem(ctx, pr.N, pr.x, pr.E, pr.hu, pr.b, pr.profile, 1)
+    if bottom is not None:
+        B.swale_set_bottom_function(ctx, *bottom)
+    B.swale_enqueue(ctx, args.warmup)
+    ms = _timed(stream, lambda: B.swale_enqueue(ctx, K))
+    B.swale_set_timing(ctx, True)
+    B.swale_enqueue(ctx, K)
+    fam = B.swale_get_timing(ctx)
+    B.swale_set_timing(ctx, False)
+    bits, steps, _ = B.swale_get_status(ctx)
+    B.swale_destroy(ctx)
+    oc = opcount.count_stage(pr.E, pr.hu, pr.b, pr.J, bc=pr.bc, sample=1 << 16, scheme=scheme)
+    dom = "reconstruction" if fam["reconstruction"][0] >= fam["update"][0] else "update"
+    fl = oc["recon_flops"] if dom == "reconstruction" else oc["update_flops"]
+    ms_dom, n_dom = fam[dom]
+    achieved = fl * pr.N / (ms_dom / n_dom * 1e-3) / 1e12
+    return {"value": pr.N * K / (ms * 1e-3), "unit": UNIT, "steps": K, "ms_per_step": ms / K, "status_bits": bits,
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_cell": fl,
+                         "avg_launch_ms": ms_dom / n_dom},
+            "fp64_flops_per_cell_stage": {"recon": oc["recon_flops"], "update": oc["update_flops"]}}
+
+
+def bench_variants(args, stream):
+    """The scheme variants beside the default one, at 2^20 cells: the non-well-balanced scheme
+    (characteristic reconstruction, plain LF flux) on the dam-break workload, and the L2-projection
+    bottom on the dam break over a rectangular bump with the bump-aligned mesh."""
+    from paper_2208_06588_gb300 import workloads as W
+    out = {}
+    pr = problem()
+    r = bench_variant(args, stream, pr, scheme="nonwb")
+    r["workload"] = WORKLOAD + "; non-well-balanced scheme (Eq. se2D / s2D)"
+    out["nonwb_dam_break"] = r
+    pr = W.bump_dam_break(N=N_CELLS)
+    r = bench_variant(args, stream, pr, bottom=pr.meta["bottom"])
+    r["workload"] = ("bump_dam_break: N=2^20 cells on [0,1500], b = 8 on [562.5,937.5], eta = 20 / 15, transmissive, "
+                     "bump-aligned motion (Eq. wangge3, T = 60), L2-projection bottom (Eq. baverage), CFL 0.6")
+    out["l2_bottom_bump_dam_break"] = r
+    return out
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle (plain C++ FP64, one thread), each step one SSP-RK3 step of
     a 2^15-cell sample of the same workload."""
@@ -507,6 +560,10 @@ def main():
         if not args.no_batched_adjoint:
             batched_adjoint = bench_batched_adjoint(args, stream, dev, rank, ws)
 
+    variants = None
+    if not args.no_variants:
+        variants = bench_variants(args, stream)
+
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
@@ -543,7 +600,7 @@ def main():
                       "l2": "working set ~230 MB per stage > 126 MB L2 (no flush needed)"},
            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
            "status_bits": bits, "steps_done_device": steps_done, "last_dt": last_dt, "batched": batched,
-           "adjoint": adjoint, "batched_adjoint": batched_adjoint,
+           "adjoint": adjoint, "batched_adjoint": batched_adjoint, "variants": variants,
            "fp64_ops_per_cell_stage": oc}
     print(json.dumps(out), flush=True)
     if ws > 1:

@@ -58,7 +58,7 @@ extern "C" {
 // out[10..14]: one interface flux alone; out[15..17]: smooth / transition / non-smooth cells.
 void opc_count_stage(int64_t N, const double* E, const double* M, const double* B, const double* J, int32_t bc,
                      double g, double eps_weno, double eps_pp, double h_dry, double alpha, int64_t c0, int64_t c1,
-                     double* out) {
+                     double* out, int32_t scheme) {
   using opc::CD;
   swale::SchemeConst P{g, eps_weno, eps_pp, h_dry, 1};
   double dxmax = 0.0;
@@ -102,14 +102,17 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
     swale::EdgeState o;
     uint8_t flag;
     uint32_t st = 0;
-    swale::recon_cell(P, h5, v0, DD, CD(dxmax), o, flag, st);
+    if (scheme == 1) swale::recon_cell_nonwb(P, h5, v0, DD, CD(dxmax), o, flag, st);
+    else swale::recon_cell(P, h5, v0, DD, CD(dxmax), o, flag, st);
     add_to(rec);
     cls[flag] += 1;
     // Update: one flux (the cell's right interface, with its own edges standing in for the
     // neighbour's), its reciprocal width, the source and the flux differences.
     opc::C = opc::Counts();
-    const swale::Flux F = swale::interface_flux(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL, o.uR,
-                                                o.uL);
+    const swale::Flux F =
+        scheme == 1 ? swale::interface_flux_plain(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL,
+                                                  o.uR, o.uL)
+                    : swale::interface_flux(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL, o.uR, o.uL);
     const CD iJc = CD(1.0) / Jv[3];
     const swale::SourceGeom sg =
         swale::source_geom(Jv[2], Jv[3], CD(1.0 / Jv[2].v), iJc, CD(1.0 / Jv[4].v), ip[2], ip[3], it[2]);
