@@ -29,7 +29,7 @@ ST_EWEIGHT, ST_NEGDEPTH, ST_NONFINITE, ST_EMESH = 1, 2, 4, 8
 
 BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
 MESH = {"static": 0, "profile": 1, "fluid_gauss": 2}
-SCHEME = {"hydrostatic": 0, "nonwb": 1}
+SCHEME = {"hydrostatic": 0, "nonwb": 1, "special": 2}
 
 
 def build(force: bool = False) -> str:
@@ -68,6 +68,10 @@ def lib():
         L.orc_tangent.argtypes = [P(d), P(i32), i64, P(d), P(d), P(d), P(d), P(d), P(d), P(d), i64, P(d), P(d),
                                   P(d), P(d), P(d)]
         L.orc_tangent.restype = u32
+        L.orc_weno_point.argtypes = [P(d), d, P(d), P(d), P(d)]
+        L.orc_weno_point.restype = None
+        L.orc_point_phi.argtypes = [P(d), P(i32), P(d), P(d), i32, P(d)]
+        L.orc_point_phi.restype = None
         L.orc_set_bottom.argtypes = [i32, i32, P(d), P(d)]
         L.orc_set_bottom.restype = None
         L.orc_bottom_average.argtypes = [P(d), P(i32), d, d]
@@ -105,7 +109,8 @@ class Params:
     # Eq. bottomrk.
     bottom: tuple | None = None
     # "hydrostatic": the well-balanced scheme of Sec. 4.1; "nonwb": the ALE-WENO scheme of
-    # Eq. se2D / s2D with local characteristic reconstruction and the plain LF flux.
+    # Eq. se2D / s2D with local characteristic reconstruction and the plain LF flux; "special":
+    # the well-balanced scheme with the special source term of Sec. 4.2 (Eq. special2D).
     scheme: str = "hydrostatic"
 
     def arrays(self):
@@ -119,6 +124,21 @@ class Params:
         ip = np.array([BC[self.bc], MESH[self.mesh], self.gauss_half, self.beta_dx_global, mode,
                        SCHEME[self.scheme]], dtype=np.int32)
         return p, ip
+
+
+def weno_point(w5, t):
+    """Mesh-only data at unit coordinate t of the cell: c[3,3], big[5], linear weights d[3]."""
+    c, big, d = np.zeros(9), np.zeros(5), np.zeros(3)
+    lib().orc_weno_point(_p(_f64(w5)), float(t), _p(c), _p(big), _p(d))
+    return {"c": c.reshape(3, 3), "big": big, "d": d}
+
+
+def point_phi(params: Params, d, beta, flag):
+    """Hybrid weights at a point (with the negative-weight split) for linear weights d."""
+    p, ip = params.arrays()
+    phi = np.zeros(3)
+    lib().orc_point_phi(_p(p), _p(ip, ctypes.c_int32), _p(_f64(d)), _p(_f64(beta)), int(flag), _p(phi))
+    return phi
 
 
 def bottom_average(params: Params, a, c):

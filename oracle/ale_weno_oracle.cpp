@@ -196,6 +196,97 @@ void weno_coeffs(const double* w5, WenoCoeffs& W) {
   }
 }
 
+/* Mesh-only WENO data of cell j at an arbitrary point t of its unit coordinate (Step 1 at a
+ * point other than an edge, e.g. the Gauss-Lobatto points of the special source term):
+ * c[r][i] weights of ubar_{j-r+i} in p_r(t), big[i] weights of ubar_{j-2+i} in the quartic at
+ * t, and the linear weights d_r(t) (matching the outermost coefficients as at the edges; at
+ * interior points they may be negative). */
+struct PointCoeffs {
+  double c[3][3];
+  double big[5];
+  double d[3];
+};
+
+void weno_point(const double* w5, double t, PointCoeffs& Q) {
+  double y[6];
+  y[2] = 0.0;
+  y[3] = 1.0;
+  y[1] = -w5[1] / w5[2];
+  y[0] = y[1] - w5[0] / w5[2];
+  y[4] = 1.0 + w5[3] / w5[2];
+  y[5] = y[4] + w5[4] / w5[2];
+  double sub[3][9], big[25];
+  for (int r = 0; r < 3; ++r) average_poly_map(3, y + 2 - r, sub[r]);
+  average_poly_map(5, y, big);
+  for (int r = 0; r < 3; ++r)
+    for (int i = 0; i < 3; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += sub[r][k * 3 + i] * ipow(t, k);
+      Q.c[r][i] = s;
+    }
+  for (int i = 0; i < 5; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < 5; ++k) s += big[k * 5 + i] * ipow(t, k);
+    Q.big[i] = s;
+  }
+  Q.d[2] = Q.big[0] / Q.c[2][0];
+  Q.d[0] = Q.big[4] / Q.c[0][2];
+  Q.d[1] = 1.0 - Q.d[0] - Q.d[2];
+}
+
+/* Hybrid weights at a point with linear weights d (Step 3), with the treatment of negative
+ * linear weights of Shi, Hu & Shu (2002) cited in Sec. 2.2: when some d_r <= 0 the WENO-Z part
+ * splits d = s+ d+ - s- d-, with d~+ = (d + 3|d|) / 2, d~- = d~+ - d, s+- = sum d~+-,
+ * d+- = d~+- / s+-; each group gets its own normalised WENO-Z weights w+- (same indicators)
+ * and phi^N = s+ w+ - s- w-. Smooth class: phi = d; transition: the blend of Step 3. */
+template <class T>
+void point_phi(const OrcParams& P, const double d[3], const T beta[3], const T& tau, const T& gam, uint8_t flag,
+               T phi[3]) {
+  if (flag == 0) {
+    for (int r = 0; r < 3; ++r) phi[r] = T(d[r]);
+    return;
+  }
+  T X[3];
+  for (int r = 0; r < 3; ++r) {
+    T q = tau / (beta[r] + T(P.eps_weno));
+    X[r] = T(1.0) + q * q;
+  }
+  T phiN[3];
+  if (d[0] > 0.0 && d[1] > 0.0 && d[2] > 0.0) {
+    T al[3], s = T(0.0);
+    for (int r = 0; r < 3; ++r) {
+      al[r] = T(d[r]) * X[r];
+      s += al[r];
+    }
+    for (int r = 0; r < 3; ++r) phiN[r] = al[r] / s;
+  } else {
+    double dp[3], dm[3], sp = 0.0, sm = 0.0;
+    for (int r = 0; r < 3; ++r) {
+      dp[r] = 0.5 * (d[r] + 3.0 * std::fabs(d[r]));
+      dm[r] = dp[r] - d[r];
+      sp += dp[r];
+      sm += dm[r];
+    }
+    T ap[3], am[3], Sp = T(0.0), Sm = T(0.0);
+    for (int r = 0; r < 3; ++r) {
+      ap[r] = T(dp[r] / sp) * X[r];
+      am[r] = T(dm[r] / sm) * X[r];
+      Sp += ap[r];
+      Sm += am[r];
+    }
+    for (int r = 0; r < 3; ++r) phiN[r] = T(sp) * ap[r] / Sp - T(sm) * am[r] / Sm;
+  }
+  if (flag == 1) {
+    T Mg = T(2.0) * gam - T(1.0);
+    for (int r = 0; r < 3; ++r) phi[r] = Mg * phiN[r] + (T(1.0) - Mg) * T(d[r]);
+  } else {
+    for (int r = 0; r < 3; ++r) phi[r] = phiN[r];
+  }
+}
+
+/* Interior 4-point Gauss-Lobatto points of the unit cell (the special source term). */
+const double kGLoT[2] = {0.5 - 0.5 / 2.2360679774997896964, 0.5 + 0.5 / 2.2360679774997896964};
+
 /* Smoothness indicator of Step 2 for the sub-stencil polynomial p_r of data v5, with the
  * factor lam = Delta x / J_j carrying the global cell length into unit coordinates:
  *   beta_r = sum_{l=1,2} (Delta x)^{2l-1} int_cell (d^l p_r / dx^l)^2 dx
@@ -275,6 +366,7 @@ template <class T>
 struct EdgeVals {
   T E[2], M[2], B[2];  // surface level, discharge, bottom (bottom re-derived after limiting)
   T h[2], u[2];        // limited depth and velocity
+  T Eg[2];             // special source scheme: eta at the two interior Gauss-Lobatto points
   uint8_t flag;        // 0 smooth, 1 transition, 2 non-smooth (Step 2)
   double gamma;        // detector value
 };
@@ -421,6 +513,23 @@ double reconstruct(const OrcParams& P, int64_t N, const T* E, const T* M, const 
       o.B[e] = vb;
     }
 
+    if (P.scheme == 2) {
+      // Special source scheme: eta at the interior Gauss-Lobatto points by the same hybrid
+      // reconstruction (shared indicators and class of this cell), linear weights at the point.
+      for (int q = 0; q < 2; ++q) {
+        PointCoeffs Q;
+        weno_point(w5, kGLoT[q], Q);
+        T phi[3];
+        point_phi(P, Q.d, beta, tau, gam, flag, phi);
+        T v = T(0.0);
+        for (int r = 0; r < 3; ++r) {
+          T pe = T(0.0);
+          for (int i = 0; i < 3; ++i) pe += T(Q.c[r][i]) * e5[2 - r + i];
+          v += phi[r] * pe;
+        }
+        o.Eg[q] = v;
+      }
+    }
     // Bound-preserving limiter in 1D: 4-point Gauss-Lobatto rule (k >= (p+2)/2 with p = 5),
     // end weights sigma_1 = sigma_4 = 1/12. The interior mean delta follows from
     // hbar = (1 - 2/12) delta + (h^L + h^R)/12.
@@ -511,8 +620,9 @@ void rhs(const OrcParams& P, int64_t N, const std::vector<EdgeVals<T>>& ed, cons
     const T EL = l.E[1], ER = r.E[0], BL = l.B[1], BR = r.B[0];
     const T hL = l.h[1], hR = r.h[0], uL = l.u[1], uR = r.u[0];
     const T wk = T(w[k]), al = T(alpha);
-    if (P.scheme == 1) {
-      // Non-well-balanced scheme (Eq. alpha2D on q = (eta, hu)): plain Lax-Friedrichs flux of
+    if (P.scheme == 1 || P.scheme == 2) {
+      // Non-well-balanced and special source schemes (Eq. alpha2D on q = (eta, hu), Eq. special2D):
+      // plain Lax-Friedrichs flux of
       // H = F(q) - w q with the limited edge states; discharge h u (zero on dry edges).
       const T mL = hL * uL, mR = hR * uR;
       const T al2 = T(alpha);
@@ -566,6 +676,33 @@ void rhs(const OrcParams& P, int64_t N, const std::vector<EdgeVals<T>>& ed, cons
         ea[k] += T(map[k * 5 + i]) * edat[i];
         ba[k] += T(map[k * 5 + i]) * bdat[i];
       }
+    }
+    if (P.scheme == 2) {
+      // Special source term (Eq. source2 in 1D with Eq. bhat2D): (g/2) [b^2 hat] - g etabar
+      // [b hat] over the two edges (outward normals +-1), plus the 4-point Gauss-Lobatto sum
+      // of -g (eta - etabar) b_x (Eq. gausssij2). eta at the points: the edge values and the
+      // interior hybrid reconstructions; b_x: the derivative of the cell's bottom interpolant
+      // (reading: a fifth-order value needs a fourth-order slope, which the sub-stencil
+      // quadratics with the value weights do not give).
+      const EdgeVals<T>& lft = ed[j];
+      const EdgeVals<T>& rgt = ed[j + 2];
+      const T bR = T(0.5) * (c.B[1] + rgt.B[0]), bL = T(0.5) * (lft.B[1] + c.B[0]);
+      const T b2R = T(0.5) * (c.B[1] * c.B[1] + rgt.B[0] * rgt.B[0]);
+      const T b2L = T(0.5) * (lft.B[1] * lft.B[1] + c.B[0] * c.B[0]);
+      const double tgl[4] = {0.0, kGLoT[0], kGLoT[1], 1.0};
+      const double wgl[4] = {1.0 / 12.0, 5.0 / 12.0, 5.0 / 12.0, 1.0 / 12.0};
+      const T eta[4] = {c.E[0], c.Eg[0], c.Eg[1], c.E[1]};
+      T S2 = T(0.0);
+      for (int q = 0; q < 4; ++q) {
+        T dbh = T(0.0);
+        for (int k = 1; k < 5; ++k) dbh += T((double)k * ipow(tgl[q], k - 1)) * ba[k];
+        S2 += T(wgl[q]) * (eta[q] - E[j]) * dbh;
+      }
+      const T Ssp = T(0.5 * g) * (b2R - b2L) - T(g) * E[j] * (bR - bL) - T(g) * S2;
+      RE[j] = -(FE[j + 1] - FE[j]);
+      RM[j] = -(FMm[j + 1] - FMp[j]) + Ssp;
+      RB[j] = FB[j + 1] - FB[j];
+      continue;
     }
     T S = T(0.0);
     for (int q = 0; q < 4; ++q) {
@@ -786,6 +923,25 @@ void orc_set_bottom(int32_t npieces, int32_t deg, const double* breaks, const do
   g_bbreaks.assign(breaks, breaks + npieces + 1);
   g_bcoef.assign(coef, coef + (size_t)npieces * (deg + 1));
   g_bdeg = deg;
+}
+
+/* Point data of one cell (weno_point): c[9], big[5], d[3] at unit coordinate t. */
+void orc_weno_point(const double* w5, double t, double* c, double* big, double* d) {
+  PointCoeffs Q;
+  weno_point(w5, t, Q);
+  std::memcpy(c, Q.c, sizeof(Q.c));
+  std::memcpy(big, Q.big, sizeof(Q.big));
+  std::memcpy(d, Q.d, sizeof(Q.d));
+}
+
+/* Hybrid weights at a point (point_phi) for linear weights d[3], indicators beta[3] and class
+ * flag (gamma from beta as in Step 2). */
+void orc_point_phi(const double* p, const int32_t* ip, const double* d, const double* beta, int32_t flag,
+                   double* phi) {
+  OrcParams P = to_params(p, ip);
+  const double tau = std::fabs(beta[0] - beta[2]);
+  const double gam = tau / ((beta[0] + beta[1] + beta[2]) / 3.0 + P.eps_weno);
+  point_phi(P, d, beta, tau, gam, (uint8_t)flag, phi);
 }
 
 /* Average of the bottom over [a, c] (the projection of one cell). */
