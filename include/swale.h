@@ -64,9 +64,14 @@ typedef enum {
 typedef enum {
   SWALE_SCHEME_HYDROSTATIC = 0, /* well-balanced scheme with hydrostatic reconstruction (Sec. 4.1):
                                    shared-indicator reconstruction of (eta, hu, b), modified flux */
-  SWALE_SCHEME_NONWB = 1        /* the ALE-WENO scheme of Eq. se2D / s2D: local characteristic
+  SWALE_SCHEME_NONWB = 1,       /* the ALE-WENO scheme of Eq. se2D / s2D: local characteristic
                                    reconstruction of (eta, hu), plain Lax-Friedrichs flux (not
                                    well-balanced; the paper's baseline) */
+  SWALE_SCHEME_SPECIAL = 2      /* well-balanced scheme with the special source term (Sec. 4.2,
+                                   Eq. special2D): the hydrostatic scheme's reconstruction, plain
+                                   LF flux, source split as in Eq. source2 with a Gauss-Lobatto
+                                   sum at reconstructed interior points (negative linear weights
+                                   there treated by the split of Shi, Hu & Shu) */
 } swale_scheme;
 
 /* Scheme and run constants. Defaults used in the paper: g = 9.812, cfl = 0.6 (0.08 for

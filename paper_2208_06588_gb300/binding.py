@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "SWALE_OK", -1: "SWALE_EINVAL", -2: "SWALE_ENOMEM", -3: "SWAL
 BIT_EWEIGHT, BIT_NEGDEPTH, BIT_NONFINITE, BIT_EMESH = 1, 2, 4, 8
 BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
 MESH = {"static": 0, "profile": 1, "fluid_gauss": 2}
-SCHEME = {"hydrostatic": 0, "nonwb": 1}
+SCHEME = {"hydrostatic": 0, "nonwb": 1, "special": 2}
 
 
 class SwaleConfig(ctypes.Structure):

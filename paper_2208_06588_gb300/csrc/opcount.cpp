@@ -102,7 +102,9 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
     swale::EdgeState o;
     uint8_t flag;
     uint32_t st = 0;
+    CD etaG[2];
     if (scheme == 1) swale::recon_cell_nonwb(P, h5, v0, DD, CD(dxmax), o, flag, st);
+    else if (scheme == 2) swale::recon_cell_special(P, h5, v0, DD, CD(dxmax), o, flag, st, etaG);
     else swale::recon_cell(P, h5, v0, DD, CD(dxmax), o, flag, st);
     add_to(rec);
     cls[flag] += 1;
@@ -110,7 +112,7 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
     // neighbour's), its reciprocal width, the source and the flux differences.
     opc::C = opc::Counts();
     const swale::Flux F =
-        scheme == 1 ? swale::interface_flux_plain(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL,
+        scheme != 0 ? swale::interface_flux_plain(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL,
                                                   o.uR, o.uL)
                     : swale::interface_flux(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL, o.uR, o.uL);
     const CD iJc = CD(1.0) / Jv[3];
@@ -118,7 +120,13 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
         swale::source_geom(Jv[2], Jv[3], CD(1.0 / Jv[2].v), iJc, CD(1.0 / Jv[4].v), ip[2], ip[3], it[2]);
     const CD hd[5] = {V[0][2] - V[2][2], V[0][3] - V[2][3], V[0][4] - V[2][4], o.hL, o.hR};
     const CD bd[5] = {V[2][2], V[2][3], V[2][4], o.BL, o.BR};
-    const CD Sj = swale::source_cell(CD(g), hd, bd, sg);
+    CD Sj;
+    if (scheme == 2) {
+      const CD eta4[4] = {o.EL, etaG[0], etaG[1], o.ER};
+      Sj = swale::source_cell_special(CD(g), V[0][3], eta4, bd, sg, o.BL, o.BR);
+    } else {
+      Sj = swale::source_cell(CD(g), hd, bd, sg);
+    }
     (void)swale::cell_rhs(F, F, Sj);
     add_to(upd);
     // The three depth averages above are formed once per cell in the kernel: remove the two

@@ -179,6 +179,10 @@ swale_status alloc_state(swale_ctx* ctx, int64_t B, int64_t Ntot, DevState& D) {
   double** edges[] = {&D.eEL, &D.eER, &D.eBL, &D.eBR, &D.ehL, &D.ehR, &D.euL, &D.euR, &D.ipair, &D.itri};
   for (double** p : edges)
     if (swale_status s = dalloc(ctx, ctx->allocs, p, ne)) return s;
+  if (ctx->cfg.scheme == SWALE_SCHEME_SPECIAL) {
+    if (swale_status s = dalloc(ctx, ctx->allocs, &D.eG1, ne)) return s;
+    if (swale_status s = dalloc(ctx, ctx->allocs, &D.eG2, ne)) return s;
+  }
   if (swale_status s = dalloc(ctx, ctx->allocs, &D.flags, ne)) return s;
   if (swale_status s = dalloc(ctx, ctx->allocs, &D.IC, (size_t)B)) return s;
   if (swale_status s = dalloc(ctx, ctx->allocs, &D.S, (size_t)B)) return s;
@@ -202,8 +206,8 @@ swale_status check_config(const swale_config* c, std::string& why) {
     why = "mesh must be 0 (static), 1 (profile) or 2 (fluid_gauss)";
     return SWALE_EINVAL;
   }
-  if (c->scheme < 0 || c->scheme > 1) {
-    why = "scheme must be 0 (hydrostatic) or 1 (nonwb)";
+  if (c->scheme < 0 || c->scheme > 2) {
+    why = "scheme must be 0 (hydrostatic), 1 (nonwb) or 2 (special)";
     return SWALE_EINVAL;
   }
   if (c->mesh == SWALE_MESH_PROFILE && !(c->mesh_T > 0)) {
@@ -305,6 +309,12 @@ void launch_recon(const StepConst& K, const DevState& D, int T, unsigned grid, c
     if (T == 64) k_recon<STAGE, 64, 0, 1><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
     else if (T == 256) k_recon<STAGE, 256, 0, 1><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
     else k_recon<STAGE, 128, 0, 1><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
+    return;
+  }
+  if (K.scheme == SWALE_SCHEME_SPECIAL) {
+    if (T == 64) k_recon<STAGE, 64, 0, 2><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
+    else if (T == 256) k_recon<STAGE, 256, 0, 2><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
+    else k_recon<STAGE, 128, 0, 2><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
     return;
   }
   if (T == 64) k_recon<STAGE, 64><<<grid, 64, 0, s>>>(K, D, E, M, B, J);

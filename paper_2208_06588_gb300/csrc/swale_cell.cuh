@@ -144,6 +144,7 @@ struct StencilDD {
 //   h[5]  widths J_{j-2..j+2};  dx  the cell length in the indicators (Step 1)
 struct CellGeom {
   real G1[2][3], G2[2][3], d[2][3], F[3], c3, c4;
+  real iab, icb;  // 1 / ((y4 - y0)(y5 - y0)), 1 / ((y5 - y1)(y5 - y0))
 };
 SWALE_HD void cell_geom(const real h[5], real dx, CellGeom& G, uint32_t& st) {
   const real h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3], h4 = h[4];
@@ -172,6 +173,8 @@ SWALE_HD void cell_geom(const real h[5], real dx, CellGeom& G, uint32_t& st) {
   const real Sc = s12 + h3 + h4;     // y5 - y1
   const real inv = recip(Sa * Sb * Sc);
   const real iab = Sc * inv, icb = Sa * inv;  // 1/(Sa Sb), 1/(Sc Sb)
+  G.iab = iab;
+  G.icb = icb;
   G.d[1][2] = h3 * (h3 + h4) * iab;
   G.d[1][0] = s12 * s012 * icb;
   G.d[0][2] = s23 * (s23 + h4) * iab;
@@ -279,18 +282,22 @@ SWALE_HD void limit_cell(const SchemeConst& P, const real ev[3][2], real hbar0, 
 //   DD        shared divided differences;   dxmax  the global cell length (Step 1)
 // Outputs the limited edge state and the class (wave speeds: wave_speed on the edge state).
 // Only the cell's own width is checked (every cell checks its own).
-SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
-                         real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
-  CellGeom G;
-  cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
-  // Indicators of h = eta - b and hu, summed (shared weights).
-  real beta[3];
+// Indicators of h = eta - b and hu, summed (the shared indicators of Eq. alphamodified).
+SWALE_HD void shared_beta(const CellGeom& G, const StencilDD& DD, real beta[3]) {
   for (int r = 0; r < 3; ++r) {
     const int a = 2 - r;
     const real d2h = DD.D2[0][a] - DD.D2[2][a], d3h = DD.D3[0][a] - DD.D3[2][a];
     const real qh = d2h + d3h * G.F[a], qm = DD.D2[1][a] + DD.D3[1][a] * G.F[a];
     beta[r] = G.c4 * (qh * qh + qm * qm) + G.c3 * (d3h * d3h + DD.D3[1][a] * DD.D3[1][a]);
   }
+}
+
+SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
+                         real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
+  CellGeom G;
+  cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
+  real beta[3];
+  shared_beta(G, DD, beta);
   real phi[2][3];
   flag = hybrid_phi(P, beta, G.d, phi);
   // Edge values of eta, hu, b with the shared weights (Step 4).
@@ -364,6 +371,102 @@ SWALE_HD void recon_cell_nonwb(const SchemeConst& P, const real h[5], const real
     ev[2][e] = fe[2][e];
   }
   limit_cell(P, ev, hb, v0[1][2], o, st);
+}
+
+// Hybrid weights at an interior point (Step 3) with linear weights d(x), which may be
+// negative there; then the WENO-Z part uses the split of Shi, Hu & Shu cited in Sec. 2.2:
+// d = s+ d+ - s- d- with d~+ = (d + 3|d|) / 2, d~- = d~+ - d, s+- = sum d~+-, d+- = d~+- / s+-,
+// each group normalised on its own with the same indicators, phi^N = s+ w+ - s- w-.
+SWALE_HD void point_phi(const SchemeConst& P, const real d[3], const real beta[3], uint8_t flag, real phi[3]) {
+  if (flag == 0) {
+    for (int r = 0; r < 3; ++r) phi[r] = d[r];
+    return;
+  }
+  const real tau = dabs(beta[0] - beta[2]);
+  real X[3];
+  for (int r = 0; r < 3; ++r) {
+    const real q = tau * recip(beta[r] + P.eps_weno);
+    X[r] = 1.0 + q * q;
+  }
+  real pn[3];
+  if (gt0(d[0]) && gt0(d[1]) && gt0(d[2])) {
+    const real a0 = d[0] * X[0], a1 = d[1] * X[1], a2 = d[2] * X[2];
+    const real is = recip(a0 + a1 + a2);
+    pn[0] = a0 * is;
+    pn[1] = a1 * is;
+    pn[2] = a2 * is;
+  } else {
+    real dp[3], dm[3];
+    for (int r = 0; r < 3; ++r) {
+      dp[r] = 0.5 * (d[r] + 3.0 * dabs(d[r]));
+      dm[r] = dp[r] - d[r];
+    }
+    const real sp = dp[0] + dp[1] + dp[2], sm = dm[0] + dm[1] + dm[2];
+    real ap[3], am[3];
+    for (int r = 0; r < 3; ++r) {
+      ap[r] = dp[r] * X[r];
+      am[r] = dm[r] * X[r];
+    }
+    // s+ (ap / sum ap) with ap from the unnormalised d~+ (the normalisation cancels).
+    const real ip = sp * recip(ap[0] + ap[1] + ap[2]), im = sm * recip(am[0] + am[1] + am[2]);
+    for (int r = 0; r < 3; ++r) pn[r] = ap[r] * ip - am[r] * im;
+  }
+  if (flag == 1) {
+    const real den = (beta[0] + beta[1] + beta[2]) * (1.0 / 3.0) + P.eps_weno;
+    const real Mg = 2.0 * (tau * recip(den)) - 1.0;
+    for (int r = 0; r < 3; ++r) phi[r] = Mg * pn[r] + (1.0 - Mg) * d[r];
+  } else {
+    for (int r = 0; r < 3; ++r) phi[r] = pn[r];
+  }
+}
+
+// Interior 4-point Gauss-Lobatto points of the unit cell, (1 -+ 1/sqrt 5) / 2.
+#define SWALE_GLO_T1 0.27639320225002103036
+#define SWALE_GLO_T2 0.72360679774997896964
+
+// Reconstruction for the special source-term scheme (Sec. 4.2): that of recon_cell plus eta at
+// the two interior Gauss-Lobatto points (Eq. gausssij2) with the cell's shared indicators and
+// class. At a point at offset x from x_{j-1/2} the Newton factors are G1 = dx_a + dx_{a+1},
+// G2 = dx_a dx_{a+1} + (dx_a + dx_{a+1}) dx_{a+2} with dx_k = x - y_k, and the outer linear
+// weights follow from the Lagrange bases of the primitive:
+//   d_2 = (dx_4 dx_5 + (dx_4 + dx_5) R_0) / ((y4-y0)(y5-y0)), R_0 = dx1 dx2 dx3 / (dx2 dx3 + dx1 dx3 + dx1 dx2),
+//   d_0 = (dx_0 dx_1 + (dx_0 + dx_1) R_5) / ((y5-y1)(y5-y0)), R_5 = dx2 dx3 dx4 / (dx3 dx4 + dx2 dx4 + dx2 dx3),
+//   d_1 = 1 - d_0 - d_2 (at x = y3 they reduce to the edge weights).
+SWALE_HD void recon_cell_special(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
+                                 real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st, real etaG[2]) {
+  CellGeom G;
+  cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
+  real beta[3];
+  shared_beta(G, DD, beta);
+  real phi[2][3];
+  flag = hybrid_phi(P, beta, G.d, phi);
+  real ev[3][2];
+  for (int v = 0; v < 3; ++v)
+    for (int e = 0; e < 2; ++e) ev[v][e] = edge_value(G, phi, v0[v], DD.D2[v], DD.D3[v], e);
+  limit_cell(P, ev, v0[0][2] - v0[2][2], v0[1][2], o, st);
+  const real h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3], h4 = h[4];
+  const real y[6] = {-(h0 + h1), -h1, real(0.0), h2, h2 + h3, h2 + h3 + h4};
+  for (int q = 0; q < 2; ++q) {
+    const real x = (q == 0 ? SWALE_GLO_T1 : SWALE_GLO_T2) * h2;
+    real dx[6];
+    for (int k = 0; k < 6; ++k) dx[k] = x - y[k];
+    const real p123 = dx[1] * dx[2] * dx[3], p234 = dx[2] * dx[3] * dx[4];
+    const real R0 = p123 * recip(dx[2] * dx[3] + dx[1] * dx[3] + dx[1] * dx[2]);
+    const real R5 = p234 * recip(dx[3] * dx[4] + dx[2] * dx[4] + dx[2] * dx[3]);
+    real d[3];
+    d[2] = (dx[4] * dx[5] + (dx[4] + dx[5]) * R0) * G.iab;
+    d[0] = (dx[0] * dx[1] + (dx[0] + dx[1]) * R5) * G.icb;
+    d[1] = 1.0 - d[0] - d[2];
+    real pp[3];
+    point_phi(P, d, beta, flag, pp);
+    real s = 0.0;
+    for (int r = 0; r < 3; ++r) {
+      const int a = 2 - r;
+      const real g1 = dx[a] + dx[a + 1], g2 = dx[a] * dx[a + 1] + g1 * dx[a + 2];
+      s += pp[r] * (v0[0][a] + DD.D2[0][a] * g1 + DD.D3[0][a] * g2);
+    }
+    etaG[q] = s;
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -481,6 +584,43 @@ SWALE_HD real source_cell(real g, const real hd[5], const real bd[5], const Sour
     S += wq[q] * hv * bdv;
   }
   return -g * S;
+}
+
+// Source of the special source-term scheme for cell j (Eq. source2 with Eq. bhat2D in 1D, the
+// Gauss-Lobatto sum of Eq. gausssij2): (g/2)(b2hat_R - b2hat_L) - g etabar (bhat_R - bhat_L)
+// - g sum_q w_q (eta_q - etabar) b_h'(t_q), with b^2hat = ((b-)^2 + (b+)^2) / 2, bhat = (b- + b+) / 2
+// at the two edges and b_h' the slope of the cell's bottom interpolant (that of source_cell) at
+// the Gauss-Lobatto points t = 0, (1 -+ 1/sqrt 5)/2, 1 (weights 1/12, 5/12, 5/12, 1/12).
+//   eta4: eta at the four points;  bd: bottom data as in source_cell;  bLm: right-edge bottom of
+//   cell j-1, bRp: left-edge bottom of cell j+1.
+SWALE_HD real source_cell_special(real g, real etabar, const real eta4[4], const real bd[5], const SourceGeom& sg,
+                                  real bLm, real bRp) {
+  const real* u = bd;
+  const real o2a = (u[3] - u[0]) * sg.irm;
+  const real o2b = u[1] - u[3];
+  const real o2c = u[4] - u[1];
+  const real o2d = (u[2] - u[4]) * sg.irp;
+  const real o3a = (o2b - o2a) * sg.i1m;
+  const real o3b = o2c - o2b;
+  const real o3c = (o2d - o2c) * sg.i1p;
+  const real o4a = (o3b - o3a) * sg.i1m;
+  const real o4b = (o3c - o3b) * sg.i1p;
+  const real o5 = (o4b - o4a) * sg.i1mp;
+  const real cb[6] = {0.0, u[0], o2a, o3a, o4a, o5};
+  const double tq[4] = {0.0, SWALE_GLO_T1, SWALE_GLO_T2, 1.0};
+  const double wq[4] = {1.0 / 12.0, 5.0 / 12.0, 5.0 / 12.0, 1.0 / 12.0};
+  real S2 = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    const double t = tq[q], t2 = t * t;
+    const double md[6] = {0, 0, 1.0, 2.0 * t, 3.0 * t2 - 2.0 * t, 4.0 * t2 * t - 6.0 * t2 + 2.0 * t};
+    const double mdd[6] = {0, 0, 0.0, 2.0, 6.0 * t - 2.0, 12.0 * t2 - 12.0 * t + 2.0};
+    real bdv = 0.0;
+    for (int k = 2; k <= 5; ++k) bdv += cb[k] * ((2.0 * md[k] + t * mdd[k]) + sg.rm * mdd[k]);
+    S2 += wq[q] * (eta4[q] - etabar) * bdv;
+  }
+  const real bL = 0.5 * (bLm + u[3]), bR = 0.5 * (u[4] + bRp);
+  const real b2L = 0.5 * (bLm * bLm + u[3] * u[3]), b2R = 0.5 * (u[4] * u[4] + bRp * bRp);
+  return (0.5 * g) * (b2R - b2L) - g * etabar * (bR - bL) - g * S2;
 }
 
 // Flux differences and source of cell j: R = (R_E, R_M, R_B) of Eq. hydro2D / bottomrk.

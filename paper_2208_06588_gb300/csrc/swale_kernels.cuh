@@ -106,6 +106,7 @@ struct DevState {
   double *eEL, *eER, *eBL, *eBR, *ehL, *ehR, *euL, *euR;
   double *ipair, *itri;        // 1/(J_c + J_{c+1}) and 1/(J_{c-1} + J_c + J_{c+1}) of the stage mesh
   double* xn;                  // nodes at t_{n+1}, written by stage 2 (L2-projection bottom only)
+  double *eG1, *eG2;           // eta at the interior Gauss-Lobatto points (special source scheme only)
   uint8_t* flags;              // stage-1 classes, edge layout
   InstConst* IC;
   DevScalars* S;
@@ -429,7 +430,9 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
       const double dxmax = bitsd(S->Jmax[STAGE - 1]);
       EdgeState o;
       uint8_t flag;
+      double etaG[2] = {0.0, 0.0};
       if (SCHEME == 1) swale::recon_cell_nonwb(K.sc, h, v0, DD, dxmax, o, flag, st);
+      else if (SCHEME == 2) swale::recon_cell_special(K.sc, h, v0, DD, dxmax, o, flag, st, etaG);
       else swale::recon_cell(K.sc, h, v0, DD, dxmax, o, flag, st);
       const int64_t idx = eb + c + 1;
       D.eEL[idx] = o.EL;
@@ -440,6 +443,10 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
       D.ehR[idx] = o.hR;
       D.euL[idx] = o.uL;
       D.euR[idx] = o.uR;
+      if (SCHEME == 2) {
+        D.eG1[idx] = etaG[0];
+        D.eG2[idx] = etaG[1];
+      }
       D.ipair[idx] = sIP[tid + 2];  // pair (c, c+1)
       D.itri[idx] = sIT[tid + 1];   // triple centred at c
       if (STAGE == 1 && MODE == 0) D.flags[idx] = flag;
@@ -567,7 +574,7 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
         // edge of cell k (edge index k+1).
         const int64_t el = eb + k, er = eb + k + 1;
         const swale::Flux F =
-            K.scheme == 1 ? swale::interface_flux_plain(K.sc.g, alpha, wk, D.eER[el], D.eEL[er], D.eBR[el], D.eBL[er],
+            K.scheme != 0 ? swale::interface_flux_plain(K.sc.g, alpha, wk, D.eER[el], D.eEL[er], D.eBR[el], D.eBL[er],
                                                         D.ehR[el], D.ehL[er], D.euR[el], D.euL[er])
                           : swale::interface_flux(K.sc.g, alpha, wk, D.eER[el], D.eEL[er], D.eBR[el], D.eBL[er],
                                                   D.ehR[el], D.ehL[er], D.euR[el], D.euL[er]);
@@ -600,7 +607,14 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
                                                       D.ipair[eb + j], D.ipair[eb + j + 1], D.itri[eb + j + 1]);
       const double hd[5] = {sH[tid], sH[tid + 1], sH[tid + 2], D.ehL[ic_e], D.ehR[ic_e]};
       const double bd[5] = {sB[tid], sB[tid + 1], sB[tid + 2], D.eBL[ic_e], D.eBR[ic_e]};
-      const double Sj = swale::source_cell(K.sc.g, hd, bd, sg);
+      double Sj;
+      if (K.scheme == 2) {
+        const double eta4[4] = {D.eEL[ic_e], D.eG1[ic_e], D.eG2[ic_e], D.eER[ic_e]};
+        Sj = swale::source_cell_special(K.sc.g, E[j], eta4, bd, sg, D.eBR[ic_e - 1],
+                                        D.eBL[ic_e + 1]);
+      } else {
+        Sj = swale::source_cell(K.sc.g, hd, bd, sg);
+      }
       const swale::CellRhs R = swale::cell_rhs(Fl, Fr, Sj);
       const double RE = R.RE, RM = R.RM, RB = R.RB;
       if (MODE == 1) {

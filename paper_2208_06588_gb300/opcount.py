@@ -52,7 +52,7 @@ def count_stage(E, M, B, J, bc="transmissive", g=9.812, eps_weno=1e-6, eps_pp=1e
                           vp(J.ctypes.data), ctypes.c_int32(BC[bc]), ctypes.c_double(g), ctypes.c_double(eps_weno),
                           ctypes.c_double(eps_pp), ctypes.c_double(h_dry), ctypes.c_double(alpha),
                           ctypes.c_int64(c0), ctypes.c_int64(c0 + n), vp(out.ctypes.data),
-                          ctypes.c_int32({"hydrostatic": 0, "nonwb": 1}[scheme]))
+                          ctypes.c_int32({"hydrostatic": 0, "nonwb": 1, "special": 2}[scheme]))
     rec, upd, flux = out[0:5] / n, out[5:10] / n, out[10:15] / n
     rf = float(rec[:4].sum())
     uf = float(upd[:4].sum() + RK_OPS)

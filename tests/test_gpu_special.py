@@ -1,0 +1,124 @@
+"""Special source-term well-balanced scheme (Sec. 4.2, Eq. special2D) on the GPU against the
+oracle: smooth accuracy run, lake at rest (smooth and step bottoms), wet/dry fronts, a dam break
+on a mesh with abrupt width jumps (negative linear weights at the interior Gauss-Lobatto points,
+the Shi-Hu-Shu split), a batch, and the adjoint refusing it."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_06588_gb300 import binding as B
+from paper_2208_06588_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2208_06588_gb300 import build
+    build.build()
+    B.lib()
+
+
+def cfg_of(pr):
+    return B.make_config(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, gauss_sigma=pr.gauss_sigma,
+                         t_end=pr.t_end, dt_fixed=pr.dt_fixed, bc=pr.bc, mesh=pr.mesh, gauss_half=pr.gauss_half,
+                         scheme="special")
+
+
+def params_of(pr):
+    return oracle.Params(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, gauss_sigma=pr.gauss_sigma,
+                         t_end=pr.t_end, dt_fixed=pr.dt_fixed, bc=pr.bc, mesh=pr.mesh, gauss_half=pr.gauss_half,
+                         scheme="special")
+
+
+def run_both(pr, nsteps):
+    s = B.Solver(cfg_of(pr))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    done = s.advance(nsteps)
+    g = s.state()
+    g["bits"] = s.status()[0]
+    s.close()
+    st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+    r = oracle.run(params_of(pr), st, pr.profile, nsteps=nsteps)
+    assert done == r["steps"]
+    return g, st, r
+
+
+def max_rel(a, r):
+    return np.abs(a - r).max() / max(np.abs(r).max(), 1e-300)
+
+
+def l1_rel(a, r, J):
+    return float(np.sum(J * np.abs(a - r)) / max(np.sum(J * np.abs(r)), 1e-300))
+
+
+@pytest.mark.parametrize("N", [200, 211])
+def test_smooth_accuracy_problem(N):
+    pr = W.accuracy_test(N)
+    g, st, r = run_both(pr, 10 ** 6)
+    assert r["status"] == 0 and g["bits"] == 0 and abs(g["t"] - 0.1) < 1e-14
+    for a, ref in ((g["eta"], st.E), (g["hu"], st.M), (g["b"], st.B)):
+        assert max_rel(a, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("bottom", ["smooth", "step"])
+def test_lake_at_rest_round_off(bottom):
+    pr = W.lake_at_rest(200, bottom)
+    g, st, r = run_both(pr, 80)
+    assert np.abs(g["eta"] - 10.0).max() < 1e-11
+    assert np.abs(g["hu"]).max() < 1e-10
+
+
+def test_wet_dry_front():
+    pr = W.moses_second(200)
+    g, st, r = run_both(pr, 150)
+    assert g["bits"] & ~B.BIT_NEGDEPTH == 0
+    assert l1_rel(g["eta"], st.E, st.J) <= 1e-9
+    assert l1_rel(g["hu"], st.M, st.J) <= 1e-9
+
+
+def test_dam_break_on_jumping_widths_uses_the_split():
+    # blocks of 3 narrow and 3 wide (16x) cells: interior-point linear weights turn negative
+    N = 300
+    J = np.tile([1.0, 1.0, 1.0, 16.0, 16.0, 16.0], N // 6)
+    x = np.concatenate([[0.0], np.cumsum(J)])
+    x = x * (10.0 / x[-1])
+    J = np.diff(x)
+    neg = 0
+    for j in range(2, N - 2):
+        for t in (0.5 - 0.5 / np.sqrt(5), 0.5 + 0.5 / np.sqrt(5)):
+            neg += int((oracle.weno_point(J[j - 2:j + 3], t)["d"] <= 0).any())
+    assert neg > 0
+    xc = 0.5 * (x[1:] + x[:-1])
+    b = 0.3 * np.exp(-((xc - 5.0) / 1.5) ** 2)
+    E = np.where(xc < 4.0, 2.0, 1.2)
+    pr = W.Problem(name="jumping_widths", x=x, h=E - b, hu=np.zeros(N), b=b, E=E, profile=np.zeros(N + 1),
+                   bc="transmissive", mesh="static", cfl=0.3)
+    g, st, r = run_both(pr, 60)
+    assert r["status"] == 0 and g["bits"] == 0
+    assert l1_rel(g["eta"], st.E, st.J) <= 1e-9
+    assert l1_rel(g["hu"], st.M, st.J) <= 1e-9
+
+
+def test_batch_and_adjoint_refusal():
+    bt = W.many_basins(B=5, n_min=64, n_max=300, seed=13)
+    cfg = B.make_config(eps_weno=bt.eps_weno, mesh_T=bt.mesh_T, bc=bt.bc, mesh=bt.mesh, scheme="special")
+    s = B.Solver(cfg)
+    s.set_batch(bt)
+    s.advance(12)
+    out = s.batch_state()
+    with pytest.raises(B.SwaleError):
+        B.swale_adjoint(s.ctx, 1, 1, 1, np.full(5, 0.5), np.zeros(5), np.zeros(5), np.zeros(s.N), np.zeros(s.N),
+                        np.zeros(s.N))
+    s.close()
+    for i in range(bt.B):
+        pr = bt.instance(i)
+        c = B.make_config(eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, bc=pr.bc, mesh=pr.mesh, cfl=pr.cfl,
+                          scheme="special")
+        si = B.Solver(c)
+        si.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+        si.advance(12)
+        gi = si.state()
+        si.close()
+        a, b_ = int(bt.off[i]), int(bt.off[i + 1])
+        np.testing.assert_array_equal(out["eta"][a:b_], gi["eta"])
