@@ -426,14 +426,18 @@ def bench_variant(args, stream, pr, scheme="hydrostatic", bottom=None):
 
 def bench_variants(args, stream):
     """The scheme variants beside the default one, at 2^20 cells: the non-well-balanced scheme
-    (characteristic reconstruction, plain LF flux) on the dam-break workload, and the L2-projection
-    bottom on the dam break over a rectangular bump with the bump-aligned mesh."""
+    (characteristic reconstruction, plain LF flux) and the special source-term scheme on the
+    dam-break workload, and the L2-projection bottom on the dam break over a rectangular bump
+    with the bump-aligned mesh."""
     from paper_2208_06588_gb300 import workloads as W
     out = {}
     pr = problem()
     r = bench_variant(args, stream, pr, scheme="nonwb")
     r["workload"] = WORKLOAD + "; non-well-balanced scheme (Eq. se2D / s2D)"
     out["nonwb_dam_break"] = r
+    r = bench_variant(args, stream, pr, scheme="special")
+    r["workload"] = WORKLOAD + "; special source-term scheme (Eq. special2D)"
+    out["special_dam_break"] = r
     pr = W.bump_dam_break(N=N_CELLS)
     r = bench_variant(args, stream, pr, bottom=pr.meta["bottom"])
     r["workload"] = ("bump_dam_break: N=2^20 cells on [0,1500], b = 8 on [562.5,937.5], eta = 20 / 15, transmissive, "
