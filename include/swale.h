@@ -241,7 +241,8 @@ swale_status swale_get_alpha_log(swale_ctx* ctx, double* log);
  * initial cell averages of eta, hu and b (Ntot values each; b varied with eta fixed).
  * The gradient is that of the discrete scheme under the replay convention: dt and the stage
  * viscosities alpha are those of the forward run, detector classes, limiter branches, dry-edge
- * tests and max/min selections are frozen (a tie follows the first argument). Checkpoints of
+ * tests and max/min selections are frozen (a tie follows the first argument); if a replay log
+ * is active (swale_alpha_log mode 2) the forward run replays it instead. Checkpoints of
  * the state every ckpt_every steps; each segment is recomputed once with per-step snapshots and
  * each step once more inside its reverse sweep. Device memory beyond the context's own: about
  * 5 (ceil(nsteps/C) + C + 2) + 23 doubles per cell with C = min(ckpt_every, nsteps), exactly

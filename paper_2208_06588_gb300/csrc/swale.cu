@@ -1188,6 +1188,30 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   ctx->alpha_cap = nsteps;
   ctx->alpha_base = device_steps(ctx);
   ctx->alpha_mode = 1;
+  if (old_mode == 2 && old_log) {
+    // A replay log is active: the forward replays its rows for these steps instead of
+    // recording new values (the gradient is then that of the scheme with those alphas).
+    const int64_t row0 = ctx->alpha_base - old_base;
+    if (row0 < 0 || row0 + nsteps > old_cap) {
+      ctx->alpha_log = old_log;
+      ctx->alpha_cap = old_cap;
+      ctx->alpha_base = old_base;
+      ctx->alpha_mode = old_mode;
+      ctx->timing = old_timing;
+      return release(fail(ctx, SWALE_EINVAL, "the active alpha replay log does not cover the adjoint's steps"));
+    }
+    e = cudaMemcpyAsync(alog, old_log + row0 * B * 3, (size_t)nsteps * B * 3 * sizeof(double),
+                        cudaMemcpyDeviceToDevice, st);
+    if (e) {
+      ctx->alpha_log = old_log;
+      ctx->alpha_cap = old_cap;
+      ctx->alpha_base = old_base;
+      ctx->alpha_mode = old_mode;
+      ctx->timing = old_timing;
+      return release(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
+    }
+    ctx->alpha_mode = 2;
+  }
   auto restore_ctx = [&]() {
     drop_graph(ctx);
     ctx->alpha_log = old_log;

@@ -212,3 +212,63 @@ def test_autograd_batched_weights_each_instance():
         sl = slice(int(off[i]), int(off[i + 1]))
         for g, r in ((E.grad[sl], gEi), (Bt.grad[sl], gBi)):
             assert np.abs(g.cpu().numpy() - wgt * r).max() <= 1e-12 * np.abs(wgt * r).max()
+
+
+def test_full_size_gradient_against_finite_differences():
+    """The adjoint benchmark case at its full size (N = 65536, 4000 steps, checkpoints every 64
+    steps, 16 gauges): the gradient along smooth perturbations of eta0 and of b matches central
+    differences of the GPU forward with the stage viscosities replayed."""
+    gp = W.gauge_problem(N=65536, nsteps=4000, G=16)
+    pr, K = gp.problem, gp.nsteps
+    J, gE, gM, gB = gpu_adjoint(pr, gp.gauges, gp.h_obs, K, ckpt=64)
+    s = B.Solver(cfg_of(pr))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    B.swale_alpha_log(s.ctx, 1, K)
+    s.advance(K)
+    alog = np.zeros(3 * K)
+    B.swale_get_alpha_log(s.ctx, alog)
+    s.close()
+
+    def misfit(E0, B0):
+        s = B.Solver(cfg_of(pr))
+        s.set_problem(pr.x, E0, pr.hu, B0, pr.profile, q0_is_eta=True)
+        B.swale_alpha_log(s.ctx, 2, K, alog)
+        Jm = np.zeros(1)
+        # the misfit of a replayed forward: the adjoint call's J (its reverse sweep is unused)
+        B.swale_adjoint(s.ctx, K, 64, gp.gauges.size, gp.gauges, np.ascontiguousarray(gp.h_obs), Jm, None, None,
+                        None)
+        s.close()
+        return Jm[0]
+
+    xc = 0.5 * (pr.x[1:] + pr.x[:-1])
+    for dE, dB in ((np.exp(-((xc - 0.3) / 0.05) ** 2), 0 * xc), (0 * xc, np.exp(-((xc - 0.55) / 0.05) ** 2))):
+        eps = 1e-5
+        fd = (misfit(pr.E + eps * dE, pr.b + eps * dB) - misfit(pr.E - eps * dE, pr.b - eps * dB)) / (2 * eps)
+        ad = gE @ dE + gB @ dB
+        assert abs(fd - ad) <= 1e-5 * abs(ad), (fd, ad)
+
+
+def test_adjoint_replays_an_active_alpha_log():
+    """With a replay log active, the forward inside swale_adjoint replays it: J equals the
+    misfit of a plain replayed forward, and a log that does not cover the steps is refused."""
+    pr, gx, rng = basin(N=256, seed=4)
+    nsteps = 12
+    obs = 0.6 + 0.05 * rng.normal(size=(nsteps, gx.size))
+    s = B.Solver(cfg_of(pr))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    B.swale_alpha_log(s.ctx, 1, nsteps)
+    s.advance(nsteps)
+    alog = np.zeros(3 * nsteps)
+    B.swale_get_alpha_log(s.ctx, alog)
+    s.close()
+    alog_scaled = 1.1 * alog  # a different, fixed viscosity history
+    J_ref = gpu_misfit_replay(pr, gx, obs, nsteps, pr.E, pr.hu, pr.b, alog_scaled)
+    s = B.Solver(cfg_of(pr))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    B.swale_alpha_log(s.ctx, 2, nsteps, alog_scaled)
+    J = np.zeros(1)
+    B.swale_adjoint(s.ctx, nsteps, 4, gx.size, gx, obs, J, None, None, None)
+    assert abs(J[0] - J_ref) <= 1e-13 * J_ref
+    with pytest.raises(B.SwaleError):  # the log's rows are used up
+        B.swale_adjoint(s.ctx, nsteps, 4, gx.size, gx, obs, J, None, None, None)
+    s.close()

@@ -270,3 +270,24 @@ def test_invalid_inputs_are_rejected():
     B.swale_destroy(ctx)
     with pytest.raises(B.SwaleError):
         B.swale_create(B.make_config(bc=7))
+
+
+def test_dam_break_full_size_2000_steps_properties():
+    """The benchmark workload at its full length (N = 2^20, 2000 steps): beyond what the oracle
+    can follow, check what the scheme guarantees at any size: eta's mass is conserved (the
+    waves have not reached the ends), the depth stays non-negative (Sec. 3.4), the state stays
+    finite, and the mesh stays ordered."""
+    pr = W.dam_break_dry()
+    s = B.Solver(cfg_of(pr))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    done = s.advance(2000)
+    g = s.state()
+    bits, steps, _ = s.status()
+    s.close()
+    assert done == 2000 and steps == 2000 and (bits & ~B.BIT_NEGDEPTH) == 0
+    J = np.diff(g["x"])
+    assert J.min() > 0
+    m0 = float(np.sum(pr.J * pr.E))
+    assert abs(float(np.sum(J * g["eta"])) - m0) <= 1e-12 * m0
+    assert (g["eta"] - g["b"]).min() >= -1e-10
+    assert np.isfinite(g["hu"]).all() and np.abs(g["hu"]).max() > 0.1
