@@ -30,6 +30,10 @@ WORKLOAD = "dam_break_dry: N=2^20 cells on [0,10], FP64, transmissive, dry regio
 METRIC = "cell-updates/s FP64 (fwd, plain single instance)"
 UNIT = "cell-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
+# DRAM bytes (read + write) of one k_recon launch on this workload, from an ncu capture of the
+# current kernel (33.6 MB read: E, M, B, J once; 27.6 MB written before the rest of the edge
+# values are consumed from L2 by the update kernel).
+RECON_DRAM_BYTES = 33_610_752 + 27_561_472
 
 
 def parse():
@@ -583,7 +587,10 @@ def main():
     achieved = flops_cell * N / (ms_dom / n_dom * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": f"k_{'recon' if dom == 'reconstruction' else 'update'} (per stage)",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": None, "flops_per_cell": flops_cell, "cells_per_launch": N,
+            "traffic": RECON_DRAM_BYTES if dom == "reconstruction" else None,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum of k_recon<1>, "
+                            "N = 2^20, current kernel)",
+            "flops_per_cell": flops_cell, "cells_per_launch": N,
             "avg_launch_ms": ms_dom / n_dom,
             "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA chain: 1.195 TFLOP/s)",
             "kernel_ms_share": {k: round(v[0] / max(sum(x[0] for x in fam.values()), 1e-30), 4)
