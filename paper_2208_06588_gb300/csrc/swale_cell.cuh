@@ -564,24 +564,32 @@ SWALE_HD real source_cell(real g, const real hd[5], const real bd[5], const Sour
     c[4] = o4a;
     c[5] = o5;
   }
-  // Basis n_k = (t + rm) m_k(t), m_2 = t, m_3 = t^2, m_4 = t^3 - t^2, m_5 = t^4 - 2 t^3 + t^2:
-  // n_k' = (m_k + t m_k') + rm m_k', n_k'' = (2 m_k' + t m_k'') + rm m_k''.
-  const double tq[4] = {SWALE_GL4_T0, SWALE_GL4_T1, SWALE_GL4_T2, SWALE_GL4_T3};
-  const double wq[4] = {SWALE_GL4_W0, SWALE_GL4_W1, SWALE_GL4_W1, SWALE_GL4_W0};
+  // Basis n_k = (t + rm) m_k(t), m_2 = t, m_3 = t^2, m_4 = t^3 - t^2, m_5 = t^4 - 2 t^3 + t^2.
+  // The interpolant Pi' = c_1 + sum_k c_k n_k' in monomials a_0 + a_1 t + ... + a_4 t^4:
+  //   n_2' = 2t + rm,  n_3' = 3t^2 + 2 rm t,  n_4' = 4t^3 + 3(rm - 1) t^2 - 2 rm t,
+  //   n_5' = 5t^4 + 4(rm - 2) t^3 + 3(1 - 2 rm) t^2 + 2 rm t.
+  // The bottom's slope is the derivative of its interpolant, sum_m m ab_m t^(m-1), and the
+  // integral of the product over [0, 1] is exact: sum_{i, m} a_i ab_m m / (i + m) (the
+  // 4-point Gauss-Legendre rule of the definition is exact for this degree-7 product too).
+  const real rm = sg.rm;
+  real a[5], ab[5];
+  const real* cs[2] = {ch, cb};
+  real* ms[2] = {a, ab};
+  for (int v = 0; v < 2; ++v) {
+    const real* c = cs[v];
+    real* o = ms[v];
+    const real q = c[3] - c[4] + c[5];
+    o[0] = c[1] + c[2] * rm;
+    o[1] = 2.0 * (c[2] + rm * q);
+    o[2] = 3.0 * q + rm * (3.0 * c[4] - 6.0 * c[5]);
+    o[3] = 4.0 * (c[4] - 2.0 * c[5]) + (4.0 * rm) * c[5];
+    o[4] = 5.0 * c[5];
+  }
   real S = 0.0;
-  for (int q = 0; q < 4; ++q) {
-    const double t = tq[q], t2 = t * t, t3 = t2 * t, t4 = t3 * t;
-    const double m[6] = {0, 0, t, t2, t3 - t2, t4 - 2.0 * t3 + t2};
-    const double md[6] = {0, 0, 1.0, 2.0 * t, 3.0 * t2 - 2.0 * t, 4.0 * t3 - 6.0 * t2 + 2.0 * t};
-    const double mdd[6] = {0, 0, 0.0, 2.0, 6.0 * t - 2.0, 12.0 * t2 - 12.0 * t + 2.0};
-    real hv = ch[1], bdv = 0.0;
-    for (int k = 2; k <= 5; ++k) {
-      const real n1 = (m[k] + t * md[k]) + sg.rm * md[k];
-      const real n2 = (2.0 * md[k] + t * mdd[k]) + sg.rm * mdd[k];
-      hv += ch[k] * n1;
-      bdv += cb[k] * n2;
-    }
-    S += wq[q] * hv * bdv;
+  for (int i = 0; i < 5; ++i) {
+    const real vi = ab[1] * (1.0 / (i + 1)) + ab[2] * (2.0 / (i + 2)) + ab[3] * (3.0 / (i + 3)) +
+                    ab[4] * (4.0 / (i + 4));
+    S += a[i] * vi;
   }
   return -g * S;
 }
