@@ -50,6 +50,10 @@ int ct_recon_tangent(const double* h, const double* v0, const double* D2, const 
     for (int a = 0; a < 4; ++a) DD.D2[v][a] = D(D2[v * 4 + a], tD2[v * 4 + a]);
     for (int a = 0; a < 3; ++a) DD.D3[v][a] = D(D3[v * 3 + a], tD3[v * 3 + a]);
   }
+  // recon_cell reconstructs the depth h = eta - b in place of b: map the third variable.
+  for (int a = 0; a < 3; ++a) vv[2][a] = vv[0][a] - vv[2][a];
+  for (int a = 0; a < 4; ++a) DD.D2[2][a] = DD.D2[0][a] - DD.D2[2][a];
+  for (int a = 0; a < 3; ++a) DD.D3[2][a] = DD.D3[0][a] - DD.D3[2][a];
   swale::EdgeState o;
   uint8_t flag;
   uint32_t st = 0;

@@ -89,6 +89,9 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
       for (int a = 0; a < 4; ++a) DD.D2[v][a] = d2[v][a + 1];
       for (int a = 0; a < 3; ++a) DD.D3[v][a] = CD((d2[v][a + 2].v - d2[v][a + 1].v) * it[a + 1].v);
     }
+    // The kernels reconstruct the depth h = eta - b in place of b (uncounted input mapping).
+    for (int a = 0; a < 4; ++a) DD.D2[2][a] = CD(DD.D2[0][a].v - DD.D2[2][a].v);
+    for (int a = 0; a < 3; ++a) DD.D3[2][a] = CD(DD.D3[0][a].v - DD.D3[2][a].v);
     // The work one cell owns: its pair (c, c+1) and its triple, counted with the kernel's code.
     opc::C = opc::Counts();
     const CD ipc = swale::pair_recip(Jv[3], Jv[4]);
@@ -99,6 +102,7 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
     for (int k = 0; k < 5; ++k) h5[k] = Jv[k + 1];
     for (int v = 0; v < 3; ++v)
       for (int a = 0; a < 3; ++a) v0[v][a] = V[v][a + 1];
+    for (int a = 0; a < 3; ++a) v0[2][a] = CD(V[0][a + 1].v - V[2][a + 1].v);
     swale::EdgeState o;
     uint8_t flag;
     uint32_t st = 0;

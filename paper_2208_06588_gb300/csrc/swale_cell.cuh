@@ -131,7 +131,8 @@ SWALE_HD real triple_recip(real Jm, real Jc, real Jp) { return recip(Jm + Jc + J
 // D3 of one variable on the triple from the D2 of its two pairs.
 SWALE_HD real triple_dd(real d2l, real d2r, real it) { return (d2r - d2l) * it; }
 
-// Divided differences of the big stencil of cell j for the three variables (eta, hu, b):
+// Divided differences of the big stencil of cell j for the three variables (eta, hu, h), h =
+// eta - b the depth:
 // D2[v][a], a = 0..3 the pairs (j-2,j-1)..(j+1,j+2); D3[v][a], a = 0..2 the triples
 // starting at j-2, j-1, j.
 struct StencilDD {
@@ -241,13 +242,13 @@ SWALE_HD real edge_value(const CellGeom& G, const real phi[2][3], const real v0[
 
 // Limiter on h = eta - b with the Gauss-Lobatto mean delta (Eq. modifiedhjn, xd in 1D; hu
 // scaled by the same theta), b re-derived as eta - h (Remark in Sec. 4.3) and velocities.
-//   ev[v][e]  edge values of (eta, hu, b);  hbar0, mbar  the cell's depth and discharge means
+//   ev[v][e]  edge values of (eta, hu, h);  hbar0, mbar  the cell's depth and discharge means
 SWALE_HD void limit_cell(const SchemeConst& P, const real ev[3][2], real hbar0, real mbar, EdgeState& o,
                          uint32_t& st) {
   real hbar = hbar0;
   if (dlt(hbar, -P.eps_pp)) st |= ST_NEGDEPTH;
   hbar = pos0(hbar);
-  real hL = ev[0][0] - ev[2][0], hR = ev[0][1] - ev[2][1];
+  real hL = ev[2][0], hR = ev[2][1];
   const real delta = (12.0 * hbar - hL - hR) * 0.1;
   const real mn = dmin(dmin(hL, hR), delta);
   const real epsv = dmin(P.eps_pp, hbar);
@@ -278,15 +279,17 @@ SWALE_HD void limit_cell(const SchemeConst& P, const real ev[3][2], real hbar0, 
 // Reconstruction of cell j (Steps 1-4 of Sec. 2.2 with the shared indicators of
 // Eq. alphamodified), bound-preserving limiter (Eq. modifiedhjn in 1D with the 4-point
 // Gauss-Lobatto rule) and the bottom re-derivation of the Remark in Sec. 4.3.
-//   h[5]      widths J_{j-2..j+2};   v0[v][a] averages of (eta, hu, b) on cells j-2+a, a = 0..2
+//   h[5]      widths J_{j-2..j+2};   v0[v][a] averages of (eta, hu, h) on cells j-2+a, a = 0..2
 //   DD        shared divided differences;   dxmax  the global cell length (Step 1)
+// The depth h = eta - b is reconstructed in place of b (the same shared weights, so the edge
+// values of b = eta - h are those of reconstructing b; Sec. 4.1 items 1-2).
 // Outputs the limited edge state and the class (wave speeds: wave_speed on the edge state).
 // Only the cell's own width is checked (every cell checks its own).
 // Indicators of h = eta - b and hu, summed (the shared indicators of Eq. alphamodified).
 SWALE_HD void shared_beta(const CellGeom& G, const StencilDD& DD, real beta[3]) {
   for (int r = 0; r < 3; ++r) {
     const int a = 2 - r;
-    const real d2h = DD.D2[0][a] - DD.D2[2][a], d3h = DD.D3[0][a] - DD.D3[2][a];
+    const real d2h = DD.D2[2][a], d3h = DD.D3[2][a];
     const real qh = d2h + d3h * G.F[a], qm = DD.D2[1][a] + DD.D3[1][a] * G.F[a];
     beta[r] = G.c4 * (qh * qh + qm * qm) + G.c3 * (d3h * d3h + DD.D3[1][a] * DD.D3[1][a]);
   }
@@ -304,7 +307,7 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3]
   real ev[3][2];
   for (int v = 0; v < 3; ++v)
     for (int e = 0; e < 2; ++e) ev[v][e] = edge_value(G, phi, v0[v], DD.D2[v], DD.D3[v], e);
-  limit_cell(P, ev, v0[0][2] - v0[2][2], v0[1][2], o, st);
+  limit_cell(P, ev, v0[2][2], v0[1][2], o, st);
 }
 
 // Reconstruction of cell j for the non-well-balanced scheme (Eq. se2D / s2D; Sec. 2.2, last
@@ -318,7 +321,7 @@ SWALE_HD void recon_cell_nonwb(const SchemeConst& P, const real h[5], const real
                                real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
   CellGeom G;
   cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
-  const real hb = v0[0][2] - v0[2][2];
+  const real hb = v0[2][2];
   const bool wet = dlt(P.h_dry, hb);
   // Rows of R^-1 = 1/(2c) [[u + c, -1], [-(u - c), 1]] (identity when dry).
   real a11 = 1.0, a12 = 0.0, a21 = 0.0, a22 = 1.0, u = 0.0, c = 0.0;
@@ -332,18 +335,19 @@ SWALE_HD void recon_cell_nonwb(const SchemeConst& P, const real h[5], const real
     a22 = i2c;
   }
   real fv0[3][3], fD2[3][4], fD3[3][3];
+  // Third field: the bottom b = eta - h.
   for (int a = 0; a < 3; ++a) {
     fv0[0][a] = a11 * v0[0][a] + a12 * v0[1][a];
     fv0[1][a] = a21 * v0[0][a] + a22 * v0[1][a];
-    fv0[2][a] = v0[2][a];
+    fv0[2][a] = v0[0][a] - v0[2][a];
     fD3[0][a] = a11 * DD.D3[0][a] + a12 * DD.D3[1][a];
     fD3[1][a] = a21 * DD.D3[0][a] + a22 * DD.D3[1][a];
-    fD3[2][a] = DD.D3[2][a];
+    fD3[2][a] = DD.D3[0][a] - DD.D3[2][a];
   }
   for (int a = 0; a < 4; ++a) {
     fD2[0][a] = a11 * DD.D2[0][a] + a12 * DD.D2[1][a];
     fD2[1][a] = a21 * DD.D2[0][a] + a22 * DD.D2[1][a];
-    fD2[2][a] = DD.D2[2][a];
+    fD2[2][a] = DD.D2[0][a] - DD.D2[2][a];
   }
   real fe[3][2];
   flag = 0;
@@ -368,7 +372,7 @@ SWALE_HD void recon_cell_nonwb(const SchemeConst& P, const real h[5], const real
       ev[0][e] = fe[0][e];
       ev[1][e] = fe[1][e];
     }
-    ev[2][e] = fe[2][e];
+    ev[2][e] = ev[0][e] - fe[2][e];  // depth = eta - b
   }
   limit_cell(P, ev, hb, v0[1][2], o, st);
 }
@@ -443,7 +447,7 @@ SWALE_HD void recon_cell_special(const SchemeConst& P, const real h[5], const re
   real ev[3][2];
   for (int v = 0; v < 3; ++v)
     for (int e = 0; e < 2; ++e) ev[v][e] = edge_value(G, phi, v0[v], DD.D2[v], DD.D3[v], e);
-  limit_cell(P, ev, v0[0][2] - v0[2][2], v0[1][2], o, st);
+  limit_cell(P, ev, v0[2][2], v0[1][2], o, st);
   const real h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3], h4 = h[4];
   const real y[6] = {-(h0 + h1), -h1, real(0.0), h2, h2 + h3, h2 + h3 + h4};
   for (int q = 0; q < 2; ++q) {

@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
       sJ[i] = jv;
       sV[0][i] = ev;
       sV[1][i] = mv;
-      sV[2][i] = bv;
+      sV[2][i] = ev - bv;  // the depth is reconstructed in place of the bottom
     }
     __syncthreads();
     for (int i = tid; i < T + 3; i += T) {
