@@ -55,7 +55,8 @@ extern "C" {
 // (add, mul, div, sqrt, cmp): the pair and triple terms a cell owns plus recon_cell;
 // out[5..9]: update per cell summed: one interface flux, the cell's reciprocal width, the
 // source geometry and source, the flux differences (the RK combination is added in Python);
-// out[10..14]: one interface flux alone; out[15..17]: smooth / transition / non-smooth cells.
+// out[10..14]: one interface flux alone; out[15..17]: smooth / transition / non-smooth cells;
+// out[18]: FLOPs of the mesh-only geometry (cell_geom) summed.
 void opc_count_stage(int64_t N, const double* E, const double* M, const double* B, const double* J, int32_t bc,
                      double g, double eps_weno, double eps_pp, double h_dry, double alpha, int64_t c0, int64_t c1,
                      double* out, int32_t scheme) {
@@ -65,6 +66,7 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
   for (int64_t j = 0; j < N; ++j) dxmax = J[j] > dxmax ? J[j] : dxmax;
   opc::Counts rec, upd, flux;
   long long cls[3] = {0, 0, 0};
+  double geom_flops = 0.0;
   auto add_to = [](opc::Counts& a) {
     a.add += opc::C.add; a.mul += opc::C.mul; a.div += opc::C.div; a.sqrt += opc::C.sqrt; a.cmp += opc::C.cmp;
   };
@@ -112,6 +114,14 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
     else swale::recon_cell(P, h5, v0, DD, CD(dxmax), o, flag, st);
     add_to(rec);
     cls[flag] += 1;
+    // The mesh-only part (cell_geom), which a stage on the mesh of the previous stage 2 reuses.
+    opc::C = opc::Counts();
+    {
+      swale::CellGeom Gm;
+      uint32_t sg = 0;
+      swale::cell_geom(h5, CD(dxmax), Gm, sg);
+    }
+    geom_flops += (double)(opc::C.add + opc::C.mul + opc::C.div + opc::C.sqrt);
     // Update: one flux (the cell's right interface, with its own edges standing in for the
     // neighbour's), its reciprocal width, the source and the flux differences.
     opc::C = opc::Counts();
@@ -146,6 +156,7 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
   out[15] = (double)cls[0];
   out[16] = (double)cls[1];
   out[17] = (double)cls[2];
+  out[18] = geom_flops;
 }
 
 }  // extern "C"

@@ -47,6 +47,9 @@ struct swale_ctx {
   // L2-projection bottom (swale_set_bottom_function); part of the state allocations.
   int32_t bot_pieces = 0, bot_deg = 0;
   double *bot_breaks = nullptr, *bot_coef = nullptr;
+  // Epoch of the mesh geometry cache; bumped whenever the state is set or restored, so that a
+  // cache entry written before is never taken for the restored state.
+  uint32_t geo_epoch = 1;
 };
 
 namespace {
@@ -112,11 +115,21 @@ StepConst step_const(const swale_ctx* ctx) {
   K.alpha_base = ctx->alpha_base;
   K.alpha_mode = ctx->alpha_mode;
   K.scheme = ctx->cfg.scheme;
+  K.geo_epoch = ctx->geo_epoch;
   K.bot_pieces = ctx->bot_pieces;
   K.bot_deg = ctx->bot_deg;
   K.bot_breaks = ctx->bot_breaks;
   K.bot_coef = ctx->bot_coef;
   return K;
+}
+
+void drop_graph(swale_ctx* ctx);
+
+// The state was set or restored: invalidate the mesh geometry cache (and the captured steps,
+// which carry the epoch).
+void bump_geo(swale_ctx* ctx) {
+  ++ctx->geo_epoch;
+  drop_graph(ctx);
 }
 
 void drop_graph(swale_ctx* ctx) {
@@ -183,6 +196,8 @@ swale_status alloc_state(swale_ctx* ctx, int64_t B, int64_t Ntot, DevState& D) {
     if (swale_status s = dalloc(ctx, ctx->allocs, &D.eG1, ne)) return s;
     if (swale_status s = dalloc(ctx, ctx->allocs, &D.eG2, ne)) return s;
   }
+  if (swale_status s = dalloc(ctx, ctx->allocs, &D.geo, (size_t)SWALE_GEOM_VALUES * ne)) return s;
+  D.geo_stride = (int64_t)ne;
   if (swale_status s = dalloc(ctx, ctx->allocs, &D.flags, ne)) return s;
   if (swale_status s = dalloc(ctx, ctx->allocs, &D.IC, (size_t)B)) return s;
   if (swale_status s = dalloc(ctx, ctx->allocs, &D.S, (size_t)B)) return s;
@@ -441,6 +456,7 @@ swale_status set_instances(swale_ctx* ctx, const std::vector<int64_t>& off, cons
   ctx->B = B;
   ctx->Ntot = Ntot;
   ctx->off = off;
+  bump_geo(ctx);
   DevState& D = ctx->D;
   cudaStream_t st = ctx->stream;
   const size_t cb = Ntot * sizeof(double), nb = (Ntot + B) * sizeof(double);
@@ -853,6 +869,7 @@ swale_status swale_autotune(swale_ctx* ctx, int32_t steps, const char* cache_pat
         if (s) break;
         float ms = 0.f;
         cudaError_t e = copy_state(false);
+        bump_geo(ctx);
         // One untimed step, then the timed ones.
         if (!e && !(s = enqueue_steps(ctx, 1))) {
           cudaEventRecord(e0, ctx->stream);
@@ -876,6 +893,7 @@ swale_status swale_autotune(swale_ctx* ctx, int32_t steps, const char* cache_pat
   if (!s) s = swale_set_tiles(ctx, bt[0], bt[1], bt[2], bt[3]);
   if (!s) {
     if (cudaError_t e = copy_state(false)) s = fail(ctx, SWALE_ECUDA, cudaGetErrorString(e));
+    bump_geo(ctx);
   }
   if (!s && cache_path && *cache_path) {
     std::ofstream outf(cache_path, std::ios::app);
@@ -1168,6 +1186,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     return r;
   };
   auto load = [&](const StateCopy& c) {
+    bump_geo(ctx);
     const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
     cudaError_t r = cudaMemcpyAsync(D.E0, c.E, Nt * sizeof(double), k, st);
     r = r ? r : cudaMemcpyAsync(D.M0, c.M, Nt * sizeof(double), k, st);

@@ -147,6 +147,7 @@ struct CellGeom {
   real G1[2][3], G2[2][3], d[2][3], F[3], c3, c4;
   real iab, icb;  // 1 / ((y4 - y0)(y5 - y0)), 1 / ((y5 - y1)(y5 - y0))
 };
+#define SWALE_GEOM_VALUES 25  // doubles in a CellGeom
 SWALE_HD void cell_geom(const real h[5], real dx, CellGeom& G, uint32_t& st) {
   const real h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3], h4 = h[4];
   if (!gt0(h2)) st |= ST_EMESH;
@@ -295,19 +296,23 @@ SWALE_HD void shared_beta(const CellGeom& G, const StencilDD& DD, real beta[3]) 
   }
 }
 
-SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
-                         real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
-  CellGeom G;
-  cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
+SWALE_HD void recon_cell_g(const SchemeConst& P, const CellGeom& G, const real v0[3][3], const StencilDD& DD,
+                           EdgeState& o, uint8_t& flag, uint32_t& st) {
   real beta[3];
   shared_beta(G, DD, beta);
   real phi[2][3];
   flag = hybrid_phi(P, beta, G.d, phi);
-  // Edge values of eta, hu, b with the shared weights (Step 4).
+  // Edge values of eta, hu, h with the shared weights (Step 4).
   real ev[3][2];
   for (int v = 0; v < 3; ++v)
     for (int e = 0; e < 2; ++e) ev[v][e] = edge_value(G, phi, v0[v], DD.D2[v], DD.D3[v], e);
   limit_cell(P, ev, v0[2][2], v0[1][2], o, st);
+}
+SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
+                         real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
+  CellGeom G;
+  cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
+  recon_cell_g(P, G, v0, DD, o, flag, st);
 }
 
 // Reconstruction of cell j for the non-well-balanced scheme (Eq. se2D / s2D; Sec. 2.2, last
@@ -317,10 +322,8 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3]
 // them, the divided differences) onto two characteristic fields; each field and the bottom get
 // their own indicators, class and weights; the edge values are mapped back with R. A dry cell
 // (h <= h_dry) reconstructs eta and hu themselves. The class is the largest of the three.
-SWALE_HD void recon_cell_nonwb(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
-                               real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
-  CellGeom G;
-  cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
+SWALE_HD void recon_cell_nonwb_g(const SchemeConst& P, const CellGeom& G, const real v0[3][3], const StencilDD& DD,
+                                 EdgeState& o, uint8_t& flag, uint32_t& st) {
   const real hb = v0[2][2];
   const bool wet = dlt(P.h_dry, hb);
   // Rows of R^-1 = 1/(2c) [[u + c, -1], [-(u - c), 1]] (identity when dry).
@@ -375,6 +378,12 @@ SWALE_HD void recon_cell_nonwb(const SchemeConst& P, const real h[5], const real
     ev[2][e] = ev[0][e] - fe[2][e];  // depth = eta - b
   }
   limit_cell(P, ev, hb, v0[1][2], o, st);
+}
+SWALE_HD void recon_cell_nonwb(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
+                               real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
+  CellGeom G;
+  cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
+  recon_cell_nonwb_g(P, G, v0, DD, o, flag, st);
 }
 
 // Hybrid weights at an interior point (Step 3) with linear weights d(x), which may be
@@ -436,10 +445,8 @@ SWALE_HD void point_phi(const SchemeConst& P, const real d[3], const real beta[3
 //   d_2 = (dx_4 dx_5 + (dx_4 + dx_5) R_0) / ((y4-y0)(y5-y0)), R_0 = dx1 dx2 dx3 / (dx2 dx3 + dx1 dx3 + dx1 dx2),
 //   d_0 = (dx_0 dx_1 + (dx_0 + dx_1) R_5) / ((y5-y1)(y5-y0)), R_5 = dx2 dx3 dx4 / (dx3 dx4 + dx2 dx4 + dx2 dx3),
 //   d_1 = 1 - d_0 - d_2 (at x = y3 they reduce to the edge weights).
-SWALE_HD void recon_cell_special(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
-                                 real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st, real etaG[2]) {
-  CellGeom G;
-  cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
+SWALE_HD void recon_cell_special_g(const SchemeConst& P, const CellGeom& G, const real h[5], const real v0[3][3],
+                                   const StencilDD& DD, EdgeState& o, uint8_t& flag, uint32_t& st, real etaG[2]) {
   real beta[3];
   shared_beta(G, DD, beta);
   real phi[2][3];
@@ -471,6 +478,12 @@ SWALE_HD void recon_cell_special(const SchemeConst& P, const real h[5], const re
     }
     etaG[q] = s;
   }
+}
+SWALE_HD void recon_cell_special(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
+                                 real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st, real etaG[2]) {
+  CellGeom G;
+  cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
+  recon_cell_special_g(P, G, h, v0, DD, o, flag, st, etaG);
 }
 
 // ------------------------------------------------------------------------------------

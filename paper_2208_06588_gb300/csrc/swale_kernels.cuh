@@ -24,6 +24,8 @@
 
 namespace swale_dev {
 
+static_assert(sizeof(swale::CellGeom) == SWALE_GEOM_VALUES * sizeof(double), "CellGeom holds SWALE_GEOM_VALUES doubles");
+
 using swale::EdgeState;
 using swale::SchemeConst;
 
@@ -46,6 +48,9 @@ struct DevScalars {
   unsigned int counter;              // reconstruction tiles finished in stage 1
   int done;
   int clipped;
+  // Mesh geometry cache: stage 2 stores the per-cell reconstruction geometry of the t_{n+1} mesh,
+  // which the next step's stage 1 reuses when the tag (context epoch, step index) matches.
+  unsigned long long geo_tag;
 };
 
 // Per-instance constants.
@@ -77,6 +82,7 @@ struct StepConst {
   int64_t alpha_base;  // step counter value of log row 0
   int32_t alpha_mode;
   int32_t scheme;  // SWALE_SCHEME_*
+  uint32_t geo_epoch;  // bumped by the host whenever the state is set or restored
   // L2-projection bottom (Eq. baverage); bot_pieces == 0: b evolves by Eq. bottomrk.
   int32_t bot_pieces, bot_deg;
   const double* bot_breaks;  // bot_pieces + 1 breakpoints
@@ -107,6 +113,9 @@ struct DevState {
   double *ipair, *itri;        // 1/(J_c + J_{c+1}) and 1/(J_{c-1} + J_c + J_{c+1}) of the stage mesh
   double* xn;                  // nodes at t_{n+1}, written by stage 2 (L2-projection bottom only)
   double *eG1, *eG2;           // eta at the interior Gauss-Lobatto points (special source scheme only)
+  // Geometry cache: SWALE_GEOM_VALUES arrays in the edge layout, geo[k * geo_stride + idx].
+  double* geo;
+  int64_t geo_stride;
   uint8_t* flags;              // stage-1 classes, edge layout
   InstConst* IC;
   DevScalars* S;
@@ -410,6 +419,11 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
     }
     __syncthreads();
     const int64_t c = c0 + tid;
+    const unsigned long long geo_now =
+        ((unsigned long long)K.geo_epoch << 32) | (unsigned long long)(S->step_idx & 0xffffffffLL);
+    const bool use_geo = STAGE == 1 && MODE == 0 && D.geo != nullptr && S->geo_tag == geo_now;
+    if (STAGE == 2 && MODE == 0 && D.geo != nullptr && c0 == -1 && tid == 0)
+      S->geo_tag = ((unsigned long long)K.geo_epoch << 32) | (unsigned long long)((S->step_idx + 1) & 0xffffffffLL);
     double wave = 0.0, ehL = 0.0, euL = 0.0, ehR = 0.0, euR = 0.0;
     bool useL = false, useR = false;
     uint32_t st = 0;
@@ -428,13 +442,28 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
         for (int a = 0; a < 3; ++a) DD.D3[v][a] = sD3[v][tid + a];
       }
       const double dxmax = bitsd(S->Jmax[STAGE - 1]);
+      const int64_t idx = eb + c + 1;
+      // Mesh geometry of the cell: from the cache that the previous step's stage 2 filled on the
+      // same mesh (t_{n+1}), else computed; stage 2 fills the cache.
+      swale::CellGeom G;
+      double* gv = reinterpret_cast<double*>(&G);
+      if (use_geo) {
+#pragma unroll
+        for (int k = 0; k < SWALE_GEOM_VALUES; ++k) gv[k] = D.geo[k * D.geo_stride + idx];
+        if (!swale::gt0(h[2])) st |= swale::ST_EMESH;
+      } else {
+        swale::cell_geom(h, K.sc.beta_dx_global ? dxmax : h[2], G, st);
+      }
+      if (STAGE == 2 && MODE == 0 && D.geo) {
+#pragma unroll
+        for (int k = 0; k < SWALE_GEOM_VALUES; ++k) D.geo[k * D.geo_stride + idx] = gv[k];
+      }
       EdgeState o;
       uint8_t flag;
       double etaG[2] = {0.0, 0.0};
-      if (SCHEME == 1) swale::recon_cell_nonwb(K.sc, h, v0, DD, dxmax, o, flag, st);
-      else if (SCHEME == 2) swale::recon_cell_special(K.sc, h, v0, DD, dxmax, o, flag, st, etaG);
-      else swale::recon_cell(K.sc, h, v0, DD, dxmax, o, flag, st);
-      const int64_t idx = eb + c + 1;
+      if (SCHEME == 1) swale::recon_cell_nonwb_g(K.sc, G, v0, DD, o, flag, st);
+      else if (SCHEME == 2) swale::recon_cell_special_g(K.sc, G, h, v0, DD, o, flag, st, etaG);
+      else swale::recon_cell_g(K.sc, G, v0, DD, o, flag, st);
       D.eEL[idx] = o.EL;
       D.eER[idx] = o.ER;
       D.eBL[idx] = o.BL;

@@ -46,7 +46,7 @@ def count_stage(E, M, B, J, bc="transmissive", g=9.812, eps_weno=1e-6, eps_pp=1e
     N = E.size
     n = N if sample is None else min(N, sample)
     c0 = (N - n) // 2
-    out = np.zeros(18)
+    out = np.zeros(19)
     vp = ctypes.c_void_p
     lib().opc_count_stage(ctypes.c_int64(N), vp(E.ctypes.data), vp(M.ctypes.data), vp(B.ctypes.data),
                           vp(J.ctypes.data), ctypes.c_int32(BC[bc]), ctypes.c_double(g), ctypes.c_double(eps_weno),
@@ -61,4 +61,5 @@ def count_stage(E, M, B, J, bc="transmissive", g=9.812, eps_weno=1e-6, eps_pp=1e
             "update_without_rk": dict(zip(keys, map(float, upd))),
             "one_flux": dict(zip(keys, map(float, flux))),
             "recon_flops": rf, "update_flops": uf, "stage_flops": rf + uf, "cells_counted": n,
+            "geom_flops": float(out[18] / n),
             "classes": [int(v) for v in out[15:18]]}
