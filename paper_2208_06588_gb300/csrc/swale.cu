@@ -106,6 +106,7 @@ StepConst step_const(const swale_ctx* ctx) {
   K.dt_fixed = ctx->cfg.dt_fixed;
   K.mesh_T = ctx->cfg.mesh_T;
   K.gauss_wsum = ctx->gauss_wsum;
+  K.gauss_iwsum = 1.0 / ctx->gauss_wsum;
   K.bc = ctx->cfg.bc;
   K.mesh = ctx->cfg.mesh;
   K.gauss_half = ctx->cfg.gauss_half;
@@ -1396,6 +1397,7 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   K.dt_fixed = 0.0;
   K.mesh_T = 1.0;
   K.gauss_wsum = 1.0;
+  K.gauss_iwsum = 1.0;
   K.bc = cfg->bc;
   K.mesh = SWALE_MESH_STATIC;
   K.gauss_half = 0;

@@ -73,6 +73,7 @@ struct StepConst {
   SchemeConst sc;
   double t_end, dt_fixed, mesh_T;
   double gauss_wsum;  // sum of the full Gaussian window, summed from -H to H
+  double gauss_iwsum; // its reciprocal
   int32_t bc, mesh, gauss_half, B;
   // Stage viscosities: log of 3 values per step and instance (index (step * B + i) * 3 + s - 1);
   // alpha_mode 1 records the computed values, 2 replays the logged ones (the adjoint's and the
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevSta
       double u = 0.0;
       if (c >= 0 && c < N) {
         const double h = E0[c] - B0[c];
-        u = h > K.sc.h_dry ? M0[c] / h : 0.0;
+        u = swale::dlt(K.sc.h_dry, h) ? M0[c] * swale::recip(h) : 0.0;
       }
       su[i] = u;
     }
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevSta
         double acc = 0.0;
         if (k - H >= 1 && k + H <= N - 1) {
           for (int m = -H; m <= H; ++m) acc += c_gauss_w[m + H] * sraw[i + m + H];
-          v = acc / K.gauss_wsum;
+          v = acc * K.gauss_iwsum;
         } else {
           double wsum = 0.0;
           for (int m = -H; m <= H; ++m) {
