@@ -245,7 +245,7 @@ swale_status swale_get_alpha_log(swale_ctx* ctx, double* log);
  * is active (swale_alpha_log mode 2) the forward run replays it instead. Checkpoints of
  * the state every ckpt_every steps; each segment is recomputed once with per-step snapshots and
  * each step once more inside its reverse sweep. Device memory beyond the context's own: about
- * 5 (ceil(nsteps/C) + C + 2) + 23 doubles per cell with C = min(ckpt_every, nsteps), exactly
+ * 5 (ceil(nsteps/C) + C + 2) + 43 doubles per cell with C = min(ckpt_every, nsteps), exactly
  * the value of swale_adjoint_bytes; all of it is freed before the call returns. The mesh must
  * be prescribed (static or profile motion) and t_end = 0. On return the context holds the
  * state after the nsteps steps.

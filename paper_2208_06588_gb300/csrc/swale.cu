@@ -352,9 +352,15 @@ unsigned grid_of(int32_t ntiles, int persistent) {
 }
 
 // Enqueues one step on the context's stream.
-swale_status enqueue_step(swale_ctx* ctx) {
+// Enqueues one step. stageD (optional, 3 entries): the device state each stage's kernels use;
+// copies of ctx->D that differ only in their edge arrays keep every stage's edge values (the
+// adjoint's recompute of a step).
+swale_status enqueue_step(swale_ctx* ctx, const DevState* stageD = nullptr) {
   const StepConst K = step_const(ctx);
   const DevState& D = ctx->D;
+  const DevState& D1 = stageD ? stageD[0] : D;
+  const DevState& D2 = stageD ? stageD[1] : D;
+  const DevState& D3 = stageD ? stageD[2] : D;
   cudaStream_t s = ctx->stream;
   const unsigned gr = grid_of(D.nr, ctx->grid_r), gu = grid_of(D.nu, ctx->grid_u);
   const int Tr = ctx->Tr, Tu = ctx->Tu;
@@ -368,12 +374,12 @@ swale_status enqueue_step(swale_ctx* ctx) {
     const size_t shm = (size_t)(3 * kMeshThreads + 4 * K.gauss_half + 4) * sizeof(double);
     L(FAM_MESH, [&] { k_mesh_gauss<<<(unsigned)std::max(D.nm, 1), kMeshThreads, shm, s>>>(K, D); });
   }
-  L(FAM_RECON, [&] { launch_recon<1>(K, D, Tr, gr, s, D.E0, D.M0, D.B0, D.J0); });
-  L(FAM_UPDATE, [&] { launch_update<1, 0>(K, D, Tu, gu, s, D.E0, D.M0, D.B0, D.J0, none); });
-  L(FAM_RECON, [&] { launch_recon<2>(K, D, Tr, gr, s, D.Ea, D.Ma, D.Ba, D.J1); });
-  L(FAM_UPDATE, [&] { launch_update<2, 0>(K, D, Tu, gu, s, D.Ea, D.Ma, D.Ba, D.J1, none); });
-  L(FAM_RECON, [&] { launch_recon<3>(K, D, Tr, gr, s, D.Eb, D.Mb, D.Bb, D.J2); });
-  L(FAM_UPDATE, [&] { launch_update<3, 0>(K, D, Tu, gu, s, D.Eb, D.Mb, D.Bb, D.J2, none); });
+  L(FAM_RECON, [&] { launch_recon<1>(K, D1, Tr, gr, s, D.E0, D.M0, D.B0, D.J0); });
+  L(FAM_UPDATE, [&] { launch_update<1, 0>(K, D1, Tu, gu, s, D.E0, D.M0, D.B0, D.J0, none); });
+  L(FAM_RECON, [&] { launch_recon<2>(K, D2, Tr, gr, s, D.Ea, D.Ma, D.Ba, D.J1); });
+  L(FAM_UPDATE, [&] { launch_update<2, 0>(K, D2, Tu, gu, s, D.Ea, D.Ma, D.Ba, D.J1, none); });
+  L(FAM_RECON, [&] { launch_recon<3>(K, D3, Tr, gr, s, D.Eb, D.Mb, D.Bb, D.J2); });
+  L(FAM_UPDATE, [&] { launch_update<3, 0>(K, D3, Tu, gu, s, D.Eb, D.Mb, D.Bb, D.J2, none); });
   if (st) return st;
   SW_CUDA(ctx, cudaGetLastError());
   return SWALE_OK;
@@ -1010,9 +1016,8 @@ long long device_steps(swale_ctx* ctx) {
 }
 
 template <int STAGE>
-void launch_adj_stage(swale_ctx* ctx, const StepConst& K, const AdjState& A, const double* E, const double* M,
-                      const double* B, const double* J) {
-  const DevState& D = ctx->D;
+void launch_adj_stage(swale_ctx* ctx, const DevState& D, const StepConst& K, const AdjState& A, const double* E,
+                      const double* M, const double* B, const double* J) {
   cudaStream_t s = ctx->stream;
   const unsigned gu = grid_of(D.nu, ctx->grid_u), gr = grid_of(D.nr, ctx->grid_r);
   const int Tu = ctx->Tu, Tr = ctx->Tr;
@@ -1040,15 +1045,6 @@ void launch_adj_rk(swale_ctx* ctx, const AdjState& A) {
   else k_adj_rk<PH, 128><<<gu, 128, 0, ctx->stream>>>(D, A);
 }
 
-template <int STAGE>
-void launch_recon_replay(swale_ctx* ctx, const StepConst& K, const double* E, const double* M, const double* B,
-                         const double* J) {
-  const DevState& D = ctx->D;
-  const unsigned gr = grid_of(D.nr, ctx->grid_r);
-  if (ctx->Tr == 64) k_recon<STAGE, 64, 1><<<gr, 64, 0, ctx->stream>>>(K, D, E, M, B, J);
-  else if (ctx->Tr == 256) k_recon<STAGE, 256, 1><<<gr, 256, 0, ctx->stream>>>(K, D, E, M, B, J);
-  else k_recon<STAGE, 128, 1><<<gr, 128, 0, ctx->stream>>>(K, D, E, M, B, J);
-}
 
 // Copies of the evolving state (q^n, J^n, nodes, per-instance scalars).
 struct StateCopy {
@@ -1063,7 +1059,7 @@ uint64_t adjoint_bytes(int64_t B, int64_t Nt, int64_t nsteps, int64_t ckpt_every
   const int64_t C = std::min(ckpt_every, nsteps), nseg = (nsteps + C - 1) / C;
   auto a = [](uint64_t n, uint64_t size) { return n * size + 256; };
   const uint64_t copy = 4 * a(Nt, 8) + a(NN, 8) + a(B, sizeof(DevScalars));
-  return 15 * a(Nt, 8) + 8 * a(NE, 8) + (uint64_t)(nseg + C + 2) * copy + a((uint64_t)B * G, 8) +
+  return 15 * a(Nt, 8) + 8 * a(NE, 8) + 20 * a(NE, 8) + (uint64_t)(nseg + C + 2) * copy + 2 * a((uint64_t)B * G, 8) +
          a((uint64_t)nsteps * B * G, 8) + a(B, 8) + a((uint64_t)nsteps * B * 3, 8);
 }
 
@@ -1148,6 +1144,14 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   for (double** p : cellbufs)
     if (!s) s = dalloc(ctx, mem, p, (size_t)Nt);
   for (int k = 0; k < 8 && !s; ++k) s = dalloc(ctx, mem, &A.ab[k], (size_t)NE);
+  // Edge values of stages 1 and 2 of the step being reversed (stage 3 keeps the context's).
+  DevState Ds[3] = {ctx->D, ctx->D, ctx->D};
+  for (int st2 = 0; st2 < 2 && !s; ++st2) {
+    DevState& d = Ds[st2];
+    double** ed[] = {&d.eEL, &d.eER, &d.eBL, &d.eBR, &d.ehL, &d.ehR, &d.euL, &d.euR, &d.ipair, &d.itri};
+    for (double** p : ed)
+      if (!s) s = dalloc(ctx, mem, p, (size_t)NE);
+  }
   std::vector<StateCopy> ckpt(nseg), seg(C);
   StateCopy fin, snap;
   for (auto& c : ckpt) alloc_copy(c);
@@ -1159,6 +1163,8 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   if (!s) s = dalloc(ctx, mem, &obs, (size_t)nsteps * B * G);
   if (!s) s = dalloc(ctx, mem, &Jacc, (size_t)B);
   if (!s) s = dalloc(ctx, mem, &alog, (size_t)nsteps * B * 3);
+  int64_t* gcell = nullptr;  // last cell of each gauge (searched from, the mesh moves little per step)
+  if (!s) s = dalloc(ctx, mem, &gcell, (size_t)B * G);
   if (s) return release(s);
   A.sE = snap.E;
   A.sM = snap.M;
@@ -1168,6 +1174,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   e = e ? e : cudaMemcpyAsync(gx, gauges_x, (size_t)B * G * sizeof(double), cudaMemcpyDefault, st);
   e = e ? e : cudaMemcpyAsync(obs, h_obs, (size_t)nsteps * B * G * sizeof(double), cudaMemcpyDefault, st);
   e = e ? e : cudaMemsetAsync(Jacc, 0, B * sizeof(double), st);
+  e = e ? e : cudaMemsetAsync(gcell, 0xff, (size_t)B * G * sizeof(int64_t), st);  // -1: not yet located
   e = e ? e : cudaMemsetAsync(A.aE, 0, Nt * sizeof(double), st);
   e = e ? e : cudaMemsetAsync(A.aM, 0, Nt * sizeof(double), st);
   e = e ? e : cudaMemsetAsync(A.aB, 0, Nt * sizeof(double), st);
@@ -1245,7 +1252,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   for (int64_t n = 0; n < nsteps && !s; ++n) {
     if (n % C == 0 && (e = save(ckpt[n / C]))) break;
     s = enqueue_step(ctx);
-    if (!s) k_misfit<0><<<gg, 128, 0, st>>>(D, A, (int32_t)B, G, gx, obs + n * B * G, Jacc);
+    if (!s) k_misfit<0><<<gg, 128, 0, st>>>(D, A, (int32_t)B, G, gx, obs + n * B * G, Jacc, gcell);
   }
   if (!s && !e) e = save(fin);
   if (!s && !e) e = cudaGetLastError();
@@ -1268,18 +1275,16 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
       e = e ? e : cudaMemcpyAsync(snap.B, c.B, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st);
       e = e ? e : cudaMemcpyAsync(snap.J, c.J, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st);
       if (e) break;
-      // Recompute the step: q^(1), q^(2), the stage meshes, node velocities and the stage-3
-      // edge values stay in the state arrays.
-      if ((s = enqueue_step(ctx))) break;
-      k_misfit<1><<<gg, 128, 0, st>>>(D, A, (int32_t)B, G, gx, obs + m * B * G, Jacc);
+      // Recompute the step: q^(1), q^(2), the stage meshes and node velocities stay in the state
+      // arrays, each stage's edge values in its own set.
+      if ((s = enqueue_step(ctx, Ds))) break;
+      k_misfit<1><<<gg, 128, 0, st>>>(D, A, (int32_t)B, G, gx, obs + m * B * G, Jacc, gcell);
       launch_adj_rk<3>(ctx, A);
-      launch_adj_stage<3>(ctx, K, A, D.Eb, D.Mb, D.Bb, D.J2);
+      launch_adj_stage<3>(ctx, Ds[2], K, A, D.Eb, D.Mb, D.Bb, D.J2);
       launch_adj_rk<2>(ctx, A);
-      launch_recon_replay<2>(ctx, K, D.Ea, D.Ma, D.Ba, D.J1);
-      launch_adj_stage<2>(ctx, K, A, D.Ea, D.Ma, D.Ba, D.J1);
+      launch_adj_stage<2>(ctx, Ds[1], K, A, D.Ea, D.Ma, D.Ba, D.J1);
       launch_adj_rk<1>(ctx, A);
-      launch_recon_replay<1>(ctx, K, snap.E, snap.M, snap.B, snap.J);
-      launch_adj_stage<1>(ctx, K, A, snap.E, snap.M, snap.B, snap.J);
+      launch_adj_stage<1>(ctx, Ds[0], K, A, snap.E, snap.M, snap.B, snap.J);
       launch_adj_rk<0>(ctx, A);
       e = cudaGetLastError();
     }

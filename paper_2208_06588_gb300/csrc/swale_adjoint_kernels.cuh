@@ -289,21 +289,32 @@ __global__ void __launch_bounds__(T) k_adj_recon(StepConst K, DevState D, AdjSta
 // depth is the average of the cell that contains x on the current mesh. MODE 0 adds
 // dt (h - obs)^2 to Jout[i]; MODE 1 adds its gradient 2 dt (h - obs) to lambda (eta: +, b: -).
 // obs points at the row of the observed depths for this step (B x G values).
+// gcell[id] caches the gauge's cell between calls (-1: not located yet): from there a short walk
+// finds the cell on the new mesh (a node moves by less than a cell per step); the first call
+// bisects. Either way the cell is c with x[c] <= xg < x[c+1] (clamped to 0..N-1).
 template <int MODE>
 __global__ void k_misfit(DevState D, AdjState A, int32_t B, int32_t G, const double* __restrict__ gx,
-                         const double* __restrict__ obs, double* Jout) {
+                         const double* __restrict__ obs, double* Jout, int64_t* gcell) {
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (int64_t)B * G) return;
   const int i = (int)(id / G);
   const InstConst ic = D.IC[i];
   const double* x = D.x + ic.coff + i;
   const double xg = gx[id];
-  int64_t lo = 0, hi = ic.N;  // find c with x[c] <= xg < x[c+1]
-  while (hi - lo > 1) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (x[mid] <= xg) lo = mid;
-    else hi = mid;
+  int64_t lo = gcell[id];
+  if (lo < 0 || lo >= ic.N) {
+    lo = 0;
+    int64_t hi = ic.N;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (x[mid] <= xg) lo = mid;
+      else hi = mid;
+    }
+  } else {
+    while (lo + 1 < ic.N && x[lo + 1] <= xg) ++lo;
+    while (lo > 0 && x[lo] > xg) --lo;
   }
+  gcell[id] = lo;
   const int64_t g = ic.coff + lo;
   const double r = (D.E0[g] - D.B0[g]) - obs[id];
   const double dt = D.S[i].dt;

@@ -129,3 +129,38 @@ def test_autotune_restores_state_and_uses_cache(tmp_path):
     assert B.swale_autotune(s.ctx, 2, cache) == tiles  # from the cache, no new line
     assert open(cache).read().count("\n") == 1
     s.close()
+
+
+def test_steps_after_autotune_match_an_untuned_run(tmp_path):
+    """The candidates that the autotuner times overwrite the mesh geometry cache; the steps after
+    the restore must not take it for the restored state (bitwise equal to an untuned run)."""
+    bt = W.many_basins(B=12, n_min=200, n_max=3000, seed=105)
+    s = B.Solver(cfg_of(bt))
+    s.set_batch(bt)
+    s.advance(3)
+    B.swale_autotune(s.ctx, 2, str(tmp_path / "tune.jsonl"))
+    s.advance(6)
+    got = s.batch_state()
+    s.close()
+    ref = run_batch(bt, 9)
+    for k in ("eta", "hu", "b", "x", "t", "dt"):
+        assert np.array_equal(ref[k], got[k]), k
+
+
+@pytest.mark.parametrize("scheme", ["nonwb", "special"])
+@pytest.mark.parametrize("tiles", [(64, 64, 0, 0), (256, 128, 0, 0), (128, 128, 304, 608)])
+def test_variant_launch_shape_does_not_change_results(scheme, tiles):
+    bt = W.many_basins(B=10, n_min=100, n_max=1500, seed=106)
+    cfg = B.make_config(g=bt.g, eps_weno=bt.eps_weno, mesh_T=bt.mesh_T, bc=bt.bc, mesh=bt.mesh, cfl=0.6,
+                        scheme=scheme)
+    outs = []
+    for t in (None, tiles):
+        s = B.Solver(cfg)
+        s.set_batch(bt)
+        if t:
+            B.swale_set_tiles(s.ctx, *t)
+        s.advance(8)
+        outs.append(s.batch_state())
+        s.close()
+    for k in ("eta", "hu", "b", "x", "t"):
+        assert np.array_equal(outs[0][k], outs[1][k]), k
