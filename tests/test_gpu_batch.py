@@ -133,7 +133,9 @@ def test_autotune_restores_state_and_uses_cache(tmp_path):
 
 def test_steps_after_autotune_match_an_untuned_run(tmp_path):
     """The candidates that the autotuner times overwrite the mesh geometry cache; the steps after
-    the restore must not take it for the restored state (bitwise equal to an untuned run)."""
+    the restore must not take it for the restored state. The first step after the restore
+    recomputes the geometry from J^{n+1} where the untuned run reuses the one from J^(1) (equal
+    in exact arithmetic), so the two agree to rounding."""
     bt = W.many_basins(B=12, n_min=200, n_max=3000, seed=105)
     s = B.Solver(cfg_of(bt))
     s.set_batch(bt)
@@ -144,12 +146,15 @@ def test_steps_after_autotune_match_an_untuned_run(tmp_path):
     s.close()
     ref = run_batch(bt, 9)
     for k in ("eta", "hu", "b", "x", "t", "dt"):
-        assert np.array_equal(ref[k], got[k]), k
+        assert np.abs(ref[k] - got[k]).max() <= 1e-13 * max(np.abs(ref[k]).max(), 1.0), k
 
 
 @pytest.mark.parametrize("scheme", ["nonwb", "special"])
 @pytest.mark.parametrize("tiles", [(64, 64, 0, 0), (256, 128, 0, 0), (128, 128, 304, 608)])
 def test_variant_launch_shape_does_not_change_results(scheme, tiles):
+    """Agreement to rounding: the compiler may fuse the geometry arithmetic into the variant's
+    reconstruction differently in each tile-size instantiation of the kernel (last-bit
+    differences once stage 1 reads the geometry stored by stage 2)."""
     bt = W.many_basins(B=10, n_min=100, n_max=1500, seed=106)
     cfg = B.make_config(g=bt.g, eps_weno=bt.eps_weno, mesh_T=bt.mesh_T, bc=bt.bc, mesh=bt.mesh, cfl=0.6,
                         scheme=scheme)
@@ -163,4 +168,4 @@ def test_variant_launch_shape_does_not_change_results(scheme, tiles):
         outs.append(s.batch_state())
         s.close()
     for k in ("eta", "hu", "b", "x", "t"):
-        assert np.array_equal(outs[0][k], outs[1][k]), k
+        assert np.abs(outs[0][k] - outs[1][k]).max() <= 1e-13 * max(np.abs(outs[0][k]).max(), 1.0), k
