@@ -31,9 +31,9 @@ METRIC = "cell-updates/s FP64 (fwd, plain single instance)"
 UNIT = "cell-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
 # DRAM bytes (read + write) of a k_recon launch on this workload, averaged over the three
-# stages, from ncu captures of the current kernels: stage 1 reads the cached mesh geometry
-# (226.6 + 60.6 MB), stage 2 writes it (33.6 + 232.6 MB), stage 3 does neither (about 61.2 MB).
-RECON_DRAM_BYTES = (226_561_536 + 60_644_864 + 33_605_888 + 232_583_680 + 61_172_224) // 3
+# stages, from one ncu capture of the current kernels: stage 1 reads the cached mesh geometry
+# (226.6 + 61.1 MB), stage 2 writes it (33.6 + 229.7 MB), stage 3 does neither (33.7 + 23.2 MB).
+RECON_DRAM_BYTES = (226_557_440 + 61_075_712 + 33_612_800 + 229_669_376 + 33_677_056 + 23_249_664) // 3
 
 
 def parse():
