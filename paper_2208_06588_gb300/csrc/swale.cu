@@ -322,15 +322,15 @@ template <int STAGE>
 void launch_recon(const StepConst& K, const DevState& D, int T, unsigned grid, cudaStream_t s, const double* E,
                   const double* M, const double* B, const double* J) {
   if (K.scheme == SWALE_SCHEME_NONWB) {
-    if (T == 64) k_recon<STAGE, 64, 0, 1><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
-    else if (T == 256) k_recon<STAGE, 256, 0, 1><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
-    else k_recon<STAGE, 128, 0, 1><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
+    if (T == 64) k_recon<STAGE, 64, 1><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
+    else if (T == 256) k_recon<STAGE, 256, 1><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
+    else k_recon<STAGE, 128, 1><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
     return;
   }
   if (K.scheme == SWALE_SCHEME_SPECIAL) {
-    if (T == 64) k_recon<STAGE, 64, 0, 2><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
-    else if (T == 256) k_recon<STAGE, 256, 0, 2><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
-    else k_recon<STAGE, 128, 0, 2><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
+    if (T == 64) k_recon<STAGE, 64, 2><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
+    else if (T == 256) k_recon<STAGE, 256, 2><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
+    else k_recon<STAGE, 128, 2><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
     return;
   }
   if (T == 64) k_recon<STAGE, 64><<<grid, 64, 0, s>>>(K, D, E, M, B, J);

@@ -364,12 +364,10 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevSta
 // reciprocals for the update kernel of the same stage, reduces the wave speed, and in stage 1
 // the instance's last tile computes its dt (and the secant factor of the prescribed motion).
 // ------------------------------------------------------------------------------------
-template <int STAGE, int T, int MODE = 0, int SCHEME = 0>
+template <int STAGE, int T, int SCHEME = 0>
 __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
                                              const double* __restrict__ Mg, const double* __restrict__ Bg,
                                              const double* __restrict__ Jg) {
-  // MODE 0: a stage of a step. MODE 1 (replay, used by the adjoint): edge values and shared
-  // reciprocals only, no reductions, classes or time step.
   __shared__ double sJ[T + 4], sV[3][T + 4];    // cells c0-2 .. c0+T+1
   __shared__ double sIP[T + 3], sD2[3][T + 3];  // pairs starting at those cells
   __shared__ double sIT[T + 2], sD3[3][T + 2];  // triples centred at cells c0-1 .. c0+T
@@ -379,7 +377,7 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
   for (int t = blockIdx.x; t < D.nr; t += gridDim.x) {
     const Tile tl = D.rtiles ? D.rtiles[t] : Tile{0, t * T - 1};
     DevScalars* S = D.S + tl.inst;
-    if (MODE == 0 && S->done) continue;
+    if (S->done) continue;
     const InstConst ic = D.IC[tl.inst];
     const int64_t N = ic.N, c0 = tl.c0;
     const double* E = Eg + ic.coff;
@@ -422,8 +420,8 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
     const int64_t c = c0 + tid;
     const unsigned long long geo_now =
         ((unsigned long long)K.geo_epoch << 32) | (unsigned long long)(S->step_idx & 0xffffffffLL);
-    const bool use_geo = STAGE == 1 && MODE == 0 && D.geo != nullptr && S->geo_tag == geo_now;
-    if (STAGE == 2 && MODE == 0 && D.geo != nullptr && c0 == -1 && tid == 0)
+    const bool use_geo = STAGE == 1 && D.geo != nullptr && S->geo_tag == geo_now;
+    if (STAGE == 2 && D.geo != nullptr && c0 == -1 && tid == 0)
       S->geo_tag = ((unsigned long long)K.geo_epoch << 32) | (unsigned long long)((S->step_idx + 1) & 0xffffffffLL);
     double wave = 0.0, ehL = 0.0, euL = 0.0, ehR = 0.0, euR = 0.0;
     bool useL = false, useR = false;
@@ -455,7 +453,7 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
       } else {
         swale::cell_geom(h, K.sc.beta_dx_global ? dxmax : h[2], G, st);
       }
-      if (STAGE == 2 && MODE == 0 && D.geo) {
+      if (STAGE == 2 && D.geo) {
 #pragma unroll
         for (int k = 0; k < SWALE_GEOM_VALUES; ++k) D.geo[k * D.geo_stride + idx] = gv[k];
       }
@@ -479,7 +477,7 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
       }
       D.ipair[idx] = sIP[tid + 2];  // pair (c, c+1)
       D.itri[idx] = sIT[tid + 1];   // triple centred at c
-      if (STAGE == 1 && MODE == 0) D.flags[idx] = flag;
+      if (STAGE == 1) D.flags[idx] = flag;
       // Edges that touch interfaces 0..N only.
       useL = (c != -1);
       useR = (c != N);
@@ -488,7 +486,6 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
       ehR = o.hR;
       euR = o.uR;
     }
-    if (MODE == 1) continue;
     wave = block_wave<T>(K.sc.g, useL, useR, ehL, euL, ehR, euR);
     block_or_status(&S->status, st);
     block_max_to(&S->A[STAGE - 1], wave);
