@@ -213,6 +213,18 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
                                const double* M, const double* B, const double* J, const double* w, double alpha,
                                double* RE, double* RM, double* RB, double* A_out, uint8_t* flags);
 
+/* Checkpoint / resume of a forward run. swale_save writes the context's state (configuration,
+ * offsets, per-instance CFL numbers, the cell averages of eta, hu and b, the widths of the GCL
+ * recursion, nodes, motion profile, per-instance scalars such as t and the step count, and
+ * the L2-projection bottom if set) to a versioned binary file; swale_load reads such a file
+ * into a context created with the same configuration (bitwise equal swale_config) and
+ * replaces its problem. A resumed run recomputes the first step's mesh geometry from the
+ * stored widths, so it agrees with the uninterrupted run to rounding. Host byte order.
+ * Errors: SWALE_EINVAL (no problem, file not readable / writable, wrong format, version or
+ * configuration), SWALE_ENOMEM, SWALE_ECUDA. */
+swale_status swale_save(swale_ctx* ctx, const char* path);
+swale_status swale_load(swale_ctx* ctx, const char* path);
+
 /* Bottom by L2 projection (Eq. baverage, Sec. 3.3) instead of its evolution by Eq. bottomrk:
  * b(x) is the piecewise polynomial with npieces pieces on breaks[npieces + 1] (increasing,
  * covering every instance's domain), piece p being sum_{k<=degree} coef[p (degree+1) + k]

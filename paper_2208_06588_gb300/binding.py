@@ -76,6 +76,8 @@ def lib():
         L.swale_adjoint.argtypes = [vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
         L.swale_adjoint_bytes.argtypes = [i64, i64, i64, i64, i32, P(ctypes.c_uint64)]
         L.swale_set_bottom_function.argtypes = [vp, i32, i32, vp, vp]
+        L.swale_save.argtypes = [vp, ctypes.c_char_p]
+        L.swale_load.argtypes = [vp, ctypes.c_char_p]
         L.swale_rhs_noalloc.argtypes = [P(SwaleConfig), vp, i64, vp, vp, vp, vp, vp, d, vp, vp, vp, P(d), vp]
         L.swale_set_timing.argtypes = [vp, i32]
         L.swale_get_timing.argtypes = [vp, vp, vp]
@@ -83,7 +85,7 @@ def lib():
                      "swale_get_flags", "swale_get_status", "swale_rhs", "swale_enqueue", "swale_set_timing",
                      "swale_get_timing", "swale_rhs_noalloc", "swale_batch_set_problem", "swale_batch_get_state",
                      "swale_set_tiles", "swale_get_tiles", "swale_autotune", "swale_alpha_log",
-                     "swale_get_alpha_log", "swale_adjoint", "swale_adjoint_bytes", "swale_set_bottom_function"):
+                     "swale_get_alpha_log", "swale_adjoint", "swale_adjoint_bytes", "swale_set_bottom_function", "swale_save", "swale_load"):
             getattr(L, name).restype = ctypes.c_int
         L.swale_last_error.argtypes = [vp]
         L.swale_last_error.restype = ctypes.c_char_p
@@ -168,6 +170,14 @@ def swale_set_bottom_function(ctx, breaks=None, coef=None):
     br = np.ascontiguousarray(breaks, dtype=np.float64)
     cf = np.ascontiguousarray(np.atleast_2d(coef), dtype=np.float64)
     _check(ctx, lib().swale_set_bottom_function(ctx, cf.shape[0], cf.shape[1] - 1, ptr(br), ptr(cf)))
+
+
+def swale_save(ctx, path):
+    _check(ctx, lib().swale_save(ctx, os.fsencode(path)))
+
+
+def swale_load(ctx, path):
+    _check(ctx, lib().swale_load(ctx, os.fsencode(path)))
 
 
 def swale_alpha_log(ctx, mode, nsteps=0, log=None):

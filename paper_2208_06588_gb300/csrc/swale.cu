@@ -416,7 +416,8 @@ swale_status enqueue_steps(swale_ctx* ctx, int64_t n) {
 // Common set-up of B instances from host vectors.
 swale_status set_instances(swale_ctx* ctx, const std::vector<int64_t>& off, const std::vector<double>& x,
                            const std::vector<double>& q, const std::vector<double>& m, const std::vector<double>& bb,
-                           const std::vector<double>& P, const std::vector<double>& cfl, bool q0_is_eta) {
+                           const std::vector<double>& P, const std::vector<double>& cfl, bool q0_is_eta,
+                           bool check_depth = true) {
   const int64_t B = (int64_t)off.size() - 1;
   const int64_t Ntot = off[B];
   std::vector<double> E(Ntot), J(Ntot);
@@ -440,7 +441,7 @@ swale_status set_instances(swale_ctx* ctx, const std::vector<int64_t>& off, cons
       if (!std::isfinite(q[g]) || !std::isfinite(m[g]) || !std::isfinite(bb[g]))
         return fail(ctx, SWALE_EINVAL, "non-finite cell average");
       E[g] = q0_is_eta ? q[g] : q[g] + bb[g];
-      if (E[g] - bb[g] < 0.0) return fail(ctx, SWALE_EINVAL, "negative depth in the initial data");
+      if (check_depth && E[g] - bb[g] < 0.0) return fail(ctx, SWALE_EINVAL, "negative depth in the initial data");
     }
     if (!(cfl[i] > 0.0) && !(ctx->cfg.dt_fixed > 0.0)) return fail(ctx, SWALE_EINVAL, "cfl must be > 0");
     ic[i].N = N;
@@ -728,6 +729,108 @@ swale_status swale_get_status(swale_ctx* ctx, uint32_t* status_bits, int64_t* st
   if (status_bits) *status_bits = bits;
   if (steps) *steps = S[0].steps;
   if (last_dt) *last_dt = S[0].dt;
+  return SWALE_OK;
+}
+
+namespace {
+constexpr char kSaveMagic[8] = {'S', 'W', 'A', 'L', 'E', 'S', 'T', '1'};
+constexpr uint32_t kSaveVersion = 1;
+}  // namespace
+
+swale_status swale_save(swale_ctx* ctx, const char* path) {
+  if (!ctx || !path) return SWALE_EINVAL;
+  if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
+  const int64_t B = ctx->B, Nt = ctx->Ntot, NN = Nt + B;
+  const DevState& D = ctx->D;
+  std::vector<double> E(Nt), M(Nt), Bb(Nt), J(Nt), x(NN), P(NN), cfl(B), br, cf;
+  std::vector<DevScalars> S(B);
+  std::vector<InstConst> ic(B);
+  cudaStream_t st = ctx->stream;
+  SW_CUDA(ctx, cudaMemcpyAsync(E.data(), D.E0, Nt * 8, cudaMemcpyDeviceToHost, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(M.data(), D.M0, Nt * 8, cudaMemcpyDeviceToHost, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(Bb.data(), D.B0, Nt * 8, cudaMemcpyDeviceToHost, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(J.data(), D.J0, Nt * 8, cudaMemcpyDeviceToHost, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(x.data(), D.x, NN * 8, cudaMemcpyDeviceToHost, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(P.data(), D.P, NN * 8, cudaMemcpyDeviceToHost, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(S.data(), D.S, B * sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+  SW_CUDA(ctx, cudaMemcpyAsync(ic.data(), D.IC, B * sizeof(InstConst), cudaMemcpyDeviceToHost, st));
+  if (ctx->bot_pieces > 0) {
+    br.resize(ctx->bot_pieces + 1);
+    cf.resize((size_t)ctx->bot_pieces * (ctx->bot_deg + 1));
+    SW_CUDA(ctx, cudaMemcpyAsync(br.data(), ctx->bot_breaks, br.size() * 8, cudaMemcpyDeviceToHost, st));
+    SW_CUDA(ctx, cudaMemcpyAsync(cf.data(), ctx->bot_coef, cf.size() * 8, cudaMemcpyDeviceToHost, st));
+  }
+  SW_CUDA(ctx, cudaStreamSynchronize(st));
+  for (int64_t i = 0; i < B; ++i) cfl[i] = ic[i].cfl;
+  std::ofstream f(path, std::ios::binary | std::ios::trunc);
+  if (!f) return fail(ctx, SWALE_EINVAL, std::string("cannot open ") + path);
+  auto put = [&](const void* p, size_t n) { f.write(reinterpret_cast<const char*>(p), (std::streamsize)n); };
+  const uint32_t ver = kSaveVersion, ssz = (uint32_t)sizeof(DevScalars);
+  put(kSaveMagic, 8);
+  put(&ver, 4);
+  put(&ssz, 4);
+  put(&ctx->cfg, sizeof(swale_config));
+  put(&B, 8);
+  put(&Nt, 8);
+  put(ctx->off.data(), (B + 1) * 8);
+  put(cfl.data(), B * 8);
+  for (const std::vector<double>* v : {&E, &M, &Bb, &J, &x, &P}) put(v->data(), v->size() * 8);
+  put(S.data(), B * sizeof(DevScalars));
+  const int32_t np = ctx->bot_pieces, deg = ctx->bot_deg;
+  put(&np, 4);
+  put(&deg, 4);
+  if (np > 0) {
+    put(br.data(), br.size() * 8);
+    put(cf.data(), cf.size() * 8);
+  }
+  f.close();
+  if (!f) return fail(ctx, SWALE_EINVAL, std::string("write failed: ") + path);
+  return SWALE_OK;
+}
+
+swale_status swale_load(swale_ctx* ctx, const char* path) {
+  if (!ctx || !path) return SWALE_EINVAL;
+  std::ifstream f(path, std::ios::binary);
+  if (!f) return fail(ctx, SWALE_EINVAL, std::string("cannot open ") + path);
+  auto get = [&](void* p, size_t n) { return (bool)f.read(reinterpret_cast<char*>(p), (std::streamsize)n); };
+  char magic[8];
+  uint32_t ver = 0, ssz = 0;
+  swale_config cfg;
+  int64_t B = 0, Nt = 0;
+  if (!get(magic, 8) || std::memcmp(magic, kSaveMagic, 8) != 0) return fail(ctx, SWALE_EINVAL, "not a state file");
+  if (!get(&ver, 4) || ver != kSaveVersion || !get(&ssz, 4) || ssz != sizeof(DevScalars))
+    return fail(ctx, SWALE_EINVAL, "state file of another version");
+  if (!get(&cfg, sizeof(cfg)) || std::memcmp(&cfg, &ctx->cfg, sizeof(cfg)) != 0)
+    return fail(ctx, SWALE_EINVAL, "the state file was written under another configuration");
+  if (!get(&B, 8) || !get(&Nt, 8) || B < 1 || Nt < 5 * B || Nt > 0x7fffffffLL || B > Nt)
+    return fail(ctx, SWALE_EINVAL, "bad sizes in the state file");
+  const int64_t NN = Nt + B;
+  std::vector<int64_t> off(B + 1);
+  std::vector<double> cfl(B), E(Nt), M(Nt), Bb(Nt), J(Nt), x(NN), P(NN);
+  std::vector<DevScalars> S(B);
+  bool ok = get(off.data(), (B + 1) * 8) && get(cfl.data(), B * 8);
+  for (std::vector<double>* v : {&E, &M, &Bb, &J, &x, &P}) ok = ok && get(v->data(), v->size() * 8);
+  ok = ok && get(S.data(), B * sizeof(DevScalars));
+  int32_t np = 0, deg = 0;
+  ok = ok && get(&np, 4) && get(&deg, 4);
+  std::vector<double> br, cf;
+  if (ok && np > 0) {
+    if (np > (1 << 20) || deg < 0 || deg > 8) return fail(ctx, SWALE_EINVAL, "bad bottom function in the state file");
+    br.resize(np + 1);
+    cf.resize((size_t)np * (deg + 1));
+    ok = get(br.data(), br.size() * 8) && get(cf.data(), cf.size() * 8);
+  }
+  if (!ok) return fail(ctx, SWALE_EINVAL, "truncated state file");
+  if (off[0] != 0 || off[B] != Nt) return fail(ctx, SWALE_EINVAL, "bad offsets in the state file");
+  // (a saved run may hold rounding-level negative depths in dry cells: not re-checked)
+  if (swale_status s = set_instances(ctx, off, x, E, M, Bb, P, cfl, true, false)) return s;
+  // The state as it was: the widths of the GCL recursion and the per-instance scalars (time,
+  // step count, extrema); no mesh geometry is cached for it.
+  for (DevScalars& v : S) v.geo_tag = 0;
+  SW_CUDA(ctx, cudaMemcpyAsync(ctx->D.J0, J.data(), Nt * 8, cudaMemcpyHostToDevice, ctx->stream));
+  SW_CUDA(ctx, cudaMemcpyAsync(ctx->D.S, S.data(), B * sizeof(DevScalars), cudaMemcpyHostToDevice, ctx->stream));
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (np > 0) return swale_set_bottom_function(ctx, np, deg, br.data(), cf.data());
   return SWALE_OK;
 }
 

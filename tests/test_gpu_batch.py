@@ -169,3 +169,57 @@ def test_variant_launch_shape_does_not_change_results(scheme, tiles):
         s.close()
     for k in ("eta", "hu", "b", "x", "t"):
         assert np.abs(outs[0][k] - outs[1][k]).max() <= 1e-13 * max(np.abs(outs[0][k]).max(), 1.0), k
+
+
+def test_save_and_resume(tmp_path):
+    """swale_save / swale_load: a run resumed from a file continues like the uninterrupted run
+    (to rounding: the first resumed step recomputes the mesh geometry), with the same time and
+    step count; a context of another configuration refuses the file."""
+    bt = W.many_basins(B=6, n_min=200, n_max=1500, seed=107)
+    path = str(tmp_path / "state.bin")
+    s = B.Solver(cfg_of(bt))
+    s.set_batch(bt)
+    s.advance(7)
+    B.swale_save(s.ctx, path)
+    s.advance(5)
+    ref = s.batch_state()
+    ref_status = s.status()
+    s.close()
+    r = B.Solver(cfg_of(bt))
+    B.swale_load(r.ctx, path)
+    r.N, r.B = int(bt.off[-1]), bt.B
+    r.advance(5)
+    got = r.batch_state()
+    assert r.status()[1] == ref_status[1] == 12
+    r.close()
+    np.testing.assert_array_equal(got["t"], ref["t"])
+    for k in ("eta", "hu", "b", "x"):
+        assert np.abs(got[k] - ref[k]).max() <= 1e-13 * max(np.abs(ref[k]).max(), 1.0), k
+    other = B.Solver(B.make_config(g=bt.g, eps_weno=bt.eps_weno, mesh_T=bt.mesh_T, bc=bt.bc, mesh=bt.mesh, cfl=0.5))
+    with pytest.raises(B.SwaleError):
+        B.swale_load(other.ctx, path)
+    other.close()
+
+
+def test_save_and_resume_with_projected_bottom(tmp_path):
+    pr = W.bump_dam_break(N=512)
+    cfg = B.make_config(cfl=pr.cfl, mesh_T=pr.mesh_T, bc=pr.bc, mesh=pr.mesh)
+    path = str(tmp_path / "bump.bin")
+    s = B.Solver(cfg)
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    B.swale_set_bottom_function(s.ctx, *pr.meta["bottom"])
+    s.advance(10)
+    B.swale_save(s.ctx, path)
+    s.advance(10)
+    ref = s.state()
+    s.close()
+    r = B.Solver(cfg)
+    B.swale_load(r.ctx, path)
+    r.N = pr.N
+    r.advance(10)
+    got = r.state()
+    r.close()
+    assert got["t"] == ref["t"]
+    np.testing.assert_array_equal(got["b"], ref["b"])  # projection of the same bottom on the same nodes
+    for k in ("eta", "hu"):
+        assert np.abs(got[k] - ref[k]).max() <= 1e-12 * np.abs(ref[k]).max(), k
