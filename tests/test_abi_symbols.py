@@ -62,3 +62,47 @@ def test_adjoint_bytes_formula():
     assert B.swale_adjoint_bytes(Bn, Nt, K, K, G) > B.swale_adjoint_bytes(Bn, Nt, K, 64, G)
     with pytest.raises(B.SwaleError):
         B.swale_adjoint_bytes(0, Nt, K, C, G)
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include "swale.h"
+
+/* A plain C client of the boundary: one instance, a few steps, the state back. */
+int run(const double* x, const double* eta, const double* hu, const double* b, int64_t n, double* out_eta) {
+  swale_config cfg = {9.812, 0.6, 1e-6, 1e-11, 1e-6, 1.0, 8.0, 0.0, 0.0,
+                      SWALE_BC_PERIODIC, SWALE_MESH_STATIC, 24, 1, SWALE_SCHEME_HYDROSTATIC};
+  swale_ctx* ctx = NULL;
+  swale_status s = swale_create(&ctx, &cfg, NULL);
+  if (s != SWALE_OK) return (int)s;
+  s = swale_set_problem(ctx, n, x, eta, hu, b, NULL, 1);
+  int64_t done = 0;
+  if (s == SWALE_OK) s = swale_advance(ctx, 10, &done);
+  if (s == SWALE_OK) s = swale_get_state(ctx, NULL, NULL, NULL, out_eta, NULL, NULL);
+  if (s != SWALE_OK) fprintf(stderr, "%s\n", swale_last_error(ctx));
+  swale_destroy(ctx);
+  return (int)s;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """include/swale.h compiles as C11 (no C++ in the boundary) and a C client links against the
+    library (nothing is run: no GPU here)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_2208_06588_gb300 import binding, build
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    inc = os.path.join(ROOT, "include")
+    obj = tmp_path / "client.o"
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-pedantic", "-fPIC", "-I", inc, "-c", str(src), "-o",
+                    str(obj)], check=True)
+    libdir = os.path.dirname(binding.LIB_PATH)
+    subprocess.run([gcc, "-shared", "-o", str(tmp_path / "libclient.so"), str(obj), "-L", libdir, "-lswale",
+                    "-Wl,-rpath," + libdir], check=True)
