@@ -34,6 +34,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max
 # stages, from one ncu capture of the current kernels: stage 1 reads the cached mesh geometry
 # (226.6 + 61.1 MB), stage 2 writes it (33.6 + 229.7 MB), stage 3 does neither (33.7 + 23.2 MB).
 RECON_DRAM_BYTES = (226_557_440 + 61_075_712 + 33_612_800 + 229_669_376 + 33_677_056 + 23_249_664) // 3
+# Fraction of cycles the FP64 pipe was busy during the same k_recon launches (ncu
+# sm__pipe_fp64_cycles_active, stages 1 and 2): the kernel is bound by FP64 instruction issue.
+RECON_FP64_PIPE_ACTIVE = (0.863 + 0.871) / 2
 
 
 def parse():
@@ -594,6 +597,7 @@ def main():
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum of k_recon, "
                             "N = 2^20, mean of the three stages)",
             "flops_per_cell": flops_cell, "cells_per_launch": N,
+            "ncu_fp64_pipe_active": RECON_FP64_PIPE_ACTIVE if dom == "reconstruction" else None,
             "avg_launch_ms": ms_dom / n_dom,
             "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA chain: 1.195 TFLOP/s)",
             "kernel_ms_share": {k: round(v[0] / max(sum(x[0] for x in fam.values()), 1e-30), 4)
