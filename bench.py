@@ -157,6 +157,24 @@ def _oracle_instance(job):
     return oracle.run(P, st, prof, nsteps=steps)["steps"] * E.size
 
 
+def cpu_oracle_small_rates():
+    """The CPU oracle, one thread, 10 steps of the small periodic instance (N = 200) and of the
+    65536-cell Gaussian basin of the adjoint case."""
+    import oracle
+    from paper_2208_06588_gb300 import workloads as W
+    out = {}
+    for name, pr in (("smooth_periodic_200", W.smooth_periodic(200)), ("gaussian_basin_65536", W.gaussian_basin())):
+        P = oracle.Params(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, bc=pr.bc, mesh=pr.mesh,
+                          dt_fixed=pr.dt_fixed)
+        st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+        t0 = time.perf_counter()
+        r = oracle.run(P, st, pr.profile, nsteps=10)
+        el = time.perf_counter() - t0
+        out[name] = {"value": pr.N * r["steps"] / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                     "sample": f"{r['steps']} steps, {el:.2f} s"}
+    return out
+
+
 def cpu_oracle_batched_rate(n_inst=1024, steps=5):
     """The CPU oracle as it stands on the batched workload's first n_inst instances, one
     instance per task over a spawned process pool with one worker per available core."""
@@ -610,6 +628,7 @@ def main():
                "sample": f"3 SSP-RK3 steps of the full 2^20-cell workload ({secs:.1f} s, one thread)"}
         if batched is not None:
             batched["cpu_baseline"] = cpu_oracle_batched_rate()
+        cpu["other_workloads"] = cpu_oracle_small_rates()
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
