@@ -2,6 +2,7 @@
 // well-balanced ALE-WENO hybrid scheme (Zhang, Xia & Xu, arXiv 2208.06588). The kernels are in
 // swale_kernels.cuh, the per-cell arithmetic in swale_cell.cuh.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -53,6 +54,15 @@ struct swale_ctx {
 };
 
 namespace {
+
+// NVTX range over a host call (a no-op unless a profiling tool is attached): the step loops,
+// graph replays, the adjoint's phases and the autotuner show up by name on a timeline.
+struct NvtxRange {
+  explicit NvtxRange(const char* m) { nvtxRangePushA(m); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 swale_status fail(swale_ctx* ctx, swale_status s, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -404,6 +414,7 @@ swale_status enqueue_steps(swale_ctx* ctx, int64_t n) {
       ctx->graph_steps = kGraphSteps;
     }
     while (n >= ctx->graph_steps) {
+      NvtxRange r("swale graph replay (8 steps)");
       SW_CUDA(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
       n -= ctx->graph_steps;
     }
@@ -594,6 +605,7 @@ swale_status swale_batch_set_problem(swale_ctx* ctx, int64_t B, const int64_t* o
 }
 
 swale_status swale_step(swale_ctx* ctx, double* dt_out) {
+  NvtxRange nvtx_range("swale_step");
   if (!ctx) return SWALE_EINVAL;
   if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
   if (swale_status s = enqueue_step(ctx)) return s;
@@ -605,6 +617,7 @@ swale_status swale_step(swale_ctx* ctx, double* dt_out) {
 }
 
 swale_status swale_advance(swale_ctx* ctx, int64_t max_steps, int64_t* steps_done) {
+  NvtxRange nvtx_range("swale_advance");
   if (!ctx) return SWALE_EINVAL;
   if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
   if (max_steps < 0) return fail(ctx, SWALE_EINVAL, "max_steps < 0");
@@ -621,6 +634,7 @@ swale_status swale_advance(swale_ctx* ctx, int64_t max_steps, int64_t* steps_don
 }
 
 swale_status swale_enqueue(swale_ctx* ctx, int64_t nsteps) {
+  NvtxRange nvtx_range("swale_enqueue");
   if (!ctx) return SWALE_EINVAL;
   if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
   if (nsteps < 0) return fail(ctx, SWALE_EINVAL, "nsteps < 0");
@@ -899,6 +913,7 @@ swale_status swale_get_tiles(swale_ctx* ctx, int32_t* tiles) {
 }
 
 swale_status swale_autotune(swale_ctx* ctx, int32_t steps, const char* cache_path, int32_t* tiles_out) {
+  NvtxRange nvtx_range("swale_autotune");
   if (!ctx) return SWALE_EINVAL;
   if (ctx->B == 0) return fail(ctx, SWALE_EINVAL, "no problem set");
   if (steps < 1) return fail(ctx, SWALE_EINVAL, "steps must be >= 1");
@@ -1351,6 +1366,8 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     ctx->timing = old_timing;
   };
   const unsigned gg = (unsigned)((B * G + 127) / 128);
+  NvtxRange nvtx_adjoint("swale_adjoint");
+  nvtxRangePushA("adjoint forward");
   // ---- forward with checkpoints and the misfit ----
   for (int64_t n = 0; n < nsteps && !s; ++n) {
     if (n % C == 0 && (e = save(ckpt[n / C]))) break;
@@ -1361,6 +1378,8 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   if (!s && !e) e = cudaGetLastError();
   ctx->alpha_mode = 2;
   StepConst K = step_const(ctx);
+  nvtxRangePop();
+  NvtxRange nvtx_reverse("adjoint reverse");
   // ---- reverse, segment by segment ----
   for (int64_t sg = nseg - 1; sg >= 0 && !s && !e; --sg) {
     const int64_t n0 = sg * C, n1 = std::min(nsteps, n0 + C);
