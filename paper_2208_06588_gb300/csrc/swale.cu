@@ -1536,6 +1536,7 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   K.bot_pieces = K.bot_deg = 0;
   K.bot_breaks = K.bot_coef = nullptr;
   K.scheme = SWALE_SCHEME_HYDROSTATIC;
+  K.geo_epoch = 0;  // no geometry cache here (D.geo is null)
   // The scalars keep the previous call's contents: start them from zero (J^n minimum at 1 so
   // the stage-1 time-step arithmetic stays finite; its result is not used here).
   InstConst ic0;
