@@ -133,6 +133,35 @@ def op_counts(pr):
     return opcount.count_stage(pr.E, pr.hu, pr.b, pr.J, bc=pr.bc, sample=1 << 16)
 
 
+def fp64_roofline(flops_per_cell_step, cell_steps_per_s, scope):
+    """Whole-job FP64 roofline: the algorithmic FLOPs of a cell-step (opcount: the kernels' own
+    per-cell code counted on the host) times the measured cell-steps per second, against the FP64
+    peak. Every kernel of the step is FP64-pipe bound (DRAM below 12 %), so this is the slower of
+    the two rooflines."""
+    achieved = flops_per_cell_step * cell_steps_per_s / 1e12
+    return {"bound": "alu", "scope": scope, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_cell_step": flops_per_cell_step}
+
+
+def batch_step_flops(bt, n_inst=16):
+    """Forward-step FLOPs per cell of a batch, averaged (cell-weighted) over its first instances."""
+    from paper_2208_06588_gb300 import opcount
+    tot = cells = 0.0
+    for i in range(min(n_inst, bt.B)):
+        pr = bt.instance(i)
+        c = opcount.count_stage(pr.E, pr.hu, pr.b, pr.J, bc=pr.bc, sample=1 << 13)
+        tot += opcount.forward_step_flops(c) * pr.N
+        cells += pr.N
+    return tot / cells
+
+
+def adjoint_step_flops(pr):
+    from paper_2208_06588_gb300 import opcount
+    c = opcount.count_stage(pr.E, pr.hu, pr.b, pr.J, bc=pr.bc, sample=1 << 13)
+    r = opcount.count_reverse(pr.E, pr.hu, pr.b, pr.J, bc=pr.bc, sample=1 << 13)
+    return opcount.adjoint_step_flops(c, r)
+
+
 def cpu_oracle_rate(n_cells, steps):
     """The CPU oracle as it stands, single thread, on a sample of the same workload."""
     import oracle
@@ -231,6 +260,7 @@ def bench_batched(args, stream, dev, rank=0, ws=1):
            "value": ntot * args.batched_steps / (ms * 1e-3), "unit": UNIT, "steps": args.batched_steps,
            "ms_per_step": ms / args.batched_steps, "tiles": list(tiles), "status_bits": bits,
            "parallelism": f"instances sharded over {ws} ranks" if ws > 1 else "single", "scaling": "weak"}
+    out["roofline"] = fp64_roofline(batch_step_flops(bt_all), out["value"], "whole step, all kernels")
     # Same work, batched vs one context per instance (launches per instance and step).
     sub = 512
     sb = W.Batch(name="subset", off=bt.off[:sub + 1].copy(), x=bt.x[:int(bt.off[sub]) + sub],
@@ -331,7 +361,9 @@ def bench_adjoint(args, stream, dev=None, ws=1):
             "forward_only_value": N * K / (ms_fwd * 1e-3),
             "peak_device_bytes": int(state_bytes + adj_bytes), "adjoint_scratch_bytes": int(adj_bytes),
             "J": float(J[0]), "grad_norms": [float(np.linalg.norm(v)) for v in (gE, gM, gB)], "status_bits": bits,
-            "call": "swale_adjoint (host gauges, observations and gradients)"}
+            "call": "swale_adjoint (host gauges, observations and gradients)",
+            "roofline": fp64_roofline(adjoint_step_flops(pr), ws * N * K / (ms * 1e-3),
+                                      "whole gradient: 3 forward steps + reverse sweep per step")}
 
 
 def bench_batched_adjoint(args, stream, dev=None, rank=0, ws=1):
@@ -381,7 +413,9 @@ def bench_batched_adjoint(args, stream, dev=None, rank=0, ws=1):
            "parallelism": f"instances sharded over {ws} ranks" if ws > 1 else "single",
            "forward_only_value": Nt * K / (ms_fwd * 1e-3), "adjoint_over_forward": ms / ms_fwd,
            "peak_device_bytes": int(state_bytes + adj_bytes), "peak_device_bytes_2000_steps": int(state_bytes + full_bytes),
-           "status_bits": bits}
+           "status_bits": bits,
+           "roofline": fp64_roofline(adjoint_step_flops(bt.instance(0)), Nt_all * K / (ms * 1e-3),
+                                     "whole gradient: 3 forward steps + reverse sweep per step")}
     # One swale_adjoint per instance on a subset, same steps, against the batch of the subset.
     sub, Ks = 32, min(K, 64)
     sb = W.Batch(name="subset", off=bt.off[:sub + 1].copy(), x=bt.x[:int(bt.off[sub]) + sub],
@@ -606,6 +640,8 @@ def main():
     # Stage 1 takes the mesh-only geometry from the previous step's stage 2 (same mesh), so a
     # reconstruction launch does on average a third of that part less.
     recon_avg = oc["recon_flops"] - oc["geom_flops"] / 3.0
+    from paper_2208_06588_gb300 import opcount
+    opcount_step = opcount.forward_step_flops(oc)
     flops_cell = recon_avg if dom == "reconstruction" else oc["update_flops"]
     ms_dom, n_dom = fam[dom]
     achieved = flops_cell * N / (ms_dom / n_dom * 1e-3) / 1e12
@@ -635,7 +671,8 @@ def main():
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "cells": N, "parallelism": f"replicas x{ws}" if ws > 1 else "single",
                       "l2": "working set ~230 MB per stage > 126 MB L2 (no flush needed)"},
-           "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+           "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
+           "step_roofline": fp64_roofline(opcount_step, value, "whole step, all kernels"), "cpu_baseline": cpu,
            "status_bits": bits, "steps_done_device": steps_done, "last_dt": last_dt, "batched": batched,
            "adjoint": adjoint, "batched_adjoint": batched_adjoint, "variants": variants,
            "fp64_ops_per_cell_stage": oc}

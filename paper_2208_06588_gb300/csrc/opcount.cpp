@@ -1,5 +1,6 @@
 // Host-only count of the FP64 arithmetic that the stage kernels perform per cell, obtained by
-// compiling the same per-cell code (swale_cell.cuh) with an operation-counting scalar type.
+// compiling the same per-cell code (swale_cell.cuh, and the reverse sweeps of swale_adjoint.cuh)
+// with an operation-counting scalar type.
 // Additions/subtractions, multiplications, divisions and square roots are counted
 // separately (a fused multiply-add on the device is one multiplication plus one addition
 // here); comparisons, min/max and sign flips are counted apart (they do not use the FP64
@@ -31,7 +32,7 @@ inline CD swale_sqrt(CD a) { ++C.sqrt; return CD(std::sqrt(a.v)); }
 }  // namespace opc
 
 #define SWALE_REAL opc::CD
-#include "swale_cell.cuh"
+#include "swale_adjoint.cuh"
 
 namespace {
 int64_t wrap(int64_t i, int64_t N, int bc) {
@@ -157,6 +158,96 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
   out[16] = (double)cls[1];
   out[17] = (double)cls[2];
   out[18] = geom_flops;
+}
+
+// Counts of the reverse sweep of one stage over cells [c0, c1) of one stage state (the same
+// stencils as opc_count_stage), with unit adjoint seeds. out[0]: reverse reconstruction per
+// cell (recon_cell_rev, the cell's own pair and triple terms recomputed, and the scatter of the
+// divided-difference adjoints to the five stencil cells); out[1]: reverse source per cell
+// (source_geom with the cell's reciprocal width, the depth data, source_cell_rev); out[2]:
+// reverse flux per interface (interface_flux_rev). FLOPs: add + mul + div + sqrt, summed.
+void opc_count_reverse(int64_t N, const double* E, const double* M, const double* B, const double* J, int32_t bc,
+                       double g, double eps_weno, double eps_pp, double h_dry, double alpha, int64_t c0, int64_t c1,
+                       double* out) {
+  using opc::CD;
+  swale::SchemeConst P{g, eps_weno, eps_pp, h_dry, 1};
+  double dxmax = 0.0;
+  for (int64_t j = 0; j < N; ++j) dxmax = J[j] > dxmax ? J[j] : dxmax;
+  auto flops = []() { return (double)(opc::C.add + opc::C.mul + opc::C.div + opc::C.sqrt); };
+  double rrec = 0.0, rsrc = 0.0, rflux = 0.0;
+  for (int64_t c = c0; c < c1; ++c) {
+    CD Jv[7], V[3][7];
+    for (int k = 0; k < 7; ++k) {
+      const int64_t i = c - 3 + k, s = wrap(i, N, bc);
+      Jv[k] = J[s];
+      V[0][k] = E[s];
+      V[1][k] = (bc == 2 && (i < 0 || i >= N)) ? -M[s] : M[s];
+      V[2][k] = B[s];
+    }
+    swale::StencilDD DD;
+    CD ip[6], d2[3][6], it[5];
+    for (int m = 0; m < 6; ++m) {
+      ip[m] = CD(1.0 / (Jv[m].v + Jv[m + 1].v));
+      for (int v = 0; v < 3; ++v) d2[v][m] = CD((V[v][m + 1].v - V[v][m].v) * ip[m].v);
+    }
+    for (int m = 0; m < 5; ++m) it[m] = CD(1.0 / (Jv[m].v + Jv[m + 1].v + Jv[m + 2].v));
+    for (int v = 0; v < 3; ++v) {
+      for (int a = 0; a < 4; ++a) DD.D2[v][a] = d2[v][a + 1];
+      for (int a = 0; a < 3; ++a) DD.D3[v][a] = CD((d2[v][a + 2].v - d2[v][a + 1].v) * it[a + 1].v);
+    }
+    CD h5[5], v0[3][3];
+    for (int k = 0; k < 5; ++k) h5[k] = Jv[k + 1];
+    for (int v = 0; v < 3; ++v)
+      for (int a = 0; a < 3; ++a) v0[v][a] = V[v][a + 1];
+    swale::EdgeState o;
+    uint8_t flag;
+    uint32_t st = 0;
+    swale::recon_cell(P, h5, v0, DD, CD(dxmax), o, flag, st);
+    // Reverse reconstruction.
+    opc::C = opc::Counts();
+    const CD ipc = swale::pair_recip(Jv[3], Jv[4]);
+    for (int v = 0; v < 3; ++v) (void)swale::pair_dd(V[v][3], V[v][4], ipc);
+    const CD itc = swale::triple_recip(Jv[2], Jv[3], Jv[4]);
+    for (int v = 0; v < 3; ++v) (void)swale::triple_dd(d2[v][2], d2[v][3], itc);
+    const swale::EdgeAdj ob = {CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0)};
+    CD v0b[3][3];
+    swale::StencilDD DDb;
+    swale::recon_cell_rev(P, h5, v0, DD, CD(dxmax), ob, v0b, DDb);
+    for (int v = 0; v < 3; ++v) {  // the kernel's scatter through D3 = (D2' - D2) it, D2 = (v' - v) ip
+      CD cv[5], d2b[4];
+      for (int a = 0; a < 4; ++a) d2b[a] = DDb.D2[v][a];
+      for (int a = 0; a < 3; ++a) {
+        const CD x = DDb.D3[v][a] * it[a + 1];
+        d2b[a + 1] = d2b[a + 1] + x;
+        d2b[a] = d2b[a] - x;
+      }
+      for (int a = 0; a < 4; ++a) {
+        const CD x = d2b[a] * ip[a + 1];
+        cv[a + 1] = cv[a + 1] + x;
+        cv[a] = cv[a] - x;
+      }
+    }
+    rrec += flops();
+    // Reverse source.
+    opc::C = opc::Counts();
+    const CD iJc = CD(1.0) / Jv[3];
+    const swale::SourceGeom sg =
+        swale::source_geom(Jv[2], Jv[3], CD(1.0 / Jv[2].v), iJc, CD(1.0 / Jv[4].v), ip[2], ip[3], it[2]);
+    const CD hd[5] = {V[0][2].v - V[2][2].v, V[0][3] - V[2][3], V[0][4].v - V[2][4].v, o.hL, o.hR};
+    const CD bd[5] = {V[2][2], V[2][3], V[2][4], o.BL, o.BR};
+    CD hdb[5], bdb[5];
+    swale::source_cell_rev(CD(g), hd, bd, sg, CD(1.0), hdb, bdb);
+    rsrc += flops();
+    // Reverse flux.
+    opc::C = opc::Counts();
+    const swale::Flux Fb = {CD(1.0), CD(1.0), CD(1.0), CD(1.0)};
+    (void)swale::interface_flux_rev(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL, o.uR, o.uL, Fb);
+    rflux += flops();
+  }
+  const double n = (double)(c1 - c0);
+  out[0] = rrec / n;
+  out[1] = rsrc / n;
+  out[2] = rflux / n;
 }
 
 }  // extern "C"

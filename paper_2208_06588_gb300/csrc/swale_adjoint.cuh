@@ -94,7 +94,9 @@ SWALE_HD void source_dd_rev(const SourceGeom& sg, const real cb[6], real ub[5]) 
 }
 
 // Adjoint of source_cell: accumulates into hdb[5], bdb[5] the adjoints of the depth and bottom
-// data for the adjoint Sb of the source value.
+// data for the adjoint Sb of the source value. The reverse of source_cell's own steps: Newton
+// coefficients by confluent divided differences, their monomial form a (depth) and ab (bottom),
+// S = -g sum_{i, m} a_i ab_m m / (i + m); then transposed in the opposite order.
 SWALE_HD void source_cell_rev(real g, const real hd[5], const real bd[5], const SourceGeom& sg, real Sb, real hdb[5],
                               real bdb[5]) {
   real ch[6], cb[6];
@@ -118,32 +120,45 @@ SWALE_HD void source_cell_rev(real g, const real hd[5], const real bd[5], const 
     c[4] = o4a;
     c[5] = (o4b - o4a) * sg.i1mp;
   }
-  const double tq[4] = {SWALE_GL4_T0, SWALE_GL4_T1, SWALE_GL4_T2, SWALE_GL4_T3};
-  const double wq[4] = {SWALE_GL4_W0, SWALE_GL4_W1, SWALE_GL4_W1, SWALE_GL4_W0};
-  real chb[6] = {0, 0, 0, 0, 0, 0}, cbb[6] = {0, 0, 0, 0, 0, 0};
-  for (int q = 0; q < 4; ++q) {
-    const double t = tq[q], t2 = t * t, t3 = t2 * t, t4 = t3 * t;
-    const double m[6] = {0, 0, t, t2, t3 - t2, t4 - 2.0 * t3 + t2};
-    const double md[6] = {0, 0, 1.0, 2.0 * t, 3.0 * t2 - 2.0 * t, 4.0 * t3 - 6.0 * t2 + 2.0 * t};
-    const double mdd[6] = {0, 0, 0.0, 2.0, 6.0 * t - 2.0, 12.0 * t2 - 12.0 * t + 2.0};
-    real n1[6], n2[6];
-    real hv = ch[1], bdv = 0.0;
-    for (int k = 2; k <= 5; ++k) {
-      n1[k] = (m[k] + t * md[k]) + sg.rm * md[k];
-      n2[k] = (2.0 * md[k] + t * mdd[k]) + sg.rm * mdd[k];
-      hv = hv + ch[k] * n1[k];
-      bdv = bdv + cb[k] * n2[k];
-    }
-    // S = -g sum_q wq hv bdv
-    const real hvb = -g * wq[q] * bdv * Sb, bdvb = -g * wq[q] * hv * Sb;
-    chb[1] = chb[1] + hvb;
-    for (int k = 2; k <= 5; ++k) {
-      chb[k] = chb[k] + hvb * n1[k];
-      cbb[k] = cbb[k] + bdvb * n2[k];
-    }
+  const real rm = sg.rm;
+  real a[5], ab[5];
+  const real* cs[2] = {ch, cb};
+  real* ms[2] = {a, ab};
+  for (int v = 0; v < 2; ++v) {
+    const real* c = cs[v];
+    real* o = ms[v];
+    const real q = c[3] - c[4] + c[5];
+    o[0] = c[1] + c[2] * rm;
+    o[1] = 2.0 * (c[2] + rm * q);
+    o[2] = 3.0 * q + rm * (3.0 * c[4] - 6.0 * c[5]);
+    o[3] = 4.0 * (c[4] - 2.0 * c[5]) + (4.0 * rm) * c[5];
+    o[4] = 5.0 * c[5];
   }
-  source_dd_rev(sg, chb, hdb);
-  source_dd_rev(sg, cbb, bdb);
+  // S = -g sum_i a_i v_i, v_i = sum_m ab_m m / (i + m): adjoints of a_i and ab_m.
+  const real gS = -g * Sb;
+  real ob[2][5];
+  for (int i = 0; i < 5; ++i)
+    ob[0][i] = gS * (ab[1] * (1.0 / (i + 1)) + ab[2] * (2.0 / (i + 2)) + ab[3] * (3.0 / (i + 3)) +
+                     ab[4] * (4.0 / (i + 4)));
+  ob[1][0] = 0.0;
+  for (int m = 1; m < 5; ++m)
+    ob[1][m] = gS * (a[0] * (double(m) / m) + a[1] * (double(m) / (m + 1)) + a[2] * (double(m) / (m + 2)) +
+                     a[3] * (double(m) / (m + 3)) + a[4] * (double(m) / (m + 4)));
+  // Transpose of the monomial form, per variable: adjoints of the Newton coefficients.
+  real cbv[2][6];
+  for (int v = 0; v < 2; ++v) {
+    const real* o = ob[v];
+    real* c = cbv[v];
+    const real qb = 2.0 * rm * o[1] + 3.0 * o[2];
+    c[0] = 0.0;
+    c[1] = o[0];
+    c[2] = rm * o[0] + 2.0 * o[1];
+    c[3] = qb;
+    c[4] = (3.0 * rm) * o[2] + 4.0 * o[3] - qb;
+    c[5] = -(6.0 * rm) * o[2] + (4.0 * rm - 8.0) * o[3] + 5.0 * o[4] + qb;
+  }
+  source_dd_rev(sg, cbv[0], hdb);
+  source_dd_rev(sg, cbv[1], bdb);
 }
 
 // Adjoint of recon_cell: from the adjoints ob of the limited edge state of cell j, the adjoints

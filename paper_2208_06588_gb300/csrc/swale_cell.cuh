@@ -16,9 +16,9 @@
 //    midpoint; the classes come from comparing tau with (beta^A + eps) and (beta^A + eps)/2.
 //  * Step 3: reciprocals of products stand in for several divisions (one division each).
 //  * Sec. 4.1 source: the quartic interpolants (three averages + two edge values) are the
-//    derivative of a confluent Newton (Hermite) form of their primitive; the Newton basis
-//    derivatives at the four Gauss-Legendre points are affine in J_{j-1}/J_j with constant
-//    coefficients.
+//    derivative of a confluent Newton (Hermite) form of their primitive, brought to monomial
+//    form; the integral of the depth times the bottom slope is then taken exactly (the
+//    four-point Gauss-Legendre rule of the definition is exact for that degree too).
 #pragma once
 
 #include <stdint.h>
@@ -527,14 +527,6 @@ SWALE_HD Flux interface_flux_plain(real g, real alpha, real w, real EL, real ER,
   f.FB = 0.5 * w * (BL + BR) + 0.5 * alpha * (BR - BL);
   return f;
 }
-
-// Four-point Gauss-Legendre rule on [0, 1]: nodes and weights.
-#define SWALE_GL4_T0 0.0694318442029737124
-#define SWALE_GL4_T1 0.330009478207571868
-#define SWALE_GL4_T2 0.669990521792428132
-#define SWALE_GL4_T3 0.930568155797026288
-#define SWALE_GL4_W0 0.173927422568726929
-#define SWALE_GL4_W1 0.326072577431273071
 
 // Width ratios of the source interpolant of cell j in its unit coordinate, from the shared
 // reciprocals: rm = J_{j-1}/J_j, irm = J_j/J_{j-1}, irp = J_j/J_{j+1}, i1m = J_j/(J_{j-1}+J_j),

@@ -13,12 +13,17 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "csrc", "opcount.cpp"), os.path.join(_HERE, "csrc", "swale_cell.cuh")]
+_SRC = [os.path.join(_HERE, "csrc", "opcount.cpp"), os.path.join(_HERE, "csrc", "swale_cell.cuh"),
+        os.path.join(_HERE, "csrc", "swale_adjoint.cuh")]
 _LIB = os.path.join(_HERE, "libswale_opcount.so")
 BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
 # RK combination of a stage per cell (stage-2 form): per variable J0*q, 0.75*(.), dt*R, Y+(.),
 # 0.25*(.), sum -> 6 operations; one reciprocal of the stage width; three products.
 RK_OPS = 3 * 6 + 1 + 3
+# Reverse of the RK combination of one step per cell (k_adj_rk's four phases): phase 3 one
+# reciprocal and 3 x 6 products; phase 2 one reciprocal and 3 x 8 operations; phase 1 one
+# reciprocal and 3 x 5; phase 0 three additions.
+RK_REV_OPS = 19 + 25 + 16 + 3
 
 _lib = None
 
@@ -37,6 +42,7 @@ def lib():
         build()
         _lib = ctypes.CDLL(_LIB)
         _lib.opc_count_stage.restype = None
+        _lib.opc_count_reverse.restype = None
     return _lib
 
 
@@ -63,3 +69,34 @@ def count_stage(E, M, B, J, bc="transmissive", g=9.812, eps_weno=1e-6, eps_pp=1e
             "recon_flops": rf, "update_flops": uf, "stage_flops": rf + uf, "cells_counted": n,
             "geom_flops": float(out[18] / n),
             "classes": [int(v) for v in out[15:18]]}
+
+
+def count_reverse(E, M, B, J, bc="transmissive", g=9.812, eps_weno=1e-6, eps_pp=1e-11, h_dry=1e-6, alpha=10.0,
+                  sample=None):
+    """FLOPs per cell of one stage's reverse sweep (reconstruction, source, one interface flux)."""
+    E, M, B, J = (np.ascontiguousarray(a, dtype=np.float64) for a in (E, M, B, J))
+    N = E.size
+    n = N if sample is None else min(N, sample)
+    c0 = (N - n) // 2
+    out = np.zeros(3)
+    vp = ctypes.c_void_p
+    lib().opc_count_reverse(ctypes.c_int64(N), vp(E.ctypes.data), vp(M.ctypes.data), vp(B.ctypes.data),
+                            vp(J.ctypes.data), ctypes.c_int32(BC[bc]), ctypes.c_double(g), ctypes.c_double(eps_weno),
+                            ctypes.c_double(eps_pp), ctypes.c_double(h_dry), ctypes.c_double(alpha),
+                            ctypes.c_int64(c0), ctypes.c_int64(c0 + n), vp(out.ctypes.data))
+    return {"recon_rev": float(out[0]), "source_rev": float(out[1]), "flux_rev": float(out[2]),
+            "stage_rev_flops": float(out.sum()), "cells_counted": n}
+
+
+def forward_step_flops(c):
+    """FP64 FLOPs per cell of one SSP-RK3 step from a count_stage result: three reconstructions,
+    less the mesh-only geometry of stage 1 (taken from the previous step's stage 2 on the same
+    mesh), and three updates. The mesh-velocity kernel is not counted."""
+    return 3.0 * c["recon_flops"] - c["geom_flops"] + 3.0 * c["update_flops"]
+
+
+def adjoint_step_flops(c, r):
+    """FP64 FLOPs per cell of one step of the checkpointed adjoint: three forward steps (the
+    forward run, the segment recompute and the recompute inside the step) and the reverse sweeps
+    of the three stages with the reverse RK combination. Gauge misfit terms are not counted."""
+    return 3.0 * forward_step_flops(c) + 3.0 * r["stage_rev_flops"] + RK_REV_OPS
