@@ -137,9 +137,10 @@ StepConst step_const(const swale_ctx* ctx) {
 void drop_graph(swale_ctx* ctx);
 
 // The state was set or restored: invalidate the mesh geometry cache (and the captured steps,
-// which carry the epoch).
+// which carry the epoch). The context's epochs are odd; the adjoint's second forward engine
+// draws even ones, so a cache tag written by one engine never matches the other's.
 void bump_geo(swale_ctx* ctx) {
-  ++ctx->geo_epoch;
+  ctx->geo_epoch += 2;
   drop_graph(ctx);
 }
 
@@ -361,17 +362,16 @@ unsigned grid_of(int32_t ntiles, int persistent) {
   return (unsigned)std::max(ntiles, 1);
 }
 
-// Enqueues one step on the context's stream.
-// Enqueues one step. stageD (optional, 3 entries): the device state each stage's kernels use;
-// copies of ctx->D that differ only in their edge arrays keep every stage's edge values (the
-// adjoint's recompute of a step).
-swale_status enqueue_step(swale_ctx* ctx, const DevState* stageD = nullptr) {
-  const StepConst K = step_const(ctx);
-  const DevState& D = ctx->D;
+// Enqueues one step of the state D on stream s with geometry-cache epoch `epoch`. stageD
+// (optional, 3 entries): the device state each stage's kernels use; copies of D that differ only
+// in their edge arrays keep every stage's edge values (the adjoint's recompute of a step).
+swale_status enqueue_step_on(swale_ctx* ctx, const DevState& D, cudaStream_t s, const DevState* stageD,
+                             uint32_t epoch) {
+  StepConst K = step_const(ctx);
+  K.geo_epoch = epoch;
   const DevState& D1 = stageD ? stageD[0] : D;
   const DevState& D2 = stageD ? stageD[1] : D;
   const DevState& D3 = stageD ? stageD[2] : D;
-  cudaStream_t s = ctx->stream;
   const unsigned gr = grid_of(D.nr, ctx->grid_r), gu = grid_of(D.nu, ctx->grid_u);
   const int Tr = ctx->Tr, Tu = ctx->Tu;
   const RhsOut none{nullptr, nullptr, nullptr, 0.0};
@@ -393,6 +393,11 @@ swale_status enqueue_step(swale_ctx* ctx, const DevState* stageD = nullptr) {
   if (st) return st;
   SW_CUDA(ctx, cudaGetLastError());
   return SWALE_OK;
+}
+
+// Enqueues one step of the context's state on its stream.
+swale_status enqueue_step(swale_ctx* ctx, const DevState* stageD = nullptr) {
+  return enqueue_step_on(ctx, ctx->D, ctx->stream, stageD, ctx->geo_epoch);
 }
 
 // Enqueues n steps: whole graphs of kGraphSteps steps, then single steps (graphs are not used
@@ -1177,8 +1182,10 @@ uint64_t adjoint_bytes(int64_t B, int64_t Nt, int64_t nsteps, int64_t ckpt_every
   const int64_t C = std::min(ckpt_every, nsteps), nseg = (nsteps + C - 1) / C;
   auto a = [](uint64_t n, uint64_t size) { return n * size + 256; };
   const uint64_t copy = 4 * a(Nt, 8) + a(NN, 8) + a(B, sizeof(DevScalars));
-  return 15 * a(Nt, 8) + 8 * a(NE, 8) + 20 * a(NE, 8) + (uint64_t)(nseg + C + 2) * copy + 2 * a((uint64_t)B * G, 8) +
-         a((uint64_t)nsteps * B * G, 8) + a(B, 8) + a((uint64_t)nsteps * B * 3, 8);
+  const uint64_t engine2 = 15 * a(Nt, 8) + 2 * a(NN, 8) + 10 * a(NE, 8) + a((uint64_t)SWALE_GEOM_VALUES * NE, 8) +
+                           a(NE, 1) + a(B, sizeof(DevScalars));
+  return 15 * a(Nt, 8) + 8 * a(NE, 8) + 20 * a(NE, 8) + engine2 + (uint64_t)(nseg + 2 * C + 2) * copy +
+         2 * a((uint64_t)B * G, 8) + a((uint64_t)nsteps * B * G, 8) + a(B, 8) + a((uint64_t)nsteps * B * 3, 8);
 }
 
 }  // namespace
@@ -1251,8 +1258,16 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     if (!s) s = dalloc(ctx, mem, &c.x, (size_t)NN);
     if (!s) s = dalloc(ctx, mem, &c.S, (size_t)B);
   };
+  // Segment recomputes run on a second, low-priority stream st2 (events: forward done, segment
+  // ready x 2 buffers, reverse of a segment done x 2 buffers).
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   auto release = [&](swale_status r) {
     cudaStreamSynchronize(st);
+    if (st2) cudaStreamSynchronize(st2);
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
+    if (st2) cudaStreamDestroy(st2);
     for (void* p : mem) cudaFree(p);
     return r;
   };
@@ -1270,10 +1285,30 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     for (double** p : ed)
       if (!s) s = dalloc(ctx, mem, p, (size_t)NE);
   }
-  std::vector<StateCopy> ckpt(nseg), seg(C);
+  // Second forward engine: its own state, stage, edge, geometry-cache and flag arrays and
+  // scalars (instance constants, work lists and the motion profile are shared, read only). It
+  // recomputes segment sg - 1 into one of two snapshot buffers while the context's stream
+  // reverses segment sg from the other.
+  DevState D2 = ctx->D;
+  {
+    double** cells2[] = {&D2.E0, &D2.M0, &D2.B0, &D2.Ea, &D2.Ma, &D2.Ba, &D2.Eb, &D2.Mb,
+                         &D2.Bb, &D2.YE, &D2.YM, &D2.YB, &D2.J0, &D2.J1, &D2.J2};
+    for (double** p : cells2)
+      if (!s) s = dalloc(ctx, mem, p, (size_t)Nt);
+    if (!s) s = dalloc(ctx, mem, &D2.x, (size_t)NN);
+    if (!s) s = dalloc(ctx, mem, &D2.w, (size_t)NN);
+    double** edges2[] = {&D2.eEL, &D2.eER, &D2.eBL, &D2.eBR, &D2.ehL, &D2.ehR, &D2.euL, &D2.euR, &D2.ipair, &D2.itri};
+    for (double** p : edges2)
+      if (!s) s = dalloc(ctx, mem, p, (size_t)NE);
+    if (!s) s = dalloc(ctx, mem, &D2.geo, (size_t)SWALE_GEOM_VALUES * NE);
+    if (!s) s = dalloc(ctx, mem, &D2.flags, (size_t)NE);
+    if (!s) s = dalloc(ctx, mem, &D2.S, (size_t)B);
+  }
+  std::vector<StateCopy> ckpt(nseg), seg(C), seg2(C);
   StateCopy fin, snap;
   for (auto& c : ckpt) alloc_copy(c);
   for (auto& c : seg) alloc_copy(c);
+  for (auto& c : seg2) alloc_copy(c);
   alloc_copy(fin);
   alloc_copy(snap);
   double *gx = nullptr, *obs = nullptr, *Jacc = nullptr, *alog = nullptr;
@@ -1299,28 +1334,36 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   e = e ? e : cudaMemsetAsync(A.lE, 0, Nt * sizeof(double), st);
   e = e ? e : cudaMemsetAsync(A.lM, 0, Nt * sizeof(double), st);
   e = e ? e : cudaMemsetAsync(A.lB, 0, Nt * sizeof(double), st);
+  int prio_least = 0, prio_greatest = 0;
+  e = e ? e : cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  e = e ? e : cudaStreamCreateWithPriority(&st2, cudaStreamNonBlocking, prio_least);
+  for (cudaEvent_t& x : ev) e = e ? e : cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
   if (e) return release(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
   DevState& D = ctx->D;
-  auto save = [&](StateCopy& c) {
+  auto save_from = [&](StateCopy& c, const DevState& X, cudaStream_t q) {
     const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
-    cudaError_t r = cudaMemcpyAsync(c.E, D.E0, Nt * sizeof(double), k, st);
-    r = r ? r : cudaMemcpyAsync(c.M, D.M0, Nt * sizeof(double), k, st);
-    r = r ? r : cudaMemcpyAsync(c.B, D.B0, Nt * sizeof(double), k, st);
-    r = r ? r : cudaMemcpyAsync(c.J, D.J0, Nt * sizeof(double), k, st);
-    r = r ? r : cudaMemcpyAsync(c.x, D.x, NN * sizeof(double), k, st);
-    r = r ? r : cudaMemcpyAsync(c.S, D.S, B * sizeof(DevScalars), k, st);
+    cudaError_t r = cudaMemcpyAsync(c.E, X.E0, Nt * sizeof(double), k, q);
+    r = r ? r : cudaMemcpyAsync(c.M, X.M0, Nt * sizeof(double), k, q);
+    r = r ? r : cudaMemcpyAsync(c.B, X.B0, Nt * sizeof(double), k, q);
+    r = r ? r : cudaMemcpyAsync(c.J, X.J0, Nt * sizeof(double), k, q);
+    r = r ? r : cudaMemcpyAsync(c.x, X.x, NN * sizeof(double), k, q);
+    r = r ? r : cudaMemcpyAsync(c.S, X.S, B * sizeof(DevScalars), k, q);
     return r;
   };
+  auto load_into = [&](const StateCopy& c, const DevState& X, cudaStream_t q) {
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    cudaError_t r = cudaMemcpyAsync(X.E0, c.E, Nt * sizeof(double), k, q);
+    r = r ? r : cudaMemcpyAsync(X.M0, c.M, Nt * sizeof(double), k, q);
+    r = r ? r : cudaMemcpyAsync(X.B0, c.B, Nt * sizeof(double), k, q);
+    r = r ? r : cudaMemcpyAsync(X.J0, c.J, Nt * sizeof(double), k, q);
+    r = r ? r : cudaMemcpyAsync(X.x, c.x, NN * sizeof(double), k, q);
+    r = r ? r : cudaMemcpyAsync(X.S, c.S, B * sizeof(DevScalars), k, q);
+    return r;
+  };
+  auto save = [&](StateCopy& c) { return save_from(c, D, st); };
   auto load = [&](const StateCopy& c) {
     bump_geo(ctx);
-    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
-    cudaError_t r = cudaMemcpyAsync(D.E0, c.E, Nt * sizeof(double), k, st);
-    r = r ? r : cudaMemcpyAsync(D.M0, c.M, Nt * sizeof(double), k, st);
-    r = r ? r : cudaMemcpyAsync(D.B0, c.B, Nt * sizeof(double), k, st);
-    r = r ? r : cudaMemcpyAsync(D.J0, c.J, Nt * sizeof(double), k, st);
-    r = r ? r : cudaMemcpyAsync(D.x, c.x, NN * sizeof(double), k, st);
-    r = r ? r : cudaMemcpyAsync(D.S, c.S, B * sizeof(DevScalars), k, st);
-    return r;
+    return load_into(c, D, st);
   };
   // The forward records the stage viscosities; every recomputation replays them.
   double* old_log = ctx->alpha_log;
@@ -1381,15 +1424,35 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   nvtxRangePop();
   NvtxRange nvtx_reverse("adjoint reverse");
   // ---- reverse, segment by segment ----
+  // The second engine recomputes segment sg from its checkpoint on st2, a snapshot per step,
+  // into buffer sg % 2 (its geometry-cache epochs are even, fresh at every segment).
+  uint32_t epoch2 = 0;
+  auto recompute_segment = [&](int64_t sg) {
+    const int64_t n0 = sg * C, n1 = std::min(nsteps, n0 + C);
+    std::vector<StateCopy>& buf = (sg & 1) ? seg2 : seg;
+    epoch2 += 2;
+    e = load_into(ckpt[sg], D2, st2);
+    for (int64_t m = n0; m < n1 && !s && !e; ++m) {
+      e = save_from(buf[m - n0], D2, st2);
+      if (!e && m + 1 < n1) s = enqueue_step_on(ctx, D2, st2, nullptr, epoch2);
+    }
+    if (!s && !e) e = cudaEventRecord(ev[1 + (sg & 1)], st2);
+  };
+  if (!s && !e) e = cudaEventRecord(ev[0], st);
+  if (!s && !e) e = cudaStreamWaitEvent(st2, ev[0], 0);
+  if (!s && !e) recompute_segment(nseg - 1);
   for (int64_t sg = nseg - 1; sg >= 0 && !s && !e; --sg) {
     const int64_t n0 = sg * C, n1 = std::min(nsteps, n0 + C);
-    e = load(ckpt[sg]);
-    for (int64_t m = n0; m < n1 && !s && !e; ++m) {
-      e = save(seg[m - n0]);
-      if (!e && m + 1 < n1) s = enqueue_step(ctx);
+    if (sg >= 1) {
+      // Segment sg - 1 goes into the buffer that the reverse of segment sg + 1 last read.
+      if (sg + 1 < nseg) e = cudaStreamWaitEvent(st2, ev[3 + ((sg + 1) & 1)], 0);
+      if (!e) recompute_segment(sg - 1);
+      if (s || e) break;
     }
+    e = cudaStreamWaitEvent(st, ev[1 + (sg & 1)], 0);
+    const std::vector<StateCopy>& buf = (sg & 1) ? seg2 : seg;
     for (int64_t m = n1 - 1; m >= n0 && !s && !e; --m) {
-      const StateCopy& c = seg[m - n0];
+      const StateCopy& c = buf[m - n0];
       e = load(c);
       // q^n, J^n of this step for stage 1 and the RK combination.
       e = e ? e : cudaMemcpyAsync(snap.E, c.E, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -1410,6 +1473,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
       launch_adj_rk<0>(ctx, A);
       e = cudaGetLastError();
     }
+    if (!s && !e) e = cudaEventRecord(ev[3 + (sg & 1)], st);
   }
   if (!s && !e) e = load(fin);
   restore_ctx();
