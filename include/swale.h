@@ -256,11 +256,13 @@ swale_status swale_get_alpha_log(swale_ctx* ctx, double* log);
  * tests and max/min selections are frozen (a tie follows the first argument); if a replay log
  * is active (swale_alpha_log mode 2) the forward run replays it instead. Checkpoints of
  * the state every ckpt_every steps; each segment is recomputed once with per-step snapshots
- * (by a second set of state arrays on a second, low-priority stream, one segment ahead of the
- * reverse sweep, which runs on the context's stream) and each step once more inside its reverse
- * sweep. Device memory beyond the context's own: about 5 (ceil(nsteps/C) + 2 C + 2) + 95
- * doubles per cell with C = min(ckpt_every, nsteps), exactly the value of swale_adjoint_bytes;
- * all of it (and the second stream) is freed before the call returns. The mesh must
+ * (by a further set of state arrays on a low-priority stream, one segment ahead of the reverse
+ * sweep) and each step once more before its reverse sweep (on a third stream, alternating
+ * between the context's arrays and one more set, one step ahead of the reverse sweep, which
+ * runs on the context's stream). Device memory beyond the context's own: about
+ * 5 (ceil(nsteps/C) + 2 C + 3) + 167 doubles per cell with C = min(ckpt_every, nsteps), exactly
+ * the value of swale_adjoint_bytes; all of it (and the two streams) is freed before the call
+ * returns. The mesh must
  * be prescribed (static or profile motion) and t_end = 0. On return the context holds the
  * state after the nsteps steps.
  * Errors: SWALE_EINVAL, SWALE_ENOMEM, SWALE_ECUDA, and the status errors of swale_advance. */

@@ -1160,8 +1160,7 @@ void launch_adj_stage(swale_ctx* ctx, const DevState& D, const StepConst& K, con
 }
 
 template <int PH>
-void launch_adj_rk(swale_ctx* ctx, const AdjState& A) {
-  const DevState& D = ctx->D;
+void launch_adj_rk(swale_ctx* ctx, const DevState& D, const AdjState& A) {
   const unsigned gu = grid_of(D.nu, ctx->grid_u);
   if (ctx->Tu == 64) k_adj_rk<PH, 64><<<gu, 64, 0, ctx->stream>>>(D, A);
   else if (ctx->Tu == 256) k_adj_rk<PH, 256><<<gu, 256, 0, ctx->stream>>>(D, A);
@@ -1182,9 +1181,9 @@ uint64_t adjoint_bytes(int64_t B, int64_t Nt, int64_t nsteps, int64_t ckpt_every
   const int64_t C = std::min(ckpt_every, nsteps), nseg = (nsteps + C - 1) / C;
   auto a = [](uint64_t n, uint64_t size) { return n * size + 256; };
   const uint64_t copy = 4 * a(Nt, 8) + a(NN, 8) + a(B, sizeof(DevScalars));
-  const uint64_t engine2 = 15 * a(Nt, 8) + 2 * a(NN, 8) + 10 * a(NE, 8) + a((uint64_t)SWALE_GEOM_VALUES * NE, 8) +
-                           a(NE, 1) + a(B, sizeof(DevScalars));
-  return 15 * a(Nt, 8) + 8 * a(NE, 8) + 20 * a(NE, 8) + engine2 + (uint64_t)(nseg + 2 * C + 2) * copy +
+  const uint64_t state_set = 15 * a(Nt, 8) + 2 * a(NN, 8) + 10 * a(NE, 8) +
+                             a((uint64_t)SWALE_GEOM_VALUES * NE, 8) + a(NE, 1) + a(B, sizeof(DevScalars));
+  return 15 * a(Nt, 8) + 8 * a(NE, 8) + 2 * state_set + 40 * a(NE, 8) + (uint64_t)(nseg + 2 * C + 3) * copy +
          2 * a((uint64_t)B * G, 8) + a((uint64_t)nsteps * B * G, 8) + a(B, 8) + a((uint64_t)nsteps * B * 3, 8);
 }
 
@@ -1258,16 +1257,20 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     if (!s) s = dalloc(ctx, mem, &c.x, (size_t)NN);
     if (!s) s = dalloc(ctx, mem, &c.S, (size_t)B);
   };
-  // Segment recomputes run on a second, low-priority stream st2 (events: forward done, segment
-  // ready x 2 buffers, reverse of a segment done x 2 buffers).
-  cudaStream_t st2 = nullptr;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // Three streams: the context's (forward run, reverse kernels), st2 (segment recomputes, low
+  // priority), st3 (the recompute of each step before its reverse sweep). Events: 0 forward
+  // done; 1-2 segment buffer b filled; 3-4 segment buffer b read; 5-6 step recompute on state
+  // set k done; 7-8 reverse sweep on state set k done.
+  cudaStream_t st2 = nullptr, st3 = nullptr;
+  cudaEvent_t ev[9] = {};
   auto release = [&](swale_status r) {
     cudaStreamSynchronize(st);
     if (st2) cudaStreamSynchronize(st2);
+    if (st3) cudaStreamSynchronize(st3);
     for (cudaEvent_t x : ev)
       if (x) cudaEventDestroy(x);
     if (st2) cudaStreamDestroy(st2);
+    if (st3) cudaStreamDestroy(st3);
     for (void* p : mem) cudaFree(p);
     return r;
   };
@@ -1277,40 +1280,50 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   for (double** p : cellbufs)
     if (!s) s = dalloc(ctx, mem, p, (size_t)Nt);
   for (int k = 0; k < 8 && !s; ++k) s = dalloc(ctx, mem, &A.ab[k], (size_t)NE);
-  // Edge values of stages 1 and 2 of the step being reversed (stage 3 keeps the context's).
-  DevState Ds[3] = {ctx->D, ctx->D, ctx->D};
-  for (int st2 = 0; st2 < 2 && !s; ++st2) {
-    DevState& d = Ds[st2];
-    double** ed[] = {&d.eEL, &d.eER, &d.eBL, &d.eBR, &d.ehL, &d.ehR, &d.euL, &d.euR, &d.ipair, &d.itri};
-    for (double** p : ed)
-      if (!s) s = dalloc(ctx, mem, p, (size_t)NE);
-  }
-  // Second forward engine: its own state, stage, edge, geometry-cache and flag arrays and
-  // scalars (instance constants, work lists and the motion profile are shared, read only). It
-  // recomputes segment sg - 1 into one of two snapshot buffers while the context's stream
-  // reverses segment sg from the other.
-  DevState D2 = ctx->D;
-  {
-    double** cells2[] = {&D2.E0, &D2.M0, &D2.B0, &D2.Ea, &D2.Ma, &D2.Ba, &D2.Eb, &D2.Mb,
-                         &D2.Bb, &D2.YE, &D2.YM, &D2.YB, &D2.J0, &D2.J1, &D2.J2};
-    for (double** p : cells2)
+  // A further set of state arrays: its own state, stage, edge, geometry-cache and flag arrays and
+  // scalars (instance constants, work lists and the motion profile are shared, read only).
+  auto alloc_state_set = [&](DevState& X) {
+    X = ctx->D;
+    double** cells[] = {&X.E0, &X.M0, &X.B0, &X.Ea, &X.Ma, &X.Ba, &X.Eb, &X.Mb,
+                        &X.Bb, &X.YE, &X.YM, &X.YB, &X.J0, &X.J1, &X.J2};
+    for (double** p : cells)
       if (!s) s = dalloc(ctx, mem, p, (size_t)Nt);
-    if (!s) s = dalloc(ctx, mem, &D2.x, (size_t)NN);
-    if (!s) s = dalloc(ctx, mem, &D2.w, (size_t)NN);
-    double** edges2[] = {&D2.eEL, &D2.eER, &D2.eBL, &D2.eBR, &D2.ehL, &D2.ehR, &D2.euL, &D2.euR, &D2.ipair, &D2.itri};
-    for (double** p : edges2)
+    if (!s) s = dalloc(ctx, mem, &X.x, (size_t)NN);
+    if (!s) s = dalloc(ctx, mem, &X.w, (size_t)NN);
+    double** edges[] = {&X.eEL, &X.eER, &X.eBL, &X.eBR, &X.ehL, &X.ehR, &X.euL, &X.euR, &X.ipair, &X.itri};
+    for (double** p : edges)
       if (!s) s = dalloc(ctx, mem, p, (size_t)NE);
-    if (!s) s = dalloc(ctx, mem, &D2.geo, (size_t)SWALE_GEOM_VALUES * NE);
-    if (!s) s = dalloc(ctx, mem, &D2.flags, (size_t)NE);
-    if (!s) s = dalloc(ctx, mem, &D2.S, (size_t)B);
+    if (!s) s = dalloc(ctx, mem, &X.geo, (size_t)SWALE_GEOM_VALUES * NE);
+    if (!s) s = dalloc(ctx, mem, &X.flags, (size_t)NE);
+    if (!s) s = dalloc(ctx, mem, &X.S, (size_t)B);
+  };
+  // The step recomputes alternate between two state sets R[0] (the context's arrays) and R[1],
+  // so that the recompute of step m - 1 (on st3) overlaps the reverse sweep of step m. Each set
+  // keeps the edge values of stages 1 and 2 in sets of their own (stage 3 keeps the set's).
+  DevState R[2], Ds[2][3];
+  R[0] = ctx->D;
+  alloc_state_set(R[1]);
+  for (int k = 0; k < 2; ++k) {
+    Ds[k][0] = Ds[k][1] = Ds[k][2] = R[k];
+    for (int t = 0; t < 2 && !s; ++t) {
+      DevState& d = Ds[k][t];
+      double** ed[] = {&d.eEL, &d.eER, &d.eBL, &d.eBR, &d.ehL, &d.ehR, &d.euL, &d.euR, &d.ipair, &d.itri};
+      for (double** p : ed)
+        if (!s) s = dalloc(ctx, mem, p, (size_t)NE);
+    }
   }
+  // Segment recomputes: a third state set D2 recomputes segment sg - 1 into one of two
+  // snapshot buffers while segment sg is reversed from the other.
+  DevState D2;
+  alloc_state_set(D2);
   std::vector<StateCopy> ckpt(nseg), seg(C), seg2(C);
-  StateCopy fin, snap;
+  StateCopy fin, snapR[2];
   for (auto& c : ckpt) alloc_copy(c);
   for (auto& c : seg) alloc_copy(c);
   for (auto& c : seg2) alloc_copy(c);
   alloc_copy(fin);
-  alloc_copy(snap);
+  alloc_copy(snapR[0]);
+  alloc_copy(snapR[1]);
   double *gx = nullptr, *obs = nullptr, *Jacc = nullptr, *alog = nullptr;
   if (!s) s = dalloc(ctx, mem, &gx, (size_t)B * G);
   if (!s) s = dalloc(ctx, mem, &obs, (size_t)nsteps * B * G);
@@ -1319,10 +1332,14 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   int64_t* gcell = nullptr;  // last cell of each gauge (searched from, the mesh moves little per step)
   if (!s) s = dalloc(ctx, mem, &gcell, (size_t)B * G);
   if (s) return release(s);
-  A.sE = snap.E;
-  A.sM = snap.M;
-  A.sB = snap.B;
-  A.sJ = snap.J;
+  // q^n and J^n of the step being reversed, per state set.
+  AdjState AR[2] = {A, A};
+  for (int k = 0; k < 2; ++k) {
+    AR[k].sE = snapR[k].E;
+    AR[k].sM = snapR[k].M;
+    AR[k].sB = snapR[k].B;
+    AR[k].sJ = snapR[k].J;
+  }
   cudaError_t e = cudaSuccess;
   e = e ? e : cudaMemcpyAsync(gx, gauges_x, (size_t)B * G * sizeof(double), cudaMemcpyDefault, st);
   e = e ? e : cudaMemcpyAsync(obs, h_obs, (size_t)nsteps * B * G * sizeof(double), cudaMemcpyDefault, st);
@@ -1337,6 +1354,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   int prio_least = 0, prio_greatest = 0;
   e = e ? e : cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   e = e ? e : cudaStreamCreateWithPriority(&st2, cudaStreamNonBlocking, prio_least);
+  e = e ? e : cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking);
   for (cudaEvent_t& x : ev) e = e ? e : cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
   if (e) return release(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
   DevState& D = ctx->D;
@@ -1424,13 +1442,14 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   nvtxRangePop();
   NvtxRange nvtx_reverse("adjoint reverse");
   // ---- reverse, segment by segment ----
-  // The second engine recomputes segment sg from its checkpoint on st2, a snapshot per step,
-  // into buffer sg % 2 (its geometry-cache epochs are even, fresh at every segment).
-  uint32_t epoch2 = 0;
+  // The set D2 recomputes segment sg from its checkpoint on st2, a snapshot per step, into
+  // buffer sg % 2. Geometry-cache epochs never coincide between state sets: the context's are
+  // odd, D2's are 2 mod 4, R[1]'s are 0 mod 4 (fresh at every load).
+  uint32_t epoch2 = 2, epochR1 = 0;
   auto recompute_segment = [&](int64_t sg) {
     const int64_t n0 = sg * C, n1 = std::min(nsteps, n0 + C);
     std::vector<StateCopy>& buf = (sg & 1) ? seg2 : seg;
-    epoch2 += 2;
+    epoch2 += 4;
     e = load_into(ckpt[sg], D2, st2);
     for (int64_t m = n0; m < n1 && !s && !e; ++m) {
       e = save_from(buf[m - n0], D2, st2);
@@ -1441,39 +1460,57 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   if (!s && !e) e = cudaEventRecord(ev[0], st);
   if (!s && !e) e = cudaStreamWaitEvent(st2, ev[0], 0);
   if (!s && !e) recompute_segment(nseg - 1);
+  bool used[2] = {false, false};
+  int64_t idx = 0;
   for (int64_t sg = nseg - 1; sg >= 0 && !s && !e; --sg) {
     const int64_t n0 = sg * C, n1 = std::min(nsteps, n0 + C);
     if (sg >= 1) {
-      // Segment sg - 1 goes into the buffer that the reverse of segment sg + 1 last read.
+      // Segment sg - 1 goes into the buffer whose snapshots of segment sg + 1 st3 has read.
       if (sg + 1 < nseg) e = cudaStreamWaitEvent(st2, ev[3 + ((sg + 1) & 1)], 0);
       if (!e) recompute_segment(sg - 1);
       if (s || e) break;
     }
-    e = cudaStreamWaitEvent(st, ev[1 + (sg & 1)], 0);
+    e = cudaStreamWaitEvent(st3, ev[1 + (sg & 1)], 0);
     const std::vector<StateCopy>& buf = (sg & 1) ? seg2 : seg;
-    for (int64_t m = n1 - 1; m >= n0 && !s && !e; --m) {
+    for (int64_t m = n1 - 1; m >= n0 && !s && !e; --m, ++idx) {
+      const int k = (int)(idx & 1);
+      const DevState& X = R[k];
       const StateCopy& c = buf[m - n0];
-      e = load(c);
-      // q^n, J^n of this step for stage 1 and the RK combination.
-      e = e ? e : cudaMemcpyAsync(snap.E, c.E, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st);
-      e = e ? e : cudaMemcpyAsync(snap.M, c.M, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st);
-      e = e ? e : cudaMemcpyAsync(snap.B, c.B, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st);
-      e = e ? e : cudaMemcpyAsync(snap.J, c.J, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      // Recompute step m on state set k (st3), once the reverse sweep that last used it is done:
+      // q^(1), q^(2), the stage meshes and node velocities stay in the set's state arrays, each
+      // stage's edge values in its own set; q^n, J^n go to the set's snapshot.
+      if (used[k]) e = cudaStreamWaitEvent(st3, ev[7 + k], 0);
+      used[k] = true;
+      uint32_t epoch;
+      if (k == 0) {
+        bump_geo(ctx);
+        epoch = ctx->geo_epoch;
+      } else {
+        epochR1 += 4;
+        epoch = epochR1;
+      }
+      e = e ? e : load_into(c, X, st3);
+      e = e ? e : cudaMemcpyAsync(snapR[k].E, c.E, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st3);
+      e = e ? e : cudaMemcpyAsync(snapR[k].M, c.M, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st3);
+      e = e ? e : cudaMemcpyAsync(snapR[k].B, c.B, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st3);
+      e = e ? e : cudaMemcpyAsync(snapR[k].J, c.J, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st3);
       if (e) break;
-      // Recompute the step: q^(1), q^(2), the stage meshes and node velocities stay in the state
-      // arrays, each stage's edge values in its own set.
-      if ((s = enqueue_step(ctx, Ds))) break;
-      k_misfit<1><<<gg, 128, 0, st>>>(D, A, (int32_t)B, G, gx, obs + m * B * G, Jacc, gcell);
-      launch_adj_rk<3>(ctx, A);
-      launch_adj_stage<3>(ctx, Ds[2], K, A, D.Eb, D.Mb, D.Bb, D.J2);
-      launch_adj_rk<2>(ctx, A);
-      launch_adj_stage<2>(ctx, Ds[1], K, A, D.Ea, D.Ma, D.Ba, D.J1);
-      launch_adj_rk<1>(ctx, A);
-      launch_adj_stage<1>(ctx, Ds[0], K, A, snap.E, snap.M, snap.B, snap.J);
-      launch_adj_rk<0>(ctx, A);
+      if ((s = enqueue_step_on(ctx, X, st3, Ds[k], epoch))) break;
+      if ((e = cudaEventRecord(ev[5 + k], st3))) break;
+      // Reverse sweep of step m on the context's stream.
+      if ((e = cudaStreamWaitEvent(st, ev[5 + k], 0))) break;
+      k_misfit<1><<<gg, 128, 0, st>>>(X, A, (int32_t)B, G, gx, obs + m * B * G, Jacc, gcell);
+      launch_adj_rk<3>(ctx, X, AR[k]);
+      launch_adj_stage<3>(ctx, Ds[k][2], K, AR[k], X.Eb, X.Mb, X.Bb, X.J2);
+      launch_adj_rk<2>(ctx, X, AR[k]);
+      launch_adj_stage<2>(ctx, Ds[k][1], K, AR[k], X.Ea, X.Ma, X.Ba, X.J1);
+      launch_adj_rk<1>(ctx, X, AR[k]);
+      launch_adj_stage<1>(ctx, Ds[k][0], K, AR[k], snapR[k].E, snapR[k].M, snapR[k].B, snapR[k].J);
+      launch_adj_rk<0>(ctx, X, AR[k]);
       e = cudaGetLastError();
+      if (!e) e = cudaEventRecord(ev[7 + k], st);
     }
-    if (!s && !e) e = cudaEventRecord(ev[3 + (sg & 1)], st);
+    if (!s && !e) e = cudaEventRecord(ev[3 + (sg & 1)], st3);
   }
   if (!s && !e) e = load(fin);
   restore_ctx();
