@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-batched-adjoint", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--variant-steps", type=int, default=100)
+    ap.add_argument("--no-loop-baseline", action="store_true",
+                    help="skip the per-instance launch-loop comparisons of the batched sections (profiling runs)")
     return ap.parse_args()
 
 
@@ -261,6 +263,8 @@ def bench_batched(args, stream, dev, rank=0, ws=1):
            "ms_per_step": ms / args.batched_steps, "tiles": list(tiles), "status_bits": bits,
            "parallelism": f"instances sharded over {ws} ranks" if ws > 1 else "single", "scaling": "weak"}
     out["roofline"] = fp64_roofline(batch_step_flops(bt_all), out["value"], "whole step, all kernels")
+    if args.no_loop_baseline:
+        return out
     # Same work, batched vs one context per instance (launches per instance and step).
     sub = 512
     sb = W.Batch(name="subset", off=bt.off[:sub + 1].copy(), x=bt.x[:int(bt.off[sub]) + sub],
@@ -416,6 +420,8 @@ def bench_batched_adjoint(args, stream, dev=None, rank=0, ws=1):
            "status_bits": bits,
            "roofline": fp64_roofline(adjoint_step_flops(bt.instance(0)), Nt_all * K / (ms * 1e-3),
                                      "whole gradient: 3 forward steps + reverse sweep per step")}
+    if args.no_loop_baseline:
+        return out
     # One swale_adjoint per instance on a subset, same steps, against the batch of the subset.
     sub, Ks = 32, min(K, 64)
     sb = W.Batch(name="subset", off=bt.off[:sub + 1].copy(), x=bt.x[:int(bt.off[sub]) + sub],

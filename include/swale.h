@@ -259,8 +259,10 @@ swale_status swale_get_alpha_log(swale_ctx* ctx, double* log);
  * (by a further set of state arrays on a low-priority stream, one segment ahead of the reverse
  * sweep) and each step once more before its reverse sweep (on a third stream, alternating
  * between the context's arrays and one more set, one step ahead of the reverse sweep, which
- * runs on the context's stream). Device memory beyond the context's own: about
- * 5 (ceil(nsteps/C) + 2 C + 3) + 167 doubles per cell with C = min(ckpt_every, nsteps), exactly
+ * runs on the context's stream). These forward runs compute the mesh geometry in every stage
+ * (no reuse of the previous step's), so the trajectory, and the gradient up to the order of
+ * atomic additions, does not depend on ckpt_every. Device memory beyond the context's own: about
+ * 5 (ceil(nsteps/C) + 2 C + 3) + 117 doubles per cell with C = min(ckpt_every, nsteps), exactly
  * the value of swale_adjoint_bytes; all of it (and the two streams) is freed before the call
  * returns. The mesh must
  * be prescribed (static or profile motion) and t_end = 0. On return the context holds the

@@ -137,10 +137,9 @@ StepConst step_const(const swale_ctx* ctx) {
 void drop_graph(swale_ctx* ctx);
 
 // The state was set or restored: invalidate the mesh geometry cache (and the captured steps,
-// which carry the epoch). The context's epochs are odd; the adjoint's second forward engine
-// draws even ones, so a cache tag written by one engine never matches the other's.
+// which carry the epoch).
 void bump_geo(swale_ctx* ctx) {
-  ctx->geo_epoch += 2;
+  ++ctx->geo_epoch;
   drop_graph(ctx);
 }
 
@@ -1181,8 +1180,7 @@ uint64_t adjoint_bytes(int64_t B, int64_t Nt, int64_t nsteps, int64_t ckpt_every
   const int64_t C = std::min(ckpt_every, nsteps), nseg = (nsteps + C - 1) / C;
   auto a = [](uint64_t n, uint64_t size) { return n * size + 256; };
   const uint64_t copy = 4 * a(Nt, 8) + a(NN, 8) + a(B, sizeof(DevScalars));
-  const uint64_t state_set = 15 * a(Nt, 8) + 2 * a(NN, 8) + 10 * a(NE, 8) +
-                             a((uint64_t)SWALE_GEOM_VALUES * NE, 8) + a(NE, 1) + a(B, sizeof(DevScalars));
+  const uint64_t state_set = 15 * a(Nt, 8) + 2 * a(NN, 8) + 10 * a(NE, 8) + a(NE, 1) + a(B, sizeof(DevScalars));
   return 15 * a(Nt, 8) + 8 * a(NE, 8) + 2 * state_set + 40 * a(NE, 8) + (uint64_t)(nseg + 2 * C + 3) * copy +
          2 * a((uint64_t)B * G, 8) + a((uint64_t)nsteps * B * G, 8) + a(B, 8) + a((uint64_t)nsteps * B * 3, 8);
 }
@@ -1280,10 +1278,19 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   for (double** p : cellbufs)
     if (!s) s = dalloc(ctx, mem, p, (size_t)Nt);
   for (int k = 0; k < 8 && !s; ++k) s = dalloc(ctx, mem, &A.ab[k], (size_t)NE);
-  // A further set of state arrays: its own state, stage, edge, geometry-cache and flag arrays and
-  // scalars (instance constants, work lists and the motion profile are shared, read only).
+  // Every forward run of the adjoint (the forward with checkpoints, the segment and the step
+  // recomputes) computes the mesh geometry in all three stages instead of taking stage 1's from
+  // the cache: a run that starts from a checkpoint has no cache entry, so with the cache the
+  // recomputed trajectory would differ from the forward one by rounding wherever a segment
+  // starts, and near a detector or limiter threshold that can flip a frozen branch. Without it
+  // the trajectory, and the gradient up to the order of atomic additions, is the same for every
+  // checkpoint interval.
+  DevState base = ctx->D;
+  base.geo = nullptr;
+  // A further set of state arrays: its own state, stage, edge and flag arrays and scalars
+  // (instance constants, work lists and the motion profile are shared, read only).
   auto alloc_state_set = [&](DevState& X) {
-    X = ctx->D;
+    X = base;
     double** cells[] = {&X.E0, &X.M0, &X.B0, &X.Ea, &X.Ma, &X.Ba, &X.Eb, &X.Mb,
                         &X.Bb, &X.YE, &X.YM, &X.YB, &X.J0, &X.J1, &X.J2};
     for (double** p : cells)
@@ -1293,7 +1300,6 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     double** edges[] = {&X.eEL, &X.eER, &X.eBL, &X.eBR, &X.ehL, &X.ehR, &X.euL, &X.euR, &X.ipair, &X.itri};
     for (double** p : edges)
       if (!s) s = dalloc(ctx, mem, p, (size_t)NE);
-    if (!s) s = dalloc(ctx, mem, &X.geo, (size_t)SWALE_GEOM_VALUES * NE);
     if (!s) s = dalloc(ctx, mem, &X.flags, (size_t)NE);
     if (!s) s = dalloc(ctx, mem, &X.S, (size_t)B);
   };
@@ -1301,7 +1307,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   // so that the recompute of step m - 1 (on st3) overlaps the reverse sweep of step m. Each set
   // keeps the edge values of stages 1 and 2 in sets of their own (stage 3 keeps the set's).
   DevState R[2], Ds[2][3];
-  R[0] = ctx->D;
+  R[0] = base;
   alloc_state_set(R[1]);
   for (int k = 0; k < 2; ++k) {
     Ds[k][0] = Ds[k][1] = Ds[k][2] = R[k];
@@ -1432,7 +1438,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   // ---- forward with checkpoints and the misfit ----
   for (int64_t n = 0; n < nsteps && !s; ++n) {
     if (n % C == 0 && (e = save(ckpt[n / C]))) break;
-    s = enqueue_step(ctx);
+    s = enqueue_step_on(ctx, base, st, nullptr, 0);
     if (!s) k_misfit<0><<<gg, 128, 0, st>>>(D, A, (int32_t)B, G, gx, obs + n * B * G, Jacc, gcell);
   }
   if (!s && !e) e = save(fin);
@@ -1443,17 +1449,14 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   NvtxRange nvtx_reverse("adjoint reverse");
   // ---- reverse, segment by segment ----
   // The set D2 recomputes segment sg from its checkpoint on st2, a snapshot per step, into
-  // buffer sg % 2. Geometry-cache epochs never coincide between state sets: the context's are
-  // odd, D2's are 2 mod 4, R[1]'s are 0 mod 4 (fresh at every load).
-  uint32_t epoch2 = 2, epochR1 = 0;
+  // buffer sg % 2.
   auto recompute_segment = [&](int64_t sg) {
     const int64_t n0 = sg * C, n1 = std::min(nsteps, n0 + C);
     std::vector<StateCopy>& buf = (sg & 1) ? seg2 : seg;
-    epoch2 += 4;
     e = load_into(ckpt[sg], D2, st2);
     for (int64_t m = n0; m < n1 && !s && !e; ++m) {
       e = save_from(buf[m - n0], D2, st2);
-      if (!e && m + 1 < n1) s = enqueue_step_on(ctx, D2, st2, nullptr, epoch2);
+      if (!e && m + 1 < n1) s = enqueue_step_on(ctx, D2, st2, nullptr, 0);
     }
     if (!s && !e) e = cudaEventRecord(ev[1 + (sg & 1)], st2);
   };
@@ -1481,21 +1484,13 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
       // stage's edge values in its own set; q^n, J^n go to the set's snapshot.
       if (used[k]) e = cudaStreamWaitEvent(st3, ev[7 + k], 0);
       used[k] = true;
-      uint32_t epoch;
-      if (k == 0) {
-        bump_geo(ctx);
-        epoch = ctx->geo_epoch;
-      } else {
-        epochR1 += 4;
-        epoch = epochR1;
-      }
       e = e ? e : load_into(c, X, st3);
       e = e ? e : cudaMemcpyAsync(snapR[k].E, c.E, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st3);
       e = e ? e : cudaMemcpyAsync(snapR[k].M, c.M, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st3);
       e = e ? e : cudaMemcpyAsync(snapR[k].B, c.B, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st3);
       e = e ? e : cudaMemcpyAsync(snapR[k].J, c.J, Nt * sizeof(double), cudaMemcpyDeviceToDevice, st3);
       if (e) break;
-      if ((s = enqueue_step_on(ctx, X, st3, Ds[k], epoch))) break;
+      if ((s = enqueue_step_on(ctx, X, st3, Ds[k], 0))) break;
       if ((e = cudaEventRecord(ev[5 + k], st3))) break;
       // Reverse sweep of step m on the context's stream.
       if ((e = cudaStreamWaitEvent(st, ev[5 + k], 0))) break;

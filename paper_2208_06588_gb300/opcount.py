@@ -97,6 +97,7 @@ def forward_step_flops(c):
 
 def adjoint_step_flops(c, r):
     """FP64 FLOPs per cell of one step of the checkpointed adjoint: three forward steps (the
-    forward run, the segment recompute and the recompute inside the step) and the reverse sweeps
-    of the three stages with the reverse RK combination. Gauge misfit terms are not counted."""
-    return 3.0 * forward_step_flops(c) + 3.0 * r["stage_rev_flops"] + RK_REV_OPS
+    forward run, the segment recompute and the recompute inside the step), each computing the
+    mesh geometry in all three stages, and the reverse sweeps of the three stages with the
+    reverse RK combination. Gauge misfit terms are not counted."""
+    return 3.0 * (forward_step_flops(c) + c["geom_flops"]) + 3.0 * r["stage_rev_flops"] + RK_REV_OPS

@@ -52,12 +52,12 @@ def test_autograd_wrapper_has_no_cpu_path():
 
 
 def test_adjoint_bytes_formula():
-    """swale_adjoint_bytes is host arithmetic: 5 (ceil(K/C) + 2 C + 3) + 167 doubles and two
+    """swale_adjoint_bytes is host arithmetic: 5 (ceil(K/C) + 2 C + 3) + 117 doubles and two
     bytes per cell, plus per-instance scalars, gauges, observations and the viscosity log."""
     from paper_2208_06588_gb300 import binding as B
     Nt, Bn, K, C, G = 1_000_000, 4, 4000, 64, 16
     n = B.swale_adjoint_bytes(Bn, Nt, K, C, G)
-    per_cell = 8 * (5 * (-(-K // C) + 2 * C + 3) + 167) + 2
+    per_cell = 8 * (5 * (-(-K // C) + 2 * C + 3) + 117) + 2
     assert per_cell * Nt <= n <= per_cell * Nt + 8 * (K * Bn * (G + 3)) + 2_000_000
     assert B.swale_adjoint_bytes(Bn, Nt, K, K, G) > B.swale_adjoint_bytes(Bn, Nt, K, 64, G)
     with pytest.raises(B.SwaleError):
