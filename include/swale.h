@@ -39,7 +39,7 @@ typedef enum {
   SWALE_ECUDA = -3,       /* a CUDA runtime call failed */
   SWALE_EMESH = -4,       /* a cell width became <= 0 (mesh assumption A1 of Sec. 2.1) */
   SWALE_ENEGDEPTH = -5,   /* reserved: negative depth is reported as a warning bit */
-  SWALE_ENONFINITE = -6,  /* a non-finite value appeared */
+  SWALE_ENONFINITE = -6,  /* a non-finite value appeared, or no finite dt (SWALE_BIT_NODT) */
   SWALE_ETIMEOUT = -7,    /* reserved */
   SWALE_EWEIGHT = -8      /* a linear weight d_r <= 0 (Sec. 2.2: needs the Shi-Hu-Shu split) */
 } swale_status;
@@ -49,6 +49,8 @@ typedef enum {
 #define SWALE_BIT_NEGDEPTH 2u   /* a cell-average depth below -eps_pp entered a stage (warning) */
 #define SWALE_BIT_NONFINITE 4u  /* non-finite value */
 #define SWALE_BIT_EMESH 8u      /* non-positive width */
+#define SWALE_BIT_NODT 16u      /* zero wave speed, static mesh and t_end = 0: the CFL dt is not
+                                   finite; the step took dt = 0 (the state is unchanged) */
 
 typedef enum { SWALE_BC_PERIODIC = 0, SWALE_BC_TRANSMISSIVE = 1, SWALE_BC_REFLECTIVE = 2 } swale_bc;
 

@@ -67,6 +67,7 @@ enum : uint32_t {
   ST_NEGDEPTH = 2u,    // a cell-average depth below -eps_pp entered a stage (warning)
   ST_NONFINITE = 4u,   // a non-finite value appeared
   ST_EMESH = 8u,       // a cell width became <= 0 (mesh assumption A1 violated)
+  ST_NODT = 16u,       // no finite time step: the step used dt = 0 (reading O21)
 };
 
 /* ------------------------------------------------------------------------------------ */
@@ -821,7 +822,13 @@ uint32_t ssprk3_step(const OrcParams& P, int64_t N, T* E, T* M, T* B, double* J,
   // The last step is clipped to t_end and then lands on it exactly.
   const bool clipped = P.t_end > 0.0 && P.t_end - *t <= dt;
   if (clipped && !replay) dt = P.t_end - *t;
-  if (P.mesh == 1) {
+  // alpha = 0 (a dry state at rest on a mesh that does not move) leaves the CFL condition with
+  // no bound; without an end time to clip to there is no step to take (reading O21).
+  if (!(dt < INFINITY)) {
+    dt = 0.0;
+    st |= ST_NODT;
+  }
+  if (P.mesh == 1 && dt > 0.0) {
     // Node speed (Eq. w1D): secant of the prescribed trajectory over [t_n, t_n + dt].
     const double s0 = std::sin(2.0 * M_PI * (*t) / P.mesh_T);
     const double s1 = std::sin(2.0 * M_PI * (*t + dt) / P.mesh_T);

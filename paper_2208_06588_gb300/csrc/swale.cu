@@ -507,6 +507,8 @@ swale_status set_instances(swale_ctx* ctx, const std::vector<int64_t>& off, cons
 }
 
 swale_status status_from_bits(swale_ctx* ctx, unsigned int bits) {
+  if (bits & swale::ST_NODT)
+    return fail(ctx, SWALE_ENONFINITE, "no finite time step: zero wave speed, no mesh motion and t_end = 0");
   if (bits & swale::ST_NONFINITE) return fail(ctx, SWALE_ENONFINITE, "non-finite value in a stage");
   if (bits & swale::ST_EMESH) return fail(ctx, SWALE_EMESH, "non-positive cell width");
   if (bits & swale::ST_EWEIGHT) return fail(ctx, SWALE_EWEIGHT, "non-positive linear weight");

@@ -52,6 +52,7 @@ enum : uint32_t {
   ST_NEGDEPTH = 2u,   // a cell-average depth below -eps_pp entered a stage (warning)
   ST_NONFINITE = 4u,  // a non-finite value appeared
   ST_EMESH = 8u,      // a cell width <= 0
+  ST_NODT = 16u,      // no finite time step (zero wave speed, no mesh motion, no end time): dt = 0
 };
 
 // Limited edge state of one cell (edge L = x_{j-1/2}^+, edge R = x_{j+1/2}^-).

@@ -521,13 +521,19 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
           dt = K.t_end - tn;
           clipped = 1;
         }
+        // alpha = 0 (a dry state at rest on a mesh that does not move) leaves the CFL condition
+        // with no bound; without an end time there is no step to take: dt = 0, flagged.
+        if (!(dt < INFINITY)) {
+          dt = 0.0;
+          atomicOr(&S->status, (unsigned int)swale::ST_NODT);
+        }
         S->dt = dt;
         S->alpha1 = alpha1;
         S->clipped = clipped;
         if (K.mesh == SWALE_MESH_PROFILE) {
           const double s0 = sin(kTwoPi * tn / K.mesh_T);
           const double s1 = sin(kTwoPi * (tn + dt) / K.mesh_T);
-          S->sdiff = (s1 - s0) / dt;
+          S->sdiff = dt > 0.0 ? (s1 - s0) / dt : 0.0;
         } else {
           S->sdiff = 0.0;
         }

@@ -129,6 +129,21 @@ def lake_at_rest(N=200, bottom="smooth", t_end=0.5, moving=True):
                  bc="transmissive", mesh="profile" if moving else "static", mesh_T=t_end, t_end=t_end)
 
 
+def dry_bed(N=64, t_end=0.0, mesh="static", seed=21):
+    """A dry bed at rest (h = 0, hu = 0 everywhere) over a sloping bottom with a bump, on a
+    seeded nonuniform mesh of [0, 1]; transmissive. With a static mesh every wave speed is zero,
+    so the CFL condition gives no bound on dt."""
+    rng = np.random.default_rng(seed)
+    J = rng.uniform(0.5, 1.5, N)
+    x = np.concatenate([[0.0], np.cumsum(J)])
+    x /= x[-1]
+    xc = 0.5 * (x[1:] + x[:-1])
+    b = 0.2 * xc + 0.3 * np.exp(-((xc - 0.6) / 0.1) ** 2)
+    prof = np.zeros(N + 1)
+    return Problem(name="dry_bed", x=x, h=np.zeros(N), hu=np.zeros(N), b=b, E=b.copy(), profile=prof,
+                   bc="transmissive", mesh=mesh, t_end=t_end)
+
+
 def moses_first(N=200, t_end=2.0, moving=True):
     """Sec. 5.1 Moses's first problem (Eq. flat2): [-200,400], flat bottom, h = 5, u = 0 for
     x <= 0 and h = 10, u = 40 otherwise; transmissive; CFL 0.08."""

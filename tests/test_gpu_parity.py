@@ -291,3 +291,33 @@ def test_dam_break_full_size_2000_steps_properties():
     assert abs(float(np.sum(J * g["eta"])) - m0) <= 1e-12 * m0
     assert (g["eta"] - g["b"]).min() >= -1e-10
     assert np.isfinite(g["hu"]).all() and np.abs(g["hu"]).max() > 0.1
+
+
+@pytest.mark.parametrize("mesh", ["static", "fluid_gauss"])
+def test_dry_bed_at_rest(mesh):
+    """A dry bed at rest has zero wave speed everywhere. With an end time the step is clipped to
+    it (one step, the state kept to round-off, as in the oracle); without one, on a mesh that
+    does not move, there is no finite CFL dt: the step takes dt = 0, sets SWALE_BIT_NODT and
+    swale_advance returns SWALE_ENONFINITE with the state unchanged (reading O21)."""
+    pr = W.dry_bed(t_end=0.3, mesh=mesh)
+    s = B.Solver(cfg_of(pr))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    assert s.advance(5) == 1
+    g = s.state()
+    bits = s.status()[0]
+    s.close()
+    st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+    r = oracle.run(params_of(pr), st, pr.profile, nsteps=5)
+    assert bits == 0 and r["status"] == 0 and g["t"] == st.t == 0.3
+    assert np.abs(g["eta"] - pr.E).max() <= 4e-16 and not g["hu"].any() and np.abs(g["b"] - pr.b).max() <= 4e-16
+    pr = W.dry_bed(t_end=0.0, mesh=mesh)
+    s = B.Solver(cfg_of(pr))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    with pytest.raises(B.SwaleError) as err:
+        s.advance(3)
+    assert err.value.code == -6 and "no finite time step" in str(err.value)
+    g = s.state()
+    bits, steps, last_dt = s.status()
+    s.close()
+    assert bits & B.BIT_NODT and steps == 3 and last_dt == 0.0 and g["t"] == 0.0
+    assert np.abs(g["eta"] - pr.E).max() <= 4e-16 and not g["hu"].any() and np.array_equal(g["x"], pr.x)

@@ -162,3 +162,23 @@ def test_dam_break_dry_small_stays_positive():
     assert abs(np.sum(st.J * h) - np.sum(pr.J * pr.h)) < 1e-12 * np.sum(pr.J * pr.h)
     assert st.J.min() > 0 and abs(st.J.sum() - 10.0) < 1e-11
     assert not (r["status"] & (oracle.ST_NONFINITE | oracle.ST_EMESH))
+
+
+def test_dry_bed_at_rest():
+    """A dry bed at rest stays at rest: with h = 0 every flux and the source vanish. With an end
+    time the CFL dt (unbounded, zero wave speed) is clipped to it and one step lands on t_end;
+    without one there is no finite dt, and the step takes dt = 0 and reports the status bit 16
+    (reading O21)."""
+    def at_rest(st, pr):  # to round-off: the RK combination divides J q by J
+        assert np.abs(st.E - pr.E).max() <= 4e-16 and np.abs(st.B - pr.b).max() <= 4e-16
+        assert not st.M.any() and np.array_equal(st.x, pr.x)
+
+    pr = W.dry_bed(t_end=0.3)
+    st, r = _run(pr, nsteps=5)
+    assert r["steps"] == 1 and r["status"] == 0 and st.t == 0.3
+    at_rest(st, pr)
+    for mesh in ("static", "fluid_gauss"):
+        pr = W.dry_bed(t_end=0.0, mesh=mesh)
+        st, r = _run(pr, nsteps=3)
+        assert r["steps"] == 3 and r["status"] == 16 and st.t == 0.0
+        at_rest(st, pr)
