@@ -242,9 +242,7 @@ def bench_batched(args, stream, dev, rank=0, ws=1):
     cfg = B.make_config(g=bt.g, eps_weno=bt.eps_weno, mesh_T=bt.mesh_T, bc=bt.bc, mesh=bt.mesh, cfl=0.6)
     s = B.Solver(cfg, stream.cuda_stream)
     s.set_batch(bt)
-    cache = os.path.join(os.path.expanduser("~"), ".cache", "swale_autotune.jsonl")
-    os.makedirs(os.path.dirname(cache), exist_ok=True)
-    tiles = B.swale_autotune(s.ctx, 3, cache)
+    tiles = B.swale_autotune(s.ctx, 3, autotune_cache())
     B.swale_enqueue(s.ctx, 3)
     stream.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -306,6 +304,12 @@ def bench_batched(args, stream, dev, rank=0, ws=1):
                                    "per_instance_loop": nsub * ksub / (ms_l * 1e-3),
                                    "speedup": ms_l / ms_b}
     return out
+
+
+def autotune_cache():
+    cache = os.path.join(os.path.expanduser("~"), ".cache", "swale_autotune.jsonl")
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    return cache
 
 
 def _events():
@@ -559,6 +563,9 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     ctx = B.swale_create(config_of(pr), stream.cuda_stream)
     B.swale_set_problem(ctx, N, pr.x, pr.E, pr.hu, pr.b, None, 1)
+    # Tile sizes from the library's autotuner (cached per device and problem shape; the state is
+    # restored after the trial steps).
+    tiles = B.swale_autotune(ctx, 3, autotune_cache())
 
     def barrier():
         if ws > 1:
@@ -605,6 +612,7 @@ def main():
     t0 = time.perf_counter()
     ctx2 = B.swale_create(config_of(pr), stream.cuda_stream)
     B.swale_set_problem(ctx2, N, pin["x"], pin["E"], pin["hu"], pin["b"], None, 1)
+    B.swale_set_tiles(ctx2, *tiles)
     B.swale_advance(ctx2, args.steps)
     B.swale_get_state(ctx2, None, outs["hu"], outs["b"], outs["eta"], outs["x"], outs["t"])
     e2e_s = time.perf_counter() - t0
@@ -617,7 +625,8 @@ def main():
     d2h = sum(v.numel() * 8 for v in outs.values())
     e2e = {"value": ws * N * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
            "d2h_bytes_per_step": d2h / args.steps,
-           "call": "swale_create + swale_set_problem(host) + swale_advance(K) + swale_get_state(host) + destroy"}
+           "call": "swale_create + swale_set_problem(host) + swale_set_tiles + swale_advance(K) + "
+                   "swale_get_state(host) + destroy"}
 
     # ---- batched and adjoint sections (every rank: sharded batches, replicated single instance) ----
     batched = None
@@ -676,6 +685,7 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "cells": N, "parallelism": f"replicas x{ws}" if ws > 1 else "single",
+                      "tiles": list(tiles),
                       "l2": "working set ~230 MB per stage > 126 MB L2 (no flush needed)"},
            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
            "step_roofline": fp64_roofline(opcount_step, value, "whole step, all kernels"), "cpu_baseline": cpu,
