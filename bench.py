@@ -32,11 +32,11 @@ UNIT = "cell-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
 # DRAM bytes (read + write) of a k_recon launch on this workload, averaged over the three
 # stages, from one ncu capture of the current kernels: stage 1 reads the cached mesh geometry
-# (226.6 + 61.1 MB), stage 2 writes it (33.6 + 229.7 MB), stage 3 does neither (33.7 + 23.2 MB).
-RECON_DRAM_BYTES = (226_557_440 + 61_075_712 + 33_612_800 + 229_669_376 + 33_677_056 + 23_249_664) // 3
+# (226.6 + 60.6 MB), stage 2 writes it (33.6 + 229.5 MB), stage 3 does neither (33.6 + 23.2 MB).
+RECON_DRAM_BYTES = (226_556_416 + 60_637_440 + 33_626_880 + 229_471_232 + 33_611_008 + 23_211_520) // 3
 # Fraction of cycles the FP64 pipe was busy during the same k_recon launches (ncu
-# sm__pipe_fp64_cycles_active, stages 1 and 2): the kernel is bound by FP64 instruction issue.
-RECON_FP64_PIPE_ACTIVE = (0.863 + 0.871) / 2
+# sm__pipe_fp64_cycles_active, the three stages): the kernel is bound by FP64 instruction issue.
+RECON_FP64_PIPE_ACTIVE = (0.8555 + 0.8711 + 0.8779) / 3
 
 
 def parse():
