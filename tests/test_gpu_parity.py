@@ -321,3 +321,37 @@ def test_dry_bed_at_rest(mesh):
     s.close()
     assert bits & B.BIT_NODT and steps == 3 and last_dt == 0.0 and g["t"] == 0.0
     assert np.abs(g["eta"] - pr.E).max() <= 4e-16 and not g["hu"].any() and np.array_equal(g["x"], pr.x)
+
+
+@pytest.mark.parametrize("mesh", ["profile", "fluid_gauss"])
+def test_constant_state_kept_under_mesh_motion(mesh):
+    """Sec. 2.3 (D-GCL) on the GPU: a constant state (eta = 3, hu = 1.5) on a flat bottom stays
+    constant to round-off while the mesh moves: the periodic prescribed motion (to t = 0.3), and
+    the fluid-driven motion on a transmissive domain, which moves the interior nodes with the
+    flow while the two end nodes stay (to t = 0.004: the end cells lose 40 % of their width)."""
+    t_end = 0.3 if mesh == "profile" else 0.004
+    pr = W.smooth_periodic(200, t_end=t_end)
+    N = pr.N
+    s = B.Solver(cfg_of(pr, mesh=mesh, bc="periodic" if mesh == "profile" else "transmissive"))
+    s.set_problem(pr.x, np.full(N, 3.0), np.full(N, 1.5), np.zeros(N), pr.profile, q0_is_eta=True)
+    done = s.advance(10 ** 6)
+    g = s.state()
+    bits = s.status()[0]
+    s.close()
+    assert done > 10 and bits == 0 and abs(g["t"] - t_end) < 1e-14
+    assert np.abs(g["eta"] - 3.0).max() < 1e-13 and np.abs(g["hu"] - 1.5).max() < 1e-12
+    assert np.abs(np.diff(g["x"]) - pr.J).max() > 1e-3  # the mesh did move
+
+
+def test_mass_conserved_periodic_gpu():
+    """Conservation of the finite-volume update on the GPU: on the periodic moving mesh the total
+    water sum_j J_j h_j stays at its initial value to round-off over a full run."""
+    pr = W.smooth_periodic(211, t_end=0.25)
+    s = B.Solver(cfg_of(pr))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    m0 = float(np.sum(pr.J * (pr.E - pr.b)))
+    done = s.advance(10 ** 6)
+    g = s.state()
+    s.close()
+    m1 = float(np.sum(np.diff(g["x"]) * g["h"]))
+    assert done > 50 and abs(m1 - m0) <= 1e-13 * m0
