@@ -157,11 +157,11 @@ def batch_step_flops(bt, n_inst=16):
     return tot / cells
 
 
-def adjoint_step_flops(pr):
+def adjoint_step_flops(pr, tape=False):
     from paper_2208_06588_gb300 import opcount
     c = opcount.count_stage(pr.E, pr.hu, pr.b, pr.J, bc=pr.bc, sample=1 << 13)
     r = opcount.count_reverse(pr.E, pr.hu, pr.b, pr.J, bc=pr.bc, sample=1 << 13)
-    return opcount.adjoint_step_flops(c, r)
+    return opcount.adjoint_step_flops(c, r, runs=2 if tape else 3)
 
 
 def cpu_oracle_rate(n_cells, steps):
@@ -358,8 +358,20 @@ def bench_adjoint(args, stream, dev=None, ws=1):
     ms = shard.max_over_ranks(_timed(stream, lambda: B.swale_adjoint(s.ctx, K, C, G, gp.gauges, obs, J, gE, gM, gB)),
                               dev)
     bits = s.status()[0]
+    # The same gradient with the tape (swale_set_adjoint_tape): every step run twice, not three
+    # times, for about 39 doubles per cell and step of two segments.
+    B.swale_set_adjoint_tape(s.ctx, 1)
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    Jt, gEt = np.zeros(1), np.zeros(N)
+    ms_t = shard.max_over_ranks(_timed(stream, lambda: B.swale_adjoint(s.ctx, K, C, G, gp.gauges, obs, Jt, gEt, None,
+                                                                       None)), dev)
     s.close()
     adj_bytes = B.swale_adjoint_bytes(1, N, K, C, G)
+    tape = {"ms_per_gradient": ms_t, "value": ws * N * K / (ms_t * 1e-3), "ckpt_every": C,
+            "adjoint_scratch_bytes": int(B.swale_adjoint_bytes(1, N, K, C, G, tape=1)),
+            "grad_eta_rel_diff": float(np.abs(gEt - gE).max() / np.abs(gE).max()),
+            "roofline": fp64_roofline(adjoint_step_flops(pr, tape=True), ws * N * K / (ms_t * 1e-3),
+                                      "whole gradient: 2 forward steps + reverse sweep per step")}
     return {"workload": f"gaussian_basin N={N} [0,1] reflective, 4 Gaussian bumps, eta0 from 32 Gaussian basis "
                         f"functions, sine mesh motion A=0.02, fixed dt; {K} SSP-RK3 steps; 16 gauges",
             "metric": "cell-updates/s FP64 (forward + adjoint)", "unit": UNIT,
@@ -369,7 +381,8 @@ def bench_adjoint(args, stream, dev=None, ws=1):
             "forward_only_value": N * K / (ms_fwd * 1e-3),
             "peak_device_bytes": int(state_bytes + adj_bytes), "adjoint_scratch_bytes": int(adj_bytes),
             "J": float(J[0]), "grad_norms": [float(np.linalg.norm(v)) for v in (gE, gM, gB)], "status_bits": bits,
-            "call": "swale_adjoint (host gauges, observations and gradients)",
+            "call": "swale_adjoint (host gauges, observations and gradients)", "mode": "recompute inside each step",
+            "tape_mode": tape,
             "roofline": fp64_roofline(adjoint_step_flops(pr), ws * N * K / (ms * 1e-3),
                                       "whole gradient: 3 forward steps + reverse sweep per step")}
 
@@ -410,6 +423,28 @@ def bench_batched_adjoint(args, stream, dev=None, rank=0, ws=1):
     ms = shard.max_over_ranks(_timed(stream, lambda: B.swale_adjoint(s.ctx, K, C, G, gb.gauges, obs, J, gE, gM, gB)),
                               dev)
     bits = s.status()[0]
+    # With the tape (swale_set_adjoint_tape): the checkpoint interval that needs the least memory
+    # for the full 2000 steps, if that fits in 80 % of the free HBM.
+    tape = None
+    free_now = torch.cuda.mem_get_info()[0]
+    cands = sorted((B.swale_adjoint_bytes(bt.B, Nt, 2000, c, G, tape=1), c) for c in (8, 16, 32, 64))
+    if cands[0][0] <= 0.8 * free_now:
+        Ct = cands[0][1]
+        B.swale_set_adjoint_tape(s.ctx, 1)
+        s.set_batch(bt)
+        shard.barrier()
+        try:
+            ms_t = shard.max_over_ranks(_timed(stream, lambda: B.swale_adjoint(s.ctx, K, Ct, G, gb.gauges, obs, J, gE,
+                                                                               gM, gB)), dev)
+            tape = {"ms": ms_t, "value": Nt_all * K / (ms_t * 1e-3), "gradients_per_s": B_all * 1e3 / ms_t,
+                    "ckpt_every": Ct, "adjoint_over_forward": ms_t / ms_fwd,
+                    "peak_device_bytes": int(state_bytes + B.swale_adjoint_bytes(bt.B, Nt, K, Ct, G, tape=1)),
+                    "peak_device_bytes_2000_steps": int(state_bytes + cands[0][0]),
+                    "roofline": fp64_roofline(adjoint_step_flops(bt.instance(0), tape=True), Nt_all * K / (ms_t * 1e-3),
+                                              "whole gradient: 2 forward steps + reverse sweep per step")}
+        except B.SwaleError as err:
+            tape = {"unavailable": str(err)}
+        B.swale_set_adjoint_tape(s.ctx, 0)
     s.close()
     adj_bytes = B.swale_adjoint_bytes(bt.B, Nt, K, C, G)
     full_bytes = B.swale_adjoint_bytes(bt.B, Nt, 2000, C, G)
@@ -423,7 +458,8 @@ def bench_batched_adjoint(args, stream, dev=None, rank=0, ws=1):
            "peak_device_bytes": int(state_bytes + adj_bytes), "peak_device_bytes_2000_steps": int(state_bytes + full_bytes),
            "status_bits": bits,
            "roofline": fp64_roofline(adjoint_step_flops(bt.instance(0)), Nt_all * K / (ms * 1e-3),
-                                     "whole gradient: 3 forward steps + reverse sweep per step")}
+                                     "whole gradient: 3 forward steps + reverse sweep per step"),
+           "mode": "recompute inside each step", "tape_mode": tape}
     if args.no_loop_baseline:
         return out
     # One swale_adjoint per instance on a subset, same steps, against the batch of the subset.

@@ -273,12 +273,24 @@ swale_status swale_get_alpha_log(swale_ctx* ctx, double* log);
 swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, int32_t G, const double* gauges_x,
                            const double* h_obs, double* J, double* dJ_deta0, double* dJ_dhu0, double* dJ_db0);
 
-/* Device bytes swale_adjoint allocates for B instances with Ntot cells in total (host-only
- * arithmetic; needs no device). Lets a caller pick ckpt_every for the memory it has: the
- * checkpoints grow as nsteps / ckpt_every, the per-segment snapshots as ckpt_every.
- * Errors: SWALE_EINVAL (a size < 1 or a NULL bytes pointer). */
+/* Device bytes swale_adjoint allocates for B instances with Ntot cells in total, without
+ * (tape = 0) or with (tape = 1) the tape of swale_set_adjoint_tape (host-only arithmetic; needs
+ * no device). Lets a caller pick ckpt_every for the memory it has: the checkpoints grow as
+ * nsteps / ckpt_every, the per-segment snapshots (and the tape: about 39 doubles per cell and
+ * step, for two segments) as ckpt_every.
+ * Errors: SWALE_EINVAL (a size < 1, tape not 0 or 1, or a NULL bytes pointer). */
 swale_status swale_adjoint_bytes(int64_t B, int64_t Ntot, int64_t nsteps, int64_t ckpt_every, int32_t G,
-                                 uint64_t* bytes);
+                                 int32_t tape, uint64_t* bytes);
+
+/* How swale_adjoint gets each step's stage data (the edge values of the three stages, q^(1),
+ * q^(2) and their widths) for the reverse sweep. enable = 0 (the default): each step is
+ * recomputed from its snapshot before its reverse sweep, so every step is run three times.
+ * enable = 1: the recompute of a segment keeps every step's stage data (a tape of about 39
+ * doubles per cell and step, for two segments), and the reverse sweep reads it:
+ * every step is run twice. The gradient is the same up to the order of atomic additions. This
+ * is a trade of memory for arithmetic that the paper does not discuss (it has no adjoint).
+ * Errors: SWALE_EINVAL. */
+swale_status swale_set_adjoint_tape(swale_ctx* ctx, int32_t enable);
 
 /* Message of the last error of this context ("" if none). Never NULL. */
 const char* swale_last_error(const swale_ctx* ctx);

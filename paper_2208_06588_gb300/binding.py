@@ -74,7 +74,8 @@ def lib():
         L.swale_alpha_log.argtypes = [vp, i32, i64, vp]
         L.swale_get_alpha_log.argtypes = [vp, vp]
         L.swale_adjoint.argtypes = [vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
-        L.swale_adjoint_bytes.argtypes = [i64, i64, i64, i64, i32, P(ctypes.c_uint64)]
+        L.swale_adjoint_bytes.argtypes = [i64, i64, i64, i64, i32, i32, P(ctypes.c_uint64)]
+        L.swale_set_adjoint_tape.argtypes = [vp, i32]
         L.swale_set_bottom_function.argtypes = [vp, i32, i32, vp, vp]
         L.swale_save.argtypes = [vp, ctypes.c_char_p]
         L.swale_load.argtypes = [vp, ctypes.c_char_p]
@@ -193,9 +194,14 @@ def swale_adjoint(ctx, nsteps, ckpt_every, G, gauges_x, h_obs, J=None, dJ_deta0=
                                     ptr(dJ_deta0), ptr(dJ_dhu0), ptr(dJ_db0)))
 
 
-def swale_adjoint_bytes(B, Ntot, nsteps, ckpt_every, G):
+def swale_set_adjoint_tape(ctx, enable):
+    _check(ctx, lib().swale_set_adjoint_tape(ctx, int(enable)))
+
+
+def swale_adjoint_bytes(B, Ntot, nsteps, ckpt_every, G, tape=0):
     n = ctypes.c_uint64(0)
-    code = lib().swale_adjoint_bytes(int(B), int(Ntot), int(nsteps), int(ckpt_every), int(G), ctypes.byref(n))
+    code = lib().swale_adjoint_bytes(int(B), int(Ntot), int(nsteps), int(ckpt_every), int(G), int(tape),
+                                     ctypes.byref(n))
     if code != SWALE_OK:
         raise SwaleError(code, "swale_adjoint_bytes")
     return n.value

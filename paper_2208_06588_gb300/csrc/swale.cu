@@ -51,6 +51,9 @@ struct swale_ctx {
   // Epoch of the mesh geometry cache; bumped whenever the state is set or restored, so that a
   // cache entry written before is never taken for the restored state.
   uint32_t geo_epoch = 1;
+  // swale_adjoint: keep every step's stage data from the segment recompute (1) instead of
+  // recomputing each step before its reverse sweep (0).
+  int32_t adjoint_tape = 0;
 };
 
 namespace {
@@ -1177,14 +1180,20 @@ struct StateCopy {
 
 // Bytes of the device arrays swale_adjoint allocates (each dalloc adds 256 bytes of slack); the
 // list follows the allocations in swale_adjoint one for one.
-uint64_t adjoint_bytes(int64_t B, int64_t Nt, int64_t nsteps, int64_t ckpt_every, int32_t G) {
+uint64_t adjoint_bytes(int64_t B, int64_t Nt, int64_t nsteps, int64_t ckpt_every, int32_t G, int32_t tape) {
   const int64_t NN = Nt + B, NE = Nt + 2 * B;
   const int64_t C = std::min(ckpt_every, nsteps), nseg = (nsteps + C - 1) / C;
   auto a = [](uint64_t n, uint64_t size) { return n * size + 256; };
   const uint64_t copy = 4 * a(Nt, 8) + a(NN, 8) + a(B, sizeof(DevScalars));
   const uint64_t state_set = 15 * a(Nt, 8) + 2 * a(NN, 8) + 10 * a(NE, 8) + a(NE, 1) + a(B, sizeof(DevScalars));
-  return 15 * a(Nt, 8) + 8 * a(NE, 8) + 2 * state_set + 40 * a(NE, 8) + (uint64_t)(nseg + 2 * C + 3) * copy +
-         2 * a((uint64_t)B * G, 8) + a((uint64_t)nsteps * B * G, 8) + a(B, 8) + a((uint64_t)nsteps * B * 3, 8);
+  const uint64_t common = 15 * a(Nt, 8) + 8 * a(NE, 8) + state_set + 2 * a((uint64_t)B * G, 8) +
+                          a((uint64_t)nsteps * B * G, 8) + a(B, 8) + a((uint64_t)nsteps * B * 3, 8);
+  if (tape) {
+    // per step of a segment: three stage edge sets, q^(1), J^(1), q^(2), J^(2), node velocities
+    const uint64_t slot = 30 * a(NE, 8) + 8 * a(Nt, 8) + a(NN, 8);
+    return common + (uint64_t)(nseg + 2 * C + 1) * copy + (uint64_t)(2 * C) * slot;
+  }
+  return common + state_set + 40 * a(NE, 8) + (uint64_t)(nseg + 2 * C + 3) * copy;
 }
 
 }  // namespace
@@ -1226,9 +1235,17 @@ swale_status swale_get_alpha_log(swale_ctx* ctx, double* log) {
 }
 
 swale_status swale_adjoint_bytes(int64_t B, int64_t Ntot, int64_t nsteps, int64_t ckpt_every, int32_t G,
-                                 uint64_t* bytes) {
-  if (!bytes || B < 1 || Ntot < 1 || nsteps < 1 || ckpt_every < 1 || G < 1) return SWALE_EINVAL;
-  *bytes = adjoint_bytes(B, Ntot, nsteps, ckpt_every, G);
+                                 int32_t tape, uint64_t* bytes) {
+  if (!bytes || B < 1 || Ntot < 1 || nsteps < 1 || ckpt_every < 1 || G < 1 || tape < 0 || tape > 1)
+    return SWALE_EINVAL;
+  *bytes = adjoint_bytes(B, Ntot, nsteps, ckpt_every, G, tape);
+  return SWALE_OK;
+}
+
+swale_status swale_set_adjoint_tape(swale_ctx* ctx, int32_t enable) {
+  if (!ctx) return SWALE_EINVAL;
+  if (enable < 0 || enable > 1) return fail(ctx, SWALE_EINVAL, "enable must be 0 or 1");
+  ctx->adjoint_tape = enable;
   return SWALE_OK;
 }
 
@@ -1246,6 +1263,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     return fail(ctx, SWALE_EINVAL, "the adjoint differentiates the hydrostatic well-balanced scheme");
   const int64_t B = ctx->B, Nt = ctx->Ntot, NN = Nt + B, NE = Nt + 2 * B;
   const int64_t C = std::min(ckpt_every, nsteps), nseg = (nsteps + C - 1) / C;
+  const bool tape = ctx->adjoint_tape != 0;
   cudaStream_t st = ctx->stream;
   std::vector<void*> mem;
   swale_status s = SWALE_OK;
@@ -1308,16 +1326,18 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   // The step recomputes alternate between two state sets R[0] (the context's arrays) and R[1],
   // so that the recompute of step m - 1 (on st3) overlaps the reverse sweep of step m. Each set
   // keeps the edge values of stages 1 and 2 in sets of their own (stage 3 keeps the set's).
+  auto alloc_edges = [&](DevState& d) {
+    double** ed[] = {&d.eEL, &d.eER, &d.eBL, &d.eBR, &d.ehL, &d.ehR, &d.euL, &d.euR, &d.ipair, &d.itri};
+    for (double** p : ed)
+      if (!s) s = dalloc(ctx, mem, p, (size_t)NE);
+  };
   DevState R[2], Ds[2][3];
-  R[0] = base;
-  alloc_state_set(R[1]);
-  for (int k = 0; k < 2; ++k) {
-    Ds[k][0] = Ds[k][1] = Ds[k][2] = R[k];
-    for (int t = 0; t < 2 && !s; ++t) {
-      DevState& d = Ds[k][t];
-      double** ed[] = {&d.eEL, &d.eER, &d.eBL, &d.eBR, &d.ehL, &d.ehR, &d.euL, &d.euR, &d.ipair, &d.itri};
-      for (double** p : ed)
-        if (!s) s = dalloc(ctx, mem, p, (size_t)NE);
+  if (!tape) {
+    R[0] = base;
+    alloc_state_set(R[1]);
+    for (int k = 0; k < 2; ++k) {
+      Ds[k][0] = Ds[k][1] = Ds[k][2] = R[k];
+      for (int t = 0; t < 2; ++t) alloc_edges(Ds[k][t]);
     }
   }
   // Segment recomputes: a third state set D2 recomputes segment sg - 1 into one of two
@@ -1329,9 +1349,34 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   for (auto& c : ckpt) alloc_copy(c);
   for (auto& c : seg) alloc_copy(c);
   for (auto& c : seg2) alloc_copy(c);
+  // Tape mode: the segment recompute keeps every step's stage data in a slot of its own (two
+  // segments' worth, like the snapshots): the edge values of the three stages, q^(1), J^(1),
+  // q^(2), J^(2) and the node velocities; the reverse sweep reads them instead of recomputing.
+  // slot[b][i][t] is state set D2 with stage t's edge arrays and the stage arrays of step i of
+  // buffer b.
+  std::vector<DevState> slot[2];
+  if (tape) {
+    for (int b = 0; b < 2; ++b) {
+      slot[b].resize((size_t)(3 * C));
+      for (int64_t i = 0; i < C; ++i) {
+        DevState base_i = D2;
+        double** st_arr[] = {&base_i.Ea, &base_i.Ma, &base_i.Ba, &base_i.J1,
+                             &base_i.Eb, &base_i.Mb, &base_i.Bb, &base_i.J2};
+        for (double** p : st_arr)
+          if (!s) s = dalloc(ctx, mem, p, (size_t)Nt);
+        if (!s) s = dalloc(ctx, mem, &base_i.w, (size_t)NN);
+        for (int t = 0; t < 3; ++t) {
+          slot[b][3 * i + t] = base_i;
+          alloc_edges(slot[b][3 * i + t]);
+        }
+      }
+    }
+  }
   alloc_copy(fin);
-  alloc_copy(snapR[0]);
-  alloc_copy(snapR[1]);
+  if (!tape) {
+    alloc_copy(snapR[0]);
+    alloc_copy(snapR[1]);
+  }
   double *gx = nullptr, *obs = nullptr, *Jacc = nullptr, *alog = nullptr;
   if (!s) s = dalloc(ctx, mem, &gx, (size_t)B * G);
   if (!s) s = dalloc(ctx, mem, &obs, (size_t)nsteps * B * G);
@@ -1362,7 +1407,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   int prio_least = 0, prio_greatest = 0;
   e = e ? e : cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   e = e ? e : cudaStreamCreateWithPriority(&st2, cudaStreamNonBlocking, prio_least);
-  e = e ? e : cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking);
+  if (!tape) e = e ? e : cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking);
   for (cudaEvent_t& x : ev) e = e ? e : cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
   if (e) return release(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
   DevState& D = ctx->D;
@@ -1458,7 +1503,13 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     e = load_into(ckpt[sg], D2, st2);
     for (int64_t m = n0; m < n1 && !s && !e; ++m) {
       e = save_from(buf[m - n0], D2, st2);
-      if (!e && m + 1 < n1) s = enqueue_step_on(ctx, D2, st2, nullptr, 0);
+      if (e) break;
+      if (tape) {  // every step, the last one of the segment included, into its slot
+        const DevState* sl = &slot[sg & 1][(size_t)(3 * (m - n0))];
+        s = enqueue_step_on(ctx, sl[2], st2, sl, 0);
+      } else if (m + 1 < n1) {
+        s = enqueue_step_on(ctx, D2, st2, nullptr, 0);
+      }
     }
     if (!s && !e) e = cudaEventRecord(ev[1 + (sg & 1)], st2);
   };
@@ -1475,8 +1526,46 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
       if (!e) recompute_segment(sg - 1);
       if (s || e) break;
     }
-    e = cudaStreamWaitEvent(st3, ev[1 + (sg & 1)], 0);
     const std::vector<StateCopy>& buf = (sg & 1) ? seg2 : seg;
+    if (tape) {
+      // Reverse sweeps from the tape: step m reads its stage data from slot m - n0 and the state
+      // after it (q^{n+1}, J^{n+1}, nodes, scalars with the step's dt and viscosities) from the
+      // next snapshot, the next segment's checkpoint or the final state.
+      e = cudaStreamWaitEvent(st, ev[1 + (sg & 1)], 0);
+      for (int64_t m = n1 - 1; m >= n0 && !s && !e; --m) {
+        const StateCopy& before = buf[m - n0];
+        const StateCopy& after = (m + 1 < n1) ? buf[m + 1 - n0] : (sg + 1 < nseg ? ckpt[sg + 1] : fin);
+        DevState X3[3];
+        for (int t = 0; t < 3; ++t) {
+          X3[t] = slot[sg & 1][(size_t)(3 * (m - n0) + t)];
+          X3[t].E0 = after.E;
+          X3[t].M0 = after.M;
+          X3[t].B0 = after.B;
+          X3[t].J0 = after.J;
+          X3[t].x = after.x;
+          X3[t].S = after.S;
+        }
+        const DevState& X = X3[2];
+        AdjState At = A;
+        At.sE = before.E;
+        At.sM = before.M;
+        At.sB = before.B;
+        At.sJ = before.J;
+        k_misfit<1><<<gg, 128, 0, st>>>(X, A, (int32_t)B, G, gx, obs + m * B * G, Jacc, gcell);
+        launch_adj_rk<3>(ctx, X, At);
+        launch_adj_stage<3>(ctx, X3[2], K, At, X.Eb, X.Mb, X.Bb, X.J2);
+        launch_adj_rk<2>(ctx, X, At);
+        launch_adj_stage<2>(ctx, X3[1], K, At, X.Ea, X.Ma, X.Ba, X.J1);
+        launch_adj_rk<1>(ctx, X, At);
+        launch_adj_stage<1>(ctx, X3[0], K, At, before.E, before.M, before.B, before.J);
+        launch_adj_rk<0>(ctx, X, At);
+        e = cudaGetLastError();
+      }
+      // The segment's snapshots and slots are free once its reverse sweep is done.
+      if (!s && !e) e = cudaEventRecord(ev[3 + (sg & 1)], st);
+      continue;
+    }
+    e = cudaStreamWaitEvent(st3, ev[1 + (sg & 1)], 0);
     for (int64_t m = n1 - 1; m >= n0 && !s && !e; --m, ++idx) {
       const int k = (int)(idx & 1);
       const DevState& X = R[k];

@@ -95,9 +95,10 @@ def forward_step_flops(c):
     return 3.0 * c["recon_flops"] - c["geom_flops"] + 3.0 * c["update_flops"]
 
 
-def adjoint_step_flops(c, r):
-    """FP64 FLOPs per cell of one step of the checkpointed adjoint: three forward steps (the
-    forward run, the segment recompute and the recompute inside the step), each computing the
-    mesh geometry in all three stages, and the reverse sweeps of the three stages with the
-    reverse RK combination. Gauge misfit terms are not counted."""
-    return 3.0 * (forward_step_flops(c) + c["geom_flops"]) + 3.0 * r["stage_rev_flops"] + RK_REV_OPS
+def adjoint_step_flops(c, r, runs=3):
+    """FP64 FLOPs per cell of one step of the checkpointed adjoint: `runs` forward steps (the
+    forward run, the segment recompute and, unless the tape keeps the stage data, the recompute
+    inside the step), each computing the mesh geometry in all three stages, and the reverse
+    sweeps of the three stages with the reverse RK combination. Gauge misfit terms are not
+    counted."""
+    return runs * (forward_step_flops(c) + c["geom_flops"]) + 3.0 * r["stage_rev_flops"] + RK_REV_OPS

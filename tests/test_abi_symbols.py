@@ -60,8 +60,14 @@ def test_adjoint_bytes_formula():
     per_cell = 8 * (5 * (-(-K // C) + 2 * C + 3) + 117) + 2
     assert per_cell * Nt <= n <= per_cell * Nt + 8 * (K * Bn * (G + 3)) + 2_000_000
     assert B.swale_adjoint_bytes(Bn, Nt, K, K, G) > B.swale_adjoint_bytes(Bn, Nt, K, 64, G)
+    # with the tape: (ceil(K/C) + 2 C + 1) state copies and 2 C tape slots of 39 doubles per cell
+    nt = B.swale_adjoint_bytes(Bn, Nt, K, C, G, tape=1)
+    per_cell_t = 8 * (5 * (-(-K // C) + 2 * C + 1) + 50 + 2 * C * 39) + 1
+    assert per_cell_t * Nt <= nt <= per_cell_t * Nt + 8 * (K * Bn * (G + 3)) + 2_000_000
     with pytest.raises(B.SwaleError):
         B.swale_adjoint_bytes(0, Nt, K, C, G)
+    with pytest.raises(B.SwaleError):
+        B.swale_adjoint_bytes(Bn, Nt, K, C, G, tape=2)
 
 
 C_CLIENT = r"""

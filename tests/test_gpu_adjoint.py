@@ -37,9 +37,10 @@ def gauge_cells(x, gx):
     return np.clip(np.searchsorted(x, gx, side="right") - 1, 0, x.size - 2)
 
 
-def gpu_adjoint(pr, gx, obs, nsteps, ckpt=8):
+def gpu_adjoint(pr, gx, obs, nsteps, ckpt=8, tape=0):
     s = B.Solver(cfg_of(pr))
     s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    B.swale_set_adjoint_tape(s.ctx, tape)
     N = pr.N
     J, gE, gM, gB = np.zeros(1), np.zeros(N), np.zeros(N), np.zeros(N)
     B.swale_adjoint(s.ctx, nsteps, ckpt, gx.size, np.ascontiguousarray(gx), np.ascontiguousarray(obs), J, gE, gM, gB)
@@ -155,7 +156,32 @@ def test_overlapped_recomputes_do_not_change_the_gradient():
             assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
 
 
-def test_batched_adjoint_equals_single_instances():
+def test_tape_gives_the_recomputed_gradient():
+    """swale_set_adjoint_tape(1): the reverse sweep reads the stage data that the segment
+    recompute kept instead of recomputing each step; the gradient must be the same (to the order
+    of atomic additions) for one segment, one-step segments and ragged ones, at a small size and
+    at 65536 cells, where the segment recomputes overlap the reverse sweep."""
+    pr, gx, rng = basin(N=300, seed=12)
+    nsteps = 21
+    obs = 0.6 + 0.05 * rng.normal(size=(nsteps, gx.size))
+    ref = gpu_adjoint(pr, gx, obs, nsteps, ckpt=5)
+    for ck in (1, 5, 8, nsteps):
+        got = gpu_adjoint(pr, gx, obs, nsteps, ckpt=ck, tape=1)
+        assert abs(got[0] - ref[0]) <= 1e-14 * ref[0]
+        for a, b in zip(got[1:], ref[1:]):
+            assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    K = 40
+    gp = W.gauge_problem(N=65536, nsteps=K, G=16)
+    ref = gpu_adjoint(gp.problem, gp.gauges, gp.h_obs, K, ckpt=16)
+    for ck in (3, 16):
+        got = gpu_adjoint(gp.problem, gp.gauges, gp.h_obs, K, ckpt=ck, tape=1)
+        assert abs(got[0] - ref[0]) <= 1e-14 * ref[0]
+        for a, b in zip(got[1:], ref[1:]):
+            assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("tape", [0, 1])
+def test_batched_adjoint_equals_single_instances(tape):
     prs = [W.gaussian_basin(N=n, seed=20 + i) for i, n in enumerate((200, 333, 256))]
     dt = min(p.dt_fixed for p in prs)
     for p in prs:
@@ -171,6 +197,7 @@ def test_batched_adjoint_equals_single_instances():
                  cfl=np.array([p.cfl for p in prs]))
     s = B.Solver(cfg_of(prs[0]))
     s.set_batch(bt)
+    B.swale_set_adjoint_tape(s.ctx, tape)
     Ntot = int(off[-1])
     J, gE, gM, gB = np.zeros(3), np.zeros(Ntot), np.zeros(Ntot), np.zeros(Ntot)
     obs_b = np.stack([np.stack([o[n] for o in obs]) for n in range(nsteps)])  # nsteps x B x G
