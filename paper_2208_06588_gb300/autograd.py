@@ -27,7 +27,7 @@ class GaugeMisfit(torch.autograd.Function):
     gradients scaled by the incoming dJ of the instance that owns each cell."""
 
     @staticmethod
-    def forward(ctx, eta0, hu0, b0, x_nodes, profile, gauges_x, h_obs, cfg, nsteps, ckpt_every, offsets, cfl):
+    def forward(ctx, eta0, hu0, b0, x_nodes, profile, gauges_x, h_obs, cfg, nsteps, ckpt_every, offsets, cfl, tape):
         dev = eta0.device
         if dev.type != "cuda":
             raise ValueError("gauge_misfit runs on CUDA tensors only")
@@ -55,6 +55,7 @@ class GaugeMisfit(torch.autograd.Function):
                 else:
                     c = None if cfl is None else np.ascontiguousarray(np.asarray(cfl, dtype=np.float64))
                     B.swale_batch_set_problem(solver.ctx, nb, off, x, E, M, Bt, prof, c, 1)
+                B.swale_set_adjoint_tape(solver.ctx, 1 if tape else 0)
                 B.swale_adjoint(solver.ctx, nsteps, ckpt_every, G, gx, obs, J, gE, gM, gB)
             finally:
                 solver.close()
@@ -66,7 +67,7 @@ class GaugeMisfit(torch.autograd.Function):
     def backward(ctx, gJ):
         gE, gM, gB = ctx.saved_tensors
         w = gJ[0] if ctx.counts is None else torch.repeat_interleave(gJ, ctx.counts)
-        return (w * gE, w * gM, w * gB) + (None,) * 9
+        return (w * gE, w * gM, w * gB) + (None,) * 10
 
 
 def ctypes_stream(dev):
@@ -75,11 +76,12 @@ def ctypes_stream(dev):
 
 
 def gauge_misfit(eta0, hu0, b0, x_nodes, profile, gauges_x, h_obs, cfg, nsteps, ckpt_every=64, offsets=None,
-                 cfl=None):
+                 cfl=None, tape=False):
     """J[B] of nsteps steps from (eta0, hu0, b0); differentiable in the three initial fields.
 
     x_nodes / profile: N+1 nodes per instance (concatenated for a batch, as in
     swale_batch_set_problem); gauges_x: B*G positions; h_obs: nsteps x B x G observed depths;
-    offsets: B+1 cell offsets of a batch (None: one instance); cfl: per-instance CFL numbers."""
+    offsets: B+1 cell offsets of a batch (None: one instance); cfl: per-instance CFL numbers;
+    tape: keep each step's stage data instead of recomputing it (swale_set_adjoint_tape)."""
     return GaugeMisfit.apply(eta0, hu0, b0, x_nodes, profile, gauges_x, h_obs, cfg, nsteps, ckpt_every, offsets,
-                             cfl)
+                             cfl, tape)

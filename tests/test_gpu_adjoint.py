@@ -228,6 +228,13 @@ def test_autograd_function_matches_the_adjoint():
     (3.0 * Jt.sum()).backward()
     for g, r in ((E.grad, gE), (M.grad, gM), (Bt.grad, gB)):
         assert np.abs(g.cpu().numpy() - 3.0 * r).max() <= 1e-12 * np.abs(3.0 * r).max()
+    # the same through the tape
+    E2 = t(pr.E).requires_grad_()
+    Jt2 = gauge_misfit(E2, t(pr.hu), t(pr.b), t(pr.x), t(pr.profile), t(gx), t(obs), cfg_of(pr), nsteps,
+                       ckpt_every=4, tape=True)
+    assert abs(Jt2.item() - J) <= 1e-14 * J
+    Jt2.sum().backward()
+    assert np.abs(E2.grad.cpu().numpy() - gE).max() <= 1e-12 * np.abs(gE).max()
 
 
 def test_autograd_batched_weights_each_instance():
