@@ -48,38 +48,63 @@ __global__ void __launch_bounds__(T) k_adj_rk(DevState D, AdjState A) {
     double* av[3] = {A.aE, A.aM, A.aB};
     double* rv[3] = {A.rE, A.rM, A.rB};
     const double J0 = A.sJ[g];
+    // All loads of the phase are issued before its first store (the arrays never alias, but
+    // the compiler cannot know), so the memory latencies overlap instead of adding up.
     if (PH == 3) {
       const double iJ3 = swale::recip(D.J0[g]);  // J^{n+1} after the recomputed step
+      double l[3];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) l[v] = lv[v][g];
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        const double Y = lv[v][g] * iJ3;
+        const double Y = l[v] * iJ3;
         pv[v][g] = (1.0 / 3.0) * J0 * Y;
         yv[v][g] = (2.0 / 3.0) * Y;
         rv[v][g] = (2.0 / 3.0) * dt * Y;
       }
     } else if (PH == 2) {
       const double iJ2 = swale::recip(D.J2[g]);
+      double y0[3], a[3], p[3];
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        const double y = yv[v][g] + av[v][g] * iJ2;
+        y0[v] = yv[v][g];
+        a[v] = av[v][g];
+        p[v] = pv[v][g];
+      }
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const double y = y0[v] + a[v] * iJ2;
         av[v][g] = 0.0;
-        pv[v][g] += 0.75 * J0 * y;
+        pv[v][g] = p[v] + 0.75 * J0 * y;
         rv[v][g] = 0.25 * dt * y;
         yv[v][g] = 0.25 * y;
       }
     } else if (PH == 1) {
       const double iJ1 = swale::recip(D.J1[g]);
+      double y0[3], a[3], p[3];
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        const double y = yv[v][g] + av[v][g] * iJ1;
+        y0[v] = yv[v][g];
+        a[v] = av[v][g];
+        p[v] = pv[v][g];
+      }
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const double y = y0[v] + a[v] * iJ1;
         av[v][g] = 0.0;
-        pv[v][g] += J0 * y;
+        pv[v][g] = p[v] + J0 * y;
         rv[v][g] = dt * y;
       }
     } else {
+      double p[3], a[3];
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        lv[v][g] = pv[v][g] + av[v][g];
+        p[v] = pv[v][g];
+        a[v] = av[v][g];
+      }
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        lv[v][g] = p[v] + a[v];
         av[v][g] = 0.0;
       }
     }
