@@ -40,7 +40,7 @@ typedef enum {
   SWALE_EMESH = -4,       /* a cell width became <= 0 (mesh assumption A1 of Sec. 2.1) */
   SWALE_ENEGDEPTH = -5,   /* reserved: negative depth is reported as a warning bit */
   SWALE_ENONFINITE = -6,  /* a non-finite value appeared, or no finite dt (SWALE_BIT_NODT) */
-  SWALE_ETIMEOUT = -7,    /* reserved */
+  SWALE_ETIMEOUT = -7,    /* a bounded device wait gave up (SWALE_BIT_TIMEOUT); the state is invalid */
   SWALE_EWEIGHT = -8      /* a linear weight d_r <= 0 (Sec. 2.2: needs the Shi-Hu-Shu split) */
 } swale_status;
 
@@ -51,6 +51,8 @@ typedef enum {
 #define SWALE_BIT_EMESH 8u      /* non-positive width */
 #define SWALE_BIT_NODT 16u      /* zero wave speed, static mesh and t_end = 0: the CFL dt is not
                                    finite; the step took dt = 0 (the state is unchanged) */
+#define SWALE_BIT_TIMEOUT 32u   /* a kernel's bounded wait for its bulk (TMA) copies gave up; the
+                                   kernel returned early and the state is not valid */
 
 typedef enum { SWALE_BC_PERIODIC = 0, SWALE_BC_TRANSMISSIVE = 1, SWALE_BC_REFLECTIVE = 2 } swale_bc;
 
@@ -131,7 +133,7 @@ swale_status swale_step(swale_ctx* ctx, double* dt_out);
 
 /* Up to max_steps steps, replayed as CUDA graphs of fixed length; stops early at t_end.
  * Synchronises at the end and reports the steps actually taken in *steps_done (may be NULL).
- * Returns SWALE_ENONFINITE / SWALE_EMESH / SWALE_EWEIGHT if the device status word has the
+ * Returns SWALE_ENONFINITE / SWALE_EMESH / SWALE_EWEIGHT / SWALE_ETIMEOUT if the device status word has the
  * matching bit (the steps were taken), else SWALE_OK. */
 swale_status swale_advance(swale_ctx* ctx, int64_t max_steps, int64_t* steps_done);
 

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libswale.so")
 SWALE_OK = 0
 STATUS_NAMES = {0: "SWALE_OK", -1: "SWALE_EINVAL", -2: "SWALE_ENOMEM", -3: "SWALE_ECUDA", -4: "SWALE_EMESH",
                 -5: "SWALE_ENEGDEPTH", -6: "SWALE_ENONFINITE", -7: "SWALE_ETIMEOUT", -8: "SWALE_EWEIGHT"}
-BIT_EWEIGHT, BIT_NEGDEPTH, BIT_NONFINITE, BIT_EMESH, BIT_NODT = 1, 2, 4, 8, 16
+BIT_EWEIGHT, BIT_NEGDEPTH, BIT_NONFINITE, BIT_EMESH, BIT_NODT, BIT_TIMEOUT = 1, 2, 4, 8, 16, 32
 BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
 MESH = {"static": 0, "profile": 1, "fluid_gauss": 2}
 SCHEME = {"hydrostatic": 0, "nonwb": 1, "special": 2}

@@ -510,6 +510,8 @@ swale_status set_instances(swale_ctx* ctx, const std::vector<int64_t>& off, cons
 }
 
 swale_status status_from_bits(swale_ctx* ctx, unsigned int bits) {
+  if (bits & swale::ST_TIMEOUT)
+    return fail(ctx, SWALE_ETIMEOUT, "a bounded wait for a bulk copy gave up; the stage was abandoned");
   if (bits & swale::ST_NODT)
     return fail(ctx, SWALE_ENONFINITE, "no finite time step: zero wave speed, no mesh motion and t_end = 0");
   if (bits & swale::ST_NONFINITE) return fail(ctx, SWALE_ENONFINITE, "non-finite value in a stage");

@@ -53,6 +53,7 @@ enum : uint32_t {
   ST_NONFINITE = 4u,  // a non-finite value appeared
   ST_EMESH = 8u,      // a cell width <= 0
   ST_NODT = 16u,      // no finite time step (zero wave speed, no mesh motion, no end time): dt = 0
+  ST_TIMEOUT = 32u,   // a bounded wait for an asynchronous copy gave up (the stage was abandoned)
 };
 
 // Limited edge state of one cell (edge L = x_{j-1/2}^+, edge R = x_{j+1/2}^-).

@@ -258,6 +258,44 @@ __device__ __forceinline__ void block_or_status(unsigned int* dst, uint32_t st) 
 }
 
 // ------------------------------------------------------------------------------------
+// Bulk (TMA) copies global -> shared, completed on an mbarrier. A copy needs 16-byte aligned
+// source and destination and a size that is a multiple of 16 bytes (callers check all three).
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+// Orders this thread's generic-proxy shared-memory accesses before later async-proxy ones.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase `parity` of bar to complete, at most kWaitTries polls (each poll itself
+// blocks for a short hardware-defined time). Returns false if it gave up.
+constexpr int kWaitTries = 1 << 20;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < kWaitTries; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// ------------------------------------------------------------------------------------
 // Per-step prologue, one thread per instance: stage maxima reset, J^{n+1} statistics become
 // those of J^n; an instance whose time reached t_end (t_end > 0) is marked done.
 // ------------------------------------------------------------------------------------
@@ -371,9 +409,17 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
   __shared__ double sJ[T + 4], sV[3][T + 4];    // cells c0-2 .. c0+T+1
   __shared__ double sIP[T + 3], sD2[3][T + 3];  // pairs starting at those cells
   __shared__ double sIT[T + 2], sD3[3][T + 2];  // triples centred at cells c0-1 .. c0+T
+  __shared__ __align__(16) double sRaw[4][T + 8];  // E, M, B, J of those cells as bulk-copied
+  __shared__ __align__(8) uint64_t sBar;           // completion of the tile's bulk copies
   __shared__ bool last;
   const int tid = threadIdx.x;
   const bool refl = (K.bc == SWALE_BC_REFLECTIVE);
+  if (tid == 0) {
+    mbar_init(&sBar);
+    fence_proxy_async();  // the initialised barrier, visible to the copy engine
+  }
+  __syncthreads();
+  uint32_t phase = 0;
   for (int t = blockIdx.x; t < D.nr; t += gridDim.x) {
     const Tile tl = D.rtiles ? D.rtiles[t] : Tile{0, t * T - 1};
     DevScalars* S = D.S + tl.inst;
@@ -386,10 +432,48 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
     const double* J = Jg + ic.coff;
     const int64_t eb = ic.coff + 2 * (int64_t)tl.inst;  // edge-array base of the instance
     __syncthreads();
+    // The stencil cells of the tile that lie in the instance, [cs, ce], arrive by four bulk
+    // copies (E, M, B, J). The copied span [ga, ge] (global element indices) is widened to
+    // 16-byte boundaries: one element before cs where needed (it exists: ga >= 1), one after ce
+    // when that element is in the arrays (the instance is not the last one, or ce < N - 1),
+    // else one fewer (that cell is loaded directly). Shared rows are shifted by `off` so that
+    // the first copied element lands on a 16-byte boundary as well. Ghost cells and anything
+    // not copied take the direct loads below.
+    const int64_t cs = c0 - 2 < 0 ? 0 : c0 - 2, ce = c0 + T + 1 < N - 1 ? c0 + T + 1 : N - 1;
+    int64_t ga = (ic.coff + cs) & ~(int64_t)1, ge = ic.coff + ce;
+    if (!(ge & 1)) ge += (ce + 1 < N || tl.inst + 1 < K.B) ? 1 : -1;
+    const int rel = (int)(ga - ic.coff - (c0 - 2));  // shared index of ga before the shift
+    const int off = 2 - (rel & 1);
+    const uint32_t bytes = ge >= ga ? (uint32_t)((ge - ga + 1) * 8) : 0u;
+    const bool bulk = bytes >= 16 && ((((uintptr_t)(Eg + ga)) | ((uintptr_t)(Mg + ga)) | ((uintptr_t)(Bg + ga)) |
+                                       ((uintptr_t)(Jg + ga))) & 15) == 0;
+    if (bulk) {
+      if (tid == 0) {
+        fence_proxy_async();  // the previous tile's reads of sRaw come before these writes
+        mbar_arrive_expect_tx(&sBar, 4 * bytes);
+        bulk_copy_g2s(&sRaw[0][rel + off], Eg + ga, bytes, &sBar);
+        bulk_copy_g2s(&sRaw[1][rel + off], Mg + ga, bytes, &sBar);
+        bulk_copy_g2s(&sRaw[2][rel + off], Bg + ga, bytes, &sBar);
+        bulk_copy_g2s(&sRaw[3][rel + off], Jg + ga, bytes, &sBar);
+      }
+      const bool done = mbar_wait_bounded(&sBar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!done)) {  // the copies did not complete: give the stage up
+        if (tid == 0) atomicOr(&S->status, (unsigned int)swale::ST_TIMEOUT);
+        return;
+      }
+    }
+    const int64_t gs = ga - ic.coff, gl = ge - ic.coff;  // copied cells (instance indices)
     for (int i = tid; i < T + 4; i += T) {
       const int64_t c = c0 - 2 + i;
       double jv = 1.0, ev = 0.0, mv = 0.0, bv = 0.0;  // filler beyond the last ghost cell
-      if (c >= -3 && c <= N + 2) {
+      if (bulk && c >= 0 && c < N && c >= gs && c <= gl) {
+        const int k = i + off;
+        ev = sRaw[0][k];
+        mv = sRaw[1][k];
+        bv = sRaw[2][k];
+        jv = sRaw[3][k];
+      } else if (c >= -3 && c <= N + 2) {
         const int64_t s = ghost(c, N, K.bc);
         jv = J[s];
         ev = E[s];
