@@ -20,7 +20,8 @@ void ct_recon_adjoint(const double* h, const double* v0, const double* D2, const
   }
   swale::EdgeAdj a{ob[0], ob[1], ob[2], ob[3], ob[4], ob[5], ob[6], ob[7]};
   double vb[3][3];
-  swale::recon_cell_rev(P, h, vv, DD, prm[4], a, vb, DDb);
+  const double it3[3] = {1.0 / (h[0] + h[1] + h[2]), 1.0 / (h[1] + h[2] + h[3]), 1.0 / (h[2] + h[3] + h[4])};
+  swale::recon_cell_rev(P, h, it3, vv, DD, prm[4], a, vb, DDb);
   for (int v = 0; v < 3; ++v) {
     for (int k = 0; k < 3; ++k) v0b[v * 3 + k] = vb[v][k];
     for (int k = 0; k < 4; ++k) D2b[v * 4 + k] = DDb.D2[v][k];

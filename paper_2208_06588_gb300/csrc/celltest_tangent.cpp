@@ -57,7 +57,8 @@ int ct_recon_tangent(const double* h, const double* v0, const double* D2, const 
   swale::EdgeState o;
   uint8_t flag;
   uint32_t st = 0;
-  swale::recon_cell(P, hh, vv, DD, D(prm[4]), o, flag, st);
+  const D it3[3] = {D(1.0 / (h[0] + h[1] + h[2])), D(1.0 / (h[1] + h[2] + h[3])), D(1.0 / (h[2] + h[3] + h[4]))};
+  swale::recon_cell(P, hh, it3, vv, DD, D(prm[4]), o, flag, st);
   const D outs[8] = {o.EL, o.ER, o.BL, o.BR, o.hL, o.hR, o.uL, o.uR};
   for (int k = 0; k < 8; ++k) {
     val[k] = outs[k].v;

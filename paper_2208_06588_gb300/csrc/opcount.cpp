@@ -110,9 +110,10 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
     uint8_t flag;
     uint32_t st = 0;
     CD etaG[2];
+    const CD it3[3] = {it[1], it[2], it[3]};  // triples starting at cells c-2, c-1, c
     if (scheme == 1) swale::recon_cell_nonwb(P, h5, v0, DD, CD(dxmax), o, flag, st);
     else if (scheme == 2) swale::recon_cell_special(P, h5, v0, DD, CD(dxmax), o, flag, st, etaG);
-    else swale::recon_cell(P, h5, v0, DD, CD(dxmax), o, flag, st);
+    else swale::recon_cell(P, h5, it3, v0, DD, CD(dxmax), o, flag, st);
     add_to(rec);
     cls[flag] += 1;
     // The mesh-only part (cell_geom), which a stage on the mesh of the previous stage 2 reuses.
@@ -121,6 +122,7 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
       swale::CellGeom Gm;
       uint32_t sg = 0;
       swale::cell_geom(h5, CD(dxmax), Gm, sg);
+      if (scheme == 0) swale::smooth_edge_coeffs(h5, it3, Gm);
     }
     geom_flops += (double)(opc::C.add + opc::C.mul + opc::C.div + opc::C.sqrt);
     // Update: one flux (the cell's right interface, with its own edges standing in for the
@@ -202,7 +204,8 @@ void opc_count_reverse(int64_t N, const double* E, const double* M, const double
     swale::EdgeState o;
     uint8_t flag;
     uint32_t st = 0;
-    swale::recon_cell(P, h5, v0, DD, CD(dxmax), o, flag, st);
+    const CD it3[3] = {it[1], it[2], it[3]};
+    swale::recon_cell(P, h5, it3, v0, DD, CD(dxmax), o, flag, st);
     // Reverse reconstruction.
     opc::C = opc::Counts();
     const CD ipc = swale::pair_recip(Jv[3], Jv[4]);
@@ -212,7 +215,7 @@ void opc_count_reverse(int64_t N, const double* E, const double* M, const double
     const swale::EdgeAdj ob = {CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0)};
     CD v0b[3][3];
     swale::StencilDD DDb;
-    swale::recon_cell_rev(P, h5, v0, DD, CD(dxmax), ob, v0b, DDb);
+    swale::recon_cell_rev(P, h5, it3, v0, DD, CD(dxmax), ob, v0b, DDb);
     for (int v = 0; v < 3; ++v) {  // the kernel's scatter through D3 = (D2' - D2) it, D2 = (v' - v) ip
       CD cv[5], d2b[4];
       for (int a = 0; a < 4; ++a) d2b[a] = DDb.D2[v][a];

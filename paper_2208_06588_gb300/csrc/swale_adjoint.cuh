@@ -163,8 +163,9 @@ SWALE_HD void source_cell_rev(real g, const real hd[5], const real bd[5], const 
 
 // Adjoint of recon_cell: from the adjoints ob of the limited edge state of cell j, the adjoints
 // of the data it read: v0b[v][a] (averages of cells j-2+a) and DDb (divided differences).
-SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
-                             real dxmax, const EdgeAdj& ob, real v0b[3][3], StencilDD& DDb) {
+//   it[3]: reciprocal sums of the triples starting at cells j-2, j-1, j (smooth-class form).
+SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real it[3], const real v0[3][3],
+                             const StencilDD& DD, real dxmax, const EdgeAdj& ob, real v0b[3][3], StencilDD& DDb) {
   // ---------------- forward recompute (as recon_cell) ----------------
   const real h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3], h4 = h[4];
   const real dx = P.beta_dx_global ? dxmax : h2;
@@ -241,17 +242,27 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real v
         for (int r = 0; r < 3; ++r) phi[ee][r] = phiN[ee][r];
     }
   }
-  real p[3][2][3], ev[3][2];
-  for (int v = 0; v < 3; ++v)
-    for (int ee = 0; ee < 2; ++ee) {
-      real s = 0.0;
-      for (int r = 0; r < 3; ++r) {
-        const int a = 2 - r;
-        p[v][ee][r] = v0[v][a] + DD.D2[v][a] * G1[ee][a] + DD.D3[v][a] * G2[ee][a];
-        s = s + phi[ee][r] * p[v][ee][r];
+  // Edge values as the forward computes them: the smooth class through the linear form
+  // v_j + sum_m K[e][m] D2[m] (linear_edge_form), the others as sum_r phi_r p_r.
+  real p[3][2][3], ev[3][2], Kf[2][4];
+  if (flag == 0) {
+    linear_edge_form(d, G1, G2, h, it, Kf);
+    for (int v = 0; v < 3; ++v)
+      for (int ee = 0; ee < 2; ++ee)
+        ev[v][ee] = v0[v][2] + Kf[ee][0] * DD.D2[v][0] + Kf[ee][1] * DD.D2[v][1] + Kf[ee][2] * DD.D2[v][2] +
+                    Kf[ee][3] * DD.D2[v][3];
+  } else {
+    for (int v = 0; v < 3; ++v)
+      for (int ee = 0; ee < 2; ++ee) {
+        real s = 0.0;
+        for (int r = 0; r < 3; ++r) {
+          const int a = 2 - r;
+          p[v][ee][r] = v0[v][a] + DD.D2[v][a] * G1[ee][a] + DD.D3[v][a] * G2[ee][a];
+          s = s + phi[ee][r] * p[v][ee][r];
+        }
+        ev[v][ee] = s;
       }
-      ev[v][ee] = s;
-    }
+  }
   const real hb0 = v0[0][2] - v0[2][2];
   const real hbar = pos0(hb0);
   const real hL0 = ev[0][0] - ev[2][0], hR0 = ev[0][1] - ev[2][1];
@@ -338,6 +349,14 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real v
     v0b[2][2] = v0b[2][2] - hbarb;
   }
   v0b[1][2] = v0b[1][2] + mbarb;
+  if (flag == 0) {  // ev[v][e] = v0[v][2] + sum_m K[e][m] D2[v][m]; K depends on the mesh only
+    for (int v = 0; v < 3; ++v)
+      for (int ee = 0; ee < 2; ++ee) {
+        v0b[v][2] = v0b[v][2] + evb[v][ee];
+        for (int m = 0; m < 4; ++m) DDb.D2[v][m] = DDb.D2[v][m] + Kf[ee][m] * evb[v][ee];
+      }
+    return;
+  }
   // Edge values: ev[v][e] = sum_r phi[e][r] p[v][e][r]
   real phib[2][3] = {{0, 0, 0}, {0, 0, 0}};
   for (int v = 0; v < 3; ++v)
@@ -350,7 +369,6 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real v
         DDb.D2[v][a] = DDb.D2[v][a] + pb * G1[ee][a];
         DDb.D3[v][a] = DDb.D3[v][a] + pb * G2[ee][a];
       }
-  if (flag == 0) return;
   // Weights: phi (transition) = Mg phiN + (1 - Mg) d, Mg = 2 tau / den - 1
   real phiNb[2][3];
   real taub = 0.0, denb = 0.0;

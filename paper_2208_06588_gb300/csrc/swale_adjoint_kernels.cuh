@@ -273,7 +273,8 @@ __global__ void __launch_bounds__(T) k_adj_recon(StepConst K, DevState D, AdjSta
     const swale::EdgeAdj ob = {A.ab[0][idx], A.ab[1][idx], A.ab[2][idx], A.ab[3][idx],
                                A.ab[4][idx], A.ab[5][idx], A.ab[6][idx], A.ab[7][idx]};
     double v0b[3][3];
-    swale::recon_cell_rev(K.sc, h, v0, DD, bitsd(S->Jmax[STAGE - 1]), ob, v0b, DDb);
+    const double it3[3] = {sIT[tid], sIT[tid + 1], sIT[tid + 2]};
+    swale::recon_cell_rev(K.sc, h, it3, v0, DD, bitsd(S->Jmax[STAGE - 1]), ob, v0b, DDb);
     // Stencil cell adjoints: cv[v][k] for cells c-2+k.
     double cv[3][5];
 #pragma unroll

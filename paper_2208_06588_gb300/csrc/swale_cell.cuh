@@ -148,8 +148,13 @@ struct StencilDD {
 struct CellGeom {
   real G1[2][3], G2[2][3], d[2][3], F[3], c3, c4;
   real iab, icb;  // 1 / ((y4 - y0)(y5 - y0)), 1 / ((y5 - y1)(y5 - y0))
+  // Edge value with the linear weights as the cell average plus a combination of the stencil's
+  // first divided differences: v(edge e) = v_j + sum_m K[e][m] D2[m] (smooth_edge_coeffs; the
+  // hydrostatic scheme only).
+  real K[2][4];
 };
-#define SWALE_GEOM_VALUES 25  // doubles in a CellGeom
+#define SWALE_GEOM_BASE 25    // doubles of a CellGeom before K (what every scheme uses)
+#define SWALE_GEOM_VALUES 33  // doubles in a CellGeom
 SWALE_HD void cell_geom(const real h[5], real dx, CellGeom& G, uint32_t& st) {
   const real h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3], h4 = h[4];
   if (!gt0(h2)) st |= ST_EMESH;
@@ -192,6 +197,42 @@ SWALE_HD void cell_geom(const real h[5], real dx, CellGeom& G, uint32_t& st) {
   G.F[2] = -(0.5 * h2 + h3);
   G.c4 = 4.0 * dx * h2;
   G.c3 = (3.0 * h2 * h2 + 36.0 * dx * dx) * dx * h2;
+  for (int e = 0; e < 2; ++e)
+    for (int m = 0; m < 4; ++m) G.K[e][m] = real(0.0);
+}
+
+// Step 4 with the linear weights d_r (the smooth class) in one linear form. With w_a = d_{2-a}
+// the weight of the sub-stencil that starts at cell a and D3[a] = (D2[a+1] - D2[a]) it[a],
+//   sum_a w_a (v0[a] + D2[a] G1[a] + D3[a] G2[a]) = sum_a w_a v0[a] + sum_m g_m D2[m],
+//   g_m = w_m G1[m] + b_{m-1} - b_m,  b_a = w_a G2[a] it[a]  (terms outside a = 0..2 absent),
+// and, as the weights sum to one and v0[2] - v0[1] = D2[1] (h1 + h2),
+// v0[2] - v0[0] = D2[1] (h1 + h2) + D2[0] (h0 + h1), sum_a w_a v0[a] = v0[2] - w_0 (h0 + h1) D2[0]
+// - (w_0 + w_1) (h1 + h2) D2[1]. So v(edge) = v_j + sum_m K[m] D2[m] with
+//   K[0] = g_0 - w_0 (h0 + h1),  K[1] = g_1 - (w_0 + w_1) (h1 + h2),  K[2] = g_2,  K[3] = g_3:
+// equal to edge_value with phi = d in exact arithmetic, exact for constant data, and four FMAs
+// per variable and edge instead of nine.
+//   h[5] the widths, it[3] the reciprocal triple sums of the triples starting at cells j-2..j.
+SWALE_HD void linear_edge_form(const real d[2][3], const real G1[2][3], const real G2[2][3], const real h[5],
+                               const real it[3], real K[2][4]) {
+  const real s01 = h[0] + h[1], s12 = h[1] + h[2];
+  for (int e = 0; e < 2; ++e) {
+    real w[3], b[3], g[4];
+    for (int a = 0; a < 3; ++a) {
+      w[a] = d[e][2 - a];
+      b[a] = w[a] * G2[e][a] * it[a];
+    }
+    g[0] = w[0] * G1[e][0] - b[0];
+    g[1] = w[1] * G1[e][1] + b[0] - b[1];
+    g[2] = w[2] * G1[e][2] + b[1] - b[2];
+    g[3] = b[2];
+    K[e][0] = g[0] - w[0] * s01;
+    K[e][1] = g[1] - (w[0] + w[1]) * s12;
+    K[e][2] = g[2];
+    K[e][3] = g[3];
+  }
+}
+SWALE_HD void smooth_edge_coeffs(const real h[5], const real it[3], CellGeom& G) {
+  linear_edge_form(G.d, G.G1, G.G2, h, it, G.K);
 }
 
 // Steps 2-3 from the indicators beta[3]: the class (smooth if gamma <= 1/2, non-smooth if
@@ -304,16 +345,26 @@ SWALE_HD void recon_cell_g(const SchemeConst& P, const CellGeom& G, const real v
   shared_beta(G, DD, beta);
   real phi[2][3];
   flag = hybrid_phi(P, beta, G.d, phi);
-  // Edge values of eta, hu, h with the shared weights (Step 4).
+  // Edge values of eta, hu, h with the shared weights (Step 4); the smooth class through the
+  // linear form of smooth_edge_coeffs.
   real ev[3][2];
-  for (int v = 0; v < 3; ++v)
-    for (int e = 0; e < 2; ++e) ev[v][e] = edge_value(G, phi, v0[v], DD.D2[v], DD.D3[v], e);
+  if (flag == 0) {
+    for (int v = 0; v < 3; ++v)
+      for (int e = 0; e < 2; ++e)
+        ev[v][e] = v0[v][2] + G.K[e][0] * DD.D2[v][0] + G.K[e][1] * DD.D2[v][1] + G.K[e][2] * DD.D2[v][2] +
+                   G.K[e][3] * DD.D2[v][3];
+  } else {
+    for (int v = 0; v < 3; ++v)
+      for (int e = 0; e < 2; ++e) ev[v][e] = edge_value(G, phi, v0[v], DD.D2[v], DD.D3[v], e);
+  }
   limit_cell(P, ev, v0[2][2], v0[1][2], o, st);
 }
-SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real v0[3][3], const StencilDD& DD,
-                         real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
+//   it[3]  reciprocal sums of the triples starting at cells j-2, j-1, j
+SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real it[3], const real v0[3][3],
+                         const StencilDD& DD, real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
   CellGeom G;
   cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
+  smooth_edge_coeffs(h, it, G);
   recon_cell_g(P, G, v0, DD, o, flag, st);
 }
 

@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevSta
 // the instance's last tile computes its dt (and the secant factor of the prescribed motion).
 // ------------------------------------------------------------------------------------
 template <int STAGE, int T, int SCHEME = 0>
-__global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
+__global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
                                              const double* __restrict__ Mg, const double* __restrict__ Bg,
                                              const double* __restrict__ Jg) {
   __shared__ double sJ[T + 4], sV[3][T + 4];    // cells c0-2 .. c0+T+1
@@ -530,16 +530,21 @@ __global__ void __launch_bounds__(T) k_recon(StepConst K, DevState D, const doub
       // same mesh (t_{n+1}), else computed; stage 2 fills the cache.
       swale::CellGeom G;
       double* gv = reinterpret_cast<double*>(&G);
+      constexpr int kGeo = SCHEME == 0 ? SWALE_GEOM_VALUES : SWALE_GEOM_BASE;  // values cached
       if (use_geo) {
 #pragma unroll
-        for (int k = 0; k < SWALE_GEOM_VALUES; ++k) gv[k] = D.geo[k * D.geo_stride + idx];
+        for (int k = 0; k < kGeo; ++k) gv[k] = D.geo[k * D.geo_stride + idx];
         if (!swale::gt0(h[2])) st |= swale::ST_EMESH;
       } else {
         swale::cell_geom(h, K.sc.beta_dx_global ? dxmax : h[2], G, st);
+        if (SCHEME == 0) {
+          const double it3[3] = {sIT[tid], sIT[tid + 1], sIT[tid + 2]};
+          swale::smooth_edge_coeffs(h, it3, G);
+        }
       }
       if (STAGE == 2 && D.geo) {
 #pragma unroll
-        for (int k = 0; k < SWALE_GEOM_VALUES; ++k) D.geo[k * D.geo_stride + idx] = gv[k];
+        for (int k = 0; k < kGeo; ++k) D.geo[k * D.geo_stride + idx] = gv[k];
       }
       EdgeState o;
       uint8_t flag;
