@@ -31,13 +31,13 @@ METRIC = "cell-updates/s FP64 (fwd, plain single instance)"
 UNIT = "cell-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
 # DRAM bytes (read + write) of a k_recon launch on this workload, averaged over the three
-# stages, from one ncu capture of the current kernels (tiles of 256 cells staged by bulk
-# copies): stage 1 reads the cached mesh geometry (226.6 + 60.7 MB), stage 2 writes it
-# (33.6 + 229.3 MB), stage 3 does neither (33.6 + 22.7 MB).
-RECON_DRAM_BYTES = (226_582_528 + 60_650_752 + 33_609_728 + 229_289_216 + 33_634_560 + 22_720_000) // 3
+# stages, from one ncu capture of the current kernels (the autotuner's 128-cell tiles, staged by
+# bulk copies): stage 1 reads the cached mesh geometry, 33 values per cell (293.7 + 65.8 MB),
+# stage 2 writes it (33.6 + 303.9 MB), stage 3 does neither (33.6 + 24.7 MB).
+RECON_DRAM_BYTES = (293_718_016 + 65_779_456 + 33_629_952 + 303_890_688 + 33_609_984 + 24_656_640) // 3
 # Fraction of cycles the FP64 pipe was busy during the same k_recon launches (ncu
 # sm__pipe_fp64_cycles_active, the three stages): the kernel is bound by FP64 instruction issue.
-RECON_FP64_PIPE_ACTIVE = (0.8251 + 0.8692 + 0.8784) / 3
+RECON_FP64_PIPE_ACTIVE = (0.7736 + 0.8652 + 0.8701) / 3
 
 
 def parse():
@@ -701,7 +701,7 @@ def main():
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": RECON_DRAM_BYTES if dom == "reconstruction" else None,
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum of k_recon, "
-                            "N = 2^20, 256-cell tiles, mean of the three stages)",
+                            "N = 2^20, 128-cell tiles, mean of the three stages)",
             "flops_per_cell": flops_cell, "cells_per_launch": N,
             "ncu_fp64_pipe_active": RECON_FP64_PIPE_ACTIVE if dom == "reconstruction" else None,
             "avg_launch_ms": ms_dom / n_dom,
