@@ -37,6 +37,29 @@ using dt::D;
 
 extern "C" {
 
+// The two forms of a smooth-class edge value for one variable on widths h[5] and averages v[5]
+// (divided differences formed from them): out = {sum over sub-stencils with the linear
+// weights at the left / right edge, cell average + linear form at the left / right edge}.
+void ct_edge_forms(const double* h, const double* v, double* out) {
+  D hh[5], D2[4], D3[3], v0[3];
+  for (int k = 0; k < 5; ++k) hh[k] = D(h[k]);
+  for (int a = 0; a < 4; ++a) D2[a] = (D(v[a + 1]) - D(v[a])) * (D(1.0) / (hh[a] + hh[a + 1]));
+  D it[3];
+  for (int a = 0; a < 3; ++a) {
+    it[a] = D(1.0) / (hh[a] + hh[a + 1] + hh[a + 2]);
+    D3[a] = (D2[a + 1] - D2[a]) * it[a];
+    v0[a] = D(v[a]);
+  }
+  swale::CellGeom G;
+  uint32_t st = 0;
+  swale::cell_geom(hh, hh[2], G, st);
+  swale::smooth_edge_coeffs(hh, it, G);
+  for (int e = 0; e < 2; ++e) {
+    out[e] = swale::edge_value(G, G.d, v0, D2, D3, e).v;
+    out[2 + e] = (v0[2] + G.K[e][0] * D2[0] + G.K[e][1] * D2[1] + G.K[e][2] * D2[2] + G.K[e][3] * D2[3]).v;
+  }
+}
+
 // in: h[5], v0[9], D2[12], D3[9]; tangents tv0[9], tD2[12], tD3[9]; prm = {g, eps, eps_pp, h_dry, dxmax}.
 // out: edge state values [8] and tangents [8] (EL, ER, BL, BR, hL, hR, uL, uR), flag.
 int ct_recon_tangent(const double* h, const double* v0, const double* D2, const double* D3, const double* tv0,
