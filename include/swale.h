@@ -294,6 +294,14 @@ swale_status swale_adjoint_bytes(int64_t B, int64_t Ntot, int64_t nsteps, int64_
  * Errors: SWALE_EINVAL. */
 swale_status swale_set_adjoint_tape(swale_ctx* ctx, int32_t enable);
 
+/* Test hook for the bounded waits of the bulk (TMA) copies that stage the reconstruction's
+ * tiles (the paper has no counterpart): the waits of the next steps give up after `tries` polls
+ * (0: the default, about a million) and expect pad_bytes more than the copies deliver, so with
+ * pad_bytes > 0 they run out. The kernel then sets SWALE_BIT_TIMEOUT and returns, the step
+ * reports SWALE_ETIMEOUT, and the context stays usable (set the problem again after resetting
+ * the hook with 0, 0). Nothing faults or hangs. Errors: SWALE_EINVAL, SWALE_ECUDA. */
+swale_status swale_set_wait_test(swale_ctx* ctx, int32_t tries, uint32_t pad_bytes);
+
 /* Message of the last error of this context ("" if none). Never NULL. */
 const char* swale_last_error(const swale_ctx* ctx);
 

@@ -76,6 +76,7 @@ def lib():
         L.swale_adjoint.argtypes = [vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
         L.swale_adjoint_bytes.argtypes = [i64, i64, i64, i64, i32, i32, P(ctypes.c_uint64)]
         L.swale_set_adjoint_tape.argtypes = [vp, i32]
+        L.swale_set_wait_test.argtypes = [vp, i32, ctypes.c_uint32]
         L.swale_set_bottom_function.argtypes = [vp, i32, i32, vp, vp]
         L.swale_save.argtypes = [vp, ctypes.c_char_p]
         L.swale_load.argtypes = [vp, ctypes.c_char_p]
@@ -192,6 +193,10 @@ def swale_get_alpha_log(ctx, log):
 def swale_adjoint(ctx, nsteps, ckpt_every, G, gauges_x, h_obs, J=None, dJ_deta0=None, dJ_dhu0=None, dJ_db0=None):
     _check(ctx, lib().swale_adjoint(ctx, int(nsteps), int(ckpt_every), int(G), ptr(gauges_x), ptr(h_obs), ptr(J),
                                     ptr(dJ_deta0), ptr(dJ_dhu0), ptr(dJ_db0)))
+
+
+def swale_set_wait_test(ctx, tries, pad_bytes):
+    _check(ctx, lib().swale_set_wait_test(ctx, int(tries), int(pad_bytes)))
 
 
 def swale_set_adjoint_tape(ctx, enable):

@@ -54,6 +54,10 @@ struct swale_ctx {
   // swale_adjoint: keep every step's stage data from the segment recompute (1) instead of
   // recomputing each step before its reverse sweep (0).
   int32_t adjoint_tape = 0;
+  // swale_set_wait_test: polls of the bulk-copy waits (0: the default) and extra bytes they
+  // expect (0).
+  int32_t wait_tries = 0;
+  uint32_t tx_pad = 0;
 };
 
 namespace {
@@ -134,6 +138,8 @@ StepConst step_const(const swale_ctx* ctx) {
   K.bot_deg = ctx->bot_deg;
   K.bot_breaks = ctx->bot_breaks;
   K.bot_coef = ctx->bot_coef;
+  K.wait_tries = ctx->wait_tries > 0 ? ctx->wait_tries : kWaitTries;
+  K.tx_pad = ctx->tx_pad;
   return K;
 }
 
@@ -1244,6 +1250,16 @@ swale_status swale_adjoint_bytes(int64_t B, int64_t Ntot, int64_t nsteps, int64_
   return SWALE_OK;
 }
 
+swale_status swale_set_wait_test(swale_ctx* ctx, int32_t tries, uint32_t pad_bytes) {
+  if (!ctx) return SWALE_EINVAL;
+  if (tries < 0) return fail(ctx, SWALE_EINVAL, "tries must be >= 0");
+  SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  drop_graph(ctx);
+  ctx->wait_tries = tries;
+  ctx->tx_pad = pad_bytes;
+  return SWALE_OK;
+}
+
 swale_status swale_set_adjoint_tape(swale_ctx* ctx, int32_t enable) {
   if (!ctx) return SWALE_EINVAL;
   if (enable < 0 || enable > 1) return fail(ctx, SWALE_EINVAL, "enable must be 0 or 1");
@@ -1722,6 +1738,8 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   K.alpha_cap = 0;
   K.alpha_base = 0;
   K.alpha_mode = 0;
+  K.wait_tries = kWaitTries;
+  K.tx_pad = 0;
   K.bot_pieces = K.bot_deg = 0;
   K.bot_breaks = K.bot_coef = nullptr;
   K.scheme = SWALE_SCHEME_HYDROSTATIC;

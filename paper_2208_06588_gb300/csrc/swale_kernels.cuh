@@ -88,6 +88,10 @@ struct StepConst {
   int32_t bot_pieces, bot_deg;
   const double* bot_breaks;  // bot_pieces + 1 breakpoints
   const double* bot_coef;    // piece p: sum_k bot_coef[p (bot_deg + 1) + k] (x - break_p)^k
+  // Bounded waits for bulk copies: polls before a wait gives up, and bytes expected beyond the
+  // copies (0; swale_set_wait_test raises it so that the waits run out, to test that path).
+  int32_t wait_tries;
+  uint32_t tx_pad;
 };
 
 // Stage viscosity of instance i in stage s of step `step` (DevScalars::step_idx): the computed
@@ -286,11 +290,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase `parity` of bar to complete, at most kWaitTries polls (each poll itself
+// Waits for the phase `parity` of bar to complete, at most `tries` polls (each poll itself
 // blocks for a short hardware-defined time). Returns false if it gave up.
 constexpr int kWaitTries = 1 << 20;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < kWaitTries; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int tries) {
+  for (int i = 0; i < tries; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -450,16 +454,17 @@ __global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, c
     if (bulk) {
       if (tid == 0) {
         fence_proxy_async();  // the previous tile's reads of sRaw come before these writes
-        mbar_arrive_expect_tx(&sBar, 4 * bytes);
+        mbar_arrive_expect_tx(&sBar, 4 * bytes + K.tx_pad);
         bulk_copy_g2s(&sRaw[0][rel + off], Eg + ga, bytes, &sBar);
         bulk_copy_g2s(&sRaw[1][rel + off], Mg + ga, bytes, &sBar);
         bulk_copy_g2s(&sRaw[2][rel + off], Bg + ga, bytes, &sBar);
         bulk_copy_g2s(&sRaw[3][rel + off], Jg + ga, bytes, &sBar);
       }
-      const bool done = mbar_wait_bounded(&sBar, phase);
+      const bool done = mbar_wait_bounded(&sBar, phase, K.wait_tries);
       phase ^= 1u;
       if (__syncthreads_or(!done)) {  // the copies did not complete: give the stage up
         if (tid == 0) atomicOr(&S->status, (unsigned int)swale::ST_TIMEOUT);
+        __nanosleep(20000);  // lets copies still in flight land before the block's shared memory goes
         return;
       }
     }

@@ -355,3 +355,31 @@ def test_mass_conserved_periodic_gpu():
     s.close()
     m1 = float(np.sum(np.diff(g["x"]) * g["h"]))
     assert done > 50 and abs(m1 - m0) <= 1e-13 * m0
+
+
+def test_bulk_copy_wait_runs_out_and_the_context_stays_usable():
+    """Failure detection without a fault: with swale_set_wait_test the reconstruction's bounded
+    waits for its bulk copies run out (they expect 16 bytes that never come, 16 polls); the
+    kernel sets SWALE_BIT_TIMEOUT and returns, swale_advance reports SWALE_ETIMEOUT, and after
+    the hook is reset the same context runs a fresh problem exactly like a new context."""
+    pr = W.smooth_periodic(1000)
+    s = B.Solver(cfg_of(pr))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    B.swale_set_wait_test(s.ctx, 16, 16)
+    with pytest.raises(B.SwaleError) as err:
+        s.advance(2)
+    assert err.value.code == -7
+    assert s.status()[0] & B.BIT_TIMEOUT
+    B.swale_set_wait_test(s.ctx, 0, 0)
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    assert s.advance(5) == 5
+    g = s.state()
+    assert s.status()[0] == 0
+    s.close()
+    r = B.Solver(cfg_of(pr))
+    r.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    r.advance(5)
+    ref = r.state()
+    r.close()
+    for k in ("eta", "hu", "b", "x"):
+        assert np.array_equal(g[k], ref[k]), k
