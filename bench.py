@@ -32,12 +32,12 @@ UNIT = "cell-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
 # DRAM bytes (read + write) of a k_recon launch on this workload, averaged over the three
 # stages, from one ncu capture of the current kernels (the autotuner's 128-cell tiles, staged by
-# bulk copies): stage 1 reads the cached mesh geometry, 33 values per cell (293.7 + 65.8 MB),
-# stage 2 writes it (33.6 + 303.9 MB), stage 3 does neither (33.6 + 24.7 MB).
-RECON_DRAM_BYTES = (293_718_016 + 65_779_456 + 33_629_952 + 303_890_688 + 33_609_984 + 24_656_640) // 3
+# bulk copies): stage 1 reads the cached mesh geometry, 33 values per cell (293.7 + 65.7 MB),
+# stage 2 writes it (33.6 + 304.2 MB), stage 3 does neither (33.6 + 24.4 MB).
+RECON_DRAM_BYTES = (293_681_920 + 65_746_176 + 33_622_016 + 304_172_032 + 33_615_104 + 24_387_840) // 3
 # Fraction of cycles the FP64 pipe was busy during the same k_recon launches (ncu
 # sm__pipe_fp64_cycles_active, the three stages): the kernel is bound by FP64 instruction issue.
-RECON_FP64_PIPE_ACTIVE = (0.7736 + 0.8652 + 0.8701) / 3
+RECON_FP64_PIPE_ACTIVE = (0.7768 + 0.8648 + 0.8703) / 3
 
 
 def parse():
