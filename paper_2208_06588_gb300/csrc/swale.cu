@@ -216,7 +216,7 @@ swale_status alloc_state(swale_ctx* ctx, int64_t B, int64_t Ntot, DevState& D) {
     if (swale_status s = dalloc(ctx, ctx->allocs, &D.eG1, ne)) return s;
     if (swale_status s = dalloc(ctx, ctx->allocs, &D.eG2, ne)) return s;
   }
-  if (swale_status s = dalloc(ctx, ctx->allocs, &D.geo, (size_t)SWALE_GEOM_VALUES * ne)) return s;
+  if (swale_status s = dalloc(ctx, ctx->allocs, &D.geo, (size_t)SWALE_GEO_ARRAYS * ne)) return s;
   D.geo_stride = (int64_t)ne;
   if (swale_status s = dalloc(ctx, ctx->allocs, &D.flags, ne)) return s;
   if (swale_status s = dalloc(ctx, ctx->allocs, &D.IC, (size_t)B)) return s;

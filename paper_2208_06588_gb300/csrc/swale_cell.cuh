@@ -155,6 +155,7 @@ struct CellGeom {
 };
 #define SWALE_GEOM_BASE 25    // doubles of a CellGeom before K (what every scheme uses)
 #define SWALE_GEOM_VALUES 33  // doubles in a CellGeom
+#define SWALE_GEO_ARRAYS (SWALE_GEOM_VALUES + 6)  // cached per cell: a CellGeom and a SourceGeom
 SWALE_HD void cell_geom(const real h[5], real dx, CellGeom& G, uint32_t& st) {
   const real h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3], h4 = h[4];
   if (!gt0(h2)) st |= ST_EMESH;

@@ -25,6 +25,7 @@
 namespace swale_dev {
 
 static_assert(sizeof(swale::CellGeom) == SWALE_GEOM_VALUES * sizeof(double), "CellGeom holds SWALE_GEOM_VALUES doubles");
+static_assert(sizeof(swale::SourceGeom) == 6 * sizeof(double), "SourceGeom holds 6 doubles");
 
 using swale::EdgeState;
 using swale::SchemeConst;
@@ -682,6 +683,12 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
       dt = S->dt;
     }
     const bool fresh_w = (MODE == 0 && STAGE == 1 && K.mesh == SWALE_MESH_PROFILE);
+    // The source geometry of the cells (width ratios) is cached beside the reconstruction's
+    // mesh geometry: stage 2 stores it and the next step's stage 1, on the same mesh, reads it
+    // under the same tag.
+    const unsigned long long geo_now =
+        ((unsigned long long)K.geo_epoch << 32) | (unsigned long long)(S->step_idx & 0xffffffffLL);
+    const bool use_sgeo = STAGE == 1 && MODE == 0 && D.geo != nullptr && S->geo_tag == geo_now;
     const double sdiff = fresh_w ? S->sdiff : 0.0;
     __syncthreads();
     for (int i = tid; i <= T; i += T) {
@@ -717,7 +724,7 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
         const int64_t s = ghost(c, N, K.bc);
         const double jv = Js[s];
         sJ[i] = jv;
-        siJ[i] = swale::recip(jv);
+        if (!use_sgeo) siJ[i] = swale::recip(jv);  // only the source geometry needs it
         sH[i] = E[s] - B[s];
         sB[i] = B[s];
       }
@@ -730,8 +737,19 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
       const swale::Flux Fl = {sF[0][tid], sF[1][tid], sF[2][tid], sF[3][tid]};
       const swale::Flux Fr = {sF[0][tid + 1], sF[1][tid + 1], sF[2][tid + 1], sF[3][tid + 1]};
       const int64_t ic_e = eb + j + 1;  // edge-array index of cell j
-      const swale::SourceGeom sg = swale::source_geom(sJ[tid], sJ[tid + 1], siJ[tid], siJ[tid + 1], siJ[tid + 2],
-                                                      D.ipair[eb + j], D.ipair[eb + j + 1], D.itri[eb + j + 1]);
+      swale::SourceGeom sg;
+      double* sgv = reinterpret_cast<double*>(&sg);
+      if (use_sgeo) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sgv[k] = D.geo[(SWALE_GEOM_VALUES + k) * D.geo_stride + ic_e];
+      } else {
+        sg = swale::source_geom(sJ[tid], sJ[tid + 1], siJ[tid], siJ[tid + 1], siJ[tid + 2], D.ipair[eb + j],
+                                D.ipair[eb + j + 1], D.itri[eb + j + 1]);
+      }
+      if (STAGE == 2 && MODE == 0 && D.geo) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) D.geo[(SWALE_GEOM_VALUES + k) * D.geo_stride + ic_e] = sgv[k];
+      }
       const double hd[5] = {sH[tid], sH[tid + 1], sH[tid + 2], D.ehL[ic_e], D.ehR[ic_e]};
       const double bd[5] = {sB[tid], sB[tid + 1], sB[tid + 2], D.eBL[ic_e], D.eBR[ic_e]};
       double Sj;
