@@ -57,7 +57,8 @@ extern "C" {
 // out[5..9]: update per cell summed: one interface flux, the cell's reciprocal width, the
 // source geometry and source, the flux differences (the RK combination is added in Python);
 // out[10..14]: one interface flux alone; out[15..17]: smooth / transition / non-smooth cells;
-// out[18]: FLOPs of the mesh-only geometry (cell_geom) summed.
+// out[18]: FLOPs of the mesh-only geometry (cell_geom) summed; out[19]: FLOPs of the source
+// term's mesh-only width ratios (source_geom and the cell's reciprocal width) summed.
 void opc_count_stage(int64_t N, const double* E, const double* M, const double* B, const double* J, int32_t bc,
                      double g, double eps_weno, double eps_pp, double h_dry, double alpha, int64_t c0, int64_t c1,
                      double* out, int32_t scheme) {
@@ -67,7 +68,7 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
   for (int64_t j = 0; j < N; ++j) dxmax = J[j] > dxmax ? J[j] : dxmax;
   opc::Counts rec, upd, flux;
   long long cls[3] = {0, 0, 0};
-  double geom_flops = 0.0;
+  double geom_flops = 0.0, sgeom_flops = 0.0;
   auto add_to = [](opc::Counts& a) {
     a.add += opc::C.add; a.mul += opc::C.mul; a.div += opc::C.div; a.sqrt += opc::C.sqrt; a.cmp += opc::C.cmp;
   };
@@ -132,9 +133,11 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
         scheme != 0 ? swale::interface_flux_plain(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL,
                                                   o.uR, o.uL)
                     : swale::interface_flux(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL, o.uR, o.uL);
+    const long long f0 = opc::C.add + opc::C.mul + opc::C.div + opc::C.sqrt;
     const CD iJc = CD(1.0) / Jv[3];
     const swale::SourceGeom sg =
         swale::source_geom(Jv[2], Jv[3], CD(1.0 / Jv[2].v), iJc, CD(1.0 / Jv[4].v), ip[2], ip[3], it[2]);
+    sgeom_flops += (double)(opc::C.add + opc::C.mul + opc::C.div + opc::C.sqrt - f0);
     const CD hd[5] = {V[0][2] - V[2][2], V[0][3] - V[2][3], V[0][4] - V[2][4], o.hL, o.hR};
     const CD bd[5] = {V[2][2], V[2][3], V[2][4], o.BL, o.BR};
     CD Sj;
@@ -160,6 +163,7 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
   out[16] = (double)cls[1];
   out[17] = (double)cls[2];
   out[18] = geom_flops;
+  out[19] = sgeom_flops;
 }
 
 // Counts of the reverse sweep of one stage over cells [c0, c1) of one stage state (the same

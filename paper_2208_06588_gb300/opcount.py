@@ -52,7 +52,7 @@ def count_stage(E, M, B, J, bc="transmissive", g=9.812, eps_weno=1e-6, eps_pp=1e
     N = E.size
     n = N if sample is None else min(N, sample)
     c0 = (N - n) // 2
-    out = np.zeros(19)
+    out = np.zeros(20)
     vp = ctypes.c_void_p
     lib().opc_count_stage(ctypes.c_int64(N), vp(E.ctypes.data), vp(M.ctypes.data), vp(B.ctypes.data),
                           vp(J.ctypes.data), ctypes.c_int32(BC[bc]), ctypes.c_double(g), ctypes.c_double(eps_weno),
@@ -67,7 +67,7 @@ def count_stage(E, M, B, J, bc="transmissive", g=9.812, eps_weno=1e-6, eps_pp=1e
             "update_without_rk": dict(zip(keys, map(float, upd))),
             "one_flux": dict(zip(keys, map(float, flux))),
             "recon_flops": rf, "update_flops": uf, "stage_flops": rf + uf, "cells_counted": n,
-            "geom_flops": float(out[18] / n),
+            "geom_flops": float(out[18] / n), "source_geom_flops": float(out[19] / n),
             "classes": [int(v) for v in out[15:18]]}
 
 
@@ -89,10 +89,11 @@ def count_reverse(E, M, B, J, bc="transmissive", g=9.812, eps_weno=1e-6, eps_pp=
 
 
 def forward_step_flops(c):
-    """FP64 FLOPs per cell of one SSP-RK3 step from a count_stage result: three reconstructions,
-    less the mesh-only geometry of stage 1 (taken from the previous step's stage 2 on the same
-    mesh), and three updates. The mesh-velocity kernel is not counted."""
-    return 3.0 * c["recon_flops"] - c["geom_flops"] + 3.0 * c["update_flops"]
+    """FP64 FLOPs per cell of one SSP-RK3 step from a count_stage result: three reconstructions
+    and three updates, less the mesh-only parts that stage 1 takes from the previous step's
+    stage 2 on the same mesh (the reconstruction's geometry and the source term's width ratios).
+    The mesh-velocity kernel is not counted."""
+    return 3.0 * c["recon_flops"] - c["geom_flops"] + 3.0 * c["update_flops"] - c["source_geom_flops"]
 
 
 def adjoint_step_flops(c, r, runs=3):
@@ -101,4 +102,5 @@ def adjoint_step_flops(c, r, runs=3):
     inside the step), each computing the mesh geometry in all three stages, and the reverse
     sweeps of the three stages with the reverse RK combination. Gauge misfit terms are not
     counted."""
-    return runs * (forward_step_flops(c) + c["geom_flops"]) + 3.0 * r["stage_rev_flops"] + RK_REV_OPS
+    return runs * (forward_step_flops(c) + c["geom_flops"] + c["source_geom_flops"]) + 3.0 * r["stage_rev_flops"] + \
+        RK_REV_OPS

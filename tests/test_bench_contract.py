@@ -33,10 +33,11 @@ def test_flop_models():
     r = opcount.count_reverse(pr.E, pr.hu, pr.b, pr.J, bc=pr.bc)
     fwd = opcount.forward_step_flops(c)
     # three reconstructions (stage 1 without the mesh geometry) and three updates
-    assert fwd == 3 * c["recon_flops"] - c["geom_flops"] + 3 * c["update_flops"]
+    assert fwd == 3 * c["recon_flops"] - c["geom_flops"] + 3 * c["update_flops"] - c["source_geom_flops"]
+    assert 5 <= c["source_geom_flops"] <= 10
     assert 1000 < fwd < 1500 and 40 < c["geom_flops"] < 120
     adj = opcount.adjoint_step_flops(c, r)
-    assert adj == 3 * (fwd + c["geom_flops"]) + 3 * r["stage_rev_flops"] + opcount.RK_REV_OPS
+    assert adj == 3 * (fwd + c["geom_flops"] + c["source_geom_flops"]) + 3 * r["stage_rev_flops"] + opcount.RK_REV_OPS
     assert r["recon_rev"] > r["source_rev"] > r["flux_rev"] > 0
     roof = bench.fp64_roofline(1000.0, 1e9, "test")
     assert roof["bound"] == "alu" and abs(roof["achieved"] - 1.0) < 1e-12
