@@ -10,7 +10,10 @@ this module only builds it with g++ and marshals numpy arrays through ctypes.
 Parity pins (tests/test_oracle_*.py) tie each function to something other than itself:
 uniform-mesh textbook WENO5 values, polynomial reproduction on random meshes, exact
 integrals, the lake-at-rest identities of Sec. 4.3, mass conservation, the exact vacuum
-Riemann solution of Moses's first problem and the convergence rates of Sec. 5.1.
+Riemann solution of Moses's first problem and the convergence rates of Sec. 5.1; the
+detector and hybrid weights against the Jiang-Shu closed forms, the fluid-driven node velocity
+against a numpy convolution, and the tangent-linear model against central differences of the
+replayed forward run (tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 
@@ -68,6 +71,10 @@ def lib():
         L.orc_tangent.argtypes = [P(d), P(i32), i64, P(d), P(d), P(d), P(d), P(d), P(d), P(d), i64, P(d), P(d),
                                   P(d), P(d), P(d)]
         L.orc_tangent.restype = u32
+        L.orc_fluid_velocity.argtypes = [P(d), P(i32), i64, P(d), P(d), P(d), P(d)]
+        L.orc_fluid_velocity.restype = None
+        L.orc_run_replay.argtypes = [P(d), P(i32), i64, P(d), P(d), P(d), P(d), P(d), P(d), P(d), i64, P(d), P(d)]
+        L.orc_run_replay.restype = u32
         L.orc_weno_point.argtypes = [P(d), d, P(d), P(d), P(d)]
         L.orc_weno_point.restype = None
         L.orc_point_phi.argtypes = [P(d), P(i32), P(d), P(d), i32, P(d)]
@@ -249,3 +256,28 @@ def tangent(params: Params, state: State, profile, dts, alphas, dE, dM, dB):
                            _p(dM), _p(dB))
     state.t = t.value
     return dE, dM, dB, st
+
+
+def fluid_velocity(params: Params, E, M, B):
+    """Node velocities w[N+1] of the fluid-driven (Gaussian-filtered) mesh motion for a state."""
+    p, ip = params.arrays()
+    E, M, B = map(_f64, (E, M, B))
+    w = np.zeros(E.size + 1)
+    lib().orc_fluid_velocity(_p(p), _p(ip, ctypes.c_int32), E.size, _p(E), _p(M), _p(B), _p(w))
+    return w
+
+
+def run_replay(params: Params, state: State, profile, dts, alphas):
+    """Advance ``state`` in place by len(dts) steps with the given dt and stage alphas (replay)."""
+    p, ip = params.arrays()
+    for name in ("E", "M", "B", "J", "x"):
+        setattr(state, name, _f64(getattr(state, name)).copy())
+    N = state.E.size
+    prof = _f64(profile if profile is not None else np.zeros(N + 1))
+    dts, alphas = _f64(dts), _f64(alphas)
+    t = ctypes.c_double(state.t)
+    st = lib().orc_run_replay(_p(p), _p(ip, ctypes.c_int32), N, _p(state.E), _p(state.M), _p(state.B),
+                              _p(state.J), _p(state.x), _p(prof), ctypes.byref(t), int(dts.size), _p(dts),
+                              _p(alphas))
+    state.t = t.value
+    return st

@@ -1043,6 +1043,33 @@ uint32_t orc_run(const double* p, const int32_t* ip, int64_t N, double* E, doubl
   return st;
 }
 
+/* Node velocities of the fluid-driven motion (fluid_gauss_velocity) for the state (E, M, B):
+ * w[N+1]. */
+void orc_fluid_velocity(const double* p, const int32_t* ip, int64_t N, const double* E, const double* M,
+                        const double* B, double* w) {
+  OrcParams P = to_params(p, ip);
+  std::vector<double> wv;
+  fluid_gauss_velocity(P, N, E, M, B, wv);
+  for (int64_t k = 0; k <= N; ++k) w[k] = wv[k];
+}
+
+/* nsteps steps of the fully discrete scheme in replay mode, in place: step n uses dts[n] and
+ * the stage viscosities alphas[3n..3n+2] (as recorded by orc_run) instead of computing them.
+ * The forward map that orc_tangent differentiates; finite differences of it check the tangent.
+ * Returns the OR of all status bits. */
+uint32_t orc_run_replay(const double* p, const int32_t* ip, int64_t N, double* E, double* M, double* B, double* J,
+                        double* x, const double* prof, double* t, int64_t nsteps, const double* dts,
+                        const double* alphas) {
+  OrcParams P = to_params(p, ip);
+  uint32_t st = 0;
+  for (int64_t n = 0; n < nsteps; ++n) {
+    double dt = dts[n];
+    double al[3] = {alphas[3 * n], alphas[3 * n + 1], alphas[3 * n + 2]};
+    st |= ssprk3_step<double>(P, N, E, M, B, J, x, prof, t, &dt, nullptr, al, 1);
+  }
+  return st;
+}
+
 /* Tangent-linear model of nsteps steps in replay mode: dt and the stage alphas are the
  * recorded ones (dts, alphas from orc_run), flags and limiter branches follow the base
  * trajectory. (dE, dM, dB) is the perturbation on entry and its image on exit. The mesh

@@ -5,7 +5,8 @@
 // Replay convention: dt and the stage viscosities alpha_s are constants (recorded by the
 // forward run); the detector classes, the limiter branch, the dry-edge tests and every max/min
 // selection are those of the forward state, a tie selecting the first argument; |x| has slope
-// sign(x). The mesh (widths, node velocities) is prescribed and carries no adjoint.
+// sign(x), with slope 0 at x = 0. The mesh (widths, node velocities) is prescribed and carries
+// no adjoint.
 //
 // Each function first recomputes the forward intermediates it needs from the same inputs as
 // its forward counterpart, then runs the reverse sweep.
@@ -403,7 +404,9 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real i
     betab[r] = betab[r] - qb * q[r] * ier;
   }
   for (int r = 0; r < 3; ++r) betab[r] = betab[r] + denb * (1.0 / 3.0);
-  const real sgn = (tdiff < 0.0) ? real(-1.0) : real(1.0);
+  // d|x|/dx = sign(x) with sign(0) = 0, the convention of the tangent-linear model. (The reverse
+  // only reaches here in the transition and non-smooth classes, where tau > 0.)
+  const real sgn = (tdiff < 0.0) ? real(-1.0) : ((tdiff > 0.0) ? real(1.0) : real(0.0));
   betab[0] = betab[0] + sgn * taub;
   betab[2] = betab[2] - sgn * taub;
   for (int r = 0; r < 3; ++r) {
