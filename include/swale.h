@@ -40,7 +40,8 @@ typedef enum {
   SWALE_EMESH = -4,       /* a cell width became <= 0 (mesh assumption A1 of Sec. 2.1) */
   SWALE_ENEGDEPTH = -5,   /* reserved: negative depth is reported as a warning bit */
   SWALE_ENONFINITE = -6,  /* a non-finite value appeared, or no finite dt (SWALE_BIT_NODT) */
-  SWALE_ETIMEOUT = -7,    /* a bounded device wait gave up (SWALE_BIT_TIMEOUT); the state is invalid */
+  SWALE_ETIMEOUT = -7,    /* a bounded device wait gave up (SWALE_BIT_TIMEOUT); the step was not
+                             committed (the state is that of the last good step) */
   SWALE_EWEIGHT = -8      /* a linear weight d_r <= 0 (Sec. 2.2: needs the Shi-Hu-Shu split) */
 } swale_status;
 
@@ -50,9 +51,9 @@ typedef enum {
 #define SWALE_BIT_NONFINITE 4u  /* non-finite value */
 #define SWALE_BIT_EMESH 8u      /* non-positive width */
 #define SWALE_BIT_NODT 16u      /* zero wave speed, static mesh and t_end = 0: the CFL dt is not
-                                   finite; the step took dt = 0 (the state is unchanged) */
+                                   finite; no step is taken (the state is unchanged) */
 #define SWALE_BIT_TIMEOUT 32u   /* a kernel's bounded wait for its bulk (TMA) copies gave up; the
-                                   kernel returned early and the state is not valid */
+                                   kernel returned early and the step was not committed */
 
 typedef enum { SWALE_BC_PERIODIC = 0, SWALE_BC_TRANSMISSIVE = 1, SWALE_BC_REFLECTIVE = 2 } swale_bc;
 
@@ -60,9 +61,12 @@ typedef enum {
   SWALE_MESH_STATIC = 0,      /* w = 0 */
   SWALE_MESH_PROFILE = 1,     /* x_k(t) = x_k(0) + P_k sin(2 pi t / mesh_T); w_k is the secant
                                  speed over each step (Eq. w1D) */
-  SWALE_MESH_FLUID_GAUSS = 2  /* w_k = Gaussian-smoothed (sigma = gauss_sigma cells, +-gauss_half
+  SWALE_MESH_FLUID_GAUSS = 2, /* w_k = Gaussian-smoothed (sigma = gauss_sigma cells, +-gauss_half
                                  nodes, renormalised) mean of the adjacent cell velocities;
                                  end nodes fixed */
+  SWALE_MESH_LINEAR = 3       /* x_k(t) = x_k(0) + P_k t: constant node velocities w_k = P_k
+                                 (Eq. velocity, Eq. meshspecial of Sec. 5.1, the graded mesh of
+                                 the big-pulse example); the profile array holds the P_k */
 } swale_mesh;
 
 typedef enum {
@@ -95,6 +99,15 @@ typedef struct {
   int32_t gauss_half;  /* filter truncation half-width in nodes, <= 64 */
   int32_t beta_dx_global; /* 1: Delta x in the indicators is max_j J_j (Step 1); 0: local J_j */
   int32_t scheme;      /* swale_scheme */
+  int32_t alpha_bound; /* 0 (default): the viscosity alpha of Eq. alpha2D as written, the largest
+                          |u - w| + sqrt(g h) over the edge states, wherever the node velocities
+                          w are known when the stage runs (every stage of the static, fluid-driven
+                          and linear motions; stages 2 and 3 of the profile motion), and in stage
+                          1 of the profile motion, whose secant w depends on dt, the bound
+                          max |u| + sqrt(g h) + W with W >= max |w|; 1: that bound in every stage */
+  int32_t limit_hu;    /* 0 (default): the bound-preserving limiter scales the depth's edge values
+                          only, as Eq. modifiedhjn is written; 1: it scales the discharge's edge
+                          values about their mean with the same theta as well */
 } swale_config;
 
 /* Creates a context bound to a CUDA stream (cudaStream_t; NULL = legacy default stream).
@@ -108,8 +121,8 @@ swale_status swale_create(swale_ctx** out, const swale_config* cfg, void* cuda_s
  *   q0       N cell averages of the depth h (q0_is_eta = 0) or of the surface eta = h + b
  *            (q0_is_eta = 1; lets a lake at rest be given exactly as eta = const)
  *   hu, b    N cell averages of the discharge and of the bottom
- *   profile  N+1 node amplitudes P_k of SWALE_MESH_PROFILE motion (ignored otherwise; may be
- *            NULL then)
+ *   profile  N+1 node amplitudes P_k of SWALE_MESH_PROFILE motion, or node velocities P_k of
+ *            SWALE_MESH_LINEAR motion (ignored otherwise; may be NULL then)
  * The time is reset to 0. Errors: SWALE_EINVAL (sizes, non-finite data, negative depth,
  * non-increasing nodes), SWALE_ENOMEM, SWALE_ECUDA. */
 swale_status swale_set_problem(swale_ctx* ctx, int64_t N, const double* x_nodes, const double* q0,
@@ -127,14 +140,21 @@ swale_status swale_batch_set_problem(swale_ctx* ctx, int64_t B, const int64_t* o
                                      const double* cfl, int32_t q0_is_eta);
 
 /* One SSP-RK3 step (three fused reconstruction + update stage pairs). If dt_out is not NULL
- * the call synchronises the stream and returns the step's dt. A step at t >= t_end (t_end > 0)
- * does nothing. Errors: SWALE_EINVAL (no problem set), SWALE_ECUDA. */
+ * the call synchronises the stream and returns the step's dt. A step at t >= t_end (t_end > 0),
+ * or after an error, does nothing. Errors: SWALE_EINVAL (no problem set), SWALE_ECUDA; the
+ * status of the step itself is read with swale_get_status (or reported by swale_advance). */
 swale_status swale_step(swale_ctx* ctx, double* dt_out);
 
 /* Up to max_steps steps, replayed as CUDA graphs of fixed length; stops early at t_end.
  * Synchronises at the end and reports the steps actually taken in *steps_done (may be NULL).
- * Returns SWALE_ENONFINITE / SWALE_EMESH / SWALE_EWEIGHT / SWALE_ETIMEOUT if the device status word has the
- * matching bit (the steps were taken), else SWALE_OK. */
+ * Error contract: a step in which an error appears (a non-finite value, a non-positive width, a
+ * non-positive linear weight, no finite dt, a bounded wait that gave up) is not committed: the
+ * instance keeps the state, nodes, widths, time and step count of its last good step, and every
+ * later step is a no-op for it (in a batch the other instances go on). The call then returns
+ * SWALE_ENONFINITE / SWALE_EMESH / SWALE_EWEIGHT / SWALE_ETIMEOUT (the device status word has the
+ * matching bit), and *steps_done counts the good steps of instance 0; else SWALE_OK. The
+ * context stays usable: a new problem (swale_set_problem, swale_batch_set_problem) clears the
+ * status. */
 swale_status swale_advance(swale_ctx* ctx, int64_t max_steps, int64_t* steps_done);
 
 /* Enqueues nsteps steps on the context's stream and returns without synchronising (steps at
@@ -186,32 +206,38 @@ swale_status swale_get_status(swale_ctx* ctx, uint32_t* status_bits, int64_t* st
 
 /* One evaluation of the semi-discrete right-hand side (Eq. hydro2D with Eq. bottomrk) for
  * the given state, independent of the context's problem: E = eta, M = hu, B = b, J widths
- * (N values each), w node velocities (N+1), alpha > 0 the global viscosity (alpha <= 0:
- * alpha = max edge |u| + sqrt(g h) plus max |w|). Outputs R_E, R_M, R_B (N), the largest edge
- * wave speed *A_out, flags (N bytes, may be NULL) and the status bits (may be NULL).
+ * (N values each), w node velocities (N+1), alpha > 0 the global viscosity (alpha <= 0: alpha
+ * of Eq. alpha2D, the largest |u - w| + sqrt(g h) over the edge states; with alpha_bound = 1,
+ * the largest |u| + sqrt(g h) plus max |w|). Outputs R_E, R_M, R_B (N), the largest edge wave
+ * speed *A_out (relative to w unless alpha_bound), flags (N bytes, may be NULL) and the status
+ * bits (may be NULL).
  * Allocates and frees its own device scratch. Synchronises. */
 swale_status swale_rhs(swale_ctx* ctx, int64_t N, const double* E, const double* M, const double* B,
                        const double* J, const double* w, double alpha, double* RE, double* RM, double* RB,
                        double* A_out, uint8_t* flags, uint32_t* status_bits);
 
-/* Allocation-free variant of swale_rhs, for callers that cannot call cudaMalloc (code running
- * inside another framework's memory pool, or work recorded into a CUDA graph whose device
- * memory must not grow). The paper has no counterpart: this is a library-side addition.
- *   cfg, cuda_stream   configuration and stream (NULL = legacy default stream); no context
+/* Allocation-free variant of swale_rhs, for callers that cannot call cudaMalloc: code running
+ * inside another framework's memory pool, which owns the device memory and must see every
+ * allocation, or work whose device memory must not grow while it runs. The paper has no
+ * counterpart: this is a library-side addition.
+ *   cfg, cuda_stream   configuration (its scheme and alpha_bound are honoured) and stream
+ *                      (NULL = legacy default stream; a stream must belong to the current
+ *                      device); no context
  *   N                  number of cells, 5 <= N <= 65536 (SWALE_NOALLOC_MAX_CELLS)
  *   E, M, B, J, w      device pointers: surface, discharge, bottom, widths (N), node velocities (N+1)
  *   alpha              the global viscosity, > 0 (it is not derived here)
  *   RE, RM, RB         device pointers, N values each: the right-hand side
- *   A_out              host pointer or NULL: largest edge wave speed; when given, the call
- *                      synchronises the stream, otherwise it returns after enqueueing
+ *   A_out              host pointer or NULL: the largest edge wave speed (relative to w unless
+ *                      cfg->alpha_bound); when given, the call synchronises the stream,
+ *                      otherwise it returns after enqueueing
  *   flags              N bytes (host or device) or NULL: detector classes
- * Scratch lives in one fixed array of about 5.3 MB per device, held from library load until
+ * Scratch lives in one fixed array of about 6.3 MB per device, held from library load until
  * the process exits; the call allocates nothing and clears what it reuses. Every call shares
  * that array, so calls that overlap on the GPU (other streams, other host threads) race; run
  * them one after the other. The first call on a device looks up the array's device address;
  * make that first call before any stream capture.
  * Errors: SWALE_EINVAL (N out of range, alpha <= 0, null or host pointer where a device pointer
- * is required, bad config), SWALE_ECUDA. */
+ * is required, a stream of another device, bad config), SWALE_ECUDA. */
 #define SWALE_NOALLOC_MAX_CELLS 65536
 swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64_t N, const double* E,
                                const double* M, const double* B, const double* J, const double* w, double alpha,
@@ -295,11 +321,14 @@ swale_status swale_adjoint_bytes(int64_t B, int64_t Ntot, int64_t nsteps, int64_
 swale_status swale_set_adjoint_tape(swale_ctx* ctx, int32_t enable);
 
 /* Test hook for the bounded waits of the bulk (TMA) copies that stage the reconstruction's
- * tiles (the paper has no counterpart): the waits of the next steps give up after `tries` polls
- * (0: the default, about a million) and expect pad_bytes more than the copies deliver, so with
- * pad_bytes > 0 they run out. The kernel then sets SWALE_BIT_TIMEOUT and returns, the step
- * reports SWALE_ETIMEOUT, and the context stays usable (set the problem again after resetting
- * the hook with 0, 0). Nothing faults or hangs. Errors: SWALE_EINVAL, SWALE_ECUDA. */
+ * tiles (the paper has no counterpart). With pad_bytes > 0, each tile of the next steps, after
+ * its real copies have landed, also waits on a second barrier that expects pad_bytes which
+ * never arrive, for `tries` polls (0: the default, about a million), so that wait runs out: the
+ * kernel then sets SWALE_BIT_TIMEOUT and returns, the step is not committed and reports
+ * SWALE_ETIMEOUT, and the context stays usable (reset the hook with 0, 0; the instance keeps the
+ * state of its last good step, a new problem clears the status). A block never returns while a
+ * copy of its own may still write its shared memory. Nothing faults or hangs.
+ * Errors: SWALE_EINVAL, SWALE_ECUDA. */
 swale_status swale_set_wait_test(swale_ctx* ctx, int32_t tries, uint32_t pad_bytes);
 
 /* Message of the last error of this context ("" if none). Never NULL. */

@@ -31,7 +31,7 @@ _LIB = os.path.join(_HERE, "liborc_aleweno.so")
 ST_EWEIGHT, ST_NEGDEPTH, ST_NONFINITE, ST_EMESH = 1, 2, 4, 8
 
 BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
-MESH = {"static": 0, "profile": 1, "fluid_gauss": 2}
+MESH = {"static": 0, "profile": 1, "fluid_gauss": 2, "linear": 3}
 SCHEME = {"hydrostatic": 0, "nonwb": 1, "special": 2}
 
 
@@ -75,6 +75,8 @@ def lib():
         L.orc_fluid_velocity.restype = None
         L.orc_run_replay.argtypes = [P(d), P(i32), i64, P(d), P(d), P(d), P(d), P(d), P(d), P(d), i64, P(d), P(d)]
         L.orc_run_replay.restype = u32
+        L.orc_count_step.argtypes = [P(d), P(i32), i64, P(d), P(d), P(d), P(d), P(d), P(d), P(d)]
+        L.orc_count_step.restype = None
         L.orc_weno_point.argtypes = [P(d), d, P(d), P(d), P(d)]
         L.orc_weno_point.restype = None
         L.orc_point_phi.argtypes = [P(d), P(i32), P(d), P(d), i32, P(d)]
@@ -119,6 +121,11 @@ class Params:
     # Eq. se2D / s2D with local characteristic reconstruction and the plain LF flux; "special":
     # the well-balanced scheme with the special source term of Sec. 4.2 (Eq. special2D).
     scheme: str = "hydrostatic"
+    # 0: alpha of Eq. alpha2D as written (|u - w| + sqrt(g h)) wherever w is known; 1: the bound
+    # max |u| + sqrt(g h) + Wbar in every stage.
+    alpha_bound: int = 0
+    # 1: the limiter's theta also scales the discharge edge values (reading O6b); 0: depth only.
+    limit_hu: int = 0
 
     def arrays(self):
         p = np.array([self.g, self.cfl, self.eps_weno, self.eps_pp, self.h_dry, self.mesh_T, self.gauss_sigma,
@@ -129,7 +136,7 @@ class Params:
             lib().orc_set_bottom(cf.shape[0], cf.shape[1] - 1, _p(br), _p(np.ascontiguousarray(cf)))
             mode = 1
         ip = np.array([BC[self.bc], MESH[self.mesh], self.gauss_half, self.beta_dx_global, mode,
-                       SCHEME[self.scheme]], dtype=np.int32)
+                       SCHEME[self.scheme], self.alpha_bound, self.limit_hu], dtype=np.int32)
         return p, ip
 
 
@@ -281,3 +288,22 @@ def run_replay(params: Params, state: State, profile, dts, alphas):
                               _p(alphas))
     state.t = t.value
     return st
+
+
+def count_step(params: Params, E, M, B, J, x, profile=None):
+    """The oracle's own operation counts, per cell, of one stage's reconstruction + limiter and of
+    one whole SSP-RK3 step on the given state: {"recon": {...}, "step": {...}} with add, mul,
+    div, sqrt and flops (their sum) each. Only arithmetic on state-dependent values is counted
+    (the oracle builds the mesh-only coefficients by Gaussian elimination, not counted)."""
+    p, ip = params.arrays()
+    E, M, B, J, x = map(_f64, (E, M, B, J, x))
+    N = E.size
+    prof = _f64(profile if profile is not None else np.zeros(N + 1))
+    c = np.zeros(8)
+    lib().orc_count_step(_p(p), _p(ip, ctypes.c_int32), N, _p(E), _p(M), _p(B), _p(J), _p(x), _p(prof), _p(c))
+    out = {}
+    for k, name in enumerate(("recon", "step")):
+        v = c[4 * k:4 * k + 4] / N
+        out[name] = dict(zip(("add", "mul", "div", "sqrt"), map(float, v)))
+        out[name]["flops"] = float(v.sum())
+    return out

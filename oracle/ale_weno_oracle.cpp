@@ -43,7 +43,8 @@ struct OrcParams {
   double t_end;        // final time; the last step is clipped to it
   double dt_fixed;     // > 0: every step uses this dt instead of the CFL formula
   int32_t bc;          // 0 periodic, 1 transmissive, 2 reflective
-  int32_t mesh;        // 0 static, 1 prescribed profile motion, 2 fluid-driven Gaussian
+  int32_t mesh;        // 0 static, 1 prescribed profile motion, 2 fluid-driven Gaussian,
+                       // 3 constant node velocities x = x0 + v t (Eq. velocity / meshspecial)
   int32_t gauss_half;  // truncation half-width of the Gaussian filter (nodes)
   int32_t beta_dx_global;  // 1: Delta x in the smoothness indicators is max_j J_j (Step 1)
   // Bottom: 0 = cell averages evolved by the ALE scheme of Eq. bottomrk (the paper's default);
@@ -53,6 +54,12 @@ struct OrcParams {
   // ALE-WENO scheme (Eq. se2D / s2D): local characteristic reconstruction of (eta, hu) and the
   // plain Lax-Friedrichs flux.
   int32_t scheme;
+  // 0: alpha as Eq. alpha2D writes it, max |u - w| + sqrt(g h), wherever w is known when the
+  // stage runs; 1: the bound max |u| + sqrt(g h) + Wbar (Wbar >= max |w|) in every stage.
+  int32_t alpha_bound;
+  // 1: the limiter's theta also scales the discharge edge values about their mean (reading O6b);
+  // 0: it limits the depth only, as Eq. modifiedhjn is written.
+  int32_t limit_hu;
   int32_t bpieces, bdeg;                  // number of pieces, polynomial degree
   const double* bbreaks;                  // bpieces + 1 increasing breakpoints
   const double* bcoef;                    // piece p: sum_k bcoef[p (bdeg+1) + k] (x - bbreaks[p])^k
@@ -105,6 +112,31 @@ inline Dual vsqrt(Dual x) {
 }
 inline Dual vmax(Dual a, Dual b) { return (b.v > a.v) ? b : a; }
 inline Dual vmin(Dual a, Dual b) { return (b.v < a.v) ? b : a; }
+
+/* Operation-counting scalar: the oracle's own count of the method's floating-point work (the
+ * numerator of the roofline of the CUDA path). Every addition, subtraction, multiplication,
+ * division and square root on a state-dependent value is counted; sign flips, |x|, max / min and
+ * comparisons are not arithmetic, and mesh-only arithmetic (double) is not counted here. */
+struct OpCount {
+  long long add = 0, mul = 0, div = 0, sqrt = 0;
+};
+OpCount g_ops;
+struct Cnt {
+  double v;
+  Cnt() : v(0) {}
+  Cnt(double a) : v(a) {}
+};
+inline Cnt operator+(Cnt a, Cnt b) { ++g_ops.add; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { ++g_ops.add; return Cnt(a.v - b.v); }
+inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+inline Cnt operator*(Cnt a, Cnt b) { ++g_ops.mul; return Cnt(a.v * b.v); }
+inline Cnt operator/(Cnt a, Cnt b) { ++g_ops.div; return Cnt(a.v / b.v); }
+inline Cnt& operator+=(Cnt& a, Cnt b) { a = a + b; return a; }
+inline double value(Cnt x) { return x.v; }
+inline Cnt vabs(Cnt x) { return Cnt(std::fabs(x.v)); }
+inline Cnt vsqrt(Cnt x) { ++g_ops.sqrt; return Cnt(std::sqrt(x.v)); }
+inline Cnt vmax(Cnt a, Cnt b) { return (b.v > a.v) ? b : a; }
+inline Cnt vmin(Cnt a, Cnt b) { return (b.v < a.v) ? b : a; }
 
 inline double ipow(double x, int k) {
   double r = 1.0;
@@ -422,11 +454,12 @@ int64_t ghost_src(int64_t i, int64_t N, int bc) {
 
 /* Reconstruction (Steps 1-4 of Sec. 2.2 with the shared weights of Eq. alphamodified),
  * then the bound-preserving limiter (Eq. modifiedhjn / xd in one dimension) and the
- * bottom re-derivation of the Remark in Sec. 4.3. Returns the largest |u| + sqrt(g h)
- * over the edges that touch interfaces 0..N (the wave-speed part of alpha, Eq. alpha2D). */
+ * bottom re-derivation of the Remark in Sec. 4.3. Returns the largest |u - w| + sqrt(g h)
+ * over the edges that touch interfaces 0..N (Eq. alpha2D; an edge of cell j at node j + e
+ * moves with w[j + e]), or the largest |u| + sqrt(g h) when w is null. */
 template <class T>
 double reconstruct(const OrcParams& P, int64_t N, const T* E, const T* M, const T* B, const double* J,
-                   std::vector<EdgeVals<T>>& ed, uint32_t& status) {
+                   std::vector<EdgeVals<T>>& ed, uint32_t& status, const double* w = nullptr) {
   const int64_t G = 3;
   std::vector<T> Ex(N + 2 * G), Mx(N + 2 * G), Bx(N + 2 * G);
   std::vector<double> Jx(N + 2 * G);
@@ -552,8 +585,10 @@ double reconstruct(const OrcParams& P, int64_t N, const T* E, const T* M, const 
     // (the positivity limiter of the cited Xing-Zhang-Shu scheme acts on (h, hu) together),
     // so that u = hu / h stays bounded where h is pulled towards the floor.
     const T mbar = m5[2];
-    o.M[0] = theta * (o.M[0] - mbar) + mbar;
-    o.M[1] = theta * (o.M[1] - mbar) + mbar;
+    if (P.limit_hu) {
+      o.M[0] = theta * (o.M[0] - mbar) + mbar;
+      o.M[1] = theta * (o.M[1] - mbar) + mbar;
+    }
     // Remark of Sec. 4.3: b^new = eta - h^new; eta itself is left untouched.
     o.B[0] = o.E[0] - hL;
     o.B[1] = o.E[1] - hR;
@@ -566,7 +601,8 @@ double reconstruct(const OrcParams& P, int64_t N, const T* E, const T* M, const 
     for (int e = 0; e < 2; ++e) {
       if ((j == -1 && e == 0) || (j == N && e == 1)) continue;
       double hpos = std::max(value(o.h[e]), 0.0);
-      double s = std::fabs(value(o.u[e])) + std::sqrt(P.g * hpos);
+      const double rel = w ? value(o.u[e]) - w[j + e] : value(o.u[e]);
+      double s = std::fabs(rel) + std::sqrt(P.g * hpos);
       A = std::max(A, s);
     }
   }
@@ -796,13 +832,23 @@ uint32_t ssprk3_step(const OrcParams& P, int64_t N, T* E, T* M, T* B, double* J,
     for (int64_t k = 0; k <= N; ++k) pm = std::max(pm, std::fabs(prof[k]));
     // Secant speeds of x = xi + P sin(2 pi t / T) are bounded by (2 pi / T) max |P|.
     Wbar = 2.0 * M_PI / P.mesh_T * pm;
+  } else if (P.mesh == 3) {
+    // Constant node velocities (Eq. velocity): the mesh of Eq. meshspecial moves on straight rays.
+    for (int64_t k = 0; k <= N; ++k) {
+      w[k] = prof[k];
+      Wbar = std::max(Wbar, std::fabs(w[k]));
+    }
   }
+  // Eq. alpha2D takes the wave speeds relative to the mesh velocity. Stage 1 of the profile
+  // motion cannot: its secant w depends on dt, which depends on alpha_1; there (and on request,
+  // alpha_bound = 1) alpha is the bound max |u| + sqrt(g h) + Wbar (reading O4).
+  const bool rel1 = !P.alpha_bound && P.mesh != 1, rel = !P.alpha_bound;
 
   // Stage 1 on the mesh at t_n.
-  double A1 = reconstruct(P, N, E, M, B, J, ed, st);
+  double A1 = reconstruct(P, N, E, M, B, J, ed, st, rel1 ? w.data() : nullptr);
   if (flags)
     for (int64_t j = 0; j < N; ++j) flags[j] = ed[j + 1].flag;
-  double alpha1 = A1 + Wbar;
+  double alpha1 = rel1 ? A1 : A1 + Wbar;
   double dt;
   if (replay) {
     dt = *dt_out;
@@ -858,8 +904,8 @@ uint32_t ssprk3_step(const OrcParams& P, int64_t N, T* E, T* M, T* B, double* J,
   if (P.bottom_mode == 1)
     for (int64_t j = 0; j < N; ++j) qB[j] = T(bottom_average(P, x[j] + dt * w[j], x[j + 1] + dt * w[j + 1]));
   // Stage 2 on the mesh at t_{n,1} = t_{n+1}.
-  double A2 = reconstruct(P, N, qE.data(), qM.data(), qB.data(), J1.data(), ed, st);
-  double alpha2 = replay ? alpha_rec[1] : A2 + Wbar;
+  double A2 = reconstruct(P, N, qE.data(), qM.data(), qB.data(), J1.data(), ed, st, rel ? w.data() : nullptr);
+  double alpha2 = replay ? alpha_rec[1] : (rel ? A2 : A2 + Wbar);
   rhs(P, N, ed, qE.data(), qM.data(), qB.data(), J1.data(), w.data(), alpha2, R_E.data(), R_M.data(), R_B.data());
   for (int64_t j = 0; j < N; ++j) {
     Y2E[j] = T(0.75) * (T(J[j]) * E[j]) + T(0.25) * (Y1E[j] + T(dt) * R_E[j]);
@@ -874,8 +920,8 @@ uint32_t ssprk3_step(const OrcParams& P, int64_t N, T* E, T* M, T* B, double* J,
     for (int64_t j = 0; j < N; ++j)
       qB[j] = T(bottom_average(P, x[j] + 0.5 * dt * w[j], x[j + 1] + 0.5 * dt * w[j + 1]));
   // Stage 3 on the mesh at t_{n,2} = (t_n + t_{n+1}) / 2.
-  double A3 = reconstruct(P, N, qE.data(), qM.data(), qB.data(), J2.data(), ed, st);
-  double alpha3 = replay ? alpha_rec[2] : A3 + Wbar;
+  double A3 = reconstruct(P, N, qE.data(), qM.data(), qB.data(), J2.data(), ed, st, rel ? w.data() : nullptr);
+  double alpha3 = replay ? alpha_rec[2] : (rel ? A3 : A3 + Wbar);
   rhs(P, N, ed, qE.data(), qM.data(), qB.data(), J2.data(), w.data(), alpha3, R_E.data(), R_M.data(), R_B.data());
   for (int64_t j = 0; j < N; ++j) {
     T Y3E = T(1.0 / 3.0) * (T(J[j]) * E[j]) + T(2.0 / 3.0) * (Y2E[j] + T(dt) * R_E[j]);
@@ -907,6 +953,8 @@ OrcParams to_params(const double* p, const int32_t* ip) {
   P.bc = ip[0]; P.mesh = ip[1]; P.gauss_half = ip[2]; P.beta_dx_global = ip[3];
   P.bottom_mode = ip[4];
   P.scheme = ip[5];
+  P.alpha_bound = ip[6];
+  P.limit_hu = ip[7];
   P.bpieces = (int32_t)g_bbreaks.size() - 1;
   P.bdeg = g_bdeg;
   P.bbreaks = g_bbreaks.data();
@@ -920,7 +968,8 @@ OrcParams to_params(const double* p, const int32_t* ip) {
 /* ------------------------------------------------------------------------------------ */
 /* C entry points used by oracle/__init__.py (ctypes). Parameters are passed as a double  */
 /* array p[9] = {g, cfl, eps_weno, eps_pp, h_dry, mesh_T, gauss_sigma, t_end, dt_fixed}   */
-/* and an int array ip[4] = {bc, mesh, gauss_half, beta_dx_global}.                       */
+/* and an int array ip[8] = {bc, mesh, gauss_half, beta_dx_global, bottom_mode, scheme,    */
+/* alpha_bound, limit_hu}.                                                                */
 /* ------------------------------------------------------------------------------------ */
 extern "C" {
 
@@ -1004,17 +1053,19 @@ double orc_reconstruct(const double* p, const int32_t* ip, int64_t N, const doub
 }
 
 /* Semi-discrete right-hand side of one stage for given node velocities w[0..N] and alpha
- * (alpha <= 0: alpha = max edge wave speed + Wbar with Wbar = max |w|). */
+ * (alpha <= 0: alpha of Eq. alpha2D, the largest |u - w| + sqrt(g h) over the edges; with
+ * alpha_bound, the largest |u| + sqrt(g h) plus max |w|). *alpha_used: the alpha applied. */
 uint32_t orc_rhs(const double* p, const int32_t* ip, int64_t N, const double* E, const double* M, const double* B,
                  const double* J, const double* w, double alpha, double* RE, double* RM, double* RB,
                  double* alpha_used) {
   OrcParams P = to_params(p, ip);
   std::vector<EdgeVals<double>> ed;
   uint32_t s = 0;
-  double A = reconstruct(P, N, E, M, B, J, ed, s);
+  double A = reconstruct(P, N, E, M, B, J, ed, s, P.alpha_bound ? nullptr : w);
   if (!(alpha > 0.0)) {
     double wb = 0.0;
-    for (int64_t k = 0; k <= N; ++k) wb = std::max(wb, std::fabs(w[k]));
+    if (P.alpha_bound)
+      for (int64_t k = 0; k <= N; ++k) wb = std::max(wb, std::fabs(w[k]));
     alpha = A + wb;
   }
   rhs(P, N, ed, E, M, B, J, w, alpha, RE, RM, RB);
@@ -1068,6 +1119,33 @@ uint32_t orc_run_replay(const double* p, const int32_t* ip, int64_t N, double* E
     st |= ssprk3_step<double>(P, N, E, M, B, J, x, prof, t, &dt, nullptr, al, 1);
   }
   return st;
+}
+
+/* The oracle's operation count (Cnt) of one stage's reconstruction + limiter on the state
+ * (E, M, B, J) and of one whole SSP-RK3 step from it, summed over the N cells:
+ * counts[0..3] = reconstruction (add, mul, div, sqrt), counts[4..7] = step. The state is not
+ * changed. */
+void orc_count_step(const double* p, const int32_t* ip, int64_t N, const double* E, const double* M,
+                    const double* B, const double* J, const double* x, const double* prof, double* counts) {
+  OrcParams P = to_params(p, ip);
+  std::vector<Cnt> e(E, E + N), m(M, M + N), b(B, B + N);
+  std::vector<double> Jc(J, J + N), xc(x, x + N + 1);
+  std::vector<EdgeVals<Cnt>> ed;
+  uint32_t st = 0;
+  g_ops = OpCount();
+  reconstruct(P, N, e.data(), m.data(), b.data(), Jc.data(), ed, st);
+  const OpCount rec = g_ops;
+  g_ops = OpCount();
+  double t = 0.0, dt = 0.0, al[3];
+  ssprk3_step<Cnt>(P, N, e.data(), m.data(), b.data(), Jc.data(), xc.data(), prof, &t, &dt, nullptr, al, 0);
+  const OpCount stp = g_ops;
+  const OpCount* c[2] = {&rec, &stp};
+  for (int k = 0; k < 2; ++k) {
+    counts[4 * k + 0] = (double)c[k]->add;
+    counts[4 * k + 1] = (double)c[k]->mul;
+    counts[4 * k + 2] = (double)c[k]->div;
+    counts[4 * k + 3] = (double)c[k]->sqrt;
+  }
 }
 
 /* Tangent-linear model of nsteps steps in replay mode: dt and the stage alphas are the

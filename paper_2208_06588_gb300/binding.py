@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "SWALE_OK", -1: "SWALE_EINVAL", -2: "SWALE_ENOMEM", -3: "SWAL
                 -5: "SWALE_ENEGDEPTH", -6: "SWALE_ENONFINITE", -7: "SWALE_ETIMEOUT", -8: "SWALE_EWEIGHT"}
 BIT_EWEIGHT, BIT_NEGDEPTH, BIT_NONFINITE, BIT_EMESH, BIT_NODT, BIT_TIMEOUT = 1, 2, 4, 8, 16, 32
 BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
-MESH = {"static": 0, "profile": 1, "fluid_gauss": 2}
+MESH = {"static": 0, "profile": 1, "fluid_gauss": 2, "linear": 3}
 SCHEME = {"hydrostatic": 0, "nonwb": 1, "special": 2}
 
 
@@ -28,15 +28,17 @@ class SwaleConfig(ctypes.Structure):
                 ("eps_pp", ctypes.c_double), ("h_dry", ctypes.c_double), ("mesh_T", ctypes.c_double),
                 ("gauss_sigma", ctypes.c_double), ("t_end", ctypes.c_double), ("dt_fixed", ctypes.c_double),
                 ("bc", ctypes.c_int32), ("mesh", ctypes.c_int32), ("gauss_half", ctypes.c_int32),
-                ("beta_dx_global", ctypes.c_int32), ("scheme", ctypes.c_int32)]
+                ("beta_dx_global", ctypes.c_int32), ("scheme", ctypes.c_int32), ("alpha_bound", ctypes.c_int32),
+                ("limit_hu", ctypes.c_int32)]
 
 
 def make_config(g=9.812, cfl=0.6, eps_weno=1e-6, eps_pp=1e-11, h_dry=1e-6, mesh_T=1.0, gauss_sigma=8.0,
                 t_end=0.0, dt_fixed=0.0, bc="periodic", mesh="static", gauss_half=24, beta_dx_global=1,
-                scheme="hydrostatic"):
+                scheme="hydrostatic", alpha_bound=0, limit_hu=0):
     return SwaleConfig(g, cfl, eps_weno, eps_pp, h_dry, mesh_T, gauss_sigma, t_end, dt_fixed,
                        BC[bc] if isinstance(bc, str) else bc, MESH[mesh] if isinstance(mesh, str) else mesh,
-                       gauss_half, beta_dx_global, SCHEME[scheme] if isinstance(scheme, str) else scheme)
+                       gauss_half, beta_dx_global, SCHEME[scheme] if isinstance(scheme, str) else scheme,
+                       int(alpha_bound), int(limit_hu))
 
 
 class SwaleError(RuntimeError):

@@ -10,7 +10,7 @@ extern "C" {
 // ob[8] adjoints of (EL, ER, BL, BR, hL, hR, uL, uR) -> v0b[9], D2b[12], D3b[9].
 void ct_recon_adjoint(const double* h, const double* v0, const double* D2, const double* D3, const double* prm,
                       const double* ob, double* v0b, double* D2b, double* D3b) {
-  swale::SchemeConst P{prm[0], prm[1], prm[2], prm[3], 1};
+  swale::SchemeConst P{prm[0], prm[1], prm[2], prm[3], 1, (int32_t)prm[5]};
   double vv[3][3];
   swale::StencilDD DD, DDb;
   for (int v = 0; v < 3; ++v) {

@@ -60,11 +60,12 @@ void ct_edge_forms(const double* h, const double* v, double* out) {
   }
 }
 
-// in: h[5], v0[9], D2[12], D3[9]; tangents tv0[9], tD2[12], tD3[9]; prm = {g, eps, eps_pp, h_dry, dxmax}.
+// in: h[5], v0[9], D2[12], D3[9]; tangents tv0[9], tD2[12], tD3[9];
+// prm = {g, eps, eps_pp, h_dry, dxmax, limit_hu}.
 // out: edge state values [8] and tangents [8] (EL, ER, BL, BR, hL, hR, uL, uR), flag.
 int ct_recon_tangent(const double* h, const double* v0, const double* D2, const double* D3, const double* tv0,
                      const double* tD2, const double* tD3, const double* prm, double* val, double* tan) {
-  swale::SchemeConst P{prm[0], prm[1], prm[2], prm[3], 1};
+  swale::SchemeConst P{prm[0], prm[1], prm[2], prm[3], 1, (int32_t)prm[5]};
   D hh[5], vv[3][3];
   swale::StencilDD DD;
   for (int k = 0; k < 5; ++k) hh[k] = D(h[k]);

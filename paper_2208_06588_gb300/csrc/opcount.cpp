@@ -63,7 +63,7 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
                      double g, double eps_weno, double eps_pp, double h_dry, double alpha, int64_t c0, int64_t c1,
                      double* out, int32_t scheme) {
   using opc::CD;
-  swale::SchemeConst P{g, eps_weno, eps_pp, h_dry, 1};
+  swale::SchemeConst P{g, eps_weno, eps_pp, h_dry, 1, 0};
   double dxmax = 0.0;
   for (int64_t j = 0; j < N; ++j) dxmax = J[j] > dxmax ? J[j] : dxmax;
   opc::Counts rec, upd, flux;
@@ -176,7 +176,7 @@ void opc_count_reverse(int64_t N, const double* E, const double* M, const double
                        double g, double eps_weno, double eps_pp, double h_dry, double alpha, int64_t c0, int64_t c1,
                        double* out) {
   using opc::CD;
-  swale::SchemeConst P{g, eps_weno, eps_pp, h_dry, 1};
+  swale::SchemeConst P{g, eps_weno, eps_pp, h_dry, 1, 0};
   double dxmax = 0.0;
   for (int64_t j = 0; j < N; ++j) dxmax = J[j] > dxmax ? J[j] : dxmax;
   auto flops = []() { return (double)(opc::C.add + opc::C.mul + opc::C.div + opc::C.sqrt); };

@@ -119,6 +119,7 @@ StepConst step_const(const swale_ctx* ctx) {
   K.sc.eps_pp = ctx->cfg.eps_pp;
   K.sc.h_dry = ctx->cfg.h_dry;
   K.sc.beta_dx_global = ctx->cfg.beta_dx_global;
+  K.sc.limit_hu = ctx->cfg.limit_hu;
   K.t_end = ctx->cfg.t_end;
   K.dt_fixed = ctx->cfg.dt_fixed;
   K.mesh_T = ctx->cfg.mesh_T;
@@ -140,8 +141,13 @@ StepConst step_const(const swale_ctx* ctx) {
   K.bot_coef = ctx->bot_coef;
   K.wait_tries = ctx->wait_tries > 0 ? ctx->wait_tries : kWaitTries;
   K.tx_pad = ctx->tx_pad;
+  K.wave_rel = ctx->cfg.alpha_bound ? 0 : 1;
   return K;
 }
+
+// Whether stage 1's alpha can use the node velocities (Eq. alpha2D as written): they are known
+// before the stage runs, except for the secant speeds of the profile motion, which depend on dt.
+int stage1_wave_rel(const swale_config& c) { return (!c.alpha_bound && c.mesh != SWALE_MESH_PROFILE) ? 1 : 0; }
 
 void drop_graph(swale_ctx* ctx);
 
@@ -202,11 +208,11 @@ swale_status dalloc(swale_ctx* ctx, std::vector<void*>& list, T** p, size_t n) {
 // Device arrays of B instances with Ntot cells in total.
 swale_status alloc_state(swale_ctx* ctx, int64_t B, int64_t Ntot, DevState& D) {
   const size_t nc = (size_t)Ntot, nn = nc + B, ne = nc + 2 * B;
-  double** cells[] = {&D.E0, &D.M0, &D.B0, &D.Ea, &D.Ma, &D.Ba, &D.Eb, &D.Mb,
-                      &D.Bb, &D.YE, &D.YM, &D.YB, &D.J0, &D.J1, &D.J2};
+  double** cells[] = {&D.E0, &D.M0, &D.B0, &D.Ea, &D.Ma, &D.Ba, &D.Eb, &D.Mb, &D.Bb,
+                      &D.YE, &D.YM, &D.YB, &D.J0, &D.J1, &D.J2, &D.bE, &D.bM, &D.bB, &D.bJ};
   for (double** p : cells)
     if (swale_status s = dalloc(ctx, ctx->allocs, p, nc)) return s;
-  double** nodes[] = {&D.x, &D.w, &D.P};
+  double** nodes[] = {&D.x, &D.w, &D.P, &D.bx};
   for (double** p : nodes)
     if (swale_status s = dalloc(ctx, ctx->allocs, p, nn)) return s;
   double** edges[] = {&D.eEL, &D.eER, &D.eBL, &D.eBR, &D.ehL, &D.ehR, &D.euL, &D.euR, &D.ipair, &D.itri};
@@ -237,8 +243,16 @@ swale_status check_config(const swale_config* c, std::string& why) {
     why = "bc must be 0 (periodic), 1 (transmissive) or 2 (reflective)";
     return SWALE_EINVAL;
   }
-  if (c->mesh < 0 || c->mesh > 2) {
-    why = "mesh must be 0 (static), 1 (profile) or 2 (fluid_gauss)";
+  if (c->mesh < 0 || c->mesh > 3) {
+    why = "mesh must be 0 (static), 1 (profile), 2 (fluid_gauss) or 3 (linear)";
+    return SWALE_EINVAL;
+  }
+  if (c->alpha_bound != 0 && c->alpha_bound != 1) {
+    why = "alpha_bound must be 0 or 1";
+    return SWALE_EINVAL;
+  }
+  if (c->limit_hu != 0 && c->limit_hu != 1) {
+    why = "limit_hu must be 0 or 1";
     return SWALE_EINVAL;
   }
   if (c->scheme < 0 || c->scheme > 2) {
@@ -392,12 +406,15 @@ swale_status enqueue_step_on(swale_ctx* ctx, const DevState& D, cudaStream_t s, 
     const size_t shm = (size_t)(3 * kMeshThreads + 4 * K.gauss_half + 4) * sizeof(double);
     L(FAM_MESH, [&] { k_mesh_gauss<<<(unsigned)std::max(D.nm, 1), kMeshThreads, shm, s>>>(K, D); });
   }
-  L(FAM_RECON, [&] { launch_recon<1>(K, D1, Tr, gr, s, D.E0, D.M0, D.B0, D.J0); });
-  L(FAM_UPDATE, [&] { launch_update<1, 0>(K, D1, Tu, gu, s, D.E0, D.M0, D.B0, D.J0, none); });
+  StepConst K1 = K;
+  K1.wave_rel = stage1_wave_rel(ctx->cfg);
+  L(FAM_RECON, [&] { launch_recon<1>(K1, D1, Tr, gr, s, D.E0, D.M0, D.B0, D.J0); });
+  L(FAM_UPDATE, [&] { launch_update<1, 0>(K1, D1, Tu, gu, s, D.E0, D.M0, D.B0, D.J0, none); });
   L(FAM_RECON, [&] { launch_recon<2>(K, D2, Tr, gr, s, D.Ea, D.Ma, D.Ba, D.J1); });
   L(FAM_UPDATE, [&] { launch_update<2, 0>(K, D2, Tu, gu, s, D.Ea, D.Ma, D.Ba, D.J1, none); });
   L(FAM_RECON, [&] { launch_recon<3>(K, D3, Tr, gr, s, D.Eb, D.Mb, D.Bb, D.J2); });
   L(FAM_UPDATE, [&] { launch_update<3, 0>(K, D3, Tu, gu, s, D.Eb, D.Mb, D.Bb, D.J2, none); });
+  L(FAM_PROLOGUE, [&] { k_commit<<<(unsigned)std::min<int64_t>(ctx->B, 1024), 256, 0, s>>>(K, D); });
   if (st) return st;
   SW_CUDA(ctx, cudaGetLastError());
   return SWALE_OK;
@@ -471,7 +488,9 @@ swale_status set_instances(swale_ctx* ctx, const std::vector<int64_t>& off, cons
     ic[i].N = N;
     ic[i].coff = c0;
     ic[i].cfl = cfl[i];
-    ic[i].Wbar_profile = (ctx->cfg.mesh == SWALE_MESH_PROFILE) ? kTwoPi / ctx->cfg.mesh_T * pmax : 0.0;
+    ic[i].Wbar_profile = (ctx->cfg.mesh == SWALE_MESH_PROFILE) ? kTwoPi / ctx->cfg.mesh_T * pmax
+                         : (ctx->cfg.mesh == SWALE_MESH_LINEAR)  ? pmax
+                                                                 : 0.0;
     ic[i].ntiles_r = 0;
     ic[i].pad_ = 0;
     std::memset(&S0[i], 0, sizeof(DevScalars));
@@ -572,8 +591,8 @@ swale_status swale_set_problem(swale_ctx* ctx, int64_t N, const double* x_nodes,
   if (N < 5) return fail(ctx, SWALE_EINVAL, "N must be >= 5");
   if (N > 0x7fffffffLL) return fail(ctx, SWALE_EINVAL, "N must be < 2^31");
   if (!x_nodes || !q0 || !hu || !b) return fail(ctx, SWALE_EINVAL, "x_nodes, q0, hu and b are required");
-  if (ctx->cfg.mesh == SWALE_MESH_PROFILE && !profile)
-    return fail(ctx, SWALE_EINVAL, "profile motion needs the node profile");
+  if ((ctx->cfg.mesh == SWALE_MESH_PROFILE || ctx->cfg.mesh == SWALE_MESH_LINEAR) && !profile)
+    return fail(ctx, SWALE_EINVAL, "profile and linear motion need the node profile");
   std::vector<double> x, q, m, bb, P;
   swale_status s;
   if ((s = fetch(ctx, x_nodes, N + 1, x)) || (s = fetch(ctx, q0, N, q)) || (s = fetch(ctx, hu, N, m)) ||
@@ -594,8 +613,8 @@ swale_status swale_batch_set_problem(swale_ctx* ctx, int64_t B, const int64_t* o
   if (B < 1 || B > 0x7fffffff) return fail(ctx, SWALE_EINVAL, "B must be >= 1");
   if (!offsets || !x_nodes || !q0 || !hu || !b)
     return fail(ctx, SWALE_EINVAL, "offsets, x_nodes, q0, hu and b are required");
-  if (ctx->cfg.mesh == SWALE_MESH_PROFILE && !profile)
-    return fail(ctx, SWALE_EINVAL, "profile motion needs the node profile");
+  if ((ctx->cfg.mesh == SWALE_MESH_PROFILE || ctx->cfg.mesh == SWALE_MESH_LINEAR) && !profile)
+    return fail(ctx, SWALE_EINVAL, "profile and linear motion need the node profile");
   std::vector<int64_t> off;
   swale_status s;
   if ((s = fetch(ctx, offsets, (size_t)B + 1, off))) return s;
@@ -765,7 +784,7 @@ swale_status swale_get_status(swale_ctx* ctx, uint32_t* status_bits, int64_t* st
 
 namespace {
 constexpr char kSaveMagic[8] = {'S', 'W', 'A', 'L', 'E', 'S', 'T', '1'};
-constexpr uint32_t kSaveVersion = 1;
+constexpr uint32_t kSaveVersion = 2;
 }  // namespace
 
 swale_status swale_save(swale_ctx* ctx, const char* path) {
@@ -1101,7 +1120,9 @@ swale_status swale_rhs(swale_ctx* ctx, int64_t N, const double* E, const double*
   if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
   double A;
   std::memcpy(&A, &Abits, 8);
-  if (!(alpha > 0.0)) {
+  if (!(alpha > 0.0) && K.wave_rel) {
+    alpha = A;  // Eq. alpha2D: the wave speeds were taken relative to w
+  } else if (!(alpha > 0.0)) {
     std::vector<double> wh(N + 1);
     e = cudaMemcpy(wh.data(), w, (N + 1) * sizeof(double), cudaMemcpyDefault);
     if (e) return cleanup(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
@@ -1274,7 +1295,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   if (nsteps < 1 || ckpt_every < 1 || G < 1 || !gauges_x || !h_obs)
     return fail(ctx, SWALE_EINVAL, "nsteps, ckpt_every, G >= 1 and gauges, observations required");
   if (ctx->cfg.mesh == SWALE_MESH_FLUID_GAUSS)
-    return fail(ctx, SWALE_EINVAL, "the adjoint needs a prescribed mesh (static or profile motion)");
+    return fail(ctx, SWALE_EINVAL, "the adjoint needs a prescribed mesh (static, profile or linear motion)");
   if (ctx->cfg.t_end > 0.0) return fail(ctx, SWALE_EINVAL, "the adjoint runs a fixed number of steps: t_end = 0");
   if (ctx->bot_pieces > 0) return fail(ctx, SWALE_EINVAL, "the adjoint evolves the bottom (no L2-projection bottom)");
   if (ctx->cfg.scheme != SWALE_SCHEME_HYDROSTATIC)
@@ -1325,6 +1346,9 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   // checkpoint interval.
   DevState base = ctx->D;
   base.geo = nullptr;
+  // The adjoint's forward runs check the status after the fact; they keep no roll-back copies
+  // (the further state sets share nothing with the context's backups).
+  base.bE = base.bM = base.bB = base.bJ = base.bx = nullptr;
   // A further set of state arrays: its own state, stage, edge and flag arrays and scalars
   // (instance constants, work lists and the motion profile are shared, read only).
   auto alloc_state_set = [&](DevState& X) {
@@ -1639,11 +1663,12 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
 // ======================================================================================
 // Allocation-free right-hand side (swale_rhs_noalloc)
 // ======================================================================================
-// Some callers cannot call cudaMalloc: code that runs inside another framework's memory
-// pool, or between the captures of a CUDA graph that must not grow device memory. For them
-// swale_rhs_noalloc evaluates the same right-hand side as swale_rhs with its scratch (the
-// edge values, shared reciprocals, detector classes and reduction scalars) in the fixed array
-// below, which every GPU that loads this library holds until the process exits.
+// Some callers cannot call cudaMalloc: code that runs inside another framework's memory pool
+// (which owns the device memory and must see every allocation), or work whose device memory
+// must not grow while it runs. For them swale_rhs_noalloc evaluates the same right-hand side as
+// swale_rhs with its scratch (the edge values, shared reciprocals, interior point values of the
+// special source scheme, detector classes and reduction scalars) in the fixed array below,
+// which every GPU that loads this library holds until the process exits.
 namespace {
 
 constexpr int64_t kNoAllocMaxCells = 65536;
@@ -1651,13 +1676,27 @@ constexpr int kNoAllocMaxDevices = 64;
 constexpr int kNoAllocTile = 128;
 
 struct NoAllocScratch {
-  double edges[10][kNoAllocMaxCells + 2];
+  double edges[12][kNoAllocMaxCells + 2];  // 8 edge arrays, 2 reciprocals, 2 point-value arrays
   uint8_t flags[kNoAllocMaxCells + 2];
   InstConst ic;
   DevScalars S;
 };
 
-// Fixed scratch of the allocation-free entry point (about 5.3 MB per device).
+// Resets the scratch scalars of one call; the values come in as kernel arguments, so the call
+// copies nothing from host memory.
+__global__ void k_noalloc_init(InstConst* ic, DevScalars* S, int64_t N, int32_t ntiles_r) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  InstConst c = {};
+  c.N = N;
+  c.cfl = 1.0;
+  c.ntiles_r = ntiles_r;
+  *ic = c;
+  DevScalars z = {};
+  z.Jmin0 = 0x3ff0000000000000ull;  // 1.0: the unused stage-1 dt arithmetic stays finite
+  *S = z;
+}
+
+// Fixed scratch of the allocation-free entry point (about 6.3 MB per device).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
 // Device address of g_noalloc_scratch per device, obtained once with that device current.
@@ -1684,7 +1723,8 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   if (!cfg || !E || !M || !B || !J || !w || !RE || !RM || !RB) return SWALE_EINVAL;
   if (N < 5 || N > kNoAllocMaxCells || !(alpha > 0.0)) return SWALE_EINVAL;
   if (!(cfg->g > 0) || !(cfg->eps_weno > 0) || !(cfg->eps_pp >= 0) || !(cfg->h_dry >= 0) || cfg->bc < 0 ||
-      cfg->bc > 2)
+      cfg->bc > 2 || cfg->scheme < 0 || cfg->scheme > 2 || (cfg->alpha_bound != 0 && cfg->alpha_bound != 1) ||
+      (cfg->limit_hu != 0 && cfg->limit_hu != 1))
     return SWALE_EINVAL;
   const void* dev_ptrs[] = {E, M, B, J, w, RE, RM, RB};
   for (const void* p : dev_ptrs)
@@ -1694,13 +1734,20 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
     cudaGetLastError();
     return SWALE_ECUDA;
   }
+  // The scratch address below is the current device's: the stream must belong to it.
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int sdev = dev;
+  if (st && cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+    cudaGetLastError();
+    return SWALE_EINVAL;
+  }
+  if (sdev != dev) return SWALE_EINVAL;
   // First call on this device: look up the device address of the scratch array.
   std::call_once(g_noalloc_once[dev], [dev] {
     g_noalloc_err[dev] = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch);
   });
   if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_addr[dev]) return SWALE_ECUDA;
   NoAllocScratch* scr = reinterpret_cast<NoAllocScratch*>(g_noalloc_addr[dev]);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
 
   DevState D{};
   D.eEL = scr->edges[0];
@@ -1713,6 +1760,10 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   D.euR = scr->edges[7];
   D.ipair = scr->edges[8];
   D.itri = scr->edges[9];
+  if (cfg->scheme == SWALE_SCHEME_SPECIAL) {
+    D.eG1 = scr->edges[10];
+    D.eG2 = scr->edges[11];
+  }
   D.flags = scr->flags;
   D.IC = &scr->ic;
   D.S = &scr->S;
@@ -1725,6 +1776,7 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   K.sc.eps_pp = cfg->eps_pp;
   K.sc.h_dry = cfg->h_dry;
   K.sc.beta_dx_global = cfg->beta_dx_global;
+  K.sc.limit_hu = cfg->limit_hu;
   K.t_end = 0.0;
   K.dt_fixed = 0.0;
   K.mesh_T = 1.0;
@@ -1742,26 +1794,21 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   K.tx_pad = 0;
   K.bot_pieces = K.bot_deg = 0;
   K.bot_breaks = K.bot_coef = nullptr;
-  K.scheme = SWALE_SCHEME_HYDROSTATIC;
+  K.scheme = cfg->scheme;
   K.geo_epoch = 0;  // no geometry cache here (D.geo is null)
-  // The scalars keep the previous call's contents: start them from zero (J^n minimum at 1 so
-  // the stage-1 time-step arithmetic stays finite; its result is not used here).
-  InstConst ic0;
-  std::memset(&ic0, 0, sizeof(ic0));
-  ic0.N = N;
-  ic0.cfl = 1.0;
-  ic0.ntiles_r = D.nr;
-  DevScalars S0;
-  std::memset(&S0, 0, sizeof(S0));
-  S0.Jmin0 = 0x3ff0000000000000ull;
-  cudaError_t e = cudaMemcpyAsync(&scr->ic, &ic0, sizeof(InstConst), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&scr->S, &S0, sizeof(DevScalars), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return SWALE_ECUDA;
+  K.wave_rel = cfg->alpha_bound ? 0 : 1;  // the largest |u - w| + sqrt(g h) (Eq. alpha2D) in A_out
+  // The scalars keep the previous call's contents: start them from zero.
+  k_noalloc_init<<<1, 32, 0, st>>>(&scr->ic, &scr->S, N, D.nr);
   k_widths_max<<<64, 256, 0, st>>>(J, N, &scr->S);
-  k_recon<1, kNoAllocTile><<<(unsigned)D.nr, kNoAllocTile, 0, st>>>(K, D, E, M, B, J);
+  if (cfg->scheme == SWALE_SCHEME_NONWB)
+    k_recon<1, kNoAllocTile, 1><<<(unsigned)D.nr, kNoAllocTile, 0, st>>>(K, D, E, M, B, J);
+  else if (cfg->scheme == SWALE_SCHEME_SPECIAL)
+    k_recon<1, kNoAllocTile, 2><<<(unsigned)D.nr, kNoAllocTile, 0, st>>>(K, D, E, M, B, J);
+  else
+    k_recon<1, kNoAllocTile><<<(unsigned)D.nr, kNoAllocTile, 0, st>>>(K, D, E, M, B, J);
   RhsOut ro{RE, RM, RB, alpha};
   k_update<2, 1, kNoAllocTile><<<(unsigned)D.nu, kNoAllocTile, 0, st>>>(K, D, E, M, B, J, ro);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, scr->flags + 1, (size_t)N, cudaMemcpyDefault, st);
   if (e == cudaSuccess && A_out) {
     unsigned long long bits = 0;

@@ -283,8 +283,10 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real i
     theta = (hbar - epsv) * iD;
     hL = theta * (hL0 - hbar) + hbar;
     hR = theta * (hR0 - hbar) + hbar;
-    mL = theta * (mL0 - mbar) + mbar;
-    mR = theta * (mR0 - mbar) + mbar;
+    if (P.limit_hu) {
+      mL = theta * (mL0 - mbar) + mbar;
+      mR = theta * (mR0 - mbar) + mbar;
+    }
   }
   const bool wetL = dlt(P.h_dry, hL), wetR = dlt(P.h_dry, hR);
   // ---------------- reverse sweep ----------------
@@ -314,13 +316,19 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real i
   }
   real hbarb = 0.0, mbarb = 0.0, hL0b, hR0b, mL0b, mR0b;
   if (active) {
-    const real thetab = hLb * (hL0 - hbar) + hRb * (hR0 - hbar) + mLb * (mL0 - mbar) + mRb * (mR0 - mbar);
+    real thetab = hLb * (hL0 - hbar) + hRb * (hR0 - hbar);
     hL0b = theta * hLb;
     hR0b = theta * hRb;
-    mL0b = theta * mLb;
-    mR0b = theta * mRb;
     hbarb = (1.0 - theta) * (hLb + hRb);
-    mbarb = (1.0 - theta) * (mLb + mRb);
+    if (P.limit_hu) {
+      thetab = thetab + mLb * (mL0 - mbar) + mRb * (mR0 - mbar);
+      mL0b = theta * mLb;
+      mR0b = theta * mRb;
+      mbarb = (1.0 - theta) * (mLb + mRb);
+    } else {
+      mL0b = mLb;
+      mR0b = mRb;
+    }
     // theta = (hbar - epsv) / (hbar - mn)
     hbarb = hbarb + thetab * (1.0 - theta) * iD;
     const real epsvb = -thetab * iD;

@@ -43,6 +43,7 @@ typedef double real;
 struct SchemeConst {
   double g, eps_weno, eps_pp, h_dry;
   int32_t beta_dx_global;
+  int32_t limit_hu;  // 1: the limiter's theta also scales hu about its mean (reading O6b)
 };
 
 
@@ -285,8 +286,8 @@ SWALE_HD real edge_value(const CellGeom& G, const real phi[2][3], const real v0[
   return s;
 }
 
-// Limiter on h = eta - b with the Gauss-Lobatto mean delta (Eq. modifiedhjn, xd in 1D; hu
-// scaled by the same theta), b re-derived as eta - h (Remark in Sec. 4.3) and velocities.
+// Limiter on h = eta - b with the Gauss-Lobatto mean delta (Eq. modifiedhjn, xd in 1D; hu scaled
+// by the same theta only if P.limit_hu), b re-derived as eta - h (Remark in Sec. 4.3), velocities.
 //   ev[v][e]  edge values of (eta, hu, h);  hbar0, mbar  the cell's depth and discharge means
 SWALE_HD void limit_cell(const SchemeConst& P, const real ev[3][2], real hbar0, real mbar, EdgeState& o,
                          uint32_t& st) {
@@ -302,8 +303,10 @@ SWALE_HD void limit_cell(const SchemeConst& P, const real ev[3][2], real hbar0, 
     const real theta = (hbar - epsv) * recip(hbar - mn);
     hL = theta * (hL - hbar) + hbar;
     hR = theta * (hR - hbar) + hbar;
-    mL = theta * (mL - mbar) + mbar;
-    mR = theta * (mR - mbar) + mbar;
+    if (P.limit_hu) {
+      mL = theta * (mL - mbar) + mbar;
+      mR = theta * (mR - mbar) + mbar;
+    }
   }
   o.EL = ev[0][0];
   o.ER = ev[0][1];

@@ -7,6 +7,7 @@
 //   k_recon<1>, k_update<1>    stage 1 on the mesh at t_n
 //   k_recon<2>, k_update<2>    stage 2 on the mesh at t_{n+1}
 //   k_recon<3>, k_update<3>    stage 3 on the mesh at t_{n+1/2}
+//   k_commit                   the step's time and step count, or its roll-back after an error
 // Every launch serves all instances of a batch: blocks walk a work list of (instance, tile)
 // entries in grid-stride order (one pass when the grid has one block per tile, a persistent
 // loop when it is smaller). A single instance uses the implicit list t -> (0, t * T + first).
@@ -14,6 +15,12 @@
 // shuffle, shared memory, one atomicMax per tile on the order-preserving bit pattern of a
 // non-negative double); in stage 1 the last tile of each instance computes that instance's
 // dt, so dt, alpha and t never visit the host and steps replay as CUDA graphs.
+//
+// Error contract: an error bit (kErrBits) raised in a step stops the instance. Kernels skip an
+// instance whose status holds one; the stage-3 update writes q^{n+1}, J^{n+1} and the nodes only
+// if no error was raised before it (keeping q^n, J^n and x^n in backup arrays), and k_commit
+// restores them if the stage-3 update itself raised one. The state is then that of the last
+// good step; later steps (also inside a captured graph) are no-ops for the instance.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,6 +45,8 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 // (unsigned order equals numeric order for non-negative IEEE doubles).
 struct DevScalars {
   double t, dt, sdiff, Wbar, alpha1;
+  unsigned int st3;                  // status bits raised by the stage-3 update (folded by k_commit)
+  unsigned int pad_;
   unsigned long long A[3];           // max edge wave speed per stage
   unsigned long long Jmax[3];        // max width of the stage meshes J^n, J^(1), J^(2)
   unsigned long long Jmin0;          // min J^n
@@ -85,6 +94,10 @@ struct StepConst {
   int32_t alpha_mode;
   int32_t scheme;  // SWALE_SCHEME_*
   uint32_t geo_epoch;  // bumped by the host whenever the state is set or restored
+  // Wave speeds of alpha (Eq. alpha2D): 1 = relative to the node velocity, |u - w| + sqrt(g h)
+  // (w known when the stage runs), 0 = |u| + sqrt(g h), with the step bound Wbar of |w| added to
+  // the maximum (stage 1 of the secant motion, whose w depends on dt; or on request).
+  int32_t wave_rel;
   // L2-projection bottom (Eq. baverage); bot_pieces == 0: b evolves by Eq. bottomrk.
   int32_t bot_pieces, bot_deg;
   const double* bot_breaks;  // bot_pieces + 1 breakpoints
@@ -118,6 +131,9 @@ struct DevState {
   double *eEL, *eER, *eBL, *eBR, *ehL, *ehR, *euL, *euR;
   double *ipair, *itri;        // 1/(J_c + J_{c+1}) and 1/(J_{c-1} + J_c + J_{c+1}) of the stage mesh
   double* xn;                  // nodes at t_{n+1}, written by stage 2 (L2-projection bottom only)
+  // Backups of q^n, J^n (cells) and x^n (nodes) written by the stage-3 update before it commits
+  // the step, restored by k_commit if that update raised an error (null: no roll-back).
+  double *bE, *bM, *bB, *bJ, *bx;
   double *eG1, *eG2;           // eta at the interior Gauss-Lobatto points (special source scheme only)
   // Geometry cache: SWALE_GEOM_VALUES arrays in the edge layout, geo[k * geo_stride + idx].
   double* geo;
@@ -130,6 +146,21 @@ struct DevState {
 };
 
 __constant__ double c_gauss_w[2 * kMaxGaussHalf + 1];
+
+// Status bits that stop an instance (SWALE_BIT_NEGDEPTH is a warning).
+constexpr unsigned int kErrBits =
+    swale::ST_EWEIGHT | swale::ST_NONFINITE | swale::ST_EMESH | swale::ST_NODT | swale::ST_TIMEOUT;
+
+// An instance takes no further part in the step: finished (t_end), or an error was raised.
+__device__ __forceinline__ bool inst_idle(const DevScalars* S) {
+  return S->done || (*(volatile const unsigned int*)&S->status & kErrBits);
+}
+
+// Node velocity array of a batch: the motion profile itself for the linear motion (constant
+// node velocities), else the node-velocity array (zero for a static mesh).
+__device__ __forceinline__ const double* node_velocities(const StepConst& K, const DevState& D) {
+  return K.mesh == SWALE_MESH_LINEAR ? D.P : D.w;
+}
 
 __device__ __forceinline__ int64_t ghost(int64_t i, int64_t N, int bc) {
   if (bc == SWALE_BC_PERIODIC) {
@@ -292,8 +323,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Waits for the phase `parity` of bar to complete, at most `tries` polls (each poll itself
-// blocks for a short hardware-defined time). Returns false if it gave up.
+// blocks for a short hardware-defined time). Returns false if it gave up. kWaitTries bounds the
+// wait for a tile's copies; when it runs out, the block waits kDrainTries more polls for those
+// copies before it leaves (a block must not exit while its copies can still write its shared
+// memory, which the SM hands to the next block).
 constexpr int kWaitTries = 1 << 20;
+constexpr int kDrainTries = 1 << 24;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int tries) {
   for (int i = 0; i < tries; ++i)
     if (mbar_try_wait(bar, parity)) return true;
@@ -308,7 +343,8 @@ __global__ void k_prologue(StepConst K, DevState D) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= K.B) return;
   DevScalars* S = D.S + i;
-  if (K.t_end > 0.0 && S->t >= K.t_end) {
+  // An error in an earlier step, or the end time reached: the instance is done.
+  if ((S->status & kErrBits) || (K.t_end > 0.0 && S->t >= K.t_end)) {
     S->done = 1;
     return;
   }
@@ -323,6 +359,7 @@ __global__ void k_prologue(StepConst K, DevState D) {
   S->Jmax[1] = S->Jmax[2] = 0ull;
   S->Wabs = S->dWabs = 0ull;
   S->counter = 0u;
+  S->st3 = 0u;
   if (K.mesh != SWALE_MESH_FLUID_GAUSS) S->Wbar = D.IC[i].Wbar_profile;
 }
 
@@ -416,19 +453,22 @@ __global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, c
   __shared__ double sIT[T + 2], sD3[3][T + 2];  // triples centred at cells c0-1 .. c0+T
   __shared__ __align__(16) double sRaw[4][T + 8];  // E, M, B, J of those cells as bulk-copied
   __shared__ __align__(8) uint64_t sBar;           // completion of the tile's bulk copies
+  __shared__ __align__(8) uint64_t sPad;           // test hook: a barrier no copy completes
   __shared__ bool last;
   const int tid = threadIdx.x;
   const bool refl = (K.bc == SWALE_BC_REFLECTIVE);
   if (tid == 0) {
     mbar_init(&sBar);
-    fence_proxy_async();  // the initialised barrier, visible to the copy engine
+    mbar_init(&sPad);
+    fence_proxy_async();  // the initialised barriers, visible to the copy engine
   }
   __syncthreads();
   uint32_t phase = 0;
   for (int t = blockIdx.x; t < D.nr; t += gridDim.x) {
     const Tile tl = D.rtiles ? D.rtiles[t] : Tile{0, t * T - 1};
     DevScalars* S = D.S + tl.inst;
-    if (S->done) continue;
+    // every thread reads the flags once, then the block agrees (the status may change meanwhile)
+    if (__syncthreads_or(inst_idle(S))) continue;
     const InstConst ic = D.IC[tl.inst];
     const int64_t N = ic.N, c0 = tl.c0;
     const double* E = Eg + ic.coff;
@@ -455,17 +495,23 @@ __global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, c
     if (bulk) {
       if (tid == 0) {
         fence_proxy_async();  // the previous tile's reads of sRaw come before these writes
-        mbar_arrive_expect_tx(&sBar, 4 * bytes + K.tx_pad);
+        mbar_arrive_expect_tx(&sBar, 4 * bytes);
         bulk_copy_g2s(&sRaw[0][rel + off], Eg + ga, bytes, &sBar);
         bulk_copy_g2s(&sRaw[1][rel + off], Mg + ga, bytes, &sBar);
         bulk_copy_g2s(&sRaw[2][rel + off], Bg + ga, bytes, &sBar);
         bulk_copy_g2s(&sRaw[3][rel + off], Jg + ga, bytes, &sBar);
+        // Test hook: a second barrier expects bytes that no copy delivers.
+        if (K.tx_pad) mbar_arrive_expect_tx(&sPad, K.tx_pad);
       }
-      const bool done = mbar_wait_bounded(&sBar, phase, K.wait_tries);
+      bool landed = mbar_wait_bounded(&sBar, phase, kWaitTries);
+      bool ok = landed;
+      if (!landed) landed = mbar_wait_bounded(&sBar, phase, kDrainTries);  // drain before leaving
+      if (K.tx_pad && landed) ok = mbar_wait_bounded(&sPad, 0u, K.wait_tries > 0 ? K.wait_tries : kWaitTries);
       phase ^= 1u;
-      if (__syncthreads_or(!done)) {  // the copies did not complete: give the stage up
+      // The copies did not complete in time (or the test barrier ran out): give the stage up.
+      // Every copy of this block has landed here unless the drain wait ran out as well.
+      if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicOr(&S->status, (unsigned int)swale::ST_TIMEOUT);
-        __nanosleep(20000);  // lets copies still in flight land before the block's shared memory goes
         return;
       }
     }
@@ -580,6 +626,11 @@ __global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, c
       euL = o.uL;
       ehR = o.hR;
       euR = o.uR;
+      if (K.wave_rel) {  // Eq. alpha2D: speeds relative to the node (cell c spans nodes c, c+1)
+        const double* wv = node_velocities(K, D) + ic.coff + tl.inst;
+        if (useL) euL -= wv[c];
+        if (useR) euR -= wv[c + 1];
+      }
     }
     wave = block_wave<T>(K.sc.g, useL, useR, ehL, euL, ehR, euR);
     block_or_status(&S->status, st);
@@ -601,7 +652,7 @@ __global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, c
           dwmax = bitsd(atomicAdd(&S->dWabs, 0ull));
           S->Wbar = Wbar;
         }
-        const double alpha1 = stage_alpha(K, tl.inst, 1, A1 + Wbar, S->step_idx);
+        const double alpha1 = stage_alpha(K, tl.inst, 1, K.wave_rel ? A1 : A1 + Wbar, S->step_idx);
         const double tn = S->t;
         double dt;
         int clipped = 0;
@@ -662,7 +713,12 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
     const Tile tl = D.utiles ? D.utiles[t] : Tile{0, t * T};
     const int inst = tl.inst;
     DevScalars* S = D.S + inst;
-    if (MODE == 0 && S->done) continue;
+    if (MODE == 0) {
+      // Skip a finished instance and one whose step has failed. In stage 3 the status does not
+      // change during the launch (this kernel raises its bits in st3), so every tile of an
+      // instance decides alike: all commit the step or none does.
+      if (__syncthreads_or(inst_idle(S))) continue;
+    }
     const InstConst ic = D.IC[inst];
     const int64_t N = ic.N, j0 = tl.c0;
     const int64_t cb = ic.coff, nb = ic.coff + inst, eb = ic.coff + 2 * (int64_t)inst;
@@ -673,7 +729,7 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
     if (MODE == 1) {
       alpha = ro.alpha;
     } else {
-      alpha = (STAGE == 1) ? S->alpha1 : bitsd(S->A[STAGE - 1]) + S->Wbar;
+      alpha = (STAGE == 1) ? S->alpha1 : bitsd(S->A[STAGE - 1]) + (K.wave_rel ? 0.0 : S->Wbar);
       if (STAGE > 1) {
         // Record / replay of stages 2 and 3 (stage 1 is handled where alpha1 is formed): every
         // tile computes the same value; the first tile of the instance records it.
@@ -700,6 +756,9 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
           if (i < T || k == N) D.w[nb + k] = wk;
         } else if (MODE == 0 && K.mesh == SWALE_MESH_STATIC) {
           wk = 0.0;
+        } else if (MODE == 0 && K.mesh == SWALE_MESH_LINEAR) {
+          wk = D.P[nb + k];  // constant node velocity (Eq. velocity)
+          if (STAGE == 1 && (i < T || k == N)) D.w[nb + k] = wk;
         } else {
           wk = D.w[nb + k];
         }
@@ -774,11 +833,14 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
         if (STAGE == 1) {
           const double J1 = J0 + dt * dw;
           const double J2 = 0.75 * J0 + 0.25 * J1 + 0.25 * dt * dw;
+          // J^{n+1} of the recursion, checked here already so that a step that would invert a
+          // cell fails before its stages run (stage 3 recomputes it from the stored J^(2)).
+          const double J3c = (1.0 / 3.0) * J0 + (2.0 / 3.0) * J2 + (2.0 / 3.0) * dt * dw;
           D.J1[g] = J1;
           D.J2[g] = J2;
           jmaxa = J1;
           jmaxb = J2;
-          if (!swale::gt0(J1) || !swale::gt0(J2)) st |= swale::ST_EMESH;
+          if (!swale::gt0(J1) || !swale::gt0(J2) || !swale::gt0(J3c)) st |= swale::ST_EMESH;
           const double yE = J0 * D.E0[g] + dt * RE, yM = J0 * D.M0[g] + dt * RM, yB = J0 * D.B0[g] + dt * RB;
           D.YE[g] = yE;
           D.YM[g] = yM;
@@ -809,9 +871,18 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
         } else {
           const double J3 = (1.0 / 3.0) * J0 + (2.0 / 3.0) * D.J2[g] + (2.0 / 3.0) * dt * dw;
           if (!swale::gt0(J3)) st |= swale::ST_EMESH;
-          const double yE = (1.0 / 3.0) * (J0 * D.E0[g]) + (2.0 / 3.0) * (D.YE[g] + dt * RE);
-          const double yM = (1.0 / 3.0) * (J0 * D.M0[g]) + (2.0 / 3.0) * (D.YM[g] + dt * RM);
-          const double yB = (1.0 / 3.0) * (J0 * D.B0[g]) + (2.0 / 3.0) * (D.YB[g] + dt * RB);
+          const double E0v = D.E0[g], M0v = D.M0[g], B0v = D.B0[g];
+          if (D.bE) {  // q^n, J^n, x^n kept for a roll-back by k_commit
+            D.bE[g] = E0v;
+            D.bM[g] = M0v;
+            D.bB[g] = B0v;
+            D.bJ[g] = J0;
+            D.bx[nb + j] = D.x[nb + j];
+            if (j == N - 1) D.bx[nb + N] = D.x[nb + N];
+          }
+          const double yE = (1.0 / 3.0) * (J0 * E0v) + (2.0 / 3.0) * (D.YE[g] + dt * RE);
+          const double yM = (1.0 / 3.0) * (J0 * M0v) + (2.0 / 3.0) * (D.YM[g] + dt * RM);
+          const double yB = (1.0 / 3.0) * (J0 * B0v) + (2.0 / 3.0) * (D.YB[g] + dt * RB);
           const double inv = swale::recip(J3);
           const double En = yE * inv, Mn = yM * inv, Bn = yB * inv;
           D.E0[g] = En;
@@ -834,17 +905,50 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
       }
     }
     if (MODE == 0) {
-      block_or_status(&S->status, st);
+      block_or_status(STAGE == 3 ? &S->st3 : &S->status, st);
       if (STAGE == 1) {
         block_max_to(&S->Jmax[1], jmaxa);
         block_max_to(&S->Jmax[2], jmaxb);
       } else if (STAGE == 3) {
         block_max_to(&S->JmaxN, jmaxb);
         block_min_to(&S->JminN, jminb);
-        if (j0 == 0 && tid == 0) {
-          S->t = S->clipped ? K.t_end : S->t + S->dt;
-          S->steps += 1;
-        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// End of a step, one block per instance (grid-stride): a clean step advances the instance's time
+// and step count; a step whose stage-3 update raised an error (after committing its cells) is
+// rolled back from the backups, and one that failed earlier wrote nothing. The stage-3 bits
+// join the status word here.
+// ------------------------------------------------------------------------------------
+__global__ void k_commit(StepConst K, DevState D) {
+  for (int i = blockIdx.x; i < K.B; i += gridDim.x) {
+    DevScalars* S = D.S + i;
+    const bool skip = S->done;
+    const unsigned int before = S->status & kErrBits, bad3 = S->st3 & kErrBits;
+    __syncthreads();  // every thread has read the words before thread 0 changes them
+    if (skip) continue;
+    if (!before && bad3 && D.bE) {
+      const InstConst ic = D.IC[i];
+      const int64_t cb = ic.coff, nb = ic.coff + i;
+      for (int64_t j = threadIdx.x; j < ic.N; j += blockDim.x) {
+        D.E0[cb + j] = D.bE[cb + j];
+        D.M0[cb + j] = D.bM[cb + j];
+        D.B0[cb + j] = D.bB[cb + j];
+        D.J0[cb + j] = D.bJ[cb + j];
+      }
+      for (int64_t k = threadIdx.x; k <= ic.N; k += blockDim.x) D.x[nb + k] = D.bx[nb + k];
+    }
+    if (threadIdx.x == 0) {
+      S->status |= S->st3;
+      if (!before && !bad3) {
+        S->t = S->clipped ? K.t_end : S->t + S->dt;
+        S->steps += 1;
+      } else {  // the widths stay those of J^n
+        S->JmaxN = S->Jmax[0];
+        S->JminN = S->Jmin0;
       }
     }
   }

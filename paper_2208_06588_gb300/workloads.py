@@ -164,6 +164,52 @@ def moses_second(N=200, t_end=1.0, moving=True):
                  mesh="profile" if moving else "static", mesh_T=t_end, t_end=t_end, cfl=0.08)
 
 
+def _pulse_nodes_start(i):
+    """Nodes of the graded mesh at t = 0 (Eq. 0.2inis), i = 0..100."""
+    i = np.asarray(i, dtype=np.float64)
+    return np.where(i <= 25, 0.0372 * i, np.where(i <= 75, 0.93 + 0.008 * (i - 25), 1.33 + 0.0268 * (i - 75)))
+
+
+def _pulse_nodes_end(i):
+    """Nodes of the graded mesh at t_end (Eq. 0.2ends), i = 0..100."""
+    i = np.asarray(i, dtype=np.float64)
+    return np.select([i <= 7, i <= 35, i <= 68, i <= 98],
+                     [2.0 * i / 35.0, 0.4 + (i - 7) / 140.0, 0.6 + 53.0 * (i - 35) / 1650.0, 1.66 + (i - 68) / 150.0],
+                     1.86 + 0.07 * (i - 98))
+
+
+def big_pulse(refine=1, eps=0.2, moving=True, t_end=0.2, cfl=0.6):
+    """Sec. 5.1 perturbation of a lake at rest (LeVeque's test): [0, 2], b = 0.25 (cos(10 pi
+    (x - 1.5)) + 1) on [1.4, 1.6] else 0, h = 1 - b + eps on [1.1, 1.2] else 1 - b, hu = 0,
+    transmissive; eps = 0.2 is the big pulse. moving=True: the graded mesh of the big-pulse
+    example, 100 cells whose nodes move with constant velocities (Eq. 0.2inis, Eq. 0.2ends,
+    Eq. velocity, Eq. meshspecial: x(t) = x(0) + w t, w = (x(t_end) - x(0)) / t_end); refine > 1
+    splits every cell into `refine` equal cells at both ends of the motion (same grading, 100 *
+    refine cells). moving=False: the uniform static mesh of the same size."""
+    N = 100 * refine
+    k = np.arange(N + 1) / refine
+    i0 = np.minimum(np.floor(k).astype(int), 99)
+    fr = k - i0
+    x0 = (1 - fr) * _pulse_nodes_start(i0) + fr * _pulse_nodes_start(i0 + 1)
+    x1 = (1 - fr) * _pulse_nodes_end(i0) + fr * _pulse_nodes_end(i0 + 1)
+    if not moving:
+        x0 = _uniform(0.0, 2.0, N)
+        x1 = x0
+    x0[0], x0[-1], x1[0], x1[-1] = 0.0, 2.0, 0.0, 2.0
+    w = (x1 - x0) / t_end
+
+    def bf(s):
+        return np.where((s >= 1.4) & (s <= 1.6), 0.25 * (np.cos(10.0 * np.pi * (s - 1.5)) + 1.0), 0.0)
+
+    def hf(s):
+        return 1.0 - bf(s) + np.where((s >= 1.1) & (s <= 1.2), eps, 0.0)
+
+    pr = _make("big_pulse", x0, hf, lambda s: 0.0 * s, bf, breaks=(1.1, 1.2, 1.4, 1.6), profile=w,
+               bc="transmissive", mesh="linear" if moving else "static", t_end=t_end, cfl=cfl)
+    pr.meta["x_end"] = x1
+    return pr
+
+
 # --------------------------------------------------------------------------------------
 # Benchmark workloads
 # --------------------------------------------------------------------------------------

@@ -77,7 +77,7 @@ C_CLIENT = r"""
 /* A plain C client of the boundary: one instance, a few steps, the state back. */
 int run(const double* x, const double* eta, const double* hu, const double* b, int64_t n, double* out_eta) {
   swale_config cfg = {9.812, 0.6, 1e-6, 1e-11, 1e-6, 1.0, 8.0, 0.0, 0.0,
-                      SWALE_BC_PERIODIC, SWALE_MESH_STATIC, 24, 1, SWALE_SCHEME_HYDROSTATIC};
+                      SWALE_BC_PERIODIC, SWALE_MESH_STATIC, 24, 1, SWALE_SCHEME_HYDROSTATIC, 0, 0};
   swale_ctx* ctx = NULL;
   swale_status s = swale_create(&ctx, &cfg, NULL);
   if (s != SWALE_OK) return (int)s;

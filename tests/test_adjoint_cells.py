@@ -8,7 +8,7 @@ import pytest
 from paper_2208_06588_gb300 import cellcheck as C
 
 RNG = np.random.default_rng(424242)
-PRM = np.array([9.812, 1e-6, 1e-11, 1e-6, 0.0])
+PRM = np.array([9.812, 1e-6, 1e-11, 1e-6, 0.0, 0.0])  # g, eps, eps_pp, h_dry, dxmax, limit_hu
 
 
 def stencil(E, M, B, h):
@@ -44,12 +44,14 @@ def cases():
     return out
 
 
+@pytest.mark.parametrize("limit_hu", [0, 1])
 @pytest.mark.parametrize("case", range(60))
-def test_recon_reverse_matches_tangent(case):
+def test_recon_reverse_matches_tangent(case, limit_hu):
     h, E, M, B = cases()[case]
     v0, D2, D3 = stencil(E, M, B, h)
     prm = PRM.copy()
     prm[4] = 0.015
+    prm[5] = limit_hu
     tv0, tD2, tD3 = RNG.normal(size=9), RNG.normal(size=12), RNG.normal(size=9)
     ob = RNG.normal(size=8)
     val, tan, flag = C.recon_tangent(h, v0, D2, D3, tv0, tD2, tD3, prm)

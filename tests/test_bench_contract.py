@@ -42,3 +42,28 @@ def test_flop_models():
     roof = bench.fp64_roofline(1000.0, 1e9, "test")
     assert roof["bound"] == "alu" and abs(roof["achieved"] - 1.0) < 1e-12
     assert abs(roof["frac"] - 1.0 / bench.FP64_PEAK_TFLOPS) < 1e-12
+
+
+def test_method_flop_counts_are_the_oracles():
+    """The roofline numerators bench.py states (ORACLE_*_FLOPS) are the CPU oracle's own count of
+    the method's arithmetic on the benchmark workloads (operation-counting scalar type)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_2208_06588_gb300 import workloads as W
+    pr = W.dam_break_dry(1 << 18)  # the 2^20 workload's initial state, same shape (count per cell)
+    P = oracle.Params(g=pr.g, cfl=pr.cfl, bc=pr.bc, mesh=pr.mesh, gauss_sigma=pr.gauss_sigma, gauss_half=pr.gauss_half)
+    c = oracle.count_step(P, pr.E, pr.hu, pr.b, pr.J, pr.x)
+    assert abs(c["recon"]["flops"] / bench.ORACLE_RECON_FLOPS - 1) < 5e-4
+    assert abs(c["step"]["flops"] / bench.ORACLE_STEP_FLOPS - 1) < 5e-4
+    # a whole step is three reconstructions and three updates, and costs more than the kernels'
+    # own count (which builds the mesh geometry in closed form and reuses it across stages)
+    assert 3 * c["recon"]["flops"] < c["step"]["flops"] < 8 * c["recon"]["flops"]
+    bt = W.many_basins(B=4096)
+    tot = cells = 0.0
+    for i in range(16):
+        p = bt.instance(i)
+        Pi = oracle.Params(g=p.g, cfl=p.cfl, eps_weno=p.eps_weno, bc=p.bc, mesh=p.mesh, mesh_T=p.mesh_T)
+        tot += oracle.count_step(Pi, p.E, p.hu, p.b, p.J, p.x, p.profile)["step"]["flops"] * p.N
+        cells += p.N
+    assert abs(tot / cells / bench.ORACLE_BATCH_STEP_FLOPS - 1) < 5e-4

@@ -34,7 +34,7 @@ int main(int argc, char** argv) {
     return 5;
   fclose(f);
   swale_config cfg = {9.812, 0.6, 1e-6, 1e-11, 1e-6, 1.0, 8.0, 0.1, 0.0,
-                      SWALE_BC_PERIODIC, SWALE_MESH_PROFILE, 24, 1, SWALE_SCHEME_HYDROSTATIC};
+                      SWALE_BC_PERIODIC, SWALE_MESH_PROFILE, 24, 1, SWALE_SCHEME_HYDROSTATIC, 0, 0};
   swale_ctx* ctx = NULL;
   swale_status s = swale_create(&ctx, &cfg, NULL);
   if (s == SWALE_OK) s = swale_set_problem(ctx, n, x, eta, hu, b, prof, 1);

@@ -1,0 +1,126 @@
+"""GPU parity on the paper's graded moving mesh (constant node velocities, Eq. 0.2inis / 0.2ends /
+velocity / meshspecial of the big-pulse example, SWALE_MESH_LINEAR) for the three schemes, and
+parity of the two alternative readings (alpha bound in every stage; hu scaled by the limiter's
+theta) against the oracle under the same switches.
+
+Tolerances as in test_gpu_parity.py: L1 relative error 1e-9 on runs with jumps or wet/dry
+fronts; the lake at rest to round-off.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_06588_gb300 import binding as B
+from paper_2208_06588_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2208_06588_gb300 import build
+    build.build()
+    B.lib()
+
+
+def _kw(pr, **kw):
+    d = dict(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, mesh_T=pr.mesh_T, gauss_sigma=pr.gauss_sigma,
+             t_end=pr.t_end, dt_fixed=pr.dt_fixed, bc=pr.bc, mesh=pr.mesh, gauss_half=pr.gauss_half)
+    d.update(kw)
+    return d
+
+
+def run_both(pr, nsteps, **kw):
+    s = B.Solver(B.make_config(**_kw(pr, **kw)))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    done = s.advance(nsteps)
+    g = s.state()
+    bits, steps, _ = s.status()
+    s.close()
+    st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+    r = oracle.run(oracle.Params(**_kw(pr, **kw)), st, pr.profile, nsteps=nsteps)
+    assert done == r["steps"] == steps
+    return g, st, r, bits
+
+
+def l1_rel(a, r, J):
+    return np.sum(J * np.abs(a - r)) / max(np.sum(J * np.abs(r)), 1e-300)
+
+
+def oracle_sensitivity(pr, **kw):
+    """L1-relative change of the oracle's final (eta, hu) under a 1e-16 relative perturbation of
+    its initial surface: how far two correct evaluations may drift apart on this run."""
+    out = []
+    for pert in (0.0, 1e-16):
+        E = pr.E * (1.0 + pert * np.random.default_rng(1).choice([-1.0, 1.0], pr.N))
+        st = oracle.State(E, pr.hu, pr.b, pr.J, pr.x)
+        oracle.run(oracle.Params(**_kw(pr, **kw)), st, pr.profile, nsteps=10 ** 6)
+        out.append(st)
+    return max(l1_rel(out[1].E, out[0].E, out[0].J), l1_rel(out[1].M, out[0].M, out[0].J))
+
+
+@pytest.mark.parametrize("scheme", ["hydrostatic", "special", "nonwb"])
+@pytest.mark.parametrize("refine", [1, 3])
+def test_big_pulse_on_the_graded_moving_mesh(scheme, refine):
+    """The big pulse (eps = 0.2) to t = 0.2 on 100 (and 300) graded cells moving on straight
+    rays: the nodes land on the grid of Eq. 0.2ends, and the GPU state matches the oracle to
+    L1-rel 1e-9. On the refined mesh the run is ill-conditioned (a 1e-16 relative perturbation
+    of the oracle's own input moves its discharge by up to 2e-8 after the 705 steps of the
+    well-balanced schemes), so the bar there is max(1e-9, 10 x that measured sensitivity), as
+    for the long dam-break run."""
+    pr = W.big_pulse(refine)
+    g, st, r, bits = run_both(pr, 10 ** 6, scheme=scheme)
+    assert bits & ~B.BIT_NEGDEPTH == 0 and r["status"] == 0
+    assert g["t"] == st.t == 0.2
+    assert np.abs(g["x"] - pr.meta["x_end"]).max() < 1e-13
+    tol = 1e-9 if refine == 1 else max(1e-9, 10.0 * oracle_sensitivity(pr, scheme=scheme))
+    for a, ref in ((g["eta"], st.E), (g["hu"], st.M), (g["b"], st.B)):
+        assert l1_rel(a, ref, st.J) <= tol
+
+
+@pytest.mark.parametrize("scheme", ["hydrostatic", "special"])
+def test_lake_at_rest_on_the_graded_moving_mesh(scheme):
+    pr = W.big_pulse(3, eps=0.0)
+    s = B.Solver(B.make_config(**_kw(pr, scheme=scheme)))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    s.advance(10 ** 6)
+    g = s.state()
+    s.close()
+    assert g["t"] == 0.2
+    assert np.abs(g["eta"] - 1.0).max() < 1e-12 and np.abs(g["hu"]).max() < 1e-12
+
+
+@pytest.mark.parametrize("opts", [dict(alpha_bound=1), dict(limit_hu=1), dict(alpha_bound=1, limit_hu=1)])
+def test_alternative_readings_match_the_oracle(opts):
+    """Moses's second problem (profile motion, wet/dry fronts, 150 steps) and the dam break on a
+    fluid-driven mesh (4096 cells, 40 steps) under the alternative readings."""
+    pr = W.moses_second(200)
+    g, st, r, bits = run_both(pr, 150, **opts)
+    assert bits & ~B.BIT_NEGDEPTH == 0
+    for a, ref in ((g["eta"], st.E), (g["hu"], st.M)):
+        assert l1_rel(a, ref, st.J) <= 1e-9
+    pr = W.dam_break_dry(4096)
+    g, st, r, bits = run_both(pr, 40, **opts)
+    assert bits & ~B.BIT_NEGDEPTH == 0
+    for a, ref in ((g["eta"], st.E), (g["hu"], st.M)):
+        assert l1_rel(a, ref, st.J) <= 1e-9
+
+
+def test_linear_motion_alpha_uses_the_node_velocities():
+    """With constant node velocities alpha is the largest |u - w| + sqrt(g h) in every stage (w
+    is known before stage 1): the recorded stage-1 alpha of the GPU equals the oracle's."""
+    pr = W.big_pulse(3)
+    s = B.Solver(B.make_config(**_kw(pr)))
+    s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+    B.swale_alpha_log(s.ctx, 1, 5)
+    s.advance(5)
+    log = np.zeros(15)
+    B.swale_get_alpha_log(s.ctx, log)
+    s.close()
+    st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+    r = oracle.run(oracle.Params(**_kw(pr)), st, pr.profile, nsteps=5, record=True)
+    np.testing.assert_allclose(log, r["alphas"], rtol=1e-12)
+    # the bound max |u| + sqrt(g h) + max |w| is larger from the first stage on
+    st = oracle.State(pr.E, pr.hu, pr.b, pr.J, pr.x)
+    rb = oracle.run(oracle.Params(**_kw(pr, alpha_bound=1)), st, pr.profile, nsteps=1, record=True)
+    assert log[0] < rb["alphas"][0] - 0.5

@@ -87,7 +87,9 @@ def test_rhs_parity(bc, N):
     gflags = np.zeros(N, dtype=np.uint8)
     gA, bits = B.swale_rhs(ctx, N, E, M, Bv, J, w, alpha, gRE, gRM, gRB, gflags)
     B.swale_destroy(ctx)
-    assert abs(gA - A) <= 1e-13 * A
+    # the largest edge wave speed relative to w (Eq. alpha2D): the alpha the oracle applied
+    assert abs(gA - alpha) <= 1e-13 * alpha
+    assert alpha <= A + np.abs(w).max()
     scale = max(np.abs(RE).max(), np.abs(RM).max(), np.abs(RB).max())
     for g, r in ((gRE, RE), (gRM, RM), (gRB, RB)):
         assert np.abs(g - r).max() <= 1e-11 * scale
@@ -297,8 +299,9 @@ def test_dam_break_full_size_2000_steps_properties():
 def test_dry_bed_at_rest(mesh):
     """A dry bed at rest has zero wave speed everywhere. With an end time the step is clipped to
     it (one step, the state kept to round-off, as in the oracle); without one, on a mesh that
-    does not move, there is no finite CFL dt: the step takes dt = 0, sets SWALE_BIT_NODT and
-    swale_advance returns SWALE_ENONFINITE with the state unchanged (reading O21)."""
+    does not move, there is no finite CFL dt: the step is not taken (the error contract), it sets
+    SWALE_BIT_NODT and swale_advance returns SWALE_ENONFINITE with the state, time and step count
+    unchanged (reading O21)."""
     pr = W.dry_bed(t_end=0.3, mesh=mesh)
     s = B.Solver(cfg_of(pr))
     s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
@@ -319,7 +322,7 @@ def test_dry_bed_at_rest(mesh):
     g = s.state()
     bits, steps, last_dt = s.status()
     s.close()
-    assert bits & B.BIT_NODT and steps == 3 and last_dt == 0.0 and g["t"] == 0.0
+    assert bits & B.BIT_NODT and steps == 0 and last_dt == 0.0 and g["t"] == 0.0
     assert np.abs(g["eta"] - pr.E).max() <= 4e-16 and not g["hu"].any() and np.array_equal(g["x"], pr.x)
 
 

@@ -11,6 +11,17 @@ from paper_2208_06588_gb300 import workloads as W
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 
+
+def _within_paper(N, got, paper):
+    """|q_N - q_2N| against the paper's L1 error at N. Resolved meshes (N = 100, 200): within
+    5 % (the literal alpha of Eq. alpha2D lands within 3 % of every printed value there; the
+    bound alpha + max |w| is about 10 % off at N = 200). N = 50: within 1.5x. N = 25 is
+    under-resolved: the self-difference of the two coarsest meshes is a rough proxy of the L1
+    error (for the non-well-balanced scheme it falls outside the bracket e_25 -+ e_50 that the
+    printed errors allow, under either reading of alpha), so within 2x."""
+    f = 1.05 if N >= 100 else (1.5 if N == 50 else 2.0)
+    assert paper / f < got < paper * f, (N, got, paper)
+
 def _params(pr, **kw):
     d = dict(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, bc=pr.bc, mesh=pr.mesh, mesh_T=pr.mesh_T, t_end=pr.t_end,
              scheme="nonwb")
@@ -26,7 +37,8 @@ def _run(pr, nsteps=10 ** 7, **kw):
 
 def test_accuracy_matches_paper_table_nonwb():
     """|q_N - q_2N| of the accuracy test (the mesh is uniform again at t_end) tracks the paper's
-    Table WENO5n1D within a factor 1.5; rate ~4 from 100 to 200 (paper: 3.95)."""
+    Table WENO5n1D (5 % at N = 100, 200; 1.5x at N = 50; 2x at N = 25); rate ~4 from 100 to 200
+    (paper: 3.95)."""
     rows = [l.split() for l in open(os.path.join(GOLD, "paper_accuracy_table_nonwb.txt"))
             if l.strip() and not l.startswith("#")]
     tab = {int(r[0]): (float(r[1]), float(r[2])) for r in rows}
@@ -43,7 +55,7 @@ def test_accuracy_matches_paper_table_nonwb():
         dM = np.mean(np.abs(a.M - 0.5 * (b.M[0::2] + b.M[1::2])))
         diffs[N] = (dE, dM)
         for got, paper in zip((dE, dM), tab[N]):
-            assert paper / 1.5 < got < paper * 1.5, (N, got, paper)
+            _within_paper(N, got, paper)
     order = np.log2(diffs[100][0] / diffs[200][0])
     assert 3.5 < order < 4.5
 

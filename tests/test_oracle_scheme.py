@@ -12,6 +12,17 @@ GOLD = os.path.join(os.path.dirname(__file__), "golden")
 G = 9.812
 
 
+
+def _within_paper(N, got, paper):
+    """|q_N - q_2N| against the paper's L1 error at N. Resolved meshes (N = 100, 200): within
+    5 % (the literal alpha of Eq. alpha2D lands within 3 % of every printed value there; the
+    bound alpha + max |w| is about 10 % off at N = 200). N = 50: within 1.5x. N = 25 is
+    under-resolved: the self-difference of the two coarsest meshes is a rough proxy of the L1
+    error (for the non-well-balanced scheme it falls outside the bracket e_25 -+ e_50 that the
+    printed errors allow, under either reading of alpha), so within 2x."""
+    f = 1.05 if N >= 100 else (1.5 if N == 50 else 2.0)
+    assert paper / f < got < paper * f, (N, got, paper)
+
 def _params(pr, **kw):
     d = dict(g=pr.g, cfl=pr.cfl, eps_weno=pr.eps_weno, bc=pr.bc, mesh=pr.mesh, mesh_T=pr.mesh_T, t_end=pr.t_end,
              gauss_sigma=pr.gauss_sigma, gauss_half=pr.gauss_half, dt_fixed=pr.dt_fixed)
@@ -33,7 +44,8 @@ def _table(name):
 def test_accuracy_matches_paper_table():
     """Sec. 5.1 accuracy test on the paper's moving mesh: |q_N - q_2N| (the mesh is uniform
     again at t_end, so coarse cells are unions of two fine cells) tracks the paper's L1
-    errors of Table WENO5h1D within a factor 1.5, and the rate from 100 to 200 is ~4."""
+    errors of Table WENO5h1D (within 5 % on the resolved meshes N = 100, 200, 1.5x at N = 50, 2x at
+    N = 25), and the rate from 100 to 200 is ~4."""
     tab = {int(r[0]): (float(r[1]), float(r[2])) for r in _table("paper_accuracy_table.txt")}
     res = {}
     for N in (25, 50, 100, 200, 400):
@@ -50,7 +62,7 @@ def test_accuracy_matches_paper_table():
         dM = np.mean(np.abs(a.M - 0.5 * (b.M[0::2] + b.M[1::2])))
         diffs[N] = (dE, dM)
         for got, paper in zip((dE, dM), tab[N]):
-            assert paper / 1.5 < got < paper * 1.5, (N, got, paper)
+            _within_paper(N, got, paper)
     order = np.log2(diffs[100][0] / diffs[200][0])
     assert 3.5 < order < 4.5  # paper: 3.94 at N = 200
 

@@ -13,6 +13,17 @@ RNG = np.random.default_rng(20220812 + 77)
 T_GLO = (0.5 - 0.5 / np.sqrt(5.0), 0.5 + 0.5 / np.sqrt(5.0))
 
 
+
+def _within_paper(N, got, paper):
+    """|q_N - q_2N| against the paper's L1 error at N. Resolved meshes (N = 100, 200): within
+    5 % (the literal alpha of Eq. alpha2D lands within 3 % of every printed value there; the
+    bound alpha + max |w| is about 10 % off at N = 200). N = 50: within 1.5x. N = 25 is
+    under-resolved: the self-difference of the two coarsest meshes is a rough proxy of the L1
+    error (for the non-well-balanced scheme it falls outside the bracket e_25 -+ e_50 that the
+    printed errors allow, under either reading of alpha), so within 2x."""
+    f = 1.05 if N >= 100 else (1.5 if N == 50 else 2.0)
+    assert paper / f < got < paper * f, (N, got, paper)
+
 def _avg_matrix(nodes, deg):
     """A[i, k]: average of x^k over [nodes[i], nodes[i+1]] (numpy, exact antiderivatives)."""
     a, b = nodes[:-1], nodes[1:]
@@ -105,7 +116,7 @@ def test_accuracy_matches_paper_table_special():
         dM = np.mean(np.abs(a.M - 0.5 * (b.M[0::2] + b.M[1::2])))
         diffs[N] = (dE, dM)
         for got, paper in zip((dE, dM), tab[N]):
-            assert paper / 1.5 < got < paper * 1.5, (N, got, paper)
+            _within_paper(N, got, paper)
     assert 3.5 < np.log2(diffs[100][0] / diffs[200][0]) < 4.5
 
 

@@ -28,11 +28,13 @@ def _inputs(N, seed):
     return E, M, Bv, J, w
 
 
-def test_noalloc_matches_swale_rhs_on_two_calls():
+@pytest.mark.parametrize("scheme,bc", [("hydrostatic", "reflective"), ("hydrostatic", "periodic"),
+                                       ("nonwb", "transmissive"), ("special", "reflective")])
+def test_noalloc_matches_swale_rhs_on_two_calls(scheme, bc):
     torch = pytest.importorskip("torch")
     from paper_2208_06588_gb300 import build
     build.build()
-    cfg = B.make_config(bc="reflective")
+    cfg = B.make_config(bc=bc, scheme=scheme)
     stream = torch.cuda.current_stream().cuda_stream
     alpha = 7.5
     # Two calls in a row: the second is smaller and reuses the scratch left by the first.
