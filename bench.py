@@ -32,12 +32,16 @@ UNIT = "cell-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
 # DRAM bytes (read + write) of a k_recon launch on this workload, averaged over the three
 # stages, from one ncu capture of the current kernels (the autotuner's 128-cell tiles, staged by
-# bulk copies): stage 1 reads the cached mesh geometry, 33 values per cell (293.7 + 65.7 MB),
-# stage 2 writes it (33.6 + 304.2 MB), stage 3 does neither (33.6 + 24.4 MB).
-RECON_DRAM_BYTES = (293_681_920 + 65_746_176 + 33_622_016 + 304_172_032 + 33_615_104 + 24_387_840) // 3
+# bulk copies): stage 1 reads the cached mesh geometry, 33 values per cell (302.2 + 67.2 MB),
+# stage 2 writes it (42.0 + 301.7 MB), stage 3 does neither (42.1 + 27.6 MB).
+RECON_DRAM_BYTES = (302_180_864 + 67_237_888 + 42_000_384 + 301_660_160 + 42_083_584 + 27_560_448) // 3
 # Fraction of cycles the FP64 pipe was busy during the same k_recon launches (ncu
 # sm__pipe_fp64_cycles_active, the three stages): the kernel is bound by FP64 instruction issue.
-RECON_FP64_PIPE_ACTIVE = (0.7768 + 0.8648 + 0.8703) / 3
+RECON_FP64_PIPE_ACTIVE = (0.7943 + 0.8649 + 0.8687) / 3
+# FP64 FLOP equivalents per cell the same launches executed (ncu dadd + dmul + 2 dfma
+# instructions over the 2^20 cells; stages 1, 2, 3): what the hardware did, beside the method's
+# and the kernels' own counts.
+RECON_EXECUTED_FLOPS = (179.4 + 279.8 + 274.5) / 3
 # The method's FP64 operations per cell, counted by the CPU oracle on an operation-counting
 # scalar type (oracle.count_step; tests/test_bench_contract.py recounts them): the arithmetic on
 # state-dependent values of one stage's reconstruction + limiter, and of one whole SSP-RK3 step,
@@ -774,6 +778,10 @@ def main():
             "kernel_count": {"flops_per_cell": kernel_flops_cell,
                              "frac": kernel_flops_cell * per_s / 1e12 / FP64_PEAK_TFLOPS},
             "ncu_fp64_pipe_active": RECON_FP64_PIPE_ACTIVE if dom == "reconstruction" else None,
+            "executed": {"flops_per_cell": RECON_EXECUTED_FLOPS,
+                         "frac": RECON_EXECUTED_FLOPS * per_s / 1e12 / FP64_PEAK_TFLOPS,
+                         "source": "ncu dadd + dmul + 2 dfma per cell of one step's k_recon launches"}
+            if dom == "reconstruction" else None,
             "avg_launch_ms": ms_dom / n_dom,
             "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA chain: 1.195 TFLOP/s)",
             "kernel_ms_share": {k: round(v[0] / max(sum(x[0] for x in fam.values()), 1e-30), 4)

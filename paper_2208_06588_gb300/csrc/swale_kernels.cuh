@@ -274,7 +274,21 @@ __device__ __forceinline__ double block_wave(double g, bool useL, bool useR, dou
   const bool cl = useL && fl >= thr, cr = useR && fr >= thr;
   double wave = 0.0;
   const bool c1 = cl || cr;
-  if (__any_sync(0xffffffffu, c1)) {
+  const unsigned cand = __ballot_sync(0xffffffffu, c1);
+  if (cand) {
+    // Flat water: when every candidate edge of the warp holds the same (h, u) bit for bit, one
+    // evaluation gives the exact maximum of them all.
+    const bool r0 = cr && !cl;
+    const int src = __ffs(cand) - 1;
+    const unsigned long long hb = dbits(__shfl_sync(0xffffffffu, r0 ? hR : hL, src));
+    const unsigned long long ub = dbits(__shfl_sync(0xffffffffu, r0 ? uR : uL, src));
+    const bool same = (!cl || (dbits(hL) == hb && dbits(uL) == ub)) && (!cr || (dbits(hR) == hb && dbits(uR) == ub));
+    if (__all_sync(0xffffffffu, same)) {
+      const double w0 = swale::wave_speed(g, bitsd(hb), bitsd(ub));
+      return c1 ? w0 : 0.0;
+    }
+  }
+  if (cand) {
     const bool right = cr && (!cl || fr > fl);
     const double w1 = swale::wave_speed(g, right ? hR : hL, right ? uR : uL);
     wave = c1 ? w1 : 0.0;
