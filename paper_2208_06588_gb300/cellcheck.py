@@ -34,6 +34,8 @@ def lib():
         build()
         _lib = ctypes.CDLL(_LIB)
         _lib.ct_recon_tangent.restype = ctypes.c_int
+        _lib.ct_f32_trunc.restype = ctypes.c_float
+        _lib.ct_f32_trunc.argtypes = [ctypes.c_double]
     return _lib
 
 
@@ -83,3 +85,18 @@ def source_adjoint(hd, bd, geom, g, Sb):
     lib().ct_source_adjoint(*map(_p, (f64(hd), f64(bd), f64(geom))), ctypes.c_double(g), ctypes.c_double(Sb),
                             _p(hdb), _p(bdb))
     return hdb, bdb
+
+
+def smooth_test(F, c4, c3, D2h, D3h, D2m, D3m, eps=1e-6):
+    """(FP32 test says surely smooth, FP64 class, FP64 indicators) of one cell's data."""
+    out = np.zeros(2, dtype=np.int32)
+    b = np.zeros(3)
+    f = ctypes.c_double
+    arrs = [f64(x) for x in (F, D2h, D3h, D2m, D3m)]  # kept alive across the call
+    lib().ct_smooth_test(_p(arrs[0]), f(c4), f(c3), *map(_p, arrs[1:]), f(eps), _p(out), _p(b))
+    return bool(out[0]), int(out[1]), b
+
+
+def f32_trunc(x):
+    """The device's double -> float conversion (toward zero, on the integer pipe), host build."""
+    return lib().ct_f32_trunc(float(x))

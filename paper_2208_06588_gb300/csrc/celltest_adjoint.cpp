@@ -44,4 +44,43 @@ void ct_source_adjoint(const double* hd, const double* bd, const double* geom, d
   swale::source_cell_rev(g, hd, bd, sg, Sb, hdb, bdb);
 }
 
+// f32_trunc on the host (the device's double -> float conversion on the integer pipe).
+float ct_f32_trunc(double x) { return swale::f32_trunc(x); }
+
+// The device's FP32 smooth-class test and the FP64 class of the same indicators. in: F[3], c4,
+// c3 (mesh factors), D2h[3], D3h[3], D2m[3], D3m[3] (divided differences of h and hu on the
+// sub-stencils starting at cells j-2 .. j), eps. out[0]: the FP32 test (1: surely smooth),
+// out[1]: the FP64 class (shared_beta + hybrid_phi), outb[3]: the FP64 indicators.
+void ct_smooth_test(const double* F, double c4, double c3, const double* D2h, const double* D3h, const double* D2m,
+                    const double* D3m, double eps, int* out, double* outb) {
+  float F32[3], d2h[3], d3h[3], d2m[3], d3m[3];
+  for (int a = 0; a < 3; ++a) {
+    F32[a] = swale::f32_trunc(F[a]);
+    d2h[a] = swale::f32_trunc(D2h[a]);
+    d3h[a] = swale::f32_trunc(D3h[a]);
+    d2m[a] = swale::f32_trunc(D2m[a]);
+    d3m[a] = swale::f32_trunc(D3m[a]);
+  }
+  out[0] = swale::sure_smooth_f32(F32, swale::f32_trunc(c4), swale::f32_trunc(c3), d2h, d3h, d2m, d3m,
+                                  swale::f32_trunc(eps)) ? 1 : 0;
+  swale::CellGeom G{};
+  for (int a = 0; a < 3; ++a) G.F[a] = F[a];
+  G.c4 = c4;
+  G.c3 = c3;
+  for (int e = 0; e < 2; ++e)
+    for (int r = 0; r < 3; ++r) G.d[e][r] = 1.0 / 3.0;
+  swale::StencilDD DD{};
+  for (int a = 0; a < 3; ++a) {
+    DD.D2[2][a] = D2h[a];
+    DD.D3[2][a] = D3h[a];
+    DD.D2[1][a] = D2m[a];
+    DD.D3[1][a] = D3m[a];
+  }
+  double beta[3], phi[2][3];
+  swale::shared_beta(G, DD, beta);
+  swale::SchemeConst P{9.812, eps, 1e-11, 1e-6, 1, 0};
+  out[1] = swale::hybrid_phi(P, beta, G.d, phi);
+  for (int r = 0; r < 3; ++r) outb[r] = beta[r];
+}
+
 }  // extern "C"

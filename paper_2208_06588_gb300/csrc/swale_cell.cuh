@@ -14,6 +14,8 @@
 //      d_2 = (y4-y3)(y5-y3) / ((y4-y0)(y5-y0)),  d_0 = (y3-y1)(y3-y0) / ((y5-y1)(y5-y0)).
 //  * Step 2: beta_r = Dx int (p_r')^2 + Dx^3 int (p_r'')^2 in closed form about the cell
 //    midpoint; the classes come from comparing tau with (beta^A + eps) and (beta^A + eps)/2.
+//    On the device the smooth class is first tested in FP32 with an error bound
+//    (sure_smooth_f32); the FP64 indicators are formed where that test cannot decide.
 //  * Step 3: reciprocals of products stand in for several divisions (one division each).
 //  * Sec. 4.1 source: the quartic interpolants (three averages + two edge values) are the
 //    derivative of a confluent Newton (Hermite) form of their primitive, brought to monomial
@@ -21,7 +23,9 @@
 //    four-point Gauss-Legendre rule of the definition is exact for that degree too).
 #pragma once
 
+#include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #if defined(__CUDACC__)
 #define SWALE_HD __host__ __device__ __forceinline__
@@ -118,6 +122,68 @@ SWALE_HD real dsqrt(real a) { return swale_sqrt(a); }
 SWALE_HD real dsqrt(real a) { return sqrt(a); }
 #endif
 #endif
+
+// Double to float on the integer pipe: the top 23 mantissa bits (rounded toward zero, relative
+// error below 2^-23), magnitudes below the normal float range to a signed zero, above it (and
+// infinities, NaNs) to a signed infinity. The hardware conversion instruction runs on the FP64
+// pipe of GB300 at the DFMA rate (measured), which is the bottleneck of the stage kernels.
+SWALE_HD float f32_trunc(double x) {
+#if defined(__CUDA_ARCH__)
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+#else
+  uint64_t b;
+  memcpy(&b, &x, 8);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+#endif
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // the float's biased exponent (1023 - 127 = 896)
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned mag = e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : (((unsigned)e << 23) | mant));
+  const unsigned r = sign | mag;
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(r);
+#else
+  float f;
+  memcpy(&f, &r, 4);
+  return f;
+#endif
+}
+
+// ------------------------------------------------------------------------------------
+// The smooth class decided in FP32 (Step 2 with the shared indicators of Eq. alphamodified).
+// GB300 runs FP32 at about 40x its FP64 rate, and in most cells the detector only has to tell
+// that gamma is far below 1/2. The indicators beta_r = c4 (qh^2 + qm^2) + c3 (D3h^2 + D3m^2),
+// q = D2 + D3 F, are evaluated in FP32 from FP32 copies of their inputs, beside their
+// magnitudes m_r = c4 (Qh^2 + Qm^2) + c3 (D3h^2 + D3m^2), Q = |D2| + |D3| |F|. A rounding-error
+// analysis of these few operations (inputs rounded once, FMAs, no cancellation in sums of
+// non-negative terms) bounds |beta_r(FP32) - beta_r| by 14 u m_r, u = 2^-24; E below takes
+// 64 u (m_0 + m_1 + m_2), which also covers the FP64 evaluation's own rounding (below 2^-48 m),
+// plus a 1e-30 floor for inputs that fall below the FP32 range. If
+//   tau32 + E <= (den32 - E) / 2,   tau = |beta_0 - beta_2|, den = mean(beta) + eps,
+// (with 8 u of relative slack on tau32 and den32) then the FP64 detector finds gamma <= 1/2 as
+// well, and the cell is smooth. Overflow or NaN make the test false, as does anything closer to
+// the threshold: the FP64 indicators then decide, as before.
+// ------------------------------------------------------------------------------------
+SWALE_HD bool sure_smooth_f32(const float F[3], float c4, float c3, const float d2h[3],
+                                                const float d3h[3], const float d2m[3], const float d3m[3],
+                                                float eps) {
+  float b[3], msum = 0.0f;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int a = 2 - r;
+    const float qh = fmaf(d3h[a], F[a], d2h[a]), qm = fmaf(d3m[a], F[a], d2m[a]);
+    const float Qh = fmaf(fabsf(d3h[a]), fabsf(F[a]), fabsf(d2h[a]));
+    const float Qm = fmaf(fabsf(d3m[a]), fabsf(F[a]), fabsf(d2m[a]));
+    const float s2 = fmaf(d3h[a], d3h[a], d3m[a] * d3m[a]);
+    b[r] = fmaf(c4, fmaf(qh, qh, qm * qm), c3 * s2);
+    msum += fmaf(c4, fmaf(Qh, Qh, Qm * Qm), c3 * s2);
+  }
+  constexpr float u = 5.9604645e-8f;  // 2^-24
+  const float tau = fabsf(b[0] - b[2]);
+  const float den = (b[0] + b[1] + b[2]) * (1.0f / 3.0f) + eps;
+  const float E = (64.0f * u) * msum + 1e-30f;
+  return tau * (1.0f + 8.0f * u) + E <= 0.5f * (den * (1.0f - 8.0f * u) - E);
+}
 
 // Wave speed |u| + sqrt(g max(h, 0)) of one limited edge state (Eq. alpha2D).
 SWALE_HD real wave_speed(real g, real h, real u) { return dabs(u) + dsqrt(g * pos0(h)); }
@@ -343,12 +409,18 @@ SWALE_HD void shared_beta(const CellGeom& G, const StencilDD& DD, real beta[3]) 
   }
 }
 
+// known_smooth: the caller has established the smooth class already (the device's FP32 test,
+// which implies gamma <= 1/2 for the FP64 indicators), so they are not formed.
 SWALE_HD void recon_cell_g(const SchemeConst& P, const CellGeom& G, const real v0[3][3], const StencilDD& DD,
-                           EdgeState& o, uint8_t& flag, uint32_t& st) {
-  real beta[3];
-  shared_beta(G, DD, beta);
+                           EdgeState& o, uint8_t& flag, uint32_t& st, bool known_smooth = false) {
   real phi[2][3];
-  flag = hybrid_phi(P, beta, G.d, phi);
+  if (known_smooth) {
+    flag = 0;
+  } else {
+    real beta[3];
+    shared_beta(G, DD, beta);
+    flag = hybrid_phi(P, beta, G.d, phi);
+  }
   // Edge values of eta, hu, h with the shared weights (Step 4); the smooth class through the
   // linear form of smooth_edge_coeffs.
   real ev[3][2];
@@ -503,11 +575,18 @@ SWALE_HD void point_phi(const SchemeConst& P, const real d[3], const real beta[3
 //   d_0 = (dx_0 dx_1 + (dx_0 + dx_1) R_5) / ((y5-y1)(y5-y0)), R_5 = dx2 dx3 dx4 / (dx3 dx4 + dx2 dx4 + dx2 dx3),
 //   d_1 = 1 - d_0 - d_2 (at x = y3 they reduce to the edge weights).
 SWALE_HD void recon_cell_special_g(const SchemeConst& P, const CellGeom& G, const real h[5], const real v0[3][3],
-                                   const StencilDD& DD, EdgeState& o, uint8_t& flag, uint32_t& st, real etaG[2]) {
-  real beta[3];
-  shared_beta(G, DD, beta);
+                                   const StencilDD& DD, EdgeState& o, uint8_t& flag, uint32_t& st, real etaG[2],
+                                   bool known_smooth = false) {
+  real beta[3] = {real(0.0), real(0.0), real(0.0)};
   real phi[2][3];
-  flag = hybrid_phi(P, beta, G.d, phi);
+  if (known_smooth) {  // the smooth class established by the caller (see recon_cell_g)
+    flag = 0;
+    for (int e = 0; e < 2; ++e)
+      for (int r = 0; r < 3; ++r) phi[e][r] = G.d[e][r];
+  } else {
+    shared_beta(G, DD, beta);
+    flag = hybrid_phi(P, beta, G.d, phi);
+  }
   real ev[3][2];
   for (int v = 0; v < 3; ++v)
     for (int e = 0; e < 2; ++e) ev[v][e] = edge_value(G, phi, v0[v], DD.D2[v], DD.D3[v], e);

@@ -210,6 +210,7 @@ __device__ __noinline__ double bottom_average(const StepConst& K, double a, doub
 }
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
 
 // Block-wide max / min of non-negative doubles, one atomicMax / atomicMin per block. The bit
@@ -260,9 +261,9 @@ template <int T>
 __device__ __forceinline__ double block_wave(double g, bool useL, bool useR, double hL, double uL, double hR,
                                              double uR) {
   __shared__ unsigned int wmax[T / 32];
-  const float gf = (float)g;
-  const float fl = useL ? fabsf((float)uL) + __fsqrt_rn(gf * fmaxf((float)hL, 0.0f)) : 0.0f;
-  const float fr = useR ? fabsf((float)uR) + __fsqrt_rn(gf * fmaxf((float)hR, 0.0f)) : 0.0f;
+  const float gf = swale::f32_trunc(g);
+  const float fl = useL ? fabsf(swale::f32_trunc(uL)) + __fsqrt_rn(gf * fmaxf(swale::f32_trunc(hL), 0.0f)) : 0.0f;
+  const float fr = useR ? fabsf(swale::f32_trunc(uR)) + __fsqrt_rn(gf * fmaxf(swale::f32_trunc(hR), 0.0f)) : 0.0f;
   const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fl, fr)));
   if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
   __syncthreads();
@@ -465,6 +466,11 @@ __global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, c
   __shared__ double sJ[T + 4], sV[3][T + 4];    // cells c0-2 .. c0+T+1
   __shared__ double sIP[T + 3], sD2[3][T + 3];  // pairs starting at those cells
   __shared__ double sIT[T + 2], sD3[3][T + 2];  // triples centred at cells c0-1 .. c0+T
+  // FP32 copies of the divided differences of hu and h for the FP32 smooth-class test (the
+  // well-balanced schemes: the shared indicators of h and hu)
+  constexpr bool kF32 = SCHEME != 1;
+  constexpr int TF = kF32 ? T : 0;
+  __shared__ float sD2f[2][TF + 3], sD3f[2][TF + 2];
   __shared__ __align__(16) double sRaw[4][T + 8];  // E, M, B, J of those cells as bulk-copied
   __shared__ __align__(8) uint64_t sBar;           // completion of the tile's bulk copies
   __shared__ __align__(8) uint64_t sPad;           // test hook: a barrier no copy completes
@@ -556,15 +562,25 @@ __global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, c
     for (int i = tid; i < T + 3; i += T) {
       const double ip = swale::pair_recip(sJ[i], sJ[i + 1]);
       sIP[i] = ip;
+      double d2[3];
 #pragma unroll
-      for (int v = 0; v < 3; ++v) sD2[v][i] = swale::pair_dd(sV[v][i], sV[v][i + 1], ip);
+      for (int v = 0; v < 3; ++v) sD2[v][i] = d2[v] = swale::pair_dd(sV[v][i], sV[v][i + 1], ip);
+      if (kF32) {
+        sD2f[0][i] = swale::f32_trunc(d2[1]);
+        sD2f[1][i] = swale::f32_trunc(d2[2]);
+      }
     }
     __syncthreads();
     for (int i = tid; i < T + 2; i += T) {
       const double it = swale::triple_recip(sJ[i], sJ[i + 1], sJ[i + 2]);
       sIT[i] = it;
+      double d3[3];
 #pragma unroll
-      for (int v = 0; v < 3; ++v) sD3[v][i] = swale::triple_dd(sD2[v][i], sD2[v][i + 1], it);
+      for (int v = 0; v < 3; ++v) sD3[v][i] = d3[v] = swale::triple_dd(sD2[v][i], sD2[v][i + 1], it);
+      if (kF32) {
+        sD3f[0][i] = swale::f32_trunc(d3[1]);
+        sD3f[1][i] = swale::f32_trunc(d3[2]);
+      }
     }
     __syncthreads();
     const int64_t c = c0 + tid;
@@ -615,9 +631,24 @@ __global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, c
       EdgeState o;
       uint8_t flag;
       double etaG[2] = {0.0, 0.0};
-      if (SCHEME == 1) swale::recon_cell_nonwb_g(K.sc, G, v0, DD, o, flag, st);
-      else if (SCHEME == 2) swale::recon_cell_special_g(K.sc, G, h, v0, DD, o, flag, st, etaG);
-      else swale::recon_cell_g(K.sc, G, v0, DD, o, flag, st);
+      if (SCHEME == 1) {
+        swale::recon_cell_nonwb_g(K.sc, G, v0, DD, o, flag, st);
+      } else {
+        // The smooth class, when FP32 can tell it for sure; else the FP64 detector decides.
+        float F32[3], d2h[3], d3h[3], d2m[3], d3m[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          F32[a] = swale::f32_trunc(G.F[a]);
+          d2h[a] = sD2f[1][tid + a];
+          d3h[a] = sD3f[1][tid + a];
+          d2m[a] = sD2f[0][tid + a];
+          d3m[a] = sD3f[0][tid + a];
+        }
+        const bool smooth32 = swale::sure_smooth_f32(F32, swale::f32_trunc(G.c4), swale::f32_trunc(G.c3), d2h, d3h,
+                                                     d2m, d3m, swale::f32_trunc(K.sc.eps_weno));
+        if (SCHEME == 2) swale::recon_cell_special_g(K.sc, G, h, v0, DD, o, flag, st, etaG, smooth32);
+        else swale::recon_cell_g(K.sc, G, v0, DD, o, flag, st, smooth32);
+      }
       D.eEL[idx] = o.EL;
       D.eER[idx] = o.ER;
       D.eBL[idx] = o.BL;
