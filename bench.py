@@ -32,16 +32,16 @@ UNIT = "cell-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
 # DRAM bytes (read + write) of a k_recon launch on this workload, averaged over the three
 # stages, from one ncu capture of the current kernels (the autotuner's 128-cell tiles, staged by
-# bulk copies): stage 1 reads the cached mesh geometry, 33 values per cell (302.2 + 67.2 MB),
-# stage 2 writes it (42.0 + 301.7 MB), stage 3 does neither (42.1 + 27.6 MB).
-RECON_DRAM_BYTES = (302_180_864 + 67_237_888 + 42_000_384 + 301_660_160 + 42_083_584 + 27_560_448) // 3
+# bulk copies): stage 1 reads the cached mesh geometry, 33 values per cell (302.4 + 68.6 MB),
+# stage 2 writes it (42.0 + 302.3 MB), stage 3 does neither (42.0 + 27.8 MB).
+RECON_DRAM_BYTES = (302_441_472 + 68_557_568 + 42_029_824 + 302_268_416 + 42_001_408 + 27_838_976) // 3
 # Fraction of cycles the FP64 pipe was busy during the same k_recon launches (ncu
 # sm__pipe_fp64_cycles_active, the three stages): the kernel is bound by FP64 instruction issue.
-RECON_FP64_PIPE_ACTIVE = (0.7943 + 0.8649 + 0.8687) / 3
+RECON_FP64_PIPE_ACTIVE = (0.6930 + 0.8558 + 0.8603) / 3
 # FP64 FLOP equivalents per cell the same launches executed (ncu dadd + dmul + 2 dfma
 # instructions over the 2^20 cells; stages 1, 2, 3): what the hardware did, beside the method's
 # and the kernels' own counts.
-RECON_EXECUTED_FLOPS = (179.4 + 279.8 + 274.5) / 3
+RECON_EXECUTED_FLOPS = (131.5 + 233.7 + 228.0) / 3
 # The method's FP64 operations per cell, counted by the CPU oracle on an operation-counting
 # scalar type (oracle.count_step; tests/test_bench_contract.py recounts them): the arithmetic on
 # state-dependent values of one stage's reconstruction + limiter, and of one whole SSP-RK3 step,
@@ -53,6 +53,12 @@ RECON_EXECUTED_FLOPS = (179.4 + 279.8 + 274.5) / 3
 ORACLE_RECON_FLOPS = 318.60
 ORACLE_STEP_FLOPS = 1891.80
 ORACLE_BATCH_STEP_FLOPS = 1893.17
+# The same counts for the scheme variants on the dam-break workload (reconstruction, step).
+ORACLE_VARIANT_FLOPS = {"nonwb": (583.01, 2613.02), "special": (366.61, 1780.82)}
+# DRAM bytes per k_update launch (stages 1, 2, 3: 159.5 + 41.3, 184.7 + 70.1, 184.7 + 52.5 MB) and
+# FP64 FLOP equivalents per cell the update launches executed (ncu, as for k_recon below).
+UPDATE_DRAM_BYTES = (159_465_984 + 41_309_184 + 184_676_096 + 70_060_288 + 184_729_600 + 52_483_072) // 3
+UPDATE_EXECUTED_FLOPS = (200.2 + 207.2 + 219.2) / 3
 
 
 def parse():
@@ -554,12 +560,17 @@ def bench_variant(args, stream, pr, scheme="hydrostatic", bottom=None):
     B.swale_destroy(ctx)
     oc = opcount.count_stage(pr.E, pr.hu, pr.b, pr.J, bc=pr.bc, sample=1 << 16, scheme=scheme)
     dom = "reconstruction" if fam["reconstruction"][0] >= fam["update"][0] else "update"
-    fl = oc["recon_flops"] - oc["geom_flops"] / 3.0 if dom == "reconstruction" else oc["update_flops"]
+    kfl = oc["recon_flops"] - oc["geom_flops"] / 3.0 if dom == "reconstruction" else oc["update_flops"]
+    o_rec, o_step = ORACLE_VARIANT_FLOPS.get(scheme, (ORACLE_RECON_FLOPS, ORACLE_STEP_FLOPS))
+    fl = (o_rec + oc["geom_flops"]) if dom == "reconstruction" else (o_step - 3.0 * o_rec) / 3.0 + oc["source_geom_flops"]
     ms_dom, n_dom = fam[dom]
-    achieved = fl * pr.N / (ms_dom / n_dom * 1e-3) / 1e12
+    per_s = pr.N / (ms_dom / n_dom * 1e-3)
+    achieved = fl * per_s / 1e12
     return {"value": pr.N * K / (ms * 1e-3), "unit": UNIT, "steps": K, "ms_per_step": ms / K, "status_bits": bits,
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_cell": fl,
+                         "flops_basis": "method (CPU oracle count + mesh-only geometry)",
+                         "kernel_count": {"flops_per_cell": kfl, "frac": kfl * per_s / 1e12 / FP64_PEAK_TFLOPS},
                          "avg_launch_ms": ms_dom / n_dom},
             "fp64_flops_per_cell_stage": {"recon": oc["recon_flops"], "update": oc["update_flops"]}}
 
@@ -769,19 +780,20 @@ def main():
     achieved = flops_cell * per_s / 1e12
     roof = {"bound": "alu", "kernel": f"k_{'recon' if dom == 'reconstruction' else 'update'} (per stage)",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": RECON_DRAM_BYTES if dom == "reconstruction" else None,
-            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum of k_recon, "
-                            "N = 2^20, 128-cell tiles, mean of the three stages)",
+            "traffic": RECON_DRAM_BYTES if dom == "reconstruction" else UPDATE_DRAM_BYTES,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum of the kernel, "
+                            "N = 2^20, the autotuned tiles, mean of the three stages)",
             "flops_per_cell": flops_cell, "cells_per_launch": N,
             "flops_basis": "method: the CPU oracle's count of the state arithmetic (operation-counting scalar) "
-                           "+ the mesh-only geometry in closed form",
+                           "+ the mesh-only geometry in closed form; the kernels reach the same result with fewer "
+                           "operations (kernel_count, executed), so this fraction can exceed the hardware's",
             "kernel_count": {"flops_per_cell": kernel_flops_cell,
                              "frac": kernel_flops_cell * per_s / 1e12 / FP64_PEAK_TFLOPS},
-            "ncu_fp64_pipe_active": RECON_FP64_PIPE_ACTIVE if dom == "reconstruction" else None,
-            "executed": {"flops_per_cell": RECON_EXECUTED_FLOPS,
-                         "frac": RECON_EXECUTED_FLOPS * per_s / 1e12 / FP64_PEAK_TFLOPS,
-                         "source": "ncu dadd + dmul + 2 dfma per cell of one step's k_recon launches"}
-            if dom == "reconstruction" else None,
+            "ncu_fp64_pipe_active": RECON_FP64_PIPE_ACTIVE if dom == "reconstruction" else (0.8539 + 0.8545 + 0.8495) / 3,
+            "executed": {"flops_per_cell": RECON_EXECUTED_FLOPS if dom == "reconstruction" else UPDATE_EXECUTED_FLOPS,
+                         "frac": (RECON_EXECUTED_FLOPS if dom == "reconstruction" else UPDATE_EXECUTED_FLOPS) * per_s
+                         / 1e12 / FP64_PEAK_TFLOPS,
+                         "source": "ncu dadd + dmul + 2 dfma per cell of one step's launches of the kernel"},
             "avg_launch_ms": ms_dom / n_dom,
             "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA chain: 1.195 TFLOP/s)",
             "kernel_ms_share": {k: round(v[0] / max(sum(x[0] for x in fam.values()), 1e-30), 4)

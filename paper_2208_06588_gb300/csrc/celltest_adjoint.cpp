@@ -48,20 +48,22 @@ void ct_source_adjoint(const double* hd, const double* bd, const double* geom, d
 float ct_f32_trunc(double x) { return swale::f32_trunc(x); }
 
 // The device's FP32 smooth-class test and the FP64 class of the same indicators. in: F[3], c4,
-// c3 (mesh factors), D2h[3], D3h[3], D2m[3], D3m[3] (divided differences of h and hu on the
-// sub-stencils starting at cells j-2 .. j), eps. out[0]: the FP32 test (1: surely smooth),
-// out[1]: the FP64 class (shared_beta + hybrid_phi), outb[3]: the FP64 indicators.
-void ct_smooth_test(const double* F, double c4, double c3, const double* D2h, const double* D3h, const double* D2m,
-                    const double* D3m, double eps, int* out, double* outb) {
-  float F32[3], d2h[3], d3h[3], d2m[3], d3m[3];
+// c3 (mesh factors), D2h[4], D2m[4] (pair differences of h and hu on the pairs starting at cells
+// j-2 .. j+1), it[3] (reciprocal triple sums), eps. out[0]: the FP32 test (1: surely smooth),
+// out[1]: the FP64 class (second differences, shared_beta, hybrid_phi as the device forms
+// them), outb[3]: the FP64 indicators.
+void ct_smooth_test(const double* F, double c4, double c3, const double* D2h, const double* D2m, const double* it,
+                    double eps, int* out, double* outb) {
+  float F32[3], d2h[4], d2m[4], itf[3];
+  for (int a = 0; a < 4; ++a) {
+    d2h[a] = swale::f32_trunc(D2h[a]);
+    d2m[a] = swale::f32_trunc(D2m[a]);
+  }
   for (int a = 0; a < 3; ++a) {
     F32[a] = swale::f32_trunc(F[a]);
-    d2h[a] = swale::f32_trunc(D2h[a]);
-    d3h[a] = swale::f32_trunc(D3h[a]);
-    d2m[a] = swale::f32_trunc(D2m[a]);
-    d3m[a] = swale::f32_trunc(D3m[a]);
+    itf[a] = swale::f32_trunc(it[a]);
   }
-  out[0] = swale::sure_smooth_f32(F32, swale::f32_trunc(c4), swale::f32_trunc(c3), d2h, d3h, d2m, d3m,
+  out[0] = swale::sure_smooth_f32(F32, swale::f32_trunc(c4), swale::f32_trunc(c3), d2h, d2m, itf,
                                   swale::f32_trunc(eps)) ? 1 : 0;
   swale::CellGeom G{};
   for (int a = 0; a < 3; ++a) G.F[a] = F[a];
@@ -70,17 +72,78 @@ void ct_smooth_test(const double* F, double c4, double c3, const double* D2h, co
   for (int e = 0; e < 2; ++e)
     for (int r = 0; r < 3; ++r) G.d[e][r] = 1.0 / 3.0;
   swale::StencilDD DD{};
-  for (int a = 0; a < 3; ++a) {
+  for (int a = 0; a < 4; ++a) {
     DD.D2[2][a] = D2h[a];
-    DD.D3[2][a] = D3h[a];
     DD.D2[1][a] = D2m[a];
-    DD.D3[1][a] = D3m[a];
   }
+  for (int v = 1; v < 3; ++v)
+    for (int a = 0; a < 3; ++a) DD.D3[v][a] = swale::triple_dd(DD.D2[v][a], DD.D2[v][a + 1], it[a]);
   double beta[3], phi[2][3];
   swale::shared_beta(G, DD, beta);
   swale::SchemeConst P{9.812, eps, 1e-11, 1e-6, 1, 0};
   out[1] = swale::hybrid_phi(P, beta, G.d, phi);
   for (int r = 0; r < 3; ++r) outb[r] = beta[r];
+}
+
+// The non-well-balanced scheme's per-field FP32 smooth tests and the FP64 classes of the same
+// fields, formed as the device forms them. in: proj[4] = a11, a12, a21, a22; D2e[4], D2m[4],
+// D2h[4] (pair differences of eta, hu, h), it[3], F[3], c4, c3, eps. out[0..2]: FP32 tests of
+// the two characteristic fields and the bottom, out[3..5]: their FP64 classes, gam[3]: their
+// FP64 gamma.
+void ct_smooth1_test(const double* proj, const double* D2e, const double* D2m, const double* D2h, const double* it,
+                     const double* F, double c4, double c3, double eps, int* out, double* gam) {
+  float F32[3], itf[3], fd[3][4], fm[3][4];
+  for (int a = 0; a < 3; ++a) {
+    F32[a] = swale::f32_trunc(F[a]);
+    itf[a] = swale::f32_trunc(it[a]);
+  }
+  const float a11 = swale::f32_trunc(proj[0]), a12 = swale::f32_trunc(proj[1]);
+  const float a21 = swale::f32_trunc(proj[2]), a22 = swale::f32_trunc(proj[3]);
+  for (int a = 0; a < 4; ++a) {
+    const float e2 = swale::f32_trunc(D2e[a]), m2 = swale::f32_trunc(D2m[a]), h2 = swale::f32_trunc(D2h[a]);
+    fd[0][a] = std::fma(a11, e2, a12 * m2);
+    fm[0][a] = std::fma(std::fabs(a11), std::fabs(e2), std::fabs(a12) * std::fabs(m2));
+    fd[1][a] = std::fma(a21, e2, a22 * m2);
+    fm[1][a] = std::fma(std::fabs(a21), std::fabs(e2), std::fabs(a22) * std::fabs(m2));
+    fd[2][a] = e2 - h2;
+    fm[2][a] = std::fabs(e2) + std::fabs(h2);
+  }
+  for (int f = 0; f < 3; ++f)
+    out[f] = swale::sure_smooth1_f32(F32, swale::f32_trunc(c4), swale::f32_trunc(c3), fd[f], fm[f], itf,
+                                     swale::f32_trunc(eps)) ? 1 : 0;
+  // FP64 as recon_cell_nonwb_g forms it
+  double D2[3][4], D3[3][3], fD2[3][4], fD3[3][3];
+  for (int a = 0; a < 4; ++a) {
+    D2[0][a] = D2e[a];
+    D2[1][a] = D2m[a];
+    D2[2][a] = D2h[a];
+  }
+  for (int v = 0; v < 3; ++v)
+    for (int a = 0; a < 3; ++a) D3[v][a] = swale::triple_dd(D2[v][a], D2[v][a + 1], it[a]);
+  for (int a = 0; a < 4; ++a) {
+    fD2[0][a] = proj[0] * D2[0][a] + proj[1] * D2[1][a];
+    fD2[1][a] = proj[2] * D2[0][a] + proj[3] * D2[1][a];
+    fD2[2][a] = D2[0][a] - D2[2][a];
+  }
+  for (int a = 0; a < 3; ++a) {
+    fD3[0][a] = proj[0] * D3[0][a] + proj[1] * D3[1][a];
+    fD3[1][a] = proj[2] * D3[0][a] + proj[3] * D3[1][a];
+    fD3[2][a] = D3[0][a] - D3[2][a];
+  }
+  swale::SchemeConst P{9.812, eps, 1e-11, 1e-6, 1, 0};
+  double d[2][3];
+  for (int e = 0; e < 2; ++e)
+    for (int r = 0; r < 3; ++r) d[e][r] = 1.0 / 3.0;
+  for (int f = 0; f < 3; ++f) {
+    double beta[3], phi[2][3];
+    for (int r = 0; r < 3; ++r) {
+      const int a = 2 - r;
+      const double q = fD2[f][a] + fD3[f][a] * F[a];
+      beta[r] = c4 * (q * q) + c3 * (fD3[f][a] * fD3[f][a]);
+    }
+    out[3 + f] = swale::hybrid_phi(P, beta, d, phi);
+    gam[f] = std::fabs(beta[0] - beta[2]) / ((beta[0] + beta[1] + beta[2]) / 3.0 + eps);
+  }
 }
 
 }  // extern "C"

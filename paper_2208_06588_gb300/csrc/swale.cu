@@ -366,6 +366,12 @@ void launch_recon(const StepConst& K, const DevState& D, int T, unsigned grid, c
     else k_recon<STAGE, 128, 2><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
     return;
   }
+  if (STAGE == 1 && D.geo) {  // stage 1 reads the cached geometry: more resident warps
+    if (T == 64) k_recon<STAGE, 64, 0, true><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
+    else if (T == 256) k_recon<STAGE, 256, 0, true><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
+    else k_recon<STAGE, 128, 0, true><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
+    return;
+  }
   if (T == 64) k_recon<STAGE, 64><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
   else if (T == 256) k_recon<STAGE, 256><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
   else k_recon<STAGE, 128><<<grid, 128, 0, s>>>(K, D, E, M, B, J);

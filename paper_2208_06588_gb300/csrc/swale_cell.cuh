@@ -153,30 +153,59 @@ SWALE_HD float f32_trunc(double x) {
 // The smooth class decided in FP32 (Step 2 with the shared indicators of Eq. alphamodified).
 // GB300 runs FP32 at about 40x its FP64 rate, and in most cells the detector only has to tell
 // that gamma is far below 1/2. The indicators beta_r = c4 (qh^2 + qm^2) + c3 (D3h^2 + D3m^2),
-// q = D2 + D3 F, are evaluated in FP32 from FP32 copies of their inputs, beside their
-// magnitudes m_r = c4 (Qh^2 + Qm^2) + c3 (D3h^2 + D3m^2), Q = |D2| + |D3| |F|. A rounding-error
-// analysis of these few operations (inputs rounded once, FMAs, no cancellation in sums of
-// non-negative terms) bounds |beta_r(FP32) - beta_r| by 14 u m_r, u = 2^-24; E below takes
-// 64 u (m_0 + m_1 + m_2), which also covers the FP64 evaluation's own rounding (below 2^-48 m),
-// plus a 1e-30 floor for inputs that fall below the FP32 range. If
+// q = D2 + D3 F, are evaluated in FP32 from FP32 copies of the pair differences D2 (top 23 bits,
+// f32_trunc), second differences formed from them in FP32, D3 = (D2_right - D2_left) it, and
+// FP32 copies of the mesh factors, beside the magnitudes
+//   m_r = c4 (Qh^2 + Qm^2) + c3 (Mh^2 + Mm^2),  Q = |D2| + M |F|,  M = (|D2_left| + |D2_right|) it.
+// A rounding-error analysis of these few operations (inputs within 2^-23 relative, FMAs, the
+// second differences within 6 u M, sums of non-negative terms) bounds |beta_r(FP32) - beta_r| by
+// 25 u m_r, u = 2^-24; E below takes 64 u (m_0 + m_1 + m_2), which also covers the rounding of
+// the FP64 indicators (below 2^-48 m), plus a 1e-30 floor for inputs below the FP32 range. If
 //   tau32 + E <= (den32 - E) / 2,   tau = |beta_0 - beta_2|, den = mean(beta) + eps,
-// (with 8 u of relative slack on tau32 and den32) then the FP64 detector finds gamma <= 1/2 as
-// well, and the cell is smooth. Overflow or NaN make the test false, as does anything closer to
-// the threshold: the FP64 indicators then decide, as before.
+// (with 8 u of relative slack on tau32 and den32, and eps rounded down) then the FP64 detector
+// finds gamma <= 1/2 as well, and the cell is smooth. Overflow or NaN make the test false, as
+// does anything closer to the threshold: the FP64 indicators then decide, as before.
+//   d2h[4], d2m[4]  pair differences of h and hu on the pairs starting at cells j-2 .. j+1
+//   it[3]           reciprocal sums of the triples starting at cells j-2 .. j
 // ------------------------------------------------------------------------------------
-SWALE_HD bool sure_smooth_f32(const float F[3], float c4, float c3, const float d2h[3],
-                                                const float d3h[3], const float d2m[3], const float d3m[3],
-                                                float eps) {
+SWALE_HD bool sure_smooth_f32(const float F[3], float c4, float c3, const float d2h[4], const float d2m[4],
+                              const float it[3], float eps) {
   float b[3], msum = 0.0f;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     const int a = 2 - r;
-    const float qh = fmaf(d3h[a], F[a], d2h[a]), qm = fmaf(d3m[a], F[a], d2m[a]);
-    const float Qh = fmaf(fabsf(d3h[a]), fabsf(F[a]), fabsf(d2h[a]));
-    const float Qm = fmaf(fabsf(d3m[a]), fabsf(F[a]), fabsf(d2m[a]));
-    const float s2 = fmaf(d3h[a], d3h[a], d3m[a] * d3m[a]);
-    b[r] = fmaf(c4, fmaf(qh, qh, qm * qm), c3 * s2);
-    msum += fmaf(c4, fmaf(Qh, Qh, Qm * Qm), c3 * s2);
+    const float d3h = (d2h[a + 1] - d2h[a]) * it[a], d3m = (d2m[a + 1] - d2m[a]) * it[a];
+    const float Mh = (fabsf(d2h[a + 1]) + fabsf(d2h[a])) * it[a], Mm = (fabsf(d2m[a + 1]) + fabsf(d2m[a])) * it[a];
+    const float qh = fmaf(d3h, F[a], d2h[a]), qm = fmaf(d3m, F[a], d2m[a]);
+    const float Qh = fmaf(Mh, fabsf(F[a]), fabsf(d2h[a])), Qm = fmaf(Mm, fabsf(F[a]), fabsf(d2m[a]));
+    b[r] = fmaf(c4, fmaf(qh, qh, qm * qm), c3 * fmaf(d3h, d3h, d3m * d3m));
+    msum += fmaf(c4, fmaf(Qh, Qh, Qm * Qm), c3 * fmaf(Mh, Mh, Mm * Mm));
+  }
+  constexpr float u = 5.9604645e-8f;  // 2^-24
+  const float tau = fabsf(b[0] - b[2]);
+  const float den = (b[0] + b[1] + b[2]) * (1.0f / 3.0f) + eps;
+  const float E = (64.0f * u) * msum + 1e-30f;
+  return tau * (1.0f + 8.0f * u) + E <= 0.5f * (den * (1.0f - 8.0f * u) - E);
+}
+
+// The same test for one field on its own (the non-well-balanced scheme's characteristic fields
+// and bottom, Sec. 2.2 last paragraph): beta_r = c4 q^2 + c3 D3^2 of the field's pair
+// differences d2[4], given in FP32 with magnitudes mag[4] that bound them together with their
+// error (the fields are combinations of the stencil's differences: |error| <= 6 u mag). The
+// analysis of sure_smooth_f32 carries over with Q = mag + M |F|, M = (mag_left + mag_right) it;
+// the bound stays within 64 u (m_0 + m_1 + m_2).
+SWALE_HD bool sure_smooth1_f32(const float F[3], float c4, float c3, const float d2[4], const float mag[4],
+                               const float it[3], float eps) {
+  float b[3], msum = 0.0f;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int a = 2 - r;
+    const float d3 = (d2[a + 1] - d2[a]) * it[a];
+    const float M = (mag[a + 1] + mag[a]) * it[a];
+    const float q = fmaf(d3, F[a], d2[a]);
+    const float Q = fmaf(M, fabsf(F[a]), mag[a]);
+    b[r] = fmaf(c4, q * q, c3 * (d3 * d3));
+    msum += fmaf(c4, Q * Q, c3 * (M * M));
   }
   constexpr float u = 5.9604645e-8f;  // 2^-24
   const float tau = fabsf(b[0] - b[2]);
@@ -451,21 +480,36 @@ SWALE_HD void recon_cell(const SchemeConst& P, const real h[5], const real it[3]
 // them, the divided differences) onto two characteristic fields; each field and the bottom get
 // their own indicators, class and weights; the edge values are mapped back with R. A dry cell
 // (h <= h_dry) reconstructs eta and hu themselves. The class is the largest of the three.
-SWALE_HD void recon_cell_nonwb_g(const SchemeConst& P, const CellGeom& G, const real v0[3][3], const StencilDD& DD,
-                                 EdgeState& o, uint8_t& flag, uint32_t& st) {
+// Rows of R^-1 = 1/(2c) [[u + c, -1], [-(u - c), 1]] at the cell's average state (identity when
+// the cell is dry), with u and c.
+struct NonwbProj {
+  real a11, a12, a21, a22, u, c;
+  bool wet;
+};
+SWALE_HD NonwbProj nonwb_proj(const SchemeConst& P, const real v0[3][3]) {
+  NonwbProj pr{real(1.0), real(0.0), real(0.0), real(1.0), real(0.0), real(0.0), false};
   const real hb = v0[2][2];
-  const bool wet = dlt(P.h_dry, hb);
-  // Rows of R^-1 = 1/(2c) [[u + c, -1], [-(u - c), 1]] (identity when dry).
-  real a11 = 1.0, a12 = 0.0, a21 = 0.0, a22 = 1.0, u = 0.0, c = 0.0;
-  if (wet) {
-    u = v0[1][2] * recip(hb);
-    c = dsqrt(P.g * hb);
-    const real i2c = 0.5 * recip(c);
-    a11 = (u + c) * i2c;
-    a12 = -i2c;
-    a21 = (c - u) * i2c;
-    a22 = i2c;
+  pr.wet = dlt(P.h_dry, hb);
+  if (pr.wet) {
+    pr.u = v0[1][2] * recip(hb);
+    pr.c = dsqrt(P.g * hb);
+    const real i2c = 0.5 * recip(pr.c);
+    pr.a11 = (pr.u + pr.c) * i2c;
+    pr.a12 = -i2c;
+    pr.a21 = (pr.c - pr.u) * i2c;
+    pr.a22 = i2c;
   }
+  return pr;
+}
+
+//   known_smooth[3] (may be null): fields whose smooth class the caller has established (the
+//   device's FP32 test, which implies it for the FP64 indicators); their indicators are not formed.
+SWALE_HD void recon_cell_nonwb_g(const SchemeConst& P, const CellGeom& G, const real v0[3][3], const StencilDD& DD,
+                                 EdgeState& o, uint8_t& flag, uint32_t& st, const NonwbProj& pr,
+                                 const bool* known_smooth = nullptr) {
+  const real hb = v0[2][2];
+  const bool wet = pr.wet;
+  const real a11 = pr.a11, a12 = pr.a12, a21 = pr.a21, a22 = pr.a22, u = pr.u, c = pr.c;
   real fv0[3][3], fD2[3][4], fD3[3][3];
   // Third field: the bottom b = eta - h.
   for (int a = 0; a < 3; ++a) {
@@ -484,14 +528,20 @@ SWALE_HD void recon_cell_nonwb_g(const SchemeConst& P, const CellGeom& G, const 
   real fe[3][2];
   flag = 0;
   for (int f = 0; f < 3; ++f) {
-    real beta[3];
-    for (int r = 0; r < 3; ++r) {
-      const int a = 2 - r;
-      const real q = fD2[f][a] + fD3[f][a] * G.F[a];
-      beta[r] = G.c4 * (q * q) + G.c3 * (fD3[f][a] * fD3[f][a]);
-    }
     real phi[2][3];
-    const uint8_t fl = hybrid_phi(P, beta, G.d, phi);
+    uint8_t fl = 0;
+    if (known_smooth && known_smooth[f]) {
+      for (int e = 0; e < 2; ++e)
+        for (int r = 0; r < 3; ++r) phi[e][r] = G.d[e][r];
+    } else {
+      real beta[3];
+      for (int r = 0; r < 3; ++r) {
+        const int a = 2 - r;
+        const real q = fD2[f][a] + fD3[f][a] * G.F[a];
+        beta[r] = G.c4 * (q * q) + G.c3 * (fD3[f][a] * fD3[f][a]);
+      }
+      fl = hybrid_phi(P, beta, G.d, phi);
+    }
     flag = fl > flag ? fl : flag;
     for (int e = 0; e < 2; ++e) fe[f][e] = edge_value(G, phi, fv0[f], fD2[f], fD3[f], e);
   }
@@ -512,7 +562,7 @@ SWALE_HD void recon_cell_nonwb(const SchemeConst& P, const real h[5], const real
                                real dxmax, EdgeState& o, uint8_t& flag, uint32_t& st) {
   CellGeom G;
   cell_geom(h, P.beta_dx_global ? dxmax : h[2], G, st);
-  recon_cell_nonwb_g(P, G, v0, DD, o, flag, st);
+  recon_cell_nonwb_g(P, G, v0, DD, o, flag, st, nonwb_proj(P, v0));
 }
 
 // Hybrid weights at an interior point (Step 3) with linear weights d(x), which may be

@@ -459,18 +459,25 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevSta
 // reciprocals for the update kernel of the same stage, reduces the wave speed, and in stage 1
 // the instance's last tile computes its dt (and the secant factor of the prescribed motion).
 // ------------------------------------------------------------------------------------
-template <int STAGE, int T, int SCHEME = 0>
-__global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
+// HIOCC: a launch bound of 8 blocks of 128 threads per SM (64 registers) instead of 4 (128), for
+// stage 1 of the well-balanced scheme when it reads the cached mesh geometry: its per-cell work is
+// light enough there that more resident warps win (measured: 0.8 % of the dam-break step), while
+// every instantiation that computes the geometry itself spills heavily under that bound.
+template <int STAGE, int T, int SCHEME = 0, bool HIOCC = false>
+__global__ void __launch_bounds__(T, (HIOCC ? 1024 : 512) / T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
                                              const double* __restrict__ Mg, const double* __restrict__ Bg,
                                              const double* __restrict__ Jg) {
   __shared__ double sJ[T + 4], sV[3][T + 4];    // cells c0-2 .. c0+T+1
   __shared__ double sIP[T + 3], sD2[3][T + 3];  // pairs starting at those cells
-  __shared__ double sIT[T + 2], sD3[3][T + 2];  // triples centred at cells c0-1 .. c0+T
-  // FP32 copies of the divided differences of hu and h for the FP32 smooth-class test (the
-  // well-balanced schemes: the shared indicators of h and hu)
-  constexpr bool kF32 = SCHEME != 1;
-  constexpr int TF = kF32 ? T : 0;
-  __shared__ float sD2f[2][TF + 3], sD3f[2][TF + 2];
+  // Triples centred at cells c0-1 .. c0+T. The well-balanced scheme forms the second differences
+  // per cell, and only where the FP32 smooth-class test cannot decide (the smooth class needs
+  // none); the other schemes form them here.
+  constexpr int TD3 = SCHEME == 0 ? 0 : T;
+  __shared__ double sIT[T + 2], sD3[3][TD3 + 2];
+  // FP32 copies of the pair differences (hu, h, and for the non-well-balanced scheme eta) and of
+  // the triple reciprocals for the FP32 smooth-class tests
+  constexpr int NV32 = SCHEME == 1 ? 3 : 2;
+  __shared__ float sD2f[NV32][T + 3], sITf[T + 2];
   __shared__ __align__(16) double sRaw[4][T + 8];  // E, M, B, J of those cells as bulk-copied
   __shared__ __align__(8) uint64_t sBar;           // completion of the tile's bulk copies
   __shared__ __align__(8) uint64_t sPad;           // test hook: a barrier no copy completes
@@ -565,22 +572,19 @@ __global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, c
       double d2[3];
 #pragma unroll
       for (int v = 0; v < 3; ++v) sD2[v][i] = d2[v] = swale::pair_dd(sV[v][i], sV[v][i + 1], ip);
-      if (kF32) {
-        sD2f[0][i] = swale::f32_trunc(d2[1]);
-        sD2f[1][i] = swale::f32_trunc(d2[2]);
-      }
+      sD2f[0][i] = swale::f32_trunc(d2[1]);
+      sD2f[1][i] = swale::f32_trunc(d2[2]);
+      if (SCHEME == 1) sD2f[NV32 - 1][i] = swale::f32_trunc(d2[0]);
     }
     __syncthreads();
     for (int i = tid; i < T + 2; i += T) {
       const double it = swale::triple_recip(sJ[i], sJ[i + 1], sJ[i + 2]);
       sIT[i] = it;
-      double d3[3];
+      if (SCHEME != 0) {
 #pragma unroll
-      for (int v = 0; v < 3; ++v) sD3[v][i] = d3[v] = swale::triple_dd(sD2[v][i], sD2[v][i + 1], it);
-      if (kF32) {
-        sD3f[0][i] = swale::f32_trunc(d3[1]);
-        sD3f[1][i] = swale::f32_trunc(d3[2]);
+        for (int v = 0; v < 3; ++v) sD3[v][i] = swale::triple_dd(sD2[v][i], sD2[v][i + 1], it);
       }
+      sITf[i] = swale::f32_trunc(it);
     }
     __syncthreads();
     const int64_t c = c0 + tid;
@@ -603,8 +607,10 @@ __global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, c
         for (int a = 0; a < 3; ++a) v0[v][a] = sV[v][tid + a];
 #pragma unroll
         for (int a = 0; a < 4; ++a) DD.D2[v][a] = sD2[v][tid + a];
+        if (SCHEME != 0) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) DD.D3[v][a] = sD3[v][tid + a];
+          for (int a = 0; a < 3; ++a) DD.D3[v][a] = sD3[v][tid + a];
+        }
       }
       const double dxmax = bitsd(S->Jmax[STAGE - 1]);
       const int64_t idx = eb + c + 1;
@@ -631,21 +637,49 @@ __global__ void __launch_bounds__(T, 512 / T) k_recon(StepConst K, DevState D, c
       EdgeState o;
       uint8_t flag;
       double etaG[2] = {0.0, 0.0};
+      float F32[3], itf[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        F32[a] = swale::f32_trunc(G.F[a]);
+        itf[a] = sITf[tid + a];
+      }
+      const float c4f = swale::f32_trunc(G.c4), c3f = swale::f32_trunc(G.c3), epsf = swale::f32_trunc(K.sc.eps_weno);
       if (SCHEME == 1) {
-        swale::recon_cell_nonwb_g(K.sc, G, v0, DD, o, flag, st);
+        // Each characteristic field and the bottom: its smooth class in FP32 when that can be
+        // told for sure, from the FP32 pair differences of eta, hu, h and the projection rows.
+        const swale::NonwbProj pr = swale::nonwb_proj(K.sc, v0);
+        const float a11 = swale::f32_trunc(pr.a11), a12 = swale::f32_trunc(pr.a12);
+        const float a21 = swale::f32_trunc(pr.a21), a22 = swale::f32_trunc(pr.a22);
+        float fd[3][4], fm[3][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float e2 = sD2f[NV32 - 1][tid + a], m2 = sD2f[0][tid + a], h2 = sD2f[1][tid + a];
+          fd[0][a] = fmaf(a11, e2, a12 * m2);
+          fm[0][a] = fmaf(fabsf(a11), fabsf(e2), fabsf(a12) * fabsf(m2));
+          fd[1][a] = fmaf(a21, e2, a22 * m2);
+          fm[1][a] = fmaf(fabsf(a21), fabsf(e2), fabsf(a22) * fabsf(m2));
+          fd[2][a] = e2 - h2;
+          fm[2][a] = fabsf(e2) + fabsf(h2);
+        }
+        bool known[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) known[f] = swale::sure_smooth1_f32(F32, c4f, c3f, fd[f], fm[f], itf, epsf);
+        swale::recon_cell_nonwb_g(K.sc, G, v0, DD, o, flag, st, pr, known);
       } else {
         // The smooth class, when FP32 can tell it for sure; else the FP64 detector decides.
-        float F32[3], d2h[3], d3h[3], d2m[3], d3m[3];
+        float d2h[4], d2m[4];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          F32[a] = swale::f32_trunc(G.F[a]);
+        for (int a = 0; a < 4; ++a) {
           d2h[a] = sD2f[1][tid + a];
-          d3h[a] = sD3f[1][tid + a];
           d2m[a] = sD2f[0][tid + a];
-          d3m[a] = sD3f[0][tid + a];
         }
-        const bool smooth32 = swale::sure_smooth_f32(F32, swale::f32_trunc(G.c4), swale::f32_trunc(G.c3), d2h, d3h,
-                                                     d2m, d3m, swale::f32_trunc(K.sc.eps_weno));
+        const bool smooth32 = swale::sure_smooth_f32(F32, c4f, c3f, d2h, d2m, itf, epsf);
+        if (SCHEME == 0 && !smooth32) {  // the FP64 detector and the WENO-Z edge values need them
+#pragma unroll
+          for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) DD.D3[v][a] = swale::triple_dd(DD.D2[v][a], DD.D2[v][a + 1], sIT[tid + a]);
+        }
         if (SCHEME == 2) swale::recon_cell_special_g(K.sc, G, h, v0, DD, o, flag, st, etaG, smooth32);
         else swale::recon_cell_g(K.sc, G, v0, DD, o, flag, st, smooth32);
       }

@@ -67,3 +67,9 @@ def test_method_flop_counts_are_the_oracles():
         tot += oracle.count_step(Pi, p.E, p.hu, p.b, p.J, p.x, p.profile)["step"]["flops"] * p.N
         cells += p.N
     assert abs(tot / cells / bench.ORACLE_BATCH_STEP_FLOPS - 1) < 5e-4
+
+    for scheme, (rec, stp) in bench.ORACLE_VARIANT_FLOPS.items():
+        Ps = oracle.Params(g=pr.g, cfl=pr.cfl, bc=pr.bc, mesh=pr.mesh, gauss_sigma=pr.gauss_sigma,
+                           gauss_half=pr.gauss_half, scheme=scheme)
+        cs = oracle.count_step(Ps, pr.E, pr.hu, pr.b, pr.J, pr.x)
+        assert abs(cs["recon"]["flops"] / rec - 1) < 5e-4 and abs(cs["step"]["flops"] / stp - 1) < 5e-4, scheme

@@ -17,30 +17,29 @@ def _gamma(b, eps):
 
 
 def _random_cell(rng, scale_spread=6.0):
-    """Mesh factors and divided differences over many orders of magnitude, with cancellation
-    between D2 and D3 F (q = D2 + D3 F small while both terms are large)."""
+    """A 5-cell stencil over many orders of magnitude of widths and data: the mesh factors of
+    the indicators (F, c4, c3 as the cell geometry forms them), the pair differences D2 of h and
+    hu on its four pairs and the reciprocal sums of its three triples. Kinds: random data, near
+    cancellation between D2 and D3 F, smooth data (small second differences), still water."""
     dx = 10.0 ** rng.uniform(-6, 2)
-    h2 = dx * rng.uniform(0.2, 1.0)
-    F = h2 * rng.uniform(-2.0, 2.0, 3)
+    w = dx * rng.uniform(0.2, 1.0, 5)  # widths J_{j-2..j+2}
+    h0, h1, h2, h3, h4 = w
+    F = np.array([1.5 * h2 + h0 + 2 * h1, 0.5 * h2 + h1, -(0.5 * h2 + h3)])
     c4 = 4.0 * dx * h2
     c3 = (3.0 * h2 * h2 + 36.0 * dx * dx) * dx * h2
+    it = 1.0 / (w[:3] + w[1:4] + w[2:])
     s = 10.0 ** rng.uniform(-scale_spread, scale_spread)
-    D3h = s / h2 * rng.normal(size=3)
-    D3m = s / h2 * rng.normal(size=3)
-    D2h = s * rng.normal(size=3)
-    D2m = s * rng.normal(size=3)
     kind = rng.integers(4)
-    if kind == 1:  # near cancellation in q
-        D2h = -D3h * F * (1.0 + 1e-6 * rng.normal(size=3))
-    elif kind == 2:  # smooth data: third differences small
-        D3h *= 1e-3
-        D3m *= 1e-3
-        D2h = D2h[0] + 1e-3 * D2h
-        D2m = D2m[0] + 1e-3 * D2m
-    elif kind == 3:  # still water: exact zeros
-        D2m = np.zeros(3)
-        D3m = np.zeros(3)
-    return F, c4, c3, D2h, D3h, D2m, D3m
+    D2h, D2m = s * rng.normal(size=4), s * rng.normal(size=4)
+    if kind == 1:  # q = D2 + D3 F nearly cancels on one sub-stencil
+        a = rng.integers(3)
+        D2h[a] = -(D2h[a + 1] * it[a] * F[a]) / (1.0 - it[a] * F[a]) * (1.0 + 1e-6 * rng.normal())
+    elif kind == 2:  # smooth data: nearly equal pair differences
+        D2h = D2h[0] * (1.0 + 1e-3 * rng.normal(size=4))
+        D2m = D2m[0] * (1.0 + 1e-3 * rng.normal(size=4))
+    elif kind == 3:  # still water: no discharge
+        D2m = np.zeros(4)
+    return F, c4, c3, D2h, D2m, it
 
 
 def test_fp32_smooth_implies_fp64_smooth_on_random_cells():
@@ -59,52 +58,61 @@ def test_fp32_smooth_implies_fp64_smooth_on_random_cells():
     assert sure_n > 0.9 * smooth_n, (sure_n, smooth_n)
 
 
-@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("seed", range(8))
 def test_fp32_test_stays_off_near_the_threshold(seed):
-    """Scale one difference so that the FP64 gamma crosses 1/2: just above it (class 1) the
-    FP32 test must never claim the smooth class, just below it it may decline."""
+    """Blend a smooth stencil (gamma near 0) into a rough one (gamma above 1) and bisect the
+    blend to where the FP64 gamma crosses 1/2: above it (class 1) the FP32 test must never claim
+    the smooth class, and a hair below it (gamma = 0.5 (1 - 1e-8)) it declines too: it keeps a
+    margin of about 1e-5 relative."""
     rng = np.random.default_rng(seed)
-    F, c4, c3, D2h, D3h, D2m, D3m = _random_cell(rng, scale_spread=2.0)
+    F, c4, c3, _, _, it = _random_cell(rng, scale_spread=2.0)
     eps = 1e-6
-    base = D2h.copy()
-
-    def at(s):
-        d = base.copy()
-        d[0] = base[0] * s
-        return C.smooth_test(F, c4, c3, d, D3h, D2m, D3m, eps=eps)
-
-    g = lambda s: _gamma(at(s)[2], eps)
-    lo, hi = 0.0, 1.0
-    # find a scale with gamma above 1/2, then bisect to the crossing
-    for _ in range(60):
-        if g(hi) > 0.5:
+    sh, sm = 10.0 ** rng.uniform(-2, 2, 2)
+    smooth_h = sh * (1.0 + 1e-3 * rng.normal(size=4))
+    smooth_m = sm * (1.0 + 1e-3 * rng.normal(size=4))
+    for _ in range(100):
+        rough_h, rough_m = sh * rng.normal(size=4) * 10.0, sm * rng.normal(size=4) * 10.0
+        if C.smooth_test(F, c4, c3, rough_h, rough_m, it, eps=eps)[1] == 2:
             break
-        hi *= 2.0
-    if g(hi) <= 0.5 or g(lo) > 0.5:
-        pytest.skip("this draw does not cross the threshold along the scaled direction")
-    for _ in range(200):
-        mid = 0.5 * (lo + hi)
-        if g(mid) > 0.5:
-            hi = mid
-        else:
-            lo = mid
-    for s in np.linspace(lo, hi, 9):
-        sure, flag, b = at(s)
+    at = lambda t: C.smooth_test(F, c4, c3, (1 - t) * smooth_h + t * rough_h, (1 - t) * smooth_m + t * rough_m, it,
+                                 eps=eps)
+    g = lambda t: _gamma(at(t)[2], eps)
+
+    def crossing(level):
+        lo, hi = 0.0, 1.0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if g(mid) > level:
+                hi = mid
+            else:
+                lo = mid
+        return lo, hi
+
+    assert g(0.0) < 0.4 and g(1.0) > 1.0
+    lo, hi = crossing(0.5)
+    for t in np.linspace(lo, 1.0, 33):
+        sure, flag, b = at(t)
         if flag != 0:
             assert not sure
-    # a little inside the smooth range the shortcut still declines (it keeps a margin)
+    for rel in (1e-12, 1e-9, 1e-7, 1e-6, 1e-5):  # just above the threshold: class 1
+        _, hi = crossing(0.5 * (1.0 + rel))
+        sure, flag, b = at(hi)
+        assert flag == 1 and not sure, rel
+    lo, _ = crossing(0.5 * (1.0 - 1e-8))
     sure, flag, b = at(lo)
     assert flag == 0 and not sure
+    # well inside the smooth class the test decides
+    assert at(0.0)[0]
 
 
 def test_fp32_test_on_still_water_and_non_finite_data():
-    F, c4, c3 = np.array([1e-3, 5e-4, -5e-4]), 4e-6, 4e-12
-    z = np.zeros(3)
-    assert C.smooth_test(F, c4, c3, z, z, z, z, 1e-6)[:2] == (True, 0)
-    nan = np.array([np.nan, 0.0, 0.0])
-    assert C.smooth_test(F, c4, c3, nan, z, z, z, 1e-6)[0] is False
-    big = np.array([1e200, 0.0, 0.0])
-    assert C.smooth_test(F, c4, c3, big, z, z, z, 1e-6)[0] is False
+    F, c4, c3, it = np.array([1e-3, 5e-4, -5e-4]), 4e-6, 4e-12, np.full(3, 1.0 / 3e-3)
+    z = np.zeros(4)
+    assert C.smooth_test(F, c4, c3, z, z, it, 1e-6)[:2] == (True, 0)
+    nan = np.array([np.nan, 0.0, 0.0, 0.0])
+    assert C.smooth_test(F, c4, c3, nan, z, it, 1e-6)[0] is False
+    big = np.array([1e200, 0.0, 0.0, 0.0])
+    assert C.smooth_test(F, c4, c3, big, z, it, 1e-6)[0] is False
 
 
 def test_f32_trunc_matches_the_float_conversion_toward_zero():
@@ -117,3 +125,75 @@ def test_f32_trunc_matches_the_float_conversion_toward_zero():
     assert np.all(np.abs(got - ref) <= np.spacing(np.abs(ref)))
     assert np.all(np.signbit(got) == np.signbit(x))
     assert C.f32_trunc(1e300) == np.inf and C.f32_trunc(-1e300) == -np.inf and C.f32_trunc(1e-50) == 0.0
+
+
+def _random_field_cell(rng):
+    """Projection rows of a wet cell (u, c) and the stencil data of eta, hu, h."""
+    F, c4, c3, D2h, D2m, it = _random_cell(rng)
+    s = np.abs(D2h).max() + np.abs(D2m).max() + 1e-300
+    D2e = D2h + s * (1e-3 * rng.normal(size=4) if rng.random() < 0.5 else rng.normal(size=4))
+    u, c = rng.normal(), 10.0 ** rng.uniform(-1, 1.5)
+    if rng.random() < 0.2:  # a dry cell: identity rows
+        proj = np.array([1.0, 0.0, 0.0, 1.0])
+    else:
+        i2c = 0.5 / c
+        proj = np.array([(u + c) * i2c, -i2c, (c - u) * i2c, i2c])
+    return proj, D2e, D2m, D2h, it, F, c4, c3
+
+
+def test_field_fp32_smooth_implies_fp64_smooth():
+    """The non-well-balanced scheme's test of each characteristic field and of the bottom."""
+    rng = np.random.default_rng(7)
+    sure_n = smooth_n = 0
+    for _ in range(15000):
+        args = _random_field_cell(rng)
+        eps = 10.0 ** rng.uniform(-12, -4)
+        sure, cls, _ = C.smooth1_test(*args, eps=eps)
+        for s_, c_ in zip(sure, cls):
+            if s_:
+                sure_n += 1
+                assert c_ == 0, (args, eps)
+            smooth_n += c_ == 0
+    assert sure_n > 0.9 * smooth_n, (sure_n, smooth_n)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_field_fp32_test_stays_off_near_the_threshold(seed):
+    """Blend smooth stencil data into rough data and bisect the blend to where a field's FP64
+    gamma crosses 1/2: just above it the field's FP32 test never claims the smooth class, a hair
+    below it it declines too."""
+    rng = np.random.default_rng(100 + seed)
+    proj, _, _, _, it, F, c4, c3 = _random_field_cell(rng)
+    eps = 1e-6
+    s = 10.0 ** rng.uniform(-2, 2)
+    smooth = [s * (1.0 + 1e-3 * rng.normal(size=4)) for _ in range(3)]
+    for _ in range(100):
+        rough = [s * 10.0 * rng.normal(size=4) for _ in range(3)]
+        if min(C.smooth1_test(proj, *rough, it, F, c4, c3, eps)[1]) == 2:
+            break
+    at = lambda t: C.smooth1_test(proj, *[(1 - t) * a + t * b for a, b in zip(smooth, rough)], it, F, c4, c3, eps)
+    g0, g1 = at(0.0)[2], at(1.0)[2]
+    crossed = 0
+    for f in range(3):
+        if not (g0[f] < 0.4 and g1[f] > 1.0):
+            continue
+        crossed += 1
+
+        def crossing(level):
+            lo, hi = 0.0, 1.0
+            for _ in range(200):
+                mid = 0.5 * (lo + hi)
+                if at(mid)[2][f] > level:
+                    hi = mid
+                else:
+                    lo = mid
+            return lo, hi
+
+        for rel in (1e-12, 1e-9, 1e-7, 1e-6, 1e-5):
+            _, hi = crossing(0.5 * (1.0 + rel))
+            sure, cls, g = at(hi)
+            assert cls[f] == 1 and not sure[f], (f, rel)
+        lo, _ = crossing(0.5 * (1.0 - 1e-8))
+        sure, cls, g = at(lo)
+        assert cls[f] == 0 and not sure[f]
+    assert crossed >= 1
