@@ -190,11 +190,11 @@ def batch_step_flops(bt, n_inst=16):
     return tot / cells
 
 
-def adjoint_step_flops(pr, tape=False):
+def adjoint_step_flops(pr, tape=False, runs=None):
     from paper_2208_06588_gb300 import opcount
     c = opcount.count_stage(pr.E, pr.hu, pr.b, pr.J, bc=pr.bc, sample=1 << 13)
     r = opcount.count_reverse(pr.E, pr.hu, pr.b, pr.J, bc=pr.bc, sample=1 << 13)
-    return opcount.adjoint_step_flops(c, r, runs=2 if tape else 3)
+    return opcount.adjoint_step_flops(c, r, runs=runs if runs else (2 if tape else 3))
 
 
 def cpu_oracle_rate(n_cells, steps):

@@ -285,18 +285,19 @@ swale_status swale_get_alpha_log(swale_ctx* ctx, double* log);
  * viscosities alpha are those of the forward run, detector classes, limiter branches, dry-edge
  * tests and max/min selections are frozen (a tie follows the first argument); if a replay log
  * is active (swale_alpha_log mode 2) the forward run replays it instead. Checkpoints of
- * the state every ckpt_every steps; each segment is recomputed once with per-step snapshots
- * (by a further set of state arrays on a low-priority stream, one segment ahead of the reverse
- * sweep) and each step once more before its reverse sweep (on a third stream, alternating
+ * the state every ckpt_every steps; each segment but the last is recomputed once with per-step
+ * snapshots (by a further set of state arrays on a low-priority stream, one segment ahead of the
+ * reverse sweep; the forward run keeps the last segment's snapshots, and in tape mode its stage
+ * data, itself) and each step once more before its reverse sweep (on a third stream, alternating
  * between the context's arrays and one more set, one step ahead of the reverse sweep, which
  * runs on the context's stream). These forward runs compute the mesh geometry in every stage
  * (no reuse of the previous step's), so the trajectory, and the gradient up to the order of
  * atomic additions, does not depend on ckpt_every. Device memory beyond the context's own: about
- * 5 (ceil(nsteps/C) + 2 C + 3) + 117 doubles per cell with C = min(ckpt_every, nsteps), exactly
- * the value of swale_adjoint_bytes; all of it (and the two streams) is freed before the call
- * returns. The mesh must
- * be prescribed (static or profile motion) and t_end = 0. On return the context holds the
- * state after the nsteps steps.
+ * 5 (ceil(nsteps/C) + b C + 3) + 117 doubles per cell with C = min(ckpt_every, nsteps) and b = 2
+ * segment buffers (1 when C = nsteps), exactly the value of swale_adjoint_bytes; all of it (and
+ * the two streams) is freed before the call returns. With ckpt_every >= nsteps every step runs
+ * twice (once in tape mode). The mesh must be prescribed (static, profile or linear motion) and
+ * t_end = 0. On return the context holds the state after the nsteps steps.
  * Errors: SWALE_EINVAL, SWALE_ENOMEM, SWALE_ECUDA, and the status errors of swale_advance. */
 swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, int32_t G, const double* gauges_x,
                            const double* h_obs, double* J, double* dJ_deta0, double* dJ_dhu0, double* dJ_db0);
@@ -305,17 +306,19 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
  * (tape = 0) or with (tape = 1) the tape of swale_set_adjoint_tape (host-only arithmetic; needs
  * no device). Lets a caller pick ckpt_every for the memory it has: the checkpoints grow as
  * nsteps / ckpt_every, the per-segment snapshots (and the tape: about 39 doubles per cell and
- * step, for two segments) as ckpt_every.
+ * step, for two segments, one when ckpt_every >= nsteps) as ckpt_every.
  * Errors: SWALE_EINVAL (a size < 1, tape not 0 or 1, or a NULL bytes pointer). */
 swale_status swale_adjoint_bytes(int64_t B, int64_t Ntot, int64_t nsteps, int64_t ckpt_every, int32_t G,
                                  int32_t tape, uint64_t* bytes);
 
 /* How swale_adjoint gets each step's stage data (the edge values of the three stages, q^(1),
  * q^(2) and their widths) for the reverse sweep. enable = 0 (the default): each step is
- * recomputed from its snapshot before its reverse sweep, so every step is run three times.
- * enable = 1: the recompute of a segment keeps every step's stage data (a tape of about 39
- * doubles per cell and step, for two segments), and the reverse sweep reads it:
- * every step is run twice. The gradient is the same up to the order of atomic additions. This
+ * recomputed from its snapshot before its reverse sweep, so every step is run three times (twice
+ * in the last segment). enable = 1: the recompute of a segment (for the last segment, the
+ * forward run) keeps every step's stage data (a tape of about 39 doubles per cell and step, for
+ * two segments), and the reverse sweep reads it: every step is run twice (once in the last
+ * segment: with ckpt_every >= nsteps the forward run is the only one). The gradient is the same
+ * up to the order of atomic additions. This
  * is a trade of memory for arithmetic that the paper does not discuss (it has no adjoint).
  * Errors: SWALE_EINVAL. */
 swale_status swale_set_adjoint_tape(swale_ctx* ctx, int32_t enable);

@@ -87,14 +87,15 @@ def source_adjoint(hd, bd, geom, g, Sb):
     return hdb, bdb
 
 
-def smooth_test(F, c4, c3, D2h, D2m, it, eps=1e-6):
-    """(FP32 test says surely smooth, FP64 class, FP64 indicators) of one cell's data: mesh
-    factors F[3], c4, c3, pair differences D2h[4], D2m[4], reciprocal triple sums it[3]."""
+def smooth_test(w5, dx, D2h, D2m, it, eps=1e-6):
+    """(FP32 test says surely smooth, FP64 class, FP64 indicators) of one cell's data: the widths
+    w5[5] and length dx of its mesh factors, pair differences D2h[4], D2m[4], reciprocal triple
+    sums it[3]."""
     out = np.zeros(2, dtype=np.int32)
     b = np.zeros(3)
     f = ctypes.c_double
-    arrs = [f64(x) for x in (F, D2h, D2m, it)]  # kept alive across the call
-    lib().ct_smooth_test(_p(arrs[0]), f(c4), f(c3), *map(_p, arrs[1:]), f(eps), _p(out), _p(b))
+    arrs = [f64(x) for x in (w5, D2h, D2m, it)]  # kept alive across the call
+    lib().ct_smooth_test(_p(arrs[0]), f(dx), *map(_p, arrs[1:]), f(eps), _p(out), _p(b))
     return bool(out[0]), int(out[1]), b
 
 
@@ -103,12 +104,12 @@ def f32_trunc(x):
     return lib().ct_f32_trunc(float(x))
 
 
-def smooth1_test(proj, D2e, D2m, D2h, it, F, c4, c3, eps=1e-6):
+def smooth1_test(proj, D2e, D2m, D2h, it, w5, dx, eps=1e-6):
     """Per-field FP32 tests, FP64 classes and FP64 gamma of the non-well-balanced scheme's three
     fields."""
     out = np.zeros(6, dtype=np.int32)
     gam = np.zeros(3)
     f = ctypes.c_double
-    arrs = [f64(x) for x in (proj, D2e, D2m, D2h, it, F)]
-    lib().ct_smooth1_test(*map(_p, arrs), f(c4), f(c3), f(eps), _p(out), _p(gam))
+    arrs = [f64(x) for x in (proj, D2e, D2m, D2h, it, w5)]
+    lib().ct_smooth1_test(*map(_p, arrs), f(dx), f(eps), _p(out), _p(gam))
     return [bool(v) for v in out[:3]], [int(v) for v in out[3:]], gam

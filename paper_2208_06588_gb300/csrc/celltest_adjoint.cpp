@@ -47,28 +47,24 @@ void ct_source_adjoint(const double* hd, const double* bd, const double* geom, d
 // f32_trunc on the host (the device's double -> float conversion on the integer pipe).
 float ct_f32_trunc(double x) { return swale::f32_trunc(x); }
 
-// The device's FP32 smooth-class test and the FP64 class of the same indicators. in: F[3], c4,
-// c3 (mesh factors), D2h[4], D2m[4] (pair differences of h and hu on the pairs starting at cells
-// j-2 .. j+1), it[3] (reciprocal triple sums), eps. out[0]: the FP32 test (1: surely smooth),
+// The device's FP32 smooth-class test and the FP64 class of the same indicators. in: w5[5] (the
+// widths J_{j-2..j+2}) and dx (the indicators' length) for the mesh factors, D2h[4], D2m[4] (pair
+// differences of h and hu on the pairs starting at cells j-2 .. j+1), it[3] (reciprocal triple
+// sums), eps. out[0]: the FP32 test (1: surely smooth),
 // out[1]: the FP64 class (second differences, shared_beta, hybrid_phi as the device forms
 // them), outb[3]: the FP64 indicators.
-void ct_smooth_test(const double* F, double c4, double c3, const double* D2h, const double* D2m, const double* it,
-                    double eps, int* out, double* outb) {
-  float F32[3], d2h[4], d2m[4], itf[3];
+void ct_smooth_test(const double* w5, double dx, const double* D2h, const double* D2m, const double* it, double eps,
+                    int* out, double* outb) {
+  float F32[3], d2h[4], d2m[4], itf[3], c4f, c3f;
   for (int a = 0; a < 4; ++a) {
     d2h[a] = swale::f32_trunc(D2h[a]);
     d2m[a] = swale::f32_trunc(D2m[a]);
   }
-  for (int a = 0; a < 3; ++a) {
-    F32[a] = swale::f32_trunc(F[a]);
-    itf[a] = swale::f32_trunc(it[a]);
-  }
-  out[0] = swale::sure_smooth_f32(F32, swale::f32_trunc(c4), swale::f32_trunc(c3), d2h, d2m, itf,
-                                  swale::f32_trunc(eps)) ? 1 : 0;
+  for (int a = 0; a < 3; ++a) itf[a] = swale::f32_trunc(it[a]);
+  swale::indicator_factors_f32(w5, dx, F32, c4f, c3f);
+  out[0] = swale::sure_smooth_f32(F32, c4f, c3f, d2h, d2m, itf, swale::f32_trunc(eps)) ? 1 : 0;
   swale::CellGeom G{};
-  for (int a = 0; a < 3; ++a) G.F[a] = F[a];
-  G.c4 = c4;
-  G.c3 = c3;
+  swale::indicator_factors(w5, dx, G);
   for (int e = 0; e < 2; ++e)
     for (int r = 0; r < 3; ++r) G.d[e][r] = 1.0 / 3.0;
   swale::StencilDD DD{};
@@ -87,16 +83,18 @@ void ct_smooth_test(const double* F, double c4, double c3, const double* D2h, co
 
 // The non-well-balanced scheme's per-field FP32 smooth tests and the FP64 classes of the same
 // fields, formed as the device forms them. in: proj[4] = a11, a12, a21, a22; D2e[4], D2m[4],
-// D2h[4] (pair differences of eta, hu, h), it[3], F[3], c4, c3, eps. out[0..2]: FP32 tests of
+// D2h[4] (pair differences of eta, hu, h), it[3], w5[5], dx, eps. out[0..2]: FP32 tests of
 // the two characteristic fields and the bottom, out[3..5]: their FP64 classes, gam[3]: their
 // FP64 gamma.
 void ct_smooth1_test(const double* proj, const double* D2e, const double* D2m, const double* D2h, const double* it,
-                     const double* F, double c4, double c3, double eps, int* out, double* gam) {
-  float F32[3], itf[3], fd[3][4], fm[3][4];
-  for (int a = 0; a < 3; ++a) {
-    F32[a] = swale::f32_trunc(F[a]);
-    itf[a] = swale::f32_trunc(it[a]);
-  }
+                     const double* w5, double dx, double eps, int* out, double* gam) {
+  float F32[3], itf[3], fd[3][4], fm[3][4], c4f, c3f;
+  for (int a = 0; a < 3; ++a) itf[a] = swale::f32_trunc(it[a]);
+  swale::indicator_factors_f32(w5, dx, F32, c4f, c3f);
+  swale::CellGeom G{};
+  swale::indicator_factors(w5, dx, G);
+  const double* F = G.F;
+  const double c4 = G.c4, c3 = G.c3;
   const float a11 = swale::f32_trunc(proj[0]), a12 = swale::f32_trunc(proj[1]);
   const float a21 = swale::f32_trunc(proj[2]), a22 = swale::f32_trunc(proj[3]);
   for (int a = 0; a < 4; ++a) {
@@ -109,8 +107,7 @@ void ct_smooth1_test(const double* proj, const double* D2e, const double* D2m, c
     fm[2][a] = std::fabs(e2) + std::fabs(h2);
   }
   for (int f = 0; f < 3; ++f)
-    out[f] = swale::sure_smooth1_f32(F32, swale::f32_trunc(c4), swale::f32_trunc(c3), fd[f], fm[f], itf,
-                                     swale::f32_trunc(eps)) ? 1 : 0;
+    out[f] = swale::sure_smooth1_f32(F32, c4f, c3f, fd[f], fm[f], itf, swale::f32_trunc(eps)) ? 1 : 0;
   // FP64 as recon_cell_nonwb_g forms it
   double D2[3][4], D3[3][3], fD2[3][4], fD3[3][3];
   for (int a = 0; a < 4; ++a) {

@@ -366,11 +366,13 @@ void launch_recon(const StepConst& K, const DevState& D, int T, unsigned grid, c
     else k_recon<STAGE, 128, 2><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
     return;
   }
-  if (STAGE == 1 && D.geo) {  // stage 1 reads the cached geometry: more resident warps
-    if (T == 64) k_recon<STAGE, 64, 0, true><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
-    else if (T == 256) k_recon<STAGE, 256, 0, true><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
-    else k_recon<STAGE, 128, 0, true><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
-    return;
+  if constexpr (STAGE == 1) {
+    if (D.geo) {  // stage 1 reads the cached geometry: more resident warps
+      if (T == 64) k_recon<STAGE, 64, 0, true><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
+      else if (T == 256) k_recon<STAGE, 256, 0, true><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
+      else k_recon<STAGE, 128, 0, true><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
+      return;
+    }
   }
   if (T == 64) k_recon<STAGE, 64><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
   else if (T == 256) k_recon<STAGE, 256><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
@@ -1223,12 +1225,15 @@ uint64_t adjoint_bytes(int64_t B, int64_t Nt, int64_t nsteps, int64_t ckpt_every
   const uint64_t state_set = 15 * a(Nt, 8) + 2 * a(NN, 8) + 10 * a(NE, 8) + a(NE, 1) + a(B, sizeof(DevScalars));
   const uint64_t common = 15 * a(Nt, 8) + 8 * a(NE, 8) + state_set + 2 * a((uint64_t)B * G, 8) +
                           a((uint64_t)nsteps * B * G, 8) + a(B, 8) + a((uint64_t)nsteps * B * 3, 8);
+  // Segment buffers (per-step snapshots, and the tape's slots): two, one being recomputed while
+  // the other is reversed; one when a single segment covers every step.
+  const uint64_t nb = nseg == 1 ? 1 : 2;
   if (tape) {
     // per step of a segment: three stage edge sets, q^(1), J^(1), q^(2), J^(2), node velocities
     const uint64_t slot = 30 * a(NE, 8) + 8 * a(Nt, 8) + a(NN, 8);
-    return common + (uint64_t)(nseg + 2 * C + 1) * copy + (uint64_t)(2 * C) * slot;
+    return common + (uint64_t)(nseg + nb * C + 1) * copy + (uint64_t)(nb * C) * slot;
   }
-  return common + state_set + 40 * a(NE, 8) + (uint64_t)(nseg + 2 * C + 3) * copy;
+  return common + state_set + 40 * a(NE, 8) + (uint64_t)(nseg + nb * C + 3) * copy;
 }
 
 }  // namespace
@@ -1392,7 +1397,9 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   // snapshot buffers while segment sg is reversed from the other.
   DevState D2;
   alloc_state_set(D2);
-  std::vector<StateCopy> ckpt(nseg), seg(C), seg2(C);
+  // Snapshot buffers of two segments (one when a single segment covers every step).
+  const int64_t nbuf = nseg == 1 ? 1 : 2;
+  std::vector<StateCopy> ckpt(nseg), seg(C), seg2(nbuf == 2 ? C : 0);
   StateCopy fin, snapR[2];
   for (auto& c : ckpt) alloc_copy(c);
   for (auto& c : seg) alloc_copy(c);
@@ -1404,7 +1411,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   // buffer b.
   std::vector<DevState> slot[2];
   if (tape) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < nbuf; ++b) {
       slot[b].resize((size_t)(3 * C));
       for (int64_t i = 0; i < C; ++i) {
         DevState base_i = D2;
@@ -1531,9 +1538,36 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   NvtxRange nvtx_adjoint("swale_adjoint");
   nvtxRangePushA("adjoint forward");
   // ---- forward with checkpoints and the misfit ----
+  // The last segment is the one the reverse sweep starts with: the forward keeps its per-step
+  // snapshots (and in tape mode its stage data) itself, so that segment is not recomputed.
+  const int64_t nlast = (nseg - 1) * C, blast = (nseg - 1) & 1;
+  std::vector<StateCopy>& buf_last = blast ? seg2 : seg;
   for (int64_t n = 0; n < nsteps && !s; ++n) {
     if (n % C == 0 && (e = save(ckpt[n / C]))) break;
-    s = enqueue_step_on(ctx, base, st, nullptr, 0);
+    if (n >= nlast) {
+      if ((e = save(buf_last[n - nlast]))) break;
+      if (tape) {  // the step's stage data into its slot; the state is the context's own
+        DevState f3[3];
+        for (int t = 0; t < 3; ++t) {
+          f3[t] = slot[blast][(size_t)(3 * (n - nlast) + t)];
+          f3[t].E0 = base.E0;
+          f3[t].M0 = base.M0;
+          f3[t].B0 = base.B0;
+          f3[t].J0 = base.J0;
+          f3[t].YE = base.YE;
+          f3[t].YM = base.YM;
+          f3[t].YB = base.YB;
+          f3[t].x = base.x;
+          f3[t].S = base.S;
+          f3[t].flags = base.flags;
+        }
+        s = enqueue_step_on(ctx, f3[2], st, f3, 0);
+      } else {
+        s = enqueue_step_on(ctx, base, st, nullptr, 0);
+      }
+    } else {
+      s = enqueue_step_on(ctx, base, st, nullptr, 0);
+    }
     if (!s) k_misfit<0><<<gg, 128, 0, st>>>(D, A, (int32_t)B, G, gx, obs + n * B * G, Jacc, gcell);
   }
   if (!s && !e) e = save(fin);
@@ -1563,7 +1597,8 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   };
   if (!s && !e) e = cudaEventRecord(ev[0], st);
   if (!s && !e) e = cudaStreamWaitEvent(st2, ev[0], 0);
-  if (!s && !e) recompute_segment(nseg - 1);
+  // The last segment's snapshots (and tape) came from the forward run itself.
+  if (!s && !e) e = cudaEventRecord(ev[1 + blast], st);
   bool used[2] = {false, false};
   int64_t idx = 0;
   for (int64_t sg = nseg - 1; sg >= 0 && !s && !e; --sg) {

@@ -149,6 +149,19 @@ SWALE_HD float f32_trunc(double x) {
 #endif
 }
 
+// The indicator factors of indicator_factors in FP32 from the widths h[5] and the length dx
+// (truncated to FP32): every term of F[0], F[1], -F[2], c4 and c3 is positive, so they come out
+// within 6 u (F), 8 u (c4) and 12 u (c3) of their values.
+SWALE_HD void indicator_factors_f32(const double h[5], double dx, float F[3], float& c4, float& c3) {
+  const float h0 = f32_trunc(h[0]), h1 = f32_trunc(h[1]), h2 = f32_trunc(h[2]), h3 = f32_trunc(h[3]);
+  const float d = f32_trunc(dx);
+  F[0] = fmaf(1.5f, h2, (h0 + h1) + h1);
+  F[1] = fmaf(0.5f, h2, h1);
+  F[2] = -fmaf(0.5f, h2, h3);
+  c4 = (4.0f * d) * h2;
+  c3 = (fmaf(3.0f * h2, h2, 36.0f * d * d) * d) * h2;
+}
+
 // ------------------------------------------------------------------------------------
 // The smooth class decided in FP32 (Step 2 with the shared indicators of Eq. alphamodified).
 // GB300 runs FP32 at about 40x its FP64 rate, and in most cells the detector only has to tell
@@ -157,10 +170,12 @@ SWALE_HD float f32_trunc(double x) {
 // f32_trunc), second differences formed from them in FP32, D3 = (D2_right - D2_left) it, and
 // FP32 copies of the mesh factors, beside the magnitudes
 //   m_r = c4 (Qh^2 + Qm^2) + c3 (Mh^2 + Mm^2),  Q = |D2| + M |F|,  M = (|D2_left| + |D2_right|) it.
-// A rounding-error analysis of these few operations (inputs within 2^-23 relative, FMAs, the
-// second differences within 6 u M, sums of non-negative terms) bounds |beta_r(FP32) - beta_r| by
-// 25 u m_r, u = 2^-24; E below takes 64 u (m_0 + m_1 + m_2), which also covers the rounding of
-// the FP64 indicators (below 2^-48 m), plus a 1e-30 floor for inputs below the FP32 range. If
+// A rounding-error analysis of these few operations (pair differences and triple reciprocals
+// within 2^-23 relative, F within 6 u, c4 within 8 u and c3 within 12 u when they are formed in
+// FP32 from such widths, FMAs, the second differences within 6 u M, sums of non-negative terms)
+// bounds |beta_r(FP32) - beta_r| by 43 u m_r, u = 2^-24; E below takes 96 u (m_0 + m_1 + m_2),
+// which also covers the rounding of the FP64 indicators (below 2^-48 m) and of the sum m itself,
+// plus a 1e-30 floor for inputs below the FP32 range. If
 //   tau32 + E <= (den32 - E) / 2,   tau = |beta_0 - beta_2|, den = mean(beta) + eps,
 // (with 8 u of relative slack on tau32 and den32, and eps rounded down) then the FP64 detector
 // finds gamma <= 1/2 as well, and the cell is smooth. Overflow or NaN make the test false, as
@@ -184,7 +199,7 @@ SWALE_HD bool sure_smooth_f32(const float F[3], float c4, float c3, const float 
   constexpr float u = 5.9604645e-8f;  // 2^-24
   const float tau = fabsf(b[0] - b[2]);
   const float den = (b[0] + b[1] + b[2]) * (1.0f / 3.0f) + eps;
-  const float E = (64.0f * u) * msum + 1e-30f;
+  const float E = (96.0f * u) * msum + 1e-30f;
   return tau * (1.0f + 8.0f * u) + E <= 0.5f * (den * (1.0f - 8.0f * u) - E);
 }
 
@@ -193,7 +208,7 @@ SWALE_HD bool sure_smooth_f32(const float F[3], float c4, float c3, const float 
 // differences d2[4], given in FP32 with magnitudes mag[4] that bound them together with their
 // error (the fields are combinations of the stencil's differences: |error| <= 6 u mag). The
 // analysis of sure_smooth_f32 carries over with Q = mag + M |F|, M = (mag_left + mag_right) it;
-// the bound stays within 64 u (m_0 + m_1 + m_2).
+// the bound stays within 96 u (m_0 + m_1 + m_2).
 SWALE_HD bool sure_smooth1_f32(const float F[3], float c4, float c3, const float d2[4], const float mag[4],
                                const float it[3], float eps) {
   float b[3], msum = 0.0f;
@@ -210,7 +225,7 @@ SWALE_HD bool sure_smooth1_f32(const float F[3], float c4, float c3, const float
   constexpr float u = 5.9604645e-8f;  // 2^-24
   const float tau = fabsf(b[0] - b[2]);
   const float den = (b[0] + b[1] + b[2]) * (1.0f / 3.0f) + eps;
-  const float E = (64.0f * u) * msum + 1e-30f;
+  const float E = (96.0f * u) * msum + 1e-30f;
   return tau * (1.0f + 8.0f * u) + E <= 0.5f * (den * (1.0f - 8.0f * u) - E);
 }
 
@@ -252,7 +267,18 @@ struct CellGeom {
 #define SWALE_GEOM_BASE 25    // doubles of a CellGeom before K (what every scheme uses)
 #define SWALE_GEOM_VALUES 33  // doubles in a CellGeom
 #define SWALE_GEO_ARRAYS (SWALE_GEOM_VALUES + 6)  // cached per cell: a CellGeom and a SourceGeom
-SWALE_HD void cell_geom(const real h[5], real dx, CellGeom& G, uint32_t& st) {
+// Indicator factors of Step 2 (F, c4, c3 of CellGeom) for the widths h[5] and the length dx.
+SWALE_HD void indicator_factors(const real h[5], real dx, CellGeom& G) {
+  const real h1 = h[1], h2 = h[2], h3 = h[3];
+  G.F[0] = 1.5 * h2 + (h[0] + h1) + h1;
+  G.F[1] = 0.5 * h2 + h1;
+  G.F[2] = -(0.5 * h2 + h3);
+  G.c4 = 4.0 * dx * h2;
+  G.c3 = (3.0 * h2 * h2 + 36.0 * dx * dx) * dx * h2;
+}
+// Geometry of the cell; with indicators = false the indicator factors are left out (the device
+// forms them in FP32 for its smooth-class test and in FP64 only where that test cannot decide).
+SWALE_HD void cell_geom(const real h[5], real dx, CellGeom& G, uint32_t& st, bool indicators = true) {
   const real h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3], h4 = h[4];
   if (!gt0(h2)) st |= ST_EMESH;
   // Node offsets relative to x_{j-1/2}: y0 = -(h0+h1), y1 = -h1, y2 = 0, y3 = h2,
@@ -289,11 +315,7 @@ SWALE_HD void cell_geom(const real h[5], real dx, CellGeom& G, uint32_t& st) {
   G.d[1][1] = 1.0 - G.d[1][0] - G.d[1][2];
   if (!gt0(G.d[0][1]) || !gt0(G.d[1][1])) st |= ST_EWEIGHT;
   // Indicator factors: F[a] = 1.5 h2 - (y_a+y_{a+1}+y_{a+2}); beta = c4 q^2 + c3 D3^2 per variable.
-  G.F[0] = 1.5 * h2 + s01 + h1;
-  G.F[1] = 0.5 * h2 + h1;
-  G.F[2] = -(0.5 * h2 + h3);
-  G.c4 = 4.0 * dx * h2;
-  G.c3 = (3.0 * h2 * h2 + 36.0 * dx * dx) * dx * h2;
+  if (indicators) indicator_factors(h, dx, G);
   for (int e = 0; e < 2; ++e)
     for (int m = 0; m < 4; ++m) G.K[e][m] = real(0.0);
 }

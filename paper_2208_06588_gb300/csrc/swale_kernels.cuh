@@ -619,12 +619,18 @@ __global__ void __launch_bounds__(T, (HIOCC ? 1024 : 512) / T) k_recon(StepConst
       swale::CellGeom G;
       double* gv = reinterpret_cast<double*>(&G);
       constexpr int kGeo = SCHEME == 0 ? SWALE_GEOM_VALUES : SWALE_GEOM_BASE;  // values cached
+      // The indicator factors (F, c4, c3) are not cached: they are formed below, in FP32 for the
+      // smooth-class test and in FP64 only where that test cannot decide.
+      constexpr int kF0 = offsetof(swale::CellGeom, F) / sizeof(double), kF1 = kF0 + 5;
+      static_assert(offsetof(swale::CellGeom, c4) / sizeof(double) == kF0 + 4, "F, c3, c4 are adjacent");
+      const double dxe = K.sc.beta_dx_global ? dxmax : h[2];
       if (use_geo) {
 #pragma unroll
-        for (int k = 0; k < kGeo; ++k) gv[k] = D.geo[k * D.geo_stride + idx];
+        for (int k = 0; k < kGeo; ++k)
+          if (k < kF0 || k >= kF1) gv[k] = D.geo[k * D.geo_stride + idx];
         if (!swale::gt0(h[2])) st |= swale::ST_EMESH;
       } else {
-        swale::cell_geom(h, K.sc.beta_dx_global ? dxmax : h[2], G, st);
+        swale::cell_geom(h, dxe, G, st, false);
         if (SCHEME == 0) {
           const double it3[3] = {sIT[tid], sIT[tid + 1], sIT[tid + 2]};
           swale::smooth_edge_coeffs(h, it3, G);
@@ -632,18 +638,18 @@ __global__ void __launch_bounds__(T, (HIOCC ? 1024 : 512) / T) k_recon(StepConst
       }
       if (STAGE == 2 && D.geo) {
 #pragma unroll
-        for (int k = 0; k < kGeo; ++k) D.geo[k * D.geo_stride + idx] = gv[k];
+        for (int k = 0; k < kGeo; ++k)
+          if (k < kF0 || k >= kF1) D.geo[k * D.geo_stride + idx] = gv[k];
       }
       EdgeState o;
       uint8_t flag;
       double etaG[2] = {0.0, 0.0};
-      float F32[3], itf[3];
+      // Indicator factors in FP32 from the FP32 widths.
+      float F32[3], itf[3], c4f, c3f;
+      swale::indicator_factors_f32(h, dxe, F32, c4f, c3f);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        F32[a] = swale::f32_trunc(G.F[a]);
-        itf[a] = sITf[tid + a];
-      }
-      const float c4f = swale::f32_trunc(G.c4), c3f = swale::f32_trunc(G.c3), epsf = swale::f32_trunc(K.sc.eps_weno);
+      for (int a = 0; a < 3; ++a) itf[a] = sITf[tid + a];
+      const float epsf = swale::f32_trunc(K.sc.eps_weno);
       if (SCHEME == 1) {
         // Each characteristic field and the bottom: its smooth class in FP32 when that can be
         // told for sure, from the FP32 pair differences of eta, hu, h and the projection rows.
@@ -664,6 +670,7 @@ __global__ void __launch_bounds__(T, (HIOCC ? 1024 : 512) / T) k_recon(StepConst
         bool known[3];
 #pragma unroll
         for (int f = 0; f < 3; ++f) known[f] = swale::sure_smooth1_f32(F32, c4f, c3f, fd[f], fm[f], itf, epsf);
+        if (!(known[0] && known[1] && known[2])) swale::indicator_factors(h, dxe, G);
         swale::recon_cell_nonwb_g(K.sc, G, v0, DD, o, flag, st, pr, known);
       } else {
         // The smooth class, when FP32 can tell it for sure; else the FP64 detector decides.
@@ -674,11 +681,14 @@ __global__ void __launch_bounds__(T, (HIOCC ? 1024 : 512) / T) k_recon(StepConst
           d2m[a] = sD2f[0][tid + a];
         }
         const bool smooth32 = swale::sure_smooth_f32(F32, c4f, c3f, d2h, d2m, itf, epsf);
-        if (SCHEME == 0 && !smooth32) {  // the FP64 detector and the WENO-Z edge values need them
+        if (!smooth32) {  // the FP64 detector (and the WENO-Z edge values) need these
+          swale::indicator_factors(h, dxe, G);
+          if (SCHEME == 0) {
 #pragma unroll
-          for (int v = 0; v < 3; ++v)
+            for (int v = 0; v < 3; ++v)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) DD.D3[v][a] = swale::triple_dd(DD.D2[v][a], DD.D2[v][a + 1], sIT[tid + a]);
+              for (int a = 0; a < 3; ++a) DD.D3[v][a] = swale::triple_dd(DD.D2[v][a], DD.D2[v][a + 1], sIT[tid + a]);
+          }
         }
         if (SCHEME == 2) swale::recon_cell_special_g(K.sc, G, h, v0, DD, o, flag, st, etaG, smooth32);
         else swale::recon_cell_g(K.sc, G, v0, DD, o, flag, st, smooth32);

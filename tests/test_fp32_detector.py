@@ -23,10 +23,7 @@ def _random_cell(rng, scale_spread=6.0):
     cancellation between D2 and D3 F, smooth data (small second differences), still water."""
     dx = 10.0 ** rng.uniform(-6, 2)
     w = dx * rng.uniform(0.2, 1.0, 5)  # widths J_{j-2..j+2}
-    h0, h1, h2, h3, h4 = w
-    F = np.array([1.5 * h2 + h0 + 2 * h1, 0.5 * h2 + h1, -(0.5 * h2 + h3)])
-    c4 = 4.0 * dx * h2
-    c3 = (3.0 * h2 * h2 + 36.0 * dx * dx) * dx * h2
+    F = np.array([1.5 * w[2] + w[0] + 2 * w[1], 0.5 * w[2] + w[1], -(0.5 * w[2] + w[3])])  # for the cancellations
     it = 1.0 / (w[:3] + w[1:4] + w[2:])
     s = 10.0 ** rng.uniform(-scale_spread, scale_spread)
     kind = rng.integers(4)
@@ -39,7 +36,7 @@ def _random_cell(rng, scale_spread=6.0):
         D2m = D2m[0] * (1.0 + 1e-3 * rng.normal(size=4))
     elif kind == 3:  # still water: no discharge
         D2m = np.zeros(4)
-    return F, c4, c3, D2h, D2m, it
+    return w, dx, D2h, D2m, it
 
 
 def test_fp32_smooth_implies_fp64_smooth_on_random_cells():
@@ -65,16 +62,16 @@ def test_fp32_test_stays_off_near_the_threshold(seed):
     the smooth class, and a hair below it (gamma = 0.5 (1 - 1e-8)) it declines too: it keeps a
     margin of about 1e-5 relative."""
     rng = np.random.default_rng(seed)
-    F, c4, c3, _, _, it = _random_cell(rng, scale_spread=2.0)
+    w5, dx, _, _, it = _random_cell(rng, scale_spread=2.0)
     eps = 1e-6
     sh, sm = 10.0 ** rng.uniform(-2, 2, 2)
     smooth_h = sh * (1.0 + 1e-3 * rng.normal(size=4))
     smooth_m = sm * (1.0 + 1e-3 * rng.normal(size=4))
     for _ in range(100):
         rough_h, rough_m = sh * rng.normal(size=4) * 10.0, sm * rng.normal(size=4) * 10.0
-        if C.smooth_test(F, c4, c3, rough_h, rough_m, it, eps=eps)[1] == 2:
+        if C.smooth_test(w5, dx, rough_h, rough_m, it, eps=eps)[1] == 2:
             break
-    at = lambda t: C.smooth_test(F, c4, c3, (1 - t) * smooth_h + t * rough_h, (1 - t) * smooth_m + t * rough_m, it,
+    at = lambda t: C.smooth_test(w5, dx, (1 - t) * smooth_h + t * rough_h, (1 - t) * smooth_m + t * rough_m, it,
                                  eps=eps)
     g = lambda t: _gamma(at(t)[2], eps)
 
@@ -106,13 +103,15 @@ def test_fp32_test_stays_off_near_the_threshold(seed):
 
 
 def test_fp32_test_on_still_water_and_non_finite_data():
-    F, c4, c3, it = np.array([1e-3, 5e-4, -5e-4]), 4e-6, 4e-12, np.full(3, 1.0 / 3e-3)
+    w5, dx, it = np.full(5, 1e-3), 1e-3, np.full(3, 1.0 / 3e-3)
     z = np.zeros(4)
-    assert C.smooth_test(F, c4, c3, z, z, it, 1e-6)[:2] == (True, 0)
+    assert C.smooth_test(w5, dx, z, z, it, 1e-6)[:2] == (True, 0)
     nan = np.array([np.nan, 0.0, 0.0, 0.0])
-    assert C.smooth_test(F, c4, c3, nan, z, it, 1e-6)[0] is False
+    assert C.smooth_test(w5, dx, nan, z, it, 1e-6)[0] is False
     big = np.array([1e200, 0.0, 0.0, 0.0])
-    assert C.smooth_test(F, c4, c3, big, z, it, 1e-6)[0] is False
+    assert C.smooth_test(w5, dx, big, z, it, 1e-6)[0] is False
+    # widths far beyond the FP32 range: the factors overflow, the test declines
+    assert C.smooth_test(np.full(5, 1e30), 1e30, z + 1.0, z, np.full(3, 1e-30), 1e-6)[0] is False
 
 
 def test_f32_trunc_matches_the_float_conversion_toward_zero():
@@ -129,7 +128,7 @@ def test_f32_trunc_matches_the_float_conversion_toward_zero():
 
 def _random_field_cell(rng):
     """Projection rows of a wet cell (u, c) and the stencil data of eta, hu, h."""
-    F, c4, c3, D2h, D2m, it = _random_cell(rng)
+    w5, dx, D2h, D2m, it = _random_cell(rng)
     s = np.abs(D2h).max() + np.abs(D2m).max() + 1e-300
     D2e = D2h + s * (1e-3 * rng.normal(size=4) if rng.random() < 0.5 else rng.normal(size=4))
     u, c = rng.normal(), 10.0 ** rng.uniform(-1, 1.5)
@@ -138,7 +137,7 @@ def _random_field_cell(rng):
     else:
         i2c = 0.5 / c
         proj = np.array([(u + c) * i2c, -i2c, (c - u) * i2c, i2c])
-    return proj, D2e, D2m, D2h, it, F, c4, c3
+    return proj, D2e, D2m, D2h, it, w5, dx
 
 
 def test_field_fp32_smooth_implies_fp64_smooth():
@@ -163,15 +162,15 @@ def test_field_fp32_test_stays_off_near_the_threshold(seed):
     gamma crosses 1/2: just above it the field's FP32 test never claims the smooth class, a hair
     below it it declines too."""
     rng = np.random.default_rng(100 + seed)
-    proj, _, _, _, it, F, c4, c3 = _random_field_cell(rng)
+    proj, _, _, _, it, w5, dx = _random_field_cell(rng)
     eps = 1e-6
     s = 10.0 ** rng.uniform(-2, 2)
     smooth = [s * (1.0 + 1e-3 * rng.normal(size=4)) for _ in range(3)]
     for _ in range(100):
         rough = [s * 10.0 * rng.normal(size=4) for _ in range(3)]
-        if min(C.smooth1_test(proj, *rough, it, F, c4, c3, eps)[1]) == 2:
+        if min(C.smooth1_test(proj, *rough, it, w5, dx, eps)[1]) == 2:
             break
-    at = lambda t: C.smooth1_test(proj, *[(1 - t) * a + t * b for a, b in zip(smooth, rough)], it, F, c4, c3, eps)
+    at = lambda t: C.smooth1_test(proj, *[(1 - t) * a + t * b for a, b in zip(smooth, rough)], it, w5, dx, eps)
     g0, g1 = at(0.0)[2], at(1.0)[2]
     crossed = 0
     for f in range(3):
