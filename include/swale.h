@@ -294,8 +294,8 @@ swale_status swale_get_alpha_log(swale_ctx* ctx, double* log);
  * (no reuse of the previous step's), so the trajectory, and the gradient up to the order of
  * atomic additions, does not depend on ckpt_every. Device memory beyond the context's own: about
  * 5 (ceil(nsteps/C) + b C + 3) + 117 doubles per cell with C = min(ckpt_every, nsteps) and b = 2
- * segment buffers (1 when C = nsteps), exactly the value of swale_adjoint_bytes; all of it (and
- * the two streams) is freed before the call returns. With ckpt_every >= nsteps every step runs
+ * segment buffers (1 when C = nsteps), taken as one block of exactly swale_adjoint_bytes bytes
+ * (a single cudaMalloc); the block and the two streams are freed before the call returns. With ckpt_every >= nsteps every step runs
  * twice (once in tape mode). The mesh must be prescribed (static, profile or linear motion) and
  * t_end = 0. On return the context holds the state after the nsteps steps.
  * Errors: SWALE_EINVAL, SWALE_ENOMEM, SWALE_ECUDA, and the status errors of swale_advance. */

@@ -5,6 +5,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1215,12 +1216,16 @@ struct StateCopy {
   DevScalars* S;
 };
 
-// Bytes of the device arrays swale_adjoint allocates (each dalloc adds 256 bytes of slack); the
-// list follows the allocations in swale_adjoint one for one.
+// Bytes one array of swale_adjoint takes in its block: rounded up to 256 bytes, plus 256 bytes of
+// slack as every device array of the library has.
+uint64_t adj_block(uint64_t bytes) { return (bytes + 255) / 256 * 256 + 256; }
+
+// Bytes of the device block swale_adjoint carves its arrays from; the list follows the arrays in
+// swale_adjoint one for one.
 uint64_t adjoint_bytes(int64_t B, int64_t Nt, int64_t nsteps, int64_t ckpt_every, int32_t G, int32_t tape) {
   const int64_t NN = Nt + B, NE = Nt + 2 * B;
   const int64_t C = std::min(ckpt_every, nsteps), nseg = (nsteps + C - 1) / C;
-  auto a = [](uint64_t n, uint64_t size) { return n * size + 256; };
+  auto a = [](uint64_t n, uint64_t size) { return adj_block(n * size); };
   const uint64_t copy = 4 * a(Nt, 8) + a(NN, 8) + a(B, sizeof(DevScalars));
   const uint64_t state_set = 15 * a(Nt, 8) + 2 * a(NN, 8) + 10 * a(NE, 8) + a(NE, 1) + a(B, sizeof(DevScalars));
   const uint64_t common = 15 * a(Nt, 8) + 8 * a(NE, 8) + state_set + 2 * a((uint64_t)B * G, 8) +
@@ -1317,13 +1322,32 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   cudaStream_t st = ctx->stream;
   std::vector<void*> mem;
   swale_status s = SWALE_OK;
+  // All of the call's device arrays are carved from one block of exactly swale_adjoint_bytes
+  // bytes: one cudaMalloc and one cudaFree per call, however many segment buffers and tape
+  // slots it holds (at large checkpoint intervals the tape alone has tens of thousands of
+  // arrays, whose separate allocations took longer than the gradient).
+  const uint64_t arena_bytes = adjoint_bytes(B, Nt, nsteps, ckpt_every, G, tape ? 1 : 0);
+  char* arena = nullptr;
+  uint64_t arena_off = 0;
+  if (cudaError_t e0 = cudaMalloc(&arena, arena_bytes)) {
+    cudaGetLastError();
+    return fail(ctx, SWALE_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e0));
+  }
+  mem.push_back(arena);
+  auto carve = [&](auto** p, size_t n) -> swale_status {
+    const uint64_t need = adj_block(n * sizeof(**p));
+    if (arena_off + need > arena_bytes) return fail(ctx, SWALE_ENOMEM, "adjoint: scratch layout exceeds its block");
+    *p = reinterpret_cast<std::remove_reference_t<decltype(*p)>>(arena + arena_off);
+    arena_off += need;
+    return SWALE_OK;
+  };
   auto alloc_copy = [&](StateCopy& c) {
-    if (!s) s = dalloc(ctx, mem, &c.E, (size_t)Nt);
-    if (!s) s = dalloc(ctx, mem, &c.M, (size_t)Nt);
-    if (!s) s = dalloc(ctx, mem, &c.B, (size_t)Nt);
-    if (!s) s = dalloc(ctx, mem, &c.J, (size_t)Nt);
-    if (!s) s = dalloc(ctx, mem, &c.x, (size_t)NN);
-    if (!s) s = dalloc(ctx, mem, &c.S, (size_t)B);
+    if (!s) s = carve(&c.E, (size_t)Nt);
+    if (!s) s = carve(&c.M, (size_t)Nt);
+    if (!s) s = carve(&c.B, (size_t)Nt);
+    if (!s) s = carve(&c.J, (size_t)Nt);
+    if (!s) s = carve(&c.x, (size_t)NN);
+    if (!s) s = carve(&c.S, (size_t)B);
   };
   // Three streams: the context's (forward run, reverse kernels), st2 (segment recomputes, low
   // priority), st3 (the recompute of each step before its reverse sweep). Events: 0 forward
@@ -1346,8 +1370,8 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   double** cellbufs[] = {&A.lE, &A.lM, &A.lB, &A.yE, &A.yM, &A.yB, &A.pE, &A.pM, &A.pB,
                          &A.aE, &A.aM, &A.aB, &A.rE, &A.rM, &A.rB};
   for (double** p : cellbufs)
-    if (!s) s = dalloc(ctx, mem, p, (size_t)Nt);
-  for (int k = 0; k < 8 && !s; ++k) s = dalloc(ctx, mem, &A.ab[k], (size_t)NE);
+    if (!s) s = carve(p, (size_t)Nt);
+  for (int k = 0; k < 8 && !s; ++k) s = carve(&A.ab[k], (size_t)NE);
   // Every forward run of the adjoint (the forward with checkpoints, the segment and the step
   // recomputes) computes the mesh geometry in all three stages instead of taking stage 1's from
   // the cache: a run that starts from a checkpoint has no cache entry, so with the cache the
@@ -1367,14 +1391,14 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     double** cells[] = {&X.E0, &X.M0, &X.B0, &X.Ea, &X.Ma, &X.Ba, &X.Eb, &X.Mb,
                         &X.Bb, &X.YE, &X.YM, &X.YB, &X.J0, &X.J1, &X.J2};
     for (double** p : cells)
-      if (!s) s = dalloc(ctx, mem, p, (size_t)Nt);
-    if (!s) s = dalloc(ctx, mem, &X.x, (size_t)NN);
-    if (!s) s = dalloc(ctx, mem, &X.w, (size_t)NN);
+      if (!s) s = carve(p, (size_t)Nt);
+    if (!s) s = carve(&X.x, (size_t)NN);
+    if (!s) s = carve(&X.w, (size_t)NN);
     double** edges[] = {&X.eEL, &X.eER, &X.eBL, &X.eBR, &X.ehL, &X.ehR, &X.euL, &X.euR, &X.ipair, &X.itri};
     for (double** p : edges)
-      if (!s) s = dalloc(ctx, mem, p, (size_t)NE);
-    if (!s) s = dalloc(ctx, mem, &X.flags, (size_t)NE);
-    if (!s) s = dalloc(ctx, mem, &X.S, (size_t)B);
+      if (!s) s = carve(p, (size_t)NE);
+    if (!s) s = carve(&X.flags, (size_t)NE);
+    if (!s) s = carve(&X.S, (size_t)B);
   };
   // The step recomputes alternate between two state sets R[0] (the context's arrays) and R[1],
   // so that the recompute of step m - 1 (on st3) overlaps the reverse sweep of step m. Each set
@@ -1382,7 +1406,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
   auto alloc_edges = [&](DevState& d) {
     double** ed[] = {&d.eEL, &d.eER, &d.eBL, &d.eBR, &d.ehL, &d.ehR, &d.euL, &d.euR, &d.ipair, &d.itri};
     for (double** p : ed)
-      if (!s) s = dalloc(ctx, mem, p, (size_t)NE);
+      if (!s) s = carve(p, (size_t)NE);
   };
   DevState R[2], Ds[2][3];
   if (!tape) {
@@ -1418,8 +1442,8 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
         double** st_arr[] = {&base_i.Ea, &base_i.Ma, &base_i.Ba, &base_i.J1,
                              &base_i.Eb, &base_i.Mb, &base_i.Bb, &base_i.J2};
         for (double** p : st_arr)
-          if (!s) s = dalloc(ctx, mem, p, (size_t)Nt);
-        if (!s) s = dalloc(ctx, mem, &base_i.w, (size_t)NN);
+          if (!s) s = carve(p, (size_t)Nt);
+        if (!s) s = carve(&base_i.w, (size_t)NN);
         for (int t = 0; t < 3; ++t) {
           slot[b][3 * i + t] = base_i;
           alloc_edges(slot[b][3 * i + t]);
@@ -1433,12 +1457,12 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     alloc_copy(snapR[1]);
   }
   double *gx = nullptr, *obs = nullptr, *Jacc = nullptr, *alog = nullptr;
-  if (!s) s = dalloc(ctx, mem, &gx, (size_t)B * G);
-  if (!s) s = dalloc(ctx, mem, &obs, (size_t)nsteps * B * G);
-  if (!s) s = dalloc(ctx, mem, &Jacc, (size_t)B);
-  if (!s) s = dalloc(ctx, mem, &alog, (size_t)nsteps * B * 3);
+  if (!s) s = carve(&gx, (size_t)B * G);
+  if (!s) s = carve(&obs, (size_t)nsteps * B * G);
+  if (!s) s = carve(&Jacc, (size_t)B);
+  if (!s) s = carve(&alog, (size_t)nsteps * B * 3);
   int64_t* gcell = nullptr;  // last cell of each gauge (searched from, the mesh moves little per step)
-  if (!s) s = dalloc(ctx, mem, &gcell, (size_t)B * G);
+  if (!s) s = carve(&gcell, (size_t)B * G);
   if (s) return release(s);
   // q^n and J^n of the step being reversed, per state set.
   AdjState AR[2] = {A, A};
