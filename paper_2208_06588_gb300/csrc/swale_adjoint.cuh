@@ -95,9 +95,10 @@ SWALE_HD void source_dd_rev(const SourceGeom& sg, const real cb[6], real ub[5]) 
 }
 
 // Adjoint of source_cell: accumulates into hdb[5], bdb[5] the adjoints of the depth and bottom
-// data for the adjoint Sb of the source value. The reverse of source_cell's own steps: Newton
+// data for the adjoint Sb of the source value. The reverse of the steps of the same map: Newton
 // coefficients by confluent divided differences, their monomial form a (depth) and ab (bottom),
-// S = -g sum_{i, m} a_i ab_m m / (i + m); then transposed in the opposite order.
+// S = -g sum_{i, m} a_i ab_m m / (i + m) (source_cell folds the factors of a_i and ab_m into
+// these constants; the map is the same); then transposed in the opposite order.
 SWALE_HD void source_cell_rev(real g, const real hd[5], const real bd[5], const SourceGeom& sg, real Sb, real hdb[5],
                               real bdb[5]) {
   real ch[6], cb[6];

@@ -782,12 +782,15 @@ SWALE_HD real source_cell(real g, const real hd[5], const real bd[5], const Sour
     c[5] = o5;
   }
   // Basis n_k = (t + rm) m_k(t), m_2 = t, m_3 = t^2, m_4 = t^3 - t^2, m_5 = t^4 - 2 t^3 + t^2.
-  // The interpolant Pi' = c_1 + sum_k c_k n_k' in monomials a_0 + a_1 t + ... + a_4 t^4:
-  //   n_2' = 2t + rm,  n_3' = 3t^2 + 2 rm t,  n_4' = 4t^3 + 3(rm - 1) t^2 - 2 rm t,
-  //   n_5' = 5t^4 + 4(rm - 2) t^3 + 3(1 - 2 rm) t^2 + 2 rm t.
+  // The interpolant Pi' = c_1 + sum_k c_k n_k' in monomials a_0 + a_1 t + ... + a_4 t^4, with
+  // q = c_3 - c_4 + c_5 and d = c_4 - 2 c_5:
+  //   a_0 = c_1 + rm c_2,  a_1 = 2 (c_2 + rm q),  a_2 = 3 (q + rm d),  a_3 = 4 (d + rm c_5),
+  //   a_4 = 5 c_5.
   // The bottom's slope is the derivative of its interpolant, sum_m m ab_m t^(m-1), and the
   // integral of the product over [0, 1] is exact: sum_{i, m} a_i ab_m m / (i + m) (the
   // 4-point Gauss-Legendre rule of the definition is exact for this degree-7 product too).
+  // The factors (i + 1) of a_i and (m + 1) of ab_m are folded into that sum's constants, so
+  // the monomial coefficients are formed without them (a_i / (i + 1)).
   const real rm = sg.rm;
   real a[5], ab[5];
   const real* cs[2] = {ch, cb};
@@ -796,16 +799,23 @@ SWALE_HD real source_cell(real g, const real hd[5], const real bd[5], const Sour
     const real* c = cs[v];
     real* o = ms[v];
     const real q = c[3] - c[4] + c[5];
-    o[0] = c[1] + c[2] * rm;
-    o[1] = 2.0 * (c[2] + rm * q);
-    o[2] = 3.0 * q + rm * (3.0 * c[4] - 6.0 * c[5]);
-    o[3] = 4.0 * (c[4] - 2.0 * c[5]) + (4.0 * rm) * c[5];
-    o[4] = 5.0 * c[5];
+    const real d = c[4] - 2.0 * c[5];
+    o[0] = c[1] + rm * c[2];
+    o[1] = c[2] + rm * q;
+    o[2] = q + rm * d;
+    o[3] = d + rm * c[5];
+    o[4] = c[5];
   }
+  // (i + 1)(m + 1) m / (i + m) for i = 0..4 (rows), m = 1..4 (columns)
+  constexpr double kW[5][4] = {{2.0, 3.0, 4.0, 5.0},
+                               {2.0, 4.0, 6.0, 8.0},
+                               {2.0, 3.0 * 6.0 / 4.0, 3.0 * 12.0 / 5.0, 3.0 * 20.0 / 6.0},
+                               {2.0, 4.0 * 6.0 / 5.0, 4.0 * 12.0 / 6.0, 4.0 * 20.0 / 7.0},
+                               {2.0, 5.0 * 6.0 / 6.0, 5.0 * 12.0 / 7.0, 5.0 * 20.0 / 8.0}};
   real S = 0.0;
+#pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const real vi = ab[1] * (1.0 / (i + 1)) + ab[2] * (2.0 / (i + 2)) + ab[3] * (3.0 / (i + 3)) +
-                    ab[4] * (4.0 / (i + 4));
+    const real vi = ab[1] * kW[i][0] + ab[2] * kW[i][1] + ab[3] * kW[i][2] + ab[4] * kW[i][3];
     S += a[i] * vi;
   }
   return -g * S;
