@@ -459,12 +459,14 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevSta
 // reciprocals for the update kernel of the same stage, reduces the wave speed, and in stage 1
 // the instance's last tile computes its dt (and the secant factor of the prescribed motion).
 // ------------------------------------------------------------------------------------
-// HIOCC: a launch bound of 8 blocks of 128 threads per SM (64 registers) instead of 4 (128), for
+// Launch bounds (resident threads per SM): HIOCC, 8 blocks of 128 threads (64 registers), for
 // stage 1 of the well-balanced scheme when it reads the cached mesh geometry: its per-cell work is
 // light enough there that more resident warps win (measured: 0.8 % of the dam-break step), while
-// every instantiation that computes the geometry itself spills heavily under that bound.
+// every instantiation that computes the geometry itself spills heavily under that bound. The
+// other well-balanced instantiations take 640 threads (5 blocks of 128, 96 registers, a few
+// spilled doubles; 0.6 % faster per step than 4 blocks of 128 registers), the other schemes 512.
 template <int STAGE, int T, int SCHEME = 0, bool HIOCC = false>
-__global__ void __launch_bounds__(T, (HIOCC ? 1024 : 512) / T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
+__global__ void __launch_bounds__(T, (HIOCC ? 1024 : (SCHEME == 0 ? 640 : 512)) / T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
                                              const double* __restrict__ Mg, const double* __restrict__ Bg,
                                              const double* __restrict__ Jg) {
   __shared__ double sJ[T + 4], sV[3][T + 4];    // cells c0-2 .. c0+T+1
@@ -624,9 +626,13 @@ __global__ void __launch_bounds__(T, (HIOCC ? 1024 : 512) / T) k_recon(StepConst
       constexpr int kF0 = offsetof(swale::CellGeom, F) / sizeof(double), kF1 = kF0 + 5;
       static_assert(offsetof(swale::CellGeom, c4) / sizeof(double) == kF0 + 4, "F, c3, c4 are adjacent");
       const double dxe = K.sc.beta_dx_global ? dxmax : h[2];
+      // The well-balanced scheme reads only the smooth-class form K here; the rest of the cached
+      // geometry (sub-stencil factors and linear weights) only for a cell whose class the FP32
+      // test leaves open.
+      constexpr int kLoad0 = SCHEME == 0 ? SWALE_GEOM_BASE : 0;
       if (use_geo) {
 #pragma unroll
-        for (int k = 0; k < kGeo; ++k)
+        for (int k = kLoad0; k < kGeo; ++k)
           if (k < kF0 || k >= kF1) gv[k] = D.geo[k * D.geo_stride + idx];
         if (!swale::gt0(h[2])) st |= swale::ST_EMESH;
       } else {
@@ -682,6 +688,11 @@ __global__ void __launch_bounds__(T, (HIOCC ? 1024 : 512) / T) k_recon(StepConst
         }
         const bool smooth32 = swale::sure_smooth_f32(F32, c4f, c3f, d2h, d2m, itf, epsf);
         if (!smooth32) {  // the FP64 detector (and the WENO-Z edge values) need these
+          if (SCHEME == 0 && use_geo) {
+#pragma unroll
+            for (int k = 0; k < kLoad0; ++k)
+              if (k < kF0 || k >= kF1) gv[k] = D.geo[k * D.geo_stride + idx];
+          }
           swale::indicator_factors(h, dxe, G);
           if (SCHEME == 0) {
 #pragma unroll
