@@ -32,16 +32,17 @@ UNIT = "cell-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
 # DRAM bytes (read + write) of a k_recon launch on this workload, averaged over the three
 # stages, from one ncu capture of the current kernels (the autotuner's 128-cell tiles, staged by
-# bulk copies): stage 1 reads the cached mesh geometry, 33 values per cell (302.4 + 68.6 MB),
-# stage 2 writes it (42.0 + 302.3 MB), stage 3 does neither (42.0 + 27.8 MB).
-RECON_DRAM_BYTES = (302_441_472 + 68_557_568 + 42_029_824 + 302_268_416 + 42_001_408 + 27_838_976) // 3
+# bulk copies): stage 1 reads the smooth-class form of the cached mesh geometry, 8 values per
+# cell, and the rest only where the FP32 test leaves the class open (111.2 + 121.9 MB), stage 2
+# writes the geometry (42.0 + 281.6 MB), stage 3 does neither (42.0 + 31.1 MB).
+RECON_DRAM_BYTES = (111_244_544 + 121_948_672 + 42_036_736 + 281_562_368 + 42_001_664 + 31_069_440) // 3
 # Fraction of cycles the FP64 pipe was busy during the same k_recon launches (ncu
 # sm__pipe_fp64_cycles_active, the three stages): the kernel is bound by FP64 instruction issue.
-RECON_FP64_PIPE_ACTIVE = (0.6930 + 0.8558 + 0.8603) / 3
+RECON_FP64_PIPE_ACTIVE = (0.7807 + 0.8544 + 0.8637) / 3
 # FP64 FLOP equivalents per cell the same launches executed (ncu dadd + dmul + 2 dfma
 # instructions over the 2^20 cells; stages 1, 2, 3): what the hardware did, beside the method's
 # and the kernels' own counts.
-RECON_EXECUTED_FLOPS = (131.5 + 233.7 + 228.0) / 3
+RECON_EXECUTED_FLOPS = (125.4 + 208.6 + 205.9) / 3
 # The method's FP64 operations per cell, counted by the CPU oracle on an operation-counting
 # scalar type (oracle.count_step; tests/test_bench_contract.py recounts them): the arithmetic on
 # state-dependent values of one stage's reconstruction + limiter, and of one whole SSP-RK3 step,
@@ -55,10 +56,12 @@ ORACLE_STEP_FLOPS = 1891.80
 ORACLE_BATCH_STEP_FLOPS = 1893.17
 # The same counts for the scheme variants on the dam-break workload (reconstruction, step).
 ORACLE_VARIANT_FLOPS = {"nonwb": (583.01, 2613.02), "special": (366.61, 1780.82)}
-# DRAM bytes per k_update launch (stages 1, 2, 3: 159.5 + 41.3, 184.7 + 70.1, 184.7 + 52.5 MB) and
-# FP64 FLOP equivalents per cell the update launches executed (ncu, as for k_recon below).
-UPDATE_DRAM_BYTES = (159_465_984 + 41_309_184 + 184_676_096 + 70_060_288 + 184_729_600 + 52_483_072) // 3
-UPDATE_EXECUTED_FLOPS = (200.2 + 207.2 + 219.2) / 3
+# DRAM bytes per k_update launch (stages 1, 2, 3: 159.5 + 41.4, 184.7 + 70.0, 184.8 + 52.2 MB), the
+# fraction of cycles its FP64 pipe was busy and the FP64 FLOP equivalents per cell it executed
+# (ncu, the same capture as for k_recon above).
+UPDATE_DRAM_BYTES = (159_469_824 + 41_373_696 + 184_669_184 + 69_971_456 + 184_781_568 + 52_249_600) // 3
+UPDATE_FP64_PIPE_ACTIVE = (0.8617 + 0.8614 + 0.8553) / 3
+UPDATE_EXECUTED_FLOPS = (185.2 + 192.2 + 204.2) / 3
 
 
 def parse():
@@ -789,7 +792,7 @@ def main():
                            "operations (kernel_count, executed), so this fraction can exceed the hardware's",
             "kernel_count": {"flops_per_cell": kernel_flops_cell,
                              "frac": kernel_flops_cell * per_s / 1e12 / FP64_PEAK_TFLOPS},
-            "ncu_fp64_pipe_active": RECON_FP64_PIPE_ACTIVE if dom == "reconstruction" else (0.8539 + 0.8545 + 0.8495) / 3,
+            "ncu_fp64_pipe_active": RECON_FP64_PIPE_ACTIVE if dom == "reconstruction" else UPDATE_FP64_PIPE_ACTIVE,
             "executed": {"flops_per_cell": RECON_EXECUTED_FLOPS if dom == "reconstruction" else UPDATE_EXECUTED_FLOPS,
                          "frac": (RECON_EXECUTED_FLOPS if dom == "reconstruction" else UPDATE_EXECUTED_FLOPS) * per_s
                          / 1e12 / FP64_PEAK_TFLOPS,
