@@ -459,6 +459,40 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevSta
 // reciprocals for the update kernel of the same stage, reduces the wave speed, and in stage 1
 // the instance's last tile computes its dt (and the secant factor of the prescribed motion).
 // ------------------------------------------------------------------------------------
+// A cell of the well-balanced scheme whose smooth class the FP32 test leaves open, out of line:
+// the rest of its cached geometry (stage 1), the indicator factors and triple differences, the
+// FP64 detector and the edge values of its class. A call, not inlined, so that this rare path's
+// registers do not weigh on the smooth cells' code; its inputs are copies.
+struct OpenCell {
+  swale::CellGeom G;
+  swale::StencilDD DD;
+  double h[5], it[3], v0[3][3], dxe;
+};
+struct OpenOut {
+  EdgeState o;
+  uint32_t st;
+  uint8_t flag;
+};
+__device__ __noinline__ OpenOut recon_open_cell(const SchemeConst P, OpenCell c, const double* geo, int64_t geo_stride,
+                                                int64_t idx) {
+  double* gv = reinterpret_cast<double*>(&c.G);
+  constexpr int kF0 = offsetof(swale::CellGeom, F) / sizeof(double), kF1 = kF0 + 5;
+  if (geo) {
+#pragma unroll
+    for (int k = 0; k < SWALE_GEOM_BASE; ++k)
+      if (k < kF0 || k >= kF1) gv[k] = geo[k * geo_stride + idx];
+  }
+  swale::indicator_factors(c.h, c.dxe, c.G);
+#pragma unroll
+  for (int v = 0; v < 3; ++v)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c.DD.D3[v][a] = swale::triple_dd(c.DD.D2[v][a], c.DD.D2[v][a + 1], c.it[a]);
+  OpenOut r;
+  r.st = 0;
+  swale::recon_cell_g(P, c.G, c.v0, c.DD, r.o, r.flag, r.st, false);
+  return r;
+}
+
 // Launch bounds (resident threads per SM): HIOCC, 8 blocks of 128 threads (64 registers), for
 // stage 1 of the well-balanced scheme when it reads the cached mesh geometry: its per-cell work is
 // light enough there that more resident warps win (measured: 0.8 % of the dam-break step), while
@@ -687,22 +721,31 @@ __global__ void __launch_bounds__(T, (HIOCC ? 1024 : (SCHEME == 0 ? 640 : 512)) 
           d2m[a] = sD2f[0][tid + a];
         }
         const bool smooth32 = swale::sure_smooth_f32(F32, c4f, c3f, d2h, d2m, itf, epsf);
-        if (!smooth32) {  // the FP64 detector (and the WENO-Z edge values) need these
-          if (SCHEME == 0 && use_geo) {
+        if (SCHEME == 0) {
+          if (smooth32) {
+            swale::recon_cell_g(K.sc, G, v0, DD, o, flag, st, true);
+          } else {  // the FP64 detector decides, out of line
+            OpenCell oc;
+            oc.G = G;
+            oc.DD = DD;
+            oc.dxe = dxe;
 #pragma unroll
-            for (int k = 0; k < kLoad0; ++k)
-              if (k < kF0 || k >= kF1) gv[k] = D.geo[k * D.geo_stride + idx];
-          }
-          swale::indicator_factors(h, dxe, G);
-          if (SCHEME == 0) {
+            for (int k = 0; k < 5; ++k) oc.h[k] = h[k];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) oc.it[a] = sIT[tid + a];
 #pragma unroll
             for (int v = 0; v < 3; ++v)
 #pragma unroll
-              for (int a = 0; a < 3; ++a) DD.D3[v][a] = swale::triple_dd(DD.D2[v][a], DD.D2[v][a + 1], sIT[tid + a]);
+              for (int a = 0; a < 3; ++a) oc.v0[v][a] = v0[v][a];
+            const OpenOut r = recon_open_cell(K.sc, oc, use_geo ? D.geo : nullptr, D.geo_stride, idx);
+            o = r.o;
+            flag = r.flag;
+            st |= r.st;
           }
+        } else {
+          if (!smooth32) swale::indicator_factors(h, dxe, G);  // the FP64 detector needs them
+          swale::recon_cell_special_g(K.sc, G, h, v0, DD, o, flag, st, etaG, smooth32);
         }
-        if (SCHEME == 2) swale::recon_cell_special_g(K.sc, G, h, v0, DD, o, flag, st, etaG, smooth32);
-        else swale::recon_cell_g(K.sc, G, v0, DD, o, flag, st, smooth32);
       }
       D.eEL[idx] = o.EL;
       D.eER[idx] = o.ER;
