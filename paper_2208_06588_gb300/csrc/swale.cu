@@ -383,6 +383,12 @@ void launch_recon(const StepConst& K, const DevState& D, int T, unsigned grid, c
 template <int STAGE, int MODE>
 void launch_update(const StepConst& K, const DevState& D, int T, unsigned grid, cudaStream_t s, const double* E,
                    const double* M, const double* B, const double* J, RhsOut ro) {
+  if (MODE == 0 && K.scheme == SWALE_SCHEME_HYDROSTATIC && K.bot_pieces == 0) {
+    if (T == 64) k_update<STAGE, MODE, 64, true><<<grid, 64, 0, s>>>(K, D, E, M, B, J, ro);
+    else if (T == 256) k_update<STAGE, MODE, 256, true><<<grid, 256, 0, s>>>(K, D, E, M, B, J, ro);
+    else k_update<STAGE, MODE, 128, true><<<grid, 128, 0, s>>>(K, D, E, M, B, J, ro);
+    return;
+  }
   if (T == 64) k_update<STAGE, MODE, 64><<<grid, 64, 0, s>>>(K, D, E, M, B, J, ro);
   else if (T == 256) k_update<STAGE, MODE, 256><<<grid, 256, 0, s>>>(K, D, E, M, B, J, ro);
   else k_update<STAGE, MODE, 128><<<grid, 128, 0, s>>>(K, D, E, M, B, J, ro);

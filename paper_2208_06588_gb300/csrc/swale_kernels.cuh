@@ -844,7 +844,9 @@ struct RhsOut {
   double alpha;
 };
 
-template <int STAGE, int MODE, int T>
+// PLAIN: an instantiation for the hydrostatic scheme without the L2-projection bottom (the
+// common case), in which the other schemes' branches are compiled out.
+template <int STAGE, int MODE, int T, bool PLAIN = false>
 __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const double* __restrict__ Eg,
                                               const double* __restrict__ Mg, const double* __restrict__ Bg,
                                               const double* __restrict__ Jsg, RhsOut ro) {
@@ -910,7 +912,7 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
         // edge of cell k (edge index k+1).
         const int64_t el = eb + k, er = eb + k + 1;
         const swale::Flux F =
-            K.scheme != 0 ? swale::interface_flux_plain(K.sc.g, alpha, wk, D.eER[el], D.eEL[er], D.eBR[el], D.eBL[er],
+            (!PLAIN && K.scheme != 0) ? swale::interface_flux_plain(K.sc.g, alpha, wk, D.eER[el], D.eEL[er], D.eBR[el], D.eBL[er],
                                                         D.ehR[el], D.ehL[er], D.euR[el], D.euL[er])
                           : swale::interface_flux(K.sc.g, alpha, wk, D.eER[el], D.eEL[er], D.eBR[el], D.eBL[er],
                                                   D.ehR[el], D.ehL[er], D.euR[el], D.euL[er]);
@@ -955,7 +957,7 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
       const double hd[5] = {sH[tid], sH[tid + 1], sH[tid + 2], D.ehL[ic_e], D.ehR[ic_e]};
       const double bd[5] = {sB[tid], sB[tid + 1], sB[tid + 2], D.eBL[ic_e], D.eBR[ic_e]};
       double Sj;
-      if (K.scheme == 2) {
+      if (!PLAIN && K.scheme == 2) {
         const double eta4[4] = {D.eEL[ic_e], D.eG1[ic_e], D.eG2[ic_e], D.eER[ic_e]};
         Sj = swale::source_cell_special(K.sc.g, E[j], eta4, bd, sg, D.eBR[ic_e - 1],
                                         D.eBL[ic_e + 1]);
@@ -992,7 +994,7 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
           D.Ea[g] = yE * inv;
           D.Ma[g] = yM * inv;
           D.Ba[g] = yB * inv;
-          if (K.bot_pieces > 0)  // bottom of stage 2: projection onto the mesh at t_{n+1}
+          if (!PLAIN && K.bot_pieces > 0)  // bottom of stage 2: projection onto the mesh at t_{n+1}
             D.Ba[g] = bottom_average(K, D.x[nb + j] + dt * wl, D.x[nb + j + 1] + dt * wr);
         } else if (STAGE == 2) {
           const double yE = 0.75 * (J0 * D.E0[g]) + 0.25 * (D.YE[g] + dt * RE);
@@ -1005,7 +1007,7 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
           D.Eb[g] = yE * inv;
           D.Mb[g] = yM * inv;
           D.Bb[g] = yB * inv;
-          if (K.bot_pieces > 0) {  // bottom of stage 3: projection onto the mesh at t_{n+1/2}
+          if (!PLAIN && K.bot_pieces > 0) {  // bottom of stage 3: projection onto the mesh at t_{n+1/2}
             const double xl = D.x[nb + j], xr = D.x[nb + j + 1];
             D.Bb[g] = bottom_average(K, xl + 0.5 * dt * wl, xr + 0.5 * dt * wr);
             D.xn[nb + j] = xl + dt * wl;  // nodes at t_{n+1} for the projection after the step
@@ -1034,7 +1036,7 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
           D.J0[g] = J3;
           jmaxb = J3;
           jminb = J3;
-          if (K.bot_pieces > 0) {  // bottom after the step: projection onto the mesh at t_{n+1}
+          if (!PLAIN && K.bot_pieces > 0) {  // bottom after the step: projection onto the mesh at t_{n+1}
             const double xl = D.xn[nb + j], xr = D.xn[nb + j + 1];
             D.B0[g] = bottom_average(K, xl, xr);
             D.x[nb + j] = xl;
