@@ -497,10 +497,10 @@ __device__ __noinline__ OpenOut recon_open_cell(const SchemeConst P, OpenCell c,
 // stage 1 of the well-balanced scheme when it reads the cached mesh geometry: its per-cell work is
 // light enough there that more resident warps win (measured: 0.8 % of the dam-break step), while
 // every instantiation that computes the geometry itself spills heavily under that bound. The
-// other well-balanced instantiations take 640 threads (5 blocks of 128, 96 registers, a few
-// spilled doubles; 0.6 % faster per step than 4 blocks of 128 registers), the other schemes 512.
+// other well-balanced instantiations take 768 threads (6 blocks of 128, 80 registers, a few
+// spilled doubles; 1.2 % faster per step than 4 blocks of 128 registers), the other schemes 512.
 template <int STAGE, int T, int SCHEME = 0, bool HIOCC = false>
-__global__ void __launch_bounds__(T, (HIOCC ? 1024 : (SCHEME == 0 ? 640 : 512)) / T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
+__global__ void __launch_bounds__(T, (HIOCC ? 1024 : (SCHEME == 0 ? 768 : 512)) / T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
                                              const double* __restrict__ Mg, const double* __restrict__ Bg,
                                              const double* __restrict__ Jg) {
   __shared__ double sJ[T + 4], sV[3][T + 4];    // cells c0-2 .. c0+T+1
@@ -637,13 +637,15 @@ __global__ void __launch_bounds__(T, (HIOCC ? 1024 : (SCHEME == 0 ? 640 : 512)) 
       swale::StencilDD DD;
 #pragma unroll
       for (int k = 0; k < 5; ++k) h[k] = sJ[tid + k];
+      // The well-balanced scheme reads its stencil data from shared memory where its class is
+      // known (below): fewer values live across the mesh geometry.
+      if (SCHEME != 0) {
 #pragma unroll
-      for (int v = 0; v < 3; ++v) {
+        for (int v = 0; v < 3; ++v) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) v0[v][a] = sV[v][tid + a];
+          for (int a = 0; a < 3; ++a) v0[v][a] = sV[v][tid + a];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) DD.D2[v][a] = sD2[v][tid + a];
-        if (SCHEME != 0) {
+          for (int a = 0; a < 4; ++a) DD.D2[v][a] = sD2[v][tid + a];
 #pragma unroll
           for (int a = 0; a < 3; ++a) DD.D3[v][a] = sD3[v][tid + a];
         }
@@ -722,21 +724,29 @@ __global__ void __launch_bounds__(T, (HIOCC ? 1024 : (SCHEME == 0 ? 640 : 512)) 
         }
         const bool smooth32 = swale::sure_smooth_f32(F32, c4f, c3f, d2h, d2m, itf, epsf);
         if (SCHEME == 0) {
-          if (smooth32) {
+          if (smooth32) {  // the cell's averages and pair differences are all the smooth class needs
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+              v0[v][2] = sV[v][tid + 2];
+#pragma unroll
+              for (int a = 0; a < 4; ++a) DD.D2[v][a] = sD2[v][tid + a];
+            }
             swale::recon_cell_g(K.sc, G, v0, DD, o, flag, st, true);
           } else {  // the FP64 detector decides, out of line
             OpenCell oc;
             oc.G = G;
-            oc.DD = DD;
             oc.dxe = dxe;
 #pragma unroll
             for (int k = 0; k < 5; ++k) oc.h[k] = h[k];
 #pragma unroll
             for (int a = 0; a < 3; ++a) oc.it[a] = sIT[tid + a];
 #pragma unroll
-            for (int v = 0; v < 3; ++v)
+            for (int v = 0; v < 3; ++v) {
 #pragma unroll
-              for (int a = 0; a < 3; ++a) oc.v0[v][a] = v0[v][a];
+              for (int a = 0; a < 3; ++a) oc.v0[v][a] = sV[v][tid + a];
+#pragma unroll
+              for (int a = 0; a < 4; ++a) oc.DD.D2[v][a] = sD2[v][tid + a];
+            }
             const OpenOut r = recon_open_cell(K.sc, oc, use_geo ? D.geo : nullptr, D.geo_stride, idx);
             o = r.o;
             flag = r.flag;
