@@ -54,10 +54,12 @@ def recon_tangent(h, v0, D2, D3, tv0, tD2, tD3, prm):
     return val, tan, flag
 
 
-def recon_adjoint(h, v0, D2, D3, prm, ob):
+def recon_adjoint(h, v0, D2, D3, prm, ob, known_smooth=False):
+    """Reverse sweep of one cell; known_smooth takes the smooth class as given (the shortcut the
+    device takes where its FP32 test holds) instead of forming the FP64 indicators."""
     v0b, D2b, D3b = np.zeros(9), np.zeros(12), np.zeros(9)
     args = [f64(x) for x in (h, v0, D2, D3, prm, ob)]
-    lib().ct_recon_adjoint(*map(_p, args), _p(v0b), _p(D2b), _p(D3b))
+    lib().ct_recon_adjoint_k(*map(_p, args), ctypes.c_int(1 if known_smooth else 0), _p(v0b), _p(D2b), _p(D3b))
     return v0b, D2b, D3b
 
 

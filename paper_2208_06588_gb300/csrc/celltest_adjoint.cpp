@@ -8,8 +8,10 @@
 extern "C" {
 
 // ob[8] adjoints of (EL, ER, BL, BR, hL, hR, uL, uR) -> v0b[9], D2b[12], D3b[9].
-void ct_recon_adjoint(const double* h, const double* v0, const double* D2, const double* D3, const double* prm,
-                      const double* ob, double* v0b, double* D2b, double* D3b) {
+// known: 1 to take the smooth class as known (the FP32 test's shortcut), 0 to let the FP64
+// detector decide.
+void ct_recon_adjoint_k(const double* h, const double* v0, const double* D2, const double* D3, const double* prm,
+                        const double* ob, int known, double* v0b, double* D2b, double* D3b) {
   swale::SchemeConst P{prm[0], prm[1], prm[2], prm[3], 1, (int32_t)prm[5]};
   double vv[3][3];
   swale::StencilDD DD, DDb;
@@ -21,12 +23,17 @@ void ct_recon_adjoint(const double* h, const double* v0, const double* D2, const
   swale::EdgeAdj a{ob[0], ob[1], ob[2], ob[3], ob[4], ob[5], ob[6], ob[7]};
   double vb[3][3];
   const double it3[3] = {1.0 / (h[0] + h[1] + h[2]), 1.0 / (h[1] + h[2] + h[3]), 1.0 / (h[2] + h[3] + h[4])};
-  swale::recon_cell_rev(P, h, it3, vv, DD, prm[4], a, vb, DDb);
+  swale::recon_cell_rev(P, h, it3, vv, DD, prm[4], a, vb, DDb, known != 0);
   for (int v = 0; v < 3; ++v) {
     for (int k = 0; k < 3; ++k) v0b[v * 3 + k] = vb[v][k];
     for (int k = 0; k < 4; ++k) D2b[v * 4 + k] = DDb.D2[v][k];
     for (int k = 0; k < 3; ++k) D3b[v * 3 + k] = DDb.D3[v][k];
   }
+}
+
+void ct_recon_adjoint(const double* h, const double* v0, const double* D2, const double* D3, const double* prm,
+                      const double* ob, double* v0b, double* D2b, double* D3b) {
+  ct_recon_adjoint_k(h, v0, D2, D3, prm, ob, 0, v0b, D2b, D3b);
 }
 
 void ct_flux_adjoint(const double* e, const double* prm, const double* Fb, double* eb) {

@@ -166,8 +166,11 @@ SWALE_HD void source_cell_rev(real g, const real hd[5], const real bd[5], const 
 // Adjoint of recon_cell: from the adjoints ob of the limited edge state of cell j, the adjoints
 // of the data it read: v0b[v][a] (averages of cells j-2+a) and DDb (divided differences).
 //   it[3]: reciprocal sums of the triples starting at cells j-2, j-1, j (smooth-class form).
+// known_smooth: the caller has established the smooth class (the FP32 test of the forward,
+// which implies gamma <= 1/2 for the FP64 indicators), so they are not formed; DDb.D3 stays 0.
 SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real it[3], const real v0[3][3],
-                             const StencilDD& DD, real dxmax, const EdgeAdj& ob, real v0b[3][3], StencilDD& DDb) {
+                             const StencilDD& DD, real dxmax, const EdgeAdj& ob, real v0b[3][3], StencilDD& DDb,
+                             bool known_smooth = false) {
   // ---------------- forward recompute (as recon_cell) ----------------
   const real h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3], h4 = h[4];
   const real dx = P.beta_dx_global ? dxmax : h2;
@@ -196,20 +199,26 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real i
   d[0][0] = h1 * s01 * icb;
   d[0][1] = 1.0 - d[0][0] - d[0][2];
   d[1][1] = 1.0 - d[1][0] - d[1][2];
-  const real F[3] = {1.5 * h2 + s01 + h1, 0.5 * h2 + h1, -(0.5 * h2 + h3)};
-  const real c4 = 4.0 * dx * h2;
-  const real c3 = (3.0 * h2 * h2 + 36.0 * dx * dx) * dx * h2;
-  real beta[3];
-  for (int r = 0; r < 3; ++r) {
-    const int a = 2 - r;
-    const real d2h = DD.D2[0][a] - DD.D2[2][a], d3h = DD.D3[0][a] - DD.D3[2][a];
-    const real qh = d2h + d3h * F[a], qm = DD.D2[1][a] + DD.D3[1][a] * F[a];
-    beta[r] = c4 * (qh * qh + qm * qm) + c3 * (d3h * d3h + DD.D3[1][a] * DD.D3[1][a]);
+  real beta[3] = {0.0, 0.0, 0.0}, tdiff = 0.0, tau = 0.0, den = 1.0;
+  real F[3] = {0.0, 0.0, 0.0}, c4 = 0.0, c3 = 0.0;  // formed with the indicators
+  uint8_t flag = 0;
+  if (!known_smooth) {
+    F[0] = 1.5 * h2 + s01 + h1;
+    F[1] = 0.5 * h2 + h1;
+    F[2] = -(0.5 * h2 + h3);
+    c4 = 4.0 * dx * h2;
+    c3 = (3.0 * h2 * h2 + 36.0 * dx * dx) * dx * h2;
+    for (int r = 0; r < 3; ++r) {
+      const int a = 2 - r;
+      const real d2h = DD.D2[0][a] - DD.D2[2][a], d3h = DD.D3[0][a] - DD.D3[2][a];
+      const real qh = d2h + d3h * F[a], qm = DD.D2[1][a] + DD.D3[1][a] * F[a];
+      beta[r] = c4 * (qh * qh + qm * qm) + c3 * (d3h * d3h + DD.D3[1][a] * DD.D3[1][a]);
+    }
+    tdiff = beta[0] - beta[2];
+    tau = dabs(tdiff);
+    den = (beta[0] + beta[1] + beta[2]) * (1.0 / 3.0) + P.eps_weno;
+    flag = le_nn(tau, 0.5 * den) ? 0 : (le_nn(den, tau) ? 2 : 1);
   }
-  const real tdiff = beta[0] - beta[2];
-  const real tau = dabs(tdiff);
-  const real den = (beta[0] + beta[1] + beta[2]) * (1.0 / 3.0) + P.eps_weno;
-  const uint8_t flag = le_nn(tau, 0.5 * den) ? 0 : (le_nn(den, tau) ? 2 : 1);
   real phi[2][3], phiN[2][3], al[2][3], q[3], e[3], isE[2], Mg = 0.0;
   if (flag == 0) {
     for (int ee = 0; ee < 2; ++ee)

@@ -200,16 +200,36 @@ __global__ void __launch_bounds__(T) k_adj_source(StepConst K, DevState D, AdjSt
   }
 }
 
+// The reverse of a cell whose class the FP32 test leaves open, out of line (the FP64 detector,
+// the WENO-Z weights and their adjoints): its registers do not weigh on the smooth cells' code.
+struct AdjOpenIn {
+  swale::StencilDD DD;
+  swale::EdgeAdj ob;
+  double h[5], it[3], v0[3][3], dxmax;
+};
+struct AdjOpenOut {
+  swale::StencilDD DDb;
+  double v0b[3][3];
+};
+__device__ __noinline__ AdjOpenOut adj_open_cell(const SchemeConst P, const AdjOpenIn c) {
+  AdjOpenOut r;
+  swale::recon_cell_rev(P, c.h, c.it, c.v0, c.DD, c.dxmax, c.ob, r.v0b, r.DDb, false);
+  return r;
+}
+
 // Reverse of the reconstruction + limiter of stage STAGE for cells -1..N (tiles of T cells
 // staged like the forward kernel): each cell's reverse sweep gives the adjoints of its stencil
 // averages and divided differences, which map to the 5 stencil cells and are added atomically.
 template <int STAGE, int T>
-__global__ void __launch_bounds__(T) k_adj_recon(StepConst K, DevState D, AdjState A, const double* __restrict__ Eg,
+__global__ void __launch_bounds__(T, 512 / T) k_adj_recon(StepConst K, DevState D, AdjState A, const double* __restrict__ Eg,
                                                  const double* __restrict__ Mg, const double* __restrict__ Bg,
                                                  const double* __restrict__ Jg) {
   __shared__ double sJ[T + 4], sV[3][T + 4];
   __shared__ double sIP[T + 3], sD2[3][T + 3];
   __shared__ double sIT[T + 2], sD3[3][T + 2];
+  // FP32 copies for the smooth-class test of the forward: pair differences of hu and of the
+  // depth (eta's minus the bottom's), triple reciprocals.
+  __shared__ float sD2f[2][T + 3], sITf[T + 2];
   const int tid = threadIdx.x;
   const bool refl = (K.bc == SWALE_BC_REFLECTIVE);
   for (int t = blockIdx.x; t < D.nr; t += gridDim.x) {
@@ -243,13 +263,17 @@ __global__ void __launch_bounds__(T) k_adj_recon(StepConst K, DevState D, AdjSta
     for (int i = tid; i < T + 3; i += T) {
       const double ip = swale::pair_recip(sJ[i], sJ[i + 1]);
       sIP[i] = ip;
+      double d2[3];
 #pragma unroll
-      for (int v = 0; v < 3; ++v) sD2[v][i] = swale::pair_dd(sV[v][i], sV[v][i + 1], ip);
+      for (int v = 0; v < 3; ++v) sD2[v][i] = d2[v] = swale::pair_dd(sV[v][i], sV[v][i + 1], ip);
+      sD2f[0][i] = swale::f32_trunc(d2[1]);
+      sD2f[1][i] = swale::f32_trunc(d2[0] - d2[2]);
     }
     __syncthreads();
     for (int i = tid; i < T + 2; i += T) {
       const double it = swale::triple_recip(sJ[i], sJ[i + 1], sJ[i + 2]);
       sIT[i] = it;
+      sITf[i] = swale::f32_trunc(it);
 #pragma unroll
       for (int v = 0; v < 3; ++v) sD3[v][i] = swale::triple_dd(sD2[v][i], sD2[v][i + 1], it);
     }
@@ -274,7 +298,42 @@ __global__ void __launch_bounds__(T) k_adj_recon(StepConst K, DevState D, AdjSta
                                A.ab[4][idx], A.ab[5][idx], A.ab[6][idx], A.ab[7][idx]};
     double v0b[3][3];
     const double it3[3] = {sIT[tid], sIT[tid + 1], sIT[tid + 2]};
-    swale::recon_cell_rev(K.sc, h, it3, v0, DD, bitsd(S->Jmax[STAGE - 1]), ob, v0b, DDb);
+    // The forward's FP32 test of the smooth class on the same data: where it holds, the FP64
+    // class is 0 as well and the indicators are not formed.
+    const double dxmax = bitsd(S->Jmax[STAGE - 1]);
+    float F32[3], c4f, c3f, itf[3], d2h[4], d2m[4];
+    swale::indicator_factors_f32(h, K.sc.beta_dx_global ? dxmax : h[2], F32, c4f, c3f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) itf[a] = sITf[tid + a];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      d2h[a] = sD2f[1][tid + a];
+      d2m[a] = sD2f[0][tid + a];
+    }
+    const bool smooth32 =
+        swale::sure_smooth_f32(F32, c4f, c3f, d2h, d2m, itf, swale::f32_trunc(K.sc.eps_weno));
+    if (smooth32) {
+      swale::recon_cell_rev(K.sc, h, it3, v0, DD, dxmax, ob, v0b, DDb, true);
+    } else {
+      AdjOpenIn in;
+      in.DD = DD;
+      in.ob = ob;
+      in.dxmax = dxmax;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) in.h[k] = h[k];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) in.it[a] = it3[a];
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) in.v0[v][a] = v0[v][a];
+      const AdjOpenOut r = adj_open_cell(K.sc, in);
+      DDb = r.DDb;
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v0b[v][a] = r.v0b[v][a];
+    }
     // Stencil cell adjoints: cv[v][k] for cells c-2+k.
     double cv[3][5];
 #pragma unroll
@@ -286,11 +345,13 @@ __global__ void __launch_bounds__(T) k_adj_recon(StepConst K, DevState D, AdjSta
       double d2b[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) d2b[a] = DDb.D2[v][a];
+      if (!smooth32) {  // DDb.D3 is 0 in the smooth class
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {  // D3[a] = (D2[a+1] - D2[a]) it[a]
-        const double x = DDb.D3[v][a] * sIT[tid + a];
-        d2b[a + 1] += x;
-        d2b[a] -= x;
+        for (int a = 0; a < 3; ++a) {  // D3[a] = (D2[a+1] - D2[a]) it[a]
+          const double x = DDb.D3[v][a] * sIT[tid + a];
+          d2b[a + 1] += x;
+          d2b[a] -= x;
+        }
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a) {  // D2[a] = (v[a+1] - v[a]) ip[a]
