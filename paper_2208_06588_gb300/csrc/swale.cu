@@ -285,7 +285,7 @@ swale_status build_tiles(swale_ctx* ctx, std::vector<InstConst>& ic) {
   drop_graph(ctx);
   free_tiles(ctx);
   const int64_t B = ctx->B;
-  const int Tr = ctx->Tr, Tu = ctx->Tu, Tm = kMeshThreads;
+  const int Tr = ctx->Tr, Tu = ctx->Tu, Tm = kMeshNodes;
   std::vector<Tile> rt, ut, mt;
   for (int64_t i = 0; i < B; ++i) {
     const int64_t N = ic[i].N;

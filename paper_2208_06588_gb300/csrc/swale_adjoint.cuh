@@ -95,10 +95,10 @@ SWALE_HD void source_dd_rev(const SourceGeom& sg, const real cb[6], real ub[5]) 
 }
 
 // Adjoint of source_cell: accumulates into hdb[5], bdb[5] the adjoints of the depth and bottom
-// data for the adjoint Sb of the source value. The reverse of the steps of the same map: Newton
-// coefficients by confluent divided differences, their monomial form a (depth) and ab (bottom),
-// S = -g sum_{i, m} a_i ab_m m / (i + m) (source_cell folds the factors of a_i and ab_m into
-// these constants; the map is the same); then transposed in the opposite order.
+// data for the adjoint Sb of the source value. The reverse of source_cell's own steps: Newton
+// coefficients by confluent divided differences, their monomial form a (depth) and ab (bottom)
+// without the factors (i + 1), S = -g sum_{i, m} a_i W[i][m] ab_m with those factors in W; then
+// transposed in the opposite order.
 SWALE_HD void source_cell_rev(real g, const real hd[5], const real bd[5], const SourceGeom& sg, real Sb, real hdb[5],
                               real bdb[5]) {
   real ch[6], cb[6];
@@ -122,6 +122,8 @@ SWALE_HD void source_cell_rev(real g, const real hd[5], const real bd[5], const 
     c[4] = o4a;
     c[5] = (o4b - o4a) * sg.i1mp;
   }
+  // The monomial coefficients without their factors (i + 1), as source_cell forms them, with
+  // q = c_3 - c_4 + c_5 and d = c_4 - 2 c_5.
   const real rm = sg.rm;
   real a[5], ab[5];
   const real* cs[2] = {ch, cb};
@@ -130,34 +132,36 @@ SWALE_HD void source_cell_rev(real g, const real hd[5], const real bd[5], const 
     const real* c = cs[v];
     real* o = ms[v];
     const real q = c[3] - c[4] + c[5];
-    o[0] = c[1] + c[2] * rm;
-    o[1] = 2.0 * (c[2] + rm * q);
-    o[2] = 3.0 * q + rm * (3.0 * c[4] - 6.0 * c[5]);
-    o[3] = 4.0 * (c[4] - 2.0 * c[5]) + (4.0 * rm) * c[5];
-    o[4] = 5.0 * c[5];
+    const real d = c[4] - 2.0 * c[5];
+    o[0] = c[1] + rm * c[2];
+    o[1] = c[2] + rm * q;
+    o[2] = q + rm * d;
+    o[3] = d + rm * c[5];
+    o[4] = c[5];
   }
-  // S = -g sum_i a_i v_i, v_i = sum_m ab_m m / (i + m): adjoints of a_i and ab_m.
+  // S = -g sum_{i, m} a_i W[i][m] ab_m: adjoints of a_i and ab_m.
+  constexpr double kW[5][4] = SWALE_SRC_W;
   const real gS = -g * Sb;
   real ob[2][5];
   for (int i = 0; i < 5; ++i)
-    ob[0][i] = gS * (ab[1] * (1.0 / (i + 1)) + ab[2] * (2.0 / (i + 2)) + ab[3] * (3.0 / (i + 3)) +
-                     ab[4] * (4.0 / (i + 4)));
+    ob[0][i] = gS * (ab[1] * kW[i][0] + ab[2] * kW[i][1] + ab[3] * kW[i][2] + ab[4] * kW[i][3]);
   ob[1][0] = 0.0;
   for (int m = 1; m < 5; ++m)
-    ob[1][m] = gS * (a[0] * (double(m) / m) + a[1] * (double(m) / (m + 1)) + a[2] * (double(m) / (m + 2)) +
-                     a[3] * (double(m) / (m + 3)) + a[4] * (double(m) / (m + 4)));
+    ob[1][m] = gS * (a[0] * kW[0][m - 1] + a[1] * kW[1][m - 1] + a[2] * kW[2][m - 1] + a[3] * kW[3][m - 1] +
+                     a[4] * kW[4][m - 1]);
   // Transpose of the monomial form, per variable: adjoints of the Newton coefficients.
   real cbv[2][6];
   for (int v = 0; v < 2; ++v) {
     const real* o = ob[v];
     real* c = cbv[v];
-    const real qb = 2.0 * rm * o[1] + 3.0 * o[2];
+    const real qb = rm * o[1] + o[2];
+    const real db = rm * o[2] + o[3];
     c[0] = 0.0;
     c[1] = o[0];
-    c[2] = rm * o[0] + 2.0 * o[1];
+    c[2] = rm * o[0] + o[1];
     c[3] = qb;
-    c[4] = (3.0 * rm) * o[2] + 4.0 * o[3] - qb;
-    c[5] = -(6.0 * rm) * o[2] + (4.0 * rm - 8.0) * o[3] + 5.0 * o[4] + qb;
+    c[4] = db - qb;
+    c[5] = rm * o[3] + o[4] + qb - 2.0 * db;
   }
   source_dd_rev(sg, cbv[0], hdb);
   source_dd_rev(sg, cbv[1], bdb);

@@ -753,6 +753,15 @@ SWALE_HD SourceGeom source_geom(real Jm, real Jc, real iJm, real iJc, real iJp, 
   return s;
 }
 
+// Weights of the source integral with the monomial factors folded in: (i + 1)(m + 1) m / (i + m)
+// for i = 0..4 (rows), m = 1..4 (columns); source_cell and its reverse use them.
+#define SWALE_SRC_W                                                      \
+  {{2.0, 3.0, 4.0, 5.0},                                                 \
+   {2.0, 4.0, 6.0, 8.0},                                                 \
+   {2.0, 3.0 * 6.0 / 4.0, 3.0 * 12.0 / 5.0, 3.0 * 20.0 / 6.0},           \
+   {2.0, 4.0 * 6.0 / 5.0, 4.0 * 12.0 / 6.0, 4.0 * 20.0 / 7.0},           \
+   {2.0, 5.0 * 6.0 / 6.0, 5.0 * 12.0 / 7.0, 5.0 * 20.0 / 8.0}}
+
 // Source term int_cell -g (eta_h - b_h) b_h' dx of Sec. 4.1, with eta_h - b_h interpolating the
 // depth data (averages h_{j-1}, h_j, h_{j+1}, limited edge depths h^L, h^R) and b_h the bottom
 // data (averages and limited edge bottoms), in the unit coordinate t of the cell.
@@ -806,12 +815,7 @@ SWALE_HD real source_cell(real g, const real hd[5], const real bd[5], const Sour
     o[3] = d + rm * c[5];
     o[4] = c[5];
   }
-  // (i + 1)(m + 1) m / (i + m) for i = 0..4 (rows), m = 1..4 (columns)
-  constexpr double kW[5][4] = {{2.0, 3.0, 4.0, 5.0},
-                               {2.0, 4.0, 6.0, 8.0},
-                               {2.0, 3.0 * 6.0 / 4.0, 3.0 * 12.0 / 5.0, 3.0 * 20.0 / 6.0},
-                               {2.0, 4.0 * 6.0 / 5.0, 4.0 * 12.0 / 6.0, 4.0 * 20.0 / 7.0},
-                               {2.0, 5.0 * 6.0 / 6.0, 5.0 * 12.0 / 7.0, 5.0 * 20.0 / 8.0}};
+  constexpr double kW[5][4] = SWALE_SRC_W;
   real S = 0.0;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {

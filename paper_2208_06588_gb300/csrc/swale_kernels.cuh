@@ -39,6 +39,7 @@ using swale::SchemeConst;
 
 constexpr int kMaxGaussHalf = 64;
 constexpr int kMeshThreads = 256;
+constexpr int kMeshNodes = kMeshThreads - 1;  // nodes a mesh-velocity tile advances by
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 // Per-instance device scalars. Maxima of non-negative doubles are kept as their bit patterns
@@ -380,9 +381,12 @@ __global__ void k_prologue(StepConst K, DevState D) {
 
 // ------------------------------------------------------------------------------------
 // Fluid-driven node velocity: raw_k = (u_{k-1} + u_k)/2 for k = 1..N-1 (u = hu/h, dry -> 0),
-// truncated renormalised Gaussian filter, w_0 = w_N = 0. A tile is kMeshThreads nodes; the
-// block stages the cell velocities, the raw node velocities and its filtered nodes in shared
-// memory (dynamic, 3 T + 4 H + 4 doubles).
+// truncated renormalised Gaussian filter, w_0 = w_N = 0. A block filters kMeshThreads nodes in
+// one pass, one per thread, and tiles advance by kMeshNodes = kMeshThreads - 1 nodes: the last
+// node of a tile is the next tile's first, filtered by both (the same sum in the same order),
+// which gives the tile the right neighbour of its last node for max |w_{k+1} - w_k| without a
+// second pass for one node. The block stages the cell velocities, the raw node velocities and
+// its filtered nodes in shared memory (dynamic, 3 T + 4 H + 4 doubles).
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevState D) {
   extern __shared__ double sh[];
@@ -392,7 +396,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevSta
   double* sraw = sh + nu;  // raw node velocities, nodes [k0 - H, k0 + T + H]
   double* sw = sraw + nr;  // filtered velocities, nodes [k0, k0 + T]
   for (int t = blockIdx.x; t < D.nm; t += gridDim.x) {
-    const Tile tl = D.mtiles ? D.mtiles[t] : Tile{0, t * T};
+    const Tile tl = D.mtiles ? D.mtiles[t] : Tile{0, t * kMeshNodes};
     DevScalars* S = D.S + tl.inst;
     if (S->done) continue;
     const InstConst ic = D.IC[tl.inst];
@@ -417,7 +421,8 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevSta
       sraw[i] = (k >= 1 && k <= N - 1) ? 0.5 * (su[i] + su[i + 1]) : 0.0;
     }
     __syncthreads();
-    for (int i = tid; i <= T; i += T) {
+    {
+      const int i = tid;
       const int64_t k = k0 + i;
       double v = 0.0;
       if (k >= 1 && k <= N - 1) {
@@ -441,7 +446,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh_gauss(StepConst K, DevSta
     __syncthreads();
     const int64_t k = k0 + tid;
     double wa = 0.0, dwa = 0.0;
-    if (k <= N) {
+    if (tid < kMeshNodes && k <= N) {
       w[k] = sw[tid];
       wa = fabs(sw[tid]);
       if (k < N) dwa = fabs(sw[tid + 1] - sw[tid]);
