@@ -169,7 +169,7 @@ void drop_graph(swale_ctx* ctx) {
 void free_tiles(swale_ctx* ctx) {
   for (void* p : ctx->tile_allocs) cudaFree(p);
   ctx->tile_allocs.clear();
-  ctx->D.rtiles = ctx->D.utiles = ctx->D.mtiles = nullptr;
+  ctx->D.rtiles = ctx->D.utiles = ctx->D.mtiles = ctx->D.ftiles = nullptr;
 }
 
 void free_alpha_log(swale_ctx* ctx) {
@@ -286,35 +286,43 @@ swale_status build_tiles(swale_ctx* ctx, std::vector<InstConst>& ic) {
   free_tiles(ctx);
   const int64_t B = ctx->B;
   const int Tr = ctx->Tr, Tu = ctx->Tu, Tm = kMeshNodes;
-  std::vector<Tile> rt, ut, mt;
+  const int Tf = Tu - 1;  // cells of a forward update tile (its Tu interfaces take one pass)
+  std::vector<Tile> rt, ut, mt, ft;
   for (int64_t i = 0; i < B; ++i) {
     const int64_t N = ic[i].N;
     const int64_t nr = (N + 2 + Tr - 1) / Tr, nu = (N + Tu - 1) / Tu, nm = (N + 1 + Tm - 1) / Tm;
+    const int64_t nf = (N + Tf - 1) / Tf;
     ic[i].ntiles_r = (int32_t)nr;
     if (B > 1) {
       for (int64_t t = 0; t < nr; ++t) rt.push_back(Tile{(int32_t)i, (int32_t)(t * Tr - 1)});
       for (int64_t t = 0; t < nu; ++t) ut.push_back(Tile{(int32_t)i, (int32_t)(t * Tu)});
       for (int64_t t = 0; t < nm; ++t) mt.push_back(Tile{(int32_t)i, (int32_t)(t * Tm)});
+      for (int64_t t = 0; t < nf; ++t) ft.push_back(Tile{(int32_t)i, (int32_t)(t * Tf)});
     } else {
       ctx->D.nr = (int32_t)nr;
       ctx->D.nu = (int32_t)nu;
       ctx->D.nm = (int32_t)nm;
+      ctx->D.nf = (int32_t)nf;
     }
   }
   if (B > 1) {
-    Tile *dr, *du, *dm;
+    Tile *dr, *du, *dm, *df;
     if (swale_status s = dalloc(ctx, ctx->tile_allocs, &dr, rt.size())) return s;
     if (swale_status s = dalloc(ctx, ctx->tile_allocs, &du, ut.size())) return s;
     if (swale_status s = dalloc(ctx, ctx->tile_allocs, &dm, mt.size())) return s;
+    if (swale_status s = dalloc(ctx, ctx->tile_allocs, &df, ft.size())) return s;
     SW_CUDA(ctx, cudaMemcpyAsync(dr, rt.data(), rt.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream));
     SW_CUDA(ctx, cudaMemcpyAsync(du, ut.data(), ut.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream));
     SW_CUDA(ctx, cudaMemcpyAsync(dm, mt.data(), mt.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream));
+    SW_CUDA(ctx, cudaMemcpyAsync(df, ft.data(), ft.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream));
     ctx->D.rtiles = dr;
     ctx->D.utiles = du;
     ctx->D.mtiles = dm;
+    ctx->D.ftiles = df;
     ctx->D.nr = (int32_t)rt.size();
     ctx->D.nu = (int32_t)ut.size();
     ctx->D.nm = (int32_t)mt.size();
+    ctx->D.nf = (int32_t)ft.size();
   }
   SW_CUDA(ctx, cudaMemcpyAsync(ctx->D.IC, ic.data(), B * sizeof(InstConst), cudaMemcpyHostToDevice, ctx->stream));
   SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -409,7 +417,7 @@ swale_status enqueue_step_on(swale_ctx* ctx, const DevState& D, cudaStream_t s, 
   const DevState& D1 = stageD ? stageD[0] : D;
   const DevState& D2 = stageD ? stageD[1] : D;
   const DevState& D3 = stageD ? stageD[2] : D;
-  const unsigned gr = grid_of(D.nr, ctx->grid_r), gu = grid_of(D.nu, ctx->grid_u);
+  const unsigned gr = grid_of(D.nr, ctx->grid_r), gu = grid_of(D.nf, ctx->grid_u);
   const int Tr = ctx->Tr, Tu = ctx->Tu;
   const RhsOut none{nullptr, nullptr, nullptr, 0.0};
   swale_status st = SWALE_OK;
@@ -1146,7 +1154,7 @@ swale_status swale_rhs(swale_ctx* ctx, int64_t N, const double* E, const double*
     alpha = A + wb;
   }
   RhsOut ro{R3, R3 + N, R3 + 2 * N, alpha};
-  launch_update<2, 1>(K, D, tmp.Tu, grid_of(D.nu, 0), st, D.E0, D.M0, D.B0, D.J0, ro);
+  launch_update<2, 1>(K, D, tmp.Tu, grid_of(D.nf, 0), st, D.E0, D.M0, D.B0, D.J0, ro);
   e = cudaGetLastError();
   e = e ? e : cudaMemcpyAsync(RE, ro.RE, cb, cudaMemcpyDefault, st);
   e = e ? e : cudaMemcpyAsync(RM, ro.RM, cb, cudaMemcpyDefault, st);
@@ -1841,6 +1849,7 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   D.w = const_cast<double*>(w);
   D.nr = (int32_t)((N + 2 + kNoAllocTile - 1) / kNoAllocTile);
   D.nu = (int32_t)((N + kNoAllocTile - 1) / kNoAllocTile);
+  D.nf = (int32_t)((N + kNoAllocTile - 2) / (kNoAllocTile - 1));
   StepConst K;
   K.sc.g = cfg->g;
   K.sc.eps_weno = cfg->eps_weno;
@@ -1878,7 +1887,7 @@ swale_status swale_rhs_noalloc(const swale_config* cfg, void* cuda_stream, int64
   else
     k_recon<1, kNoAllocTile><<<(unsigned)D.nr, kNoAllocTile, 0, st>>>(K, D, E, M, B, J);
   RhsOut ro{RE, RM, RB, alpha};
-  k_update<2, 1, kNoAllocTile><<<(unsigned)D.nu, kNoAllocTile, 0, st>>>(K, D, E, M, B, J, ro);
+  k_update<2, 1, kNoAllocTile><<<(unsigned)D.nf, kNoAllocTile, 0, st>>>(K, D, E, M, B, J, ro);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, scr->flags + 1, (size_t)N, cudaMemcpyDefault, st);
   if (e == cudaSuccess && A_out) {

@@ -144,6 +144,10 @@ struct DevState {
   DevScalars* S;
   const Tile *rtiles, *utiles, *mtiles;  // work lists (null: one instance, implicit tiles)
   int32_t nr, nu, nm;                    // tiles in each list
+  // The forward update's tiles: T - 1 cells for a block of T threads, so that its T interfaces
+  // take one pass (utiles, of T cells, serve the adjoint's kernels).
+  const Tile* ftiles;
+  int32_t nf;
 };
 
 __constant__ double c_gauss_w[2 * kMaxGaussHalf + 1];
@@ -850,9 +854,10 @@ __global__ void __launch_bounds__(T, (HIOCC ? 1024 : (SCHEME == 0 ? 768 : 512)) 
 // ------------------------------------------------------------------------------------
 // Fluxes, source and the RK combination of stage STAGE for cells 0..N_i-1 (rows a1, a8, a9;
 // MODE 0), or the bare right-hand side of one instance (MODE 1, used by swale_rhs). A tile is
-// T consecutive cells: each of its interfaces' fluxes is computed once into shared memory;
-// the widths, their reciprocals and the depth / bottom averages of the tile plus one halo
-// cell each side are staged there too.
+// T - 1 consecutive cells for a block of T threads: its T interfaces' fluxes are computed once,
+// one per thread, into shared memory (a tile of T cells would leave its last interface to a
+// second pass of a single thread); the widths, their reciprocals and the depth / bottom
+// averages of the tile plus one halo cell each side are staged there too.
 // ------------------------------------------------------------------------------------
 struct RhsOut {
   double *RE, *RM, *RB;
@@ -865,12 +870,13 @@ template <int STAGE, int MODE, int T, bool PLAIN = false>
 __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const double* __restrict__ Eg,
                                               const double* __restrict__ Mg, const double* __restrict__ Bg,
                                               const double* __restrict__ Jsg, RhsOut ro) {
-  __shared__ double sF[4][T + 1], sW[T + 1];                      // interfaces / nodes j0 .. j0+T
-  __shared__ double sJ[T + 2], siJ[T + 2], sH[T + 2], sB[T + 2];  // cells j0-1 .. j0+T
+  __shared__ double sF[4][T], sW[T];                              // interfaces / nodes j0 .. j0+T-1
+  __shared__ double sJ[T + 1], siJ[T + 1], sH[T + 1], sB[T + 1];  // cells j0-1 .. j0+T-1
   const int tid = threadIdx.x;
   (void)Mg;
-  for (int t = blockIdx.x; t < D.nu; t += gridDim.x) {
-    const Tile tl = D.utiles ? D.utiles[t] : Tile{0, t * T};
+  constexpr int TC = T - 1;  // cells of a tile; its T interfaces j0 .. j0 + TC, one per thread
+  for (int t = blockIdx.x; t < D.nf; t += gridDim.x) {
+    const Tile tl = D.ftiles ? D.ftiles[t] : Tile{0, t * TC};
     const int inst = tl.inst;
     DevScalars* S = D.S + inst;
     if (MODE == 0) {
@@ -907,18 +913,19 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
     const bool use_sgeo = STAGE == 1 && MODE == 0 && D.geo != nullptr && S->geo_tag == geo_now;
     const double sdiff = fresh_w ? S->sdiff : 0.0;
     __syncthreads();
-    for (int i = tid; i <= T; i += T) {
+    {
+      const int i = tid;
       const int64_t k = j0 + i;  // node / interface index
       if (k <= N) {
         double wk;
         if (fresh_w) {
           wk = D.P[nb + k] * sdiff;
-          if (i < T || k == N) D.w[nb + k] = wk;
+          if (i < TC || k == N) D.w[nb + k] = wk;
         } else if (MODE == 0 && K.mesh == SWALE_MESH_STATIC) {
           wk = 0.0;
         } else if (MODE == 0 && K.mesh == SWALE_MESH_LINEAR) {
           wk = D.P[nb + k];  // constant node velocity (Eq. velocity)
-          if (STAGE == 1 && (i < T || k == N)) D.w[nb + k] = wk;
+          if (STAGE == 1 && (i < TC || k == N)) D.w[nb + k] = wk;
         } else {
           wk = D.w[nb + k];
         }
@@ -937,7 +944,7 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
         sF[3][i] = F.FB;
       }
     }
-    for (int i = tid; i < T + 2; i += T) {
+    for (int i = tid; i < TC + 2; i += T) {
       const int64_t c = j0 - 1 + i;
       if (c >= -1 && c <= N) {
         const int64_t s = ghost(c, N, K.bc);
@@ -952,7 +959,7 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
     const int64_t j = j0 + tid;
     double jmaxa = 0.0, jmaxb = 0.0, jminb = INFINITY;
     uint32_t st = 0;
-    if (j < N) {
+    if (tid < TC && j < N) {
       const swale::Flux Fl = {sF[0][tid], sF[1][tid], sF[2][tid], sF[3][tid]};
       const swale::Flux Fr = {sF[0][tid + 1], sF[1][tid + 1], sF[2][tid + 1], sF[3][tid + 1]};
       const int64_t ic_e = eb + j + 1;  // edge-array index of cell j
