@@ -180,17 +180,19 @@ swale_status swale_get_state(swale_ctx* ctx, double* h, double* hu, double* b, d
 swale_status swale_batch_get_state(swale_ctx* ctx, double* hu, double* b, double* eta, double* x_nodes, double* t,
                                    double* dt);
 
-/* Launch shape: the tile (cells per block: 64, 128 or 256) of the reconstruction and update
- * kernels and their grid (0 = one block per tile; G > 0 = a persistent grid of G blocks
+/* Launch shape: the tile (threads per block: 64, 128 or 256; a reconstruction tile is that many
+ * cells, a forward update tile one cell fewer, so that its interfaces take one pass) of the
+ * reconstruction and update kernels and their grid (0 = one block per tile; G > 0 = a persistent grid of G blocks
  * walking the (instance, tile) work list). tiles[4] = {recon_tile, update_tile, recon_grid,
  * update_grid}. Results do not depend on the launch shape (bitwise). */
 swale_status swale_set_tiles(swale_ctx* ctx, int32_t recon_tile, int32_t update_tile, int32_t recon_grid,
                              int32_t update_grid);
 swale_status swale_get_tiles(swale_ctx* ctx, int32_t* tiles);
 
-/* Autotuner: times `steps` steps (after one untimed step) for each tile size pair in
- * {64, 128, 256}^2, each with one block per tile and with a persistent grid, from a snapshot of
- * the current state that is restored afterwards, and keeps the fastest. With a cache_path, a
+/* Autotuner: times `steps` steps (after one untimed step, the best of three such timings) for
+ * each tile size pair in {64, 128, 256}^2, each with one block per tile and with a persistent
+ * grid, from a snapshot of the current state that is restored afterwards, and keeps the
+ * fastest. With a cache_path, a
  * matching entry (key: SM count, B, log2 of the total cells, mesh kind) is used without timing,
  * and a new result is appended as one JSON object per line. tiles_out[4] (may be NULL) receives
  * the chosen shape. Allocates a temporary snapshot (5 doubles per cell). */
