@@ -1038,7 +1038,7 @@ swale_status swale_autotune(swale_ctx* ctx, int32_t steps, const char* cache_pat
   if (cudaError_t e = copy_state(true)) return release(fail(ctx, SWALE_ECUDA, cudaGetErrorString(e)));
   const bool timing = ctx->timing;
   ctx->timing = false;
-  const int occ_r = 4, occ_u = 8;  // resident 128-thread blocks per SM of the persistent candidates
+  const int occ_r = 6, occ_u = 8;  // resident 128-thread blocks per SM of the persistent candidates
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
