@@ -34,12 +34,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max
 # stages, from one ncu capture of the current kernels (the autotuner's pick on that box: 256-cell
 # reconstruction tiles, staged by bulk copies): stage 1 reads the smooth-class form of the
 # cached mesh geometry, 8 values per cell, and the rest only where the FP32 test leaves the class
-# open (109.3 + 47.2 MB), stage 2 writes the geometry (42.1 + 272.6 MB), stage 3 does neither
-# (42.0 + 27.3 MB).
-RECON_DRAM_BYTES = (109_259_776 + 47_176_704 + 42_120_704 + 272_576_512 + 42_027_776 + 27_312_640) // 3
+# open (109.3 + 47.1 MB), stage 2 writes the geometry (42.1 + 272.5 MB), stage 3 does neither
+# (42.1 + 27.4 MB).
+RECON_DRAM_BYTES = (109_250_816 + 47_147_520 + 42_124_800 + 272_467_456 + 42_105_088 + 27_435_008) // 3
 # Fraction of cycles the FP64 pipe was busy during the same k_recon launches (ncu
 # sm__pipe_fp64_cycles_active, the three stages): the kernel is bound by FP64 instruction issue.
-RECON_FP64_PIPE_ACTIVE = (0.8300 + 0.8580 + 0.8650) / 3
+RECON_FP64_PIPE_ACTIVE = (0.8290 + 0.8580 + 0.8650) / 3
 # FP64 FLOP equivalents per cell the same launches executed (ncu dadd + dmul + 2 dfma
 # instructions over the 2^20 cells; stages 1, 2, 3): what the hardware did, beside the method's
 # and the kernels' own counts.
@@ -57,12 +57,12 @@ ORACLE_STEP_FLOPS = 1891.80
 ORACLE_BATCH_STEP_FLOPS = 1893.17
 # The same counts for the scheme variants on the dam-break workload (reconstruction, step).
 ORACLE_VARIANT_FLOPS = {"nonwb": (583.01, 2613.02), "special": (366.61, 1780.82)}
-# DRAM bytes per k_update launch (stages 1, 2, 3: 159.5 + 41.8, 184.6 + 65.2, 184.7 + 48.4 MB), the
+# DRAM bytes per k_update launch (stages 1, 2, 3: 159.6 + 40.4, 184.6 + 65.6, 184.6 + 48.4 MB), the
 # fraction of cycles its FP64 pipe was busy and the FP64 FLOP equivalents per cell it executed
-# (ncu, the same capture as for k_recon above; 256-cell update tiles).
-UPDATE_DRAM_BYTES = (159_452_672 + 41_819_648 + 184_612_864 + 65_232_128 + 184_665_344 + 48_376_064) // 3
-UPDATE_FP64_PIPE_ACTIVE = (0.8640 + 0.8580 + 0.8580) / 3
-UPDATE_EXECUTED_FLOPS = (185.2 + 192.2 + 204.2) / 3
+# (ncu, the same capture as for k_recon above; 128-thread update blocks, 127-cell tiles).
+UPDATE_DRAM_BYTES = (159_597_824 + 40_424_448 + 184_598_784 + 65_593_600 + 184_634_624 + 48_376_576) // 3
+UPDATE_FP64_PIPE_ACTIVE = (0.8620 + 0.8620 + 0.8550) / 3
+UPDATE_EXECUTED_FLOPS = (185.4 + 192.5 + 204.5) / 3
 
 
 def parse():
