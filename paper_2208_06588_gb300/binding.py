@@ -84,12 +84,14 @@ def lib():
         L.swale_load.argtypes = [vp, ctypes.c_char_p]
         L.swale_rhs_noalloc.argtypes = [P(SwaleConfig), vp, i64, vp, vp, vp, vp, vp, d, vp, vp, vp, P(d), vp]
         L.swale_set_timing.argtypes = [vp, i32]
+        L.swale_check_recip.argtypes = [vp, i64, vp, vp]
         L.swale_get_timing.argtypes = [vp, vp, vp]
         for name in ("swale_create", "swale_set_problem", "swale_step", "swale_advance", "swale_get_state",
                      "swale_get_flags", "swale_get_status", "swale_rhs", "swale_enqueue", "swale_set_timing",
                      "swale_get_timing", "swale_rhs_noalloc", "swale_batch_set_problem", "swale_batch_get_state",
                      "swale_set_tiles", "swale_get_tiles", "swale_autotune", "swale_alpha_log",
-                     "swale_get_alpha_log", "swale_adjoint", "swale_adjoint_bytes", "swale_set_bottom_function", "swale_save", "swale_load"):
+                     "swale_get_alpha_log", "swale_adjoint", "swale_adjoint_bytes", "swale_set_bottom_function", "swale_save", "swale_load",
+                     "swale_check_recip"):
             getattr(L, name).restype = ctypes.c_int
         L.swale_last_error.argtypes = [vp]
         L.swale_last_error.restype = ctypes.c_char_p
@@ -266,6 +268,13 @@ def swale_rhs_noalloc(cfg: SwaleConfig, stream, N, E, M, B, J, w, alpha, RE, RM,
     if code != SWALE_OK:
         raise SwaleError(code, "swale_rhs_noalloc")
     return A.value
+
+
+def swale_check_recip(stream, n, x, y):
+    """y = the kernels' reciprocal of x (device arrays of n doubles), asynchronous on stream."""
+    code = lib().swale_check_recip(stream, int(n), ptr(x), ptr(y))
+    if code != SWALE_OK:
+        raise SwaleError(code, "swale_check_recip")
 
 
 def swale_last_error(ctx):

@@ -1264,6 +1264,14 @@ uint64_t adjoint_bytes(int64_t B, int64_t Nt, int64_t nsteps, int64_t ckpt_every
 
 }  // namespace
 
+namespace {
+// The kernels' reciprocal (swale::recip) applied element-wise, grid-stride.
+__global__ void k_check_recip(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = swale::recip(x[i]);
+}
+}  // namespace
+
 extern "C" {
 
 swale_status swale_alpha_log(swale_ctx* ctx, int32_t mode, int64_t nsteps, const double* log) {
@@ -1316,6 +1324,21 @@ swale_status swale_set_wait_test(swale_ctx* ctx, int32_t tries, uint32_t pad_byt
   ctx->wait_tries = tries;
   ctx->tx_pad = pad_bytes;
   return SWALE_OK;
+}
+
+swale_status swale_check_recip(void* cuda_stream, int64_t n, const double* x, double* y) {
+  if (n < 0 || (n > 0 && (!x || !y))) return SWALE_EINVAL;
+  if (n == 0) return SWALE_OK;
+  cudaPointerAttributes ax{}, ay{};
+  if (cudaPointerGetAttributes(&ax, x) != cudaSuccess || cudaPointerGetAttributes(&ay, y) != cudaSuccess) {
+    cudaGetLastError();
+    return SWALE_EINVAL;
+  }
+  if (ax.type != cudaMemoryTypeDevice || ay.type != cudaMemoryTypeDevice) return SWALE_EINVAL;
+  const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+  k_check_recip<<<(unsigned)blocks, 256, 0, s>>>(x, y, n);
+  return cudaGetLastError() == cudaSuccess ? SWALE_OK : SWALE_ECUDA;
 }
 
 swale_status swale_set_adjoint_tape(swale_ctx* ctx, int32_t enable) {

@@ -72,8 +72,12 @@ struct EdgeState {
 // pipe. On the device (double, no counting type) these helpers therefore compare IEEE bit
 // patterns on the integer pipe (an order-preserving key: the bits, with the magnitude bits
 // flipped for negative values) and form reciprocals from the hardware's 20-bit reciprocal
-// approximation refined by one cubic Newton step (y <- y (1 + e + e^2), e = 1 - x y), which
-// leaves a relative error below 2^-52 (3 FMAs instead of a full division). Zero, infinite and
+// approximation refined by one third-order step of the Newton-Raphson family for 1/x
+// (Householder's order-3 iteration: with e = 1 - x y the exact reciprocal is y / (1 - e) =
+// y (1 + e + e^2 + ...), and the step keeps the series to e^2, y <- y (1 + e + e^2), so the
+// relative error goes from e to e^3). With e below 2^-20 that leaves the final rounding: within
+// one unit in the last place of the correctly rounded 1 / x (swale_check_recip exposes it for
+// that test; 3 FMAs instead of a full division). Zero, infinite and
 // subnormal arguments give NaN there; no caller passes them on valid data. Elsewhere they are
 // the plain operators. Ties of min / max return the first argument.
 // ------------------------------------------------------------------------------------
