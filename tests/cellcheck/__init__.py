@@ -1,8 +1,9 @@
-"""Host builds of the per-cell arithmetic for checking the hand-written adjoint.
+"""Host builds of the per-cell arithmetic for checking the hand-written adjoint (test tooling).
 
-csrc/celltest_tangent.cpp compiles swale_cell.cuh on a forward-mode dual scalar (tangents);
-csrc/celltest_adjoint.cpp compiles the reverse sweeps of swale_adjoint.cuh. Both are linked
-into libswale_cellcheck.so; tests compare <ob, T u> with <T^T ob, u> per function.
+celltest_tangent.cpp compiles the library's swale_cell.cuh on a forward-mode dual scalar
+(tangents); celltest_adjoint.cpp compiles the reverse sweeps of swale_adjoint.cuh. Both are
+linked into libswale_cellcheck.so beside them; tests compare <ob, T u> with <T^T ob, u> per
+function, and check the FP32 smooth-class test against the FP64 detector.
 """
 from __future__ import annotations
 
@@ -13,8 +14,8 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_C = os.path.join(_HERE, "csrc")
-_SRC = [os.path.join(_C, f) for f in ("celltest_tangent.cpp", "celltest_adjoint.cpp")]
+_C = os.path.join(os.path.dirname(os.path.dirname(_HERE)), "paper_2208_06588_gb300", "csrc")
+_SRC = [os.path.join(_HERE, f) for f in ("celltest_tangent.cpp", "celltest_adjoint.cpp")]
 _DEPS = _SRC + [os.path.join(_C, f) for f in ("swale_cell.cuh", "swale_adjoint.cuh")]
 _LIB = os.path.join(_HERE, "libswale_cellcheck.so")
 _lib = None
@@ -23,7 +24,7 @@ _lib = None
 def build(force=False):
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(p) for p in _DEPS):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-o", tmp, *_SRC], check=True)
+        subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-I", _C, "-o", tmp, *_SRC], check=True)
         os.replace(tmp, _LIB)
     return _LIB
 

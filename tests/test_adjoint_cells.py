@@ -5,7 +5,7 @@ scheme has (smooth / transition / non-smooth classes, limiter on / off, wet / dr
 import numpy as np
 import pytest
 
-from paper_2208_06588_gb300 import cellcheck as C
+from tests import cellcheck as C
 
 RNG = np.random.default_rng(424242)
 PRM = np.array([9.812, 1e-6, 1e-11, 1e-6, 0.0, 0.0])  # g, eps, eps_pp, h_dry, dxmax, limit_hu

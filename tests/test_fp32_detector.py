@@ -9,7 +9,7 @@ never a second opinion. It must also say so for most clearly smooth cells, or it
 import numpy as np
 import pytest
 
-from paper_2208_06588_gb300 import cellcheck as C
+from tests import cellcheck as C
 
 
 def _gamma(b, eps):
