@@ -58,7 +58,8 @@ extern "C" {
 // source geometry and source, the flux differences (the RK combination is added in Python);
 // out[10..14]: one interface flux alone; out[15..17]: smooth / transition / non-smooth cells;
 // out[18]: FLOPs of the mesh-only geometry (cell_geom) summed; out[19]: FLOPs of the source
-// term's mesh-only width ratios (source_geom and the cell's reciprocal width) summed.
+// term's mesh-only values (source_form, or source_geom for the special scheme, and the cell's
+// reciprocal width) summed.
 void opc_count_stage(int64_t N, const double* E, const double* M, const double* B, const double* J, int32_t bc,
                      double g, double eps_weno, double eps_pp, double h_dry, double alpha, int64_t c0, int64_t c1,
                      double* out, int32_t scheme) {
@@ -135,8 +136,12 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
                     : swale::interface_flux(CD(g), CD(alpha), CD(0.01), o.ER, o.EL, o.BR, o.BL, o.hR, o.hL, o.uR, o.uL);
     const long long f0 = opc::C.add + opc::C.mul + opc::C.div + opc::C.sqrt;
     const CD iJc = CD(1.0) / Jv[3];
-    const swale::SourceGeom sg =
-        swale::source_geom(Jv[2], Jv[3], CD(1.0 / Jv[2].v), iJc, CD(1.0 / Jv[4].v), ip[2], ip[3], it[2]);
+    swale::SourceGeom sg;
+    swale::SourceForm sf;
+    if (scheme == 2)
+      sg = swale::source_geom(Jv[2], Jv[3], CD(1.0 / Jv[2].v), iJc, CD(1.0 / Jv[4].v), ip[2], ip[3], it[2]);
+    else
+      sf = swale::source_form(Jv[2], Jv[3], Jv[4], CD(1.0 / Jv[2].v), iJc, CD(1.0 / Jv[4].v), ip[2], ip[3], it[2]);
     sgeom_flops += (double)(opc::C.add + opc::C.mul + opc::C.div + opc::C.sqrt - f0);
     const CD hd[5] = {V[0][2] - V[2][2], V[0][3] - V[2][3], V[0][4] - V[2][4], o.hL, o.hR};
     const CD bd[5] = {V[2][2], V[2][3], V[2][4], o.BL, o.BR};
@@ -145,7 +150,7 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
       const CD eta4[4] = {o.EL, etaG[0], etaG[1], o.ER};
       Sj = swale::source_cell_special(CD(g), V[0][3], eta4, bd, sg, o.BL, o.BR);
     } else {
-      Sj = swale::source_cell(CD(g), hd, bd, sg);
+      Sj = swale::source_cell_form(CD(g), hd, bd, sf);
     }
     (void)swale::cell_rhs(F, F, Sj);
     add_to(upd);
@@ -170,7 +175,7 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
 // stencils as opc_count_stage), with unit adjoint seeds. out[0]: reverse reconstruction per
 // cell (recon_cell_rev, the cell's own pair and triple terms recomputed, and the scatter of the
 // divided-difference adjoints to the five stencil cells); out[1]: reverse source per cell
-// (source_geom with the cell's reciprocal width, the depth data, source_cell_rev); out[2]:
+// (source_form with the cell's reciprocal width, the depth data, source_cell_form_rev); out[2]:
 // reverse flux per interface (interface_flux_rev). FLOPs: add + mul + div + sqrt, summed.
 void opc_count_reverse(int64_t N, const double* E, const double* M, const double* B, const double* J, int32_t bc,
                        double g, double eps_weno, double eps_pp, double h_dry, double alpha, int64_t c0, int64_t c1,
@@ -238,12 +243,12 @@ void opc_count_reverse(int64_t N, const double* E, const double* M, const double
     // Reverse source.
     opc::C = opc::Counts();
     const CD iJc = CD(1.0) / Jv[3];
-    const swale::SourceGeom sg =
-        swale::source_geom(Jv[2], Jv[3], CD(1.0 / Jv[2].v), iJc, CD(1.0 / Jv[4].v), ip[2], ip[3], it[2]);
+    const swale::SourceForm sf =
+        swale::source_form(Jv[2], Jv[3], Jv[4], CD(1.0 / Jv[2].v), iJc, CD(1.0 / Jv[4].v), ip[2], ip[3], it[2]);
     const CD hd[5] = {V[0][2].v - V[2][2].v, V[0][3] - V[2][3], V[0][4].v - V[2][4].v, o.hL, o.hR};
     const CD bd[5] = {V[2][2], V[2][3], V[2][4], o.BL, o.BR};
-    CD hdb[5], bdb[5];
-    swale::source_cell_rev(CD(g), hd, bd, sg, CD(1.0), hdb, bdb);
+    CD hdb[5] = {}, bdb[5] = {};
+    swale::source_cell_form_rev(CD(g), hd, bd, sf, CD(1.0), hdb, bdb);
     rsrc += flops();
     // Reverse flux.
     opc::C = opc::Counts();

@@ -167,6 +167,36 @@ SWALE_HD void source_cell_rev(real g, const real hd[5], const real bd[5], const 
   source_dd_rev(sg, cbv[1], bdb);
 }
 
+// Adjoint of source_cell_form: accumulates into hdb[5], bdb[5] the adjoints of the depth and
+// bottom data for the adjoint Sb of the source value. With acc = h_j (db_R - db_L) + sum_k dh_k u_k
+// and u = A db (+ the diagonal part), the adjoint of dh_k is u_k and that of db_l is
+// v_l = sum_k dh_k A_kl (+ the diagonal part and +-h_j for R, L); h_j and b_j enter the
+// differences with the sign -1.
+SWALE_HD void source_cell_form_rev(real g, const real hd[5], const real bd[5], const SourceForm& A, real Sb,
+                                   real hdb[5], real bdb[5]) {
+  const real hc = hd[1], bc = bd[1];
+  const real db0 = bd[0] - bc, db2 = bd[2] - bc, db3 = bd[3] - bc, db4 = bd[4] - bc;
+  const real dh0 = hd[0] - hc, dh2 = hd[2] - hc, dh3 = hd[3] - hc, dh4 = hd[4] - hc;
+  real u[4];
+  source_form_rows(A, db0, db2, db3, db4, u);
+  real v[4];
+  v[0] = -(A.a02 * dh2) - A.a03 * dh3 - A.a04 * dh4;
+  v[1] = A.a02 * dh0 - A.a23 * dh3 - A.a24 * dh4;
+  v[2] = (A.a03 * dh0 + A.a23 * dh2) - A.a34 * dh4 - (hc + 0.5 * dh3);
+  v[3] = (A.a04 * dh0 + A.a24 * dh2) + A.a34 * dh3 + (hc + 0.5 * dh4);
+  const real ab = -g * Sb;  // adjoint of acc
+  hdb[0] = hdb[0] + ab * u[0];
+  hdb[2] = hdb[2] + ab * u[1];
+  hdb[3] = hdb[3] + ab * u[2];
+  hdb[4] = hdb[4] + ab * u[3];
+  hdb[1] = hdb[1] + ab * ((db4 - db3) - ((u[0] + u[1]) + (u[2] + u[3])));
+  bdb[0] = bdb[0] + ab * v[0];
+  bdb[2] = bdb[2] + ab * v[1];
+  bdb[3] = bdb[3] + ab * v[2];
+  bdb[4] = bdb[4] + ab * v[3];
+  bdb[1] = bdb[1] - ab * ((v[0] + v[1]) + (v[2] + v[3]));
+}
+
 // Adjoint of recon_cell: from the adjoints ob of the limited edge state of cell j, the adjoints
 // of the data it read: v0b[v][a] (averages of cells j-2+a) and DDb (divided differences).
 //   it[3]: reciprocal sums of the triples starting at cells j-2, j-1, j (smooth-class form).

@@ -180,13 +180,13 @@ __global__ void __launch_bounds__(T) k_adj_source(StepConst K, DevState D, AdjSt
     const double* B = Bg + cb;
     const double* Js = Jsg + cb;
     const double Jm = Js[jm], Jc = Js[j], Jp = Js[jp];
-    const swale::SourceGeom sg = swale::source_geom(Jm, Jc, swale::recip(Jm), swale::recip(Jc), swale::recip(Jp), D.ipair[eb + j],
-                                                    D.ipair[eb + j + 1], D.itri[eb + j + 1]);
+    const swale::SourceForm sf = swale::source_form(Jm, Jc, Jp, swale::recip(Jm), swale::recip(Jc), swale::recip(Jp),
+                                                    D.ipair[eb + j], D.ipair[eb + j + 1], D.itri[eb + j + 1]);
     const int64_t ie = eb + j + 1;
     const double hd[5] = {E[jm] - B[jm], E[j] - B[j], E[jp] - B[jp], D.ehL[ie], D.ehR[ie]};
     const double bd[5] = {B[jm], B[j], B[jp], D.eBL[ie], D.eBR[ie]};
     double hdb[5] = {0, 0, 0, 0, 0}, bdb[5] = {0, 0, 0, 0, 0};
-    swale::source_cell_rev(K.sc.g, hd, bd, sg, A.rM[cb + j], hdb, bdb);
+    swale::source_cell_form_rev(K.sc.g, hd, bd, sf, A.rM[cb + j], hdb, bdb);
     A.ab[4][ie] += hdb[3];
     A.ab[5][ie] += hdb[4];
     A.ab[2][ie] += bdb[3];

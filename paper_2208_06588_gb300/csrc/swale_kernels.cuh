@@ -33,6 +33,7 @@ namespace swale_dev {
 
 static_assert(sizeof(swale::CellGeom) == SWALE_GEOM_VALUES * sizeof(double), "CellGeom holds SWALE_GEOM_VALUES doubles");
 static_assert(sizeof(swale::SourceGeom) == 6 * sizeof(double), "SourceGeom holds 6 doubles");
+static_assert(sizeof(swale::SourceForm) == 6 * sizeof(double), "SourceForm holds 6 doubles");
 
 using swale::EdgeState;
 using swale::SchemeConst;
@@ -867,7 +868,7 @@ struct RhsOut {
 // PLAIN: an instantiation for the hydrostatic scheme without the L2-projection bottom (the
 // common case), in which the other schemes' branches are compiled out.
 template <int STAGE, int MODE, int T, bool PLAIN = false>
-__global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const double* __restrict__ Eg,
+__global__ void __launch_bounds__(T, PLAIN ? 1024 / T : 1) k_update(StepConst K, DevState D, const double* __restrict__ Eg,
                                               const double* __restrict__ Mg, const double* __restrict__ Bg,
                                               const double* __restrict__ Jsg, RhsOut ro) {
   __shared__ double sF[4][T], sW[T];                              // interfaces / nodes j0 .. j0+T-1
@@ -963,28 +964,43 @@ __global__ void __launch_bounds__(T) k_update(StepConst K, DevState D, const dou
       const swale::Flux Fl = {sF[0][tid], sF[1][tid], sF[2][tid], sF[3][tid]};
       const swale::Flux Fr = {sF[0][tid + 1], sF[1][tid + 1], sF[2][tid + 1], sF[3][tid + 1]};
       const int64_t ic_e = eb + j + 1;  // edge-array index of cell j
-      swale::SourceGeom sg;
-      double* sgv = reinterpret_cast<double*>(&sg);
-      if (use_sgeo) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) sgv[k] = D.geo[(SWALE_GEOM_VALUES + k) * D.geo_stride + ic_e];
-      } else {
-        sg = swale::source_geom(sJ[tid], sJ[tid + 1], siJ[tid], siJ[tid + 1], siJ[tid + 2], D.ipair[eb + j],
-                                D.ipair[eb + j + 1], D.itri[eb + j + 1]);
-      }
-      if (STAGE == 2 && MODE == 0 && D.geo) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) D.geo[(SWALE_GEOM_VALUES + k) * D.geo_stride + ic_e] = sgv[k];
-      }
       const double hd[5] = {sH[tid], sH[tid + 1], sH[tid + 2], D.ehL[ic_e], D.ehR[ic_e]};
       const double bd[5] = {sB[tid], sB[tid + 1], sB[tid + 2], D.eBL[ic_e], D.eBR[ic_e]};
+      // Six mesh-only values of the source per cell: the antisymmetric form (SourceForm), or the
+      // width ratios (SourceGeom) for the special scheme's point-wise source.
       double Sj;
       if (!PLAIN && K.scheme == 2) {
+        swale::SourceGeom sg;
+        double* const src6 = reinterpret_cast<double*>(&sg);
+        if (use_sgeo) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) src6[k] = D.geo[(SWALE_GEOM_VALUES + k) * D.geo_stride + ic_e];
+        } else {
+          sg = swale::source_geom(sJ[tid], sJ[tid + 1], siJ[tid], siJ[tid + 1], siJ[tid + 2], D.ipair[eb + j],
+                                  D.ipair[eb + j + 1], D.itri[eb + j + 1]);
+        }
+        if (STAGE == 2 && MODE == 0 && D.geo) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) D.geo[(SWALE_GEOM_VALUES + k) * D.geo_stride + ic_e] = src6[k];
+        }
         const double eta4[4] = {D.eEL[ic_e], D.eG1[ic_e], D.eG2[ic_e], D.eER[ic_e]};
         Sj = swale::source_cell_special(K.sc.g, E[j], eta4, bd, sg, D.eBR[ic_e - 1],
                                         D.eBL[ic_e + 1]);
       } else {
-        Sj = swale::source_cell(K.sc.g, hd, bd, sg);
+        swale::SourceForm sf;
+        double* const src6 = reinterpret_cast<double*>(&sf);
+        if (use_sgeo) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) src6[k] = D.geo[(SWALE_GEOM_VALUES + k) * D.geo_stride + ic_e];
+        } else {
+          sf = swale::source_form(sJ[tid], sJ[tid + 1], sJ[tid + 2], siJ[tid], siJ[tid + 1], siJ[tid + 2],
+                                  D.ipair[eb + j], D.ipair[eb + j + 1], D.itri[eb + j + 1]);
+        }
+        if (STAGE == 2 && MODE == 0 && D.geo) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) D.geo[(SWALE_GEOM_VALUES + k) * D.geo_stride + ic_e] = src6[k];
+        }
+        Sj = swale::source_cell_form(K.sc.g, hd, bd, sf);
       }
       const swale::CellRhs R = swale::cell_rhs(Fl, Fr, Sj);
       const double RE = R.RE, RM = R.RM, RB = R.RB;

@@ -90,6 +90,21 @@ def source_adjoint(hd, bd, geom, g, Sb):
     return hdb, bdb
 
 
+def source_form_tangent(hd, bd, thd, tbd, w3, g):
+    S, tS = ctypes.c_double(0), ctypes.c_double(0)
+    lib().ct_source_form_tangent(*map(_p, (f64(hd), f64(bd), f64(thd), f64(tbd), f64(w3))), ctypes.c_double(g),
+                                 ctypes.byref(S), ctypes.byref(tS))
+    return S.value, tS.value
+
+
+def source_form_adjoint(hd, bd, w3, g, Sb):
+    """(hdb, bdb, S by the form, S by the monomial form)."""
+    hdb, bdb, out = np.zeros(5), np.zeros(5), np.zeros(2)
+    arrs = [f64(x) for x in (hd, bd, w3)]
+    lib().ct_source_form_adjoint(*map(_p, arrs), ctypes.c_double(g), ctypes.c_double(Sb), _p(hdb), _p(bdb), _p(out))
+    return hdb, bdb, out[0], out[1]
+
+
 def smooth_test(w5, dx, D2h, D2m, it, eps=1e-6):
     """(FP32 test says surely smooth, FP64 class, FP64 indicators) of one cell's data: the widths
     w5[5] and length dx of its mesh factors, pair differences D2h[4], D2m[4], reciprocal triple

@@ -118,4 +118,21 @@ void ct_source_tangent(const double* hd, const double* bd, const double* thd, co
   *tS = s.d;
 }
 
+// The antisymmetric form of the same source (source_form, source_cell_form) from the widths
+// w3 = (J_{j-1}, J_j, J_{j+1}). out: S, tS (tangent).
+void ct_source_form_tangent(const double* hd, const double* bd, const double* thd, const double* tbd, const double* w3,
+                            double g, double* S, double* tS) {
+  D a[5], b[5];
+  for (int k = 0; k < 5; ++k) {
+    a[k] = D(hd[k], thd[k]);
+    b[k] = D(bd[k], tbd[k]);
+  }
+  const double Jm = w3[0], Jc = w3[1], Jp = w3[2];
+  const swale::SourceForm f = swale::source_form(D(Jm), D(Jc), D(Jp), D(1.0 / Jm), D(1.0 / Jc), D(1.0 / Jp),
+                                                 D(1.0 / (Jm + Jc)), D(1.0 / (Jc + Jp)), D(1.0 / (Jm + Jc + Jp)));
+  const D s = swale::source_cell_form(D(g), a, b, f);
+  *S = s.v;
+  *tS = s.d;
+}
+
 }  // extern "C"

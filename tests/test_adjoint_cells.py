@@ -146,3 +146,80 @@ def test_smooth_class_linear_form_equals_the_sub_stencil_sum():
         c = np.full(5, v[2])
         L.ct_edge_forms(ptr(h), ptr(c), ptr(out))
         assert out[2] == v[2] and out[3] == v[2]
+
+
+def _exact_source(hd, bd, w3, g):
+    """-g int_0^1 p q' dt in exact rational arithmetic: p, q the quartics of the cell's unit
+    coordinate whose averages over the three cells (widths w3 relative to the middle one) and
+    values at t = 0, 1 are the data hd, bd (solved by fraction-exact elimination)."""
+    from fractions import Fraction as Fr
+    rm, rp = Fr(w3[0]) / Fr(w3[1]), Fr(w3[2]) / Fr(w3[1])
+
+    def avg(a, b, i):
+        return (Fr(b) ** (i + 1) - Fr(a) ** (i + 1)) / (i + 1) / (Fr(b) - Fr(a))
+
+    rows = [[avg(-rm, 0, i) for i in range(5)], [avg(0, 1, i) for i in range(5)],
+            [avg(1, 1 + rp, i) for i in range(5)], [Fr(int(i == 0)) for i in range(5)], [Fr(1)] * 5]
+
+    def solve(data):
+        M = [r[:] + [Fr(d)] for r, d in zip(rows, data)]
+        for c in range(5):
+            p = next(r for r in range(c, 5) if M[r][c] != 0)
+            M[c], M[p] = M[p], M[c]
+            for r in range(5):
+                if r != c and M[r][c] != 0:
+                    f = M[r][c] / M[c][c]
+                    M[r] = [a - f * b for a, b in zip(M[r], M[c])]
+        return [M[i][5] / M[i][i] for i in range(5)]
+
+    a, b = solve(hd), solve(bd)
+    return -Fr(g) * sum(a[i] * b[m] * Fr(m, i + m) for i in range(5) for m in range(1, 5))
+
+
+@pytest.mark.parametrize("spread", [0.3, 1.5, 3.0])
+def test_source_form_is_the_exact_integral(spread):
+    """The antisymmetric bilinear form of the source (source_form, source_cell_form) against the
+    exact integral of the interpolant product, on random widths (ratios up to e^(2 spread)) and
+    random or smooth data; the confluent monomial form (source_cell) is checked the same way with
+    a looser bound (it loses digits at large width ratios)."""
+    rng = np.random.default_rng(int(spread * 10))
+    for t in range(40):
+        w3 = np.exp(rng.uniform(-spread, spread, 3))
+        if t % 2:
+            xs = np.array([-w3[0] / 2, w3[1] / 2, w3[1] + w3[2] / 2, 0.0, w3[1]]) / w3[1]
+            hd, bd = 1.0 + 0.1 * np.sin(xs), 0.5 + 0.05 * np.cos(2 * xs)
+        else:
+            hd, bd = rng.uniform(0.1, 2.0, 5), rng.uniform(0.0, 1.0, 5)
+        ex = float(_exact_source(hd, bd, w3, 9.812))
+        _, _, Sf, Sm = C.source_form_adjoint(hd, bd, w3, 9.812, 1.0)
+        scale = 9.812 * np.abs(hd).max() * np.abs(bd - bd[1]).max()
+        assert abs(Sf - ex) <= 1e-13 * scale, (t, Sf, ex)
+        assert abs(Sm - ex) <= 1e-10 * scale, (t, Sm, ex)
+
+
+@pytest.mark.parametrize("trial", range(20))
+def test_source_form_reverse_matches_tangent(trial):
+    rng = np.random.default_rng(300 + trial)
+    w3 = np.exp(rng.uniform(-1.5, 1.5, 3))
+    hd, bd = rng.uniform(0.1, 2, 5), rng.uniform(0, 1, 5)
+    thd, tbd, Sb = rng.normal(size=5), rng.normal(size=5), rng.normal()
+    S, tS = C.source_form_tangent(hd, bd, thd, tbd, w3, 9.812)
+    hdb, bdb, Sf, _ = C.source_form_adjoint(hd, bd, w3, 9.812, Sb)
+    assert S == Sf
+    lhs, rhs = Sb * tS, hdb @ thd + bdb @ tbd
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + np.abs(hdb * thd).sum() + np.abs(bdb * tbd).sum())
+
+
+def test_source_form_at_rest_is_the_pressure_jump():
+    """Depth data h = eta - b with eta constant: the form gives -g (eta (b_R - b_L) - (b_R^2 -
+    b_L^2) / 2) to rounding (the antisymmetric part vanishes on dh = -db), the identity behind the
+    well-balanced property (Sec. 4.3)."""
+    rng = np.random.default_rng(77)
+    for t in range(200):
+        w3 = np.exp(rng.uniform(-2.0, 2.0, 3))
+        bd = rng.uniform(0.0, 1.0, 5)
+        eta = 1.0 + rng.uniform(0.0, 2.0)
+        hd = eta - bd
+        _, _, Sf, _ = C.source_form_adjoint(hd, bd, w3, 9.812, 1.0)
+        jump = -9.812 * (eta * (bd[4] - bd[3]) - 0.5 * (bd[4] ** 2 - bd[3] ** 2))
+        assert abs(Sf - jump) <= 1e-14 * 9.812 * eta, (t, Sf, jump)

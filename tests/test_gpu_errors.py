@@ -152,3 +152,43 @@ def test_timeout_keeps_the_last_good_step():
     ref = _good_run(x, E, hu, b, P, 5)
     for key in KEYS:
         assert np.array_equal(g[key], ref[key]), key
+
+
+def test_adjoint_larger_than_the_device_is_refused_and_the_context_goes_on():
+    """A gradient whose checkpoints cannot fit in device memory: swale_adjoint returns
+    SWALE_ENOMEM (its one scratch allocation fails; nothing runs), and the context then steps and
+    differentiates like a fresh one."""
+    import torch
+    N, G = 20000, 2
+    x, E, hu, b, P = inverting(N=N, a=0.0)
+    cfg = dict(CFG, dt_fixed=1e-5)  # CFL about 0.6 on 20000 cells
+    total = torch.cuda.mem_get_info()[1]
+    nsteps = int(2 * total // (5 * 8 * N)) + 1
+    need = B.swale_adjoint_bytes(1, N, nsteps, 1, G)
+    assert need > 1.5 * total
+    gx = np.array([0.25, 0.75])
+    obs = np.full((nsteps, G), 0.9)  # the full observation array, although it is never read
+
+    def solver():
+        s = B.Solver(B.make_config(**cfg))
+        s.set_problem(x, E, hu, b, P, q0_is_eta=True)
+        return s
+
+    s = solver()
+    with pytest.raises(B.SwaleError) as err:
+        B.swale_adjoint(s.ctx, nsteps, 1, G, gx, obs, np.zeros(1), np.zeros(N))
+    assert err.value.code == -2
+    assert s.status()[0] == 0
+    assert s.advance(3) == 3
+    g = s.state()
+    J = np.zeros(1)
+    B.swale_adjoint(s.ctx, 4, 2, G, gx, obs[:4], J, np.zeros(N))
+    s.close()
+    r = solver()
+    assert r.advance(3) == 3
+    ref = r.state()
+    assert r.status()[0] == 0
+    r.close()
+    for key in KEYS:
+        assert np.array_equal(g[key], ref[key]), key
+    assert np.isfinite(J[0]) and J[0] > 0
