@@ -34,16 +34,21 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max
 # stages, from one ncu capture of the current kernels (the autotuner's pick on that box: 256-cell
 # reconstruction tiles, staged by bulk copies): stage 1 reads the smooth-class form of the
 # cached mesh geometry, 8 values per cell, and the rest only where the FP32 test leaves the class
-# open (109.3 + 47.1 MB), stage 2 writes the geometry (42.1 + 272.5 MB), stage 3 does neither
-# (42.1 + 27.4 MB).
-RECON_DRAM_BYTES = (109_250_816 + 47_147_520 + 42_124_800 + 272_467_456 + 42_105_088 + 27_435_008) // 3
+# open (109.2 + 46.6 MB), stage 2 writes the geometry (42.1 + 272.6 MB), stage 3 does neither
+# (42.0 + 27.8 MB).
+RECON_DRAM_BYTES = (109_205_760 + 46_568_192 + 42_138_112 + 272_582_144 + 42_033_152 + 27_768_832) // 3
 # Fraction of cycles the FP64 pipe was busy during the same k_recon launches (ncu
 # sm__pipe_fp64_cycles_active, the three stages): the kernel is bound by FP64 instruction issue.
-RECON_FP64_PIPE_ACTIVE = (0.8290 + 0.8580 + 0.8650) / 3
+RECON_FP64_PIPE_ACTIVE = (0.8237 + 0.8566 + 0.8647) / 3
 # FP64 FLOP equivalents per cell the same launches executed (ncu dadd + dmul + 2 dfma
 # instructions over the 2^20 cells; stages 1, 2, 3): what the hardware did, beside the method's
 # and the kernels' own counts.
-RECON_EXECUTED_FLOPS = (125.2 + 208.4 + 204.6) / 3
+RECON_EXECUTED_FLOPS = (120.9 + 204.1 + 200.4) / 3
+# The source term's mesh-only part in the method figures: the interpolant's width ratios in
+# closed form (6 products and the cell's reciprocal width), as the paper's construction needs
+# them. The kernels spend more there (the six entries of the antisymmetric source form, counted
+# in their own figures) to spend less on the state arithmetic.
+METHOD_SOURCE_GEOM_FLOPS = 7.0
 # The method's FP64 operations per cell, counted by the CPU oracle on an operation-counting
 # scalar type (oracle.count_step; tests/test_bench_contract.py recounts them): the arithmetic on
 # state-dependent values of one stage's reconstruction + limiter, and of one whole SSP-RK3 step,
@@ -52,22 +57,17 @@ RECON_EXECUTED_FLOPS = (125.2 + 208.4 + 204.6) / 3
 # elimination, which is not a figure of the method; the method figures add the kernels'
 # closed-form count of that mesh-only part in every stage (no reuse across stages). These are
 # the roofline numerators, so a kernel change that removes work does not lower the fraction.
-# The source term's mesh-only part in the method figures: the interpolant's width ratios in
-# closed form (6 products and the cell's reciprocal width), as the paper's construction needs
-# them. The kernels spend more there (the six entries of the antisymmetric source form, counted
-# in their own figures) to spend less on the state arithmetic.
-METHOD_SOURCE_GEOM_FLOPS = 7.0
 ORACLE_RECON_FLOPS = 318.60
 ORACLE_STEP_FLOPS = 1891.80
 ORACLE_BATCH_STEP_FLOPS = 1893.17
 # The same counts for the scheme variants on the dam-break workload (reconstruction, step).
 ORACLE_VARIANT_FLOPS = {"nonwb": (583.01, 2613.02), "special": (366.61, 1780.82)}
-# DRAM bytes per k_update launch (stages 1, 2, 3: 159.6 + 40.4, 184.6 + 65.6, 184.6 + 48.4 MB), the
+# DRAM bytes per k_update launch (stages 1, 2, 3: 159.4 + 40.5, 184.7 + 65.4, 184.8 + 47.7 MB), the
 # fraction of cycles its FP64 pipe was busy and the FP64 FLOP equivalents per cell it executed
 # (ncu, the same capture as for k_recon above; 128-thread update blocks, 127-cell tiles).
-UPDATE_DRAM_BYTES = (159_597_824 + 40_424_448 + 184_598_784 + 65_593_600 + 184_634_624 + 48_376_576) // 3
-UPDATE_FP64_PIPE_ACTIVE = (0.8620 + 0.8620 + 0.8550) / 3
-UPDATE_EXECUTED_FLOPS = (185.4 + 192.5 + 204.5) / 3
+UPDATE_DRAM_BYTES = (159_437_312 + 40_500_224 + 184_734_208 + 65_380_096 + 184_763_136 + 47_675_392) // 3
+UPDATE_FP64_PIPE_ACTIVE = (0.8549 + 0.8577 + 0.8529) / 3
+UPDATE_EXECUTED_FLOPS = (128.4 + 183.5 + 195.5) / 3
 
 
 def parse():
