@@ -74,99 +74,6 @@ SWALE_HD EdgeAdj interface_flux_rev(real g, real alpha, real w, real EL, real ER
   return a;
 }
 
-// Reverse of the confluent divided differences of source_cell for one data vector u[0..4]
-// given the adjoints cb[1..5] of the Newton coefficients; accumulates into ub[0..4].
-SWALE_HD void source_dd_rev(const SourceGeom& sg, const real cb[6], real ub[5]) {
-  const real o5b = cb[5];
-  const real o4ab = cb[4] - o5b * sg.i1mp;
-  const real o4bb = o5b * sg.i1mp;
-  const real o3ab = cb[3] - o4ab * sg.i1m;
-  const real o3bb = o4ab * sg.i1m - o4bb * sg.i1p;
-  const real o3cb = o4bb * sg.i1p;
-  const real o2ab = cb[2] - o3ab * sg.i1m;
-  const real o2bb = o3ab * sg.i1m - o3bb;
-  const real o2cb = o3bb - o3cb * sg.i1p;
-  const real o2db = o3cb * sg.i1p;
-  ub[0] = ub[0] + cb[1] - o2ab * sg.irm;
-  ub[3] = ub[3] + o2ab * sg.irm - o2bb;
-  ub[1] = ub[1] + o2bb - o2cb;
-  ub[4] = ub[4] + o2cb - o2db * sg.irp;
-  ub[2] = ub[2] + o2db * sg.irp;
-}
-
-// Adjoint of source_cell: accumulates into hdb[5], bdb[5] the adjoints of the depth and bottom
-// data for the adjoint Sb of the source value. The reverse of source_cell's own steps: Newton
-// coefficients by confluent divided differences, their monomial form a (depth) and ab (bottom)
-// without the factors (i + 1), S = -g sum_{i, m} a_i W[i][m] ab_m with those factors in W; then
-// transposed in the opposite order.
-SWALE_HD void source_cell_rev(real g, const real hd[5], const real bd[5], const SourceGeom& sg, real Sb, real hdb[5],
-                              real bdb[5]) {
-  real ch[6], cb[6];
-  const real* dat[2] = {hd, bd};
-  real* cf[2] = {ch, cb};
-  for (int v = 0; v < 2; ++v) {
-    const real* u = dat[v];
-    const real o2a = (u[3] - u[0]) * sg.irm;
-    const real o2b = u[1] - u[3];
-    const real o2c = u[4] - u[1];
-    const real o2d = (u[2] - u[4]) * sg.irp;
-    const real o3a = (o2b - o2a) * sg.i1m;
-    const real o3b = o2c - o2b;
-    const real o3c = (o2d - o2c) * sg.i1p;
-    const real o4a = (o3b - o3a) * sg.i1m;
-    const real o4b = (o3c - o3b) * sg.i1p;
-    real* c = cf[v];
-    c[1] = u[0];
-    c[2] = o2a;
-    c[3] = o3a;
-    c[4] = o4a;
-    c[5] = (o4b - o4a) * sg.i1mp;
-  }
-  // The monomial coefficients without their factors (i + 1), as source_cell forms them, with
-  // q = c_3 - c_4 + c_5 and d = c_4 - 2 c_5.
-  const real rm = sg.rm;
-  real a[5], ab[5];
-  const real* cs[2] = {ch, cb};
-  real* ms[2] = {a, ab};
-  for (int v = 0; v < 2; ++v) {
-    const real* c = cs[v];
-    real* o = ms[v];
-    const real q = c[3] - c[4] + c[5];
-    const real d = c[4] - 2.0 * c[5];
-    o[0] = c[1] + rm * c[2];
-    o[1] = c[2] + rm * q;
-    o[2] = q + rm * d;
-    o[3] = d + rm * c[5];
-    o[4] = c[5];
-  }
-  // S = -g sum_{i, m} a_i W[i][m] ab_m: adjoints of a_i and ab_m.
-  constexpr double kW[5][4] = SWALE_SRC_W;
-  const real gS = -g * Sb;
-  real ob[2][5];
-  for (int i = 0; i < 5; ++i)
-    ob[0][i] = gS * (ab[1] * kW[i][0] + ab[2] * kW[i][1] + ab[3] * kW[i][2] + ab[4] * kW[i][3]);
-  ob[1][0] = 0.0;
-  for (int m = 1; m < 5; ++m)
-    ob[1][m] = gS * (a[0] * kW[0][m - 1] + a[1] * kW[1][m - 1] + a[2] * kW[2][m - 1] + a[3] * kW[3][m - 1] +
-                     a[4] * kW[4][m - 1]);
-  // Transpose of the monomial form, per variable: adjoints of the Newton coefficients.
-  real cbv[2][6];
-  for (int v = 0; v < 2; ++v) {
-    const real* o = ob[v];
-    real* c = cbv[v];
-    const real qb = rm * o[1] + o[2];
-    const real db = rm * o[2] + o[3];
-    c[0] = 0.0;
-    c[1] = o[0];
-    c[2] = rm * o[0] + o[1];
-    c[3] = qb;
-    c[4] = db - qb;
-    c[5] = rm * o[3] + o[4] + qb - 2.0 * db;
-  }
-  source_dd_rev(sg, cbv[0], hdb);
-  source_dd_rev(sg, cbv[1], bdb);
-}
-
 // Adjoint of source_cell_form: accumulates into hdb[5], bdb[5] the adjoints of the depth and
 // bottom data for the adjoint Sb of the source value. With acc = h_j (db_R - db_L) + sum_k dh_k u_k
 // and u = A db (+ the diagonal part), the adjoint of dh_k is u_k and that of db_l is

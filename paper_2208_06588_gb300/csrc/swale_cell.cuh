@@ -759,81 +759,13 @@ SWALE_HD SourceGeom source_geom(real Jm, real Jc, real iJm, real iJc, real iJp, 
   return s;
 }
 
-// Weights of the source integral with the monomial factors folded in: (i + 1)(m + 1) m / (i + m)
-// for i = 0..4 (rows), m = 1..4 (columns); source_cell and its reverse use them.
-#define SWALE_SRC_W                                                      \
-  {{2.0, 3.0, 4.0, 5.0},                                                 \
-   {2.0, 4.0, 6.0, 8.0},                                                 \
-   {2.0, 3.0 * 6.0 / 4.0, 3.0 * 12.0 / 5.0, 3.0 * 20.0 / 6.0},           \
-   {2.0, 4.0 * 6.0 / 5.0, 4.0 * 12.0 / 6.0, 4.0 * 20.0 / 7.0},           \
-   {2.0, 5.0 * 6.0 / 6.0, 5.0 * 12.0 / 7.0, 5.0 * 20.0 / 8.0}}
-
-// Source term int_cell -g (eta_h - b_h) b_h' dx of Sec. 4.1, with eta_h - b_h interpolating the
-// depth data (averages h_{j-1}, h_j, h_{j+1}, limited edge depths h^L, h^R) and b_h the bottom
-// data (averages and limited edge bottoms), in the unit coordinate t of the cell.
-SWALE_HD real source_cell(real g, const real hd[5], const real bd[5], const SourceGeom& sg) {
-  // Confluent divided differences of the primitive on nodes (-rm, 0, 0, 1, 1, 1+rp):
-  // data order (avg_{j-1}, avg_j, avg_{j+1}, v_L, v_R).
-  real ch[6], cb[6];
-  const real* dat[2] = {hd, bd};
-  real* cf[2] = {ch, cb};
-  for (int v = 0; v < 2; ++v) {
-    const real* u = dat[v];
-    const real o2a = (u[3] - u[0]) * sg.irm;  // [z1, z2, z2]
-    const real o2b = u[1] - u[3];             // [z2, z2, z3]
-    const real o2c = u[4] - u[1];             // [z2, z3, z3]
-    const real o2d = (u[2] - u[4]) * sg.irp;  // [z3, z3, z4]
-    const real o3a = (o2b - o2a) * sg.i1m;    // [z1, z2, z2, z3]
-    const real o3b = o2c - o2b;               // [z2, z2, z3, z3]
-    const real o3c = (o2d - o2c) * sg.i1p;    // [z2, z3, z3, z4]
-    const real o4a = (o3b - o3a) * sg.i1m;    // [z1, z2, z2, z3, z3]
-    const real o4b = (o3c - o3b) * sg.i1p;    // [z2, z2, z3, z3, z4]
-    const real o5 = (o4b - o4a) * sg.i1mp;    // [z1 .. z4]
-    real* c = cf[v];
-    c[1] = u[0];
-    c[2] = o2a;
-    c[3] = o3a;
-    c[4] = o4a;
-    c[5] = o5;
-  }
-  // Basis n_k = (t + rm) m_k(t), m_2 = t, m_3 = t^2, m_4 = t^3 - t^2, m_5 = t^4 - 2 t^3 + t^2.
-  // The interpolant Pi' = c_1 + sum_k c_k n_k' in monomials a_0 + a_1 t + ... + a_4 t^4, with
-  // q = c_3 - c_4 + c_5 and d = c_4 - 2 c_5:
-  //   a_0 = c_1 + rm c_2,  a_1 = 2 (c_2 + rm q),  a_2 = 3 (q + rm d),  a_3 = 4 (d + rm c_5),
-  //   a_4 = 5 c_5.
-  // The bottom's slope is the derivative of its interpolant, sum_m m ab_m t^(m-1), and the
-  // integral of the product over [0, 1] is exact: sum_{i, m} a_i ab_m m / (i + m) (the
-  // 4-point Gauss-Legendre rule of the definition is exact for this degree-7 product too).
-  // The factors (i + 1) of a_i and (m + 1) of ab_m are folded into that sum's constants, so
-  // the monomial coefficients are formed without them (a_i / (i + 1)).
-  const real rm = sg.rm;
-  real a[5], ab[5];
-  const real* cs[2] = {ch, cb};
-  real* ms[2] = {a, ab};
-  for (int v = 0; v < 2; ++v) {
-    const real* c = cs[v];
-    real* o = ms[v];
-    const real q = c[3] - c[4] + c[5];
-    const real d = c[4] - 2.0 * c[5];
-    o[0] = c[1] + rm * c[2];
-    o[1] = c[2] + rm * q;
-    o[2] = q + rm * d;
-    o[3] = d + rm * c[5];
-    o[4] = c[5];
-  }
-  constexpr double kW[5][4] = SWALE_SRC_W;
-  real S = 0.0;
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const real vi = ab[1] * kW[i][0] + ab[2] * kW[i][1] + ab[3] * kW[i][2] + ab[4] * kW[i][3];
-    S += a[i] * vi;
-  }
-  return -g * S;
-}
-
-// The same source integral as an antisymmetric bilinear form. With phi_k the quartic cardinal
-// functions of the five data (phi_k reproduces datum k and annihilates the others), the integral
-// is h^T K b with K_kl = int_0^1 phi_k phi_l' dt. Integrating by parts, K + K^T = e_R e_R^T -
+// Source term int_cell -g (eta_h - b_h) b_h' dx of Sec. 4.1, with eta_h - b_h the quartic
+// interpolating the depth data (averages h_{j-1}, h_j, h_{j+1}, limited edge depths h^L, h^R;
+// the data order of hd) and b_h the quartic of the bottom data bd (averages and limited edge
+// bottoms), in the unit coordinate t of the cell, evaluated exactly as an antisymmetric bilinear
+// form. With phi_k the quartic cardinal functions of the five data (phi_k reproduces datum k and
+// annihilates the others), the integral is h^T K b with K_kl = int_0^1 phi_k phi_l' dt.
+// Integrating by parts, K + K^T = e_R e_R^T -
 // e_L e_L^T (the data v_L, v_R are the interpolants' values at t = 0, 1), and K 1 = 0 (a constant
 // bottom has no slope). So K = A + (e_R e_R^T - e_L e_L^T) / 2 with A antisymmetric and, in the
 // differences from the cell's own average (dh_k = h_k - h_j, db_k = b_k - b_j, k in {j-1, j+1,
@@ -848,9 +780,9 @@ SWALE_HD real source_cell(real g, const real hd[5], const real bd[5], const Sour
 //   A24 = -(14 r_m^2 + 21 r_m + 9) / (70 r_p (1 + r_m) (1 + r_p)^2 (1 + r_m + r_p))
 //   A34 = -(r_m^2 (35 r_p^2 + 35 r_p + 14) + r_m (35 r_p^2 + 21 r_p + 7) + 14 r_p^2 + 7 r_p + 2)
 //         / (70 r_m r_p (1 + r_m) (1 + r_p))
-// (exact integrals of the cardinal functions; equal to source_cell in exact arithmetic, about 29
-// FP64 operations per cell against 67, and 40 for the six entries, which stage 1 reads from the
-// mesh cache). At rest (h = eta - b, eta constant) the form gives -g (eta (b_R - b_L) -
+// (exact integrals of the cardinal functions: about 29 FP64 operations per cell, against 67 for
+// the product of the two interpolants in monomial form, and 40 for the six entries, which stage
+// 1 reads from the mesh cache). At rest (h = eta - b, eta constant) the form gives -g (eta (b_R - b_L) -
 // (b_R^2 - b_L^2) / 2), the pressure jump, as dh^T A db = -db^T A db = 0.
 struct SourceForm {
   real a02, a03, a04, a23, a24, a34;
@@ -885,7 +817,7 @@ SWALE_HD void source_form_rows(const SourceForm& A, real db0, real db2, real db3
   u[2] = (-(A.a03 * db0) - A.a23 * db2) + A.a34 * db4 - 0.5 * db3;
   u[3] = (-(A.a04 * db0) - A.a24 * db2) - A.a34 * db3 + 0.5 * db4;
 }
-// Source term of source_cell (same data, same value in exact arithmetic) from the form A.
+// The source term from the form A (data hd, bd as above).
 SWALE_HD real source_cell_form(real g, const real hd[5], const real bd[5], const SourceForm& A) {
   const real hc = hd[1], bc = bd[1];
   const real db0 = bd[0] - bc, db2 = bd[2] - bc, db3 = bd[3] - bc, db4 = bd[4] - bc;
@@ -902,9 +834,9 @@ SWALE_HD real source_cell_form(real g, const real hd[5], const real bd[5], const
 // Source of the special source-term scheme for cell j (Eq. source2 with Eq. bhat2D in 1D, the
 // Gauss-Lobatto sum of Eq. gausssij2): (g/2)(b2hat_R - b2hat_L) - g etabar (bhat_R - bhat_L)
 // - g sum_q w_q (eta_q - etabar) b_h'(t_q), with b^2hat = ((b-)^2 + (b+)^2) / 2, bhat = (b- + b+) / 2
-// at the two edges and b_h' the slope of the cell's bottom interpolant (that of source_cell) at
+// at the two edges and b_h' the slope of the cell's bottom interpolant (the quartic of bd) at
 // the Gauss-Lobatto points t = 0, (1 -+ 1/sqrt 5)/2, 1 (weights 1/12, 5/12, 5/12, 1/12).
-//   eta4: eta at the four points;  bd: bottom data as in source_cell;  bLm: right-edge bottom of
+//   eta4: eta at the four points;  bd: bottom data as in source_cell_form;  bLm: right-edge bottom of
 //   cell j-1, bRp: left-edge bottom of cell j+1.
 SWALE_HD real source_cell_special(real g, real etabar, const real eta4[4], const real bd[5], const SourceGeom& sg,
                                   real bLm, real bRp) {

@@ -76,20 +76,6 @@ def flux_adjoint(e, prm, Fb):
     return eb
 
 
-def source_tangent(hd, bd, thd, tbd, geom, g):
-    S, tS = ctypes.c_double(0), ctypes.c_double(0)
-    lib().ct_source_tangent(*map(_p, (f64(hd), f64(bd), f64(thd), f64(tbd), f64(geom))), ctypes.c_double(g),
-                            ctypes.byref(S), ctypes.byref(tS))
-    return S.value, tS.value
-
-
-def source_adjoint(hd, bd, geom, g, Sb):
-    hdb, bdb = np.zeros(5), np.zeros(5)
-    lib().ct_source_adjoint(*map(_p, (f64(hd), f64(bd), f64(geom))), ctypes.c_double(g), ctypes.c_double(Sb),
-                            _p(hdb), _p(bdb))
-    return hdb, bdb
-
-
 def source_form_tangent(hd, bd, thd, tbd, w3, g):
     S, tS = ctypes.c_double(0), ctypes.c_double(0)
     lib().ct_source_form_tangent(*map(_p, (f64(hd), f64(bd), f64(thd), f64(tbd), f64(w3))), ctypes.c_double(g),
@@ -98,11 +84,11 @@ def source_form_tangent(hd, bd, thd, tbd, w3, g):
 
 
 def source_form_adjoint(hd, bd, w3, g, Sb):
-    """(hdb, bdb, S by the form, S by the monomial form)."""
-    hdb, bdb, out = np.zeros(5), np.zeros(5), np.zeros(2)
+    """(hdb, bdb, S) of the antisymmetric source form."""
+    hdb, bdb, out = np.zeros(5), np.zeros(5), np.zeros(1)
     arrs = [f64(x) for x in (hd, bd, w3)]
     lib().ct_source_form_adjoint(*map(_p, arrs), ctypes.c_double(g), ctypes.c_double(Sb), _p(hdb), _p(bdb), _p(out))
-    return hdb, bdb, out[0], out[1]
+    return hdb, bdb, out[0]
 
 
 def smooth_test(w5, dx, D2h, D2m, it, eps=1e-6):

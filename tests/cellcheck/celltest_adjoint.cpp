@@ -44,15 +44,8 @@ void ct_flux_adjoint(const double* e, const double* prm, const double* Fb, doubl
   for (int k = 0; k < 8; ++k) eb[k] = o[k];
 }
 
-void ct_source_adjoint(const double* hd, const double* bd, const double* geom, double g, double Sb, double* hdb,
-                       double* bdb) {
-  swale::SourceGeom sg{geom[0], geom[1], geom[2], geom[3], geom[4], geom[5]};
-  for (int k = 0; k < 5; ++k) hdb[k] = bdb[k] = 0.0;
-  swale::source_cell_rev(g, hd, bd, sg, Sb, hdb, bdb);
-}
-
 // Reverse of the antisymmetric source form from the widths w3 = (J_{j-1}, J_j, J_{j+1}); out[0] =
-// the source by the form, out[1] = by the monomial form (source_cell), for value checks.
+// the source value.
 void ct_source_form_adjoint(const double* hd, const double* bd, const double* w3, double g, double Sb, double* hdb,
                             double* bdb, double* out) {
   const double Jm = w3[0], Jc = w3[1], Jp = w3[2];
@@ -60,10 +53,7 @@ void ct_source_form_adjoint(const double* hd, const double* bd, const double* w3
                                                  1.0 / (Jc + Jp), 1.0 / (Jm + Jc + Jp));
   for (int k = 0; k < 5; ++k) hdb[k] = bdb[k] = 0.0;
   swale::source_cell_form_rev(g, hd, bd, f, Sb, hdb, bdb);
-  const swale::SourceGeom sg = swale::source_geom(Jm, Jc, 1.0 / Jm, 1.0 / Jc, 1.0 / Jp, 1.0 / (Jm + Jc),
-                                                  1.0 / (Jc + Jp), 1.0 / (Jm + Jc + Jp));
   out[0] = swale::source_cell_form(g, hd, bd, f);
-  out[1] = swale::source_cell(g, hd, bd, sg);
 }
 
 // f32_trunc on the host (the device's double -> float conversion on the integer pipe).

@@ -1,5 +1,5 @@
 // Host build of the per-cell arithmetic on a forward-mode dual scalar: tangents of
-// recon_cell, interface_flux and source_cell for the dot-product checks of their hand-written
+// recon_cell, interface_flux and source_cell_form for the dot-product checks of their hand-written
 // reverse sweeps (swale_adjoint.cuh). Test tooling.
 #include <cmath>
 #include <cstdint>
@@ -104,21 +104,7 @@ void ct_flux_tangent(const double* e, const double* te, const double* prm, doubl
   }
 }
 
-// in: hd[5], bd[5], thd[5], tbd[5]; geom[6] = (rm, irm, irp, i1m, i1p, i1mp); g. out: S, tS.
-void ct_source_tangent(const double* hd, const double* bd, const double* thd, const double* tbd, const double* geom,
-                       double g, double* S, double* tS) {
-  D a[5], b[5];
-  for (int k = 0; k < 5; ++k) {
-    a[k] = D(hd[k], thd[k]);
-    b[k] = D(bd[k], tbd[k]);
-  }
-  swale::SourceGeom sg{D(geom[0]), D(geom[1]), D(geom[2]), D(geom[3]), D(geom[4]), D(geom[5])};
-  const D s = swale::source_cell(D(g), a, b, sg);
-  *S = s.v;
-  *tS = s.d;
-}
-
-// The antisymmetric form of the same source (source_form, source_cell_form) from the widths
+// The source term as the antisymmetric form (source_form, source_cell_form) from the widths
 // w3 = (J_{j-1}, J_j, J_{j+1}). out: S, tS (tangent).
 void ct_source_form_tangent(const double* hd, const double* bd, const double* thd, const double* tbd, const double* w3,
                             double g, double* S, double* tS) {
