@@ -173,7 +173,8 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
 
 // Counts of the reverse sweep of one stage over cells [c0, c1) of one stage state (the same
 // stencils as opc_count_stage), with unit adjoint seeds. out[0]: reverse reconstruction per
-// cell (recon_cell_rev, the cell's own pair and triple terms recomputed, and the scatter of the
+// cell (recon_cell_rev_lin for a smooth-class cell, from the linear form the forward recompute
+// stored, else recon_cell_rev; the cell's own pair and triple terms recomputed, and the scatter of the
 // divided-difference adjoints to the five stencil cells); out[1]: reverse source per cell
 // (source_form with the cell's reciprocal width, the depth data, source_cell_form_rev); out[2]:
 // reverse flux per interface (interface_flux_rev). FLOPs: add + mul + div + sqrt, summed.
@@ -215,6 +216,11 @@ void opc_count_reverse(int64_t N, const double* E, const double* M, const double
     uint32_t st = 0;
     const CD it3[3] = {it[1], it[2], it[3]};
     swale::recon_cell(P, h5, it3, v0, DD, CD(dxmax), o, flag, st);
+    // The smooth class's linear form as the forward recompute stores it (not counted here).
+    swale::CellGeom Gk;
+    uint32_t stk = 0;
+    swale::cell_geom(h5, CD(dxmax), Gk, stk, false);
+    swale::smooth_edge_coeffs(h5, it3, Gk);
     // Reverse reconstruction.
     opc::C = opc::Counts();
     const CD ipc = swale::pair_recip(Jv[3], Jv[4]);
@@ -224,11 +230,14 @@ void opc_count_reverse(int64_t N, const double* E, const double* M, const double
     const swale::EdgeAdj ob = {CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0)};
     CD v0b[3][3];
     swale::StencilDD DDb;
-    swale::recon_cell_rev(P, h5, it3, v0, DD, CD(dxmax), ob, v0b, DDb);
+    // A smooth-class cell reverses from the stored linear form (the kernel's path where its FP32
+    // test shows the class), the others recompute the geometry and the weights.
+    if (flag == 0) swale::recon_cell_rev_lin(P, Gk.K, v0, DD, ob, v0b, DDb);
+    else swale::recon_cell_rev(P, h5, it3, v0, DD, CD(dxmax), ob, v0b, DDb);
     for (int v = 0; v < 3; ++v) {  // the kernel's scatter through D3 = (D2' - D2) it, D2 = (v' - v) ip
       CD cv[5], d2b[4];
       for (int a = 0; a < 4; ++a) d2b[a] = DDb.D2[v][a];
-      for (int a = 0; a < 3; ++a) {
+      for (int a = 0; a < 3 && flag != 0; ++a) {  // DDb.D3 is 0 in the smooth class
         const CD x = DDb.D3[v][a] * it[a + 1];
         d2b[a + 1] = d2b[a + 1] + x;
         d2b[a] = d2b[a] - x;

@@ -375,6 +375,12 @@ void launch_recon(const StepConst& K, const DevState& D, int T, unsigned grid, c
     else k_recon<STAGE, 128, 2><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
     return;
   }
+  if (D.gK) {  // the adjoint's recomputes: also store the smooth-class linear form
+    if (T == 64) k_recon<STAGE, 64, 0, false, true><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
+    else if (T == 256) k_recon<STAGE, 256, 0, false, true><<<grid, 256, 0, s>>>(K, D, E, M, B, J);
+    else k_recon<STAGE, 128, 0, false, true><<<grid, 128, 0, s>>>(K, D, E, M, B, J);
+    return;
+  }
   if constexpr (STAGE == 1) {
     if (D.geo) {  // stage 1 reads the cached geometry: more resident warps
       if (T == 64) k_recon<STAGE, 64, 0, true><<<grid, 64, 0, s>>>(K, D, E, M, B, J);
@@ -1255,11 +1261,13 @@ uint64_t adjoint_bytes(int64_t B, int64_t Nt, int64_t nsteps, int64_t ckpt_every
   // the other is reversed; one when a single segment covers every step.
   const uint64_t nb = nseg == 1 ? 1 : 2;
   if (tape) {
-    // per step of a segment: three stage edge sets, q^(1), J^(1), q^(2), J^(2), node velocities
-    const uint64_t slot = 30 * a(NE, 8) + 8 * a(Nt, 8) + a(NN, 8);
+    // per step of a segment: three stage edge sets with their smooth-class linear forms, q^(1),
+    // J^(1), q^(2), J^(2), node velocities
+    const uint64_t slot = 30 * a(NE, 8) + 3 * a(8 * (uint64_t)NE, 8) + 8 * a(Nt, 8) + a(NN, 8);
     return common + (uint64_t)(nseg + nb * C + 1) * copy + (uint64_t)(nb * C) * slot;
   }
-  return common + state_set + 40 * a(NE, 8) + (uint64_t)(nseg + nb * C + 3) * copy;
+  // two state sets of the step recompute: four further stage edge sets and six linear forms
+  return common + state_set + 40 * a(NE, 8) + 6 * a(8 * (uint64_t)NE, 8) + (uint64_t)(nseg + nb * C + 3) * copy;
 }
 
 }  // namespace
@@ -1459,6 +1467,9 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     for (int k = 0; k < 2; ++k) {
       Ds[k][0] = Ds[k][1] = Ds[k][2] = R[k];
       for (int t = 0; t < 2; ++t) alloc_edges(Ds[k][t]);
+      // each stage's smooth-class linear form, for the reverse reconstruction of that stage
+      for (int t = 0; t < 3; ++t)
+        if (!s) s = carve(&Ds[k][t].gK, (size_t)8 * NE);
     }
   }
   // Segment recomputes: a third state set D2 recomputes segment sg - 1 into one of two
@@ -1491,6 +1502,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
         for (int t = 0; t < 3; ++t) {
           slot[b][3 * i + t] = base_i;
           alloc_edges(slot[b][3 * i + t]);
+          if (!s) s = carve(&slot[b][3 * i + t].gK, (size_t)8 * NE);
         }
       }
     }

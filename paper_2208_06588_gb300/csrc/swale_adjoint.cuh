@@ -104,6 +104,102 @@ SWALE_HD void source_cell_form_rev(real g, const real hd[5], const real bd[5], c
   bdb[1] = bdb[1] - ab * ((v[0] + v[1]) + (v[2] + v[3]));
 }
 
+// The limiter of recon_cell (Eq. modifiedhjn, xd in 1D), forward and reverse, for the edge values
+// ev[v][e] of (eta, hu, h) and the cell averages v0[v][2]: from the adjoints ob of the limited
+// edge state, the adjoints evb of the edge values, and the adjoints of the cell's own averages of
+// eta, hu and h added to v0b[v][2]. Shared by recon_cell_rev and recon_cell_rev_lin.
+SWALE_HD void limit_cell_rev(const SchemeConst& P, const real ev[3][2], const real v0[3][3], const EdgeAdj& ob,
+                             real evb[3][2], real v0b[3][3]) {
+  const real hb0 = v0[0][2] - v0[2][2];
+  const real hbar = pos0(hb0);
+  const real hL0 = ev[0][0] - ev[2][0], hR0 = ev[0][1] - ev[2][1];
+  const real delta = (12.0 * hbar - hL0 - hR0) * 0.1;
+  const bool selR1 = dlt(hR0, hL0);
+  const real m1 = selR1 ? hR0 : hL0;
+  const bool selD = dlt(delta, m1);
+  const real mn = selD ? delta : m1;
+  const bool epsSel = dlt(hbar, P.eps_pp);  // epsv = min(eps_pp, hbar) selects hbar
+  const real epsv = epsSel ? hbar : real(P.eps_pp);
+  const real mL0 = ev[1][0], mR0 = ev[1][1], mbar = v0[1][2];
+  const bool active = dlt(mn, epsv);
+  real theta = 1.0, iD = 0.0;
+  real hL = hL0, hR = hR0, mL = mL0, mR = mR0;
+  if (active) {
+    iD = recip(hbar - mn);
+    theta = (hbar - epsv) * iD;
+    hL = theta * (hL0 - hbar) + hbar;
+    hR = theta * (hR0 - hbar) + hbar;
+    if (P.limit_hu) {
+      mL = theta * (mL0 - mbar) + mbar;
+      mR = theta * (mR0 - mbar) + mbar;
+    }
+  }
+  const bool wetL = dlt(P.h_dry, hL), wetR = dlt(P.h_dry, hR);
+  for (int v = 0; v < 3; ++v)
+    for (int e = 0; e < 2; ++e) evb[v][e] = 0.0;
+  real hLb = ob.hL, hRb = ob.hR, mLb = 0.0, mRb = 0.0;
+  // EL = ev[0][0], BL = EL - hL (same on the right)
+  evb[0][0] = ob.EL + ob.BL;
+  hLb = hLb - ob.BL;
+  evb[0][1] = ob.ER + ob.BR;
+  hRb = hRb - ob.BR;
+  // u = m / h on wet edges
+  if (wetL) {
+    const real iL = recip(hL);
+    mLb = mLb + ob.uL * iL;
+    hLb = hLb - ob.uL * mL * iL * iL;
+  }
+  if (wetR) {
+    const real iR = recip(hR);
+    mRb = mRb + ob.uR * iR;
+    hRb = hRb - ob.uR * mR * iR * iR;
+  }
+  real hbarb = 0.0, mbarb = 0.0, hL0b, hR0b, mL0b, mR0b;
+  if (active) {
+    real thetab = hLb * (hL0 - hbar) + hRb * (hR0 - hbar);
+    hL0b = theta * hLb;
+    hR0b = theta * hRb;
+    hbarb = (1.0 - theta) * (hLb + hRb);
+    if (P.limit_hu) {
+      thetab = thetab + mLb * (mL0 - mbar) + mRb * (mR0 - mbar);
+      mL0b = theta * mLb;
+      mR0b = theta * mRb;
+      mbarb = (1.0 - theta) * (mLb + mRb);
+    } else {
+      mL0b = mLb;
+      mR0b = mRb;
+    }
+    // theta = (hbar - epsv) / (hbar - mn)
+    hbarb = hbarb + thetab * (1.0 - theta) * iD;
+    const real epsvb = -thetab * iD;
+    const real mnb = thetab * theta * iD;
+    if (epsSel) hbarb = hbarb + epsvb;
+    real deltab = 0.0;
+    if (selD) deltab = mnb;
+    else if (selR1) hR0b = hR0b + mnb;
+    else hL0b = hL0b + mnb;
+    hbarb = hbarb + 1.2 * deltab;
+    hL0b = hL0b - 0.1 * deltab;
+    hR0b = hR0b - 0.1 * deltab;
+  } else {
+    hL0b = hLb;
+    hR0b = hRb;
+    mL0b = mLb;
+    mR0b = mRb;
+  }
+  evb[0][0] = evb[0][0] + hL0b;
+  evb[2][0] = evb[2][0] - hL0b;
+  evb[1][0] = evb[1][0] + mL0b;
+  evb[0][1] = evb[0][1] + hR0b;
+  evb[2][1] = evb[2][1] - hR0b;
+  evb[1][1] = evb[1][1] + mR0b;
+  if (!(hb0 < 0.0)) {
+    v0b[0][2] = v0b[0][2] + hbarb;
+    v0b[2][2] = v0b[2][2] - hbarb;
+  }
+  v0b[1][2] = v0b[1][2] + mbarb;
+}
+
 // Adjoint of recon_cell: from the adjoints ob of the limited edge state of cell j, the adjoints
 // of the data it read: v0b[v][a] (averages of cells j-2+a) and DDb (divided differences).
 //   it[3]: reciprocal sums of the triples starting at cells j-2, j-1, j (smooth-class form).
@@ -215,31 +311,6 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real i
         ev[v][ee] = s;
       }
   }
-  const real hb0 = v0[0][2] - v0[2][2];
-  const real hbar = pos0(hb0);
-  const real hL0 = ev[0][0] - ev[2][0], hR0 = ev[0][1] - ev[2][1];
-  const real delta = (12.0 * hbar - hL0 - hR0) * 0.1;
-  const bool selR1 = dlt(hR0, hL0);
-  const real m1 = selR1 ? hR0 : hL0;
-  const bool selD = dlt(delta, m1);
-  const real mn = selD ? delta : m1;
-  const bool epsSel = dlt(hbar, P.eps_pp);  // epsv = min(eps_pp, hbar) selects hbar
-  const real epsv = epsSel ? hbar : real(P.eps_pp);
-  const real mL0 = ev[1][0], mR0 = ev[1][1], mbar = v0[1][2];
-  const bool active = dlt(mn, epsv);
-  real theta = 1.0, iD = 0.0;
-  real hL = hL0, hR = hR0, mL = mL0, mR = mR0;
-  if (active) {
-    iD = recip(hbar - mn);
-    theta = (hbar - epsv) * iD;
-    hL = theta * (hL0 - hbar) + hbar;
-    hR = theta * (hR0 - hbar) + hbar;
-    if (P.limit_hu) {
-      mL = theta * (mL0 - mbar) + mbar;
-      mR = theta * (mR0 - mbar) + mbar;
-    }
-  }
-  const bool wetL = dlt(P.h_dry, hL), wetR = dlt(P.h_dry, hR);
   // ---------------- reverse sweep ----------------
   for (int v = 0; v < 3; ++v)
     for (int a = 0; a < 3; ++a) v0b[v][a] = 0.0;
@@ -247,68 +318,8 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real i
     for (int a = 0; a < 4; ++a) DDb.D2[v][a] = 0.0;
     for (int a = 0; a < 3; ++a) DDb.D3[v][a] = 0.0;
   }
-  real evb[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-  real hLb = ob.hL, hRb = ob.hR, mLb = 0.0, mRb = 0.0;
-  // EL = ev[0][0], BL = EL - hL (same on the right)
-  evb[0][0] = ob.EL + ob.BL;
-  hLb = hLb - ob.BL;
-  evb[0][1] = ob.ER + ob.BR;
-  hRb = hRb - ob.BR;
-  // u = m / h on wet edges
-  if (wetL) {
-    const real iL = recip(hL);
-    mLb = mLb + ob.uL * iL;
-    hLb = hLb - ob.uL * mL * iL * iL;
-  }
-  if (wetR) {
-    const real iR = recip(hR);
-    mRb = mRb + ob.uR * iR;
-    hRb = hRb - ob.uR * mR * iR * iR;
-  }
-  real hbarb = 0.0, mbarb = 0.0, hL0b, hR0b, mL0b, mR0b;
-  if (active) {
-    real thetab = hLb * (hL0 - hbar) + hRb * (hR0 - hbar);
-    hL0b = theta * hLb;
-    hR0b = theta * hRb;
-    hbarb = (1.0 - theta) * (hLb + hRb);
-    if (P.limit_hu) {
-      thetab = thetab + mLb * (mL0 - mbar) + mRb * (mR0 - mbar);
-      mL0b = theta * mLb;
-      mR0b = theta * mRb;
-      mbarb = (1.0 - theta) * (mLb + mRb);
-    } else {
-      mL0b = mLb;
-      mR0b = mRb;
-    }
-    // theta = (hbar - epsv) / (hbar - mn)
-    hbarb = hbarb + thetab * (1.0 - theta) * iD;
-    const real epsvb = -thetab * iD;
-    const real mnb = thetab * theta * iD;
-    if (epsSel) hbarb = hbarb + epsvb;
-    real deltab = 0.0;
-    if (selD) deltab = mnb;
-    else if (selR1) hR0b = hR0b + mnb;
-    else hL0b = hL0b + mnb;
-    hbarb = hbarb + 1.2 * deltab;
-    hL0b = hL0b - 0.1 * deltab;
-    hR0b = hR0b - 0.1 * deltab;
-  } else {
-    hL0b = hLb;
-    hR0b = hRb;
-    mL0b = mLb;
-    mR0b = mRb;
-  }
-  evb[0][0] = evb[0][0] + hL0b;
-  evb[2][0] = evb[2][0] - hL0b;
-  evb[1][0] = evb[1][0] + mL0b;
-  evb[0][1] = evb[0][1] + hR0b;
-  evb[2][1] = evb[2][1] - hR0b;
-  evb[1][1] = evb[1][1] + mR0b;
-  if (!(hb0 < 0.0)) {
-    v0b[0][2] = v0b[0][2] + hbarb;
-    v0b[2][2] = v0b[2][2] - hbarb;
-  }
-  v0b[1][2] = v0b[1][2] + mbarb;
+  real evb[3][2];
+  limit_cell_rev(P, ev, v0, ob, evb, v0b);
   if (flag == 0) {  // ev[v][e] = v0[v][2] + sum_m K[e][m] D2[v][m]; K depends on the mesh only
     for (int v = 0; v < 3; ++v)
       for (int ee = 0; ee < 2; ++ee) {
@@ -382,6 +393,31 @@ SWALE_HD void recon_cell_rev(const SchemeConst& P, const real h[5], const real i
     DDb.D3[0][a] = DDb.D3[0][a] + d3hb;
     DDb.D3[2][a] = DDb.D3[2][a] - d3hb;
   }
+}
+
+// recon_cell_rev for a cell of the smooth class whose linear form K (smooth_edge_coeffs) the
+// forward recompute stored: the edge values v_j + sum_m K[e][m] D2[m] are formed from it, so the
+// mesh geometry is not recomputed; the same reverse as recon_cell_rev with known_smooth.
+SWALE_HD void recon_cell_rev_lin(const SchemeConst& P, const real Kf[2][4], const real v0[3][3], const StencilDD& DD,
+                                 const EdgeAdj& ob, real v0b[3][3], StencilDD& DDb) {
+  real ev[3][2];
+  for (int v = 0; v < 3; ++v)
+    for (int ee = 0; ee < 2; ++ee)
+      ev[v][ee] = v0[v][2] + Kf[ee][0] * DD.D2[v][0] + Kf[ee][1] * DD.D2[v][1] + Kf[ee][2] * DD.D2[v][2] +
+                  Kf[ee][3] * DD.D2[v][3];
+  for (int v = 0; v < 3; ++v)
+    for (int a = 0; a < 3; ++a) v0b[v][a] = 0.0;
+  for (int v = 0; v < 3; ++v) {
+    for (int a = 0; a < 4; ++a) DDb.D2[v][a] = 0.0;
+    for (int a = 0; a < 3; ++a) DDb.D3[v][a] = 0.0;
+  }
+  real evb[3][2];
+  limit_cell_rev(P, ev, v0, ob, evb, v0b);
+  for (int v = 0; v < 3; ++v)
+    for (int ee = 0; ee < 2; ++ee) {
+      v0b[v][2] = v0b[v][2] + evb[v][ee];
+      for (int m = 0; m < 4; ++m) DDb.D2[v][m] = DDb.D2[v][m] + Kf[ee][m] * evb[v][ee];
+    }
 }
 
 }  // namespace swale

@@ -313,7 +313,14 @@ __global__ void __launch_bounds__(T, 512 / T) k_adj_recon(StepConst K, DevState 
     const bool smooth32 =
         swale::sure_smooth_f32(F32, c4f, c3f, d2h, d2m, itf, swale::f32_trunc(K.sc.eps_weno));
     if (smooth32) {
-      swale::recon_cell_rev(K.sc, h, it3, v0, DD, dxmax, ob, v0b, DDb, true);
+      if (D.gK) {  // the linear form the forward recompute stored for this stage
+        double Kf[2][4];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) Kf[k >> 2][k & 3] = D.gK[k * D.geo_stride + idx];
+        swale::recon_cell_rev_lin(K.sc, Kf, v0, DD, ob, v0b, DDb);
+      } else {
+        swale::recon_cell_rev(K.sc, h, it3, v0, DD, dxmax, ob, v0b, DDb, true);
+      }
     } else {
       AdjOpenIn in;
       in.DD = DD;

@@ -140,6 +140,10 @@ struct DevState {
   // Geometry cache: SWALE_GEOM_VALUES arrays in the edge layout, geo[k * geo_stride + idx].
   double* geo;
   int64_t geo_stride;
+  // The smooth class's linear form K[2][4] of each cell on the stage mesh (8 arrays in the edge
+  // layout, gK[k * geo_stride + idx]), stored by the hydrostatic reconstruction when set: the
+  // adjoint's recomputes, whose reverse reconstruction reads it instead of the mesh geometry.
+  double* gK;
   uint8_t* flags;              // stage-1 classes, edge layout
   InstConst* IC;
   DevScalars* S;
@@ -509,7 +513,10 @@ __device__ __noinline__ OpenOut recon_open_cell(const SchemeConst P, OpenCell c,
 // every instantiation that computes the geometry itself spills heavily under that bound. The
 // other well-balanced instantiations take 768 threads (6 blocks of 128, 80 registers, a few
 // spilled doubles; 1.2 % faster per step than 4 blocks of 128 registers), the other schemes 512.
-template <int STAGE, int T, int SCHEME = 0, bool HIOCC = false>
+// STOREK: an instantiation of the hydrostatic scheme that also stores each cell's smooth-class
+// linear form in D.gK (the adjoint's recomputes), so that the forward's own instantiations keep
+// their registers.
+template <int STAGE, int T, int SCHEME = 0, bool HIOCC = false, bool STOREK = false>
 __global__ void __launch_bounds__(T, (HIOCC ? 1024 : (SCHEME == 0 ? 768 : 512)) / T) k_recon(StepConst K, DevState D, const double* __restrict__ Eg,
                                              const double* __restrict__ Mg, const double* __restrict__ Bg,
                                              const double* __restrict__ Jg) {
@@ -692,6 +699,10 @@ __global__ void __launch_bounds__(T, (HIOCC ? 1024 : (SCHEME == 0 ? 768 : 512)) 
 #pragma unroll
         for (int k = 0; k < kGeo; ++k)
           if (k < kF0 || k >= kF1) D.geo[k * D.geo_stride + idx] = gv[k];
+      }
+      if (STOREK && SCHEME == 0) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) D.gK[k * D.geo_stride + idx] = G.K[k >> 2][k & 3];
       }
       EdgeState o;
       uint8_t flag;

@@ -64,6 +64,14 @@ def recon_adjoint(h, v0, D2, D3, prm, ob, known_smooth=False):
     return v0b, D2b, D3b
 
 
+def recon_adjoint_lin(h, v0, D2, prm, ob):
+    """Reverse sweep of a smooth-class cell from the forward's stored linear form."""
+    v0b, D2b, D3b = np.zeros(9), np.zeros(12), np.zeros(9)
+    args = [f64(x) for x in (h, v0, D2, prm, ob)]
+    lib().ct_recon_adjoint_lin(*map(_p, args), _p(v0b), _p(D2b), _p(D3b))
+    return v0b, D2b, D3b
+
+
 def flux_tangent(e, te, prm):
     F, tF = np.zeros(4), np.zeros(4)
     lib().ct_flux_tangent(*map(_p, (f64(e), f64(te), f64(prm))), _p(F), _p(tF))

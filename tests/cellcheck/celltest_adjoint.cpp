@@ -36,6 +36,33 @@ void ct_recon_adjoint(const double* h, const double* v0, const double* D2, const
   ct_recon_adjoint_k(h, v0, D2, D3, prm, ob, 0, v0b, D2b, D3b);
 }
 
+// recon_cell_rev_lin with the linear form K that the forward's own geometry gives (cell_geom,
+// smooth_edge_coeffs, as the reconstruction kernel stores it): v0b[9], D2b[12], D3b[9].
+void ct_recon_adjoint_lin(const double* h, const double* v0, const double* D2, const double* prm, const double* ob,
+                          double* v0b, double* D2b, double* D3b) {
+  swale::SchemeConst P{prm[0], prm[1], prm[2], prm[3], 1, (int32_t)prm[5]};
+  swale::CellGeom G;
+  uint32_t st = 0;
+  swale::cell_geom(h, prm[4], G, st, false);
+  const double it3[3] = {1.0 / (h[0] + h[1] + h[2]), 1.0 / (h[1] + h[2] + h[3]), 1.0 / (h[2] + h[3] + h[4])};
+  swale::smooth_edge_coeffs(h, it3, G);
+  double vv[3][3];
+  swale::StencilDD DD, DDb;
+  for (int v = 0; v < 3; ++v) {
+    for (int a = 0; a < 3; ++a) vv[v][a] = v0[v * 3 + a];
+    for (int a = 0; a < 4; ++a) DD.D2[v][a] = D2[v * 4 + a];
+    for (int a = 0; a < 3; ++a) DD.D3[v][a] = 0.0;
+  }
+  swale::EdgeAdj a{ob[0], ob[1], ob[2], ob[3], ob[4], ob[5], ob[6], ob[7]};
+  double vb[3][3];
+  swale::recon_cell_rev_lin(P, G.K, vv, DD, a, vb, DDb);
+  for (int v = 0; v < 3; ++v) {
+    for (int k = 0; k < 3; ++k) v0b[v * 3 + k] = vb[v][k];
+    for (int k = 0; k < 4; ++k) D2b[v * 4 + k] = DDb.D2[v][k];
+    for (int k = 0; k < 3; ++k) D3b[v * 3 + k] = DDb.D3[v][k];
+  }
+}
+
 void ct_flux_adjoint(const double* e, const double* prm, const double* Fb, double* eb) {
   swale::Flux f{Fb[0], Fb[1], Fb[2], Fb[3]};
   const swale::EdgeAdj a = swale::interface_flux_rev(prm[0], prm[1], prm[2], e[0], e[1], e[2], e[3], e[4], e[5], e[6],

@@ -87,6 +87,35 @@ def test_recon_reverse_known_smooth_is_the_same_sweep(limit_hu):
     assert n0 >= 10
 
 
+@pytest.mark.parametrize("limit_hu", [0, 1])
+def test_recon_reverse_from_the_stored_linear_form(limit_hu):
+    """The reverse reconstruction of a smooth-class cell from the linear form that the forward's
+    own geometry gives (the form the forward recompute of the adjoint stores) is the reverse sweep
+    that recomputes the geometry, to rounding, and so the transpose of the forward's tangent."""
+    n0 = 0
+    for case in range(60):
+        h, E, M, B = cases()[case]
+        v0, D2, D3 = stencil(E, M, B, h)
+        prm = PRM.copy()
+        prm[4] = 0.015
+        prm[5] = limit_hu
+        tv0, tD2 = RNG.normal(size=9), RNG.normal(size=12)
+        val, tan, flag = C.recon_tangent(h, v0, D2, D3, tv0, tD2, np.zeros(9), prm)
+        if flag != 0:
+            continue
+        n0 += 1
+        ob = RNG.normal(size=8)
+        known = C.recon_adjoint(h, v0, D2, D3, prm, ob, known_smooth=True)
+        lin = C.recon_adjoint_lin(h, v0, D2, prm, ob)
+        for a, b in zip(known, lin):
+            assert np.allclose(a, b, rtol=1e-13, atol=1e-13 * (np.abs(a).max() + 1e-300)), (case, a, b)
+        assert not lin[2].any()
+        v0b, D2b, _ = lin
+        lhs, rhs = ob @ tan, v0b @ tv0 + D2b @ tD2
+        assert abs(lhs - rhs) <= 1e-12 * (np.abs(ob * tan).sum() + np.abs(v0b * tv0).sum() + np.abs(D2b * tD2).sum())
+    assert n0 >= 10
+
+
 def test_recon_cases_cover_every_class():
     flags = set()
     for h, E, M, B in cases():
