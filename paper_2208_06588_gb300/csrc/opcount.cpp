@@ -226,7 +226,8 @@ void opc_count_reverse(int64_t N, const double* E, const double* M, const double
     const CD ipc = swale::pair_recip(Jv[3], Jv[4]);
     for (int v = 0; v < 3; ++v) (void)swale::pair_dd(V[v][3], V[v][4], ipc);
     const CD itc = swale::triple_recip(Jv[2], Jv[3], Jv[4]);
-    for (int v = 0; v < 3; ++v) (void)swale::triple_dd(d2[v][2], d2[v][3], itc);
+    if (flag != 0)  // the third differences only where the class is open
+      for (int v = 0; v < 3; ++v) (void)swale::triple_dd(d2[v][2], d2[v][3], itc);
     const swale::EdgeAdj ob = {CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0), CD(1.0)};
     CD v0b[3][3];
     swale::StencilDD DDb;

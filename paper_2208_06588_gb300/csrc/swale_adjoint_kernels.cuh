@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(T, 512 / T) k_adj_recon(StepConst K, DevState 
                                                  const double* __restrict__ Jg) {
   __shared__ double sJ[T + 4], sV[3][T + 4];
   __shared__ double sIP[T + 3], sD2[3][T + 3];
-  __shared__ double sIT[T + 2], sD3[3][T + 2];
+  __shared__ double sIT[T + 2];
   // FP32 copies for the smooth-class test of the forward: pair differences of hu and of the
   // depth (eta's minus the bottom's), triple reciprocals.
   __shared__ float sD2f[2][T + 3], sITf[T + 2];
@@ -274,8 +274,6 @@ __global__ void __launch_bounds__(T, 512 / T) k_adj_recon(StepConst K, DevState 
       const double it = swale::triple_recip(sJ[i], sJ[i + 1], sJ[i + 2]);
       sIT[i] = it;
       sITf[i] = swale::f32_trunc(it);
-#pragma unroll
-      for (int v = 0; v < 3; ++v) sD3[v][i] = swale::triple_dd(sD2[v][i], sD2[v][i + 1], it);
     }
     __syncthreads();
     const int64_t c = c0 + tid;
@@ -290,8 +288,6 @@ __global__ void __launch_bounds__(T, 512 / T) k_adj_recon(StepConst K, DevState 
       for (int a = 0; a < 3; ++a) v0[v][a] = sV[v][tid + a];
 #pragma unroll
       for (int a = 0; a < 4; ++a) DD.D2[v][a] = sD2[v][tid + a];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) DD.D3[v][a] = sD3[v][tid + a];
     }
     const int64_t idx = eb + c + 1;
     const swale::EdgeAdj ob = {A.ab[0][idx], A.ab[1][idx], A.ab[2][idx], A.ab[3][idx],
@@ -322,6 +318,11 @@ __global__ void __launch_bounds__(T, 512 / T) k_adj_recon(StepConst K, DevState 
         swale::recon_cell_rev(K.sc, h, it3, v0, DD, dxmax, ob, v0b, DDb, true);
       }
     } else {
+      // The third differences, only where the class is open (the smooth class needs none).
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) DD.D3[v][a] = swale::triple_dd(DD.D2[v][a], DD.D2[v][a + 1], it3[a]);
       AdjOpenIn in;
       in.DD = DD;
       in.ob = ob;
