@@ -176,7 +176,7 @@ void opc_count_stage(int64_t N, const double* E, const double* M, const double* 
 // cell (recon_cell_rev_lin for a smooth-class cell, from the linear form the forward recompute
 // stored, else recon_cell_rev; the cell's own pair and triple terms recomputed, and the scatter of the
 // divided-difference adjoints to the five stencil cells); out[1]: reverse source per cell
-// (source_form with the cell's reciprocal width, the depth data, source_cell_form_rev); out[2]:
+// (the depth data and source_cell_form_rev on the stored form entries); out[2]:
 // reverse flux per interface (interface_flux_rev). FLOPs: add + mul + div + sqrt, summed.
 void opc_count_reverse(int64_t N, const double* E, const double* M, const double* B, const double* J, int32_t bc,
                        double g, double eps_weno, double eps_pp, double h_dry, double alpha, int64_t c0, int64_t c1,
@@ -250,11 +250,10 @@ void opc_count_reverse(int64_t N, const double* E, const double* M, const double
       }
     }
     rrec += flops();
-    // Reverse source.
+    // Reverse source, from the form entries the forward recompute stored (not counted here).
+    const swale::SourceForm sf = swale::source_form(Jv[2], Jv[3], Jv[4], CD(1.0 / Jv[2].v), CD(1.0 / Jv[3].v),
+                                                    CD(1.0 / Jv[4].v), ip[2], ip[3], it[2]);
     opc::C = opc::Counts();
-    const CD iJc = CD(1.0) / Jv[3];
-    const swale::SourceForm sf =
-        swale::source_form(Jv[2], Jv[3], Jv[4], CD(1.0 / Jv[2].v), iJc, CD(1.0 / Jv[4].v), ip[2], ip[3], it[2]);
     const CD hd[5] = {V[0][2].v - V[2][2].v, V[0][3] - V[2][3], V[0][4].v - V[2][4].v, o.hL, o.hR};
     const CD bd[5] = {V[2][2], V[2][3], V[2][4], o.BL, o.BR};
     CD hdb[5] = {}, bdb[5] = {};

@@ -397,6 +397,13 @@ void launch_recon(const StepConst& K, const DevState& D, int T, unsigned grid, c
 template <int STAGE, int MODE>
 void launch_update(const StepConst& K, const DevState& D, int T, unsigned grid, cudaStream_t s, const double* E,
                    const double* M, const double* B, const double* J, RhsOut ro) {
+  if (MODE == 0 && K.scheme == SWALE_SCHEME_HYDROSTATIC && K.bot_pieces == 0 && D.gK) {
+    // the adjoint's recomputes: also store the source form's entries
+    if (T == 64) k_update<STAGE, MODE, 64, true, true><<<grid, 64, 0, s>>>(K, D, E, M, B, J, ro);
+    else if (T == 256) k_update<STAGE, MODE, 256, true, true><<<grid, 256, 0, s>>>(K, D, E, M, B, J, ro);
+    else k_update<STAGE, MODE, 128, true, true><<<grid, 128, 0, s>>>(K, D, E, M, B, J, ro);
+    return;
+  }
   if (MODE == 0 && K.scheme == SWALE_SCHEME_HYDROSTATIC && K.bot_pieces == 0) {
     if (T == 64) k_update<STAGE, MODE, 64, true><<<grid, 64, 0, s>>>(K, D, E, M, B, J, ro);
     else if (T == 256) k_update<STAGE, MODE, 256, true><<<grid, 256, 0, s>>>(K, D, E, M, B, J, ro);
@@ -1261,13 +1268,13 @@ uint64_t adjoint_bytes(int64_t B, int64_t Nt, int64_t nsteps, int64_t ckpt_every
   // the other is reversed; one when a single segment covers every step.
   const uint64_t nb = nseg == 1 ? 1 : 2;
   if (tape) {
-    // per step of a segment: three stage edge sets with their smooth-class linear forms, q^(1),
-    // J^(1), q^(2), J^(2), node velocities
-    const uint64_t slot = 30 * a(NE, 8) + 3 * a(8 * (uint64_t)NE, 8) + 8 * a(Nt, 8) + a(NN, 8);
+    // per step of a segment: three stage edge sets with their smooth-class linear and source
+    // forms, q^(1), J^(1), q^(2), J^(2), node velocities
+    const uint64_t slot = 30 * a(NE, 8) + 3 * a(14 * (uint64_t)NE, 8) + 8 * a(Nt, 8) + a(NN, 8);
     return common + (uint64_t)(nseg + nb * C + 1) * copy + (uint64_t)(nb * C) * slot;
   }
-  // two state sets of the step recompute: four further stage edge sets and six linear forms
-  return common + state_set + 40 * a(NE, 8) + 6 * a(8 * (uint64_t)NE, 8) + (uint64_t)(nseg + nb * C + 3) * copy;
+  // two state sets of the step recompute: four further stage edge sets and six sets of forms
+  return common + state_set + 40 * a(NE, 8) + 6 * a(14 * (uint64_t)NE, 8) + (uint64_t)(nseg + nb * C + 3) * copy;
 }
 
 }  // namespace
@@ -1467,9 +1474,9 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
     for (int k = 0; k < 2; ++k) {
       Ds[k][0] = Ds[k][1] = Ds[k][2] = R[k];
       for (int t = 0; t < 2; ++t) alloc_edges(Ds[k][t]);
-      // each stage's smooth-class linear form, for the reverse reconstruction of that stage
+      // each stage's smooth-class linear form and source form, for that stage's reverse kernels
       for (int t = 0; t < 3; ++t)
-        if (!s) s = carve(&Ds[k][t].gK, (size_t)8 * NE);
+        if (!s) s = carve(&Ds[k][t].gK, (size_t)14 * NE);
     }
   }
   // Segment recomputes: a third state set D2 recomputes segment sg - 1 into one of two
@@ -1502,7 +1509,7 @@ swale_status swale_adjoint(swale_ctx* ctx, int64_t nsteps, int64_t ckpt_every, i
         for (int t = 0; t < 3; ++t) {
           slot[b][3 * i + t] = base_i;
           alloc_edges(slot[b][3 * i + t]);
-          if (!s) s = carve(&slot[b][3 * i + t].gK, (size_t)8 * NE);
+          if (!s) s = carve(&slot[b][3 * i + t].gK, (size_t)14 * NE);
         }
       }
     }

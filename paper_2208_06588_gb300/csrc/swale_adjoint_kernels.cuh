@@ -180,9 +180,17 @@ __global__ void __launch_bounds__(T) k_adj_source(StepConst K, DevState D, AdjSt
     const double* B = Bg + cb;
     const double* Js = Jsg + cb;
     const double Jm = Js[jm], Jc = Js[j], Jp = Js[jp];
-    const swale::SourceForm sf = swale::source_form(Jm, Jc, Jp, swale::recip(Jm), swale::recip(Jc), swale::recip(Jp),
-                                                    D.ipair[eb + j], D.ipair[eb + j + 1], D.itri[eb + j + 1]);
     const int64_t ie = eb + j + 1;
+    // The source form's entries: as the forward recompute's update stored them, else computed.
+    swale::SourceForm sf;
+    if (D.gK) {
+      double* const f = reinterpret_cast<double*>(&sf);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) f[k] = D.gK[(8 + k) * D.geo_stride + ie];
+    } else {
+      sf = swale::source_form(Jm, Jc, Jp, swale::recip(Jm), swale::recip(Jc), swale::recip(Jp), D.ipair[eb + j],
+                              D.ipair[eb + j + 1], D.itri[eb + j + 1]);
+    }
     const double hd[5] = {E[jm] - B[jm], E[j] - B[j], E[jp] - B[jp], D.ehL[ie], D.ehR[ie]};
     const double bd[5] = {B[jm], B[j], B[jp], D.eBL[ie], D.eBR[ie]};
     double hdb[5] = {0, 0, 0, 0, 0}, bdb[5] = {0, 0, 0, 0, 0};

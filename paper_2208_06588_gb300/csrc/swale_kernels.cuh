@@ -140,9 +140,10 @@ struct DevState {
   // Geometry cache: SWALE_GEOM_VALUES arrays in the edge layout, geo[k * geo_stride + idx].
   double* geo;
   int64_t geo_stride;
-  // The smooth class's linear form K[2][4] of each cell on the stage mesh (8 arrays in the edge
-  // layout, gK[k * geo_stride + idx]), stored by the hydrostatic reconstruction when set: the
-  // adjoint's recomputes, whose reverse reconstruction reads it instead of the mesh geometry.
+  // Per cell of the stage mesh, 14 arrays in the edge layout (gK[k * geo_stride + idx]): the
+  // smooth class's linear form K[2][4] (k < 8), stored by the hydrostatic reconstruction, and the
+  // source term's six form entries (k = 8..13), stored by the update; set only for the adjoint's
+  // recomputes, whose reverse kernels read them instead of recomputing the mesh geometry.
   double* gK;
   uint8_t* flags;              // stage-1 classes, edge layout
   InstConst* IC;
@@ -877,8 +878,9 @@ struct RhsOut {
 };
 
 // PLAIN: an instantiation for the hydrostatic scheme without the L2-projection bottom (the
-// common case), in which the other schemes' branches are compiled out.
-template <int STAGE, int MODE, int T, bool PLAIN = false>
+// common case), in which the other schemes' branches are compiled out. STOREK: one that also
+// stores the source form's entries in D.gK (the adjoint's recomputes).
+template <int STAGE, int MODE, int T, bool PLAIN = false, bool STOREK = false>
 __global__ void __launch_bounds__(T, PLAIN ? 1024 / T : 1) k_update(StepConst K, DevState D, const double* __restrict__ Eg,
                                               const double* __restrict__ Mg, const double* __restrict__ Bg,
                                               const double* __restrict__ Jsg, RhsOut ro) {
@@ -1010,6 +1012,10 @@ __global__ void __launch_bounds__(T, PLAIN ? 1024 / T : 1) k_update(StepConst K,
         if (STAGE == 2 && MODE == 0 && D.geo) {
 #pragma unroll
           for (int k = 0; k < 6; ++k) D.geo[(SWALE_GEOM_VALUES + k) * D.geo_stride + ic_e] = src6[k];
+        }
+        if (STOREK) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) D.gK[(8 + k) * D.geo_stride + ic_e] = src6[k];
         }
         Sj = swale::source_cell_form(K.sc.g, hd, bd, sf);
       }

@@ -52,18 +52,18 @@ def test_autograd_wrapper_has_no_cpu_path():
 
 
 def test_adjoint_bytes_formula():
-    """swale_adjoint_bytes is host arithmetic: 5 (ceil(K/C) + 2 C + 3) + 165 doubles and two
+    """swale_adjoint_bytes is host arithmetic: 5 (ceil(K/C) + 2 C + 3) + 201 doubles and two
     bytes per cell, plus per-instance scalars, gauges, observations and the viscosity log, and
     up to 511 bytes per array (each is rounded up to 256 bytes and keeps 256 bytes of slack)."""
     from paper_2208_06588_gb300 import binding as B
     Nt, Bn, K, C, G = 1_000_000, 4, 4000, 64, 16
     n = B.swale_adjoint_bytes(Bn, Nt, K, C, G)
-    per_cell = 8 * (5 * (-(-K // C) + 2 * C + 3) + 165) + 2
+    per_cell = 8 * (5 * (-(-K // C) + 2 * C + 3) + 201) + 2
     assert per_cell * Nt <= n <= per_cell * Nt + 8 * (K * Bn * (G + 3)) + 2_000_000
     assert B.swale_adjoint_bytes(Bn, Nt, K, K, G) > B.swale_adjoint_bytes(Bn, Nt, K, 64, G)
-    # with the tape: (ceil(K/C) + 2 C + 1) state copies and 2 C tape slots of 63 doubles per cell
+    # with the tape: (ceil(K/C) + 2 C + 1) state copies and 2 C tape slots of 81 doubles per cell
     nt = B.swale_adjoint_bytes(Bn, Nt, K, C, G, tape=1)
-    per_cell_t = 8 * (5 * (-(-K // C) + 2 * C + 1) + 50 + 2 * C * 63) + 1
+    per_cell_t = 8 * (5 * (-(-K // C) + 2 * C + 1) + 50 + 2 * C * 81) + 1
     assert per_cell_t * Nt <= nt <= per_cell_t * Nt + 8 * (K * Bn * (G + 3)) + 4_000_000
     with pytest.raises(B.SwaleError):
         B.swale_adjoint_bytes(0, Nt, K, C, G)
