@@ -878,8 +878,10 @@ struct RhsOut {
 };
 
 // PLAIN: an instantiation for the hydrostatic scheme without the L2-projection bottom (the
-// common case), in which the other schemes' branches are compiled out. STOREK: one that also
-// stores the source form's entries in D.gK (the adjoint's recomputes).
+// common case), in which the other schemes' branches are compiled out; it is held to 64
+// registers (8 blocks of 128 threads per SM: without the bound stage 1 takes 71 and 7 blocks,
+// measured slower). STOREK: one that also stores the source form's entries in D.gK (the
+// adjoint's recomputes).
 template <int STAGE, int MODE, int T, bool PLAIN = false, bool STOREK = false>
 __global__ void __launch_bounds__(T, PLAIN ? 1024 / T : 1) k_update(StepConst K, DevState D, const double* __restrict__ Eg,
                                               const double* __restrict__ Mg, const double* __restrict__ Bg,
