@@ -338,11 +338,13 @@ swale_status swale_set_wait_test(swale_ctx* ctx, int32_t tries, uint32_t pad_byt
 
 /* Check of the reciprocal that every kernel here uses in place of a division (the paper has
  * no counterpart): y[i] = the kernels' 1 / x[i] for i < n, on the given stream (NULL: the
- * legacy default stream), asynchronous. x and y are device arrays of n doubles (they may be
- * the same array). The reciprocal is the hardware approximation refined by one third-order
- * Newton-Raphson (Householder) step; for normal, finite, non-zero x it is within one unit in
- * the last place of the correctly rounded 1 / x. Zero, infinite and subnormal x give NaN.
- * Errors: SWALE_EINVAL (n < 0, a NULL or non-device array), SWALE_ECUDA (launch). */
+ * legacy default stream; it must belong to the current device), asynchronous. x and y are
+ * arrays of n doubles on the current device (they may be the same array). The reciprocal is
+ * the hardware approximation refined by one third-order Newton-Raphson (Householder) step; for
+ * normal, finite, non-zero x it is within one unit in the last place of the correctly rounded
+ * 1 / x. Zero, infinite and subnormal x give NaN.
+ * Errors: SWALE_EINVAL (n < 0, a NULL array, or one not on the current device), SWALE_ECUDA
+ * (launch). */
 swale_status swale_check_recip(void* cuda_stream, int64_t n, const double* x, double* y);
 
 /* Message of the last error of this context ("" if none). Never NULL. */

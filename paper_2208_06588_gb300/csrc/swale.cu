@@ -1350,6 +1350,11 @@ swale_status swale_check_recip(void* cuda_stream, int64_t n, const double* x, do
     return SWALE_EINVAL;
   }
   if (ax.type != cudaMemoryTypeDevice || ay.type != cudaMemoryTypeDevice) return SWALE_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || ax.device != dev || ay.device != dev) {
+    cudaGetLastError();
+    return SWALE_EINVAL;  // the arrays must live on the current device (the stream's)
+  }
   const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
   k_check_recip<<<(unsigned)blocks, 256, 0, s>>>(x, y, n);
