@@ -142,6 +142,41 @@ def test_accuracy_problem_parity():
         assert max_rel(a, b) < 1e-11
 
 
+@pytest.mark.parametrize("scheme,table,rows", [("hydrostatic", "paper_accuracy_table.txt", (200, 400, 800)),
+                                                ("nonwb", "paper_accuracy_table_nonwb.txt", (200, 400)),
+                                                ("special", "paper_accuracy_table_special.txt", (200, 400))])
+def test_accuracy_table_rows_on_the_gpu(scheme, table, rows):
+    """The CUDA path on the accuracy test at sizes the oracle takes minutes for: its
+    self-differences |q_N - q_2N| land within 3 % of the L1 errors the paper prints in Table
+    WENO5h1D (the hydrostatic and special columns) and Table WENO5n1D (tests/golden/; the
+    oracle's own self-differences are 0.8-1.8 % from them), and eta's mass on the finest mesh is
+    kept to 1e-11 (periodic; rounding over about 30,000 steps)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", table)
+    tab = {int(r[0]): (float(r[1]), float(r[2])) for r in
+           (l.split() for l in open(path) if l.strip() and not l.startswith("#"))}
+    res = {}
+    sizes = list(rows) + [2 * rows[-1]]
+    for N in sizes:
+        pr = W.accuracy_test(N)
+        s = B.Solver(cfg_of(pr, scheme=scheme))
+        s.set_problem(pr.x, pr.E, pr.hu, pr.b, pr.profile, q0_is_eta=True)
+        while s.advance(4096) == 4096:  # chunks: steps past t_end are no-ops, but still launched
+            pass
+        g = s.state()
+        assert s.status()[0] == 0 and abs(g["t"] - 0.1) < 1e-14
+        s.close()
+        res[N] = (g["eta"], g["hu"])
+        if N == sizes[-1]:
+            J0, J1 = np.diff(pr.x), np.diff(g["x"])
+            assert abs(np.sum(J1 * g["eta"]) - np.sum(J0 * pr.E)) < 1e-11 * np.sum(J0 * pr.E)
+    for N in rows:
+        a, b = res[N], res[2 * N]
+        got = [np.mean(np.abs(a[k] - 0.5 * (b[k][0::2] + b[k][1::2]))) for k in range(2)]
+        for x, paper in zip(got, tab[N]):
+            assert paper / 1.03 < x < paper * 1.03, (N, x, paper)
+
+
 def test_lake_at_rest_paper_smooth_bottom():
     pr = W.lake_at_rest(200, "smooth")
     g, st, r, bits = run_both(pr, 10 ** 6)
