@@ -145,8 +145,10 @@ swale_status swale_batch_set_problem(swale_ctx* ctx, int64_t B, const int64_t* o
  * status of the step itself is read with swale_get_status (or reported by swale_advance). */
 swale_status swale_step(swale_ctx* ctx, double* dt_out);
 
-/* Up to max_steps steps, replayed as CUDA graphs of fixed length; stops early at t_end.
- * Synchronises at the end and reports the steps actually taken in *steps_done (may be NULL).
+/* Up to max_steps steps, replayed as CUDA graphs of fixed length; stops early at t_end (with
+ * an end time the steps go out in chunks of 64 to 4096 steps, and the call returns once every
+ * instance has reached t_end or stopped on an error). Synchronises at the end and reports the
+ * steps actually taken in *steps_done (may be NULL).
  * Error contract: a step in which an error appears (a non-finite value, a non-positive width, a
  * non-positive linear weight, no finite dt, a bounded wait that gave up) is not committed: the
  * instance keeps the state, nodes, widths, time and step count of its last good step, and every

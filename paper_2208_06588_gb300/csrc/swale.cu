@@ -696,8 +696,32 @@ swale_status swale_advance(swale_ctx* ctx, int64_t max_steps, int64_t* steps_don
   long long s0 = 0;
   SW_CUDA(ctx, cudaMemcpyAsync(&s0, &ctx->D.S->steps, sizeof(s0), cudaMemcpyDeviceToHost, ctx->stream));
   SW_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (swale_status s = enqueue_steps(ctx, max_steps)) return s;
   std::vector<DevScalars> S;
+  const double t_end = ctx->cfg.t_end;
+  if (t_end > 0.0) {
+    // With an end time, the steps go out in chunks of growing length (64 .. 4096 steps); after
+    // each, the host reads the instances' scalars and stops once every instance has reached
+    // t_end or stopped on an error (the prologue's test), so that a generous max_steps does not
+    // launch a long tail of no-op steps.
+    int64_t left = max_steps, chunk = 64;
+    while (left > 0) {
+      const int64_t n = std::min(left, chunk);
+      if (swale_status s = enqueue_steps(ctx, n)) return s;
+      left -= n;
+      if (left == 0) break;
+      if (swale_status s = read_scalars(ctx, S)) return s;
+      bool idle = true;
+      for (const DevScalars& v : S)
+        if (!((v.status & kErrBits) || v.t >= t_end)) {
+          idle = false;
+          break;
+        }
+      if (idle) break;
+      chunk = std::min<int64_t>(2 * chunk, 4096);
+    }
+  } else {
+    if (swale_status s = enqueue_steps(ctx, max_steps)) return s;
+  }
   if (swale_status s = read_scalars(ctx, S)) return s;
   unsigned int bits = 0;
   for (const DevScalars& v : S) bits |= v.status;
