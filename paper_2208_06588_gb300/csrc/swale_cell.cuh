@@ -780,10 +780,10 @@ SWALE_HD SourceGeom source_geom(real Jm, real Jc, real iJm, real iJc, real iJp, 
 //   A24 = -(14 r_m^2 + 21 r_m + 9) / (70 r_p (1 + r_m) (1 + r_p)^2 (1 + r_m + r_p))
 //   A34 = -(r_m^2 (35 r_p^2 + 35 r_p + 14) + r_m (35 r_p^2 + 21 r_p + 7) + 14 r_p^2 + 7 r_p + 2)
 //         / (70 r_m r_p (1 + r_m) (1 + r_p))
-// (exact integrals of the cardinal functions: about 29 FP64 operations per cell, against 67 for
-// the product of the two interpolants in monomial form, and 40 for the six entries, which stage
-// 1 reads from the mesh cache). At rest (h = eta - b, eta constant) the form gives -g (eta (b_R - b_L) -
-// (b_R^2 - b_L^2) / 2), the pressure jump, as dh^T A db = -db^T A db = 0.
+// (exact integrals of the cardinal functions: about 29 FP64 instructions per cell, against 67
+// for the product of the two interpolants in monomial form, and about 41 for the six entries,
+// which stage 1 reads from the mesh cache). At rest (h = eta - b, eta constant) the form gives
+// -g (eta (b_R - b_L) - (b_R^2 - b_L^2) / 2), the pressure jump, as dh^T A db = -db^T A db = 0.
 struct SourceForm {
   real a02, a03, a04, a23, a24, a34;
 };
